@@ -1,0 +1,557 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each ``pin_*`` function builds small seeded inputs, runs the oracle (the default
+build, or a build with a planted mistake passed as ``L``) and raises
+``AssertionError`` when the oracle departs from a closed form, an invariant, a
+textbook special case or an exact identity.  None of them retypes an oracle
+formula: they compare it with analytic solutions (Ritter, Savage-Hutter),
+conservation and symmetry laws, and differential-geometric identities.
+
+Citations are to arXiv:2104.06784 (App. A equations by label, Sect. 2.1-2.2).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from oracle.oracle import OracleSim
+from paper_2104_06784_gb300 import workloads as W
+
+G = 9.81
+
+
+def _sim(dem, dx, dy, params, L):
+    return OracleSim(dem, dx, dy, params, library=L)
+
+
+def _pure_fluid(**over):
+    return W.default_params(**over)
+
+
+def _pure_solid(**over):
+    p = W.default_params(rho_f=0.0, **over)  # alpha_rho = 0
+    return p
+
+
+# ----------------------------------------------------------------------------
+# geometry (Sect. 2.1; App. A: J_b = det Omega_b, (A_ij) = Omega_b^-1, n, c = n_Z)
+
+
+def pin_geometry_plane(L=None):
+    """Inclined planes: J = sec(zeta), c = cos(zeta), n = (sin z cos t,
+    sin z sin t, cos z), the 2x2 block of Omega_b^-1 inverts the surface metric
+    g = I + grad b grad b^T, dn = 0, and v_xi = v_X, v_eta = v_Y."""
+    nx, ny, dx = 12, 10, 3.0
+    for zeta in (0.0, 20.0, 35.0, 60.0):
+        for theta in (0.0, 37.0, 90.0, 200.0):
+            tz, th = math.radians(zeta), math.radians(theta)
+            x = (np.arange(nx) + 0.5) * dx
+            y = (np.arange(ny) + 0.5) * dx
+            X, Y = np.meshgrid(x, y)
+            dem = -math.tan(tz) * (X * math.cos(th) + Y * math.sin(th))
+            s = _sim(dem, dx, dx, W.default_params(), L)
+            g = s.geometry()
+            tol = 1e-12
+            assert np.allclose(g["J"], 1 / math.cos(tz), rtol=tol, atol=0), "J_b != sec(zeta)"
+            assert np.allclose(g["c"], math.cos(tz), rtol=tol, atol=tol), "c != cos(zeta)"
+            n_ex = (math.sin(tz) * math.cos(th), math.sin(tz) * math.sin(th), math.cos(tz))
+            for k, name in enumerate(("nX", "nY", "nZ")):
+                assert np.allclose(g[name], n_ex[k], atol=tol), f"{name} wrong"
+            bx = -math.tan(tz) * math.cos(th)
+            by = -math.tan(tz) * math.sin(th)
+            gm = np.array([[1 + bx * bx, bx * by], [bx * by, 1 + by * by]])
+            A = np.array([[g["A11"][3, 4], g["A12"][3, 4]], [g["A21"][3, 4], g["A22"][3, 4]]])
+            assert np.allclose(A @ gm, np.eye(2), atol=1e-12), "A is not the inverse metric"
+            for name in ("dnX_dxi", "dnY_dxi", "dnZ_dxi", "dnX_deta", "dnY_deta", "dnZ_deta"):
+                assert np.abs(g[name]).max() < 1e-12, f"{name} != 0 on a plane"
+            vx, vy = 1.7, -0.6
+            xi, eta = s.tangential(4, 3, vx, vy)
+            assert abs(xi - vx) < 1e-13 and abs(eta - vy) < 1e-13, "v_xi != v_X under xi = X"
+    # the incline along X: A = diag(cos^2 zeta, 1)
+    s = _sim(W.incline_dem(8, 6, 2.0, 2.0, 30.0), 2.0, 2.0, W.default_params(), L)
+    g = s.geometry()
+    assert np.allclose(g["A11"], math.cos(math.radians(30)) ** 2, atol=1e-14)
+    assert np.allclose(g["A22"], 1.0, atol=1e-14)
+
+
+def pin_curvature(L=None):
+    """kappa (App. A, below Eq. Src_nd_Topo) is the normal curvature times the
+    squared 3D speed, negative on a concave bed: on a quadratic surface it
+    equals -II(v, v)/|m| exactly; on the arc of radius R it tends to -V^2/R."""
+    # quadratic surface: second differences are exact there
+    nx, ny, dx = 20, 18, 4.0
+    cxx, cxy, cyy = 0.004, -0.0015, 0.0025
+    dem = W.paraboloid_dem(nx, ny, dx, dx, cxx, cxy, cyy)
+    s = _sim(dem, dx, dx, W.default_params(), L)
+    x = (np.arange(nx) + 0.5) * dx - nx * dx / 2
+    y = (np.arange(ny) + 0.5) * dx - ny * dx / 2
+    for (i, j) in ((3, 4), (10, 9), (16, 2)):
+        bX = cxx * x[i] + cxy * y[j]
+        bY = cxy * x[i] + cyy * y[j]
+        for (vx, vy) in ((2.0, 0.0), (-1.0, 3.0), (0.7, -2.2)):
+            ex = -(cxx * vx * vx + 2 * cxy * vx * vy + cyy * vy * vy) / math.sqrt(1 + bX * bX + bY * bY)
+            got = s.kappa(i, j, vx, vy)
+            assert abs(got - ex) <= 1e-12 * (abs(ex) + 1e-12), f"kappa {got} != {ex} on a paraboloid"
+    # a unit normal's derivatives are orthogonal to it: n . dn/dxi = n . dn/deta = 0
+    g = s.geometry()
+    for d in ("dxi", "deta"):
+        dot = g["nX"] * g[f"dnX_{d}"] + g["nY"] * g[f"dnY_{d}"] + g["nZ"] * g[f"dnZ_{d}"]
+        assert np.abs(dot).max() < 1e-15, f"n . dn/{d} != 0"
+    # circular arc (radius 100 m): kappa -> -V^2/R with O(dy^2) error
+    errs = []
+    for dy in (2.0, 1.0):
+        ny = int(400 / dy)
+        dem = W.arc_plane_dem(4, ny, dy, dy)
+        s = _sim(dem, dy, dy, W.default_params(), L)
+        y = (np.arange(ny) + 0.5) * dy
+        j = int(np.argmin(np.abs(y - 228.0)))  # inside the arc (200 .. 257 m)
+        by = (y[j] - 200.0) / math.sqrt(100.0 ** 2 - (y[j] - 200.0) ** 2)
+        vy = 5.0
+        V2 = vy * vy * (1 + by * by)
+        errs.append(abs(s.kappa(1, j, 0.0, vy) + V2 / 100.0) / (V2 / 100.0))
+    assert errs[-1] < 1e-3, f"arc curvature error {errs[-1]}"
+    assert errs[0] / max(errs[1], 1e-300) > 3.0, f"arc curvature not second order: {errs}"
+
+
+# ----------------------------------------------------------------------------
+# conservation (Eqs. MassEq_TopoS0/F0) with closed boundaries
+
+
+def pin_conservation_closed(L=None, steps=300):
+    cfg = W.release_config(cfl=0.1)
+    s = _sim(cfg["dem"], cfg["dx"], cfg["dy"], cfg["params"], L)
+    s.set_release(cfg["h"], cfg["phi_s"])
+    b0 = s.budget()
+    s.step(steps)
+    b = s.budget()
+    assert b["clamp_cells"] == 0, "positivity clamp fired at CFL 0.1"
+    for ph in ("s", "f"):
+        rel = abs(b[f"vol_{ph}"] - b0[f"vol_{ph}"]) / b0[f"vol_{ph}"]
+        assert rel < 1e-13, f"phase {ph} volume drift {rel}"
+    # symmetric pile on an X-invariant bed: no net X momentum
+    assert abs(b["mom_xs"]) < 1e-9 * abs(b["mom_ys"]) and abs(b["mom_xf"]) < 1e-9 * abs(b["mom_yf"])
+    assert b["mom_ys"] < 0 and b["mom_yf"] < 0, "pile does not move downslope (south)"
+
+
+# ----------------------------------------------------------------------------
+# bodies at rest
+
+
+def pin_lake_flat(L=None):
+    nx = ny = 16
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, _pure_fluid(), L)
+    s.set_release(np.full((ny, nx), 2.0), np.zeros((ny, nx)))
+    U0 = s.get_U()
+    s.step(20)
+    U = s.get_U()
+    assert np.abs(U[[1, 2, 4, 5]]).max() == 0.0, "flat lake moved"
+    assert np.abs(U - U0).max() < 1e-14
+
+
+def _plane_equilibrium(L, phi_s, delta_b, zeta=20.0, fluid_pg_mode=0):
+    """Depth with dh/dX = sin(zeta)/cos^2(zeta): the leading-order model's own
+    hydrostatic state of a fluid on a plane (dh/ds = tan(zeta) along slope).
+    Returns the largest interior momentum after two steps and its scale."""
+    nx, ny, dx, dt = 64, 5, 2.0, 0.05
+    dem = W.incline_dem(nx, ny, dx, dx, zeta)
+    tz = math.radians(zeta)
+    x = (np.arange(nx) + 0.5) * dx
+    h = np.broadcast_to(2.0 + x * math.sin(tz) / math.cos(tz) ** 2, (ny, nx)).copy()
+    p = W.default_params(delta_b_deg=delta_b, bc=(W.BC_TRANSMISSIVE,) * 4, fluid_pg_mode=fluid_pg_mode)
+    s = _sim(dem, dx, dx, p, L)
+    s.set_release(h, np.full((ny, nx), phi_s))
+    s.step_dt(dt)
+    s.step_dt(dt)
+    U = s.get_U()
+    inner = U[:, :, 12:nx - 12]
+    scale = dt * G * h.max() * math.sin(tz) * (1 / math.cos(tz))
+    return max(np.abs(inner[[1, 2, 4, 5]]).max(), 0.0), scale
+
+
+def pin_lake_plane(L=None):
+    m, scale = _plane_equilibrium(L, phi_s=0.0, delta_b=25.0)
+    assert m < 1e-12 * scale, f"fluid equilibrium on a plane moved: {m}"
+
+
+def pin_mixture_plane_rest(L=None):
+    """Mixture (phi^s = 0.6) in the fluid's equilibrium on a 20 deg plane with
+    basal friction strong enough to hold the grains: stays at rest only if the
+    fluid feels -phi^f grad P overall, i.e. the pressure-gradient source of the
+    fluid carries phi^s (reading R1 of Eq. SrcF_f_Topo)."""
+    m, scale = _plane_equilibrium(L, phi_s=0.6, delta_b=25.0)
+    assert m < 1e-12 * scale, f"mixture equilibrium on a plane moved: {m}"
+
+
+def pin_heap_rest(L=None):
+    """Pure-solid parabolic heap (surface slope 0.1 < tan 25 deg) on a flat bed
+    and on a 20 deg plane: every cell of the heap stays exactly at rest
+    (Coulomb stopping, Eq. Src_nd_Topo).  The central scheme's numerical
+    diffusion wets the margin, where the neighbour's face pressure pushes cells
+    whose friction was zero at the stage start; that creep must die out (Heun
+    halves a stopped cell's momentum each step).  On a 30 deg plane the heap
+    slides (sin 30 > cos 30 tan 25)."""
+    nx = ny = 48
+    dx = 5.0
+    h = W.parabolic_cap(nx, ny, dx, dx, 24, 24, 20, 5.0)
+    heap = h > 0
+    for dem, moves in ((W.flat_dem(nx, ny), False), (W.incline_dem(nx, ny, dx, dx, 20.0), False),
+                       (W.incline_dem(nx, ny, dx, dx, 30.0), True)):
+        s = _sim(dem, dx, dx, _pure_solid(delta_b_deg=25.0), L)
+        s.set_release(h, np.ones((ny, nx)))
+        s.step(30)
+        U = s.get_U()
+        mom = np.abs(U[1:3]).max(axis=0)
+        if moves:
+            assert mom[heap].max() > 1e-2, "heap held on a 30 deg plane with a 25 deg friction angle"
+            continue
+        assert mom[heap].max() == 0.0, f"heap at rest moved ({mom[heap].max()})"
+        s.step(70)
+        pr = s.primitive()
+        assert np.abs(s.get_U()[1:3])[:, heap].max() == 0.0, "heap at rest moved"
+        vmax = max(np.abs(pr[k]).max() for k in ("vx_s", "vy_s"))
+        assert vmax < 1e-15, f"margin creep does not die out ({vmax} m/s)"
+
+
+# ----------------------------------------------------------------------------
+# Ritter dam break: pure fluid, flat, frictionless (exact shallow-water solution)
+
+
+def _ritter_error(L, dx, t_end=20.0, h0=10.0, length=2000.0):
+    nx = int(length / dx)
+    x = (np.arange(nx) + 0.5) * dx - length / 2
+    h = np.where(x < 0, h0, 0.0)[None, :]
+    s = _sim(W.flat_dem(nx, 1), dx, dx, _pure_fluid(cfl=0.1), L)
+    s.set_release(h, np.zeros((1, nx)))
+    while s.t < t_end:
+        s.step(10)
+    t = s.t
+    c0 = math.sqrt(G * h0)
+    ex = np.where(x < -c0 * t, h0, np.where(x > 2 * c0 * t, 0.0, (2 * c0 - x / t) ** 2 / (9 * G)))
+    num = s.primitive()["h"][0]
+    return np.abs(num - ex).sum() / ex.sum()
+
+
+def pin_ritter(L=None):
+    e10 = _ritter_error(L, 10.0)
+    e5 = _ritter_error(L, 5.0)
+    assert e5 < 0.01, f"Ritter L1 error {e5} at 400 cells"
+    assert e5 < 0.75 * e10, f"Ritter error does not converge: {e10} -> {e5}"
+
+
+# ----------------------------------------------------------------------------
+# Savage-Hutter similarity solution (pure solid, K = 1, plane at zeta)
+
+
+def _sh_reference(t_end, H0, L0, zeta, delta):
+    """Centre s_c and half-length L of the parabolic cap: s_c'' = g (sin z -
+    tan d cos z), L'' = 2 g cos z H0 L0 / L^2 (RK4, fine steps)."""
+    a = G * (math.sin(zeta) - math.tan(delta) * math.cos(zeta))
+    k = 2 * G * math.cos(zeta) * H0 * L0
+
+    def f(y):
+        return np.array([y[1], k / y[0] ** 2])
+
+    y = np.array([L0, 0.0])
+    n = 20000
+    h = t_end / n
+    for _ in range(n):
+        k1 = f(y)
+        k2 = f(y + 0.5 * h * k1)
+        k3 = f(y + 0.5 * h * k2)
+        k4 = f(y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return 0.5 * a * t_end ** 2, y[0]
+
+
+def pin_savage_hutter(L=None):
+    zeta, delta = math.radians(35.0), math.radians(25.0)
+    H0, L0, dx = 5.0, 100.0, 1.0
+    nx = 1400
+    x = (np.arange(nx) + 0.5) * dx
+    X0 = 200.0
+    h = H0 * np.clip(1 - ((x - X0) / (L0 * math.cos(zeta))) ** 2, 0, None)
+    s = _sim(W.incline_dem(nx, 1, dx, dx, 35.0), dx, dx, _pure_solid(delta_b_deg=25.0, cfl=0.1), L)
+    s.set_release(h[None, :], np.ones((1, nx)))
+    t_end = 8.0
+    while s.t < t_end:
+        s.step(5)
+    ds_ref, L_ref = _sh_reference(s.t, H0, L0, zeta, delta)
+    U1 = s.get_U()[0, 0]
+    sc = x / math.cos(zeta)  # arc length along the slope
+    m = U1.sum()
+    c = (sc * U1).sum() / m
+    var = ((sc - c) ** 2 * U1).sum() / m
+    ds = c - X0 / math.cos(zeta)
+    Lnum = math.sqrt(5 * var)  # parabola: variance = L^2 / 5
+    assert abs(ds - ds_ref) / ds_ref < 5e-3, f"SH centre travel {ds} vs {ds_ref}"
+    assert abs(Lnum - L_ref) / (L_ref - L0) < 0.05, f"SH half-length {Lnum} vs {L_ref}"
+
+
+# ----------------------------------------------------------------------------
+# interphase drag (Eqs. Src_v_Topo, SrcF_v_Topo)
+
+
+def pin_drag(L=None):
+    """Uniform mixture on a flat, frictionless bed: rho^s q^s + rho^f q^f is
+    conserved, and v^f - v^s decays by the Heun factor 1 - z + z^2/2 per step
+    with z = c_D (phi^s + alpha phi^f) dt."""
+    nx = ny = 6
+    cd, dt, phs = 0.8, 0.1, 0.6
+    p = W.default_params(c_d=cd, delta_b_deg=0.0, bc=(W.BC_TRANSMISSIVE,) * 4)
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, p, L)
+    one = np.ones((ny, nx))
+    s.set_release(2.0 * one, phs * one, 1.0 * one, 0.5 * one, 3.0 * one, -1.0 * one)
+    al = p["rho_f"] / p["rho_s"]
+    z = cd * (phs + al * (1 - phs)) * dt
+    U0 = s.get_U()
+    mix0 = p["rho_s"] * U0[1:3] + p["rho_f"] * U0[4:6]
+    n = 12
+    for _ in range(n):
+        s.step_dt(dt)
+    pr = s.primitive()
+    fac = (1 - z + z * z / 2) ** n
+    for comp, d0 in (("x", 2.0), ("y", -1.5)):
+        dv = pr[f"v{comp}_f"] - pr[f"v{comp}_s"]
+        assert np.allclose(dv, d0 * fac, rtol=1e-12, atol=0), f"drag decay {dv.flat[0]} vs {d0 * fac}"
+    U = s.get_U()
+    mix = p["rho_s"] * U[1:3] + p["rho_f"] * U[4:6]
+    assert np.allclose(mix, mix0, rtol=1e-13, atol=1e-12 * np.abs(mix0).max()), "drag not momentum-neutral"
+
+
+# ----------------------------------------------------------------------------
+# wave speeds and the CFL time step (Sect. 2.2; reading R7)
+
+
+def pin_wave_speed(L=None):
+    """At rest: shallow-water celerity sqrt(g h) for a pure fluid and for a
+    pure solid without buoyancy (K = 1); on an X-incline sqrt(g cos z h) across
+    the slope; moving fluid adds |v|; dt = CFL min(dx, dy) / a_max."""
+    nx, ny = 5, 4
+    one = np.ones((ny, nx))
+    s = _sim(W.flat_dem(nx, ny), 5.0, 4.0, _pure_fluid(cfl=0.1), L)
+    s.set_release(2.0 * one, 0 * one)
+    assert abs(s.max_speed() - math.sqrt(G * 2.0)) < 1e-14
+    assert abs(s.cfl_dt() - 0.1 * 4.0 / math.sqrt(G * 2.0)) < 1e-15
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, _pure_solid(), L)
+    s.set_release(3.0 * one, one)
+    assert abs(s.max_speed() - math.sqrt(G * 3.0)) < 1e-14
+    s = _sim(W.incline_dem(nx, ny, 5.0, 5.0, 30.0), 5.0, 5.0, _pure_fluid(), L)
+    s.set_release(2.0 * one, 0 * one)
+    assert abs(s.max_speed() - math.sqrt(G * math.cos(math.radians(30)) * 2.0)) < 1e-13
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, _pure_fluid(), L)
+    s.set_release(2.0 * one, 0 * one, None, None, -3.0 * one, 1.0 * one)
+    assert abs(s.max_speed() - (3.0 + math.sqrt(G * 2.0))) < 1e-13
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, _pure_fluid(dt_max=0.7), L)
+    s.set_release(0 * one, 0 * one)
+    assert s.max_speed() == 0.0 and s.cfl_dt() == 0.7, "dry domain must take dt_max"
+
+
+# ----------------------------------------------------------------------------
+# 90 degree rotation invariance
+
+
+def _rot(f):
+    """(X, Y) -> (L - Y, X) on a square grid: f'[j', i'] = f[n - 1 - i', j']."""
+    return np.ascontiguousarray(f[::-1, :].T)
+
+
+def pin_rotation(L=None, steps=40):
+    n = 40
+    cfg = W.release_config(nx=n, ny=n, cfl=0.2)
+    rng = np.random.default_rng(3)
+    phi = rng.uniform(0.4, 0.7, (n, n))
+    h = cfg["h"] * (1 + 0.2 * rng.random((n, n)))
+    dem = cfg["dem"] + rng.random((n, n))
+    a = _sim(dem, 5.0, 5.0, cfg["params"], L)
+    a.set_release(h, phi)
+    b = _sim(_rot(dem), 5.0, 5.0, cfg["params"], L)
+    b.set_release(_rot(h), _rot(phi))
+    for _ in range(steps):
+        dt = a.cfl_dt()
+        dtb = b.cfl_dt()
+        assert abs(dt - dtb) <= 1e-14 * dt, "rotated run takes a different dt"
+        a.step_dt(dt)
+        b.step_dt(dt)
+    Ua, Ub = a.get_U(), b.get_U()
+    exp = np.stack([_rot(Ua[0]), -_rot(Ua[2]), _rot(Ua[1]), _rot(Ua[3]), -_rot(Ua[5]), _rot(Ua[4])])
+    scale = np.abs(Ua).max()
+    err = np.abs(Ub - exp).max() / scale
+    assert err < 1e-12, f"rotation invariance broken: {err}"
+
+
+# ----------------------------------------------------------------------------
+# Mode-II inflow (Sect. 3.1.2; reading R11) and budgets
+
+
+def pin_inflow(L=None):
+    """The ghost state carries the unit discharge Q/W at critical depth
+    (v_n equals the model's celerity sqrt(g c A_nn h)); the volume balance
+    closes: volume(t) = time-integrated boundary flux + clamp volume."""
+    cfg = W.inflow_config(nx=64, ny=40, dx=5.0, inlet_cells=8)
+    s = _sim(cfg["dem"], cfg["dx"], cfg["dy"], cfg["params"], L)
+    f = cfg["inflow"]
+    s.set_inflow(f["side"], f["i0"], f["i1"], f["t"], f["Q"], f["phi"])
+    for tt in (30.0, 60.0, 150.0):
+        Q = np.interp(tt, f["t"], f["Q"])
+        q = Q / ((f["i1"] - f["i0"]) * cfg["dy"])
+        for gi in (-1, -2):
+            u = s.inflow_state(0, gi, f["i0"] + 2, tt)
+            gm = s.cell_geom(gi, f["i0"] + 2)
+            Jh = u[0] + u[3]
+            vn = (u[1] + u[4]) / Jh
+            assert abs(Jh * vn - q) < 1e-12 * q, "inflow ghost does not carry Q/W"
+            h = Jh / gm["J"]
+            cel = math.sqrt(G * gm["c"] * gm["A11"] * h)
+            assert abs(vn - cel) < 1e-12 * cel, "inflow ghost is not at critical depth"
+            assert abs(u[0] / Jh - 0.5) < 1e-15
+    assert np.all(s.inflow_state(0, -1, f["i0"], 400.0) == 0.0), "no inflow after the hydrograph ends"
+    while s.t < 40.0:
+        s.step(20)
+    b = s.budget()
+    for ph in ("s", "f"):
+        vol = b[f"vol_{ph}"]
+        assert vol > 0
+        assert abs(vol - b[f"bnd_in_{ph}"] - b[f"clamp_{ph}"]) < 1e-12 * vol, "volume budget does not close"
+
+
+# ----------------------------------------------------------------------------
+# Coulomb friction and the curvature term in the basal pressure
+
+
+def pin_friction(L=None):
+    """(a) A uniform pure-solid layer sliding on a 30 deg plane (delta_b = 20
+    deg): one stage changes J h^s v_X^s = h v_s by dt h g (sin z -+ cos z tan d)
+    (friction opposes the motion, downslope or upslope).  (b) At the bottom of
+    a concave parabolic bed of radius R the basal pressure is h (g + V^2/R)
+    (centripetal term, Eq. Src_nd_Topo with kappa < 0), so one stage removes
+    dt h (g + V^2/R) tan d of momentum.  (c) Over a convex crest with V^2/R > g
+    the layer lifts off: p_b is clamped at 0 and no friction acts."""
+    zeta, delta, h, dt = 30.0, 20.0, 2.0, 0.05
+    tz, td = math.radians(zeta), math.radians(delta)
+    nx, ny, dx = 8, 6, 2.0
+    one = np.ones((ny, nx))
+    p = _pure_solid(delta_b_deg=delta, bc=(W.BC_TRANSMISSIVE,) * 4)
+    for vs in (4.0, -4.0):
+        s = _sim(W.incline_dem(nx, ny, dx, dx, zeta), dx, dx, p, L)
+        s.set_release(h * one, one, vs * math.cos(tz) * one, 0 * one)
+        U0 = s.get_U()
+        out = s.stage(0.0, dt)
+        dq = G * h * (math.sin(tz) - math.copysign(1.0, vs) * math.cos(tz) * math.tan(td))
+        assert np.allclose(out[1], U0[1] + dt * dq, rtol=1e-12, atol=0), "slide on a plane: wrong acceleration"
+        assert np.abs(out[2]).max() == 0.0
+    R, V = 10.0, 12.0
+    nx = 21
+    x = (np.arange(nx) + 0.5) * dx
+    X0 = x[nx // 2]
+    for sign in (1.0, -1.0):
+        dem = np.broadcast_to(sign * (x - X0) ** 2 / (2 * R), (3, nx)).copy()
+        q = _sim(dem, dx, dx, p, L)
+        U = np.zeros((6, 3, nx))
+        U[0] = h
+        U[1] = h * V
+        q.set_U(U)
+        out = q.stage(0.0, dt)
+        got = out[1, 1, nx // 2]
+        if sign > 0:
+            exp = h * V - dt * h * (G + V * V / R) * math.tan(td)
+            assert abs(got - exp) < 1e-12 * h * V, f"centripetal basal pressure: {got} vs {exp}"
+        else:
+            assert V * V / R > G
+            assert abs(got - h * V) < 1e-12 * h * V, "lift-off: friction must vanish when p_b < 0"
+
+
+def pin_closed_box(L=None, steps=400):
+    """A mixture column released in the middle of a closed box on an oblique
+    plane reaches all four walls; each phase's volume is conserved to
+    round-off and the clamp never fires at CFL 0.1."""
+    nx, ny, dx = 30, 24, 2.0
+    x = (np.arange(nx) + 0.5) * dx
+    y = (np.arange(ny) + 0.5) * dx
+    X, Y = np.meshgrid(x, y)
+    dem = 0.04 * X + 0.03 * Y
+    h = W.parabolic_cap(nx, ny, dx, dx, 15, 12, 6, 4.0)
+    s = _sim(dem, dx, dx, W.default_params(cfl=0.1, delta_b_deg=10.0), L)
+    s.set_release(h, np.full((ny, nx), 0.55))
+    b0 = s.budget()
+    s.step(steps)
+    b = s.budget()
+    pr = s.primitive()
+    assert min(pr["h"][:, 0].max(), pr["h"][:, -1].max(), pr["h"][0].max(), pr["h"][-1].max()) > 1e-3, \
+        "flow did not reach every wall"
+    assert b["clamp_cells"] == 0
+    for ph in ("s", "f"):
+        rel = abs(b[f"vol_{ph}"] - b0[f"vol_{ph}"]) / b0[f"vol_{ph}"]
+        assert rel < 1e-13, f"closed box: phase {ph} volume drift {rel}"
+
+
+# ----------------------------------------------------------------------------
+# fluid viscosity (Eq. SrcF_vis_Topo) and fluid basal friction (Eq. SrcF_nd_Topo)
+
+
+def pin_viscous(L=None):
+    """On a flat bed (A = I, J = 1) with uniform depth the viscous source of a
+    sinusoidal shear or stretch of the fluid velocity is nu phi^f times
+    h v'' (shear) or 2 h v'' (stretch along the component's own axis), with
+    v'' = -k^2 v; second-order accurate at 32 cells per wavelength."""
+    n, dx, h, V, nu, dt = 64, 1.0, 1.5, 0.8, 0.3, 1e-3
+    k = 2 * math.pi / (32 * dx)
+    c = (np.arange(n) + 0.5) * dx
+    Xc, Yc = np.meshgrid(c, c)
+    cases = (("vx_f", Yc, 4, 1.0), ("vx_f", Xc, 4, 2.0), ("vy_f", Xc, 5, 1.0), ("vy_f", Yc, 5, 2.0))
+    for name, coord, comp, factor in cases:
+        outs = []
+        for nuv in (0.0, nu):
+            p = _pure_fluid(nu_f=nuv, bc=(W.BC_TRANSMISSIVE,) * 4)
+            s = _sim(W.flat_dem(n, n), dx, dx, p, L)
+            vel = {"vx_f": None, "vy_f": None}
+            vel[name] = V * np.sin(k * coord)
+            s.set_release(np.full((n, n), h), np.zeros((n, n)), None, None, vel["vx_f"], vel["vy_f"])
+            outs.append(s.stage(0.0, dt)[comp])
+        S = (outs[1] - outs[0]) / dt
+        ex = -factor * nu * h * k * k * V * np.sin(k * coord)
+        inner = (slice(6, n - 6), slice(6, n - 6))
+        err = np.abs(S[inner] - ex[inner]).max() / np.abs(ex[inner]).max()
+        assert err < 5e-3, f"viscous term {name}({'Y' if coord is Yc else 'X'}): error {err}"
+
+
+def pin_fluid_friction(L=None):
+    """Uniform pure-fluid flow on a flat bed with fluid basal friction k_f:
+    dv/dt = -k_f v, so v is multiplied by the Heun factor 1 - z + z^2/2,
+    z = k_f dt, at each step."""
+    n, kf, dt = 6, 0.5, 0.1
+    one = np.ones((n, n))
+    s = _sim(W.flat_dem(n, n), 5.0, 5.0, _pure_fluid(k_f=kf, bc=(W.BC_TRANSMISSIVE,) * 4), L)
+    s.set_release(2.0 * one, 0 * one, None, None, 3.0 * one, -2.0 * one)
+    for _ in range(10):
+        s.step_dt(dt)
+    z = kf * dt
+    fac = (1 - z + z * z / 2) ** 10
+    pr = s.primitive()
+    assert np.allclose(pr["vx_f"], 3.0 * fac, rtol=1e-13) and np.allclose(pr["vy_f"], -2.0 * fac, rtol=1e-13)
+
+
+def pin_mixture_no_separation(L=None):
+    """A uniform mixture (phi^s = 0.6) at rest on a flat, frictionless bed with
+    a linear depth gradient moves as one fluid: the solid's own pressure
+    (factor 1 - alpha_rho) plus its buoyancy (alpha_rho phi^s grad P, Eq.
+    Src_f_Topo) and the fluid's pressure minus the reaction phi^s grad P (R1)
+    give both phases the acceleration -g dh/dX, so no drag arises."""
+    nx, ny, dx, dt, slope = 40, 5, 2.0, 0.02, 0.01
+    x = (np.arange(nx) + 0.5) * dx
+    h = np.broadcast_to(2.0 + slope * x, (ny, nx)).copy()
+    p = W.default_params(delta_b_deg=0.0, bc=(W.BC_TRANSMISSIVE,) * 4)
+    s = _sim(W.flat_dem(nx, ny), dx, dx, p, L)
+    s.set_release(h, np.full((ny, nx), 0.6))
+    out = s.stage(0.0, dt)
+    inner = (slice(None), slice(4, nx - 4))
+    vs = out[1][inner] / out[0][inner]
+    vf = out[4][inner] / out[3][inner]
+    ex = -dt * G * slope
+    assert np.allclose(vs, ex, rtol=1e-12, atol=0), f"solid acceleration {vs.flat[0] / dt} vs {ex / dt}"
+    assert np.allclose(vf, ex, rtol=1e-12, atol=0), f"fluid acceleration {vf.flat[0] / dt} vs {ex / dt}"
+
+
+ALL_PINS = [pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
+            pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag, pin_wave_speed,
+            pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction]

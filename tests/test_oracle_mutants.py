@@ -1,0 +1,129 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case copies ``oracle/oracle.c`` to a temporary directory, plants one
+plausible mistake (a dropped term, a wrong sign, index or factor, a transposed
+operand), compiles it on the CPU and runs the pins of ``oracle_pins`` against
+it.  At least one pin must fail, which shows the pins constrain that part of
+the oracle.  Nothing here touches a GPU.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+from oracle import oracle as O
+from tests import oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
+
+# (what the mistake is, text in oracle.c, replacement)
+MUTANTS = [
+    ("solid buoyancy dropped (Eq. Src_f_Topo)",
+     "double sf_s = -p->eps * al * phs * grad;", "double sf_s = 0.0 * grad;"),
+    ("fluid pressure-gradient source as printed, phi^f (R1 undone)",
+     "double fpg = (p->fluid_pg_mode == 1) ? phf : phs;", "double fpg = phf;"),
+    ("A_11 dropped from the solid pressure flux",
+     "F[1] = J * hs * vXs * vns + p->eps * J * h * Ad1 * Ns;", "F[1] = J * hs * vXs * vns + p->eps * J * h * Ns;"),
+    ("c dropped from the mean fluid pressure",
+     "double pf = p->g * c * h / 2.0;", "double pf = p->g * h / 2.0;"),
+    ("(1 - alpha) dropped from the solid pressure",
+     "double Ns = p->g * c * (1.0 - al) * hs / 2.0;", "double Ns = p->g * c * hs / 2.0;"),
+    ("KT numerical diffusion with the wrong sign",
+     "- 0.5 * a * (up[c] - um[c]);", "+ 0.5 * a * (up[c] - um[c]);"),
+    ("maxmod instead of minmod",
+     "return (a > 0.0) ? fmin(a, b) : fmax(a, b);", "return (a > 0.0) ? fmax(a, b) : fmin(a, b);"),
+    ("slopes not halved at the faces",
+     "um[c] = uL + 0.5 * sL;", "um[c] = uL + sL;"),
+    ("Heun average replaced by the second stage",
+     "s->U[c][k] = 0.5 * (s->U[c][k] + s->W2[c][k]);", "s->U[c][k] = s->W2[c][k];"),
+    ("solid drag with the wrong sign",
+     "double sv_s = J * al * p->c_d * phs * phf * h * (vf[m] - vs[m]);",
+     "double sv_s = J * al * p->c_d * phs * phf * h * (vs[m] - vf[m]);"),
+    ("alpha_rho dropped from the solid drag",
+     "double sv_s = J * al * p->c_d * phs * phf * h * (vf[m] - vs[m]);",
+     "double sv_s = J * p->c_d * phs * phf * h * (vf[m] - vs[m]);"),
+    ("fluid basal friction with the wrong sign",
+     "double sd_f = -J * phf * h * p->k_f * vf[m];", "double sd_f = J * phf * h * p->k_f * vf[m];"),
+    ("kappa without the v_Z term",
+     "for (int m = 0; m < 3; m++) k += v[m] * (G->dn[m][0] * xi + G->dn[m][1] * eta);",
+     "for (int m = 0; m < 2; m++) k += v[m] * (G->dn[m][0] * xi + G->dn[m][1] * eta);"),
+    ("kappa added to the basal pressure instead of subtracted",
+     "double pbs = hs * (p->g * c0 * (1.0 - al) - p->eps_chi * ks);",
+     "double pbs = hs * (p->g * c0 * (1.0 - al) + p->eps_chi * ks);"),
+    ("lift-off clamp of p_b removed",
+     "if (pbs < 0.0) pbs = 0.0;", "if (pbs < -1e300) pbs = 0.0;"),
+    ("chain-rule term of dn/dX dropped",
+     "out[k] = dm[k] / mm - m[k] * mdm / (mm2 * mm);", "out[k] = dm[k] / mm;"),
+    ("Omega_b^-1 entry transposed",
+     "R[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / d;",
+     "R[0][2] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / d;"),
+    ("central slope over dx instead of 2 dx",
+     "double bX = (B(i + 1, j) - B(i - 1, j)) / (2.0 * dx);", "double bX = (B(i + 1, j) - B(i - 1, j)) / dx;"),
+    ("face slope over 2 dx",
+     "double bX = (B(i + 1, j) - B(i, j)) / dx;", "double bX = (B(i + 1, j) - B(i, j)) / (2.0 * dx);"),
+    ("friction without tan(delta_b)",
+     "double Fr = dt * J * pbs * tanb;", "double Fr = dt * J * pbs;"),
+    ("friction without J_b",
+     "double Fr = dt * J * pbs * tanb;", "double Fr = dt * pbs * tanb;"),
+    ("friction speed without v_Z",
+     "double qn = sqrt(qX * qX + qY * qY + qZ * qZ);", "double qn = sqrt(qX * qX + qY * qY);"),
+    ("west wall keeps its normal momentum",
+     "U[1][IS(s, gw, j)] = -U[1][IS(s, gw, j)];", "U[1][IS(s, gw, j)] = U[1][IS(s, gw, j)];"),
+    ("north wall keeps its normal momentum",
+     "U[2][IS(s, i, gn)] = -U[2][IS(s, i, gn)];", "U[2][IS(s, i, gn)] = U[2][IS(s, i, gn)];"),
+    ("time step proportional to the wave speed",
+     "double dt = (amax > 0.0) ? s->p.cfl * dmin / amax : s->p.dt_max;",
+     "double dt = (amax > 0.0) ? s->p.cfl * dmin * amax : s->p.dt_max;"),
+    ("solid celerity without the 1/2",
+     "(1.0 - al) * (h + hs) / 2.0);", "(1.0 - al) * (h + hs));"),
+    ("inflow depth with a square root instead of a cube root",
+     "double hc = cbrt(q * q / (G->J * G->J * p->eps * p->g * G->c * Ann));",
+     "double hc = sqrt(q * q / (G->J * G->J * p->eps * p->g * G->c * Ann));"),
+    ("boundary budget read on the first interior face",
+     "bin[0] += (s->Hx[0][IS(s, -1, j)] - s->Hx[0][IS(s, nx - 1, j)]) * s->dy;",
+     "bin[0] += (s->Hx[0][IS(s, 0, j)] - s->Hx[0][IS(s, nx - 1, j)]) * s->dy;"),
+    ("viscous stretch term without its factor 2",
+     "double svX = 2.0 * (brX[1][0] - brX[0][0]) / s->dx", "double svX = 1.0 * (brX[1][0] - brX[0][0]) / s->dx"),
+    ("viscous shear bracket with A_22 dropped",
+     "brY[sd][0] = Jh * (A12 * dvx[0] + A22 * dvy[0] + A11 * dvx[1] + A21 * dvy[1]);",
+     "brY[sd][0] = Jh * (A12 * dvx[0] + A11 * dvx[1] + A21 * dvy[1]);"),
+    ("pressure-gradient difference over the wrong face",
+     "double dPxi = (s->Px[k] - s->Px[IS(s, i - 1, j)]) / s->dx;",
+     "double dPxi = (s->Px[k] - s->Px[IS(s, i, j)]) / s->dx;"),
+    ("mass flux uses v_eta on xi faces",
+     "double vns = d == 0 ? xs : es;", "double vns = es;"),
+]
+
+
+@pytest.fixture(scope="module")
+def tmpdir_mod():
+    with tempfile.TemporaryDirectory() as d:
+        yield d
+
+
+def _build_mutant(src_text: str, old: str, new: str, path: str):
+    assert src_text.count(old) >= 1, f"mutation anchor not found: {old}"
+    text = src_text.replace(old, new, 1)
+    c = path + ".c"
+    with open(c, "w") as f:
+        f.write(text)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", path, c, "-lm"])
+    return O.load(path)
+
+
+@pytest.mark.parametrize("what,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(what, old, new, tmpdir_mod):
+    src = open(SRC).read()
+    path = os.path.join(tmpdir_mod, f"mut{abs(hash(what)) % 10**8}.so")
+    L = _build_mutant(src, old, new, path)
+    failed = []
+    for pin in P.ALL_PINS:
+        try:
+            pin(L)
+        except Exception as e:  # AssertionError, or NaN/overflow surfacing as errors
+            failed.append(f"{pin.__name__}: {type(e).__name__}")
+            break
+    assert failed, f"planted mistake not caught by any pin: {what}"
