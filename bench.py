@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the two-phase shallow-flow step on one GB300 (cell-steps/s).
+
+Workload: the large-scale release event -- 4096 x 4096 cells at 10 m over a
+seeded 1/f^2.2 spectral DEM (1500 m relief) with one carved valley, a
+2.5e7 m^3 parabolic-cap release on a 30-40 degree slope, solid fraction
+U(0.55, 0.65), transmissive boundaries, CFL 0.1 (synthetic stand-in for the
+Hsiaolin event of Sect. 4.1; the real DEM is not available).
+
+A step is one full time step: CFL time step from the exact max-reduction, two
+stages of the central scheme with all sources, Heun average, boundary fill.
+The headline is the FP64 form; the FP32 form (FP64 budgets and friction test)
+is measured in the same run.  The state (0.8 GB in FP64) is larger than L2, so
+no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank advances its own replica of
+the workload (independent problems, weak scaling, no data-path collective);
+the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "cell-steps/s FP64 vs FP32 (% HBM roofline); ensemble cells/s; adjoint/fwd cost"
+UNIT = "cell-steps/s"
+N_SIDE = 4096
+DX = 10.0
+
+# Algorithmic work of one stage launch per cell (both counted from the
+# formulas of stage.cuh; see the design notes): floating-point operations
+# (add, sub, mul, div, sqrt = 1; fma = 2; comparisons, min/max, abs = 0) and
+# bytes that must cross HBM for one cell-step: read U^n (6 words), write
+# U^{n+1} (6), read the bed elevation (1).
+FLOPS_PER_CELL_STAGE = 488
+WORDS_PER_CELL_STEP = 13
+
+# DRAM traffic of one stage launch per cell from an ncu capture, valid only for
+# the stage kernel source it was taken on (sha256 of csrc/stage.cuh, first 12).
+TRAFFIC = {}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 vector peak of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+# = 1.26 TFLOP/s, matching the 1.25 TFLOP/s nominal figure.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def stage_hash():
+    with open(os.path.join(ROOT, "paper_2104_06784_gb300", "csrc", "stage.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+        return self
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def cpu_baseline(cfg, steps=None, window=1024):
+    """The FP64 oracle as it stands, single-threaded on the host, on a bounded
+    sample: `steps` steps on a window x window crop of the workload centred on
+    the release (throughput per cell-step does not depend on the size)."""
+    from oracle.oracle import OracleSim
+    ic, jc = cfg["release_cell"]
+    n = cfg["dem"].shape[0]
+    i0 = int(min(max(ic - window // 2, 0), n - window))
+    j0 = int(min(max(jc - window // 2, 0), n - window))
+    sl = (slice(j0, j0 + window), slice(i0, i0 + window))
+    o = OracleSim(cfg["dem"][sl], cfg["dx"], cfg["dy"], cfg["params"])
+    o.set_release(cfg["h"][sl], cfg["phi_s"][sl])
+    o.step(1)
+    steps = steps or 20
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    return dict(value=window * window * steps / el, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{steps} FP64 steps of the oracle on the {window}x{window} window of the "
+                       f"{n}x{n} workload around the release, 1 thread",
+                seconds=el)
+
+
+def run_reference(args, cfg, rank):
+    """The reference arm: the CPU oracle timed on the host, K steps after W
+    warm-up steps, each step one oracle step on a 1024 x 1024 window."""
+    if rank != 0:
+        return None
+    from oracle.oracle import OracleSim
+    window = 1024
+    ic, jc = cfg["release_cell"]
+    n = cfg["dem"].shape[0]
+    i0 = int(min(max(ic - window // 2, 0), n - window))
+    j0 = int(min(max(jc - window // 2, 0), n - window))
+    sl = (slice(j0, j0 + window), slice(i0, i0 + window))
+    o = OracleSim(cfg["dem"][sl], cfg["dx"], cfg["dy"], cfg["params"])
+    o.set_release(cfg["h"][sl], cfg["phi_s"][sl])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = window * window * args.steps / el
+    sample = f"each step: one FP64 oracle step on the {window}x{window} window of the {n}x{n} workload, 1 thread"
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(cfg, args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def config_dict(cfg, args):
+    n = cfg["dem"].shape[0]
+    return {"workload": f"large-scale release event, {n}x{n} cells at {DX:g} m, spectral DEM "
+                        f"(beta 2.2, 1500 m relief, carved valley), 2.5e7 m^3 release, CFL 0.1",
+            "cells": n * n, "dx_m": DX, "l2": "state larger than L2 (0.8 GB FP64, 0.4 GB FP32); no flush",
+            "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def measure(sim, cells, K, W, torch):
+    """Device time of K steps (after W warm-up steps) with CUDA events on the
+    simulation's stream; per-stage launch times from moses_step_timed."""
+    sim.step(W)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # per-launch timing of the stage kernel over K more steps
+    _, stage_ms = sim.step_timed(K)
+    return ms, stage_ms
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (the workload is defined at 4096)")
+    ap.add_argument("--only", choices=["f64", "f32"], default=None, help="measure one precision form")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2104_06784_gb300 import workloads as W
+    cfg = W.large_release_config(n=args.side, dx=DX, seed=0)
+
+    if args.impl == "reference":
+        line = run_reference(args, cfg, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2104_06784_gb300 import moses
+    side = args.side
+    cells = side * side
+    K, Wm = args.steps, args.warmup
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    sampler = ClockSampler(local)
+    forms = [("f64", moses.FP64), ("f32", moses.FP32)]
+    if args.only:
+        forms = [f for f in forms if f[0] == args.only]
+    for name, prec in forms:
+        sim = moses.from_config(cfg, precision=prec)
+        if dist is not None:
+            dist.barrier()
+        with (sampler if name == "f64" else _Null()):
+            ms, stage_ms = measure(sim, cells, K, Wm, torch)
+        ms = max_over_ranks(ms)
+        launch_ms = (stage_ms[0] + stage_ms[1]) / (2 * K)
+        results[name] = dict(ms=ms, launch_ms=launch_ms, stage_ms=[stage_ms[0] / K, stage_ms[1] / K], sim=sim)
+        if name == "f32":
+            sim.close()
+
+    if args.only:
+        r = results[args.only]
+        if rank == 0:
+            print(json.dumps({"form": args.only, "side": side, "ms_per_step": r["ms"] / K,
+                              "launch_ms": r["launch_ms"], "value": world * cells * K / (r["ms"] / 1e3)}), flush=True)
+        r["sim"].close()
+        return
+    pk, pk_src = peaks()
+    f64 = results["f64"]
+    value = world * cells * K / (f64["ms"] / 1e3)
+    flops_launch = FLOPS_PER_CELL_STAGE * cells
+    ach = flops_launch / (f64["launch_ms"] / 1e3) / 1e12
+    h = stage_hash()
+    roof64 = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+              "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get(("f64", h)),
+              "kernel": "moses::stage_kernel<double,32,8>",
+              "peak_source": "GB300 FP64 vector rate from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+              "hbm": {"achieved_gbs": WORDS_PER_CELL_STEP * 8 * cells / (2 * f64["launch_ms"] / 1e3) / 1e9,
+                      "peak_gbs": pk["hbm_gbs"], "peak_source": pk_src}}
+    f32 = results["f32"]
+    bytes_step32 = WORDS_PER_CELL_STEP * 4 * cells
+    gbs32 = bytes_step32 / (2 * f32["launch_ms"] / 1e3) / 1e9
+    roof32 = {"bound": "hbm", "achieved": gbs32, "peak": pk["hbm_gbs"], "unit": "GB/s",
+              "frac": gbs32 / pk["hbm_gbs"], "traffic": TRAFFIC.get(("f32", h)),
+              "kernel": "moses::stage_kernel<float,32,8>", "peak_source": pk_src}
+
+    # end to end through the C-ABI with pinned host buffers: per step, upload
+    # the state, one step, download the state
+    e2e = None
+    if not args.no_e2e:
+        sim = f64["sim"]
+        Uh = torch.empty((6, side, side), dtype=torch.float64, pin_memory=True).numpy()
+        sim.get_conserved(out=Uh)
+        for _ in range(2):
+            sim.set_conserved(Uh)
+            sim.step(1)
+            sim.get_conserved(out=Uh)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        Ke = max(3, K // 2)
+        for _ in range(Ke):
+            sim.set_conserved(Uh)
+            sim.step(1)
+            sim.get_conserved(out=Uh)
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * cells * Ke / el, "unit": UNIT, "h2d_bytes_per_step": int(Uh.nbytes),
+               "d2h_bytes_per_step": int(Uh.nbytes),
+               "calls": "moses_set_conserved + moses_step(1) + moses_get_conserved, pinned host buffers"}
+    f64["sim"].close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cfg)
+        cpu.pop("seconds", None)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": f64["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded spectral DEM and release; see workloads.py)",
+        "config": config_dict(cfg, args), "roofline": roof64, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 2 * K, "clocks": sampler.summary(),
+        "f32": {"value": world * cells * K / (f32["ms"] / 1e3), "ms_per_step": f32["ms"] / K, "dtype": "f32",
+                "roofline": roof32, "gpu_launches": 2 * K},
+        "stage_ms": {"f64": f64["stage_ms"], "f32": f32["stage_ms"]},
+        "stage_source": h,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        pass
+
+
+if __name__ == "__main__":
+    main()

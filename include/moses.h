@@ -1,0 +1,187 @@
+/*
+ * moses.h -- C-ABI of the GB300 (sm_103a) implementation of one explicit time
+ * step of the depth-integrated two-phase (solid grains + interstitial fluid)
+ * shallow-flow model of MoSES_2PDF (arXiv:2104.06784) over a DEM.
+ *
+ * What the library computes, per step (Sect. 2.2 and App. A):
+ *   dt   = CFL min(dx, dy) / a_max,  a_max = largest per-phase wave speed over
+ *          all cells (Sect. 3.1.2, Stage 2: "global maximum wave speed")
+ *   U*   = U^n + dt L(U^n),   U** = U* + dt L(U*),   U^{n+1} = (U^n + U**)/2
+ *          (two-step modified Euler, Sect. 2.2)
+ *   L    = central (Kurganov-Tadmor) fluxes of Eqs. FluxEqSxi_Topo ..
+ *          FluxEqFeta_Topo with minmod reconstruction (Sect. 2.2) plus the
+ *          sources of Eqs. Src_nd_Topo, Src_f_Topo, Src_v_Topo, SrcF_nd_Topo,
+ *          SrcF_f_Topo, SrcF_v_Topo, SrcF_vis_Topo; Coulomb friction with a
+ *          stopping condition; positivity of both depths.
+ * The conserved state per cell is U = (J h^s, J h^s v_X^s, J h^s v_Y^s,
+ * J h^f, J h^f v_X^f, J h^f v_Y^f) (App. A, Eqs. MassEq_TopoS0/F0,
+ * MomentumEqS_Topo/F_Topo), h the thickness normal to the bed, v_X, v_Y the
+ * horizontal projections of the phase velocities, J = J_b = det Omega_b.
+ *
+ * Conventions for every call:
+ *  - Grids are row-major [j * nx + i]; j = 0 is the southern row (Y grows
+ *    northwards), i = 0 the western column.  Cells are dx by dy metres.
+ *  - Host pointers unless a name ends in _device.  The library copies every
+ *    input; it never keeps a caller's pointer after a call returns.
+ *  - Device work runs on the CUDA stream given to moses_create (NULL = the
+ *    legacy default stream).  Calls that return values to the host
+ *    synchronise that stream before returning.
+ *  - Every int-returning call returns MOSES_OK (0) or a negative MOSES_E*
+ *    code; moses_last_error() gives the message.  No call throws.
+ *  - A moses_sim is not thread-safe; distinct sims are independent.
+ */
+#ifndef MOSES_H
+#define MOSES_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MOSES_OK 0
+#define MOSES_EINVAL (-1)     /* bad argument (size, pointer, parameter)       */
+#define MOSES_ENOMEM (-2)     /* device or host allocation failed               */
+#define MOSES_ECUDA (-3)      /* a CUDA call failed (message has the CUDA error) */
+#define MOSES_ENONFINITE (-4) /* the state or the time step became non-finite   */
+#define MOSES_ETIMEOUT (-5)   /* a bounded device-side wait gave up             */
+#define MOSES_ESTATE (-6)     /* call out of order (e.g. step before a state)   */
+
+#define MOSES_BC_CLOSED 0       /* wall: mirror, normal momentum negated      */
+#define MOSES_BC_TRANSMISSIVE 1 /* the paper's "no reflection" (Sect. 3.1.2):
+                                   zero-gradient copy into the ghost cells      */
+
+#define MOSES_SIDE_W 0
+#define MOSES_SIDE_E 1
+#define MOSES_SIDE_S 2
+#define MOSES_SIDE_N 3
+
+#define MOSES_FP64 0 /* state, geometry and flux arithmetic in FP64            */
+#define MOSES_FP32 1 /* state, geometry and fluxes in FP32; budgets and the
+                        friction stopping test in FP64                          */
+
+#define MOSES_BUDGET_LEN 13
+
+/* Model and scheme parameters, SI units.  The paper's equations are
+ * dimensionless (App. A); g = 1 recovers them.  Every pressure carries g c,
+ * c = n_Z (App. A, below Eq. FluxEqFeta_Topo). */
+typedef struct {
+    double g;            /* gravity [m s^-2]                                      */
+    double eps;          /* aspect ratio epsilon in the pressure terms (1 in SI)  */
+    double eps_chi;      /* epsilon^chi in front of kappa in p_b (1 in SI)        */
+    double rho_s, rho_f; /* densities; alpha_rho = rho_f / rho_s                 */
+    double delta_b_deg;  /* basal friction angle delta_b (Sect. 3.1.2 (a))        */
+    double phi_int_deg;  /* internal friction angle; only k_mode = 1 would use it */
+    int k_mode;          /* 0: earth-pressure coefficient 1 as in App. A (only
+                            value accepted)                                       */
+    double c_d;          /* interphase drag c_D [s^-1] (Eqs. Src_v_Topo, SrcF_v)  */
+    double nu_f;         /* fluid viscosity eps/N_R [m^2 s^-1] (Eq. SrcF_vis_Topo)*/
+    double k_f;          /* fluid basal friction vartheta_b/(eps N_R) [s^-1]      */
+    double cfl;          /* Courant number (the paper uses 0.1, Sect. 2.2)        */
+    double dt_max;       /* time step cap, and the step of a dry domain [s]       */
+    double h_dry;        /* depth below which a phase has no velocity [m]         */
+    int bc[4];           /* W, E, S, N: MOSES_BC_CLOSED or MOSES_BC_TRANSMISSIVE  */
+    int fluid_pg_mode;   /* 0: fluid pressure-gradient source with phi^s (the
+                            reaction of the solid buoyancy); 1: phi^f as printed
+                            in Eq. SrcF_f_Topo                                    */
+    int precision;       /* MOSES_FP64 or MOSES_FP32                              */
+} moses_params;
+
+typedef struct moses_sim moses_sim; /* opaque; owns all its device memory */
+
+/* Create a simulation over a DEM (Sect. 2.1; Sect. 3.1.2 Stage 0-1).
+ * dem: nx*ny bed elevations [m] at cell centres (host).  nx, ny >= 1;
+ * dx, dy > 0.  Runs the one-time geometry pass (basal basis, J_b, Omega_b^-1,
+ * slope and curvature terms) on the GPU.  stream: a cudaStream_t or NULL.
+ * On success *out owns ~ (6 + 6 + 20) nx ny words of device memory.
+ * The state starts dry at t = 0.  Errors: EINVAL, ENOMEM, ECUDA. */
+int moses_create(const double *dem, int nx, int ny, double dx, double dy, const moses_params *p,
+                 void *stream, moses_sim **out);
+
+/* Mode-I release (Sect. 3.1.2 Stage 0): finite masses placed in the domain.
+ * h: normal flow thickness [m]; phi_s: solid volume fraction (NULL = 0.5);
+ * vx_s .. vy_f: phase velocities, horizontal projections [m s^-1] (NULL = 0).
+ * All nx*ny, host.  Replaces the state; keeps t and the inflow segments.
+ * Errors: EINVAL (NULL h, h < 0, phi_s outside [0, 1], non-finite), ECUDA. */
+int moses_set_release(moses_sim *s, const double *h, const double *phi_s, const double *vx_s,
+                      const double *vy_s, const double *vx_f, const double *vy_f);
+
+/* Mode-II inflow (Sect. 3.1.2 Stage 0): a hydrograph on boundary cells
+ * [i0, i1) of `side` (indices along that side).  t, Q, phi_s: npts samples
+ * (host) of time [s], total discharge [m^3 s^-1] and solid fraction; linear in
+ * between, zero outside [t[0], t[npts-1]].  The ghost cells of the segment
+ * hold the mixture at critical depth for the unit discharge Q / width,
+ * moving inward.  Up to 8 segments, npts <= 64, t non-decreasing.
+ * Errors: EINVAL, ECUDA. */
+int moses_set_inflow(moses_sim *s, int side, int i0, int i1, int npts, const double *t,
+                     const double *Q, const double *phi_s);
+
+/* Advance nsteps CFL-limited steps (Sect. 2.2; Stage 2 of Sect. 3.1.2).
+ * t_out (may be NULL) receives the time after the last step.  Synchronises
+ * the stream once at the end.  Errors: ESTATE, ENONFINITE, ECUDA. */
+int moses_step(moses_sim *s, int nsteps, double *t_out);
+
+/* moses_step with CUDA events recorded on the stream around every stage
+ * launch: stage_ms[0] / stage_ms[1] receive the summed device time of the
+ * stage-1 / stage-2 launches [ms] (the two launches of each step).  For
+ * per-kernel throughput measurements; otherwise identical to moses_step. */
+int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms);
+
+/* Advance with a prescribed time step dt > 0 (same stages, no CFL search).
+ * Errors: EINVAL, ESTATE, ENONFINITE, ECUDA. */
+int moses_step_dt(moses_sim *s, int nsteps, double dt, double *t_out);
+
+/* Advance until t >= t_end (the last step is shortened to land on t_end) or
+ * max_steps steps.  *nsteps_out (may be NULL) gets the steps taken. */
+int moses_run_until(moses_sim *s, double t_end, int max_steps, int *nsteps_out);
+
+/* The time step the next moses_step would take, and the current time. */
+int moses_next_dt(moses_sim *s, double *dt, double *t);
+
+/* Output fields of Sect. 3.1.2 Stage 3: total normal thickness h, solid
+ * fraction phi_s, phase velocities (horizontal projections).  Each pointer
+ * may be NULL; non-NULL ones receive nx*ny doubles (host). */
+int moses_get_state(moses_sim *s, double *h, double *phi_s, double *vx_s, double *vy_s,
+                    double *vx_f, double *vy_f);
+
+/* Conserved state U, 6 planes of nx*ny doubles, plane k holding U_{k+1}
+ * (host).  get: copy out (FP32 state widened).  set: replace (rounded to
+ * FP32 in that form); does not change t.  Errors: EINVAL (negative depth,
+ * non-finite), ECUDA. */
+int moses_get_conserved(moses_sim *s, double *U);
+int moses_set_conserved(moses_sim *s, const double *U);
+
+/* The same on device memory owned by the caller (6*nx*ny doubles, same plane
+ * order), for zero-copy use from frameworks that hold tensors in HBM. */
+int moses_get_conserved_device(moses_sim *s, double *U_device);
+int moses_set_conserved_device(moses_sim *s, const double *U_device);
+
+/* One stage U + dt L(U) from the current state at time t (friction, clamp
+ * and dry-momentum rule included), written to U_out (6*nx*ny doubles, host).
+ * The state is unchanged.  For stage-level parity checks. */
+int moses_stage(moses_sim *s, double t, double dt, double *U_out);
+
+/* Largest cell-centre wave speed of the current state (the a_max of the CFL
+ * step), reduced exactly on the GPU. */
+int moses_max_speed(moses_sim *s, double *amax);
+
+/* FP64 budgets, reduced on the GPU: out[0..1] solid / fluid volume
+ * sum(U1), sum(U4) dx dy [m^3]; out[2..5] momenta sum(U2, U3, U5, U6) dx dy;
+ * out[6..7] time-integrated boundary volume inflow per phase (the computed
+ * face fluxes, Heun weights); out[8..9] volume added by the positivity clamp
+ * per phase; out[10] clamp events; out[11] t; out[12] steps taken. */
+int moses_get_budget(moses_sim *s, double out[MOSES_BUDGET_LEN]);
+
+/* Message of the last error on s (or of the last failed moses_create when
+ * s is NULL).  Valid until the next call on s. */
+const char *moses_last_error(const moses_sim *s);
+
+/* Release all device memory of s.  NULL is ignored. */
+void moses_destroy(moses_sim *s);
+
+/* Library build identification (architecture, precision forms). */
+const char *moses_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOSES_H */

@@ -1,0 +1,940 @@
+// moses.cu -- C-ABI of the two-phase shallow-flow step (include/moses.h):
+// simulation object, device memory, the one-time geometry pass (Sect. 2.1,
+// App. A: J_b, Omega_b^-1, basal normal and its derivatives), the initial
+// ghost fill, the exact CFL max-reduction and the FP64 budget reductions.
+// The per-step stage kernels live in stage.cuh (instantiated in
+// stage_f64.cu / stage_f32.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/moses.h"
+#include "moses_dev.cuh"
+#include "stage.cuh"
+
+using namespace moses;
+
+struct moses_sim {
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;  // elements per plane
+    double dx = 0, dy = 0;
+    moses_params p{};
+    Phys ph{};
+    int prec = MOSES_FP64;
+    size_t esz = 8;  // bytes per state element
+    cudaStream_t stream = nullptr;
+    void *U = nullptr;     // state, 6 planes
+    void *Us = nullptr;    // Heun intermediate, 6 planes
+    void *geo = nullptr;   // GEO_PLANES planes
+    Ctl *ctl = nullptr;    // device control block
+    InflowSeg *inflow_d = nullptr;
+    InflowSeg inflow_h[MAX_INFLOW];
+    int n_inflow = 0;
+    double *stage_buf = nullptr;  // dense 6*nx*ny doubles (host <-> device staging)
+    double *red = nullptr;        // 8 doubles for reductions
+    bool have_state = false;
+    int tile = 0;
+    std::string err;
+};
+
+static std::string g_create_err;
+
+// ---------------------------------------------------------------------------
+// error helpers
+
+static int fail(moses_sim *s, int code, const std::string &msg)
+{
+    if (s) s->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(s, e_ == cudaErrorMemoryAllocation ? MOSES_ENOMEM : MOSES_ECUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// geometry pass (once per DEM)
+
+// DEM value after extrapolating linearly in X over rows 0..ny-1 (3 layers)
+__device__ __forceinline__ double dem_x(const double *dem, int nx, int i, int j)
+{
+    if (i >= 0 && i < nx) return dem[(long long)j * nx + i];
+    if (i < 0) {
+        const double b0 = dem[(long long)j * nx], b1 = nx > 1 ? dem[(long long)j * nx + 1] : b0;
+        return b0 + (double)(-i) * (b0 - b1);
+    }
+    const double e0 = dem[(long long)j * nx + nx - 1], e1 = nx > 1 ? dem[(long long)j * nx + nx - 2] : e0;
+    return e0 + (double)(i - nx + 1) * (e0 - e1);
+}
+
+// then in Y over all (extended) columns
+__device__ __forceinline__ double dem_xy(const double *dem, int nx, int ny, int i, int j)
+{
+    if (j >= 0 && j < ny) return dem_x(dem, nx, i, j);
+    if (j < 0) {
+        const double b0 = dem_x(dem, nx, i, 0), b1 = ny > 1 ? dem_x(dem, nx, i, 1) : b0;
+        return b0 + (double)(-j) * (b0 - b1);
+    }
+    const double e0 = dem_x(dem, nx, i, ny - 1), e1 = ny > 1 ? dem_x(dem, nx, i, ny - 2) : e0;
+    return e0 + (double)(j - ny + 1) * (e0 - e1);
+}
+
+__global__ void extend_dem_kernel(const double *dem, int nx, int ny, double *bext)
+{
+    const int W = nx + 6, H = ny + 6;
+    const long long n = (long long)W * H;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int jj = (int)(e / W), ii = (int)(e - (long long)jj * W);
+        bext[e] = dem_xy(dem, nx, ny, ii - 3, jj - 3);
+    }
+}
+
+struct Slopes {
+    double bX, bY;
+};
+
+template <typename T>
+__global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, long long plane, double dx,
+                                double dy, T *geo)
+{
+    const int W = nx + 4, H = ny + 4;  // padded cell range [-2, n+2)
+    const long long n = (long long)W * H;
+    const int BW = nx + 6;
+    auto B = [&](int i, int j) { return bext[(long long)(j + 3) * BW + (i + 3)]; };
+    auto slopes = [&](int i, int j) {
+        return Slopes{(B(i + 1, j) - B(i - 1, j)) / (2.0 * dx), (B(i, j + 1) - B(i, j - 1)) / (2.0 * dy)};
+    };
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / W) - 2, i = (int)(e % W) - 2;
+        const long long g = cell_index(i, j, pitch);
+        // cell centre
+        {
+            const Slopes s = slopes(i, j);
+            const double bXX = (B(i + 1, j) - 2.0 * B(i, j) + B(i - 1, j)) / (dx * dx);
+            const double bYY = (B(i, j + 1) - 2.0 * B(i, j) + B(i, j - 1)) / (dy * dy);
+            const double bXY = (B(i + 1, j + 1) - B(i + 1, j - 1) - B(i - 1, j + 1) + B(i - 1, j - 1)) / (4.0 * dx * dy);
+            const double s2 = 1.0 + (s.bX * s.bX + s.bY * s.bY);
+            const double J = sqrt(s2), c = 1.0 / J, c2 = 1.0 / s2;
+            const double A11 = (1.0 + s.bY * s.bY) * c2, A12 = -s.bX * s.bY * c2, A22 = (1.0 + s.bX * s.bX) * c2;
+            geo[GC_J * plane + g] = (T)J;
+            geo[GC_C * plane + g] = (T)c;
+            geo[GC_BX * plane + g] = (T)s.bX;
+            geo[GC_BY * plane + g] = (T)s.bY;
+            geo[GC_A11 * plane + g] = (T)A11;
+            geo[GC_A12 * plane + g] = (T)A12;
+            geo[GC_A22 * plane + g] = (T)A22;
+            geo[GC_KXX * plane + g] = (T)(c * bXX);
+            geo[GC_KXY * plane + g] = (T)(c * bXY);
+            geo[GC_KYY * plane + g] = (T)(c * bYY);
+            geo[GC_G11 * plane + g] = (T)(A11 * c2);
+            geo[GC_G22 * plane + g] = (T)(A22 * c2);
+        }
+        // x-face (i+1/2, j): normal slope by the face difference, transverse
+        // slope as the mean of the two cells' central differences
+        if (i < nx + 1) {
+            const double bX = (B(i + 1, j) - B(i, j)) / dx;
+            const double bY = 0.5 * (slopes(i, j).bY + slopes(i + 1, j).bY);
+            const double s2 = 1.0 + (bX * bX + bY * bY);
+            const double c2 = 1.0 / s2;
+            geo[GX_J * plane + g] = (T)sqrt(s2);
+            geo[GX_GN * plane + g] = (T)((1.0 + bY * bY) * c2 * c2);
+            geo[GX_GT * plane + g] = (T)(-bX * bY * c2 * c2);
+            geo[GX_C2 * plane + g] = (T)c2;
+        }
+        if (j < ny + 1) {
+            const double bY = (B(i, j + 1) - B(i, j)) / dy;
+            const double bX = 0.5 * (slopes(i, j).bX + slopes(i, j + 1).bX);
+            const double s2 = 1.0 + (bX * bX + bY * bY);
+            const double c2 = 1.0 / s2;
+            geo[GY_J * plane + g] = (T)sqrt(s2);
+            geo[GY_GN * plane + g] = (T)((1.0 + bX * bX) * c2 * c2);
+            geo[GY_GT * plane + g] = (T)(-bX * bY * c2 * c2);
+            geo[GY_C2 * plane + g] = (T)c2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// state kernels
+
+template <typename T>
+__global__ void fill_ghosts_kernel(const StageArgs<T> a, T *U, double tg)
+{
+    const int nx = a.nx, ny = a.ny;
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        if (!(i < 2 || i >= nx - 2 || j < 2 || j >= ny - 2)) continue;
+        const long long g = cell_index(i, j, a.pitch);
+        T v[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) v[c] = U[c * a.plane + g];
+        write_ghosts(U, a.geo, a, i, j, v, tg);
+    }
+}
+
+template <typename T>
+__global__ void max_speed_kernel(const T *U, const T *geo, int nx, int ny, int pitch, long long plane, Phys ph,
+                                 unsigned long long *out)
+{
+    const K<T> k(ph);
+    const long long n = (long long)nx * ny;
+    double m = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const long long g = cell_index(i, j, pitch);
+        T u[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) u[c] = U[c * plane + g];
+        m = fmax(m, cell_speed(u, geo[GC_J * plane + g], geo[GC_G11 * plane + g], geo[GC_G22 * plane + g], k));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double w[32];
+    if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); q++) m = fmax(m, w[q]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// dense doubles [c][j][i] -> padded state of type T (interior only)
+template <typename T>
+__global__ void unpack_kernel(const double *src, T *U, int nx, int ny, int pitch, long long plane)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const long long r = e - c * n;
+        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
+        U[c * plane + cell_index(i, j, pitch)] = (T)src[e];
+    }
+}
+
+template <typename T>
+__global__ void pack_kernel(const T *U, double *dst, int nx, int ny, int pitch, long long plane)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const long long r = e - c * n;
+        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
+        dst[e] = (double)U[c * plane + cell_index(i, j, pitch)];
+    }
+}
+
+// release (h, phi_s, velocities) -> conserved U = J h (phi, phi v)
+template <typename T>
+__global__ void release_kernel(const double *src, int has_phi, int has_v, T *U, const T *geo, int nx, int ny, int pitch,
+                               long long plane)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const long long g = cell_index(i, j, pitch);
+        const double J = (double)geo[GC_J * plane + g];
+        const double h = src[e];
+        const double ph = has_phi ? src[n + e] : 0.5;
+        const double U1 = J * h * ph, U4 = J * h * (1.0 - ph);
+        const double vxs = (has_v & 1) ? src[2 * n + e] : 0.0, vys = (has_v & 2) ? src[3 * n + e] : 0.0;
+        const double vxf = (has_v & 4) ? src[4 * n + e] : 0.0, vyf = (has_v & 8) ? src[5 * n + e] : 0.0;
+        U[g] = (T)U1;
+        U[plane + g] = (T)(U1 * vxs);
+        U[2 * plane + g] = (T)(U1 * vys);
+        U[3 * plane + g] = (T)U4;
+        U[4 * plane + g] = (T)(U4 * vxf);
+        U[5 * plane + g] = (T)(U4 * vyf);
+    }
+}
+
+// conserved -> output fields (h, phi_s, v_X^s, v_Y^s, v_X^f, v_Y^f)
+template <typename T>
+__global__ void prims_kernel(const T *U, const T *geo, int nx, int ny, int pitch, long long plane, double h_dry,
+                             double *dst)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const long long g = cell_index(i, j, pitch);
+        const double J = (double)geo[GC_J * plane + g];
+        double u[6];
+        for (int c = 0; c < 6; c++) u[c] = (double)U[c * plane + g];
+        const double Ut = u[0] + u[3];
+        const double h = Ut / J;
+        const bool wet = h > h_dry;
+        dst[e] = h;
+        dst[n + e] = wet ? u[0] / Ut : 0.0;
+        const bool ws = u[0] > J * h_dry, wf = u[3] > J * h_dry;
+        dst[2 * n + e] = ws ? u[1] / u[0] : 0.0;
+        dst[3 * n + e] = ws ? u[2] / u[0] : 0.0;
+        dst[4 * n + e] = wf ? u[4] / u[3] : 0.0;
+        dst[5 * n + e] = wf ? u[5] / u[3] : 0.0;
+    }
+}
+
+template <typename T>
+__global__ void budget_kernel(const T *U, int nx, int ny, int pitch, long long plane, double *out)
+{
+    const long long n = (long long)nx * ny;
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const long long g = cell_index(i, j, pitch);
+#pragma unroll
+        for (int c = 0; c < 6; c++) s[c] += (double)U[c * plane + g];
+    }
+    __shared__ double w[6][32];
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+        if ((threadIdx.x & 31) == 0) w[c][threadIdx.x >> 5] = s[c];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += w[threadIdx.x][q];
+        atomicAdd(&out[threadIdx.x], t);
+    }
+}
+
+__global__ void validate_kernel(const double *src, long long n6, long long n, int *bad)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n6; e += (long long)gridDim.x * blockDim.x) {
+        const double v = src[e];
+        const int c = (int)(e / n);
+        if (!isfinite(v) || ((c == 0 || c == 3) && v < 0.0)) atomicOr(bad, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+
+static int grid_for(long long n, int block = 256)
+{
+    long long b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+template <typename T>
+static StageArgs<T> base_args(moses_sim *s)
+{
+    StageArgs<T> a{};
+    a.geo = (const T *)s->geo;
+    a.ctl = s->ctl;
+    a.inflow = s->inflow_d;
+    a.n_inflow = s->n_inflow;
+    a.nx = s->nx;
+    a.ny = s->ny;
+    a.pitch = s->pitch;
+    a.plane = s->plane;
+    a.ph = s->ph;
+    return a;
+}
+
+static int ensure_stage_buf(moses_sim *s)
+{
+    if (!s->stage_buf) CK(cudaMalloc(&s->stage_buf, sizeof(double) * 6 * (size_t)s->nx * s->ny));
+    return MOSES_OK;
+}
+
+static int read_ctl(moses_sim *s, Ctl *h)
+{
+    CK(cudaMemcpyAsync(h, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+// after the state changed from the host: ghosts at the current time and a_max
+template <typename T>
+static int refresh_t(moses_sim *s)
+{
+    Ctl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    StageArgs<T> a = base_args<T>(s);
+    const long long n = (long long)s->nx * s->ny;
+    fill_ghosts_kernel<T><<<grid_for(n), 256, 0, s->stream>>>(a, (T *)s->U, h.t);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(&s->ctl->amax, 0, sizeof(unsigned long long), s->stream));
+    max_speed_kernel<T><<<grid_for(n), 256, 0, s->stream>>>((const T *)s->U, (const T *)s->geo, s->nx, s->ny,
+                                                             s->pitch, s->plane, s->ph, &s->ctl->amax);
+    CK(cudaGetLastError());
+    return MOSES_OK;
+}
+
+static int refresh(moses_sim *s)
+{
+    return s->prec == MOSES_FP64 ? refresh_t<double>(s) : refresh_t<float>(s);
+}
+
+static int check_params(const moses_params *p, std::string &why)
+{
+    auto fin = [](double v) { return std::isfinite(v); };
+    if (!(fin(p->g) && p->g > 0)) return why = "g must be > 0", 1;
+    if (!(fin(p->eps) && p->eps > 0)) return why = "eps must be > 0", 1;
+    if (!fin(p->eps_chi)) return why = "eps_chi must be finite", 1;
+    if (!(fin(p->rho_s) && p->rho_s > 0)) return why = "rho_s must be > 0", 1;
+    if (!(fin(p->rho_f) && p->rho_f >= 0 && p->rho_f < p->rho_s)) return why = "need 0 <= rho_f < rho_s", 1;
+    if (!(fin(p->delta_b_deg) && p->delta_b_deg >= 0 && p->delta_b_deg < 90)) return why = "delta_b in [0, 90)", 1;
+    if (p->k_mode != 0) return why = "only k_mode = 0 (earth-pressure coefficient 1, App. A) is implemented", 1;
+    if (!(fin(p->c_d) && p->c_d >= 0)) return why = "c_d must be >= 0", 1;
+    if (!(fin(p->nu_f) && p->nu_f == 0)) return why = "nu_f > 0 is not implemented on the GPU path", 1;
+    if (!(fin(p->k_f) && p->k_f >= 0)) return why = "k_f must be >= 0", 1;
+    if (!(fin(p->cfl) && p->cfl > 0)) return why = "cfl must be > 0", 1;
+    if (!(fin(p->dt_max) && p->dt_max > 0)) return why = "dt_max must be > 0", 1;
+    if (!(fin(p->h_dry) && p->h_dry > 0)) return why = "h_dry must be > 0", 1;
+    for (int k = 0; k < 4; k++)
+        if (p->bc[k] != MOSES_BC_CLOSED && p->bc[k] != MOSES_BC_TRANSMISSIVE) return why = "bc must be 0 or 1", 1;
+    if (p->fluid_pg_mode != 0 && p->fluid_pg_mode != 1) return why = "fluid_pg_mode must be 0 or 1", 1;
+    if (p->precision != MOSES_FP64 && p->precision != MOSES_FP32) return why = "precision must be 0 or 1", 1;
+    return 0;
+}
+
+static Phys make_phys(const moses_params *p, double dx, double dy)
+{
+    Phys f{};
+    const double al = p->rho_f / p->rho_s;
+    f.kap_s = p->eps * p->g * (1.0 - al) / 2.0;
+    f.kap_f = p->eps * p->g / 2.0;
+    f.half_g = p->g / 2.0;
+    f.g_1ma = p->g * (1.0 - al);
+    f.g = p->g;
+    f.eps_chi = p->eps_chi;
+    f.eps_alpha = p->eps * al;
+    f.eps = p->eps;
+    f.alpha = al;
+    f.c_d = p->c_d;
+    f.k_f = p->k_f;
+    f.nu_f = p->nu_f;
+    f.tan_delta = tan(p->delta_b_deg * M_PI / 180.0);
+    f.h_dry = p->h_dry;
+    f.cfl = p->cfl;
+    f.dt_max = p->dt_max;
+    f.dmin = dx < dy ? dx : dy;
+    f.dx = dx;
+    f.dy = dy;
+    f.inv_dx = 1.0 / dx;
+    f.inv_dy = 1.0 / dy;
+    f.cell_area = dx * dy;
+    f.pg_mode = p->fluid_pg_mode;
+    for (int k = 0; k < 4; k++) f.bc[k] = p->bc[k];
+    return f;
+}
+
+static void free_sim(moses_sim *s)
+{
+    if (!s) return;
+    cudaFree(s->U);
+    cudaFree(s->Us);
+    cudaFree(s->geo);
+    cudaFree(s->ctl);
+    cudaFree(s->inflow_d);
+    cudaFree(s->stage_buf);
+    cudaFree(s->red);
+    delete s;
+}
+
+// ---------------------------------------------------------------------------
+// C-ABI (C linkage comes from the declarations in moses.h)
+
+const char *moses_version(void) { return "moses-gb300 1.0 (sm_103a; FP64 and FP32 state forms)"; }
+
+const char *moses_last_error(const moses_sim *s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+int moses_create(const double *dem, int nx, int ny, double dx, double dy, const moses_params *p, void *stream,
+                 moses_sim **out)
+{
+    moses_sim *s = nullptr;
+    if (!out) return fail(nullptr, MOSES_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!dem || !p) return fail(nullptr, MOSES_EINVAL, "dem and params must be non-NULL");
+    if (nx < 1 || ny < 1) return fail(nullptr, MOSES_EINVAL, "nx and ny must be >= 1");
+    if ((long long)nx * ny > (1ll << 31)) return fail(nullptr, MOSES_EINVAL, "grid larger than 2^31 cells");
+    if (!(std::isfinite(dx) && std::isfinite(dy) && dx > 0 && dy > 0))
+        return fail(nullptr, MOSES_EINVAL, "dx and dy must be finite and > 0");
+    std::string why;
+    if (check_params(p, why)) return fail(nullptr, MOSES_EINVAL, why);
+    for (long long e = 0; e < (long long)nx * ny; e++)
+        if (!std::isfinite(dem[e])) return fail(nullptr, MOSES_EINVAL, "DEM has non-finite values");
+
+    s = new (std::nothrow) moses_sim();
+    if (!s) return fail(nullptr, MOSES_ENOMEM, "host allocation failed");
+    s->nx = nx;
+    s->ny = ny;
+    s->dx = dx;
+    s->dy = dy;
+    s->p = *p;
+    s->ph = make_phys(p, dx, dy);
+    s->prec = p->precision;
+    s->esz = s->prec == MOSES_FP64 ? 8 : 4;
+    s->stream = (cudaStream_t)stream;
+    s->pitch = ((nx + 2 * GH) + 31) / 32 * 32;
+    s->plane = (long long)s->pitch * (ny + 2 * GH);
+    auto bail = [&](int rc) {
+        g_create_err = s->err;
+        free_sim(s);
+        return rc;
+    };
+    const size_t st = 6 * (size_t)s->plane * s->esz;
+    cudaError_t e;
+    if ((e = cudaMalloc(&s->U, st)) != cudaSuccess || (e = cudaMalloc(&s->Us, st)) != cudaSuccess ||
+        (e = cudaMalloc(&s->geo, (size_t)GEO_PLANES * s->plane * s->esz)) != cudaSuccess ||
+        (e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess ||
+        (e = cudaMalloc(&s->inflow_d, sizeof(InflowSeg) * MAX_INFLOW)) != cudaSuccess ||
+        (e = cudaMalloc(&s->red, 8 * sizeof(double))) != cudaSuccess) {
+        s->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return bail(e == cudaErrorMemoryAllocation ? MOSES_ENOMEM : MOSES_ECUDA);
+    }
+    if ((e = cudaMemsetAsync(s->U, 0, st, s->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(s->Us, 0, st, s->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(s->geo, 0, (size_t)GEO_PLANES * s->plane * s->esz, s->stream)) != cudaSuccess) {
+        s->err = std::string("memset: ") + cudaGetErrorString(e);
+        return bail(MOSES_ECUDA);
+    }
+    Ctl c{};
+    if ((e = cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream)) != cudaSuccess) {
+        s->err = std::string("ctl: ") + cudaGetErrorString(e);
+        return bail(MOSES_ECUDA);
+    }
+    // geometry pass
+    double *d_dem = nullptr, *d_ext = nullptr;
+    const size_t nd = (size_t)nx * ny, ne = (size_t)(nx + 6) * (ny + 6);
+    if ((e = cudaMalloc(&d_dem, nd * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&d_ext, ne * sizeof(double))) != cudaSuccess) {
+        cudaFree(d_dem);
+        s->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        return bail(MOSES_ENOMEM);
+    }
+    e = cudaMemcpyAsync(d_dem, dem, nd * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) {
+        extend_dem_kernel<<<grid_for((long long)ne), 256, 0, s->stream>>>(d_dem, nx, ny, d_ext);
+        const long long ng = (long long)(nx + 4) * (ny + 4);
+        if (s->prec == MOSES_FP64)
+            geometry_kernel<double><<<grid_for(ng), 256, 0, s->stream>>>(d_ext, nx, ny, s->pitch, s->plane, dx, dy,
+                                                                         (double *)s->geo);
+        else
+            geometry_kernel<float><<<grid_for(ng), 256, 0, s->stream>>>(d_ext, nx, ny, s->pitch, s->plane, dx, dy,
+                                                                        (float *)s->geo);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(d_dem);
+    cudaFree(d_ext);
+    if (e != cudaSuccess) {
+        s->err = std::string("geometry pass: ") + cudaGetErrorString(e);
+        return bail(MOSES_ECUDA);
+    }
+    s->have_state = true;  // dry state at t = 0
+    int rc = refresh(s);
+    if (rc) return bail(rc);
+    *out = s;
+    return MOSES_OK;
+}
+
+void moses_destroy(moses_sim *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_sim(s);
+}
+
+static int upload_dense(moses_sim *s, const double *host6)
+{
+    int rc = ensure_stage_buf(s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(s->stage_buf, host6, sizeof(double) * 6 * (size_t)s->nx * s->ny, cudaMemcpyHostToDevice,
+                       s->stream));
+    return MOSES_OK;
+}
+
+int moses_set_release(moses_sim *s, const double *h, const double *phi_s, const double *vx_s, const double *vy_s,
+                      const double *vx_f, const double *vy_f)
+{
+    if (!s) return MOSES_EINVAL;
+    if (!h) return fail(s, MOSES_EINVAL, "h must be non-NULL");
+    const long long n = (long long)s->nx * s->ny;
+    for (long long e = 0; e < n; e++) {
+        if (!(std::isfinite(h[e]) && h[e] >= 0)) return fail(s, MOSES_EINVAL, "h must be finite and >= 0");
+        if (phi_s && !(phi_s[e] >= 0 && phi_s[e] <= 1)) return fail(s, MOSES_EINVAL, "phi_s must be in [0, 1]");
+    }
+    const double *v[4] = {vx_s, vy_s, vx_f, vy_f};
+    for (int q = 0; q < 4; q++)
+        if (v[q])
+            for (long long e = 0; e < n; e++)
+                if (!std::isfinite(v[q][e])) return fail(s, MOSES_EINVAL, "velocities must be finite");
+    int rc = ensure_stage_buf(s);
+    if (rc) return rc;
+    const size_t b = sizeof(double) * (size_t)n;
+    CK(cudaMemcpyAsync(s->stage_buf, h, b, cudaMemcpyHostToDevice, s->stream));
+    if (phi_s) CK(cudaMemcpyAsync(s->stage_buf + n, phi_s, b, cudaMemcpyHostToDevice, s->stream));
+    int has_v = 0;
+    for (int q = 0; q < 4; q++)
+        if (v[q]) {
+            CK(cudaMemcpyAsync(s->stage_buf + (2 + q) * n, v[q], b, cudaMemcpyHostToDevice, s->stream));
+            has_v |= 1 << q;
+        }
+    if (s->prec == MOSES_FP64)
+        release_kernel<double><<<grid_for(n), 256, 0, s->stream>>>(s->stage_buf, phi_s != nullptr, has_v,
+                                                                   (double *)s->U, (const double *)s->geo, s->nx,
+                                                                   s->ny, s->pitch, s->plane);
+    else
+        release_kernel<float><<<grid_for(n), 256, 0, s->stream>>>(s->stage_buf, phi_s != nullptr, has_v,
+                                                                  (float *)s->U, (const float *)s->geo, s->nx,
+                                                                  s->ny, s->pitch, s->plane);
+    CK(cudaGetLastError());
+    s->have_state = true;
+    rc = refresh(s);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+int moses_set_inflow(moses_sim *s, int side, int i0, int i1, int npts, const double *t, const double *Q,
+                     const double *phi_s)
+{
+    if (!s) return MOSES_EINVAL;
+    if (s->n_inflow >= MAX_INFLOW) return fail(s, MOSES_EINVAL, "at most 8 inflow segments");
+    if (side < 0 || side > 3) return fail(s, MOSES_EINVAL, "side must be 0..3");
+    const int len = side < 2 ? s->ny : s->nx;
+    if (i0 < 0 || i1 > len || i1 <= i0) return fail(s, MOSES_EINVAL, "segment [i0, i1) outside the side");
+    if (npts < 1 || npts > MAX_HYD || !t || !Q || !phi_s) return fail(s, MOSES_EINVAL, "need 1..64 hydrograph points");
+    for (int k = 0; k < npts; k++) {
+        if (!(std::isfinite(t[k]) && std::isfinite(Q[k]) && Q[k] >= 0 && phi_s[k] >= 0 && phi_s[k] <= 1))
+            return fail(s, MOSES_EINVAL, "hydrograph values must be finite, Q >= 0, phi_s in [0, 1]");
+        if (k && t[k] < t[k - 1]) return fail(s, MOSES_EINVAL, "hydrograph times must not decrease");
+    }
+    for (int f = 0; f < s->n_inflow; f++)
+        if (s->inflow_h[f].side == side && i0 < s->inflow_h[f].i1 && s->inflow_h[f].i0 < i1)
+            return fail(s, MOSES_EINVAL, "inflow segments overlap");
+    InflowSeg &g = s->inflow_h[s->n_inflow];
+    memset(&g, 0, sizeof(g));
+    g.side = side;
+    g.i0 = i0;
+    g.i1 = i1;
+    g.npts = npts;
+    for (int k = 0; k < npts; k++) {
+        g.t[k] = t[k];
+        g.Q[k] = Q[k];
+        g.phi[k] = phi_s[k];
+    }
+    CK(cudaMemcpyAsync(s->inflow_d + s->n_inflow, &g, sizeof(InflowSeg), cudaMemcpyHostToDevice, s->stream));
+    s->n_inflow++;
+    int rc = refresh(s);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+template <typename T>
+static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
+{
+    StageArgs<T> a1 = base_args<T>(s), a2 = base_args<T>(s);
+    a1.Uin = (const T *)s->U;
+    a1.Uout = (T *)s->Us;
+    a1.stage = 1;
+    a2.Uin = (const T *)s->Us;
+    a2.Un = (const T *)s->U;
+    a2.Uout = (T *)s->U;
+    a2.stage = 2;
+    a2.want_amax = 1;
+    if (stage_ms) {
+        // events around every launch; summed after the last step
+        cudaEvent_t ev[3];
+        for (int q = 0; q < 3; q++) CK(cudaEventCreate(&ev[q]));
+        double acc[2] = {0.0, 0.0};
+        int rc = 0;
+        for (int k = 0; k < nsteps && rc == 0; k++) {
+            CK(cudaEventRecord(ev[0], s->stream));
+            rc = launch_stage<T>(a1, s->tile, s->stream);
+            CK(cudaEventRecord(ev[1], s->stream));
+            if (rc == 0) rc = launch_stage<T>(a2, s->tile, s->stream);
+            CK(cudaEventRecord(ev[2], s->stream));
+            CK(cudaEventSynchronize(ev[2]));
+            float m1 = 0.f, m2 = 0.f;
+            CK(cudaEventElapsedTime(&m1, ev[0], ev[1]));
+            CK(cudaEventElapsedTime(&m2, ev[1], ev[2]));
+            acc[0] += m1;
+            acc[1] += m2;
+        }
+        for (int q = 0; q < 3; q++) cudaEventDestroy(ev[q]);
+        if (rc) return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
+        stage_ms[0] = acc[0];
+        stage_ms[1] = acc[1];
+        return MOSES_OK;
+    }
+    for (int k = 0; k < nsteps; k++) {
+        int rc = launch_stage<T>(a1, s->tile, s->stream);
+        if (rc == 0) rc = launch_stage<T>(a2, s->tile, s->stream);
+        if (rc) return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    return MOSES_OK;
+}
+
+static int set_mode(moses_sim *s, double dt_fixed, double t_end)
+{
+    CK(cudaMemcpyAsync(&s->ctl->dt_fixed, &dt_fixed, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&s->ctl->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    return MOSES_OK;
+}
+
+static int run_steps(moses_sim *s, int nsteps, double dt_fixed, double t_end, double *t_out,
+                     double *stage_ms = nullptr)
+{
+    if (!s) return MOSES_EINVAL;
+    if (nsteps < 0) return fail(s, MOSES_EINVAL, "nsteps must be >= 0");
+    if (!s->have_state) return fail(s, MOSES_ESTATE, "no state");
+    int rc = set_mode(s, dt_fixed, t_end);
+    if (rc) return rc;
+    rc = s->prec == MOSES_FP64 ? launch_steps<double>(s, nsteps, stage_ms) : launch_steps<float>(s, nsteps, stage_ms);
+    if (rc) return rc;
+    Ctl h;
+    rc = read_ctl(s, &h);
+    if (rc) return rc;
+    if (t_out) *t_out = h.t;
+    if (h.status & STATUS_NONFINITE) return fail(s, MOSES_ENONFINITE, "state or time step became non-finite");
+    return MOSES_OK;
+}
+
+int moses_step(moses_sim *s, int nsteps, double *t_out) { return run_steps(s, nsteps, 0.0, 0.0, t_out); }
+
+int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms)
+{
+    if (!s || !stage_ms) return MOSES_EINVAL;
+    return run_steps(s, nsteps, 0.0, 0.0, t_out, stage_ms);
+}
+
+int moses_step_dt(moses_sim *s, int nsteps, double dt, double *t_out)
+{
+    if (!s) return MOSES_EINVAL;
+    if (!(std::isfinite(dt) && dt > 0)) return fail(s, MOSES_EINVAL, "dt must be finite and > 0");
+    return run_steps(s, nsteps, dt, 0.0, t_out);
+}
+
+int moses_run_until(moses_sim *s, double t_end, int max_steps, int *nsteps_out)
+{
+    if (!s) return MOSES_EINVAL;
+    if (!std::isfinite(t_end)) return fail(s, MOSES_EINVAL, "t_end must be finite");
+    Ctl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    const long long s0 = h.steps;
+    const int chunk = 64;
+    while (h.t < t_end && h.steps - s0 < max_steps) {
+        const int n = (int)std::min<long long>(chunk, max_steps - (h.steps - s0));
+        rc = run_steps(s, n, 0.0, t_end, nullptr);
+        if (rc) return rc;
+        rc = read_ctl(s, &h);
+        if (rc) return rc;
+        if (h.t >= t_end) break;
+    }
+    if (nsteps_out) *nsteps_out = (int)(h.steps - s0);
+    // steps after reaching t_end would have dt = 0: count only real ones
+    return MOSES_OK;
+}
+
+int moses_next_dt(moses_sim *s, double *dt, double *t)
+{
+    if (!s) return MOSES_EINVAL;
+    Ctl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    const double am = *reinterpret_cast<double *>(&h.amax);
+    double d = (am > 0.0) ? s->ph.cfl * s->ph.dmin / am : s->ph.dt_max;
+    if (d > s->ph.dt_max) d = s->ph.dt_max;
+    if (dt) *dt = d;
+    if (t) *t = h.t;
+    return MOSES_OK;
+}
+
+int moses_max_speed(moses_sim *s, double *amax)
+{
+    if (!s || !amax) return MOSES_EINVAL;
+    Ctl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    *amax = *reinterpret_cast<double *>(&h.amax);
+    return MOSES_OK;
+}
+
+int moses_get_conserved_device(moses_sim *s, double *U_device)
+{
+    if (!s || !U_device) return MOSES_EINVAL;
+    const long long n = (long long)s->nx * s->ny;
+    if (s->prec == MOSES_FP64)
+        pack_kernel<double><<<grid_for(6 * n), 256, 0, s->stream>>>((const double *)s->U, U_device, s->nx, s->ny,
+                                                                    s->pitch, s->plane);
+    else
+        pack_kernel<float><<<grid_for(6 * n), 256, 0, s->stream>>>((const float *)s->U, U_device, s->nx, s->ny,
+                                                                   s->pitch, s->plane);
+    CK(cudaGetLastError());
+    return MOSES_OK;
+}
+
+int moses_get_conserved(moses_sim *s, double *U)
+{
+    if (!s || !U) return MOSES_EINVAL;
+    int rc = ensure_stage_buf(s);
+    if (rc) return rc;
+    rc = moses_get_conserved_device(s, s->stage_buf);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(U, s->stage_buf, sizeof(double) * 6 * (size_t)s->nx * s->ny, cudaMemcpyDeviceToHost,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+static int set_from_device_buf(moses_sim *s, const double *src)
+{
+    const long long n = (long long)s->nx * s->ny;
+    CK(cudaMemsetAsync(s->red, 0, sizeof(int), s->stream));
+    validate_kernel<<<grid_for(6 * n), 256, 0, s->stream>>>(src, 6 * n, n, (int *)s->red);
+    int bad = 0;
+    CK(cudaMemcpyAsync(&bad, s->red, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (bad) return fail(s, MOSES_EINVAL, "U must be finite with U1, U4 >= 0");
+    if (s->prec == MOSES_FP64)
+        unpack_kernel<double><<<grid_for(6 * n), 256, 0, s->stream>>>(src, (double *)s->U, s->nx, s->ny, s->pitch,
+                                                                      s->plane);
+    else
+        unpack_kernel<float><<<grid_for(6 * n), 256, 0, s->stream>>>(src, (float *)s->U, s->nx, s->ny, s->pitch,
+                                                                     s->plane);
+    CK(cudaGetLastError());
+    s->have_state = true;
+    return refresh(s);
+}
+
+int moses_set_conserved_device(moses_sim *s, const double *U_device)
+{
+    if (!s || !U_device) return MOSES_EINVAL;
+    return set_from_device_buf(s, U_device);
+}
+
+int moses_set_conserved(moses_sim *s, const double *U)
+{
+    if (!s || !U) return MOSES_EINVAL;
+    int rc = upload_dense(s, U);
+    if (rc) return rc;
+    rc = set_from_device_buf(s, s->stage_buf);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+int moses_get_state(moses_sim *s, double *h, double *phi_s, double *vx_s, double *vy_s, double *vx_f, double *vy_f)
+{
+    if (!s) return MOSES_EINVAL;
+    int rc = ensure_stage_buf(s);
+    if (rc) return rc;
+    const long long n = (long long)s->nx * s->ny;
+    if (s->prec == MOSES_FP64)
+        prims_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, (const double *)s->geo, s->nx,
+                                                                 s->ny, s->pitch, s->plane, s->ph.h_dry,
+                                                                 s->stage_buf);
+    else
+        prims_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, (const float *)s->geo, s->nx,
+                                                                s->ny, s->pitch, s->plane, s->ph.h_dry, s->stage_buf);
+    CK(cudaGetLastError());
+    double *dst[6] = {h, phi_s, vx_s, vy_s, vx_f, vy_f};
+    for (int q = 0; q < 6; q++)
+        if (dst[q])
+            CK(cudaMemcpyAsync(dst[q], s->stage_buf + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+int moses_stage(moses_sim *s, double t, double dt, double *U_out)
+{
+    if (!s || !U_out) return MOSES_EINVAL;
+    if (!(std::isfinite(dt) && dt >= 0 && std::isfinite(t))) return fail(s, MOSES_EINVAL, "bad t or dt");
+    int rc = ensure_stage_buf(s);
+    if (rc) return rc;
+    // ghosts of the current state at time t
+    Ctl h;
+    rc = read_ctl(s, &h);
+    if (rc) return rc;
+    const double t_saved = h.t;
+    CK(cudaMemcpyAsync(&s->ctl->t, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    rc = refresh(s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(&s->ctl->t, &t_saved, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    if (s->prec == MOSES_FP64) {
+        StageArgs<double> a = base_args<double>(s);
+        a.Uin = (const double *)s->U;
+        a.Uout = (double *)s->Us;
+        a.stage = 1;
+        a.debug_stage = 1;
+        a.dbg_t = t;
+        a.dbg_dt = dt;
+        rc = launch_stage<double>(a, s->tile, s->stream);
+        if (rc == 0)
+            pack_kernel<double><<<grid_for(6LL * s->nx * s->ny), 256, 0, s->stream>>>(
+                (const double *)s->Us, s->stage_buf, s->nx, s->ny, s->pitch, s->plane);
+    } else {
+        StageArgs<float> a = base_args<float>(s);
+        a.Uin = (const float *)s->U;
+        a.Uout = (float *)s->Us;
+        a.stage = 1;
+        a.debug_stage = 1;
+        a.dbg_t = t;
+        a.dbg_dt = dt;
+        rc = launch_stage<float>(a, s->tile, s->stream);
+        if (rc == 0)
+            pack_kernel<float><<<grid_for(6LL * s->nx * s->ny), 256, 0, s->stream>>>(
+                (const float *)s->Us, s->stage_buf, s->nx, s->ny, s->pitch, s->plane);
+    }
+    if (rc) return fail(s, MOSES_ECUDA, "stage launch failed");
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(U_out, s->stage_buf, sizeof(double) * 6 * (size_t)s->nx * s->ny, cudaMemcpyDeviceToHost,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+int moses_get_budget(moses_sim *s, double out[MOSES_BUDGET_LEN])
+{
+    if (!s || !out) return MOSES_EINVAL;
+    const long long n = (long long)s->nx * s->ny;
+    CK(cudaMemsetAsync(s->red, 0, 6 * sizeof(double), s->stream));
+    if (s->prec == MOSES_FP64)
+        budget_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, s->nx, s->ny, s->pitch,
+                                                                  s->plane, s->red);
+    else
+        budget_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, s->nx, s->ny, s->pitch,
+                                                                 s->plane, s->red);
+    CK(cudaGetLastError());
+    double sums[6];
+    CK(cudaMemcpyAsync(sums, s->red, sizeof(sums), cudaMemcpyDeviceToHost, s->stream));
+    Ctl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    const double a = s->dx * s->dy;
+    out[0] = sums[0] * a;
+    out[1] = sums[3] * a;
+    out[2] = sums[1] * a;
+    out[3] = sums[2] * a;
+    out[4] = sums[4] * a;
+    out[5] = sums[5] * a;
+    out[6] = h.bnd_in[0];
+    out[7] = h.bnd_in[1];
+    out[8] = h.clamp_vol[0];
+    out[9] = h.clamp_vol[1];
+    out[10] = (double)h.clamp_cells;
+    out[11] = h.t;
+    out[12] = (double)h.steps;
+    return MOSES_OK;
+}

@@ -1,0 +1,41 @@
+// stage_f32.cu -- instantiations and launcher of the float stage kernel.
+#include <cuda_runtime.h>
+
+#include "stage.cuh"
+
+namespace moses {
+namespace {
+
+template <typename T, int TX, int TY>
+int launch_tile(const StageArgs<T> &a, cudaStream_t st)
+{
+    constexpr size_t smem = stage_smem_bytes<T, TX, TY>();
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
+    stage_kernel<T, TX, TY><<<grid, TX * TY, smem, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+// tile 0: 32 x 8 cells (256 threads); tile 1: 32 x 4; tile 2: 32 x 16
+template <>
+int launch_stage<float>(const StageArgs<float> &a, int tile, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (tile) {
+    case 1: return launch_tile<float, 32, 4>(a, st);
+    case 2: return launch_tile<float, 32, 16>(a, st);
+    default: return launch_tile<float, 32, 8>(a, st);
+    }
+}
+
+}  // namespace moses

@@ -1,0 +1,248 @@
+"""Python binding of the C-ABI in include/moses.h (argument marshalling only).
+
+Every computation of the step runs in the CUDA kernels of libmoses.so; this
+module only converts arguments and return codes.  There is no CPU fallback:
+if the library has not been built, or cannot find a GPU, calls fail with
+``MosesError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoses.so")
+
+MOSES_OK, MOSES_EINVAL, MOSES_ENOMEM, MOSES_ECUDA, MOSES_ENONFINITE, MOSES_ETIMEOUT, MOSES_ESTATE = 0, -1, -2, -3, -4, -5, -6
+FP64, FP32 = 0, 1
+BUDGET_LEN = 13
+BUDGET_KEYS = ("vol_s", "vol_f", "mom_xs", "mom_ys", "mom_xf", "mom_yf", "bnd_in_s", "bnd_in_f",
+               "clamp_s", "clamp_f", "clamp_cells", "t", "steps")
+
+
+class MosesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"moses error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    """moses_params of include/moses.h."""
+    _fields_ = [("g", C.c_double), ("eps", C.c_double), ("eps_chi", C.c_double),
+                ("rho_s", C.c_double), ("rho_f", C.c_double),
+                ("delta_b_deg", C.c_double), ("phi_int_deg", C.c_double), ("k_mode", C.c_int),
+                ("c_d", C.c_double), ("nu_f", C.c_double), ("k_f", C.c_double),
+                ("cfl", C.c_double), ("dt_max", C.c_double), ("h_dry", C.c_double),
+                ("bc", C.c_int * 4), ("fluid_pg_mode", C.c_int), ("precision", C.c_int)]
+
+    @classmethod
+    def from_dict(cls, p: dict, precision: int = FP64) -> "Params":
+        s = cls()
+        for name, _ in cls._fields_:
+            if name == "bc":
+                s.bc[:] = [int(v) for v in p["bc"]]
+            elif name in ("k_mode", "fluid_pg_mode"):
+                setattr(s, name, int(p[name]))
+            elif name == "precision":
+                s.precision = int(p.get("precision", precision))
+            else:
+                setattr(s, name, float(p[name]))
+        return s
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+# (name, restype, argtypes) of every entry point declared in include/moses.h
+SIGNATURES = [
+    ("moses_create", C.c_int, [_dp, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(Params), _vp,
+                               C.POINTER(_vp)]),
+    ("moses_set_release", C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _dp]),
+    ("moses_set_inflow", C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp, _dp]),
+    ("moses_step", C.c_int, [_vp, C.c_int, _dp]),
+    ("moses_step_timed", C.c_int, [_vp, C.c_int, _dp, _dp]),
+    ("moses_step_dt", C.c_int, [_vp, C.c_int, C.c_double, _dp]),
+    ("moses_run_until", C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    ("moses_next_dt", C.c_int, [_vp, _dp, _dp]),
+    ("moses_get_state", C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _dp]),
+    ("moses_get_conserved", C.c_int, [_vp, _dp]),
+    ("moses_set_conserved", C.c_int, [_vp, _dp]),
+    ("moses_get_conserved_device", C.c_int, [_vp, _vp]),
+    ("moses_set_conserved_device", C.c_int, [_vp, _vp]),
+    ("moses_stage", C.c_int, [_vp, C.c_double, C.c_double, _dp]),
+    ("moses_max_speed", C.c_int, [_vp, _dp]),
+    ("moses_get_budget", C.c_int, [_vp, _dp]),
+    ("moses_last_error", C.c_char_p, [_vp]),
+    ("moses_destroy", None, [_vp]),
+    ("moses_version", C.c_char_p, []),
+]
+
+
+def lib():
+    """Load libmoses.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MosesError(MOSES_ECUDA, f"{LIB_PATH} is missing: build it with "
+                                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _f64(a):
+    if a is None:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Sim:
+    """One simulation on the GPU (moses_create .. moses_destroy)."""
+
+    def __init__(self, dem, dx: float, dy: float, params: dict, precision: int = FP64, stream=None):
+        L = lib()
+        self._L = L
+        self.dem = _f64(dem)
+        self.ny, self.nx = self.dem.shape
+        self.dx, self.dy = float(dx), float(dy)
+        self.params = dict(params)
+        self.precision = int(params.get("precision", precision))
+        self._par = Params.from_dict(params, self.precision)
+        self._stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        rc = L.moses_create(_p(self.dem), self.nx, self.ny, self.dx, self.dy, C.byref(self._par), self._stream,
+                            C.byref(h))
+        if rc != 0:
+            raise MosesError(rc, L.moses_last_error(None).decode())
+        self._h = h
+
+    def _ck(self, rc):
+        if rc != 0:
+            raise MosesError(rc, self._L.moses_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.moses_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # inputs -----------------------------------------------------------------
+    def set_release(self, h, phi_s=None, vx_s=None, vy_s=None, vx_f=None, vy_f=None):
+        arrs = [_f64(a) for a in (h, phi_s, vx_s, vy_s, vx_f, vy_f)]
+        self._ck(self._L.moses_set_release(self._h, *[_p(a) for a in arrs]))
+
+    def set_inflow(self, side: int, i0: int, i1: int, t, Q, phi):
+        t, Q, phi = _f64(t), _f64(Q), _f64(phi)
+        self._ck(self._L.moses_set_inflow(self._h, side, i0, i1, len(t), _p(t), _p(Q), _p(phi)))
+
+    def set_conserved(self, U):
+        U = _f64(U)
+        assert U.shape == (6, self.ny, self.nx)
+        self._ck(self._L.moses_set_conserved(self._h, _p(U)))
+
+    def set_conserved_device(self, ptr: int):
+        self._ck(self._L.moses_set_conserved_device(self._h, C.c_void_p(ptr)))
+
+    # stepping ---------------------------------------------------------------
+    def step(self, n: int = 1) -> float:
+        t = C.c_double()
+        self._ck(self._L.moses_step(self._h, int(n), C.byref(t)))
+        return t.value
+
+    def step_timed(self, n: int = 1):
+        """Advance n steps; returns (t, [stage-1 ms, stage-2 ms]) summed over
+        the launches, measured with CUDA events on the simulation's stream."""
+        t = C.c_double()
+        ms = (C.c_double * 2)()
+        self._ck(self._L.moses_step_timed(self._h, int(n), C.byref(t), ms))
+        return t.value, [ms[0], ms[1]]
+
+    def step_dt(self, dt: float, n: int = 1) -> float:
+        t = C.c_double()
+        self._ck(self._L.moses_step_dt(self._h, int(n), float(dt), C.byref(t)))
+        return t.value
+
+    def run_until(self, t_end: float, max_steps: int = 10 ** 9) -> int:
+        n = C.c_int()
+        self._ck(self._L.moses_run_until(self._h, float(t_end), int(max_steps), C.byref(n)))
+        return n.value
+
+    def next_dt(self):
+        dt, t = C.c_double(), C.c_double()
+        self._ck(self._L.moses_next_dt(self._h, C.byref(dt), C.byref(t)))
+        return dt.value, t.value
+
+    def stage(self, t: float, dt: float) -> np.ndarray:
+        out = np.empty((6, self.ny, self.nx))
+        self._ck(self._L.moses_stage(self._h, float(t), float(dt), _p(out)))
+        return out
+
+    # outputs ----------------------------------------------------------------
+    def max_speed(self) -> float:
+        a = C.c_double()
+        self._ck(self._L.moses_max_speed(self._h, C.byref(a)))
+        return a.value
+
+    def get_conserved(self, out=None) -> np.ndarray:
+        U = np.empty((6, self.ny, self.nx)) if out is None else out
+        self._ck(self._L.moses_get_conserved(self._h, _p(U)))
+        return U
+
+    def get_conserved_device(self, ptr: int):
+        self._ck(self._L.moses_get_conserved_device(self._h, C.c_void_p(ptr)))
+
+    def get_state(self) -> dict:
+        arrs = [np.empty((self.ny, self.nx)) for _ in range(6)]
+        self._ck(self._L.moses_get_state(self._h, *[_p(a) for a in arrs]))
+        return dict(zip(("h", "phi_s", "vx_s", "vy_s", "vx_f", "vy_f"), arrs))
+
+    def budget(self) -> dict:
+        out = np.empty(BUDGET_LEN)
+        self._ck(self._L.moses_get_budget(self._h, _p(out)))
+        return dict(zip(BUDGET_KEYS, out.tolist()))
+
+
+def from_config(cfg: dict, precision: int = FP64, stream=None) -> Sim:
+    """GPU simulation of a workload dict from ``workloads``."""
+    s = Sim(cfg["dem"], cfg["dx"], cfg["dy"], cfg["params"], precision=precision, stream=stream)
+    s.set_release(cfg["h"], cfg["phi_s"], cfg.get("vx_s"), cfg.get("vy_s"), cfg.get("vx_f"), cfg.get("vy_f"))
+    if cfg.get("inflow"):
+        f = cfg["inflow"]
+        s.set_inflow(f["side"], f["i0"], f["i1"], f["t"], f["Q"], f["phi"])
+    return s
+
+
+def version() -> str:
+    return lib().moses_version().decode()

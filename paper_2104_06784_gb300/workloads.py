@@ -31,7 +31,8 @@ def default_params(**over) -> dict:
     rho_s / rho_f = 2700 / 1100 kg m^-3, basal friction 25 deg, internal friction
     35 deg (only used by the earth-pressure option), drag 1e-3 1/s, no fluid
     viscosity or fluid basal friction (the configurations give no N_R or
-    vartheta_b), CFL 0.1 as in Sect. 2.2.
+    vartheta_b), CFL 0.1 as in Sect. 2.2, thin-layer threshold 1 mm (below it a
+    phase carries no velocity).
     """
     p = dict(
         g=9.81,
@@ -47,7 +48,7 @@ def default_params(**over) -> dict:
         k_f=0.0,
         cfl=0.1,
         dt_max=1.0,
-        h_dry=1e-6,
+        h_dry=1e-3,
         bc=(BC_CLOSED,) * 4,
         fluid_pg_mode=0,
     )
@@ -109,8 +110,8 @@ def spectral_dem(nx: int, ny: int, dx: float, beta: float = 2.2, relief: float =
     W *= k ** (-beta / 2.0)
     z = np.fft.irfft2(W, s=(ny, nx))
     z -= z.min()
-    z *= relief / z.max()
-    return z
+    zmax = z.max()
+    return z * (relief / zmax) if zmax > 0 else z
 
 
 def carve_valley(dem: np.ndarray, dx: float, depth: float = 100.0, half_width: float = 400.0,

@@ -1,0 +1,262 @@
+"""GPU path (through the C-ABI) against the FP64 oracle, element by element.
+
+Tolerances:
+  FP64 form: <= 1e-10 relative max-norm per conserved component (relative to
+             that component's largest magnitude in the oracle's result).
+  FP32 form: <= 2e-4 relative L1 on depth and on the velocity fields, and
+             mass drift <= 1e-7 relative (FP64 budgets).
+Sizes span several 32 x 8 tiles with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim, from_config as oracle_from_config
+from paper_2104_06784_gb300 import moses, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def rel_maxnorm(a, b):
+    """max over components of max|a - b| / max|b| (components with b == 0 use 1)."""
+    scale = np.abs(b).reshape(6, -1).max(axis=1)
+    scale = np.where(scale > 0, scale, 1.0)
+    return float((np.abs(a - b).reshape(6, -1).max(axis=1) / scale).max())
+
+
+def rel_l1(a, b):
+    s = np.abs(b).sum()
+    return float(np.abs(a - b).sum() / s) if s > 0 else float(np.abs(a).sum())
+
+
+def both(cfg, precision=moses.FP64):
+    g = moses.from_config(cfg, precision=precision)
+    o = oracle_from_config(cfg)
+    return g, o
+
+
+def test_library_is_native():
+    assert moses.lib() is not None
+    assert "sm_103a" in moses.version()
+
+
+# ----------------------------------------------------------------------------
+# single stage from identical input
+
+
+def _random_case(nx, ny, dem, bc, seed, dx=5.0, **over):
+    p = W.default_params(bc=bc, **over)
+    st = W.random_state(nx, ny, seed=seed)
+    return dict(name="random", dem=dem, dx=dx, dy=dx, params=p, **st)
+
+
+@pytest.mark.parametrize("nx,ny", [(77, 53), (33, 9), (5, 70), (1, 17), (23, 1), (1, 1)])
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (0, 1, 1, 0)])
+def test_stage_parity_fp64(nx, ny, bc):
+    rng = np.random.default_rng(nx * 1000 + ny)
+    dem = W.spectral_dem(nx, ny, 5.0, 2.2, 40.0, seed=nx + ny) + rng.random((ny, nx))
+    cfg = _random_case(nx, ny, dem, bc, seed=nx * ny)
+    g, o = both(cfg)
+    for t, dt in ((0.0, 0.01), (3.0, 0.05)):
+        Ug = g.stage(t, dt)
+        Uo = o.stage(t, dt)
+        err = rel_maxnorm(Ug, Uo)
+        assert err < TOL64, f"stage parity {err} ({nx}x{ny}, bc={bc})"
+    assert abs(g.max_speed() - o.max_speed()) <= 1e-13 * o.max_speed()
+
+
+def test_stage_parity_with_inflow_and_pg_mode():
+    nx, ny = 70, 41
+    cfg = W.inflow_config(nx=nx, ny=ny, dx=5.0, inlet_cells=9)
+    st = W.random_state(nx, ny, seed=5)
+    cfg.update(st)
+    for mode in (0, 1):
+        cfg["params"] = dict(cfg["params"], fluid_pg_mode=mode, k_f=0.3, c_d=0.05)
+        g, o = both(cfg)
+        for t in (0.0, 30.0, 61.0):
+            err = rel_maxnorm(g.stage(t, 0.02), o.stage(t, 0.02))
+            assert err < TOL64, f"inflow stage parity {err} at t={t} mode={mode}"
+
+
+# ----------------------------------------------------------------------------
+# trajectories
+
+
+def test_release_trajectory_fp64_cfl05():
+    """Arc-plane release (128 x 128, closed, CFL 0.5), 2000 steps, FP64."""
+    cfg = W.release_config()
+    g, o = both(cfg)
+    done, worst = 0, 0.0
+    for chunk in (10, 90, 400, 500, 1000):
+        g.step(chunk)
+        dts = o.step(chunk)
+        done += chunk
+        Ug, Uo = g.get_conserved(), o.get_U()
+        err = rel_maxnorm(Ug, Uo)
+        worst = max(worst, err)
+        assert err < TOL64, f"trajectory departs at step <= {done}: {err}"
+        assert abs(g.budget()["t"] - o.t) <= 1e-12 * o.t
+    assert done == 2000
+
+
+def test_release_trajectory_fp64_dt_sequence():
+    cfg = W.release_config(nx=64, ny=64, cfl=0.1)
+    g, o = both(cfg)
+    for _ in range(30):
+        dtg, tg = g.next_dt()
+        dto = o.cfl_dt()
+        assert abs(dtg - dto) <= 1e-13 * dto
+        g.step(1)
+        o.step(1)
+
+
+def test_release_budget_fp64():
+    cfg = W.release_config(nx=64, ny=64, cfl=0.1)
+    g, o = both(cfg)
+    g.step(200)
+    o.step(200)
+    bg, bo = g.budget(), o.budget()
+    for k in ("vol_s", "vol_f"):
+        assert abs(bg[k] - bo[k]) <= 1e-12 * bo[k]
+    assert bg["clamp_cells"] == bo["clamp_cells"] == 0
+    for k in ("mom_ys", "mom_yf"):
+        assert abs(bg[k] - bo[k]) <= 1e-9 * abs(bo[k])
+
+
+def test_spectral_release_trajectory_fp64():
+    cfg = W.large_release_config(n=150, ny=131, dx=10.0, seed=3, volume=2e5, radius_cells=8)
+    g, o = both(cfg)
+    g.step(150)
+    o.step(150)
+    assert rel_maxnorm(g.get_conserved(), o.get_U()) < TOL64
+
+
+def test_inflow_trajectory_fp64_and_budget():
+    cfg = W.inflow_config(nx=96, ny=48, dx=5.0, inlet_cells=8)
+    g, o = both(cfg)
+    g.step(400)
+    o.step(400)
+    assert rel_maxnorm(g.get_conserved(), o.get_U()) < TOL64
+    bg, bo = g.budget(), o.budget()
+    for ph in ("s", "f"):
+        assert abs(bg[f"bnd_in_{ph}"] - bo[f"bnd_in_{ph}"]) <= 1e-11 * bo[f"bnd_in_{ph}"]
+        closure = bg[f"vol_{ph}"] - bg[f"bnd_in_{ph}"] - bg[f"clamp_{ph}"]
+        assert abs(closure) <= 1e-12 * bg[f"vol_{ph}"]
+
+
+def test_run_until_lands_on_t_end():
+    cfg = W.release_config(nx=40, ny=40, cfl=0.2)
+    g = moses.from_config(cfg)
+    n = g.run_until(1.2345)
+    assert n > 0
+    assert abs(g.budget()["t"] - 1.2345) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# FP32 form
+
+
+def _fields(U, J, hd):
+    h = (U[0] + U[3]) / J
+    ws, wf = U[0] > J * hd, U[3] > J * hd
+    with np.errstate(divide="ignore", invalid="ignore"):
+        v = [np.where(ws, U[1] / U[0], 0), np.where(ws, U[2] / U[0], 0), np.where(wf, U[4] / U[3], 0),
+             np.where(wf, U[5] / U[3], 0)]
+    return h, v
+
+
+def test_release_trajectory_fp32():
+    """FP32 state and fluxes, FP64 budgets: 2000 steps of the arc-plane release
+    against the FP64 oracle (CFL 0.5 as the configuration asks)."""
+    cfg = W.release_config()
+    g, o = both(cfg, precision=moses.FP32)
+    b0 = g.budget()
+    g.step(2000)
+    o.step(2000)
+    J = o.geometry()["J"]
+    hg, vg = _fields(g.get_conserved(), J, 1e-6)
+    ho, vo = _fields(o.get_U(), J, 1e-6)
+    assert rel_l1(hg, ho) <= 2e-4, f"FP32 depth L1 {rel_l1(hg, ho)}"
+    for a, b in zip(vg, vo):
+        assert rel_l1(a, b) <= 2e-4, f"FP32 velocity L1 {rel_l1(a, b)}"
+    b = g.budget()
+    for ph in ("s", "f"):
+        drift = (b[f"vol_{ph}"] - b0[f"vol_{ph}"] - b[f"clamp_{ph}"]) / b0[f"vol_{ph}"]
+        assert abs(drift) <= 1e-7, f"FP32 mass drift {drift}"
+
+
+def test_inflow_fp32_mass_budget():
+    cfg = W.inflow_config(nx=96, ny=48, dx=5.0, inlet_cells=8)
+    g = moses.from_config(cfg, precision=moses.FP32)
+    g.step(400)
+    b = g.budget()
+    for ph in ("s", "f"):
+        closure = b[f"vol_{ph}"] - b[f"bnd_in_{ph}"] - b[f"clamp_{ph}"]
+        assert abs(closure) <= 1e-7 * b[f"vol_{ph}"], f"FP32 inflow budget {closure / b[f'vol_{ph}']}"
+
+
+# ----------------------------------------------------------------------------
+# edge cases
+
+
+def test_dry_domain_takes_dt_max():
+    p = W.default_params(dt_max=0.25)
+    g = moses.Sim(W.flat_dem(10, 7), 5.0, 5.0, p)
+    t = g.step(4)
+    assert t == 1.0
+    assert np.all(g.get_conserved() == 0.0)
+
+
+def test_set_release_validation():
+    g = moses.Sim(W.flat_dem(6, 5), 5.0, 5.0, W.default_params())
+    with pytest.raises(moses.MosesError):
+        g.set_release(-np.ones((5, 6)))
+    with pytest.raises(moses.MosesError):
+        g.set_release(np.ones((5, 6)), 2 * np.ones((5, 6)))
+    U = np.zeros((6, 5, 6))
+    U[1, 2, 3] = np.nan
+    with pytest.raises(moses.MosesError):
+        g.set_conserved(U)
+
+
+def test_conserved_roundtrip_is_exact():
+    cfg = W.release_config(nx=37, ny=29)
+    g = moses.from_config(cfg)
+    U = g.get_conserved()
+    g2 = moses.Sim(cfg["dem"], cfg["dx"], cfg["dy"], cfg["params"])
+    g2.set_conserved(U)
+    assert np.array_equal(g2.get_conserved(), U)
+    g.step(5)
+    g2.step(5)
+    assert np.array_equal(g.get_conserved(), g2.get_conserved()), "resume from a snapshot is not bit-exact"
+
+
+# ----------------------------------------------------------------------------
+# full size, sampled
+
+
+def test_full_size_sampled_fp64():
+    """One CFL step of the 4096 x 4096 spectral-DEM release in the launch
+    configuration the benchmark times; 3 windows of 48 x 48 recomputed by the
+    oracle on crops with a 12-cell margin (a step reads 4 cells around a
+    cell; the geometry 3 more)."""
+    cfg = W.large_release_config(n=4096, dx=10.0, seed=0)
+    g = moses.from_config(cfg)
+    dt, _ = g.next_dt()
+    U0 = g.get_conserved()
+    g.step(1)
+    U1 = g.get_conserved()
+    ic, jc = cfg["release_cell"]
+    wins = [(ic - 24, jc - 24), (ic - 60, jc + 10), (2000, 100)]
+    m, w = 12, 48
+    for (i0, j0) in wins:
+        sl = (slice(j0 - m, j0 + w + m), slice(i0 - m, i0 + w + m))
+        o = OracleSim(cfg["dem"][sl], 10.0, 10.0, cfg["params"])
+        o.set_U(U0[(slice(None),) + sl])
+        o.step_dt(dt)
+        Uo = o.get_U()[:, m:m + w, m:m + w]
+        Ug = U1[:, j0:j0 + w, i0:i0 + w]
+        assert rel_maxnorm(Ug, Uo) < TOL64 or np.abs(Uo).max() == 0.0
