@@ -177,6 +177,37 @@ const char *moses_last_error(const moses_sim *s);
 /* Release all device memory of s.  NULL is ignored. */
 void moses_destroy(moses_sim *s);
 
+/* ---- Step without device allocation --------------------------------------
+ * The paper has no counterpart to this call.  It is for callers that cannot
+ * let a library allocate device memory: code that records its work into a
+ * CUDA graph, host programs that reserve all device memory in their own pool,
+ * processes under a hard device-memory limit.  It advances one FP64 Heun step
+ * of a grid of at most MOSES_STATIC_MAX_NX x MOSES_STATIC_MAX_NY cells and
+ * calls no cudaMalloc, cudaFree or allocating library routine: its scratch
+ * (extended DEM, geometry, padded state, Heun intermediate, control block,
+ * about 5.6 MB) is a statically sized device array that every GPU loading the
+ * library holds until the process exits.
+ *   dem_device   nx*ny bed elevations (device memory, caller's)
+ *   U_in_device  6*nx*ny conserved state, same plane order as
+ *                moses_get_conserved (device memory, caller's)
+ *   U_out_device 6*nx*ny, receives U^{n+1}; may equal U_in_device
+ *   t            time of U_in (start of the step); closed / transmissive
+ *                boundaries only (no inflow segments); p->precision must be
+ *                MOSES_FP64 and p->nu_f 0
+ *   dt_out       host pointer receiving the time step taken (the call then
+ *                synchronises the stream), or NULL (fully asynchronous)
+ *   stream       cudaStream_t or NULL
+ * The first call on a device looks up that device's copy of the array
+ * (cudaGetSymbolAddress); make it before any stream capture.  Every call
+ * shares the array, so calls that overlap on the GPU (other streams, other
+ * threads) race; serialise them.  Errors (read with moses_last_error(NULL)):
+ * EINVAL for sizes beyond the limit or bad arguments, ECUDA. */
+#define MOSES_STATIC_MAX_NX 128
+#define MOSES_STATIC_MAX_NY 128
+int moses_step_static(const double *dem_device, int nx, int ny, double dx, double dy,
+                      const moses_params *p, const double *U_in_device, double *U_out_device,
+                      double t, double *dt_out, void *stream);
+
 /* Library build identification (architecture, precision forms). */
 const char *moses_version(void);
 

@@ -938,3 +938,109 @@ int moses_get_budget(moses_sim *s, double out[MOSES_BUDGET_LEN])
     out[12] = (double)h.steps;
     return MOSES_OK;
 }
+
+// ---------------------------------------------------------------------------
+// No-allocation step (moses_step_static).  Some callers cannot let a library
+// call cudaMalloc: code that records its work into a CUDA graph, hosts that
+// pre-reserve all device memory in their own pool, or processes that run
+// under a hard device-memory limit.  For them, one FP64 Heun step of a small
+// grid runs with all of its scratch (extended DEM, geometry planes, padded
+// state, Heun intermediate, control block) in the statically sized device
+// array below, which every GPU that loads this library holds until exit.
+// Every call shares the array: calls that overlap on the GPU race.
+
+namespace {
+
+constexpr int kStaticPitch = ((MOSES_STATIC_MAX_NX + 2 * GH) + 31) / 32 * 32;
+constexpr long long kStaticPlane = (long long)kStaticPitch * (MOSES_STATIC_MAX_NY + 2 * GH);
+constexpr long long kStaticCtl = 64;  // doubles reserved for the control block
+constexpr long long kStaticDem = ((long long)(MOSES_STATIC_MAX_NX + 6) * (MOSES_STATIC_MAX_NY + 6) + 31) / 32 * 32;
+constexpr long long kStaticDoubles = kStaticCtl + kStaticDem + (long long)(GEO_PLANES + 12) * kStaticPlane;
+static_assert(sizeof(Ctl) <= kStaticCtl * sizeof(double), "control block does not fit");
+
+static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
+
+double *g_static_ptr[64] = {};
+
+__global__ void static_ctl_init_kernel(Ctl *ctl, double t)
+{
+    *ctl = Ctl{};
+    ctl->t = t;
+}
+
+}  // namespace
+
+int moses_step_static(const double *dem_device, int nx, int ny, double dx, double dy, const moses_params *p,
+                      const double *U_in_device, double *U_out_device, double t, double *dt_out, void *stream)
+{
+    moses_sim *s = nullptr;  // errors of this call go to moses_last_error(NULL)
+    if (!dem_device || !p || !U_in_device || !U_out_device) return fail(s, MOSES_EINVAL, "NULL argument");
+    if (nx < 1 || ny < 1 || nx > MOSES_STATIC_MAX_NX || ny > MOSES_STATIC_MAX_NY)
+        return fail(s, MOSES_EINVAL, "moses_step_static: grid must be 1..128 x 1..128 cells (static scratch limit)");
+    if (!(std::isfinite(dx) && std::isfinite(dy) && dx > 0 && dy > 0) || !std::isfinite(t))
+        return fail(s, MOSES_EINVAL, "dx, dy must be finite and > 0, t finite");
+    std::string why;
+    if (check_params(p, why)) return fail(s, MOSES_EINVAL, why);
+    if (p->precision != MOSES_FP64) return fail(s, MOSES_EINVAL, "moses_step_static runs the FP64 form only");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(s, MOSES_EINVAL, "device ordinal out of range");
+    if (!g_static_ptr[dev]) {
+        // host code may not use the array's name as a device address: ask the
+        // runtime for this device's copy (first call per device; do it before
+        // any stream capture)
+        void *ptr = nullptr;
+        CK(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        g_static_ptr[dev] = (double *)ptr;
+    }
+    double *base = g_static_ptr[dev];
+    cudaStream_t st = (cudaStream_t)stream;
+    const int pitch = ((nx + 2 * GH) + 31) / 32 * 32;
+    const long long plane = (long long)pitch * (ny + 2 * GH);
+    Ctl *ctl = (Ctl *)base;
+    double *bext = base + kStaticCtl;
+    double *geo = bext + kStaticDem;
+    double *U = geo + GEO_PLANES * plane;
+    double *Us = U + 6 * plane;
+    const long long n = (long long)nx * ny;
+    // everything read below is written first except the unused tile corners:
+    // clear the state planes so that stale data of earlier calls never enters
+    CK(cudaMemsetAsync(U, 0, sizeof(double) * 12 * plane, st));
+    static_ctl_init_kernel<<<1, 1, 0, st>>>(ctl, t);
+    extend_dem_kernel<<<grid_for((long long)(nx + 6) * (ny + 6)), 256, 0, st>>>(dem_device, nx, ny, bext);
+    geometry_kernel<double><<<grid_for((long long)(nx + 4) * (ny + 4)), 256, 0, st>>>(bext, nx, ny, pitch, plane, dx,
+                                                                                     dy, geo);
+    unpack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U_in_device, U, nx, ny, pitch, plane);
+    CK(cudaGetLastError());
+    StageArgs<double> a{};
+    a.geo = geo;
+    a.ctl = ctl;
+    a.inflow = nullptr;
+    a.n_inflow = 0;
+    a.nx = nx;
+    a.ny = ny;
+    a.pitch = pitch;
+    a.plane = plane;
+    a.ph = make_phys(p, dx, dy);
+    fill_ghosts_kernel<double><<<grid_for(n), 256, 0, st>>>(a, U, t);
+    max_speed_kernel<double><<<grid_for(n), 256, 0, st>>>(U, geo, nx, ny, pitch, plane, a.ph, &ctl->amax);
+    CK(cudaGetLastError());
+    StageArgs<double> a1 = a, a2 = a;
+    a1.Uin = U;
+    a1.Uout = Us;
+    a1.stage = 1;
+    a2.Uin = Us;
+    a2.Un = U;
+    a2.Uout = U;
+    a2.stage = 2;
+    a2.want_amax = 1;
+    if (launch_stage<double>(a1, 0, st) || launch_stage<double>(a2, 0, st))
+        return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
+    pack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U, U_out_device, nx, ny, pitch, plane);
+    CK(cudaGetLastError());
+    if (dt_out) {
+        CK(cudaMemcpyAsync(dt_out, &ctl->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return MOSES_OK;
+}

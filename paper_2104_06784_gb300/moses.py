@@ -75,6 +75,8 @@ SIGNATURES = [
     ("moses_stage", C.c_int, [_vp, C.c_double, C.c_double, _dp]),
     ("moses_max_speed", C.c_int, [_vp, _dp]),
     ("moses_get_budget", C.c_int, [_vp, _dp]),
+    ("moses_step_static", C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(Params), _vp, _vp,
+                                    C.c_double, _dp, _vp]),
     ("moses_last_error", C.c_char_p, [_vp]),
     ("moses_destroy", None, [_vp]),
     ("moses_version", C.c_char_p, []),
