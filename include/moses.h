@@ -185,7 +185,7 @@ void moses_destroy(moses_sim *s);
  * of a grid of at most MOSES_STATIC_MAX_NX x MOSES_STATIC_MAX_NY cells and
  * calls no cudaMalloc, cudaFree or allocating library routine: its scratch
  * (extended DEM, geometry, padded state, Heun intermediate, control block,
- * about 5.6 MB) is a statically sized device array that every GPU loading the
+ * about 7.7 MB) is a statically sized device array that every GPU loading the
  * library holds until the process exits.
  *   dem_device   nx*ny bed elevations (device memory, caller's)
  *   U_in_device  6*nx*ny conserved state, same plane order as

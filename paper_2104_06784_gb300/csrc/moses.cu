@@ -106,7 +106,7 @@ struct Slopes {
 
 template <typename T>
 __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, long long plane, double dx,
-                                double dy, T *geo)
+                                double dy, Phys ph, T *geo)
 {
     const int W = nx + 4, H = ny + 4;  // padded cell range [-2, n+2)
     const long long n = (long long)W * H;
@@ -115,10 +115,13 @@ __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, l
     auto slopes = [&](int i, int j) {
         return Slopes{(B(i + 1, j) - B(i - 1, j)) / (2.0 * dx), (B(i, j + 1) - B(i, j - 1)) / (2.0 * dy)};
     };
+    auto put = [&](int q, long long g, double v) { geo[q * plane + g] = (T)v; };
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(e / W) - 2, i = (int)(e % W) - 2;
         const long long g = cell_index(i, j, pitch);
-        // cell centre
+        // cell centre: slopes by central differences, curvature by second
+        // differences; Omega_b = [(1,0,bX), (0,1,bY), n], J = det, A = 2x2
+        // block of its inverse (the inverse metric of the bed surface)
         {
             const Slopes s = slopes(i, j);
             const double bXX = (B(i + 1, j) - 2.0 * B(i, j) + B(i - 1, j)) / (dx * dx);
@@ -127,18 +130,25 @@ __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, l
             const double s2 = 1.0 + (s.bX * s.bX + s.bY * s.bY);
             const double J = sqrt(s2), c = 1.0 / J, c2 = 1.0 / s2;
             const double A11 = (1.0 + s.bY * s.bY) * c2, A12 = -s.bX * s.bY * c2, A22 = (1.0 + s.bX * s.bX) * c2;
-            geo[GC_J * plane + g] = (T)J;
-            geo[GC_C * plane + g] = (T)c;
-            geo[GC_BX * plane + g] = (T)s.bX;
-            geo[GC_BY * plane + g] = (T)s.bY;
-            geo[GC_A11 * plane + g] = (T)A11;
-            geo[GC_A12 * plane + g] = (T)A12;
-            geo[GC_A22 * plane + g] = (T)A22;
-            geo[GC_KXX * plane + g] = (T)(c * bXX);
-            geo[GC_KXY * plane + g] = (T)(c * bXY);
-            geo[GC_KYY * plane + g] = (T)(c * bYY);
-            geo[GC_G11 * plane + g] = (T)(A11 * c2);
-            geo[GC_G22 * plane + g] = (T)(A22 * c2);
+            put(GC_J, g, J);
+            put(GC_C, g, c);
+            put(GC_JHD, g, J * ph.h_dry);
+            put(GC_GC1, g, ph.g_1ma * c);
+            put(GC_GCF, g, ph.g * c);
+            put(GC_BX, g, s.bX);
+            put(GC_BY, g, s.bY);
+            put(GC_MNX, g, -c * s.bX);
+            put(GC_MNY, g, -c * s.bY);
+            put(GC_A11, g, A11);
+            put(GC_A12, g, A12);
+            put(GC_A22, g, A22);
+            put(GC_KXX, g, c * bXX);
+            put(GC_KXY2, g, 2.0 * c * bXY);
+            put(GC_KYY, g, c * bYY);
+            put(GC_SXS, g, ph.kap_s * A11 * c2);
+            put(GC_SXF, g, 2.0 * ph.kap_f * A11 * c2);
+            put(GC_SYS, g, ph.kap_s * A22 * c2);
+            put(GC_SYF, g, 2.0 * ph.kap_f * A22 * c2);
         }
         // x-face (i+1/2, j): normal slope by the face difference, transverse
         // slope as the mean of the two cells' central differences
@@ -147,20 +157,28 @@ __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, l
             const double bY = 0.5 * (slopes(i, j).bY + slopes(i + 1, j).bY);
             const double s2 = 1.0 + (bX * bX + bY * bY);
             const double c2 = 1.0 / s2;
-            geo[GX_J * plane + g] = (T)sqrt(s2);
-            geo[GX_GN * plane + g] = (T)((1.0 + bY * bY) * c2 * c2);
-            geo[GX_GT * plane + g] = (T)(-bX * bY * c2 * c2);
-            geo[GX_C2 * plane + g] = (T)c2;
+            const double An = (1.0 + bY * bY) * c2 * c2, At = -bX * bY * c2 * c2;  // A11 c^2, A12 c^2
+            put(GX_JHD, g, sqrt(s2) * ph.h_dry);
+            put(GX_SN, g, ph.kap_s * An);
+            put(GX_ST, g, ph.kap_s * At);
+            put(GX_FN, g, ph.kap_f * An);
+            put(GX_FT, g, ph.kap_f * At);
+            put(GX_FN2, g, 2.0 * ph.kap_f * An);
+            put(GX_HG, g, ph.half_g * c2);
         }
         if (j < ny + 1) {
             const double bY = (B(i, j + 1) - B(i, j)) / dy;
             const double bX = 0.5 * (slopes(i, j).bX + slopes(i, j + 1).bX);
             const double s2 = 1.0 + (bX * bX + bY * bY);
             const double c2 = 1.0 / s2;
-            geo[GY_J * plane + g] = (T)sqrt(s2);
-            geo[GY_GN * plane + g] = (T)((1.0 + bX * bX) * c2 * c2);
-            geo[GY_GT * plane + g] = (T)(-bX * bY * c2 * c2);
-            geo[GY_C2 * plane + g] = (T)c2;
+            const double An = (1.0 + bX * bX) * c2 * c2, At = -bX * bY * c2 * c2;  // A22 c^2, A21 c^2
+            put(GY_JHD, g, sqrt(s2) * ph.h_dry);
+            put(GY_SN, g, ph.kap_s * An);
+            put(GY_ST, g, ph.kap_s * At);
+            put(GY_FN, g, ph.kap_f * An);
+            put(GY_FT, g, ph.kap_f * At);
+            put(GY_FN2, g, 2.0 * ph.kap_f * An);
+            put(GY_HG, g, ph.half_g * c2);
         }
     }
 }
@@ -188,7 +206,7 @@ template <typename T>
 __global__ void max_speed_kernel(const T *U, const T *geo, int nx, int ny, int pitch, long long plane, Phys ph,
                                  unsigned long long *out)
 {
-    const K<T> k(ph);
+    (void)ph;
     const long long n = (long long)nx * ny;
     double m = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -197,7 +215,7 @@ __global__ void max_speed_kernel(const T *U, const T *geo, int nx, int ny, int p
         T u[6];
 #pragma unroll
         for (int c = 0; c < 6; c++) u[c] = U[c * plane + g];
-        m = fmax(m, cell_speed(u, geo[GC_J * plane + g], geo[GC_G11 * plane + g], geo[GC_G22 * plane + g], k));
+        m = fmax(m, (double)cell_speed(u, geo, plane, g));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -210,35 +228,43 @@ __global__ void max_speed_kernel(const T *U, const T *geo, int nx, int ny, int p
     }
 }
 
-// dense doubles [c][j][i] -> padded state of type T (interior only)
+// dense doubles [c][j][i] -> padded state of type T (interior only); with R
+// (FP32 form) the masses are split into value + rounding remainder
 template <typename T>
-__global__ void unpack_kernel(const double *src, T *U, int nx, int ny, int pitch, long long plane)
+__global__ void unpack_kernel(const double *src, T *U, T *R, int nx, int ny, int pitch, long long plane)
 {
     const long long n = (long long)nx * ny;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(e / n);
         const long long r = e - c * n;
         const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
-        U[c * plane + cell_index(i, j, pitch)] = (T)src[e];
+        const long long g = cell_index(i, j, pitch);
+        const double v = src[e];
+        const T hi = (T)v;
+        U[c * plane + g] = hi;
+        if (R && (c == 0 || c == 3)) R[(c / 3) * plane + g] = (T)(v - (double)hi);
     }
 }
 
 template <typename T>
-__global__ void pack_kernel(const T *U, double *dst, int nx, int ny, int pitch, long long plane)
+__global__ void pack_kernel(const T *U, const T *R, double *dst, int nx, int ny, int pitch, long long plane)
 {
     const long long n = (long long)nx * ny;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(e / n);
         const long long r = e - c * n;
         const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
-        dst[e] = (double)U[c * plane + cell_index(i, j, pitch)];
+        const long long g = cell_index(i, j, pitch);
+        double v = (double)U[c * plane + g];
+        if (R && (c == 0 || c == 3)) v += (double)R[(c / 3) * plane + g];
+        dst[e] = v;
     }
 }
 
 // release (h, phi_s, velocities) -> conserved U = J h (phi, phi v)
 template <typename T>
-__global__ void release_kernel(const double *src, int has_phi, int has_v, T *U, const T *geo, int nx, int ny, int pitch,
-                               long long plane)
+__global__ void release_kernel(const double *src, int has_phi, int has_v, T *U, T *R, const T *geo, int nx, int ny,
+                               int pitch, long long plane)
 {
     const long long n = (long long)nx * ny;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -254,6 +280,10 @@ __global__ void release_kernel(const double *src, int has_phi, int has_v, T *U, 
         U[plane + g] = (T)(U1 * vxs);
         U[2 * plane + g] = (T)(U1 * vys);
         U[3 * plane + g] = (T)U4;
+        if (R) {
+            R[g] = (T)(U1 - (double)(T)U1);
+            R[plane + g] = (T)(U4 - (double)(T)U4);
+        }
         U[4 * plane + g] = (T)(U4 * vxf);
         U[5 * plane + g] = (T)(U4 * vyf);
     }
@@ -261,8 +291,8 @@ __global__ void release_kernel(const double *src, int has_phi, int has_v, T *U, 
 
 // conserved -> output fields (h, phi_s, v_X^s, v_Y^s, v_X^f, v_Y^f)
 template <typename T>
-__global__ void prims_kernel(const T *U, const T *geo, int nx, int ny, int pitch, long long plane, double h_dry,
-                             double *dst)
+__global__ void prims_kernel(const T *U, const T *R, const T *geo, int nx, int ny, int pitch, long long plane,
+                             double h_dry, double *dst)
 {
     const long long n = (long long)nx * ny;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -271,6 +301,10 @@ __global__ void prims_kernel(const T *U, const T *geo, int nx, int ny, int pitch
         const double J = (double)geo[GC_J * plane + g];
         double u[6];
         for (int c = 0; c < 6; c++) u[c] = (double)U[c * plane + g];
+        if (R) {
+            u[0] += (double)R[g];
+            u[3] += (double)R[plane + g];
+        }
         const double Ut = u[0] + u[3];
         const double h = Ut / J;
         const bool wet = h > h_dry;
@@ -285,7 +319,7 @@ __global__ void prims_kernel(const T *U, const T *geo, int nx, int ny, int pitch
 }
 
 template <typename T>
-__global__ void budget_kernel(const T *U, int nx, int ny, int pitch, long long plane, double *out)
+__global__ void budget_kernel(const T *U, const T *R, int nx, int ny, int pitch, long long plane, double *out)
 {
     const long long n = (long long)nx * ny;
     double s[6] = {0, 0, 0, 0, 0, 0};
@@ -294,6 +328,10 @@ __global__ void budget_kernel(const T *U, int nx, int ny, int pitch, long long p
         const long long g = cell_index(i, j, pitch);
 #pragma unroll
         for (int c = 0; c < 6; c++) s[c] += (double)U[c * plane + g];
+        if (R) {
+            s[0] += (double)R[g];
+            s[3] += (double)R[plane + g];
+        }
     }
     __shared__ double w[6][32];
 #pragma unroll
@@ -330,6 +368,13 @@ static int grid_for(long long n, int block = 256)
     return (int)b;
 }
 
+// remainder planes (FP32 form) that follow the six state planes of a buffer
+template <typename T>
+static T *rem(moses_sim *s, void *buf)
+{
+    return s->prec == MOSES_FP32 ? (T *)buf + 6 * s->plane : nullptr;
+}
+
 template <typename T>
 static StageArgs<T> base_args(moses_sim *s)
 {
@@ -343,6 +388,7 @@ static StageArgs<T> base_args(moses_sim *s)
     a.pitch = s->pitch;
     a.plane = s->plane;
     a.ph = s->ph;
+    a.k = make_kt<T>(s->ph);
     return a;
 }
 
@@ -397,7 +443,7 @@ static int check_params(const moses_params *p, std::string &why)
     if (!(fin(p->k_f) && p->k_f >= 0)) return why = "k_f must be >= 0", 1;
     if (!(fin(p->cfl) && p->cfl > 0)) return why = "cfl must be > 0", 1;
     if (!(fin(p->dt_max) && p->dt_max > 0)) return why = "dt_max must be > 0", 1;
-    if (!(fin(p->h_dry) && p->h_dry > 0)) return why = "h_dry must be > 0", 1;
+    if (!(fin(p->h_dry) && p->h_dry >= 1e-30)) return why = "h_dry must be >= 1e-30", 1;
     for (int k = 0; k < 4; k++)
         if (p->bc[k] != MOSES_BC_CLOSED && p->bc[k] != MOSES_BC_TRANSMISSIVE) return why = "bc must be 0 or 1", 1;
     if (p->fluid_pg_mode != 0 && p->fluid_pg_mode != 1) return why = "fluid_pg_mode must be 0 or 1", 1;
@@ -490,7 +536,7 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
         free_sim(s);
         return rc;
     };
-    const size_t st = 6 * (size_t)s->plane * s->esz;
+    const size_t st = (s->prec == MOSES_FP32 ? 8 : 6) * (size_t)s->plane * s->esz;
     cudaError_t e;
     if ((e = cudaMalloc(&s->U, st)) != cudaSuccess || (e = cudaMalloc(&s->Us, st)) != cudaSuccess ||
         (e = cudaMalloc(&s->geo, (size_t)GEO_PLANES * s->plane * s->esz)) != cudaSuccess ||
@@ -526,10 +572,10 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
         const long long ng = (long long)(nx + 4) * (ny + 4);
         if (s->prec == MOSES_FP64)
             geometry_kernel<double><<<grid_for(ng), 256, 0, s->stream>>>(d_ext, nx, ny, s->pitch, s->plane, dx, dy,
-                                                                         (double *)s->geo);
+                                                                         s->ph, (double *)s->geo);
         else
             geometry_kernel<float><<<grid_for(ng), 256, 0, s->stream>>>(d_ext, nx, ny, s->pitch, s->plane, dx, dy,
-                                                                        (float *)s->geo);
+                                                                        s->ph, (float *)s->geo);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -590,11 +636,11 @@ int moses_set_release(moses_sim *s, const double *h, const double *phi_s, const 
         }
     if (s->prec == MOSES_FP64)
         release_kernel<double><<<grid_for(n), 256, 0, s->stream>>>(s->stage_buf, phi_s != nullptr, has_v,
-                                                                   (double *)s->U, (const double *)s->geo, s->nx,
+                                                                   (double *)s->U, nullptr, (const double *)s->geo, s->nx,
                                                                    s->ny, s->pitch, s->plane);
     else
         release_kernel<float><<<grid_for(n), 256, 0, s->stream>>>(s->stage_buf, phi_s != nullptr, has_v,
-                                                                  (float *)s->U, (const float *)s->geo, s->nx,
+                                                                  (float *)s->U, rem<float>(s, s->U), (const float *)s->geo, s->nx,
                                                                   s->ny, s->pitch, s->plane);
     CK(cudaGetLastError());
     s->have_state = true;
@@ -646,10 +692,15 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
     StageArgs<T> a1 = base_args<T>(s), a2 = base_args<T>(s);
     a1.Uin = (const T *)s->U;
     a1.Uout = (T *)s->Us;
+    a1.Rin = rem<T>(s, s->U);
+    a1.Rout = rem<T>(s, s->Us);
     a1.stage = 1;
     a2.Uin = (const T *)s->Us;
     a2.Un = (const T *)s->U;
     a2.Uout = (T *)s->U;
+    a2.Rin = rem<T>(s, s->Us);
+    a2.Rn = rem<T>(s, s->U);
+    a2.Rout = rem<T>(s, s->U);
     a2.stage = 2;
     a2.want_amax = 1;
     if (stage_ms) {
@@ -776,10 +827,10 @@ int moses_get_conserved_device(moses_sim *s, double *U_device)
     if (!s || !U_device) return MOSES_EINVAL;
     const long long n = (long long)s->nx * s->ny;
     if (s->prec == MOSES_FP64)
-        pack_kernel<double><<<grid_for(6 * n), 256, 0, s->stream>>>((const double *)s->U, U_device, s->nx, s->ny,
+        pack_kernel<double><<<grid_for(6 * n), 256, 0, s->stream>>>((const double *)s->U, nullptr, U_device, s->nx, s->ny,
                                                                     s->pitch, s->plane);
     else
-        pack_kernel<float><<<grid_for(6 * n), 256, 0, s->stream>>>((const float *)s->U, U_device, s->nx, s->ny,
+        pack_kernel<float><<<grid_for(6 * n), 256, 0, s->stream>>>((const float *)s->U, rem<float>(s, s->U), U_device, s->nx, s->ny,
                                                                    s->pitch, s->plane);
     CK(cudaGetLastError());
     return MOSES_OK;
@@ -808,10 +859,10 @@ static int set_from_device_buf(moses_sim *s, const double *src)
     CK(cudaStreamSynchronize(s->stream));
     if (bad) return fail(s, MOSES_EINVAL, "U must be finite with U1, U4 >= 0");
     if (s->prec == MOSES_FP64)
-        unpack_kernel<double><<<grid_for(6 * n), 256, 0, s->stream>>>(src, (double *)s->U, s->nx, s->ny, s->pitch,
+        unpack_kernel<double><<<grid_for(6 * n), 256, 0, s->stream>>>(src, (double *)s->U, nullptr, s->nx, s->ny, s->pitch,
                                                                       s->plane);
     else
-        unpack_kernel<float><<<grid_for(6 * n), 256, 0, s->stream>>>(src, (float *)s->U, s->nx, s->ny, s->pitch,
+        unpack_kernel<float><<<grid_for(6 * n), 256, 0, s->stream>>>(src, (float *)s->U, rem<float>(s, s->U), s->nx, s->ny, s->pitch,
                                                                      s->plane);
     CK(cudaGetLastError());
     s->have_state = true;
@@ -842,11 +893,11 @@ int moses_get_state(moses_sim *s, double *h, double *phi_s, double *vx_s, double
     if (rc) return rc;
     const long long n = (long long)s->nx * s->ny;
     if (s->prec == MOSES_FP64)
-        prims_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, (const double *)s->geo, s->nx,
+        prims_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, nullptr, (const double *)s->geo, s->nx,
                                                                  s->ny, s->pitch, s->plane, s->ph.h_dry,
                                                                  s->stage_buf);
     else
-        prims_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, (const float *)s->geo, s->nx,
+        prims_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, rem<float>(s, s->U), (const float *)s->geo, s->nx,
                                                                 s->ny, s->pitch, s->plane, s->ph.h_dry, s->stage_buf);
     CK(cudaGetLastError());
     double *dst[6] = {h, phi_s, vx_s, vy_s, vx_f, vy_f};
@@ -883,11 +934,13 @@ int moses_stage(moses_sim *s, double t, double dt, double *U_out)
         rc = launch_stage<double>(a, s->tile, s->stream);
         if (rc == 0)
             pack_kernel<double><<<grid_for(6LL * s->nx * s->ny), 256, 0, s->stream>>>(
-                (const double *)s->Us, s->stage_buf, s->nx, s->ny, s->pitch, s->plane);
+                (const double *)s->Us, nullptr, s->stage_buf, s->nx, s->ny, s->pitch, s->plane);
     } else {
         StageArgs<float> a = base_args<float>(s);
         a.Uin = (const float *)s->U;
         a.Uout = (float *)s->Us;
+        a.Rin = rem<float>(s, s->U);
+        a.Rout = rem<float>(s, s->Us);
         a.stage = 1;
         a.debug_stage = 1;
         a.dbg_t = t;
@@ -895,7 +948,7 @@ int moses_stage(moses_sim *s, double t, double dt, double *U_out)
         rc = launch_stage<float>(a, s->tile, s->stream);
         if (rc == 0)
             pack_kernel<float><<<grid_for(6LL * s->nx * s->ny), 256, 0, s->stream>>>(
-                (const float *)s->Us, s->stage_buf, s->nx, s->ny, s->pitch, s->plane);
+                (const float *)s->Us, rem<float>(s, s->Us), s->stage_buf, s->nx, s->ny, s->pitch, s->plane);
     }
     if (rc) return fail(s, MOSES_ECUDA, "stage launch failed");
     CK(cudaGetLastError());
@@ -911,10 +964,10 @@ int moses_get_budget(moses_sim *s, double out[MOSES_BUDGET_LEN])
     const long long n = (long long)s->nx * s->ny;
     CK(cudaMemsetAsync(s->red, 0, 6 * sizeof(double), s->stream));
     if (s->prec == MOSES_FP64)
-        budget_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, s->nx, s->ny, s->pitch,
+        budget_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, nullptr, s->nx, s->ny, s->pitch,
                                                                   s->plane, s->red);
     else
-        budget_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, s->nx, s->ny, s->pitch,
+        budget_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, rem<float>(s, s->U), s->nx, s->ny, s->pitch,
                                                                  s->plane, s->red);
     CK(cudaGetLastError());
     double sums[6];
@@ -1008,9 +1061,10 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     CK(cudaMemsetAsync(U, 0, sizeof(double) * 12 * plane, st));
     static_ctl_init_kernel<<<1, 1, 0, st>>>(ctl, t);
     extend_dem_kernel<<<grid_for((long long)(nx + 6) * (ny + 6)), 256, 0, st>>>(dem_device, nx, ny, bext);
+    const Phys phs = make_phys(p, dx, dy);
     geometry_kernel<double><<<grid_for((long long)(nx + 4) * (ny + 4)), 256, 0, st>>>(bext, nx, ny, pitch, plane, dx,
-                                                                                     dy, geo);
-    unpack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U_in_device, U, nx, ny, pitch, plane);
+                                                                                     dy, phs, geo);
+    unpack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U_in_device, U, nullptr, nx, ny, pitch, plane);
     CK(cudaGetLastError());
     StageArgs<double> a{};
     a.geo = geo;
@@ -1021,7 +1075,8 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     a.ny = ny;
     a.pitch = pitch;
     a.plane = plane;
-    a.ph = make_phys(p, dx, dy);
+    a.ph = phs;
+    a.k = make_kt<double>(phs);
     fill_ghosts_kernel<double><<<grid_for(n), 256, 0, st>>>(a, U, t);
     max_speed_kernel<double><<<grid_for(n), 256, 0, st>>>(U, geo, nx, ny, pitch, plane, a.ph, &ctl->amax);
     CK(cudaGetLastError());
@@ -1036,7 +1091,7 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     a2.want_amax = 1;
     if (launch_stage<double>(a1, 0, st) || launch_stage<double>(a2, 0, st))
         return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
-    pack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U, U_out_device, nx, ny, pitch, plane);
+    pack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U, nullptr, U_out_device, nx, ny, pitch, plane);
     CK(cudaGetLastError());
     if (dt_out) {
         CK(cudaMemcpyAsync(dt_out, &ctl->dt, sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -6,6 +6,8 @@
 //               to 32 elements; interior cell (i, j) at (j + 2) * pitch + i + 2
 //   state U   : 6 planes, U1..U6 (structure of arrays), element type T
 //   scratch U*: 6 planes (the Heun intermediate state)
+//   FP32 form : 2 more planes after each of U and U*, the FP32 rounding
+//               remainders of the two mass components (compensated mass)
 //   geometry  : GEO_PLANES planes of T, computed once per DEM
 //   control   : one Ctl block (time, dt, a_max bits, FP64 budgets, status)
 #pragma once
@@ -17,28 +19,43 @@ constexpr int GH = 2;          // ghost layers of the state
 constexpr int MAX_INFLOW = 8;  // inflow segments per simulation
 constexpr int MAX_HYD = 64;    // samples per hydrograph
 
-// geometry planes (cell centres and faces; faces indexed by their lower cell)
+// Geometry planes, computed once per DEM and parameter set (cell centres and
+// faces; faces indexed by their lower cell).  kap_s = eps g (1 - alpha) / 2,
+// kap_f = eps g / 2; A = (A_ij) the 2x2 block of Omega_b^-1; c = n_Z = 1/J.
 enum GeoPlane : int {
     GC_J = 0,   // J_b = sqrt(1 + bX^2 + bY^2)
-    GC_C,       // c = n_Z = 1 / J_b
+    GC_C,       // c = n_Z
+    GC_JHD,     // J h_dry            (dry test of a phase: U > J h_dry)
+    GC_GC1,     // g (1 - alpha) c    (J p_b^s = U1 (g (1 - alpha) c - eps^chi kappa^s))
+    GC_GCF,     // g c                (J p_b^f = U4 (g c - eps^chi kappa^f))
     GC_BX,      // dB/dX (central difference)
     GC_BY,      // dB/dY
-    GC_A11,     // (Omega_b^-1)_11 = (1 + bY^2) / J^2
-    GC_A12,     // (Omega_b^-1)_12 = (Omega_b^-1)_21 = -bX bY / J^2
-    GC_A22,     // (Omega_b^-1)_22 = (1 + bX^2) / J^2
-    GC_KXX,     // c bXX   (curvature of the bed; kappa = -(KXX vX^2 + 2 KXY vX vY + KYY vY^2))
-    GC_KXY,     // c bXY
+    GC_MNX,     // -c bX = n_X        (s_n = J p_b (n_X, n_Y))
+    GC_MNY,     // -c bY = n_Y
+    GC_A11,     // (1 + bY^2) / J^2
+    GC_A12,     // -bX bY / J^2 (= A21)
+    GC_A22,     // (1 + bX^2) / J^2
+    GC_KXX,     // c bXX     kappa = -(KXX vX^2 + KXY2 vX vY + KYY vY^2)
+    GC_KXY2,    // 2 c bXY
     GC_KYY,     // c bYY
-    GC_G11,     // A11 c^2 (cell-centre wave speed along xi)
-    GC_G22,     // A22 c^2 (along eta)
-    GX_J,       // x-face (i+1/2, j): J_b
-    GX_GN,      //   A11 c^2 : pressure coefficient of the X-momentum flux
-    GX_GT,      //   A12 c^2 : pressure coefficient of the Y-momentum flux
-    GX_C2,      //   c^2     : P = J h pbar^f = (g/2) c^2 (J h)^2
-    GY_J,       // y-face (i, j+1/2): J_b
-    GY_GN,      //   A22 c^2 : Y-momentum flux
-    GY_GT,      //   A21 c^2 : X-momentum flux
-    GY_C2,
+    GC_SXS,     // kap_s A11 c^2      cell-centre wave speeds (CFL)
+    GC_SXF,     // 2 kap_f A11 c^2
+    GC_SYS,     // kap_s A22 c^2
+    GC_SYF,     // 2 kap_f A22 c^2
+    GX_JHD,     // x-face (i+1/2, j): J h_dry
+    GX_SN,      //   kap_s A11 c^2 : solid X-momentum pressure coefficient, solid speed
+    GX_ST,      //   kap_s A12 c^2 : solid Y-momentum pressure coefficient
+    GX_FN,      //   kap_f A11 c^2 : fluid X-momentum
+    GX_FT,      //   kap_f A12 c^2 : fluid Y-momentum
+    GX_FN2,     //   2 kap_f A11 c^2 : fluid speed
+    GX_HG,      //   (g/2) c^2 : P = J h pbar^f = (g/2) c^2 (J h)^2
+    GY_JHD,     // y-face (i, j+1/2)
+    GY_SN,      //   kap_s A22 c^2 : solid Y-momentum, solid speed
+    GY_ST,      //   kap_s A21 c^2 : solid X-momentum
+    GY_FN,      //   kap_f A22 c^2
+    GY_FT,      //   kap_f A21 c^2
+    GY_FN2,     //   2 kap_f A22 c^2
+    GY_HG,      //   (g/2) c^2
     GEO_PLANES
 };
 
@@ -84,12 +101,42 @@ struct Phys {
     int bc[4];
 };
 
+// Constants of the stage kernel in its arithmetic type, prepared on the host
+// (the FP32 form then runs no FP64 conversions per thread).
+template <typename T>
+struct KT {
+    T eps_chi, eps_alpha, eps, alpha, c_d, k_f, hinv_dx, hinv_dy, tan_delta;
+    double tan_delta_d;
+};
+
+template <typename T>
+inline KT<T> make_kt(const Phys &p)
+{
+    KT<T> k;
+    k.eps_chi = (T)p.eps_chi;
+    k.eps_alpha = (T)p.eps_alpha;
+    k.eps = (T)p.eps;
+    k.alpha = (T)p.alpha;
+    k.c_d = (T)p.c_d;
+    k.k_f = (T)p.k_f;
+    k.hinv_dx = (T)(0.5 * p.inv_dx);
+    k.hinv_dy = (T)(0.5 * p.inv_dy);
+    k.tan_delta = (T)p.tan_delta;
+    k.tan_delta_d = p.tan_delta;
+    return k;
+}
+
 // Everything a stage kernel needs.
 template <typename T>
 struct StageArgs {
     const T *Uin;      // stage input (ghosts valid on the four sides)
     const T *Un;       // stage 2: U^n for the Heun average (interior); else null
     T *Uout;           // stage output (may equal Un in stage 2: same cell only)
+    // FP32 form only: rounding remainders of the two mass components (2 planes
+    // each; the mass of a cell is U + R); null in the FP64 form
+    const T *Rin;
+    const T *Rn;
+    T *Rout;
     const T *geo;
     Ctl *ctl;
     const InflowSeg *inflow;
@@ -97,6 +144,7 @@ struct StageArgs {
     int nx, ny, pitch;
     long long plane;   // elements per plane
     Phys ph;
+    KT<T> k;
     int stage;         // 1 or 2
     int want_amax;     // stage 2: reduce a_max of U^{n+1}
     int debug_stage;   // 1: single stage to Uout with a given dt (no Heun)

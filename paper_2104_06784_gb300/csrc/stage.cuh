@@ -8,15 +8,26 @@
 // SrcF_v_Topo).  Coulomb friction is applied semi-implicitly with a stopping
 // condition, then the positivity clamp and the dry-momentum rule.
 //
-// Work decomposition: one CTA per TX x TY tile.  The CTA stages the 6 state
-// planes of the tile plus a 2-cell halo in shared memory (coalesced loads),
-// computes every x-face and y-face flux of the tile exactly once into shared
-// memory, then updates its cells.  In stage 2 it also forms the Heun average
-// in place, writes the ghost cells of the new state (boundary conditions
-// fused into the producer), and reduces the CFL wave speed: warp shuffle max,
-// CTA max, one atomicMax on the IEEE bits of a non-negative double (exact and
+// Work decomposition: one CTA per TX x TY tile.  The CTA stages the six
+// state planes of the tile plus a 2-cell halo in shared memory (coalesced
+// loads), computes each cell's minmod slopes once, every x- and y-face flux
+// once, then updates its cells.  In stage 2 it also forms the Heun average in
+// place, writes the ghost cells of the new state (boundary conditions fused
+// into the producer) and reduces the CFL wave speed: warp shuffle max, CTA
+// max, one atomicMax on the IEEE bits of a non-negative double (exact,
 // independent of order).  The last CTA to finish (ticket counter, no waiting)
 // turns the maximum into the next time step.
+//
+// GB300 executes two FP64 FMAs per clock per SM, so the FP64 form is bound by
+// the FP64 pipe.  Everything that can leave it does: the minmod limiter, the
+// dry tests, the stopping decision and every max are integer operations on
+// the IEEE bit patterns (exact for the non-negative operands they see);
+// reciprocals and square roots start from the hardware approximations
+// (rcp/rsqrt.approx.ftz.f64) and take two Newton-Raphson steps (quadratic for
+// 1/x, y <- y (2 - x y); the sqrt residual step s <- s + (x - s^2) r/2),
+// which lands within an ulp or two of the correctly rounded result; fluxes
+// are kept doubled so the factor 1/2 folds into 1/dx; products of parameters
+// and geometry are precomputed per cell and face.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -24,106 +35,174 @@
 
 namespace moses {
 
+// ---- bit-pattern helpers ----------------------------------------------------
+__device__ __forceinline__ long long ibits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int ibits(float x) { return __float_as_int(x); }
+
+// a > b for b > 0: signed comparison of the bit patterns (negative a, with
+// the sign bit set, compare below every positive b)
 template <typename T>
-struct K {  // constants in the arithmetic type
-    T kap_s, kap_f2, kap_f, half_g, g_1ma, g, eps_chi, eps_alpha, eps, alpha, c_d, k_f, h_dry, inv_dx,
-        inv_dy;
-    double tan_delta;
-    __device__ explicit K(const Phys &p)
-        : kap_s((T)p.kap_s), kap_f2((T)(2.0 * p.kap_f)), kap_f((T)p.kap_f), half_g((T)p.half_g),
-          g_1ma((T)p.g_1ma), g((T)p.g), eps_chi((T)p.eps_chi), eps_alpha((T)p.eps_alpha), eps((T)p.eps),
-          alpha((T)p.alpha), c_d((T)p.c_d), k_f((T)p.k_f), h_dry((T)p.h_dry), inv_dx((T)p.inv_dx),
-          inv_dy((T)p.inv_dy), tan_delta(p.tan_delta)
-    {
-    }
-};
-
-__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double tabs(double x) { return fabs(x); }
-__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
-__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
-__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
-__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
-
-__device__ __forceinline__ bool nonfinite(double x)
+__device__ __forceinline__ bool gtp(T a, T b)
 {
-    return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
+    return ibits(a) > ibits(b);
 }
+// max of two non-negative values
+template <typename T>
+__device__ __forceinline__ T maxnn(T a, T b)
+{
+    return ibits(a) >= ibits(b) ? a : b;
+}
+// max(x, 0)
+template <typename T>
+__device__ __forceinline__ T pos(T x)
+{
+    return ibits(x) < 0 ? T(0) : x;
+}
+// x < 0 (and not -0)
+__device__ __forceinline__ bool negative(double x) { return ibits(x) < 0 && (ibits(x) << 1) != 0; }
+__device__ __forceinline__ bool negative(float x) { return ibits(x) < 0 && (ibits(x) << 1) != 0; }
+
+__device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000; }
 __device__ __forceinline__ bool nonfinite(float x) { return (__float_as_int(x) & 0x7f800000) == 0x7f800000; }
 
-// minmod of two one-sided undivided differences (Sect. 2.2)
-template <typename T>
-__device__ __forceinline__ T minmod(T a, T b)
+// minmod of two one-sided undivided differences (Sect. 2.2): 0 if the signs
+// differ or either is 0, else the one of smaller magnitude
+__device__ __forceinline__ double minmod(double a, double b)
 {
-    if (a * b <= T(0)) return T(0);
-    return a > T(0) ? tmin(a, b) : tmax(a, b);
+    const long long ia = ibits(a), ib = ibits(b);
+    const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
+    if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0.0;
+    return ma < mb ? a : b;
+}
+__device__ __forceinline__ float minmod(float a, float b)
+{
+    const int ia = ibits(a), ib = ibits(b);
+    const int ma = ia & 0x7fffffff, mb = ib & 0x7fffffff;
+    if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0.0f;
+    return ma < mb ? a : b;
 }
 
+// ---- reciprocal and square root ---------------------------------------------
+// 1/x for x > 0 normal: hardware approximation + two Newton-Raphson steps
+__device__ __forceinline__ double frcp(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+__device__ __forceinline__ float frcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// sqrt(x), 0 for x <= 0 or subnormal: s0 = x r0 from the approximate
+// reciprocal square root r0, then two residual steps s <- s + (x - s^2) r0/2
+__device__ __forceinline__ double fsqrt(double x)
+{
+    if (ibits(x) < 0x0010000000000000ll) return 0.0;
+    double r;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double h = 0.5 * r;
+    double s = x * r;
+    double e = fma(-s, s, x);
+    s = fma(e, h, s);
+    e = fma(-s, s, x);
+    return fma(e, h, s);
+}
+__device__ __forceinline__ float fsqrt(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// 1/sqrt(x) for x > 0 normal: approximation + two Newton steps
+__device__ __forceinline__ double frsqrt(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double t = x * y;
+    y = y * fma(-0.5 * t, y, 1.5);
+    t = x * y;
+    return y * fma(-0.5 * t, y, 1.5);
+}
+__device__ __forceinline__ float frsqrt(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// error-free sum (Knuth's TwoSum): s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+
+// ---- face flux -----------------------------------------------------------------
 template <typename T>
 struct FaceGeo {
-    T J, gn, gt, c2;
+    T jhd;  // J h_dry
+    T sn;   // kap_s A_dd c^2 : solid pressure coefficient of the normal momentum, solid speed
+    T st;   // kap_s A_dt c^2 : solid pressure coefficient of the transverse momentum
+    T fn, ft, fn2;  // kap_f A_dd c^2, kap_f A_dt c^2, 2 kap_f A_dd c^2
+    T hg;   // (g/2) c^2
 };
 
 // Physical flux of one reconstructed state through a face of direction d
-// (0: xi = X, 1: eta = Y), the per-phase local speeds and P = J h pbar^f.
+// (0: xi = X, 1: eta = Y), the per-phase local speeds (R7) and P = J h pbar^f.
 // With xi = X, eta = Y the tangential velocity v_xi equals v_X, the mass flux
 // J h^p v_xi^p is the momentum component U_{2+d}, and the pressure terms
-// eps J h A_dk Nbar^s, eps J h A_dk pbar^f become (A_dk c^2) kap (J h) U.
-template <typename T>
-__device__ __forceinline__ void side_flux(const T u[6], const FaceGeo<T> &G, int d, const K<T> &k, T F[6],
-                                          T &as, T &af, T &P)
+// eps J h A_dk Nbar^s, eps J h A_dk pbar^f become (kap A_dk c^2) (J h) U.
+template <typename T, int D>
+__device__ __forceinline__ void side_flux(const T u[6], const FaceGeo<T> &G, T F[6], T &as, T &af, T &P)
 {
     const T Ut = u[0] + u[3];
-    const T hd = G.J * k.h_dry;
-    const bool ws = u[0] > hd, wf = u[3] > hd;
-    const T rs = ws ? T(1) / u[0] : T(0);
-    const T rf = wf ? T(1) / u[3] : T(0);
-    const T vns = (d == 0 ? u[1] : u[2]) * rs;
-    const T vnf = (d == 0 ? u[4] : u[5]) * rf;
-    const T cX = d == 0 ? G.gn : G.gt;
-    const T cY = d == 0 ? G.gt : G.gn;
-    const T ps = k.kap_s * Ut * u[0];
-    const T pf = k.kap_f * Ut * Ut;
-    F[0] = ws ? (d == 0 ? u[1] : u[2]) : T(0);
-    F[1] = u[1] * vns + cX * ps;
-    F[2] = u[2] * vns + cY * ps;
-    F[3] = wf ? (d == 0 ? u[4] : u[5]) : T(0);
-    F[4] = u[4] * vnf + cX * pf;
-    F[5] = u[5] * vnf + cY * pf;
-    as = tabs(vns) + tsqrt(G.gn * k.kap_s * (Ut + u[0]));
-    af = tabs(vnf) + tsqrt(G.gn * k.kap_f2 * Ut);
-    P = k.half_g * G.c2 * Ut * Ut;
+    const bool ws = gtp(u[0], G.jhd), wf = gtp(u[3], G.jhd);
+    const T rs = ws ? frcp(u[0]) : T(0);
+    const T rf = wf ? frcp(u[3]) : T(0);
+    const T uns = D == 0 ? u[1] : u[2];
+    const T unf = D == 0 ? u[4] : u[5];
+    const T vns = uns * rs, vnf = unf * rf;
+    const T Ps = Ut * u[0], Pf = Ut * Ut;
+    // X-momentum uses the normal coefficient on x-faces, the transverse one
+    // on y-faces; Y-momentum the other way round
+    const T sX = D == 0 ? G.sn : G.st, sY = D == 0 ? G.st : G.sn;
+    const T fX = D == 0 ? G.fn : G.ft, fY = D == 0 ? G.ft : G.fn;
+    F[0] = ws ? uns : T(0);
+    F[1] = fma(sX, Ps, u[1] * vns);
+    F[2] = fma(sY, Ps, u[2] * vns);
+    F[3] = wf ? unf : T(0);
+    F[4] = fma(fX, Pf, u[4] * vnf);
+    F[5] = fma(fY, Pf, u[5] * vnf);
+    as = tabs(vns) + fsqrt(G.sn * (Ut + u[0]));
+    af = tabs(vnf) + fsqrt(G.fn2 * Ut);
+    P = G.hg * Pf;
 }
 
-// Central flux through one face from the four cells a | b || c | d along the
-// face normal (values um = b + slope_b/2, up = c - slope_c/2).
-template <typename T>
-__device__ __forceinline__ void face_flux(const T *s0, int stride_c, int o_a, int o_b, int o_c, int o_d,
-                                          const FaceGeo<T> &G, int d, const K<T> &k, T H[7])
+// Twice the central flux through one face, from the face values um (left /
+// lower cell) and up (right / upper cell): H2 = F(um) + F(up) - a (up - um),
+// a = max of the two sides' local speeds per phase; H2[6] = P(um) + P(up).
+template <typename T, int D>
+__device__ __forceinline__ void face_flux2(const T um[6], const T up[6], const FaceGeo<T> &G, T H[7])
 {
-    T um[6], up[6];
-#pragma unroll
-    for (int c = 0; c < 6; c++) {
-        const T *p = s0 + c * stride_c;
-        const T ua = p[o_a], ub = p[o_b], uc = p[o_c], ud = p[o_d];
-        const T dC = uc - ub;
-        um[c] = ub + T(0.5) * minmod(ub - ua, dC);
-        up[c] = uc - T(0.5) * minmod(dC, ud - uc);
-    }
     T Fm[6], Fp[6], asm_, afm, asp, afp, Pm, Pp;
-    side_flux(um, G, d, k, Fm, asm_, afm, Pm);
-    side_flux(up, G, d, k, Fp, asp, afp, Pp);
-    const T as = tmax(asm_, asp), af = tmax(afm, afp);
+    side_flux<T, D>(um, G, Fm, asm_, afm, Pm);
+    side_flux<T, D>(up, G, Fp, asp, afp, Pp);
+    const T as = maxnn(asm_, asp), af = maxnn(afm, afp);
 #pragma unroll
-    for (int c = 0; c < 6; c++) {
-        const T a = c < 3 ? as : af;
-        H[c] = T(0.5) * (Fm[c] + Fp[c]) - T(0.5) * a * (up[c] - um[c]);
-    }
-    H[6] = T(0.5) * (Pm + Pp);
+    for (int c = 0; c < 6; c++) H[c] = fma(-(c < 3 ? as : af), up[c] - um[c], Fm[c] + Fp[c]);
+    H[6] = Pm + Pp;
 }
 
+// ---- Mode-II inflow and ghost cells ---------------------------------------------
 __device__ __forceinline__ double interp_series(const double *t, const double *v, int n, double tt)
 {
     if (n <= 0 || tt < t[0] || tt > t[n - 1]) return 0.0;
@@ -185,7 +264,6 @@ __device__ void write_ghosts(T *U, const T *geo, const StageArgs<T> &a, int i, i
     if (i < 2 || i >= nx - 2) {
 #pragma unroll
         for (int side = 0; side < 2; side++) {
-            // inflow rows on this side
             int seg = -1;
             for (int f = 0; f < a.n_inflow; f++)
                 if (a.inflow[f].side == side && j >= a.inflow[f].i0 && j < a.inflow[f].i1) seg = f;
@@ -245,21 +323,21 @@ __device__ void write_ghosts(T *U, const T *geo, const StageArgs<T> &a, int i, i
     }
 }
 
-// largest cell-centre wave speed of a state (R7), both phases, both axes
+// Largest cell-centre wave speed of a state (R7), both phases, both axes.
+// g: pointer to the cell's geometry (plane stride `plane`).
 template <typename T>
-__device__ __forceinline__ double cell_speed(const T u[6], T J, T g11, T g22, const K<T> &k)
+__device__ __forceinline__ T cell_speed(const T u[6], const T *geo, long long plane, long long g)
 {
+    const T jhd = geo[GC_JHD * plane + g];
     const T Ut = u[0] + u[3];
-    const T hd = J * k.h_dry;
-    const T rs = u[0] > hd ? T(1) / u[0] : T(0);
-    const T rf = u[3] > hd ? T(1) / u[3] : T(0);
-    const T cs = k.kap_s * (Ut + u[0]);
-    const T cf = k.kap_f2 * Ut;
-    T m = tabs(u[1] * rs) + tsqrt(g11 * cs);
-    m = tmax(m, tabs(u[4] * rf) + tsqrt(g11 * cf));
-    m = tmax(m, tabs(u[2] * rs) + tsqrt(g22 * cs));
-    m = tmax(m, tabs(u[5] * rf) + tsqrt(g22 * cf));
-    return (double)m;
+    const T rs = gtp(u[0], jhd) ? frcp(u[0]) : T(0);
+    const T rf = gtp(u[3], jhd) ? frcp(u[3]) : T(0);
+    const T cs = Ut + u[0];
+    T m = tabs(u[1] * rs) + fsqrt(geo[GC_SXS * plane + g] * cs);
+    m = maxnn(m, tabs(u[4] * rf) + fsqrt(geo[GC_SXF * plane + g] * Ut));
+    m = maxnn(m, tabs(u[2] * rs) + fsqrt(geo[GC_SYS * plane + g] * cs));
+    m = maxnn(m, tabs(u[5] * rf) + fsqrt(geo[GC_SYF * plane + g] * Ut));
+    return m;
 }
 
 __device__ __forceinline__ double dt_from(const Ctl *ctl, const Phys &ph, double amax)
@@ -275,17 +353,74 @@ __device__ __forceinline__ double dt_from(const Ctl *ctl, const Phys &ph, double
     return dt;
 }
 
+// Semi-implicit Coulomb friction with stopping (R6): q* = (q1, q2) after all
+// other terms, F = dt J p_b^s tan(delta_b); the tangential 3D momentum is
+// |q*|_3 = |(q1, q2, bX q1 + bY q2)|; stop if |q*|_3 <= F, else scale by
+// 1 - F / |q*|_3.  The decision is taken in FP64 in both forms; the FP32 form
+// first decides in FP32 when the two sides differ by more than 2^-10
+// relative (far above its rounding), which gives the same outcome.
+__device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, double bY, double Fr)
+{
+    const double qZ = fma(bX, q1, bY * q2);
+    const double qn2 = fma(q1, q1, fma(q2, q2, qZ * qZ));
+    if (!gtp(qn2, Fr * Fr)) {  // includes qn2 == 0
+        q1 = 0.0;
+        q2 = 0.0;
+        return;
+    }
+    const double r = fma(-Fr, frsqrt(qn2), 1.0);
+    q1 *= r;
+    q2 *= r;
+}
+// FP64 stopping decision of the FP32 form when FP32 cannot tell the two sides
+// apart; kept out of line so that the common path carries no FP64 work
+static __device__ __noinline__ bool stop_fp64(float q1, float q2, float bX, float bY, double dt, float Jpbs, double tan_d)
+{
+    const double Frd = dt * (double)Jpbs * tan_d;
+    const double dq1 = q1, dq2 = q2, dZ = (double)bX * dq1 + (double)bY * dq2;
+    return !(dq1 * dq1 + dq2 * dq2 + dZ * dZ > Frd * Frd);
+}
+
+__device__ __forceinline__ void coulomb(float &q1, float &q2, float bX, float bY, float Fr, double dt,
+                                        float Jpbs, double tan_d)
+{
+    const float qZ = fmaf(bX, q1, bY * q2);
+    const float qn2 = fmaf(q1, q1, fmaf(q2, q2, qZ * qZ));
+    const float F2 = Fr * Fr;
+    bool stop;
+    if (qn2 > F2 * (1.0f + 0x1p-10f)) stop = false;
+    else if (qn2 < F2 * (1.0f - 0x1p-10f)) stop = true;
+    else stop = stop_fp64(q1, q2, bX, bY, dt, Jpbs, tan_d);
+    if (stop) {
+        q1 = 0.0f;
+        q2 = 0.0f;
+        return;
+    }
+    const float r = fmaf(-Fr, frsqrt(qn2), 1.0f);
+    q1 *= r;
+    q2 *= r;
+}
+__device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, double bY, double Fr, double,
+                                        double, double)
+{
+    coulomb(q1, q2, bX, bY, Fr);
+}
+
+// ---- the stage kernel -------------------------------------------------------------
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) stage_kernel(const StageArgs<T> a)
+__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
 {
     constexpr int NT = TX * TY;
     constexpr int SW = TX + 4, SH = TY + 4, SP = SW * SH;
-    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+    constexpr int NSX = (TX + 2) * TY, NSY = TX * (TY + 2);  // cells with x- / y-slopes
+    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);  // x- / y-faces
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sU = reinterpret_cast<T *>(smem_raw);
-    T *sHx = sU + 6 * SP;   // [7][TY][TX+1]
-    T *sHy = sHx + 7 * NXF; // [7][TY+1][TX]
-    __shared__ double red_d[NT / 32];
+    T *sU = reinterpret_cast<T *>(smem_raw);  // [6][SH][SW]
+    T *sSx = sU + 6 * SP;                      // [6][TY][TX+2]   minmod slopes along x
+    T *sSy = sSx + 6 * NSX;                    // [6][TY+2][TX]   along y
+    T *sHx = sSy + 6 * NSY;                    // [7][TY][TX+1]   2 x flux, 2 x P
+    T *sHy = sHx + 7 * NXF;                    // [7][TY+1][TX]
+    __shared__ T red[NT / 32];
     __shared__ double acc[4];
     __shared__ unsigned int acc_n;
     __shared__ bool last_block;
@@ -294,26 +429,33 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(const StageArgs<T> a)
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
-    const K<T> k(a.ph);
+    const KT<T> &k = a.k;
     const T *geo = a.geo;
     Ctl *ctl = a.ctl;
+    __shared__ double s_t, s_dt;
+    __shared__ T s_dtT;
 
-    double t_now, dt;
-    if (a.debug_stage) {
-        t_now = a.dbg_t;
-        dt = a.dbg_dt;
-    } else if (a.stage == 1) {
-        t_now = ctl->t;
-        dt = dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
-    } else {
-        t_now = ctl->t;
-        dt = ctl->dt;
+    // the step's time and time step, once per CTA
+    if (tid == 0) {
+        double t_now, dt;
+        if (a.debug_stage) {
+            t_now = a.dbg_t;
+            dt = a.dbg_dt;
+        } else if (a.stage == 1) {
+            t_now = ctl->t;
+            dt = dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
+        } else {
+            t_now = ctl->t;
+            dt = ctl->dt;
+        }
+        s_t = t_now;
+        s_dt = dt;
+        s_dtT = (T)dt;
+        acc_n = 0;
     }
-    const T dtT = (T)dt;
     if (tid < 4) acc[tid] = 0.0;
-    if (tid == 0) acc_n = 0;
 
-    // ---- stage the tile + 2-cell halo of the six state planes -------------
+    // ---- stage the tile + 2-cell halo of the six state planes -----------
     for (int e = tid; e < 6 * SP; e += NT) {
         const int c = e / SP, r = e - c * SP;
         const int ly = r / SW, lx = r - ly * SW;
@@ -323,22 +465,53 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(const StageArgs<T> a)
         sU[e] = v;
     }
     __syncthreads();
+    const double t_now = s_t, dt = s_dt;
+    const T dtT = s_dtT;
+
+    // ---- minmod slopes, once per cell and direction -----------------------
+    for (int e = tid; e < 6 * NSX; e += NT) {  // cells x0-1 .. x0+TX, rows y0 .. y0+TY-1
+        const int c = e / NSX, r = e - c * NSX;
+        const int ly = r / (TX + 2), lx = r - ly * (TX + 2);
+        const T *p = sU + c * SP + (ly + 2) * SW + lx + 1;
+        sSx[e] = minmod(p[0] - p[-1], p[1] - p[0]);
+    }
+    for (int e = tid; e < 6 * NSY; e += NT) {  // rows y0-1 .. y0+TY, cells x0 .. x0+TX-1
+        const int c = e / NSY, r = e - c * NSY;
+        const int ly = r / TX, lx = r - ly * TX;
+        const T *p = sU + c * SP + (ly + 1) * SW + lx + 2;
+        sSy[e] = minmod(p[0] - p[-SW], p[SW] - p[0]);
+    }
+    __syncthreads();
 
     // ---- x-faces (i+1/2, j), i = x0-1 .. x0+TX-1 ---------------------------
     for (int f = tid; f < NXF; f += NT) {
         const int ly = f / (TX + 1), lx = f - ly * (TX + 1);
         const int i = x0 + lx - 1, j = y0 + ly;
         if (j >= ny || i >= nx) continue;
-        const long long gidx = cell_index(i, j, pitch);
-        FaceGeo<T> G{geo[GX_J * plane + gidx], geo[GX_GN * plane + gidx], geo[GX_GT * plane + gidx],
-                     geo[GX_C2 * plane + gidx]};
-        const int ob = (ly + 2) * SW + lx + 1;  // left cell in smem
+        const long long g = cell_index(i, j, pitch);
+        const FaceGeo<T> G{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
+                           geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
+                           geo[GX_HG * plane + g]};
+        const int ou = (ly + 2) * SW + lx + 1;  // left cell in sU
+        const int os = ly * (TX + 2) + lx;      // left cell in sSx
+        T um[6], up[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            um[c] = fma(T(0.5), sSx[c * NSX + os], sU[c * SP + ou]);
+            up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
+        }
         T H[7];
-        face_flux(sU, SP, ob - 1, ob, ob + 1, ob + 2, G, 0, k, H);
+        face_flux2<T, 0>(um, up, G, H);
+        if constexpr (sizeof(T) == 4) {
+            // FP32: the mass change this face gives each neighbour, rounded once
+            H[0] *= dtT * k.hinv_dx;
+            H[3] *= dtT * k.hinv_dx;
+        }
 #pragma unroll
         for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
         if (!a.debug_stage && (i == -1 || i == nx - 1)) {
-            const double w = 0.5 * dt * a.ph.dy * (i == -1 ? 1.0 : -1.0);
+            // Heun weight 1/2 x boundary volume flux of this stage
+            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dy) * (i == -1 ? 1.0 : -1.0);
             atomicAdd(&acc[0], w * (double)H[0]);
             atomicAdd(&acc[1], w * (double)H[3]);
         }
@@ -348,109 +521,125 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(const StageArgs<T> a)
         const int ly = f / TX, lx = f - ly * TX;
         const int i = x0 + lx, j = y0 + ly - 1;
         if (i >= nx || j >= ny) continue;
-        const long long gidx = cell_index(i, j, pitch);
-        FaceGeo<T> G{geo[GY_J * plane + gidx], geo[GY_GN * plane + gidx], geo[GY_GT * plane + gidx],
-                     geo[GY_C2 * plane + gidx]};
-        const int ob = (ly + 1) * SW + lx + 2;  // lower cell in smem
+        const long long g = cell_index(i, j, pitch);
+        const FaceGeo<T> G{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
+                           geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
+                           geo[GY_HG * plane + g]};
+        const int ou = (ly + 1) * SW + lx + 2;  // lower cell in sU
+        const int os = ly * TX + lx;            // lower cell in sSy
+        T um[6], up[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            um[c] = fma(T(0.5), sSy[c * NSY + os], sU[c * SP + ou]);
+            up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
+        }
         T H[7];
-        face_flux(sU, SP, ob - SW, ob, ob + SW, ob + 2 * SW, G, 1, k, H);
+        face_flux2<T, 1>(um, up, G, H);
+        if constexpr (sizeof(T) == 4) {
+            H[0] *= dtT * k.hinv_dy;
+            H[3] *= dtT * k.hinv_dy;
+        }
 #pragma unroll
         for (int c = 0; c < 7; c++) sHy[c * NYF + f] = H[c];
         if (!a.debug_stage && (j == -1 || j == ny - 1)) {
-            const double w = 0.5 * dt * a.ph.dx * (j == -1 ? 1.0 : -1.0);
+            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dx) * (j == -1 ? 1.0 : -1.0);
             atomicAdd(&acc[0], w * (double)H[0]);
             atomicAdd(&acc[1], w * (double)H[3]);
         }
     }
     __syncthreads();
 
-    // ---- cell update --------------------------------------------------------
+    // ---- cell update ------------------------------------------------------
     const int lx = tid % TX, ly = tid / TX;
     const int i = x0 + lx, j = y0 + ly;
-    double speed = 0.0;
+    T speed = T(0);
     bool bad = false;
     if (i < nx && j < ny) {
-        const long long gidx = cell_index(i, j, pitch);
+        const long long g = cell_index(i, j, pitch);
         const int os = (ly + 2) * SW + lx + 2;
         T u[6];
 #pragma unroll
         for (int c = 0; c < 6; c++) u[c] = sU[c * SP + os];
-        const T J = geo[GC_J * plane + gidx], c0 = geo[GC_C * plane + gidx];
-        const T bX = geo[GC_BX * plane + gidx], bY = geo[GC_BY * plane + gidx];
-        const T A11 = geo[GC_A11 * plane + gidx], A12 = geo[GC_A12 * plane + gidx],
-                A22 = geo[GC_A22 * plane + gidx];
-        const T kXX = geo[GC_KXX * plane + gidx], kXY = geo[GC_KXY * plane + gidx],
-                kYY = geo[GC_KYY * plane + gidx];
-        const T hd = J * k.h_dry;
+        const T jhd = geo[GC_JHD * plane + g];
         const T Ut = u[0] + u[3];
-        // volume fractions phi^s, phi^f of the mixture (0 when h <= h_dry)
-        const bool wet = Ut * c0 > k.h_dry;
-        const T rUt = wet ? T(1) / Ut : T(0);
+        // volume fractions phi^s, phi^f (0 where h <= h_dry)
+        const T rUt = gtp(Ut, jhd) ? frcp(Ut) : T(0);
         const T phs = u[0] * rUt, phf = u[3] * rUt;
-        const bool ws = u[0] > hd, wf = u[3] > hd;
-        const T rs = ws ? T(1) / u[0] : T(0), rf = wf ? T(1) / u[3] : T(0);
+        const T rs = gtp(u[0], jhd) ? frcp(u[0]) : T(0);
+        const T rf = gtp(u[3], jhd) ? frcp(u[3]) : T(0);
         const T vXs = u[1] * rs, vYs = u[2] * rs, vXf = u[4] * rf, vYf = u[5] * rf;
-        // kappa = v . (dn/dxi v_xi + dn/deta v_eta) = -c (bXX vX^2 + 2 bXY vX vY + bYY vY^2)
-        const T ks = -(kXX * vXs * vXs + T(2) * kXY * vXs * vYs + kYY * vYs * vYs);
-        const T kf = -(kXX * vXf * vXf + T(2) * kXY * vXf * vYf + kYY * vYf * vYf);
-        // J p_b for each phase, clamped at 0 (lift-off)
-        const T Jpbs = tmax(T(0), u[0] * (k.g_1ma * c0 - k.eps_chi * ks));
-        const T Jpbf = tmax(T(0), u[3] * (k.g * c0 - k.eps_chi * kf));
-        // s_n = J p_b (n_X, n_Y) = J p_b c (-bX, -bY)
-        const T nsX = -c0 * bX, nsY = -c0 * bY;
-        // gradient of P = J h pbar^f from its face values
+        // -kappa = c (bXX vX^2 + 2 bXY vX vY + bYY vY^2): the centripetal term
+        // sum_k v_k (dn_k/dxi v_xi + dn_k/deta v_eta) with v tangent to the bed
+        const T kXX = geo[GC_KXX * plane + g], kXY2 = geo[GC_KXY2 * plane + g], kYY = geo[GC_KYY * plane + g];
+        const T nks = fma(kXX, vXs * vXs, fma(kXY2, vXs * vYs, kYY * (vYs * vYs)));
+        const T nkf = fma(kXX, vXf * vXf, fma(kXY2, vXf * vYf, kYY * (vYf * vYf)));
+        // J p_b = U (g c (1 - alpha) - eps^chi kappa), clamped at 0 (lift-off)
+        const T Jpbs = pos(u[0] * fma(k.eps_chi, nks, geo[GC_GC1 * plane + g]));
+        const T Jpbf = pos(u[3] * fma(k.eps_chi, nkf, geo[GC_GCF * plane + g]));
+        const T nX = geo[GC_MNX * plane + g], nY = geo[GC_MNY * plane + g];
+        // gradient of P = J h pbar^f from its (doubled) face values
         const int fx = ly * (TX + 1) + lx, fy = ly * TX + lx;
-        const T dPx = (sHx[6 * NXF + fx + 1] - sHx[6 * NXF + fx]) * k.inv_dx;
-        const T dPy = (sHy[6 * NYF + fy + TX] - sHy[6 * NYF + fy]) * k.inv_dy;
-        const T gX = A11 * dPx + A12 * dPy, gY = A12 * dPx + A22 * dPy;
-        const T fpg = a.ph.pg_mode == 1 ? phf : phs;
-        const T bs = -k.eps_alpha * phs, bf = k.eps * fpg;
-        // interphase drag J c_D phi^s phi^f h = c_D phi^s phi^f (J h)
-        const T D = k.c_d * phs * phf * Ut;
+        const T dPx = (sHx[6 * NXF + fx + 1] - sHx[6 * NXF + fx]) * k.hinv_dx;
+        const T dPy = (sHy[6 * NYF + fy + TX] - sHy[6 * NYF + fy]) * k.hinv_dy;
+        const T A11 = geo[GC_A11 * plane + g], A12 = geo[GC_A12 * plane + g], A22 = geo[GC_A22 * plane + g];
+        const T gX = fma(A11, dPx, A12 * dPy), gY = fma(A12, dPx, A22 * dPy);
+        const T bs = -k.eps_alpha * phs;                         // s_f^s = bs grad
+        const T bf = k.eps * (a.ph.pg_mode == 1 ? phf : phs);   // s_f^f = bf grad (R1)
+        const T D = k.c_d * phs * phf * Ut;                     // J c_D phi^s phi^f h
+        const T aD = k.alpha * D;
         const T dvX = vXf - vXs, dvY = vYf - vYs;
-        const T ff = k.k_f * phf * Ut;  // fluid basal friction J phi^f h k_f
+        const T ff = k.k_f * phf * Ut;                          // J phi^f h k_f
         T S[6];
         S[0] = T(0);
         S[3] = T(0);
-        S[1] = Jpbs * nsX + bs * gX + k.alpha * D * dvX;
-        S[2] = Jpbs * nsY + bs * gY + k.alpha * D * dvY;
-        S[4] = Jpbf * nsX + bf * gX - D * dvX - ff * vXf;
-        S[5] = Jpbf * nsY + bf * gY - D * dvY - ff * vYf;
+        S[1] = fma(Jpbs, nX, fma(bs, gX, aD * dvX));
+        S[2] = fma(Jpbs, nY, fma(bs, gY, aD * dvY));
+        S[4] = fma(Jpbf, nX, fma(bf, gX, -fma(D, dvX, ff * vXf)));
+        S[5] = fma(Jpbf, nY, fma(bf, gY, -fma(D, dvY, ff * vYf)));
         T out[6];
+        T lo[2] = {T(0), T(0)};  // FP32: rounding remainders of the masses
 #pragma unroll
         for (int c = 0; c < 6; c++) {
-            const T divx = (sHx[c * NXF + fx + 1] - sHx[c * NXF + fx]) * k.inv_dx;
-            const T divy = (sHy[c * NYF + fy + TX] - sHy[c * NYF + fy]) * k.inv_dy;
-            out[c] = u[c] + dtT * (S[c] - (divx + divy));
-        }
-        // Coulomb friction with stopping (semi-implicit, direction from q*),
-        // decided in FP64 in both precision forms
-        {
-            const double qX = (double)out[1], qY = (double)out[2];
-            const double qZ = (double)bX * qX + (double)bY * qY;
-            const double qn = sqrt(qX * qX + qY * qY + qZ * qZ);
-            const double Fr = dt * (double)Jpbs * k.tan_delta;
-            if (qn <= Fr) {
-                out[1] = T(0);
-                out[2] = T(0);
-            } else {
-                const double r = 1.0 - Fr / qn;
-                out[1] = (T)(qX * r);
-                out[2] = (T)(qY * r);
+            if constexpr (sizeof(T) == 4) {
+                if (c == 0 || c == 3) {
+                    // mass: U + R plus the four scaled face terms, summed
+                    // without loss (TwoSum), renormalised into (U, R)
+                    float s = u[c], e = a.Rin[(c / 3) * plane + g], t;
+                    const float terms[4] = {sHx[c * NXF + fx], -sHx[c * NXF + fx + 1], sHy[c * NYF + fy],
+                                            -sHy[c * NYF + fy + TX]};
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        two_sum(s, terms[q], s, t);
+                        e += t;
+                    }
+                    out[c] = s + e;
+                    lo[c / 3] = e - (out[c] - s);
+                    continue;
+                }
             }
+            const T dx2 = sHx[c * NXF + fx + 1] - sHx[c * NXF + fx];
+            const T dy2 = sHy[c * NYF + fy + TX] - sHy[c * NYF + fy];
+            const T div = fma(dx2, k.hinv_dx, dy2 * k.hinv_dy);
+            out[c] = fma(dtT, S[c] - div, u[c]);
         }
+        if constexpr (sizeof(T) == 8)
+            coulomb(out[1], out[2], geo[GC_BX * plane + g], geo[GC_BY * plane + g], dt * Jpbs * k.tan_delta);
+        else
+            coulomb(out[1], out[2], geo[GC_BX * plane + g], geo[GC_BY * plane + g], dtT * Jpbs * k.tan_delta, dt,
+                    Jpbs, k.tan_delta_d);
         // positivity clamp (counted) and dry momentum
 #pragma unroll
         for (int ph = 0; ph < 2; ph++) {
             const int c = 3 * ph;
-            if (out[c] < T(0)) {
+            if (negative(out[c])) {
                 if (!a.debug_stage) {
-                    atomicAdd(&acc[2 + ph], -0.5 * (double)out[c] * a.ph.cell_area);
+                    atomicAdd(&acc[2 + ph], -0.5 * ((double)out[c] + (double)lo[ph]) * a.ph.cell_area);
                     atomicAdd(&acc_n, 1u);
                 }
                 out[c] = T(0);
+                lo[ph] = T(0);
             }
-            if (out[c] <= hd) {
+            if (!gtp(out[c], jhd)) {
                 out[c + 1] = T(0);
                 out[c + 2] = T(0);
             }
@@ -458,34 +647,49 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(const StageArgs<T> a)
         if (a.stage == 2 && !a.debug_stage) {
             // Heun average with U^n (same cell), dry momentum again
 #pragma unroll
-            for (int c = 0; c < 6; c++) out[c] = T(0.5) * (a.Un[c * plane + gidx] + out[c]);
+            for (int c = 0; c < 6; c++) {
+                if constexpr (sizeof(T) == 4) {
+                    if (c == 0 || c == 3) {
+                        // (U^n + R^n + U** + R**) / 2 on (value, remainder) pairs
+                        float s, e;
+                        two_sum(a.Un[c * plane + g], out[c], s, e);
+                        e += a.Rn[(c / 3) * plane + g] + lo[c / 3];
+                        s *= 0.5f;
+                        e *= 0.5f;
+                        out[c] = s + e;
+                        lo[c / 3] = e - (out[c] - s);
+                        continue;
+                    }
+                }
+                out[c] = T(0.5) * (a.Un[c * plane + g] + out[c]);
+            }
 #pragma unroll
             for (int ph = 0; ph < 2; ph++)
-                if (out[3 * ph] <= hd) {
+                if (!gtp(out[3 * ph], jhd)) {
                     out[3 * ph + 1] = T(0);
                     out[3 * ph + 2] = T(0);
                 }
-            if (a.want_amax)
-                speed = cell_speed(out, J, geo[GC_G11 * plane + gidx], geo[GC_G22 * plane + gidx], k);
+            if (a.want_amax) speed = cell_speed(out, geo, plane, g);
         }
 #pragma unroll
         for (int c = 0; c < 6; c++) bad |= nonfinite(out[c]);
-        if (a.debug_stage) {
-            store6(a.Uout, plane, gidx, out);
-        } else {
-            store6(a.Uout, plane, gidx, out);
-            write_ghosts(a.Uout, geo, a, i, j, out, t_now + dt);
+        store6(a.Uout, plane, g, out);
+        if constexpr (sizeof(T) == 4) {
+            a.Rout[g] = lo[0];
+            a.Rout[plane + g] = lo[1];
         }
+        if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, out, t_now + dt);
     }
 
     if (a.debug_stage) return;
 
-    // ---- CTA reductions -----------------------------------------------------
+    // ---- CTA reductions ---------------------------------------------------
     if (bad) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
     if (a.stage == 2 && a.want_amax) {
+        if (nonfinite(speed)) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) speed = fmax(speed, __shfl_xor_sync(0xffffffffu, speed, o));
-        if ((tid & 31) == 0) red_d[tid >> 5] = speed;
+        for (int o = 16; o > 0; o >>= 1) speed = maxnn(speed, __shfl_xor_sync(0xffffffffu, speed, o));
+        if ((tid & 31) == 0) red[tid >> 5] = speed;
     }
     __syncthreads();
     if (tid == 0) {
@@ -499,9 +703,9 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(const StageArgs<T> a)
         if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0) ctl->dt = dt;
         if (a.stage == 2) {
             if (a.want_amax) {
-                double m = 0.0;
-                for (int w = 0; w < NT / 32; w++) m = fmax(m, red_d[w]);
-                atomicMax(&ctl->amax_acc, (unsigned long long)__double_as_longlong(m));
+                T m = T(0);
+                for (int w = 0; w < NT / 32; w++) m = maxnn(m, red[w]);
+                atomicMax(&ctl->amax_acc, (unsigned long long)__double_as_longlong((double)m));
             }
             __threadfence();
             const unsigned int nb = gridDim.x * gridDim.y;
@@ -519,15 +723,14 @@ __global__ void __launch_bounds__(TX *TY) stage_kernel(const StageArgs<T> a)
             ctl->t = ctl->t + ctl->dt;
             ctl->steps += 1;
         }
-        const double am = __longlong_as_double((long long)m);
-        if (a.want_amax && am != am) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
     }
 }
 
 template <typename T, int TX, int TY>
 constexpr size_t stage_smem_bytes()
 {
-    return sizeof(T) * (6 * (TX + 4) * (TY + 4) + 7 * (TX + 1) * TY + 7 * TX * (TY + 1));
+    return sizeof(T) * (6 * (TX + 4) * (TY + 4) + 6 * (TX + 2) * TY + 6 * TX * (TY + 2) + 7 * (TX + 1) * TY +
+                        7 * TX * (TY + 1));
 }
 
 }  // namespace moses
