@@ -177,6 +177,29 @@ const char *moses_last_error(const moses_sim *s);
 /* Release all device memory of s.  NULL is ignored. */
 void moses_destroy(moses_sim *s);
 
+/* ---- Ensembles --------------------------------------------------------------
+ * Many independent simulations advanced together, for the "abundant plausible
+ * scenarios" and parameter back-calculation use of Sect. 5: each member keeps
+ * its own DEM, grid size, parameters, time and CFL time step.  One batched
+ * launch per Heun stage covers the 32 x 8 tiles of every member, and the time
+ * loop is recorded once as a CUDA graph (16 steps) that moses_batch_step
+ * replays.  Members are ordinary moses_sim objects created on the same stream
+ * with the same precision form; their states and budgets are read with the
+ * per-simulation calls.  The batch does not own them: destroy the batch before
+ * its members.  Errors (moses_batch_last_error): EINVAL, ESTATE, ENONFINITE,
+ * ECUDA. */
+typedef struct moses_batch moses_batch;
+int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out);
+/* every member advances nsteps CFL-limited steps; synchronises at the end */
+int moses_batch_step(moses_batch *b, int nsteps);
+/* the same, with CUDA events on the batch's stream around the steps: *ms
+ * receives their device time [ms] */
+int moses_batch_step_timed(moses_batch *b, int nsteps, double *ms);
+/* number of tiles (CTAs) in one batched stage launch */
+int moses_batch_tiles(const moses_batch *b);
+const char *moses_batch_last_error(const moses_batch *b);
+void moses_batch_destroy(moses_batch *b);
+
 /* ---- Step without device allocation --------------------------------------
  * The paper has no counterpart to this call.  It is for callers that cannot
  * let a library allocate device memory: code that records its work into a

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/moses.h"
 #include "moses_dev.cuh"
@@ -1098,4 +1099,232 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
         CK(cudaStreamSynchronize(st));
     }
     return MOSES_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Ensembles: many independent simulations (own DEM, parameters, grid size,
+// time step) advanced together.  One batched launch per Heun stage covers the
+// tiles of every member; the time loop is recorded once as a CUDA graph of
+// kGraphSteps steps and replayed, so a whole run is a handful of graph
+// launches.  Members stay ordinary moses_sim objects.
+
+struct moses_batch {
+    int n = 0;
+    int prec = MOSES_FP64;
+    cudaStream_t stream = nullptr;       // the batch's own stream (graphs cannot be
+                                         // recorded on the legacy default stream)
+    cudaStream_t user_stream = nullptr;  // the members' stream
+    cudaEvent_t ev = nullptr;
+    std::vector<moses_sim *> sims;
+    void *args1 = nullptr, *args2 = nullptr;  // StageArgs<T>[n] for stage 1 / 2
+    BatchTile *tiles = nullptr;
+    int ntiles = 0;
+    Ctl **ctls = nullptr;
+    int *status = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string err;
+};
+
+namespace {
+constexpr int kGraphSteps = 16;
+constexpr int kBatchTX = 32, kBatchTY = 8;
+
+__global__ void batch_status_kernel(Ctl *const *ctls, int n, int *out)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        ctls[k]->dt_fixed = 0.0;
+        ctls[k]->t_end = 0.0;
+        if (ctls[k]->status) atomicOr(out, ctls[k]->status);
+    }
+}
+
+int batch_fail(moses_batch *b, int code, const std::string &msg)
+{
+    if (b) b->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+template <typename T>
+int batch_launch_step(moses_batch *b)
+{
+    if (launch_stage_batch<T>((const StageArgs<T> *)b->args1, b->tiles, b->ntiles, b->stream)) return -1;
+    if (launch_stage_batch<T>((const StageArgs<T> *)b->args2, b->tiles, b->ntiles, b->stream)) return -1;
+    return 0;
+}
+
+template <typename T>
+int batch_build(moses_batch *b)
+{
+    std::vector<StageArgs<T>> a1(b->n), a2(b->n);
+    std::vector<BatchTile> tiles;
+    std::vector<Ctl *> ctls(b->n);
+    for (int k = 0; k < b->n; k++) {
+        moses_sim *s = b->sims[k];
+        a1[k] = base_args<T>(s);
+        a1[k].Uin = (const T *)s->U;
+        a1[k].Uout = (T *)s->Us;
+        a1[k].Rin = rem<T>(s, s->U);
+        a1[k].Rout = rem<T>(s, s->Us);
+        a1[k].stage = 1;
+        a2[k] = base_args<T>(s);
+        a2[k].Uin = (const T *)s->Us;
+        a2[k].Un = (const T *)s->U;
+        a2[k].Uout = (T *)s->U;
+        a2[k].Rin = rem<T>(s, s->Us);
+        a2[k].Rn = rem<T>(s, s->U);
+        a2[k].Rout = rem<T>(s, s->U);
+        a2[k].stage = 2;
+        a2[k].want_amax = 1;
+        const int tx = (s->nx + kBatchTX - 1) / kBatchTX, ty = (s->ny + kBatchTY - 1) / kBatchTY;
+        for (int by = 0; by < ty; by++)
+            for (int bx = 0; bx < tx; bx++) tiles.push_back(BatchTile{k, bx, by, (unsigned)(tx * ty)});
+        ctls[k] = s->ctl;
+    }
+    b->ntiles = (int)tiles.size();
+    moses_sim *s = nullptr;  // CK reports into g_create_err
+    CK(cudaMalloc(&b->args1, sizeof(StageArgs<T>) * b->n));
+    CK(cudaMalloc(&b->args2, sizeof(StageArgs<T>) * b->n));
+    CK(cudaMalloc(&b->tiles, sizeof(BatchTile) * tiles.size()));
+    CK(cudaMalloc(&b->ctls, sizeof(Ctl *) * b->n));
+    CK(cudaMalloc(&b->status, sizeof(int)));
+    CK(cudaMemcpyAsync(b->args1, a1.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->args2, a2.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->ctls, ctls.data(), sizeof(Ctl *) * b->n, cudaMemcpyHostToDevice, b->stream));
+    // set the launch attributes outside any capture, then record the graph
+    if (launch_stage_batch<T>((const StageArgs<T> *)b->args1, b->tiles, 0, b->stream))
+        return batch_fail(b, MOSES_ECUDA, "batched stage kernel attributes");
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (int q = 0; q < kGraphSteps && rc == 0; q++) rc = batch_launch_step<T>(b);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+    if (rc || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return batch_fail(b, MOSES_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    }
+    b->graph = g;
+    CK(cudaGraphInstantiate(&b->exec, g, 0));
+    return MOSES_OK;
+}
+
+void free_batch(moses_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->args1);
+    cudaFree(b->args2);
+    cudaFree(b->tiles);
+    cudaFree(b->ctls);
+    cudaFree(b->status);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+}  // namespace
+
+int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out)
+{
+    if (!out) return batch_fail(nullptr, MOSES_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !sims) return batch_fail(nullptr, MOSES_EINVAL, "need n >= 1 simulations");
+    for (int k = 0; k < n; k++) {
+        if (!sims[k]) return batch_fail(nullptr, MOSES_EINVAL, "NULL simulation in the batch");
+        if (sims[k]->prec != sims[0]->prec) return batch_fail(nullptr, MOSES_EINVAL, "members must share the precision");
+        if (sims[k]->stream != sims[0]->stream) return batch_fail(nullptr, MOSES_EINVAL, "members must share the stream");
+        if (!sims[k]->have_state) return batch_fail(nullptr, MOSES_ESTATE, "member without a state");
+        for (int q = 0; q < k; q++)
+            if (sims[q] == sims[k]) return batch_fail(nullptr, MOSES_EINVAL, "a simulation appears twice");
+    }
+    moses_batch *b = new (std::nothrow) moses_batch();
+    if (!b) return batch_fail(nullptr, MOSES_ENOMEM, "host allocation failed");
+    b->n = n;
+    b->prec = sims[0]->prec;
+    b->user_stream = sims[0]->stream;
+    b->sims.assign(sims, sims + n);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(b->ev, b->user_stream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev, 0) != cudaSuccess) {
+        g_create_err = "batch stream or event creation failed";
+        free_batch(b);
+        return MOSES_ECUDA;
+    }
+    const int rc = b->prec == MOSES_FP64 ? batch_build<double>(b) : batch_build<float>(b);
+    if (rc) {
+        if (b->err.empty()) b->err = g_create_err;
+        g_create_err = b->err;
+        free_batch(b);
+        return rc;
+    }
+    *out = b;
+    return MOSES_OK;
+}
+
+static int batch_step(moses_batch *b, int nsteps, double *ms);
+
+int moses_batch_step(moses_batch *b, int nsteps) { return batch_step(b, nsteps, nullptr); }
+
+int moses_batch_step_timed(moses_batch *b, int nsteps, double *ms)
+{
+    if (!ms) return batch_fail(b, MOSES_EINVAL, "ms is NULL");
+    return batch_step(b, nsteps, ms);
+}
+
+static int batch_step(moses_batch *b, int nsteps, double *ms)
+{
+    if (!b) return MOSES_EINVAL;
+    if (nsteps < 0) return batch_fail(b, MOSES_EINVAL, "nsteps must be >= 0");
+    moses_sim *s = nullptr;
+    // order after the members' pending work
+    CK(cudaEventRecord(b->ev, b->user_stream));
+    CK(cudaStreamWaitEvent(b->stream, b->ev, 0));
+    CK(cudaMemsetAsync(b->status, 0, sizeof(int), b->stream));
+    batch_status_kernel<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctls, b->n, b->status);  // CFL mode
+    CK(cudaGetLastError());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, b->stream));
+    }
+    int left = nsteps;
+    while (left >= kGraphSteps) {
+        CK(cudaGraphLaunch(b->exec, b->stream));
+        left -= kGraphSteps;
+    }
+    for (; left > 0; left--) {
+        const int rc = b->prec == MOSES_FP64 ? batch_launch_step<double>(b) : batch_launch_step<float>(b);
+        if (rc) return batch_fail(b, MOSES_ECUDA, "batched stage launch failed");
+    }
+    if (ms) {
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float m = 0.f;
+        CK(cudaEventElapsedTime(&m, e0, e1));
+        *ms = m;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    CK(cudaMemsetAsync(b->status, 0, sizeof(int), b->stream));
+    batch_status_kernel<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctls, b->n, b->status);
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (st & STATUS_NONFINITE) return batch_fail(b, MOSES_ENONFINITE, "a member became non-finite");
+    return MOSES_OK;
+}
+
+int moses_batch_tiles(const moses_batch *b) { return b ? b->ntiles : 0; }
+
+const char *moses_batch_last_error(const moses_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+void moses_batch_destroy(moses_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    free_batch(b);
 }

@@ -128,7 +128,7 @@ inline KT<T> make_kt(const Phys &p)
 
 // Everything a stage kernel needs.
 template <typename T>
-struct StageArgs {
+struct alignas(8) StageArgs {
     const T *Uin;      // stage input (ghosts valid on the four sides)
     const T *Un;       // stage 2: U^n for the Heun average (interior); else null
     T *Uout;           // stage output (may equal Un in stage 2: same cell only)
@@ -160,7 +160,10 @@ __host__ __device__ inline long long cell_index(int i, int j, int pitch)
 
 // launchers of the templated stage kernels (one translation unit per type)
 namespace moses {
+struct BatchTile;
 template <typename T>
 int launch_stage(const StageArgs<T> &a, int tile, void *stream);
-int stage_tiles_available(int *tiles, int max);
+// batched stage over a work list of `ntiles` tiles (tile shape 32 x 8)
+template <typename T>
+int launch_stage_batch(const StageArgs<T> *args_device, const BatchTile *tiles_device, int ntiles, void *stream);
 }  // namespace moses

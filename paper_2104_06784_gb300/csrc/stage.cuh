@@ -407,8 +407,10 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
 }
 
 // ---- the stage kernel -------------------------------------------------------------
+// One stage on the tile (bx, by) of the simulation described by `a`; nb is the
+// number of CTAs working on that simulation in this launch (for the ticket).
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
+__device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
     constexpr int NT = TX * TY;
     constexpr int SW = TX + 4, SH = TY + 4, SP = SW * SH;
@@ -426,7 +428,7 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
     __shared__ bool last_block;
 
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
     const KT<T> &k = a.k;
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
             atomicAdd(&ctl->clamp_vol[1], acc[3]);
             atomicAdd(&ctl->clamp_cells, (unsigned long long)acc_n);
         }
-        if (a.stage == 1 && blockIdx.x == 0 && blockIdx.y == 0) ctl->dt = dt;
+        if (a.stage == 1 && bx == 0 && by == 0) ctl->dt = dt;
         if (a.stage == 2) {
             if (a.want_amax) {
                 T m = T(0);
@@ -708,7 +710,6 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
                 atomicMax(&ctl->amax_acc, (unsigned long long)__double_as_longlong((double)m));
             }
             __threadfence();
-            const unsigned int nb = gridDim.x * gridDim.y;
             last_block = (atomicAdd(&ctl->ticket, 1u) == nb - 1);
         }
     }
@@ -724,6 +725,37 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
             ctl->steps += 1;
         }
     }
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
+{
+    stage_tile<T, TX, TY>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+}
+
+// Ensemble form: one launch runs the same stage of many simulations.  Each CTA
+// takes one entry of the work list (simulation, tile x, tile y), copies that
+// simulation's arguments into shared memory and runs the tile.  Every
+// simulation keeps its own control block, so its own time and time step.
+struct BatchTile {
+    int sim, bx, by;
+    unsigned int nb;  // CTAs of this simulation in the launch
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
+    stage_kernel_batch(const StageArgs<T> *__restrict__ args, const BatchTile *__restrict__ tiles)
+{
+    __shared__ StageArgs<T> sa;
+    const BatchTile w = tiles[blockIdx.x];
+    {
+        // cooperative copy of the descriptor (plain 4-byte words)
+        const int *src = reinterpret_cast<const int *>(args + w.sim);
+        int *dst = reinterpret_cast<int *>(&sa);
+        for (int q = threadIdx.x; q < (int)(sizeof(StageArgs<T>) / 4); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    stage_tile<T, TX, TY>(sa, w.bx, w.by, w.nb);
 }
 
 template <typename T, int TX, int TY>

@@ -38,4 +38,22 @@ int launch_stage<float>(const StageArgs<float> &a, int tile, void *stream)
     }
 }
 
+template <>
+int launch_stage_batch<float>(const StageArgs<float> *args_device, const BatchTile *tiles_device, int ntiles, void *stream)
+{
+    constexpr size_t smem = stage_smem_bytes<float, 32, 8>();
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(stage_kernel_batch<float, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    if (ntiles <= 0) return 0;
+    stage_kernel_batch<float, 32, 8><<<ntiles, 256, smem, (cudaStream_t)stream>>>(args_device, tiles_device);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace moses

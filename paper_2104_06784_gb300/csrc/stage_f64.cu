@@ -38,4 +38,22 @@ int launch_stage<double>(const StageArgs<double> &a, int tile, void *stream)
     }
 }
 
+template <>
+int launch_stage_batch<double>(const StageArgs<double> *args_device, const BatchTile *tiles_device, int ntiles, void *stream)
+{
+    constexpr size_t smem = stage_smem_bytes<double, 32, 8>();
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        if (cudaFuncSetAttribute(stage_kernel_batch<double, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return -1;
+        attr_set[dev] = true;
+    }
+    if (ntiles <= 0) return 0;
+    stage_kernel_batch<double, 32, 8><<<ntiles, 256, smem, (cudaStream_t)stream>>>(args_device, tiles_device);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace moses

@@ -77,6 +77,12 @@ SIGNATURES = [
     ("moses_get_budget", C.c_int, [_vp, _dp]),
     ("moses_step_static", C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(Params), _vp, _vp,
                                     C.c_double, _dp, _vp]),
+    ("moses_batch_create", C.c_int, [C.c_int, C.POINTER(_vp), C.POINTER(_vp)]),
+    ("moses_batch_step", C.c_int, [_vp, C.c_int]),
+    ("moses_batch_step_timed", C.c_int, [_vp, C.c_int, _dp]),
+    ("moses_batch_tiles", C.c_int, [_vp]),
+    ("moses_batch_last_error", C.c_char_p, [_vp]),
+    ("moses_batch_destroy", None, [_vp]),
     ("moses_last_error", C.c_char_p, [_vp]),
     ("moses_destroy", None, [_vp]),
     ("moses_version", C.c_char_p, []),
@@ -234,6 +240,50 @@ class Sim:
         out = np.empty(BUDGET_LEN)
         self._ck(self._L.moses_get_budget(self._h, _p(out)))
         return dict(zip(BUDGET_KEYS, out.tolist()))
+
+
+class Batch:
+    """An ensemble of simulations advanced together (moses_batch_*)."""
+
+    def __init__(self, sims):
+        self._L = lib()
+        self.sims = list(sims)
+        arr = (_vp * len(self.sims))(*[s._h.value for s in self.sims])
+        h = C.c_void_p()
+        rc = self._L.moses_batch_create(len(self.sims), arr, C.byref(h))
+        if rc != 0:
+            raise MosesError(rc, self._L.moses_batch_last_error(None).decode())
+        self._h = h
+
+    def step(self, n: int = 1):
+        rc = self._L.moses_batch_step(self._h, int(n))
+        if rc != 0:
+            raise MosesError(rc, self._L.moses_batch_last_error(self._h).decode())
+
+    def step_timed(self, n: int = 1) -> float:
+        """Advance n steps; device time [ms] from CUDA events on the batch stream."""
+        ms = C.c_double()
+        rc = self._L.moses_batch_step_timed(self._h, int(n), C.byref(ms))
+        if rc != 0:
+            raise MosesError(rc, self._L.moses_batch_last_error(self._h).decode())
+        return ms.value
+
+    @property
+    def tiles(self) -> int:
+        return self._L.moses_batch_tiles(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.moses_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def from_config(cfg: dict, precision: int = FP64, stream=None) -> Sim:
