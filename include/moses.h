@@ -200,6 +200,38 @@ int moses_batch_tiles(const moses_batch *b);
 const char *moses_batch_last_error(const moses_batch *b);
 void moses_batch_destroy(moses_batch *b);
 
+/* ---- Adjoint: gradients of a deposit misfit --------------------------------
+ * For the parameter back-calculation of Sect. 5: runs nsteps CFL steps from
+ * the current state and returns L = sum_cells (h^s - h^s_target)^2 dx dy at
+ * the end (h^s = J h^s / J, the solid's normal thickness) with its gradient.
+ * The adjoint holds the recorded time steps fixed and uses the derivative of
+ * the branch the forward took at every kink (minmod, max of the local speeds,
+ * Coulomb stopping -> 0, positivity clamp and dry rule -> 0).  The state is
+ * checkpointed every ckpt_every steps (<= 0: ceil(sqrt(nsteps))) and each
+ * segment is recomputed before it is swept backwards.
+ *   hs_target    nx*ny target solid thickness [m] (host)
+ *   loss         L [m^4]; may be NULL
+ *   g_params     [0] dL/d delta_b per degree, [1] dL/d phi_int (0: the
+ *                model has no internal friction, k_mode 0), [2] dL/d c_D
+ *   g_state0     6*nx*ny dL/dU at the start (host) or NULL
+ *   g_release_h  nx*ny dL/dh of the release thickness (host) or NULL, with
+ *                release_phi the release's solid fraction (NULL: U1/(U1+U4))
+ *   timing_ms    [0] forward run, [1] recompute + backward sweep (CUDA
+ *                events), or NULL
+ * Afterwards the state and the time are those at the end of the forward run.
+ * Not available with nu_f > 0.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double *hs_target, double *loss,
+                         double g_params[3], double *g_state0, double *g_release_h, const double *release_phi,
+                         double timing_ms[2]);
+
+/* Adjoint of one stage at the current state (the reverse of moses_stage with
+ * the time step dt held fixed): lam_in = (dS/dU)^T lam_out, both 6*nx*nx
+ * doubles on the host in the plane order of moses_get_conserved;
+ * g_param[0..1] (may be NULL) receive lam_out . dS/d tan(delta_b) and
+ * lam_out . dS/d c_D.  For stage-level gradient checks. */
+int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out, double *lam_in,
+                        double *g_param);
+
 /* ---- Step without device allocation --------------------------------------
  * The paper has no counterpart to this call.  It is for callers that cannot
  * let a library allocate device memory: code that records its work into a

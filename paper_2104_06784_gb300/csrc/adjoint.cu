@@ -1,0 +1,373 @@
+// adjoint.cu -- gradient of a deposit misfit through many steps of the
+// two-phase scheme (moses_adjoint_misfit): forward run with the CFL time steps
+// recorded and the state checkpointed every C steps, then for each segment,
+// from the last to the first, the segment is recomputed with the recorded time
+// steps (keeping U^n and the Heun intermediate U* of every step) and swept
+// backwards with the stage adjoints of adjoint.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "adjoint.cuh"
+#include "internal.cuh"
+
+using namespace moses;
+
+namespace {
+
+constexpr int ATX = 32, ATY = 8;
+
+template <typename T>
+constexpr size_t adj_cell_smem()
+{
+    return stage_smem_bytes<T, ATX, ATY>();
+}
+
+template <typename T>
+int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
+{
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    constexpr size_t smA = adj_cell_smem<T>();
+    constexpr size_t smB = FaceAdjSmem<T, ATX, ATY>::bytes;
+    if (dev >= 0 && dev < 64 && !attr[dev]) {
+        if (cudaFuncSetAttribute(adj_cell_kernel<T, ATX, ATY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB) !=
+                cudaSuccess)
+            return -1;
+        attr[dev] = true;
+    }
+    const dim3 grid((q.f.nx + ATX - 1) / ATX, (q.f.ny + ATY - 1) / ATY);
+    adj_cell_kernel<T, ATX, ATY><<<grid, ATX * ATY, smA, st>>>(q);
+    adj_face_kernel<T, ATX, ATY><<<grid, ATX * ATY, smB, st>>>(q);
+    adj_fold_kernel<T><<<(q.f.nx + q.f.ny + 127) / 128, 128, 0, st>>>(q);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+// before step n: its start time; after it: its time step
+__global__ void record_t_kernel(const Ctl *ctl, double *ts, int n) { ts[n] = ctl->t; }
+__global__ void record_dt_kernel(const Ctl *ctl, double *dts, int n) { dts[n] = ctl->dt; }
+// recompute a step exactly as the forward run took it: same time (the inflow
+// hydrograph depends on it) and same time step
+__global__ void set_dt_kernel(Ctl *ctl, double t, double dt)
+{
+    ctl->t = t;
+    ctl->dt_fixed = dt;
+}
+
+// L = sum (h^s - h^s_target)^2 dx dy with h^s = U1 / J; lam = dL/dU (U1 only)
+template <typename T>
+__global__ void misfit_kernel(const T *U, const T *R, const T *geo, const double *target, int nx, int ny, int pitch,
+                              long long plane, double area, T *lam, double *loss)
+{
+    const long long n = (long long)nx * ny;
+    double acc = 0.0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const long long g = cell_index(i, j, pitch);
+        const double J = (double)geo[GC_J * plane + g];
+        double U1 = (double)U[g];
+        if (R) U1 += (double)R[g];
+        const double d = U1 / J - target[e];
+        acc += d * d * area;
+        lam[g] = (T)(2.0 * area * d / J);
+#pragma unroll
+        for (int c = 1; c < 6; c++) lam[c * plane + g] = T(0);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// dL/dh of the release h (U1 = J h phi, U4 = J h (1 - phi), momenta = U v)
+template <typename T>
+__global__ void release_grad_kernel(const T *lam, const T *U0, const T *geo, const double *phi, int nx, int ny,
+                                    int pitch, long long plane, double *out)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const long long g = cell_index(i, j, pitch);
+        const double J = (double)geo[GC_J * plane + g];
+        const double u1 = (double)U0[g], u4 = (double)U0[3 * plane + g];
+        double ph = phi ? phi[e] : ((u1 + u4) > 0.0 ? u1 / (u1 + u4) : 0.5);
+        double gs = (double)lam[g], gf = (double)lam[3 * plane + g];
+        if (u1 > 0.0) gs += ((double)U0[plane + g] * (double)lam[plane + g] + (double)U0[2 * plane + g] * (double)lam[2 * plane + g]) / u1;
+        if (u4 > 0.0) gf += ((double)U0[4 * plane + g] * (double)lam[4 * plane + g] + (double)U0[5 * plane + g] * (double)lam[5 * plane + g]) / u4;
+        out[e] = J * (ph * gs + (1.0 - ph) * gf);
+    }
+}
+
+template <typename T>
+__global__ void pack_lam_kernel(const T *lam, double *dst, int nx, int ny, int pitch, long long plane)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const long long r = e - c * n;
+        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
+        dst[e] = (double)lam[c * plane + cell_index(i, j, pitch)];
+    }
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { cudaFree(p); }
+};
+
+template <typename T>
+int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, double *loss_out, double *g_params,
+                 double *g_state0, double *g_release_h, const double *release_phi, double *timing)
+{
+    cudaStream_t st = s->stream;
+    const int nx = s->nx, ny = s->ny, pitch = s->pitch;
+    const long long plane = s->plane;
+    const long long n = (long long)nx * ny;
+    const size_t sb = (s->prec == MOSES_FP32 ? 8 : 6) * (size_t)plane * sizeof(T);  // a full state buffer
+    const size_t lb = 6 * (size_t)plane * sizeof(T);
+    const int nck = (nsteps + C - 1) / C;
+    DevBuf dts_d, ck, seg, lam, lam_half, lamA, lamB, lpre, ldp, lacc, gpar, loss_d, tgt, phi_d, hbuf;
+    CK(cudaMalloc(&dts_d.p, 2 * sizeof(double) * nsteps));
+    CK(cudaMalloc(&ck.p, sb * nck));
+    CK(cudaMalloc(&seg.p, sb * (2 * C + 1)));
+    for (DevBuf *b : {&lam, &lam_half, &lamA, &lamB, &lpre, &lacc}) {
+        CK(cudaMalloc(&b->p, lb));
+        CK(cudaMemsetAsync(b->p, 0, lb, st));
+    }
+    CK(cudaMalloc(&ldp.p, 2 * (size_t)plane * sizeof(T)));
+    CK(cudaMemsetAsync(ldp.p, 0, 2 * (size_t)plane * sizeof(T), st));
+    CK(cudaMalloc(&gpar.p, 2 * sizeof(double)));
+    CK(cudaMemsetAsync(gpar.p, 0, 2 * sizeof(double), st));
+    CK(cudaMalloc(&loss_d.p, sizeof(double)));
+    CK(cudaMemsetAsync(loss_d.p, 0, sizeof(double), st));
+    CK(cudaMalloc(&tgt.p, sizeof(double) * n));
+    CK(cudaMemcpyAsync(tgt.p, hs_target, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    if (release_phi) {
+        CK(cudaMalloc(&phi_d.p, sizeof(double) * n));
+        CK(cudaMemcpyAsync(phi_d.p, release_phi, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    }
+    char *ckp = (char *)ck.p, *segp = (char *)seg.p;
+    auto segU = [&](int q) { return (void *)(segp + sb * q); };          // U^{start+q}, q = 0..C
+    auto segS = [&](int q) { return (void *)(segp + sb * (C + 1 + q)); };  // U* of step start+q
+
+    cudaEvent_t ev[4];
+    for (int q = 0; q < 4; q++) CK(cudaEventCreate(&ev[q]));
+    CK(cudaEventRecord(ev[0], st));
+
+    // ---- forward run, CFL time steps recorded, checkpoints every C steps ----
+    StageArgs<T> a1 = base_args<T>(s), a2 = base_args<T>(s);
+    a1.Uin = (const T *)s->U;
+    a1.Uout = (T *)s->Us;
+    a1.Rin = rem<T>(s, s->U);
+    a1.Rout = rem<T>(s, s->Us);
+    a1.stage = 1;
+    a2.Uin = (const T *)s->Us;
+    a2.Un = (const T *)s->U;
+    a2.Uout = (T *)s->U;
+    a2.Rin = rem<T>(s, s->Us);
+    a2.Rn = rem<T>(s, s->U);
+    a2.Rout = rem<T>(s, s->U);
+    a2.stage = 2;
+    a2.want_amax = 1;
+    const double zero = 0.0;
+    CK(cudaMemcpyAsync(&s->ctl->dt_fixed, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(&s->ctl->t_end, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
+    for (int k = 0; k < nsteps; k++) {
+        if (k % C == 0) CK(cudaMemcpyAsync(ckp + sb * (k / C), s->U, sb, cudaMemcpyDeviceToDevice, st));
+        record_t_kernel<<<1, 1, 0, st>>>(s->ctl, (double *)dts_d.p + nsteps, k);
+        if (launch_stage<T>(a1, 0, st) || launch_stage<T>(a2, 0, st)) return fail(s, MOSES_ECUDA, "forward launch");
+        record_dt_kernel<<<1, 1, 0, st>>>(s->ctl, (double *)dts_d.p, k);
+    }
+    CK(cudaGetLastError());
+    Ctl ctl_end;
+    CK(cudaMemcpyAsync(&ctl_end, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    DevBuf fin;
+    CK(cudaMalloc(&fin.p, sb));
+    CK(cudaMemcpyAsync(fin.p, s->U, sb, cudaMemcpyDeviceToDevice, st));
+    misfit_kernel<T><<<grid_for(n), 256, 0, st>>>((const T *)s->U, rem<T>(s, s->U), (const T *)s->geo,
+                                                   (const double *)tgt.p, nx, ny, pitch, plane, s->dx * s->dy,
+                                                   (T *)lam.p, (double *)loss_d.p);
+    std::vector<double> dts(2 * (size_t)nsteps);  // time steps, then start times
+    CK(cudaMemcpyAsync(dts.data(), dts_d.p, 2 * sizeof(double) * nsteps, cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ev[1], st));
+    CK(cudaStreamSynchronize(st));
+
+    // ---- backward over the segments ----
+    AdjArgs<T> q{};
+    q.lam_pre = (T *)lpre.p;
+    q.lam_dp = (T *)ldp.p;
+    q.lam_acc = (T *)lacc.p;
+    q.g_param = (double *)gpar.p;
+    for (int kseg = nck - 1; kseg >= 0; kseg--) {
+        const int start = kseg * C, end = std::min(start + C, nsteps);
+        CK(cudaMemcpyAsync(s->U, ckp + sb * kseg, sb, cudaMemcpyDeviceToDevice, st));
+        for (int k = start; k < end; k++) {
+            CK(cudaMemcpyAsync(segU(k - start), s->U, sb, cudaMemcpyDeviceToDevice, st));
+            set_dt_kernel<<<1, 1, 0, st>>>(s->ctl, dts[nsteps + k], dts[k]);
+            if (launch_stage<T>(a1, 0, st)) return fail(s, MOSES_ECUDA, "recompute launch");
+            CK(cudaMemcpyAsync(segS(k - start), s->Us, sb, cudaMemcpyDeviceToDevice, st));
+            if (launch_stage<T>(a2, 0, st)) return fail(s, MOSES_ECUDA, "recompute launch");
+        }
+        CK(cudaMemcpyAsync(segU(end - start), s->U, sb, cudaMemcpyDeviceToDevice, st));
+        for (int k = end - 1; k >= start; k--) {
+            adj_heun_mask_kernel<T><<<grid_for(n), 256, 0, st>>>((const T *)segU(k + 1 - start), (const T *)s->geo,
+                                                                (const T *)lam.p, (T *)lam_half.p, nx, ny, pitch,
+                                                                plane);
+            // stage 2 at U*: lam_out = lam_half -> lamA
+            q.f = base_args<T>(s);
+            q.f.Uin = (const T *)segS(k - start);
+            q.f.debug_stage = 1;
+            q.f.dbg_dt = dts[k];
+            q.lam_out = (const T *)lam_half.p;
+            q.lam_in = (T *)lamA.p;
+            if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
+            // stage 1 at U^n: lam_out = lamA -> lamB
+            q.f.Uin = (const T *)segU(k - start);
+            q.lam_out = (const T *)lamA.p;
+            q.lam_in = (T *)lamB.p;
+            if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
+            adj_combine_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const T *)lam_half.p, (const T *)lamB.p,
+                                                                  (T *)lam.p, nx, ny, pitch, plane);
+        }
+    }
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ev[2], st));
+    // ---- outputs; the state and the clock go back to the end of the forward run ----
+    double gp[2] = {0, 0}, loss = 0;
+    CK(cudaMemcpyAsync(gp, gpar.p, sizeof(gp), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&loss, loss_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (g_state0) {
+        CK(cudaMalloc(&hbuf.p, sizeof(double) * 6 * n));
+        pack_lam_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const T *)lam.p, (double *)hbuf.p, nx, ny, pitch, plane);
+        CK(cudaMemcpyAsync(g_state0, hbuf.p, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+    }
+    if (g_release_h) {
+        DevBuf gh;
+        CK(cudaMalloc(&gh.p, sizeof(double) * n));
+        release_grad_kernel<T><<<grid_for(n), 256, 0, st>>>((const T *)lam.p, (const T *)ckp, (const T *)s->geo,
+                                                            (const double *)phi_d.p, nx, ny, pitch, plane,
+                                                            (double *)gh.p);
+        CK(cudaMemcpyAsync(g_release_h, gh.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    CK(cudaMemcpyAsync(s->U, fin.p, sb, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(s->ctl, &ctl_end, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(ev[3], st));
+    CK(cudaStreamSynchronize(st));
+    if (timing) {
+        float f = 0, b = 0;
+        cudaEventElapsedTime(&f, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        timing[0] = f;
+        timing[1] = b;
+    }
+    for (int q2 = 0; q2 < 4; q2++) cudaEventDestroy(ev[q2]);
+    const double tand = s->ph.tan_delta;
+    if (loss_out) *loss_out = loss;
+    if (g_params) {
+        g_params[0] = gp[0] * (1.0 + tand * tand) * (M_PI / 180.0);  // per degree of delta_b
+        g_params[1] = 0.0;  // k_mode 0: the internal friction angle does not enter the model
+        g_params[2] = gp[1];
+    }
+    return MOSES_OK;
+}
+
+}  // namespace
+
+int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double *hs_target, double *loss,
+                         double g_params[3], double *g_state0, double *g_release_h, const double *release_phi,
+                         double timing_ms[2])
+{
+    if (!s) return MOSES_EINVAL;
+    if (!hs_target) return fail(s, MOSES_EINVAL, "hs_target must be non-NULL");
+    if (nsteps < 1) return fail(s, MOSES_EINVAL, "nsteps must be >= 1");
+    if (ckpt_every < 1) ckpt_every = (int)std::ceil(std::sqrt((double)nsteps));
+    if (ckpt_every > nsteps) ckpt_every = nsteps;
+    if (s->p.nu_f != 0.0) return fail(s, MOSES_EINVAL, "the adjoint does not cover the viscous term");
+    if (!s->have_state) return fail(s, MOSES_ESTATE, "no state");
+    return s->prec == MOSES_FP64
+               ? adjoint_impl<double>(s, nsteps, ckpt_every, hs_target, loss, g_params, g_state0, g_release_h,
+                                      release_phi, timing_ms)
+               : adjoint_impl<float>(s, nsteps, ckpt_every, hs_target, loss, g_params, g_state0, g_release_h,
+                                     release_phi, timing_ms);
+}
+
+namespace {
+template <typename T>
+__global__ void unpack_lam_kernel(const double *src, T *lam, int nx, int ny, int pitch, long long plane)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const long long r = e - c * n;
+        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
+        lam[c * plane + cell_index(i, j, pitch)] = (T)src[e];
+    }
+}
+
+template <typename T>
+int stage_adjoint_impl(moses_sim *s, double dt, const double *lam_out, double *lam_in, double *g_param)
+{
+    cudaStream_t st = s->stream;
+    const long long n = (long long)s->nx * s->ny;
+    const size_t lb = 6 * (size_t)s->plane * sizeof(T);
+    DevBuf lo, li, lpre, ldp, lacc, gp, hb;
+    CK(cudaMalloc(&lo.p, lb));
+    CK(cudaMalloc(&li.p, lb));
+    CK(cudaMalloc(&lpre.p, lb));
+    CK(cudaMalloc(&lacc.p, lb));
+    CK(cudaMalloc(&ldp.p, 2 * (size_t)s->plane * sizeof(T)));
+    CK(cudaMalloc(&gp.p, 2 * sizeof(double)));
+    CK(cudaMalloc(&hb.p, sizeof(double) * 6 * n));
+    CK(cudaMemsetAsync(lo.p, 0, lb, st));
+    CK(cudaMemsetAsync(li.p, 0, lb, st));
+    CK(cudaMemsetAsync(gp.p, 0, 2 * sizeof(double), st));
+    CK(cudaMemcpyAsync(hb.p, lam_out, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
+    unpack_lam_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const double *)hb.p, (T *)lo.p, s->nx, s->ny, s->pitch,
+                                                          s->plane);
+    AdjArgs<T> q{};
+    q.f = base_args<T>(s);
+    q.f.Uin = (const T *)s->U;
+    q.f.debug_stage = 1;
+    q.f.dbg_dt = dt;
+    q.lam_out = (const T *)lo.p;
+    q.lam_in = (T *)li.p;
+    q.lam_pre = (T *)lpre.p;
+    q.lam_dp = (T *)ldp.p;
+    q.lam_acc = (T *)lacc.p;
+    q.g_param = (double *)gp.p;
+    if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
+    pack_lam_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const T *)li.p, (double *)hb.p, s->nx, s->ny, s->pitch,
+                                                        s->plane);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(lam_in, hb.p, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+    double g[2];
+    CK(cudaMemcpyAsync(g, gp.p, sizeof(g), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (g_param) {
+        g_param[0] = g[0];
+        g_param[1] = g[1];
+    }
+    return MOSES_OK;
+}
+}  // namespace
+
+int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out, double *lam_in, double *g_param)
+{
+    if (!s || !lam_out || !lam_in) return MOSES_EINVAL;
+    if (!(std::isfinite(dt) && dt >= 0)) return fail(s, MOSES_EINVAL, "bad dt");
+    // ghosts of the current state at time t, as moses_stage sees them
+    double *tmp = nullptr;
+    cudaStream_t st = s->stream;
+    CK(cudaMallocHost(&tmp, sizeof(double) * 6 * (size_t)s->nx * s->ny));
+    int rc = moses_stage(s, t, dt, tmp);
+    cudaFreeHost(tmp);
+    if (rc) return rc;
+    (void)st;
+    return s->prec == MOSES_FP64 ? stage_adjoint_impl<double>(s, dt, lam_out, lam_in, g_param)
+                                 : stage_adjoint_impl<float>(s, dt, lam_out, lam_in, g_param);
+}

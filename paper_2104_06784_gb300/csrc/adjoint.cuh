@@ -1,0 +1,683 @@
+// adjoint.cuh -- reverse (vector-Jacobian) form of one stage of the
+// two-phase shallow-flow scheme, for gradients of a deposit misfit with respect
+// to the basal friction, the drag coefficient and the initial state.
+//
+// The stage U -> S(U) of stage.cuh is differentiated with the time step held
+// fixed (it is recorded by the forward run).  Where the scheme has kinks the
+// derivative of the branch the forward took is used: minmod -> the selected
+// difference (0 when the limiter returns 0); max of the two local speeds -> the
+// selected side; Coulomb stopping -> 0 for a stopped cell; positivity clamp
+// and dry rule -> 0 for the clamped or zeroed values; |v| -> sign(v).
+//
+// The adjoint of a stage is computed by three kernels so that every tile
+// gathers (no scatter across tiles):
+//   A  per cell: recompute the forward tile, reverse the masks, the friction,
+//      the sources and the update.  Writes the adjoint of the pre-friction
+//      output lam_pre (6), of the pressure gradient (dP/dxi, dP/deta), the
+//      cell's own contributions lam_acc (identity + sources + friction), and
+//      the parameter partials (tan delta_b, c_D) reduced per CTA.
+//   B  per face: recompute the face states (halo 3), form the flux adjoints
+//      from lam_pre and the pressure adjoints of the two neighbours, reverse
+//      the central flux and the minmod reconstruction, and gather per cell:
+//      lam_in = lam_acc + face terms, also for ghost cells at the boundary.
+//   C  fold the ghost cells' adjoints into their mirror / copy sources
+//      (inflow ghosts are constants).
+#pragma once
+#include "stage.cuh"
+
+namespace moses {
+
+__device__ __forceinline__ double tsgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+__device__ __forceinline__ float tsgn(float x) { return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f); }
+
+// adjoint of side_flux: given the adjoints of F (6), as, af and P, add the
+// adjoint of the reconstructed state u to lu
+template <typename T, int D>
+__device__ __forceinline__ void side_flux_vjp(const T u[6], const FaceGeo<T> &G, const T lF[6], T las, T laf, T lP,
+                                              T lu[6])
+{
+    const T Ut = u[0] + u[3];
+    const bool ws = gtp(u[0], G.jhd), wf = gtp(u[3], G.jhd);
+    const T rs = ws ? frcp(u[0]) : T(0);
+    const T rf = wf ? frcp(u[3]) : T(0);
+    const T uns = D == 0 ? u[1] : u[2];
+    const T unf = D == 0 ? u[4] : u[5];
+    const T vns = uns * rs, vnf = unf * rf;
+    const T sX = D == 0 ? G.sn : G.st, sY = D == 0 ? G.st : G.sn;
+    const T fX = D == 0 ? G.fn : G.ft, fY = D == 0 ? G.ft : G.fn;
+    const T qs = fsqrt(G.sn * (Ut + u[0])), qf = fsqrt(G.fn2 * Ut);
+    // F1 = sX Ps + u1 vns, F2 = sY Ps + u2 vns, F4 = fX Pf + u4 vnf, F5 = fY Pf + u5 vnf
+    const T lvns = lF[1] * u[1] + lF[2] * u[2] + las * tsgn(vns);
+    const T lvnf = lF[4] * u[4] + lF[5] * u[5] + laf * tsgn(vnf);
+    const T lPs = lF[1] * sX + lF[2] * sY;
+    const T lPf = lF[4] * fX + lF[5] * fY + lP * G.hg;
+    // Ps = Ut u0, Pf = Ut^2, as = |vns| + sqrt(sn (Ut + u0)), af = |vnf| + sqrt(fn2 Ut)
+    T lUt = lPs * u[0] + T(2) * Ut * lPf;
+    T lu0 = lPs * Ut;
+    if (qs > T(0)) {
+        const T t = las * G.sn / (T(2) * qs);
+        lUt += t;
+        lu0 += t;
+    }
+    if (qf > T(0)) lUt += laf * G.fn2 / (T(2) * qf);
+    lu[1] += lF[1] * vns;
+    lu[2] += lF[2] * vns;
+    lu[4] += lF[4] * vnf;
+    lu[5] += lF[5] * vnf;
+    // vns = uns / u0 (wet), F0 = uns (wet)
+    const T luns = lvns * rs + (ws ? lF[0] : T(0));
+    const T lunf = lvnf * rf + (wf ? lF[3] : T(0));
+    T lu3 = T(0);
+    if (ws) lu0 -= lvns * vns * rs;
+    if (wf) lu3 -= lvnf * vnf * rf;
+    lu[0] += lu0 + lUt;
+    lu[3] += lu3 + lUt;
+    lu[1 + D] += luns;
+    lu[4 + D] += lunf;
+}
+
+// adjoint of face_flux2 (H2 = F(um) + F(up) - a (up - um), H2[6] = P(um) + P(up))
+template <typename T, int D>
+__device__ __forceinline__ void face_flux2_vjp(const T um[6], const T up[6], const FaceGeo<T> &G, const T lH[6],
+                                               T lP2, T lum[6], T lup[6])
+{
+    T Fm[6], Fp[6], asm_, afm, asp, afp, Pm, Pp;
+    side_flux<T, D>(um, G, Fm, asm_, afm, Pm);
+    side_flux<T, D>(up, G, Fp, asp, afp, Pp);
+    const bool ms = ibits(asm_) >= ibits(asp), mf = ibits(afm) >= ibits(afp);  // maxnn picks the first on ties
+    const T as = ms ? asm_ : asp, af = mf ? afm : afp;
+    T las = T(0), laf = T(0);
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+        const T a = c < 3 ? as : af;
+        const T d = up[c] - um[c];
+        if (c < 3) las -= lH[c] * d;
+        else laf -= lH[c] * d;
+        lum[c] = a * lH[c];
+        lup[c] = -a * lH[c];
+    }
+    side_flux_vjp<T, D>(um, G, lH, ms ? las : T(0), mf ? laf : T(0), lP2, lum);
+    side_flux_vjp<T, D>(up, G, lH, ms ? T(0) : las, mf ? T(0) : laf, lP2, lup);
+}
+
+// minmod selection: 0 -> returned 0, 1 -> returned a, 2 -> returned b
+__device__ __forceinline__ int minmod_sel(double a, double b)
+{
+    const long long ia = ibits(a), ib = ibits(b);
+    const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
+    if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0;
+    return ma < mb ? 1 : 2;
+}
+__device__ __forceinline__ int minmod_sel(float a, float b)
+{
+    const int ia = ibits(a), ib = ibits(b);
+    const int ma = ia & 0x7fffffff, mb = ib & 0x7fffffff;
+    if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0;
+    return ma < mb ? 1 : 2;
+}
+
+// Arguments of the adjoint kernels
+template <typename T>
+struct AdjArgs {
+    StageArgs<T> f;   // the forward stage (Uin = the stage input; geometry, constants)
+    const T *lam_out; // adjoint of the stage output (6 planes, interior)
+    T *lam_pre;       // A -> B: adjoint of the pre-friction output (6 planes)
+    T *lam_dp;        // A -> B: adjoint of dP/dxi, dP/deta (2 planes)
+    T *lam_acc;       // A -> B: the cell's own contributions (6 planes)
+    T *lam_in;        // B: adjoint of the stage input (6 planes, ghosts included)
+    double *g_param;  // [0] d/d tan(delta_b), [1] d/d c_D (FP64 accumulators)
+};
+
+}  // namespace moses
+
+namespace moses {
+
+// ---- kernel A: cell adjoint ------------------------------------------------
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_cell_kernel(const AdjArgs<T> q)
+{
+    constexpr int NT = TX * TY;
+    constexpr int SW = TX + 4, SH = TY + 4, SP = SW * SH;
+    constexpr int NSX = (TX + 2) * TY, NSY = TX * (TY + 2);
+    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sU = reinterpret_cast<T *>(smem_raw);
+    T *sSx = sU + 6 * SP;
+    T *sSy = sSx + 6 * NSX;
+    T *sHx = sSy + 6 * NSY;
+    T *sHy = sHx + 7 * NXF;
+    __shared__ double red[2][NT / 32];
+
+    const StageArgs<T> &a = q.f;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const long long plane = a.plane;
+    const KT<T> &k = a.k;
+    const T *geo = a.geo;
+    const double dt = a.dbg_dt;
+    const T dtT = (T)dt;
+
+    for (int e = tid; e < 6 * SP; e += NT) {
+        const int c = e / SP, r = e - c * SP;
+        const int ly = r / SW, lx = r - ly * SW;
+        const int gi = x0 - 2 + lx, gj = y0 - 2 + ly;
+        T v = T(0);
+        if (gi < nx + 2 && gj < ny + 2) v = a.Uin[c * plane + cell_index(gi, gj, pitch)];
+        sU[e] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < 6 * NSX; e += NT) {
+        const int c = e / NSX, r = e - c * NSX;
+        const int ly = r / (TX + 2), lx = r - ly * (TX + 2);
+        const T *p = sU + c * SP + (ly + 2) * SW + lx + 1;
+        sSx[e] = minmod(p[0] - p[-1], p[1] - p[0]);
+    }
+    for (int e = tid; e < 6 * NSY; e += NT) {
+        const int c = e / NSY, r = e - c * NSY;
+        const int ly = r / TX, lx = r - ly * TX;
+        const T *p = sU + c * SP + (ly + 1) * SW + lx + 2;
+        sSy[e] = minmod(p[0] - p[-SW], p[SW] - p[0]);
+    }
+    __syncthreads();
+    for (int f = tid; f < NXF; f += NT) {
+        const int ly = f / (TX + 1), lx = f - ly * (TX + 1);
+        const int i = x0 + lx - 1, j = y0 + ly;
+        if (j >= ny || i >= nx) continue;
+        const long long g = cell_index(i, j, pitch);
+        const FaceGeo<T> G{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
+                           geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
+                           geo[GX_HG * plane + g]};
+        const int ou = (ly + 2) * SW + lx + 1, os = ly * (TX + 2) + lx;
+        T um[6], up[6], H[7];
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            um[c] = fma(T(0.5), sSx[c * NSX + os], sU[c * SP + ou]);
+            up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
+        }
+        face_flux2<T, 0>(um, up, G, H);
+#pragma unroll
+        for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
+    }
+    for (int f = tid; f < NYF; f += NT) {
+        const int ly = f / TX, lx = f - ly * TX;
+        const int i = x0 + lx, j = y0 + ly - 1;
+        if (i >= nx || j >= ny) continue;
+        const long long g = cell_index(i, j, pitch);
+        const FaceGeo<T> G{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
+                           geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
+                           geo[GY_HG * plane + g]};
+        const int ou = (ly + 1) * SW + lx + 2, os = ly * TX + lx;
+        T um[6], up[6], H[7];
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            um[c] = fma(T(0.5), sSy[c * NSY + os], sU[c * SP + ou]);
+            up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
+        }
+        face_flux2<T, 1>(um, up, G, H);
+#pragma unroll
+        for (int c = 0; c < 7; c++) sHy[c * NYF + f] = H[c];
+    }
+    __syncthreads();
+
+    const int lx = tid % TX, ly = tid / TX;
+    const int i = x0 + lx, j = y0 + ly;
+    double g_tan = 0.0, g_cd = 0.0;
+    if (i < nx && j < ny) {
+        const long long g = cell_index(i, j, pitch);
+        const int os = (ly + 2) * SW + lx + 2;
+        T u[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) u[c] = sU[c * SP + os];
+        // ---- forward (as in stage_tile) ----
+        const T jhd = geo[GC_JHD * plane + g];
+        const T Ut = u[0] + u[3];
+        const bool wmix = gtp(Ut, jhd), ws = gtp(u[0], jhd), wf = gtp(u[3], jhd);
+        const T rUt = wmix ? frcp(Ut) : T(0);
+        const T phs = u[0] * rUt, phf = u[3] * rUt;
+        const T rs = ws ? frcp(u[0]) : T(0), rf = wf ? frcp(u[3]) : T(0);
+        const T vXs = u[1] * rs, vYs = u[2] * rs, vXf = u[4] * rf, vYf = u[5] * rf;
+        const T kXX = geo[GC_KXX * plane + g], kXY2 = geo[GC_KXY2 * plane + g], kYY = geo[GC_KYY * plane + g];
+        const T nks = fma(kXX, vXs * vXs, fma(kXY2, vXs * vYs, kYY * (vYs * vYs)));
+        const T nkf = fma(kXX, vXf * vXf, fma(kXY2, vXf * vYf, kYY * (vYf * vYf)));
+        const T gc1 = geo[GC_GC1 * plane + g], gcf = geo[GC_GCF * plane + g];
+        const T ps_raw = u[0] * fma(k.eps_chi, nks, gc1), pf_raw = u[3] * fma(k.eps_chi, nkf, gcf);
+        const T Jpbs = pos(ps_raw), Jpbf = pos(pf_raw);
+        const T nX = geo[GC_MNX * plane + g], nY = geo[GC_MNY * plane + g];
+        const T bX = geo[GC_BX * plane + g], bY = geo[GC_BY * plane + g];
+        const int fx = ly * (TX + 1) + lx, fy = ly * TX + lx;
+        const T dPx = (sHx[6 * NXF + fx + 1] - sHx[6 * NXF + fx]) * k.hinv_dx;
+        const T dPy = (sHy[6 * NYF + fy + TX] - sHy[6 * NYF + fy]) * k.hinv_dy;
+        const T A11 = geo[GC_A11 * plane + g], A12 = geo[GC_A12 * plane + g], A22 = geo[GC_A22 * plane + g];
+        const T gX = fma(A11, dPx, A12 * dPy), gY = fma(A12, dPx, A22 * dPy);
+        const bool pgf = a.ph.pg_mode == 1;
+        const T bs = -k.eps_alpha * phs;
+        const T bf = k.eps * (pgf ? phf : phs);
+        const T D = k.c_d * phs * phf * Ut;
+        const T aD = k.alpha * D;
+        const T dvX = vXf - vXs, dvY = vYf - vYs;
+        const T ff = k.k_f * phf * Ut;
+        T S[6];
+        S[0] = T(0);
+        S[3] = T(0);
+        S[1] = fma(Jpbs, nX, fma(bs, gX, aD * dvX));
+        S[2] = fma(Jpbs, nY, fma(bs, gY, aD * dvY));
+        S[4] = fma(Jpbf, nX, fma(bf, gX, -fma(D, dvX, ff * vXf)));
+        S[5] = fma(Jpbf, nY, fma(bf, gY, -fma(D, dvY, ff * vYf)));
+        T pre[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            const T dx2 = sHx[c * NXF + fx + 1] - sHx[c * NXF + fx];
+            const T dy2 = sHy[c * NYF + fy + TX] - sHy[c * NYF + fy];
+            const T div = fma(dx2, k.hinv_dx, dy2 * k.hinv_dy);
+            pre[c] = fma(dtT, S[c] - div, u[c]);
+        }
+        // friction forward quantities
+        const T Fr = dtT * Jpbs * k.tan_delta;
+        const T q1 = pre[1], q2 = pre[2];
+        const T qZ = fma(bX, q1, bY * q2);
+        const T qn2 = fma(q1, q1, fma(q2, q2, qZ * qZ));
+        bool stopped;  // the forward's decision (FP32: with its FP64 tie-break)
+        if constexpr (sizeof(T) == 4) {
+            const float F2 = Fr * Fr;
+            if (qn2 > F2 * (1.0f + 0x1p-10f)) stopped = false;
+            else if (qn2 < F2 * (1.0f - 0x1p-10f)) stopped = true;
+            else stopped = stop_fp64(q1, q2, bX, bY, dt, Jpbs, k.tan_delta_d);
+        } else {
+            stopped = !gtp(qn2, Fr * Fr);
+        }
+        const bool rubs = !stopped && ibits(Fr) > 0;  // friction acts (and q* is not subnormal)
+        const T rr = rubs ? frsqrt(qn2) : T(0);
+        const T r = rubs ? fma(-Fr, rr, T(1)) : T(1);
+        T post[6] = {pre[0], stopped ? T(0) : q1 * r, stopped ? T(0) : q2 * r, pre[3], pre[4], pre[5]};
+        bool clamped[2], dry[2];
+#pragma unroll
+        for (int ph = 0; ph < 2; ph++) {
+            clamped[ph] = negative(post[3 * ph]);
+            const T m = clamped[ph] ? T(0) : post[3 * ph];
+            dry[ph] = !gtp(m, jhd);
+        }
+        // ---- reverse ----
+        T lo[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) lo[c] = q.lam_out[c * plane + g];
+        // clamp and dry rule
+#pragma unroll
+        for (int ph = 0; ph < 2; ph++) {
+            if (clamped[ph]) lo[3 * ph] = T(0);
+            if (dry[ph]) {
+                lo[3 * ph + 1] = T(0);
+                lo[3 * ph + 2] = T(0);
+            }
+        }
+        // friction
+        T lpre[6] = {lo[0], T(0), T(0), lo[3], lo[4], lo[5]};
+        T lFr = T(0);
+        if (!stopped && !rubs) {
+            lpre[1] = lo[1];
+            lpre[2] = lo[2];
+        }
+        if (rubs) {
+            const T s = lo[1] * q1 + lo[2] * q2;
+            const T t = ((s * rr) * rr) * (Fr * rr);  // s rr <= |lo|: no overflow for tiny |q*|
+            lpre[1] = fma(r, lo[1], t * fma(qZ, bX, q1));
+            lpre[2] = fma(r, lo[2], t * fma(qZ, bY, q2));
+            lFr = -s * rr;
+        }
+        T lJpbs = lFr * dtT * k.tan_delta;
+        g_tan += (double)(lFr * dtT * Jpbs);
+        // update pre = u + dt (S - div): identity, sources; div goes to faces via lam_pre
+        T lu[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) lu[c] = lpre[c];
+        T lS[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) lS[c] = dtT * lpre[c];
+        // sources
+        lJpbs += lS[1] * nX + lS[2] * nY;
+        T lJpbf = lS[4] * nX + lS[5] * nY;
+        const T lbs = lS[1] * gX + lS[2] * gY;
+        const T lbf = lS[4] * gX + lS[5] * gY;
+        const T lgX = lS[1] * bs + lS[4] * bf, lgY = lS[2] * bs + lS[5] * bf;
+        const T laD = lS[1] * dvX + lS[2] * dvY;
+        T lD = -(lS[4] * dvX + lS[5] * dvY) + laD * k.alpha;
+        T ldvX = lS[1] * aD - lS[4] * D, ldvY = lS[2] * aD - lS[5] * D;
+        const T lff = -(lS[4] * vXf + lS[5] * vYf);
+        T lvXf = -lS[4] * ff + ldvX, lvYf = -lS[5] * ff + ldvY;
+        T lvXs = -ldvX, lvYs = -ldvY;
+        T lphs = T(0), lphf = T(0), lUt = T(0);
+        // ff = k_f phf Ut ; D = c_D phs phf Ut
+        lphf += lff * k.k_f * Ut;
+        lUt += lff * k.k_f * phf;
+        g_cd += (double)(lD * phs * phf * Ut);
+        lphs += lD * k.c_d * phf * Ut;
+        lphf += lD * k.c_d * phs * Ut;
+        lUt += lD * k.c_d * phs * phf;
+        // bs = -eps alpha phs ; bf = eps phi
+        lphs -= lbs * k.eps_alpha;
+        if (pgf) lphf += lbf * k.eps;
+        else lphs += lbf * k.eps;
+        // gX, gY -> the pressure-gradient adjoints (to faces)
+        const T ldPx = lgX * A11 + lgY * A12, ldPy = lgX * A12 + lgY * A22;
+        // J p_b = max(0, U (g c - eps_chi kappa))
+        T lnks = T(0), lnkf = T(0);
+        if (ibits(ps_raw) > 0) {
+            lu[0] += lJpbs * fma(k.eps_chi, nks, gc1);
+            lnks = lJpbs * u[0] * k.eps_chi;
+        }
+        if (ibits(pf_raw) > 0) {
+            lu[3] += lJpbf * fma(k.eps_chi, nkf, gcf);
+            lnkf = lJpbf * u[3] * k.eps_chi;
+        }
+        lvXs += lnks * fma(T(2) * kXX, vXs, kXY2 * vYs);
+        lvYs += lnks * fma(kXY2, vXs, T(2) * kYY * vYs);
+        lvXf += lnkf * fma(T(2) * kXX, vXf, kXY2 * vYf);
+        lvYf += lnkf * fma(kXY2, vXf, T(2) * kYY * vYf);
+        // velocities v = q / U
+        lu[1] += lvXs * rs;
+        lu[2] += lvYs * rs;
+        lu[4] += lvXf * rf;
+        lu[5] += lvYf * rf;
+        if (ws) lu[0] -= (lvXs * vXs + lvYs * vYs) * rs;
+        if (wf) lu[3] -= (lvXf * vXf + lvYf * vYf) * rf;
+        // volume fractions phi = U / Ut
+        lu[0] += lphs * rUt;
+        lu[3] += lphf * rUt;
+        if (wmix) lUt -= (lphs * phs + lphf * phf) * rUt;
+        lu[0] += lUt;
+        lu[3] += lUt;
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            q.lam_pre[c * plane + g] = lpre[c];
+            q.lam_acc[c * plane + g] = lu[c];
+        }
+        q.lam_dp[g] = ldPx;
+        q.lam_dp[plane + g] = ldPy;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        g_tan += __shfl_xor_sync(0xffffffffu, g_tan, o);
+        g_cd += __shfl_xor_sync(0xffffffffu, g_cd, o);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = g_tan;
+        red[1][tid >> 5] = g_cd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = 0; w < NT / 32; w++) {
+            s0 += red[0][w];
+            s1 += red[1][w];
+        }
+        if (s0 != 0.0) atomicAdd(&q.g_param[0], s0);
+        if (s1 != 0.0) atomicAdd(&q.g_param[1], s1);
+    }
+}
+
+}  // namespace moses
+
+namespace moses {
+
+// ---- kernel B: face adjoint and gather ----------------------------------------
+// D = 0: x-faces over rows of the tile; D = 1: y-faces over columns.  Along the
+// face normal the tile covers cells [o0 - 2, o0 + L + 1] with slopes, faces with
+// lower cell in [o0 - 2, o0 + L], slope adjoints for cells [o0 - 1, o0 + L].
+template <typename T, int TX, int TY>
+struct FaceAdjSmem {
+    static constexpr int SW3 = TX + 6, SH3 = TY + 6, SP3 = SW3 * SH3;
+    static constexpr int NS = (TY * (TX + 4) > (TY + 4) * TX) ? TY * (TX + 4) : (TY + 4) * TX;
+    static constexpr int NF = (TY * (TX + 3) > (TY + 3) * TX) ? TY * (TX + 3) : (TY + 3) * TX;
+    static constexpr int NL = (TY * (TX + 2) > (TY + 2) * TX) ? TY * (TX + 2) : (TY + 2) * TX;
+    static constexpr size_t bytes = sizeof(T) * (6 * SP3 + 6 * NS + 12 * NF + 6 * NL) + 6 * NS;
+};
+
+template <typename T, int TX, int TY, int D>
+__device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, unsigned char *sSel, T *sLum,
+                                             T *sLup, T *sLs, T lres[6])
+{
+    using SM = FaceAdjSmem<T, TX, TY>;
+    constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3;
+    constexpr int L = D == 0 ? TX : TY;   // cells of the tile along the normal
+    constexpr int M = D == 0 ? TY : TX;   // lines of the tile
+    constexpr int NSl = L + 4, NFl = L + 3, NLl = L + 2;
+    constexpr int NS = M * NSl, NF = M * NFl, NL = M * NLl;
+    constexpr int STEP = D == 0 ? 1 : SW3;  // smem stride along the normal
+    const StageArgs<T> &a = q.f;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int o0 = D == 0 ? x0 : y0;
+    const int n = D == 0 ? a.nx : a.ny, nt = D == 0 ? a.ny : a.nx;  // along, across
+    const int pitch = a.pitch;
+    const long long plane = a.plane;
+    const T *geo = a.geo;
+    const T hinv = D == 0 ? a.k.hinv_dx : a.k.hinv_dy;
+    const T dtT = (T)a.dbg_dt;
+    auto sidx = [&](int m, int p) {  // smem index of cell at line m, normal position p (tile coords)
+        return D == 0 ? (m + 3) * SW3 + (p + 3) : (p + 3) * SW3 + (m + 3);
+    };
+    auto gidx = [&](int m, int p) {  // global (i, j) of line m, normal position p (tile coords)
+        return D == 0 ? cell_index(x0 + p, y0 + m, pitch) : cell_index(x0 + m, y0 + p, pitch);
+    };
+    // slopes and their selections, cells p = -2 .. L+1
+    for (int e = tid; e < 6 * NS; e += NT) {
+        const int c = e / NS, r = e - c * NS;
+        const int m = r / NSl, p = r - m * NSl - 2;
+        const T *u = sU + c * SP3 + sidx(m, p);
+        const T d1 = u[0] - u[-STEP], d2 = u[STEP] - u[0];
+        sS[e] = minmod(d1, d2);
+        sSel[e] = (unsigned char)minmod_sel(d1, d2);
+    }
+    __syncthreads();
+    // face adjoints, faces with lower cell p = -2 .. L
+    for (int e = tid; e < NF; e += NT) {
+        const int m = e / NFl, p = e - m * NFl - 2;
+        const int lo = o0 + p;                       // lower cell index along the normal
+        const int line = (D == 0 ? y0 : x0) + m;     // index across
+        const bool exists = lo >= -1 && lo <= n - 1 && line < nt;
+        T lum[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, lup[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        if (exists) {
+            const long long g = gidx(m, p);
+            FaceGeo<T> G;
+            if (D == 0)
+                G = FaceGeo<T>{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
+                               geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
+                               geo[GX_HG * plane + g]};
+            else
+                G = FaceGeo<T>{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
+                               geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
+                               geo[GY_HG * plane + g]};
+            const bool in_lo = lo >= 0, in_hi = lo + 1 <= n - 1;
+            const long long gl = g, gh = D == 0 ? g + 1 : g + pitch;
+            T lH[6];
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const T a1 = in_hi ? q.lam_pre[c * plane + gh] : T(0);
+                const T a0 = in_lo ? q.lam_pre[c * plane + gl] : T(0);
+                lH[c] = dtT * hinv * (a1 - a0);
+            }
+            const T d0 = in_lo ? q.lam_dp[D * plane + gl] : T(0);
+            const T d1 = in_hi ? q.lam_dp[D * plane + gh] : T(0);
+            const T lP2 = hinv * (d0 - d1);
+            T um[6], up[6];
+            const int sl = m * NSl + (p + 2);  // slope index of the lower cell
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                um[c] = fma(T(0.5), sS[c * NS + sl], sU[c * SP3 + sidx(m, p)]);
+                up[c] = fma(T(-0.5), sS[c * NS + sl + 1], sU[c * SP3 + sidx(m, p + 1)]);
+            }
+            face_flux2_vjp<T, D>(um, up, G, lH, lP2, lum, lup);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            sLum[c * NF + e] = lum[c];
+            sLup[c * NF + e] = lup[c];
+        }
+    }
+    __syncthreads();
+    // slope adjoints, cells p = -1 .. L: lam_sigma = (lam_um(face p) - lam_up(face p-1)) / 2
+    for (int e = tid; e < 6 * NL; e += NT) {
+        const int c = e / NL, r = e - c * NL;
+        const int m = r / NLl, p = r - m * NLl - 1;
+        const int f = m * NFl + (p + 2);  // face with lower cell p
+        sLs[e] = T(0.5) * (sLum[c * NF + f] - sLup[c * NF + f - 1]);
+    }
+    __syncthreads();
+    // gather for cell p at line m
+    // p in [-2, L+1]: faces p (lower cell p) and p-1 exist in the tile's range for
+    // p in [-1, L]; slope adjoints exist for cells [-1, L]
+    auto gather = [&](int m, int p, int c) -> T {
+        const int f = m * NFl + (p + 2);
+        T v = T(0);
+        if (p <= L) v += sLum[c * NF + f];
+        if (p >= -1) v += sLup[c * NF + f - 1];
+        const int sl = m * NSl + (p + 2);
+        const int lidx = m * NLl + (p + 1);
+        if (p >= -1 && p <= L) {
+            const unsigned char s0 = sSel[c * NS + sl];
+            if (s0 == 1) v += sLs[c * NL + lidx];
+            else if (s0 == 2) v -= sLs[c * NL + lidx];
+        }
+        if (p + 1 >= -1 && p + 1 <= L && sSel[c * NS + sl + 1] == 1) v -= sLs[c * NL + lidx + 1];
+        if (p - 1 >= -1 && p - 1 <= L && sSel[c * NS + sl - 1] == 2) v += sLs[c * NL + lidx - 1];
+        return v;
+    };
+    // interior cell of this thread
+    {
+        const int lx = tid % TX, ly = tid / TX;
+        const int m = D == 0 ? ly : lx, p = D == 0 ? lx : ly;
+#pragma unroll
+        for (int c = 0; c < 6; c++) lres[c] += gather(m, p, c);
+    }
+    // ghost cells beyond the domain boundary along this direction
+    for (int e = tid; e < 4 * M; e += NT) {
+        const int m = e / 4, w = e - m * 4;
+        const int line = (D == 0 ? y0 : x0) + m;
+        if (line >= nt) continue;
+        const int gpos = w < 2 ? -1 - w : n + (w - 2);  // -1, -2, n, n+1
+        // owners: the first tile for -1, -2; the tile holding cell n-1 for n, n+1
+        if (w < 2 ? o0 != 0 : !(o0 <= n - 1 && n - 1 < o0 + L)) continue;
+        const int p = gpos - o0;
+        const long long g = D == 0 ? cell_index(gpos, line, pitch) : cell_index(line, gpos, pitch);
+#pragma unroll
+        for (int c = 0; c < 6; c++) q.lam_in[c * plane + g] = gather(m, p, c);
+    }
+    __syncthreads();
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_face_kernel(const AdjArgs<T> q)
+{
+    using SM = FaceAdjSmem<T, TX, TY>;
+    constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sU = reinterpret_cast<T *>(smem_raw);
+    T *sS = sU + 6 * SP3;
+    T *sLum = sS + 6 * SM::NS;
+    T *sLup = sLum + 6 * SM::NF;
+    T *sLs = sLup + 6 * SM::NF;
+    unsigned char *sSel = reinterpret_cast<unsigned char *>(sLs + 6 * SM::NL);
+    const StageArgs<T> &a = q.f;
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const long long plane = a.plane;
+    // stage input with a 3-cell halo (cells beyond the 2 ghost layers read 0;
+    // no forward face uses them)
+    for (int e = tid; e < 6 * SP3; e += NT) {
+        const int c = e / SP3, r = e - c * SP3;
+        const int ly = r / SW3, lx = r - ly * SW3;
+        const int gi = x0 - 3 + lx, gj = y0 - 3 + ly;
+        T v = T(0);
+        if (gi >= -2 && gj >= -2 && gi < nx + 2 && gj < ny + 2) v = a.Uin[c * plane + cell_index(gi, gj, pitch)];
+        sU[e] = v;
+    }
+    __syncthreads();
+    T lres[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, lres);
+    adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, lres);
+    const int i = x0 + tid % TX, j = y0 + tid / TX;
+    if (i < nx && j < ny) {
+        const long long g = cell_index(i, j, pitch);
+#pragma unroll
+        for (int c = 0; c < 6; c++) q.lam_in[c * plane + g] = q.lam_acc[c * plane + g] + lres[c];
+    }
+}
+
+// ---- kernel C: fold the ghost adjoints into their sources ----------------------
+template <typename T>
+__global__ void adj_fold_kernel(const AdjArgs<T> q)
+{
+    const StageArgs<T> &a = q.f;
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const long long plane = a.plane;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool xs = e < ny;  // W/E sides for row e, else S/N sides for column e - ny
+    const int line = xs ? e : e - ny;
+    if (line >= (xs ? ny : nx)) return;
+    for (int side = xs ? 0 : 2; side < (xs ? 2 : 4); side++) {
+        bool inflow = false;
+        for (int f = 0; f < a.n_inflow; f++)
+            if (a.inflow[f].side == side && line >= a.inflow[f].i0 && line < a.inflow[f].i1) inflow = true;
+        if (inflow) continue;  // ghost state is a given function of time
+        const bool closed = a.ph.bc[side] == 0;
+        const int nn = xs ? nx : ny;
+        for (int kk = 0; kk < GH; kk++) {
+            int gpos, src;
+            if (side == 0 || side == 2) {
+                gpos = -1 - kk;
+                src = closed ? (kk < nn ? kk : nn - 1) : 0;
+            } else {
+                gpos = nn + kk;
+                src = closed ? (nn - 1 - kk >= 0 ? nn - 1 - kk : 0) : nn - 1;
+            }
+            const long long gg = xs ? cell_index(gpos, line, pitch) : cell_index(line, gpos, pitch);
+            const long long gs = xs ? cell_index(src, line, pitch) : cell_index(line, src, pitch);
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                T v = q.lam_in[c * plane + gg];
+                if (closed && ((xs && (c == 1 || c == 4)) || (!xs && (c == 2 || c == 5)))) v = -v;
+                atomicAdd(&q.lam_in[c * plane + gs], v);
+            }
+        }
+    }
+}
+
+// ---- step-level helpers -------------------------------------------------------
+// lam_half = 1/2 lam^{n+1} with the momenta zeroed where U^{n+1} is dry
+// (adjoint of the Heun average followed by the dry rule)
+template <typename T>
+__global__ void adj_heun_mask_kernel(const T *Unext, const T *geo, const T *lam_next, T *lam_half, int nx, int ny,
+                                     int pitch, long long plane)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const long long g = cell_index(i, j, pitch);
+        const T jhd = geo[GC_JHD * plane + g];
+#pragma unroll
+        for (int ph = 0; ph < 2; ph++) {
+            const bool dry = !gtp(Unext[3 * ph * plane + g], jhd);
+#pragma unroll
+            for (int c = 3 * ph; c < 3 * ph + 3; c++)
+                lam_half[c * plane + g] = (dry && c != 3 * ph) ? T(0) : T(0.5) * lam_next[c * plane + g];
+        }
+    }
+}
+
+// lam^n = lam_half + lam_stage1 (interior)
+template <typename T>
+__global__ void adj_combine_kernel(const T *lam_half, const T *lam_stage, T *lam_n, int nx, int ny, int pitch,
+                                   long long plane)
+{
+    const long long n = (long long)nx * ny;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const long long r = e - c * n;
+        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
+        const long long g = c * plane + cell_index(i, j, pitch);
+        lam_n[g] = lam_half[g] + lam_stage[g];
+    }
+}
+
+}  // namespace moses

@@ -1,0 +1,88 @@
+// internal.cuh -- the simulation object and host helpers shared by the
+// translation units of the library (not part of the public C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/moses.h"
+#include "moses_dev.cuh"
+
+using namespace moses;
+
+struct moses_sim {
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;  // elements per plane
+    double dx = 0, dy = 0;
+    moses_params p{};
+    Phys ph{};
+    int prec = MOSES_FP64;
+    size_t esz = 8;  // bytes per state element
+    cudaStream_t stream = nullptr;
+    void *U = nullptr;     // state, 6 planes
+    void *Us = nullptr;    // Heun intermediate, 6 planes
+    void *geo = nullptr;   // GEO_PLANES planes
+    Ctl *ctl = nullptr;    // device control block
+    InflowSeg *inflow_d = nullptr;
+    InflowSeg inflow_h[MAX_INFLOW];
+    int n_inflow = 0;
+    double *stage_buf = nullptr;  // dense 6*nx*ny doubles (host <-> device staging)
+    double *red = nullptr;        // 8 doubles for reductions
+    bool have_state = false;
+    int tile = 0;
+    std::string err;
+};
+
+extern std::string g_create_err;
+
+// ---------------------------------------------------------------------------
+// error helpers
+
+inline int fail(moses_sim *s, int code, const std::string &msg)
+{
+    if (s) s->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(s, e_ == cudaErrorMemoryAllocation ? MOSES_ENOMEM : MOSES_ECUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+    } while (0)
+
+
+inline int grid_for(long long n, int block = 256)
+{
+    long long b = (n + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+// remainder planes (FP32 form) that follow the six state planes of a buffer
+template <typename T>
+inline T *rem(moses_sim *s, void *buf)
+{
+    return s->prec == MOSES_FP32 ? (T *)buf + 6 * s->plane : nullptr;
+}
+
+template <typename T>
+inline StageArgs<T> base_args(moses_sim *s)
+{
+    StageArgs<T> a{};
+    a.geo = (const T *)s->geo;
+    a.ctl = s->ctl;
+    a.inflow = s->inflow_d;
+    a.n_inflow = s->n_inflow;
+    a.nx = s->nx;
+    a.ny = s->ny;
+    a.pitch = s->pitch;
+    a.plane = s->plane;
+    a.ph = s->ph;
+    a.k = make_kt<T>(s->ph);
+    return a;
+}
+

@@ -119,21 +119,27 @@ __device__ __forceinline__ float fsqrt(float x)
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// 1/sqrt(x) for x > 0 normal: approximation + two Newton steps
+// 1/sqrt(x) for x > 0: approximation + two Newton steps.  The approximation
+// flushes subnormal inputs to zero, so those are scaled by 2^512 (2^64 in FP32)
+// first and the result by 2^256 (2^32) after.
 __device__ __forceinline__ double frsqrt(double x)
 {
+    const bool sub = ibits(x) < 0x0010000000000000ll;
+    const double xs = sub ? x * 0x1p512 : x;
     double y;
-    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double t = x * y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(xs));
+    double t = xs * y;
     y = y * fma(-0.5 * t, y, 1.5);
-    t = x * y;
-    return y * fma(-0.5 * t, y, 1.5);
+    t = xs * y;
+    y = y * fma(-0.5 * t, y, 1.5);
+    return sub ? y * 0x1p256 : y;
 }
 __device__ __forceinline__ float frsqrt(float x)
 {
+    const bool sub = ibits(x) < 0x00800000;
     float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(sub ? x * 0x1p64f : x));
+    return sub ? y * 0x1p32f : y;
 }
 // error-free sum (Knuth's TwoSum): s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
@@ -368,6 +374,7 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
         q2 = 0.0;
         return;
     }
+    if (ibits(Fr) <= 0) return;  // no friction (lift-off or dry): r = 1, also for subnormal |q*|
     const double r = fma(-Fr, frsqrt(qn2), 1.0);
     q1 *= r;
     q2 *= r;
@@ -396,6 +403,7 @@ __device__ __forceinline__ void coulomb(float &q1, float &q2, float bX, float bY
         q2 = 0.0f;
         return;
     }
+    if (ibits(Fr) <= 0) return;  // no friction: r = 1
     const float r = fmaf(-Fr, frsqrt(qn2), 1.0f);
     q1 *= r;
     q2 *= r;

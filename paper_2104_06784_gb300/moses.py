@@ -83,6 +83,8 @@ SIGNATURES = [
     ("moses_batch_tiles", C.c_int, [_vp]),
     ("moses_batch_last_error", C.c_char_p, [_vp]),
     ("moses_batch_destroy", None, [_vp]),
+    ("moses_adjoint_misfit", C.c_int, [_vp, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
+    ("moses_stage_adjoint", C.c_int, [_vp, C.c_double, C.c_double, _dp, _dp, _dp]),
     ("moses_last_error", C.c_char_p, [_vp]),
     ("moses_destroy", None, [_vp]),
     ("moses_version", C.c_char_p, []),
@@ -236,6 +238,30 @@ class Sim:
         self._ck(self._L.moses_get_state(self._h, *[_p(a) for a in arrs]))
         return dict(zip(("h", "phi_s", "vx_s", "vy_s", "vx_f", "vy_f"), arrs))
 
+    def stage_adjoint(self, t: float, dt: float, lam_out):
+        """(dS/dU)^T lam_out for one stage at the current state; also the
+        parameter partials [d/d tan(delta_b), d/d c_D]."""
+        lo = _f64(lam_out)
+        li = np.empty((6, self.ny, self.nx))
+        gp = np.zeros(2)
+        self._ck(self._L.moses_stage_adjoint(self._h, float(t), float(dt), _p(lo), _p(li), _p(gp)))
+        return li, gp
+
+    def adjoint_misfit(self, nsteps: int, hs_target, ckpt_every: int = 0, release_phi=None,
+                       want_state=False, want_release=True):
+        """Loss, parameter gradients [d/d delta_b (per deg), d/d phi_int, d/d c_D],
+        dL/dh of the release and optionally dL/dU at the start; timings [ms]."""
+        tgt = _f64(hs_target)
+        loss = C.c_double()
+        gp = np.zeros(3)
+        gs = np.empty((6, self.ny, self.nx)) if want_state else None
+        gh = np.empty((self.ny, self.nx)) if want_release else None
+        phi = _f64(release_phi)
+        tm = np.zeros(2)
+        self._ck(self._L.moses_adjoint_misfit(self._h, int(nsteps), int(ckpt_every), _p(tgt), C.byref(loss), _p(gp),
+                                              _p(gs), _p(gh), _p(phi), _p(tm)))
+        return dict(loss=loss.value, g_params=gp, g_state0=gs, g_release_h=gh, timing_ms=tm)
+
     def budget(self) -> dict:
         out = np.empty(BUDGET_LEN)
         self._ck(self._L.moses_get_budget(self._h, _p(out)))
@@ -298,3 +324,41 @@ def from_config(cfg: dict, precision: int = FP64, stream=None) -> Sim:
 
 def version() -> str:
     return lib().moses_version().decode()
+
+
+def deposit_misfit(cfg: dict, h0, delta_b_deg, c_d, phi_int_deg, hs_target, nsteps: int, ckpt_every: int = 0,
+                   precision: int = FP32):
+    """Deposit misfit L = sum (h^s(t_N) - h^s_target)^2 dx dy as a differentiable
+    torch function of the release thickness h0, the basal friction angle
+    delta_b (degrees), the drag coefficient c_D and the internal friction
+    angle phi_int (degrees; it does not enter the model, gradient 0).
+
+    The forward pass and the gradients both come from moses_adjoint_misfit
+    (one forward run, checkpointed recomputation, reverse sweep); backward
+    scales the stored gradients by the incoming gradient.
+    """
+    import torch
+
+    class _Misfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, h0_t, db_t, cd_t, pi_t):
+            params = dict(cfg["params"], delta_b_deg=float(db_t), c_d=float(cd_t), phi_int_deg=float(pi_t))
+            sim = Sim(cfg["dem"], cfg["dx"], cfg["dy"], params, precision=precision)
+            try:
+                sim.set_release(h0_t.detach().cpu().double().numpy(), cfg["phi_s"])
+                r = sim.adjoint_misfit(nsteps, hs_target, ckpt_every=ckpt_every, release_phi=cfg["phi_s"])
+            finally:
+                sim.close()
+            gh = torch.from_numpy(r["g_release_h"]).to(h0_t.device, h0_t.dtype)
+            gp = torch.tensor(r["g_params"], dtype=torch.float64)
+            ctx.save_for_backward(gh, gp)
+            return torch.tensor(r["loss"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gout):
+            gh, gp = ctx.saved_tensors
+            g = gout.to(torch.float64)
+            return (gout.to(gh.dtype) * gh, (g * gp[0]).to(torch.float64), (g * gp[2]).to(torch.float64),
+                    (g * gp[1]).to(torch.float64))
+
+    return _Misfit.apply(h0, delta_b_deg, c_d, phi_int_deg)
