@@ -1,9 +1,10 @@
 // adjoint.cu -- gradient of a deposit misfit through many steps of the
 // two-phase scheme (moses_adjoint_misfit): forward run with the CFL time steps
-// recorded and the state checkpointed every C steps, then for each segment,
-// from the last to the first, the segment is recomputed with the recorded time
-// steps (keeping U^n and the Heun intermediate U* of every step) and swept
-// backwards with the stage adjoints of adjoint.cuh.
+// and start times recorded and the state checkpointed every C steps, then for
+// each segment, from the last to the first, the segment is recomputed with the
+// recorded times by the recording stage kernel (keeping U^n, the Heun
+// intermediate U* and each stage's record) and swept backwards with the stage
+// adjoints of adjoint.cuh.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -20,31 +21,23 @@ namespace {
 constexpr int ATX = 32, ATY = 8;
 
 template <typename T>
-constexpr size_t adj_cell_smem()
-{
-    return stage_smem_bytes<T, ATX, ATY>();
-}
-
-template <typename T>
 int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
 {
     static bool attr[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    constexpr size_t smA = adj_cell_smem<T>();
     constexpr size_t smB = FaceAdjSmem<T, ATX, ATY>::bytes;
     if (dev >= 0 && dev < 64 && !attr[dev]) {
-        if (cudaFuncSetAttribute(adj_cell_kernel<T, ATX, ATY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB) !=
-                cudaSuccess)
+        if (cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB) !=
+            cudaSuccess)
             return -1;
         attr[dev] = true;
     }
     const dim3 grid((q.f.nx + ATX - 1) / ATX, (q.f.ny + ATY - 1) / ATY);
-    adj_cell_kernel<T, ATX, ATY><<<grid, ATX * ATY, smA, st>>>(q);
+    adj_cell_kernel<T><<<dim3((q.f.nx + 31) / 32, (q.f.ny + 7) / 8), 256, 0, st>>>(q);
     adj_face_kernel<T, ATX, ATY><<<grid, ATX * ATY, smB, st>>>(q);
-    adj_fold_kernel<T><<<(q.f.nx + q.f.ny + 127) / 128, 128, 0, st>>>(q);
+    const int nfold = 6 * (2 * q.f.nx + 2 * q.f.ny);
+    adj_fold_kernel<T><<<(nfold + 255) / 256, 256, 0, st>>>(q);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -130,11 +123,13 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     const size_t sb = (s->prec == MOSES_FP32 ? 8 : 6) * (size_t)plane * sizeof(T);  // a full state buffer
     const size_t lb = 6 * (size_t)plane * sizeof(T);
     const int nck = (nsteps + C - 1) / C;
-    DevBuf dts_d, ck, seg, lam, lam_half, lamA, lamB, lpre, ldp, lacc, gpar, loss_d, tgt, phi_d, hbuf;
+    const size_t rb = 6 * (size_t)plane * sizeof(T);  // one stage's record
+    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, lacc, gpar, loss_d, tgt, phi_d, hbuf;
     CK(cudaMalloc(&dts_d.p, 2 * sizeof(double) * nsteps));
     CK(cudaMalloc(&ck.p, sb * nck));
     CK(cudaMalloc(&seg.p, sb * (2 * C + 1)));
-    for (DevBuf *b : {&lam, &lam_half, &lamA, &lamB, &lpre, &lacc}) {
+    CK(cudaMalloc(&recb.p, rb * 2 * C));
+    for (DevBuf *b : {&lam, &lamA, &lpre, &lacc}) {
         CK(cudaMalloc(&b->p, lb));
         CK(cudaMemsetAsync(b->p, 0, lb, st));
     }
@@ -150,9 +145,10 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
         CK(cudaMalloc(&phi_d.p, sizeof(double) * n));
         CK(cudaMemcpyAsync(phi_d.p, release_phi, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     }
-    char *ckp = (char *)ck.p, *segp = (char *)seg.p;
-    auto segU = [&](int q) { return (void *)(segp + sb * q); };          // U^{start+q}, q = 0..C
-    auto segS = [&](int q) { return (void *)(segp + sb * (C + 1 + q)); };  // U* of step start+q
+    char *ckp = (char *)ck.p, *segp = (char *)seg.p, *recp = (char *)recb.p;
+    auto segU = [&](int q) { return (T *)(segp + sb * q); };            // U^{start+q}, q = 0..C
+    auto segS = [&](int q) { return (T *)(segp + sb * (C + 1 + q)); };  // U* of step start+q
+    auto rec = [&](int q, int stage) { return (T *)(recp + rb * (2 * q + stage - 1)); };
 
     cudaEvent_t ev[4];
     for (int q = 0; q < 4; q++) CK(cudaEventCreate(&ev[q]));
@@ -185,9 +181,6 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     CK(cudaGetLastError());
     Ctl ctl_end;
     CK(cudaMemcpyAsync(&ctl_end, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    DevBuf fin;
-    CK(cudaMalloc(&fin.p, sb));
-    CK(cudaMemcpyAsync(fin.p, s->U, sb, cudaMemcpyDeviceToDevice, st));
     misfit_kernel<T><<<grid_for(n), 256, 0, st>>>((const T *)s->U, rem<T>(s, s->U), (const T *)s->geo,
                                                    (const double *)tgt.p, nx, ny, pitch, plane, s->dx * s->dy,
                                                    (T *)lam.p, (double *)loss_d.p);
@@ -202,36 +195,51 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     q.lam_dp = (T *)ldp.p;
     q.lam_acc = (T *)lacc.p;
     q.g_param = (double *)gpar.p;
+    q.lam_next = (const T *)lam.p;
     for (int kseg = nck - 1; kseg >= 0; kseg--) {
         const int start = kseg * C, end = std::min(start + C, nsteps);
-        CK(cudaMemcpyAsync(s->U, ckp + sb * kseg, sb, cudaMemcpyDeviceToDevice, st));
+        // recompute the segment into its buffers, recording each stage
+        CK(cudaMemcpyAsync(segU(0), ckp + sb * kseg, sb, cudaMemcpyDeviceToDevice, st));
         for (int k = start; k < end; k++) {
-            CK(cudaMemcpyAsync(segU(k - start), s->U, sb, cudaMemcpyDeviceToDevice, st));
+            const int m = k - start;
             set_dt_kernel<<<1, 1, 0, st>>>(s->ctl, dts[nsteps + k], dts[k]);
-            if (launch_stage<T>(a1, 0, st)) return fail(s, MOSES_ECUDA, "recompute launch");
-            CK(cudaMemcpyAsync(segS(k - start), s->Us, sb, cudaMemcpyDeviceToDevice, st));
-            if (launch_stage<T>(a2, 0, st)) return fail(s, MOSES_ECUDA, "recompute launch");
+            StageArgs<T> r1 = a1, r2 = a2;
+            r1.Uin = segU(m);
+            r1.Uout = segS(m);
+            r1.Rin = rem<T>(s, segU(m));
+            r1.Rout = rem<T>(s, segS(m));
+            r1.rec = rec(m, 1);
+            r2.Uin = segS(m);
+            r2.Un = segU(m);
+            r2.Uout = segU(m + 1);
+            r2.Rin = rem<T>(s, segS(m));
+            r2.Rn = rem<T>(s, segU(m));
+            r2.Rout = rem<T>(s, segU(m + 1));
+            r2.rec = rec(m, 2);
+            r2.want_amax = 0;
+            if (launch_stage_rec<T>(r1, st) || launch_stage_rec<T>(r2, st))
+                return fail(s, MOSES_ECUDA, "recompute launch");
         }
-        CK(cudaMemcpyAsync(segU(end - start), s->U, sb, cudaMemcpyDeviceToDevice, st));
         for (int k = end - 1; k >= start; k--) {
-            adj_heun_mask_kernel<T><<<grid_for(n), 256, 0, st>>>((const T *)segU(k + 1 - start), (const T *)s->geo,
-                                                                (const T *)lam.p, (T *)lam_half.p, nx, ny, pitch,
-                                                                plane);
-            // stage 2 at U*: lam_out = lam_half -> lamA
+            const int m = k - start;
             q.f = base_args<T>(s);
-            q.f.Uin = (const T *)segS(k - start);
             q.f.debug_stage = 1;
             q.f.dbg_dt = dts[k];
-            q.lam_out = (const T *)lam_half.p;
+            q.U_next = segU(m + 1);
+            // stage 2 at U*: lam_out = the Heun term of lam^{n+1} -> lamA
+            q.f.Uin = segS(m);
+            q.f.rec = rec(m, 2);
+            q.heun = 2;
+            q.lam_out = nullptr;
             q.lam_in = (T *)lamA.p;
             if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
-            // stage 1 at U^n: lam_out = lamA -> lamB
-            q.f.Uin = (const T *)segU(k - start);
+            // stage 1 at U^n: lam_out = lamA; lam^n = its input adjoint + the Heun term, over lam^{n+1}
+            q.f.Uin = segU(m);
+            q.f.rec = rec(m, 1);
+            q.heun = 1;
             q.lam_out = (const T *)lamA.p;
-            q.lam_in = (T *)lamB.p;
+            q.lam_in = (T *)lam.p;
             if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
-            adj_combine_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const T *)lam_half.p, (const T *)lamB.p,
-                                                                  (T *)lam.p, nx, ny, pitch, plane);
         }
     }
     CK(cudaGetLastError());
@@ -254,7 +262,6 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
         CK(cudaMemcpyAsync(g_release_h, gh.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
-    CK(cudaMemcpyAsync(s->U, fin.p, sb, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(s->ctl, &ctl_end, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(ev[3], st));
     CK(cudaStreamSynchronize(st));
@@ -310,12 +317,13 @@ __global__ void unpack_lam_kernel(const double *src, T *lam, int nx, int ny, int
 }
 
 template <typename T>
-int stage_adjoint_impl(moses_sim *s, double dt, const double *lam_out, double *lam_in, double *g_param)
+int stage_adjoint_impl(moses_sim *s, double t, double dt, const double *lam_out, double *lam_in, double *g_param)
 {
     cudaStream_t st = s->stream;
     const long long n = (long long)s->nx * s->ny;
     const size_t lb = 6 * (size_t)s->plane * sizeof(T);
-    DevBuf lo, li, lpre, ldp, lacc, gp, hb;
+    DevBuf lo, li, lpre, ldp, lacc, gp, hb, recb;
+    CK(cudaMalloc(&recb.p, lb));
     CK(cudaMalloc(&lo.p, lb));
     CK(cudaMalloc(&li.p, lb));
     CK(cudaMalloc(&lpre.p, lb));
@@ -329,11 +337,21 @@ int stage_adjoint_impl(moses_sim *s, double dt, const double *lam_out, double *l
     CK(cudaMemcpyAsync(hb.p, lam_out, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
     unpack_lam_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const double *)hb.p, (T *)lo.p, s->nx, s->ny, s->pitch,
                                                           s->plane);
+    // the stage again, recording what the cell adjoint needs (ghosts of U are
+    // those of time t, filled by moses_stage)
+    StageArgs<T> f = base_args<T>(s);
+    f.Uin = (const T *)s->U;
+    f.Uout = (T *)s->Us;
+    f.Rin = rem<T>(s, s->U);
+    f.Rout = rem<T>(s, s->Us);
+    f.stage = 1;
+    f.debug_stage = 1;
+    f.dbg_t = t;
+    f.dbg_dt = dt;
+    f.rec = (T *)recb.p;
+    if (launch_stage_rec<T>(f, st)) return fail(s, MOSES_ECUDA, "recording stage launch");
     AdjArgs<T> q{};
-    q.f = base_args<T>(s);
-    q.f.Uin = (const T *)s->U;
-    q.f.debug_stage = 1;
-    q.f.dbg_dt = dt;
+    q.f = f;
     q.lam_out = (const T *)lo.p;
     q.lam_in = (T *)li.p;
     q.lam_pre = (T *)lpre.p;
@@ -362,12 +380,10 @@ int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out
     if (!(std::isfinite(dt) && dt >= 0)) return fail(s, MOSES_EINVAL, "bad dt");
     // ghosts of the current state at time t, as moses_stage sees them
     double *tmp = nullptr;
-    cudaStream_t st = s->stream;
     CK(cudaMallocHost(&tmp, sizeof(double) * 6 * (size_t)s->nx * s->ny));
     int rc = moses_stage(s, t, dt, tmp);
     cudaFreeHost(tmp);
     if (rc) return rc;
-    (void)st;
-    return s->prec == MOSES_FP64 ? stage_adjoint_impl<double>(s, dt, lam_out, lam_in, g_param)
-                                 : stage_adjoint_impl<float>(s, dt, lam_out, lam_in, g_param);
+    return s->prec == MOSES_FP64 ? stage_adjoint_impl<double>(s, t, dt, lam_out, lam_in, g_param)
+                                 : stage_adjoint_impl<float>(s, t, dt, lam_out, lam_in, g_param);
 }

@@ -11,17 +11,24 @@
 //
 // The adjoint of a stage is computed by three kernels so that every tile
 // gathers (no scatter across tiles):
-//   A  per cell: recompute the forward tile, reverse the masks, the friction,
-//      the sources and the update.  Writes the adjoint of the pre-friction
-//      output lam_pre (6), of the pressure gradient (dP/dxi, dP/deta), the
-//      cell's own contributions lam_acc (identity + sources + friction), and
-//      the parameter partials (tan delta_b, c_D) reduced per CTA.
+//   A  per cell, pointwise: from the stage input, the trial state before
+//      friction and the pressure gradient that the recording forward stage
+//      kept (StageArgs::rec), reverse the masks, the friction, the sources and
+//      the update.  Writes the adjoint of the pre-friction output lam_pre (6),
+//      of the pressure gradient (dP/dxi, dP/deta), the cell's own
+//      contributions lam_acc (identity + sources + friction), and the
+//      parameter partials (tan delta_b, c_D) reduced per CTA.
 //   B  per face: recompute the face states (halo 3), form the flux adjoints
 //      from lam_pre and the pressure adjoints of the two neighbours, reverse
 //      the central flux and the minmod reconstruction, and gather per cell:
 //      lam_in = lam_acc + face terms, also for ghost cells at the boundary.
 //   C  fold the ghost cells' adjoints into their mirror / copy sources
 //      (inflow ghosts are constants).
+// Heun: U^{n+1} = dry(1/2 (U^n + S(S(U^n)))).  With lam^{n+1} given, the
+// second stage's A takes lam_out = 1/2 lam^{n+1} with the momenta zeroed where
+// U^{n+1} is dry, and the first stage's B adds that same term to its cell
+// result, writing lam^n over lam^{n+1} in place (each cell reads its own
+// value before it writes it; no other thread reads it).
 #pragma once
 #include "stage.cuh"
 
@@ -119,117 +126,60 @@ __device__ __forceinline__ int minmod_sel(float a, float b)
 // Arguments of the adjoint kernels
 template <typename T>
 struct AdjArgs {
-    StageArgs<T> f;   // the forward stage (Uin = the stage input; geometry, constants)
-    const T *lam_out; // adjoint of the stage output (6 planes, interior)
+    StageArgs<T> f;   // the forward stage (Uin = the stage input, rec = its record; geometry, constants)
+    const T *lam_out; // adjoint of the stage output (6 planes, interior); unused when heun == 2
     T *lam_pre;       // A -> B: adjoint of the pre-friction output (6 planes)
     T *lam_dp;        // A -> B: adjoint of dP/dxi, dP/deta (2 planes)
     T *lam_acc;       // A -> B: the cell's own contributions (6 planes)
     T *lam_in;        // B: adjoint of the stage input (6 planes, ghosts included)
     double *g_param;  // [0] d/d tan(delta_b), [1] d/d c_D (FP64 accumulators)
+    // Heun: 2 = second stage (A reads lam_next), 1 = first stage (B adds the
+    // direct term; lam_in == lam_next), 0 = a lone stage
+    int heun;
+    const T *lam_next;  // lam^{n+1} (6 planes, interior)
+    const T *U_next;    // U^{n+1} (its dry mask)
 };
+
+// 1/2 lam^{n+1}, momenta zeroed where U^{n+1} is dry (adjoint of the Heun
+// average followed by the dry rule), component c of cell g
+template <typename T>
+__device__ __forceinline__ T heun_half(const AdjArgs<T> &q, long long g, int c, T jhd)
+{
+    const long long plane = q.f.plane;
+    const int ph = c / 3;
+    if (c != 3 * ph && !gtp(q.U_next[3 * ph * plane + g], jhd)) return T(0);
+    return T(0.5) * q.lam_next[c * plane + g];
+}
 
 }  // namespace moses
 
 namespace moses {
 
-// ---- kernel A: cell adjoint ------------------------------------------------
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_cell_kernel(const AdjArgs<T> q)
+// ---- kernel A: cell adjoint (pointwise) --------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
 {
-    constexpr int NT = TX * TY;
-    constexpr int SW = TX + 4, SH = TY + 4, SP = SW * SH;
-    constexpr int NSX = (TX + 2) * TY, NSY = TX * (TY + 2);
-    constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sU = reinterpret_cast<T *>(smem_raw);
-    T *sSx = sU + 6 * SP;
-    T *sSy = sSx + 6 * NSX;
-    T *sHx = sSy + 6 * NSY;
-    T *sHy = sHx + 7 * NXF;
+    constexpr int NT = 256;
     __shared__ double red[2][NT / 32];
-
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int i = blockIdx.x * 32 + (tid & 31), j = blockIdx.y * 8 + (tid >> 5);
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
     const KT<T> &k = a.k;
     const T *geo = a.geo;
     const double dt = a.dbg_dt;
     const T dtT = (T)dt;
-
-    for (int e = tid; e < 6 * SP; e += NT) {
-        const int c = e / SP, r = e - c * SP;
-        const int ly = r / SW, lx = r - ly * SW;
-        const int gi = x0 - 2 + lx, gj = y0 - 2 + ly;
-        T v = T(0);
-        if (gi < nx + 2 && gj < ny + 2) v = a.Uin[c * plane + cell_index(gi, gj, pitch)];
-        sU[e] = v;
-    }
-    __syncthreads();
-    for (int e = tid; e < 6 * NSX; e += NT) {
-        const int c = e / NSX, r = e - c * NSX;
-        const int ly = r / (TX + 2), lx = r - ly * (TX + 2);
-        const T *p = sU + c * SP + (ly + 2) * SW + lx + 1;
-        sSx[e] = minmod(p[0] - p[-1], p[1] - p[0]);
-    }
-    for (int e = tid; e < 6 * NSY; e += NT) {
-        const int c = e / NSY, r = e - c * NSY;
-        const int ly = r / TX, lx = r - ly * TX;
-        const T *p = sU + c * SP + (ly + 1) * SW + lx + 2;
-        sSy[e] = minmod(p[0] - p[-SW], p[SW] - p[0]);
-    }
-    __syncthreads();
-    for (int f = tid; f < NXF; f += NT) {
-        const int ly = f / (TX + 1), lx = f - ly * (TX + 1);
-        const int i = x0 + lx - 1, j = y0 + ly;
-        if (j >= ny || i >= nx) continue;
-        const long long g = cell_index(i, j, pitch);
-        const FaceGeo<T> G{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
-                           geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
-                           geo[GX_HG * plane + g]};
-        const int ou = (ly + 2) * SW + lx + 1, os = ly * (TX + 2) + lx;
-        T um[6], up[6], H[7];
-#pragma unroll
-        for (int c = 0; c < 6; c++) {
-            um[c] = fma(T(0.5), sSx[c * NSX + os], sU[c * SP + ou]);
-            up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
-        }
-        face_flux2<T, 0>(um, up, G, H);
-#pragma unroll
-        for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
-    }
-    for (int f = tid; f < NYF; f += NT) {
-        const int ly = f / TX, lx = f - ly * TX;
-        const int i = x0 + lx, j = y0 + ly - 1;
-        if (i >= nx || j >= ny) continue;
-        const long long g = cell_index(i, j, pitch);
-        const FaceGeo<T> G{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
-                           geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
-                           geo[GY_HG * plane + g]};
-        const int ou = (ly + 1) * SW + lx + 2, os = ly * TX + lx;
-        T um[6], up[6], H[7];
-#pragma unroll
-        for (int c = 0; c < 6; c++) {
-            um[c] = fma(T(0.5), sSy[c * NSY + os], sU[c * SP + ou]);
-            up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
-        }
-        face_flux2<T, 1>(um, up, G, H);
-#pragma unroll
-        for (int c = 0; c < 7; c++) sHy[c * NYF + f] = H[c];
-    }
-    __syncthreads();
-
-    const int lx = tid % TX, ly = tid / TX;
-    const int i = x0 + lx, j = y0 + ly;
     double g_tan = 0.0, g_cd = 0.0;
     if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
-        const int os = (ly + 2) * SW + lx + 2;
-        T u[6];
+        T u[6], pre4[4];
 #pragma unroll
-        for (int c = 0; c < 6; c++) u[c] = sU[c * SP + os];
-        // ---- forward (as in stage_tile) ----
+        for (int c = 0; c < 6; c++) u[c] = a.Uin[c * plane + g];
+#pragma unroll
+        for (int c = 0; c < 4; c++) pre4[c] = a.rec[c * plane + g];
+        const T dPx = a.rec[4 * plane + g], dPy = a.rec[5 * plane + g];
+        // ---- forward quantities of the cell (as in stage_tile) ----
         const T jhd = geo[GC_JHD * plane + g];
         const T Ut = u[0] + u[3];
         const bool wmix = gtp(Ut, jhd), ws = gtp(u[0], jhd), wf = gtp(u[3], jhd);
@@ -242,12 +192,9 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_cell_kernel(const
         const T nkf = fma(kXX, vXf * vXf, fma(kXY2, vXf * vYf, kYY * (vYf * vYf)));
         const T gc1 = geo[GC_GC1 * plane + g], gcf = geo[GC_GCF * plane + g];
         const T ps_raw = u[0] * fma(k.eps_chi, nks, gc1), pf_raw = u[3] * fma(k.eps_chi, nkf, gcf);
-        const T Jpbs = pos(ps_raw), Jpbf = pos(pf_raw);
+        const T Jpbs = pos(ps_raw);
         const T nX = geo[GC_MNX * plane + g], nY = geo[GC_MNY * plane + g];
         const T bX = geo[GC_BX * plane + g], bY = geo[GC_BY * plane + g];
-        const int fx = ly * (TX + 1) + lx, fy = ly * TX + lx;
-        const T dPx = (sHx[6 * NXF + fx + 1] - sHx[6 * NXF + fx]) * k.hinv_dx;
-        const T dPy = (sHy[6 * NYF + fy + TX] - sHy[6 * NYF + fy]) * k.hinv_dy;
         const T A11 = geo[GC_A11 * plane + g], A12 = geo[GC_A12 * plane + g], A22 = geo[GC_A22 * plane + g];
         const T gX = fma(A11, dPx, A12 * dPy), gY = fma(A12, dPx, A22 * dPy);
         const bool pgf = a.ph.pg_mode == 1;
@@ -257,50 +204,28 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_cell_kernel(const
         const T aD = k.alpha * D;
         const T dvX = vXf - vXs, dvY = vYf - vYs;
         const T ff = k.k_f * phf * Ut;
-        T S[6];
-        S[0] = T(0);
-        S[3] = T(0);
-        S[1] = fma(Jpbs, nX, fma(bs, gX, aD * dvX));
-        S[2] = fma(Jpbs, nY, fma(bs, gY, aD * dvY));
-        S[4] = fma(Jpbf, nX, fma(bf, gX, -fma(D, dvX, ff * vXf)));
-        S[5] = fma(Jpbf, nY, fma(bf, gY, -fma(D, dvY, ff * vYf)));
-        T pre[6];
-#pragma unroll
-        for (int c = 0; c < 6; c++) {
-            const T dx2 = sHx[c * NXF + fx + 1] - sHx[c * NXF + fx];
-            const T dy2 = sHy[c * NYF + fy + TX] - sHy[c * NYF + fy];
-            const T div = fma(dx2, k.hinv_dx, dy2 * k.hinv_dy);
-            pre[c] = fma(dtT, S[c] - div, u[c]);
-        }
-        // friction forward quantities
+        // friction on the recorded trial momentum
         const T Fr = dtT * Jpbs * k.tan_delta;
-        const T q1 = pre[1], q2 = pre[2];
+        const T q1 = pre4[1], q2 = pre4[2];
         const T qZ = fma(bX, q1, bY * q2);
         const T qn2 = fma(q1, q1, fma(q2, q2, qZ * qZ));
         bool stopped;  // the forward's decision (FP32: with its FP64 tie-break)
-        if constexpr (sizeof(T) == 4) {
-            const float F2 = Fr * Fr;
-            if (qn2 > F2 * (1.0f + 0x1p-10f)) stopped = false;
-            else if (qn2 < F2 * (1.0f - 0x1p-10f)) stopped = true;
-            else stopped = stop_fp64(q1, q2, bX, bY, dt, Jpbs, k.tan_delta_d);
-        } else {
-            stopped = !gtp(qn2, Fr * Fr);
-        }
-        const bool rubs = !stopped && ibits(Fr) > 0;  // friction acts (and q* is not subnormal)
+        if constexpr (sizeof(T) == 4) stopped = coulomb_stops(q1, q2, bX, bY, Fr, qn2, dt, Jpbs, k.tan_delta_d);
+        else stopped = !gtp(qn2, Fr * Fr);
+        const bool rubs = !stopped && ibits(Fr) > 0;  // friction acts
         const T rr = rubs ? frsqrt(qn2) : T(0);
         const T r = rubs ? fma(-Fr, rr, T(1)) : T(1);
-        T post[6] = {pre[0], stopped ? T(0) : q1 * r, stopped ? T(0) : q2 * r, pre[3], pre[4], pre[5]};
         bool clamped[2], dry[2];
 #pragma unroll
         for (int ph = 0; ph < 2; ph++) {
-            clamped[ph] = negative(post[3 * ph]);
-            const T m = clamped[ph] ? T(0) : post[3 * ph];
+            clamped[ph] = negative(pre4[3 * ph]);
+            const T m = clamped[ph] ? T(0) : pre4[3 * ph];
             dry[ph] = !gtp(m, jhd);
         }
         // ---- reverse ----
         T lo[6];
 #pragma unroll
-        for (int c = 0; c < 6; c++) lo[c] = q.lam_out[c * plane + g];
+        for (int c = 0; c < 6; c++) lo[c] = q.heun == 2 ? heun_half(q, g, c, jhd) : q.lam_out[c * plane + g];
         // clamp and dry rule
 #pragma unroll
         for (int ph = 0; ph < 2; ph++) {
@@ -318,30 +243,29 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_cell_kernel(const
             lpre[2] = lo[2];
         }
         if (rubs) {
-            const T s = lo[1] * q1 + lo[2] * q2;
-            const T t = ((s * rr) * rr) * (Fr * rr);  // s rr <= |lo|: no overflow for tiny |q*|
+            const T sq = lo[1] * q1 + lo[2] * q2;
+            const T t = ((sq * rr) * rr) * (Fr * rr);  // sq rr <= |lo|: no overflow for tiny |q*|
             lpre[1] = fma(r, lo[1], t * fma(qZ, bX, q1));
             lpre[2] = fma(r, lo[2], t * fma(qZ, bY, q2));
-            lFr = -s * rr;
+            lFr = -sq * rr;
         }
         T lJpbs = lFr * dtT * k.tan_delta;
         g_tan += (double)(lFr * dtT * Jpbs);
         // update pre = u + dt (S - div): identity, sources; div goes to faces via lam_pre
-        T lu[6];
+        T lu[6], lS[6];
 #pragma unroll
-        for (int c = 0; c < 6; c++) lu[c] = lpre[c];
-        T lS[6];
-#pragma unroll
-        for (int c = 0; c < 6; c++) lS[c] = dtT * lpre[c];
-        // sources
+        for (int c = 0; c < 6; c++) {
+            lu[c] = lpre[c];
+            lS[c] = dtT * lpre[c];
+        }
         lJpbs += lS[1] * nX + lS[2] * nY;
-        T lJpbf = lS[4] * nX + lS[5] * nY;
+        const T lJpbf = lS[4] * nX + lS[5] * nY;
         const T lbs = lS[1] * gX + lS[2] * gY;
         const T lbf = lS[4] * gX + lS[5] * gY;
         const T lgX = lS[1] * bs + lS[4] * bf, lgY = lS[2] * bs + lS[5] * bf;
         const T laD = lS[1] * dvX + lS[2] * dvY;
-        T lD = -(lS[4] * dvX + lS[5] * dvY) + laD * k.alpha;
-        T ldvX = lS[1] * aD - lS[4] * D, ldvY = lS[2] * aD - lS[5] * D;
+        const T lD = -(lS[4] * dvX + lS[5] * dvY) + laD * k.alpha;
+        const T ldvX = lS[1] * aD - lS[4] * D, ldvY = lS[2] * aD - lS[5] * D;
         const T lff = -(lS[4] * vXf + lS[5] * vYf);
         T lvXf = -lS[4] * ff + ldvX, lvYf = -lS[5] * ff + ldvY;
         T lvXs = -ldvX, lvYs = -ldvY;
@@ -565,8 +489,9 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
     __syncthreads();
 }
 
+// FP32: three 256-thread CTAs per SM (80 registers); FP64: shared memory allows two
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_face_kernel(const AdjArgs<T> q)
+__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY)) adj_face_kernel(const AdjArgs<T> q)
 {
     using SM = FaceAdjSmem<T, TX, TY>;
     constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3;
@@ -599,84 +524,58 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) adj_face_kernel(const
     const int i = x0 + tid % TX, j = y0 + tid / TX;
     if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
+        const T jhd = q.heun == 1 ? a.geo[GC_JHD * plane + g] : T(0);
 #pragma unroll
-        for (int c = 0; c < 6; c++) q.lam_in[c * plane + g] = q.lam_acc[c * plane + g] + lres[c];
+        for (int c = 0; c < 6; c++) {
+            T v = q.lam_acc[c * plane + g] + lres[c];
+            if (q.heun == 1) v += heun_half(q, g, c, jhd);
+            q.lam_in[c * plane + g] = v;
+        }
     }
 }
 
 // ---- kernel C: fold the ghost adjoints into their sources ----------------------
+// one thread per (component, side, line along the side)
 template <typename T>
 __global__ void adj_fold_kernel(const AdjArgs<T> q)
 {
     const StageArgs<T> &a = q.f;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
+    const int per_c = 2 * ny + 2 * nx;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool xs = e < ny;  // W/E sides for row e, else S/N sides for column e - ny
-    const int line = xs ? e : e - ny;
-    if (line >= (xs ? ny : nx)) return;
-    for (int side = xs ? 0 : 2; side < (xs ? 2 : 4); side++) {
-        bool inflow = false;
-        for (int f = 0; f < a.n_inflow; f++)
-            if (a.inflow[f].side == side && line >= a.inflow[f].i0 && line < a.inflow[f].i1) inflow = true;
-        if (inflow) continue;  // ghost state is a given function of time
-        const bool closed = a.ph.bc[side] == 0;
-        const int nn = xs ? nx : ny;
-        for (int kk = 0; kk < GH; kk++) {
-            int gpos, src;
-            if (side == 0 || side == 2) {
-                gpos = -1 - kk;
-                src = closed ? (kk < nn ? kk : nn - 1) : 0;
-            } else {
-                gpos = nn + kk;
-                src = closed ? (nn - 1 - kk >= 0 ? nn - 1 - kk : 0) : nn - 1;
-            }
-            const long long gg = xs ? cell_index(gpos, line, pitch) : cell_index(line, gpos, pitch);
-            const long long gs = xs ? cell_index(src, line, pitch) : cell_index(line, src, pitch);
-#pragma unroll
-            for (int c = 0; c < 6; c++) {
-                T v = q.lam_in[c * plane + gg];
-                if (closed && ((xs && (c == 1 || c == 4)) || (!xs && (c == 2 || c == 5)))) v = -v;
-                atomicAdd(&q.lam_in[c * plane + gs], v);
-            }
-        }
+    if (e >= 6 * per_c) return;
+    const int c = e / per_c;
+    int r = e - c * per_c;
+    int side, line;
+    if (r < 2 * ny) {
+        side = r / ny;  // W, E
+        line = r - side * ny;
+    } else {
+        r -= 2 * ny;
+        side = 2 + r / nx;  // S, N
+        line = r - (side - 2) * nx;
     }
-}
-
-// ---- step-level helpers -------------------------------------------------------
-// lam_half = 1/2 lam^{n+1} with the momenta zeroed where U^{n+1} is dry
-// (adjoint of the Heun average followed by the dry rule)
-template <typename T>
-__global__ void adj_heun_mask_kernel(const T *Unext, const T *geo, const T *lam_next, T *lam_half, int nx, int ny,
-                                     int pitch, long long plane)
-{
-    const long long n = (long long)nx * ny;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
-        const long long g = cell_index(i, j, pitch);
-        const T jhd = geo[GC_JHD * plane + g];
-#pragma unroll
-        for (int ph = 0; ph < 2; ph++) {
-            const bool dry = !gtp(Unext[3 * ph * plane + g], jhd);
-#pragma unroll
-            for (int c = 3 * ph; c < 3 * ph + 3; c++)
-                lam_half[c * plane + g] = (dry && c != 3 * ph) ? T(0) : T(0.5) * lam_next[c * plane + g];
+    const bool xs = side < 2;
+    for (int f = 0; f < a.n_inflow; f++)
+        if (a.inflow[f].side == side && line >= a.inflow[f].i0 && line < a.inflow[f].i1)
+            return;  // ghost state is a given function of time
+    const bool closed = a.ph.bc[side] == 0;
+    const bool flip = closed && (xs ? (c == 1 || c == 4) : (c == 2 || c == 5));
+    const int nn = xs ? nx : ny;
+    for (int kk = 0; kk < GH; kk++) {
+        int gpos, src;
+        if (side == 0 || side == 2) {
+            gpos = -1 - kk;
+            src = closed ? (kk < nn ? kk : nn - 1) : 0;
+        } else {
+            gpos = nn + kk;
+            src = closed ? (nn - 1 - kk >= 0 ? nn - 1 - kk : 0) : nn - 1;
         }
-    }
-}
-
-// lam^n = lam_half + lam_stage1 (interior)
-template <typename T>
-__global__ void adj_combine_kernel(const T *lam_half, const T *lam_stage, T *lam_n, int nx, int ny, int pitch,
-                                   long long plane)
-{
-    const long long n = (long long)nx * ny;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < 6 * n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e / n);
-        const long long r = e - c * n;
-        const int j = (int)(r / nx), i = (int)(r - (long long)j * nx);
-        const long long g = c * plane + cell_index(i, j, pitch);
-        lam_n[g] = lam_half[g] + lam_stage[g];
+        const long long gg = xs ? cell_index(gpos, line, pitch) : cell_index(line, gpos, pitch);
+        const long long gs = xs ? cell_index(src, line, pitch) : cell_index(line, src, pitch);
+        const T v = q.lam_in[c * plane + gg];
+        if (v != T(0)) atomicAdd(&q.lam_in[c * plane + gs], flip ? -v : v);
     }
 }
 

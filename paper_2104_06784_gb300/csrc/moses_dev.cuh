@@ -149,6 +149,10 @@ struct alignas(8) StageArgs {
     int want_amax;     // stage 2: reduce a_max of U^{n+1}
     int debug_stage;   // 1: single stage to Uout with a given dt (no Heun)
     double dbg_t, dbg_dt;
+    // recording form only (the adjoint's recompute): per interior cell the
+    // trial masses and solid momenta before friction and the clamp, and the
+    // gradient of P (6 planes: U1*, U2*, U3*, U4*, dP/dxi, dP/deta)
+    T *rec;
 };
 
 __host__ __device__ inline long long cell_index(int i, int j, int pitch)
@@ -163,6 +167,9 @@ namespace moses {
 struct BatchTile;
 template <typename T>
 int launch_stage(const StageArgs<T> &a, int tile, void *stream);
+// the same stage (tile 32 x 8) that also writes a.rec
+template <typename T>
+int launch_stage_rec(const StageArgs<T> &a, void *stream);
 // batched stage over a work list of `ntiles` tiles (tile shape 32 x 8)
 template <typename T>
 int launch_stage_batch(const StageArgs<T> *args_device, const BatchTile *tiles_device, int ntiles, void *stream);

@@ -388,16 +388,24 @@ static __device__ __noinline__ bool stop_fp64(float q1, float q2, float bX, floa
     return !(dq1 * dq1 + dq2 * dq2 + dZ * dZ > Frd * Frd);
 }
 
+// The FP32 form's stopping decision.  |q*|^2 that underflowed to 0 stops the
+// cell: only a cell with a vanishing basal pressure (a dry one) can get there
+// with F^2 > 0 in FP64, and the dry rule zeroes its momentum anyway.
+__device__ __forceinline__ bool coulomb_stops(float q1, float q2, float bX, float bY, float Fr, float qn2, double dt,
+                                              float Jpbs, double tan_d)
+{
+    const float F2 = Fr * Fr;
+    if (qn2 > F2 * (1.0f + 0x1p-10f)) return false;
+    if (qn2 < F2 * (1.0f - 0x1p-10f) || ibits(qn2) == 0) return true;
+    return stop_fp64(q1, q2, bX, bY, dt, Jpbs, tan_d);
+}
+
 __device__ __forceinline__ void coulomb(float &q1, float &q2, float bX, float bY, float Fr, double dt,
                                         float Jpbs, double tan_d)
 {
     const float qZ = fmaf(bX, q1, bY * q2);
     const float qn2 = fmaf(q1, q1, fmaf(q2, q2, qZ * qZ));
-    const float F2 = Fr * Fr;
-    bool stop;
-    if (qn2 > F2 * (1.0f + 0x1p-10f)) stop = false;
-    else if (qn2 < F2 * (1.0f - 0x1p-10f)) stop = true;
-    else stop = stop_fp64(q1, q2, bX, bY, dt, Jpbs, tan_d);
+    const bool stop = coulomb_stops(q1, q2, bX, bY, Fr, qn2, dt, Jpbs, tan_d);
     if (stop) {
         q1 = 0.0f;
         q2 = 0.0f;
@@ -417,7 +425,7 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
 // ---- the stage kernel -------------------------------------------------------------
 // One stage on the tile (bx, by) of the simulation described by `a`; nb is the
 // number of CTAs working on that simulation in this launch (for the ticket).
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool REC = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
     constexpr int NT = TX * TY;
@@ -632,6 +640,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             const T div = fma(dx2, k.hinv_dx, dy2 * k.hinv_dy);
             out[c] = fma(dtT, S[c] - div, u[c]);
         }
+        if constexpr (REC) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) a.rec[c * plane + g] = out[c];
+            a.rec[4 * plane + g] = dPx;
+            a.rec[5 * plane + g] = dPy;
+        }
         if constexpr (sizeof(T) == 8)
             coulomb(out[1], out[2], geo[GC_BX * plane + g], geo[GC_BY * plane + g], dt * Jpbs * k.tan_delta);
         else
@@ -735,10 +749,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool REC = false>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
 {
-    stage_tile<T, TX, TY>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+    stage_tile<T, TX, TY, REC>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // Ensemble form: one launch runs the same stage of many simulations.  Each CTA

@@ -6,7 +6,7 @@
 namespace moses {
 namespace {
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool REC = false>
 int launch_tile(const StageArgs<T> &a, cudaStream_t st)
 {
     constexpr size_t smem = stage_smem_bytes<T, TX, TY>();
@@ -14,13 +14,13 @@ int launch_tile(const StageArgs<T> &a, cudaStream_t st)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
             return -1;
         attr_set[dev] = true;
     }
     const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-    stage_kernel<T, TX, TY><<<grid, TX * TY, smem, st>>>(a);
+    stage_kernel<T, TX, TY, REC><<<grid, TX * TY, smem, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -36,6 +36,13 @@ int launch_stage<float>(const StageArgs<float> &a, int tile, void *stream)
     case 2: return launch_tile<float, 32, 16>(a, st);
     default: return launch_tile<float, 32, 8>(a, st);
     }
+}
+
+template <>
+int launch_stage_rec<float>(const StageArgs<float> &a, void *stream)
+{
+    if (!a.rec) return -1;
+    return launch_tile<float, 32, 8, true>(a, (cudaStream_t)stream);
 }
 
 template <>

@@ -243,6 +243,19 @@ def large_release_config(n: int = 4096, dx: float = 10.0, seed: int = 0, ny: int
                 phi_s=phi, steps=10000, release_cell=(int(ic), int(jc)))
 
 
+def adjoint_config(n: int = 1024, dx: float = 5.0, seed: int = 0, **over) -> dict:
+    """Calibration workload: the large-release terrain at n x n cells of dx
+    (spectral DEM, relief 1500 m x n / 4096, one carved valley) with a
+    1e6 m^3 parabolic-cap release of radius 43 cells on a 30-40 deg slope;
+    FP32 state; 5000 steps with a checkpoint every 71; the target deposit comes
+    from the hidden basal friction 22 deg and drag 3e-3 1/s, the start is
+    25 deg and 1e-3 1/s."""
+    cfg = large_release_config(n=n, dx=dx, seed=seed, volume=1e6, radius_cells=43.0, **over)
+    cfg.update(name=f"adjoint calibration {n}x{n} dx={dx} m", steps=5000, ckpt_every=71, precision="fp32",
+               hidden=dict(delta_b_deg=22.0, c_d=3e-3))
+    return cfg
+
+
 def inflow_config(nx: int = 2048, ny: int = 1024, dx: float = 5.0, inlet_cells: int = 20, **over) -> dict:
     """Channel-and-fan DEM with a triangular hydrograph (peak 800 m^3/s at
     60 s, zero by 300 s, solid fraction 0.5) at an inlet of `inlet_cells`
