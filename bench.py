@@ -228,6 +228,51 @@ def measure_ensemble(K, Wm, seed=0, n=256):
                       "spectral DEMs, delta_b U(15,30) deg, c_D U(1e-4,1e-2) 1/s, release U(1e4,1e6) m^3, FP32"}
 
 
+def measure_adjoint(torch, n=1024):
+    """Adjoint calibration workload, FP32 forward: 1024 x 1024 cells at 5 m,
+    spectral DEM, 5000 steps with a checkpoint every 71.  The target deposit
+    comes from a forward run with the hidden basal friction 22 deg and drag
+    3e-3 1/s; the gradient of the deposit misfit at 25 deg, 1e-3 1/s is taken
+    with respect to delta_b, phi_int, c_D and the release thickness.  Times:
+    the forward run alone (CUDA events), then the forward run with
+    checkpoints and the backward pass (recompute + reverse sweep) of
+    moses_adjoint_misfit (CUDA events inside the library)."""
+    from paper_2104_06784_gb300 import moses, workloads as W
+    cfg = W.adjoint_config(n=n)
+    N, C = cfg["steps"], cfg["ckpt_every"]
+    ct = dict(cfg)
+    ct["params"] = dict(cfg["params"], **cfg["hidden"])
+    with moses.from_config(ct, precision=moses.FP32) as gt:
+        gt.step(N)
+        st = gt.get_state()
+    hs_t = st["h"] * st["phi_s"]
+    with moses.from_config(cfg, precision=moses.FP32) as f:
+        f.step(3)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f.step(N)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1)
+    with moses.from_config(cfg, precision=moses.FP32) as g:
+        r = g.adjoint_misfit(N, hs_t, ckpt_every=C, release_phi=cfg["phi_s"])
+    tf, tb = (float(x) for x in r["timing_ms"])
+    gh = r["g_release_h"]
+    return {"config": f"adjoint calibration, {n}x{n} cells at 5 m, spectral DEM, 1e6 m^3 release, FP32 forward, "
+                      f"{N} steps, checkpoint every {C}; target from delta_b 22 deg, c_D 3e-3",
+            "steps": N, "ckpt_every": C, "dtype": "f32", "forward_ms": fwd_ms,
+            "adjoint_forward_ms": tf, "adjoint_backward_ms": tb,
+            "backward_over_forward": tb / fwd_ms, "total_over_forward": (tf + tb) / fwd_ms,
+            "loss": r["loss"],
+            "grad": {"delta_b_per_deg": float(r["g_params"][0]), "phi_int_per_deg": float(r["g_params"][1]),
+                     "c_d": float(r["g_params"][2]), "release_h_l2": float(np.sqrt((gh * gh).sum()))},
+            # forward: 2 stages + 2 records per step, misfit; backward: per step 1 time reset,
+            # 2 recording stages, 2 x (cell, face, fold); release gradient
+            "gpu_launches": 4 * N + 1 + 9 * N + 1}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,6 +282,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (the workload is defined at 4096)")
     ap.add_argument("--only", choices=["f64", "f32"], default=None, help="measure one precision form")
     args = ap.parse_args()
@@ -349,6 +395,8 @@ def main():
     if ens is not None and world > 1:
         ens["value"] = world * ens["value"]
 
+    adj = None if args.no_adjoint else measure_adjoint(torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg)
@@ -363,6 +411,7 @@ def main():
         "f32": {"value": world * cells * K / (f32["ms"] / 1e3), "ms_per_step": f32["ms"] / K, "dtype": "f32",
                 "roofline": roof32, "gpu_launches": 2 * K},
         "ensemble": ens,
+        "adjoint": adj,
         "stage_ms": {"f64": f64["stage_ms"], "f32": f32["stage_ms"]},
         "stage_source": h,
     }

@@ -28,8 +28,11 @@ int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
     cudaGetDevice(&dev);
     constexpr size_t smB = FaceAdjSmem<T, ATX, ATY>::bytes;
     if (dev >= 0 && dev < 64 && !attr[dev]) {
+        // the largest shared-memory carve-out, so that three FP32 CTAs fit on an SM
         if (cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB) !=
-            cudaSuccess)
+                cudaSuccess ||
+            cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return -1;
         attr[dev] = true;
     }

@@ -347,21 +347,29 @@ namespace moses {
 // D = 0: x-faces over rows of the tile; D = 1: y-faces over columns.  Along the
 // face normal the tile covers cells [o0 - 2, o0 + L + 1] with slopes, faces with
 // lower cell in [o0 - 2, o0 + L], slope adjoints for cells [o0 - 1, o0 + L].
+// In the FP32 form the face geometry (per direction) and the cell adjoints
+// lam_pre, lam_dp of the tile and a 2-cell halo are staged in shared memory
+// up front, so that the face loop reads no global memory; FP64 reads them in
+// the loop (its shared memory is full at two CTAs per SM).
 template <typename T, int TX, int TY>
 struct FaceAdjSmem {
+    static constexpr bool STAGE = sizeof(T) == 4;
     static constexpr int SW3 = TX + 6, SH3 = TY + 6, SP3 = SW3 * SH3;
     static constexpr int NS = (TY * (TX + 4) > (TY + 4) * TX) ? TY * (TX + 4) : (TY + 4) * TX;
     static constexpr int NF = (TY * (TX + 3) > (TY + 3) * TX) ? TY * (TX + 3) : (TY + 3) * TX;
     static constexpr int NL = (TY * (TX + 2) > (TY + 2) * TX) ? TY * (TX + 2) : (TY + 2) * TX;
-    static constexpr size_t bytes = sizeof(T) * (6 * SP3 + 6 * NS + 12 * NF + 6 * NL) + 6 * NS;
+    static constexpr int LW = TX + 4, LP = LW * (TY + 4);  // lam box: tile + 2-cell halo
+    static constexpr size_t sel_bytes = (6 * NS + 15) / 16 * 16;
+    static constexpr size_t base = sizeof(T) * (6 * SP3 + 6 * NS + 12 * NF + 6 * NL) + sel_bytes;
+    static constexpr size_t bytes = base + (STAGE ? sizeof(T) * (8 * LP + 7 * NF) : 0);
 };
 
 template <typename T, int TX, int TY, int D>
 __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, unsigned char *sSel, T *sLum,
-                                             T *sLup, T *sLs, T lres[6])
+                                             T *sLup, T *sLs, const T *sLam, T *sG, T lres[6])
 {
     using SM = FaceAdjSmem<T, TX, TY>;
-    constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3;
+    constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3, LW = SM::LW, LP = SM::LP;
     constexpr int L = D == 0 ? TX : TY;   // cells of the tile along the normal
     constexpr int M = D == 0 ? TY : TX;   // lines of the tile
     constexpr int NSl = L + 4, NFl = L + 3, NLl = L + 2;
@@ -383,6 +391,19 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
     auto gidx = [&](int m, int p) {  // global (i, j) of line m, normal position p (tile coords)
         return D == 0 ? cell_index(x0 + p, y0 + m, pitch) : cell_index(x0 + m, y0 + p, pitch);
     };
+    auto lidx = [&](int m, int p) {  // lam box index of line m, normal position p
+        return D == 0 ? (m + 2) * LW + (p + 2) : (p + 2) * LW + (m + 2);
+    };
+    if constexpr (SM::STAGE) {
+        // face geometry of this direction, faces with lower cell p = -2 .. L
+        for (int e = tid; e < 7 * NF; e += NT) {
+            const int c = e / NF, r = e - c * NF;
+            const int m = r / NFl, p = r - m * NFl - 2;
+            const int lo = o0 + p, line = (D == 0 ? y0 : x0) + m;
+            const bool ok = lo >= -1 && lo <= n - 1 && line < nt;
+            cp_async_elem(sG + e, ok ? geo + ((D == 0 ? GX_JHD : GY_JHD) + c) * plane + gidx(m, p) : geo, ok);
+        }
+    }
     // slopes and their selections, cells p = -2 .. L+1
     for (int e = tid; e < 6 * NS; e += NT) {
         const int c = e / NS, r = e - c * NS;
@@ -392,6 +413,7 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
         sS[e] = minmod(d1, d2);
         sSel[e] = (unsigned char)minmod_sel(d1, d2);
     }
+    if constexpr (SM::STAGE) cp_async_wait_all();  // the face geometry
     __syncthreads();
     // face adjoints, faces with lower cell p = -2 .. L
     for (int e = tid; e < NF; e += NT) {
@@ -401,27 +423,38 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
         const bool exists = lo >= -1 && lo <= n - 1 && line < nt;
         T lum[6] = {T(0), T(0), T(0), T(0), T(0), T(0)}, lup[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         if (exists) {
-            const long long g = gidx(m, p);
             FaceGeo<T> G;
-            if (D == 0)
-                G = FaceGeo<T>{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
-                               geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
-                               geo[GX_HG * plane + g]};
-            else
-                G = FaceGeo<T>{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
-                               geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
-                               geo[GY_HG * plane + g]};
-            const bool in_lo = lo >= 0, in_hi = lo + 1 <= n - 1;
-            const long long gl = g, gh = D == 0 ? g + 1 : g + pitch;
-            T lH[6];
+            T lH[6], d0, d1;
+            if constexpr (SM::STAGE) {
+                G = FaceGeo<T>{sG[e], sG[NF + e], sG[2 * NF + e], sG[3 * NF + e], sG[4 * NF + e], sG[5 * NF + e],
+                               sG[6 * NF + e]};
+                // cells outside the domain hold 0 in the lam box
+                const int bl = lidx(m, p), bh = lidx(m, p + 1);
 #pragma unroll
-            for (int c = 0; c < 6; c++) {
-                const T a1 = in_hi ? q.lam_pre[c * plane + gh] : T(0);
-                const T a0 = in_lo ? q.lam_pre[c * plane + gl] : T(0);
-                lH[c] = dtT * hinv * (a1 - a0);
+                for (int c = 0; c < 6; c++) lH[c] = dtT * hinv * (sLam[c * LP + bh] - sLam[c * LP + bl]);
+                d0 = sLam[(6 + D) * LP + bl];
+                d1 = sLam[(6 + D) * LP + bh];
+            } else {
+                const long long g = gidx(m, p);
+                if (D == 0)
+                    G = FaceGeo<T>{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
+                                   geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
+                                   geo[GX_HG * plane + g]};
+                else
+                    G = FaceGeo<T>{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
+                                   geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
+                                   geo[GY_HG * plane + g]};
+                const bool in_lo = lo >= 0, in_hi = lo + 1 <= n - 1;
+                const long long gl = g, gh = D == 0 ? g + 1 : g + pitch;
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    const T a1 = in_hi ? q.lam_pre[c * plane + gh] : T(0);
+                    const T a0 = in_lo ? q.lam_pre[c * plane + gl] : T(0);
+                    lH[c] = dtT * hinv * (a1 - a0);
+                }
+                d0 = in_lo ? q.lam_dp[D * plane + gl] : T(0);
+                d1 = in_hi ? q.lam_dp[D * plane + gh] : T(0);
             }
-            const T d0 = in_lo ? q.lam_dp[D * plane + gl] : T(0);
-            const T d1 = in_hi ? q.lam_dp[D * plane + gh] : T(0);
             const T lP2 = hinv * (d0 - d1);
             T um[6], up[6];
             const int sl = m * NSl + (p + 2);  // slope index of the lower cell
@@ -502,25 +535,38 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     T *sLup = sLum + 6 * SM::NF;
     T *sLs = sLup + 6 * SM::NF;
     unsigned char *sSel = reinterpret_cast<unsigned char *>(sLs + 6 * SM::NL);
+    T *sLam = reinterpret_cast<T *>(smem_raw + SM::base);  // FP32 form: [8][TY+4][TX+4]
+    T *sG = sLam + 8 * SM::LP;                              // FP32 form: [7][NF]
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
+    if constexpr (SM::STAGE) {
+        // lam_pre (6) and lam_dp (2) of the tile and a 2-cell halo; 0 outside the domain
+        for (int e = tid; e < 8 * SM::LP; e += NT) {
+            const int c = e / SM::LP, r = e - c * SM::LP;
+            const int ly = r / SM::LW, lx = r - ly * SM::LW;
+            const int gi = x0 - 2 + lx, gj = y0 - 2 + ly;
+            const bool ok = gi >= 0 && gj >= 0 && gi < nx && gj < ny;
+            const long long g = ok ? cell_index(gi, gj, pitch) : 0;
+            cp_async_elem(sLam + e, c < 6 ? q.lam_pre + c * plane + g : q.lam_dp + (c - 6) * plane + g, ok);
+        }
+    }
     // stage input with a 3-cell halo (cells beyond the 2 ghost layers read 0;
     // no forward face uses them)
     for (int e = tid; e < 6 * SP3; e += NT) {
         const int c = e / SP3, r = e - c * SP3;
         const int ly = r / SW3, lx = r - ly * SW3;
         const int gi = x0 - 3 + lx, gj = y0 - 3 + ly;
-        T v = T(0);
-        if (gi >= -2 && gj >= -2 && gi < nx + 2 && gj < ny + 2) v = a.Uin[c * plane + cell_index(gi, gj, pitch)];
-        sU[e] = v;
+        const bool ok = gi >= -2 && gj >= -2 && gi < nx + 2 && gj < ny + 2;
+        cp_async_elem(sU + e, a.Uin + (ok ? c * plane + cell_index(gi, gj, pitch) : 0), ok);
     }
+    cp_async_wait_all();
     __syncthreads();
     T lres[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, lres);
-    adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, lres);
+    adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sG, lres);
+    adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sG, lres);
     const int i = x0 + tid % TX, j = y0 + tid / TX;
     if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);

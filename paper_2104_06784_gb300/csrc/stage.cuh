@@ -141,6 +141,19 @@ __device__ __forceinline__ float frsqrt(float x)
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(sub ? x * 0x1p64f : x));
     return sub ? y * 0x1p32f : y;
 }
+// Asynchronous global -> shared copy of one element (cp.async, no register
+// round trip, many in flight per thread); !valid writes 0 and reads nothing.
+// The copies of a thread complete at cp_async_wait_all().
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned n = valid ? (unsigned)sizeof(T) : 0u;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(sizeof(T)), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // error-free sum (Knuth's TwoSum): s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -474,14 +487,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     if (tid < 4) acc[tid] = 0.0;
 
     // ---- stage the tile + 2-cell halo of the six state planes -----------
+    // (asynchronous copies: every element of the thread in flight at once)
     for (int e = tid; e < 6 * SP; e += NT) {
         const int c = e / SP, r = e - c * SP;
         const int ly = r / SW, lx = r - ly * SW;
         const int gi = x0 - 2 + lx, gj = y0 - 2 + ly;
-        T v = T(0);
-        if (gi < nx + 2 && gj < ny + 2) v = a.Uin[c * plane + cell_index(gi, gj, pitch)];
-        sU[e] = v;
+        const bool ok = gi < nx + 2 && gj < ny + 2;
+        cp_async_elem(sU + e, a.Uin + (ok ? c * plane + cell_index(gi, gj, pitch) : 0), ok);
     }
+    cp_async_wait_all();
     __syncthreads();
     const double t_now = s_t, dt = s_dt;
     const T dtT = s_dtT;
