@@ -21,7 +21,7 @@ struct moses_sim {
     cudaStream_t stream = nullptr;
     void *U = nullptr;     // state, 6 planes
     void *Us = nullptr;    // Heun intermediate, 6 planes
-    void *geo = nullptr;   // GEO_PLANES planes
+    void *geo = nullptr;   // geo_planes(s) planes
     Ctl *ctl = nullptr;    // device control block
     InflowSeg *inflow_d = nullptr;
     InflowSeg inflow_h[MAX_INFLOW];
@@ -61,6 +61,8 @@ inline int grid_for(long long n, int block = 256)
     if (b > 152 * 32) b = 152 * 32;
     return (int)b;
 }
+
+inline int geo_planes(const moses_sim *s) { return s->prec == MOSES_FP32 ? GEO_PLANES_F32 : GEO_PLANES; }
 
 // remainder planes (FP32 form) that follow the six state planes of a buffer
 template <typename T>

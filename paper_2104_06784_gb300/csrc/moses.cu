@@ -142,6 +142,13 @@ __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, l
             put(GY_FN2, g, 2.0 * ph.kap_f * An);
             put(GY_HG, g, ph.half_g * c2);
         }
+        if constexpr (sizeof(T) == 4) {
+            const Slopes s = slopes(i, j);
+            put(GS_SX, g, s.bX);
+            put(GS_SY, g, s.bY);
+            if (i < nx + 1) put(GS_DBX, g, (B(i + 1, j) - B(i, j)) / dx);
+            if (j < ny + 1) put(GS_DBY, g, (B(i, j + 1) - B(i, j)) / dy);
+        }
     }
 }
 
@@ -469,7 +476,7 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
     const size_t st = (s->prec == MOSES_FP32 ? 8 : 6) * (size_t)s->plane * s->esz;
     cudaError_t e;
     if ((e = cudaMalloc(&s->U, st)) != cudaSuccess || (e = cudaMalloc(&s->Us, st)) != cudaSuccess ||
-        (e = cudaMalloc(&s->geo, (size_t)GEO_PLANES * s->plane * s->esz)) != cudaSuccess ||
+        (e = cudaMalloc(&s->geo, (size_t)geo_planes(s) * s->plane * s->esz)) != cudaSuccess ||
         (e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = cudaMalloc(&s->inflow_d, sizeof(InflowSeg) * MAX_INFLOW)) != cudaSuccess ||
         (e = cudaMalloc(&s->red, 8 * sizeof(double))) != cudaSuccess) {
@@ -478,7 +485,7 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
     }
     if ((e = cudaMemsetAsync(s->U, 0, st, s->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(s->Us, 0, st, s->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(s->geo, 0, (size_t)GEO_PLANES * s->plane * s->esz, s->stream)) != cudaSuccess) {
+        (e = cudaMemsetAsync(s->geo, 0, (size_t)geo_planes(s) * s->plane * s->esz, s->stream)) != cudaSuccess) {
         s->err = std::string("memset: ") + cudaGetErrorString(e);
         return bail(MOSES_ECUDA);
     }

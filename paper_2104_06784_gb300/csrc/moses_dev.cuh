@@ -58,6 +58,12 @@ enum GeoPlane : int {
     GY_HG,      //   (g/2) c^2
     GEO_PLANES
 };
+// FP32 form only: four more planes from which the stage kernel rebuilds the
+// cell and face geometry in the tile (the same formulas as the geometry pass,
+// in FP32): the cell's central slopes bX, bY and the face-normal differences
+// (b_{i+1,j} - b_{i,j}) / dx, (b_{i,j+1} - b_{i,j}) / dy.  Curvatures follow
+// as differences of these: bXX from DBX, bYY from DBY, bXY from SY along X.
+enum SlopePlane : int { GS_SX = GEO_PLANES, GS_SY, GS_DBX, GS_DBY, GEO_PLANES_F32 };
 
 // Device control block, one per simulation (or per ensemble member).
 struct Ctl {
@@ -106,6 +112,8 @@ struct Phys {
 template <typename T>
 struct KT {
     T eps_chi, eps_alpha, eps, alpha, c_d, k_f, hinv_dx, hinv_dy, tan_delta;
+    // geometry rebuilt from slopes (FP32 form)
+    T kap_s, kap_f, kap_f2, half_g, g_1ma, g, h_dry, inv_dx, inv_dy, inv_2dx;
     double tan_delta_d;
 };
 
@@ -122,6 +130,16 @@ inline KT<T> make_kt(const Phys &p)
     k.hinv_dx = (T)(0.5 * p.inv_dx);
     k.hinv_dy = (T)(0.5 * p.inv_dy);
     k.tan_delta = (T)p.tan_delta;
+    k.kap_s = (T)p.kap_s;
+    k.kap_f = (T)p.kap_f;
+    k.kap_f2 = (T)(2.0 * p.kap_f);
+    k.half_g = (T)p.half_g;
+    k.g_1ma = (T)p.g_1ma;
+    k.g = (T)p.g;
+    k.h_dry = (T)p.h_dry;
+    k.inv_dx = (T)p.inv_dx;
+    k.inv_dy = (T)p.inv_dy;
+    k.inv_2dx = (T)(0.5 * p.inv_dx);
     k.tan_delta_d = p.tan_delta;
     return k;
 }

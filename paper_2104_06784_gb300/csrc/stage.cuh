@@ -342,21 +342,69 @@ __device__ void write_ghosts(T *U, const T *geo, const StageArgs<T> &a, int i, i
     }
 }
 
-// Largest cell-centre wave speed of a state (R7), both phases, both axes.
-// g: pointer to the cell's geometry (plane stride `plane`).
+// Largest cell-centre wave speed of a state (R7), both phases, both axes,
+// from the cell's J h_dry and its four speed coefficients.
 template <typename T>
-__device__ __forceinline__ T cell_speed(const T u[6], const T *geo, long long plane, long long g)
+__device__ __forceinline__ T cell_speed(const T u[6], T jhd, T sxs, T sxf, T sys, T syf)
 {
-    const T jhd = geo[GC_JHD * plane + g];
     const T Ut = u[0] + u[3];
     const T rs = gtp(u[0], jhd) ? frcp(u[0]) : T(0);
     const T rf = gtp(u[3], jhd) ? frcp(u[3]) : T(0);
     const T cs = Ut + u[0];
-    T m = tabs(u[1] * rs) + fsqrt(geo[GC_SXS * plane + g] * cs);
-    m = maxnn(m, tabs(u[4] * rf) + fsqrt(geo[GC_SXF * plane + g] * Ut));
-    m = maxnn(m, tabs(u[2] * rs) + fsqrt(geo[GC_SYS * plane + g] * cs));
-    m = maxnn(m, tabs(u[5] * rf) + fsqrt(geo[GC_SYF * plane + g] * Ut));
+    T m = tabs(u[1] * rs) + fsqrt(sxs * cs);
+    m = maxnn(m, tabs(u[4] * rf) + fsqrt(sxf * Ut));
+    m = maxnn(m, tabs(u[2] * rs) + fsqrt(sys * cs));
+    m = maxnn(m, tabs(u[5] * rf) + fsqrt(syf * Ut));
     return m;
+}
+// the same with the coefficients read from the geometry planes of cell g
+template <typename T>
+__device__ __forceinline__ T cell_speed(const T u[6], const T *geo, long long plane, long long g)
+{
+    return cell_speed(u, geo[GC_JHD * plane + g], geo[GC_SXS * plane + g], geo[GC_SXF * plane + g],
+                      geo[GC_SYS * plane + g], geo[GC_SYF * plane + g]);
+}
+
+// ---- FP32 form: geometry rebuilt from bed slopes in the tile -------------------
+// The formulas of the geometry pass (Sect. 2.1): Omega_b = [(1,0,bX),
+// (0,1,bY), n], J = sqrt(1 + bX^2 + bY^2), c = 1/J, A = the 2x2 block of the
+// inverse metric; curvature terms c bXX, 2 c bXY, c bYY.
+struct CellGeo32 {
+    float jhd, gc1, gcf, bX, bY, nX, nY, A11, A12, A22, kXX, kXY2, kYY, sxs, sxf, sys, syf;
+};
+__device__ __forceinline__ CellGeo32 cell_geo32(float sX, float sY, float bXX, float bXY, float bYY, const KT<float> &k)
+{
+    CellGeo32 G;
+    const float s2 = fmaf(sX, sX, fmaf(sY, sY, 1.0f));
+    const float c = frsqrt(s2), c2 = c * c;
+    G.jhd = s2 * c * k.h_dry;
+    G.gc1 = k.g_1ma * c;
+    G.gcf = k.g * c;
+    G.bX = sX;
+    G.bY = sY;
+    G.nX = -c * sX;
+    G.nY = -c * sY;
+    G.A11 = fmaf(sY, sY, 1.0f) * c2;
+    G.A12 = -sX * sY * c2;
+    G.A22 = fmaf(sX, sX, 1.0f) * c2;
+    G.kXX = c * bXX;
+    G.kXY2 = 2.0f * c * bXY;
+    G.kYY = c * bYY;
+    G.sxs = k.kap_s * G.A11 * c2;
+    G.sxf = k.kap_f2 * G.A11 * c2;
+    G.sys = k.kap_s * G.A22 * c2;
+    G.syf = k.kap_f2 * G.A22 * c2;
+    return G;
+}
+// face of normal slope bn (the face difference) and transverse slope bt (mean
+// of the two cells' central differences)
+__device__ __forceinline__ FaceGeo<float> face_geo32(float bn, float bt, const KT<float> &k)
+{
+    const float s2 = fmaf(bn, bn, fmaf(bt, bt, 1.0f));
+    const float c2 = frcp(s2), cc = c2 * c2;
+    const float An = fmaf(bt, bt, 1.0f) * cc, At = -bn * bt * cc;
+    return FaceGeo<float>{fsqrt(s2) * k.h_dry, k.kap_s * An, k.kap_s * At, k.kap_f * An, k.kap_f * At,
+                          k.kap_f2 * An, k.half_g * c2};
 }
 
 __device__ __forceinline__ double dt_from(const Ctl *ctl, const Phys &ph, double amax)
@@ -451,6 +499,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     T *sSy = sSx + 6 * NSX;                    // [6][TY+2][TX]   along y
     T *sHx = sSy + 6 * NSY;                    // [7][TY][TX+1]   2 x flux, 2 x P
     T *sHy = sHx + 7 * NXF;                    // [7][TY+1][TX]
+    // FP32 form: bed slopes of the tile + 1-cell halo, [4][TY+2][TX+2]
+    // (SX, SY, DBX, DBY); the geometry is rebuilt from them
+    constexpr bool GL = sizeof(T) == 4;
+    constexpr int BW = TX + 2, NB = (TX + 2) * (TY + 2);
+    T *sB = sHy + 7 * NYF;
+    auto SB = [&](int c, int cx, int cy) -> T { return sB[c * NB + cy * BW + cx]; };
     __shared__ T red[NT / 32];
     __shared__ double acc[4];
     __shared__ unsigned int acc_n;
@@ -495,6 +549,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         const bool ok = gi < nx + 2 && gj < ny + 2;
         cp_async_elem(sU + e, a.Uin + (ok ? c * plane + cell_index(gi, gj, pitch) : 0), ok);
     }
+    if constexpr (GL) {
+        for (int e = tid; e < 4 * NB; e += NT) {  // cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
+            const int c = e / NB, r = e - c * NB;
+            const int ly = r / BW, lx = r - ly * BW;
+            const int gi = x0 - 1 + lx, gj = y0 - 1 + ly;
+            const bool ok = gi <= nx && gj <= ny;
+            cp_async_elem(sB + e, geo + (ok ? (GS_SX + c) * plane + cell_index(gi, gj, pitch) : 0), ok);
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
     const double t_now = s_t, dt = s_dt;
@@ -520,10 +583,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         const int ly = f / (TX + 1), lx = f - ly * (TX + 1);
         const int i = x0 + lx - 1, j = y0 + ly;
         if (j >= ny || i >= nx) continue;
-        const long long g = cell_index(i, j, pitch);
-        const FaceGeo<T> G{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
+        FaceGeo<T> G;
+        if constexpr (GL) {  // lower cell at (lx, ly + 1) of the slope tile
+            G = face_geo32(SB(2, lx, ly + 1), 0.5f * (SB(1, lx, ly + 1) + SB(1, lx + 1, ly + 1)), k);
+        } else {
+            const long long g = cell_index(i, j, pitch);
+            G = FaceGeo<T>{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
                            geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
                            geo[GX_HG * plane + g]};
+        }
         const int ou = (ly + 2) * SW + lx + 1;  // left cell in sU
         const int os = ly * (TX + 2) + lx;      // left cell in sSx
         T um[6], up[6];
@@ -553,10 +621,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         const int ly = f / TX, lx = f - ly * TX;
         const int i = x0 + lx, j = y0 + ly - 1;
         if (i >= nx || j >= ny) continue;
-        const long long g = cell_index(i, j, pitch);
-        const FaceGeo<T> G{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
+        FaceGeo<T> G;
+        if constexpr (GL) {  // lower cell at (lx + 1, ly) of the slope tile
+            G = face_geo32(SB(3, lx + 1, ly), 0.5f * (SB(0, lx + 1, ly) + SB(0, lx + 1, ly + 1)), k);
+        } else {
+            const long long g = cell_index(i, j, pitch);
+            G = FaceGeo<T>{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
                            geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
                            geo[GY_HG * plane + g]};
+        }
         const int ou = (ly + 1) * SW + lx + 2;  // lower cell in sU
         const int os = ly * TX + lx;            // lower cell in sSy
         T um[6], up[6];
@@ -589,10 +662,43 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
         const int os = (ly + 2) * SW + lx + 2;
+        // the cell's geometry: FP32 rebuilt from the slope tile, FP64 read
+        CellGeo32 cgf{};
+        if constexpr (GL) {
+            const int cx = lx + 1, cy = ly + 1;
+            cgf = cell_geo32(SB(0, cx, cy), SB(1, cx, cy), (SB(2, cx, cy) - SB(2, cx - 1, cy)) * k.inv_dx,
+                             (SB(1, cx + 1, cy) - SB(1, cx - 1, cy)) * k.inv_2dx,
+                             (SB(3, cx, cy) - SB(3, cx, cy - 1)) * k.inv_dy, k);
+        }
+        const auto CG = [&](const int P) -> T {
+            if constexpr (GL) {
+                switch (P) {
+                case GC_JHD: return cgf.jhd;
+                case GC_GC1: return cgf.gc1;
+                case GC_GCF: return cgf.gcf;
+                case GC_BX: return cgf.bX;
+                case GC_BY: return cgf.bY;
+                case GC_MNX: return cgf.nX;
+                case GC_MNY: return cgf.nY;
+                case GC_A11: return cgf.A11;
+                case GC_A12: return cgf.A12;
+                case GC_A22: return cgf.A22;
+                case GC_KXX: return cgf.kXX;
+                case GC_KXY2: return cgf.kXY2;
+                case GC_KYY: return cgf.kYY;
+                case GC_SXS: return cgf.sxs;
+                case GC_SXF: return cgf.sxf;
+                case GC_SYS: return cgf.sys;
+                default: return cgf.syf;
+                }
+            } else {
+                return geo[P * plane + g];
+            }
+        };
         T u[6];
 #pragma unroll
         for (int c = 0; c < 6; c++) u[c] = sU[c * SP + os];
-        const T jhd = geo[GC_JHD * plane + g];
+        const T jhd = CG(GC_JHD);
         const T Ut = u[0] + u[3];
         // volume fractions phi^s, phi^f (0 where h <= h_dry)
         const T rUt = gtp(Ut, jhd) ? frcp(Ut) : T(0);
@@ -602,18 +708,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         const T vXs = u[1] * rs, vYs = u[2] * rs, vXf = u[4] * rf, vYf = u[5] * rf;
         // -kappa = c (bXX vX^2 + 2 bXY vX vY + bYY vY^2): the centripetal term
         // sum_k v_k (dn_k/dxi v_xi + dn_k/deta v_eta) with v tangent to the bed
-        const T kXX = geo[GC_KXX * plane + g], kXY2 = geo[GC_KXY2 * plane + g], kYY = geo[GC_KYY * plane + g];
+        const T kXX = CG(GC_KXX), kXY2 = CG(GC_KXY2), kYY = CG(GC_KYY);
         const T nks = fma(kXX, vXs * vXs, fma(kXY2, vXs * vYs, kYY * (vYs * vYs)));
         const T nkf = fma(kXX, vXf * vXf, fma(kXY2, vXf * vYf, kYY * (vYf * vYf)));
         // J p_b = U (g c (1 - alpha) - eps^chi kappa), clamped at 0 (lift-off)
-        const T Jpbs = pos(u[0] * fma(k.eps_chi, nks, geo[GC_GC1 * plane + g]));
-        const T Jpbf = pos(u[3] * fma(k.eps_chi, nkf, geo[GC_GCF * plane + g]));
-        const T nX = geo[GC_MNX * plane + g], nY = geo[GC_MNY * plane + g];
+        const T Jpbs = pos(u[0] * fma(k.eps_chi, nks, CG(GC_GC1)));
+        const T Jpbf = pos(u[3] * fma(k.eps_chi, nkf, CG(GC_GCF)));
+        const T nX = CG(GC_MNX), nY = CG(GC_MNY);
         // gradient of P = J h pbar^f from its (doubled) face values
         const int fx = ly * (TX + 1) + lx, fy = ly * TX + lx;
         const T dPx = (sHx[6 * NXF + fx + 1] - sHx[6 * NXF + fx]) * k.hinv_dx;
         const T dPy = (sHy[6 * NYF + fy + TX] - sHy[6 * NYF + fy]) * k.hinv_dy;
-        const T A11 = geo[GC_A11 * plane + g], A12 = geo[GC_A12 * plane + g], A22 = geo[GC_A22 * plane + g];
+        const T A11 = CG(GC_A11), A12 = CG(GC_A12), A22 = CG(GC_A22);
         const T gX = fma(A11, dPx, A12 * dPy), gY = fma(A12, dPx, A22 * dPy);
         const T bs = -k.eps_alpha * phs;                         // s_f^s = bs grad
         const T bf = k.eps * (a.ph.pg_mode == 1 ? phf : phs);   // s_f^f = bf grad (R1)
@@ -661,9 +767,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             a.rec[5 * plane + g] = dPy;
         }
         if constexpr (sizeof(T) == 8)
-            coulomb(out[1], out[2], geo[GC_BX * plane + g], geo[GC_BY * plane + g], dt * Jpbs * k.tan_delta);
+            coulomb(out[1], out[2], CG(GC_BX), CG(GC_BY), dt * Jpbs * k.tan_delta);
         else
-            coulomb(out[1], out[2], geo[GC_BX * plane + g], geo[GC_BY * plane + g], dtT * Jpbs * k.tan_delta, dt,
+            coulomb(out[1], out[2], CG(GC_BX), CG(GC_BY), dtT * Jpbs * k.tan_delta, dt,
                     Jpbs, k.tan_delta_d);
         // positivity clamp (counted) and dry momentum
 #pragma unroll
@@ -707,7 +813,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                     out[3 * ph + 1] = T(0);
                     out[3 * ph + 2] = T(0);
                 }
-            if (a.want_amax) speed = cell_speed(out, geo, plane, g);
+            if (a.want_amax) speed = cell_speed(out, CG(GC_JHD), CG(GC_SXS), CG(GC_SXF), CG(GC_SYS), CG(GC_SYF));
         }
 #pragma unroll
         for (int c = 0; c < 6; c++) bad |= nonfinite(out[c]);
@@ -797,8 +903,9 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
 template <typename T, int TX, int TY>
 constexpr size_t stage_smem_bytes()
 {
+    // state halo tile, slopes, face fluxes; FP32: bed-slope tile
     return sizeof(T) * (6 * (TX + 4) * (TY + 4) + 6 * (TX + 2) * TY + 6 * TX * (TY + 2) + 7 * (TX + 1) * TY +
-                        7 * TX * (TY + 1));
+                        7 * TX * (TY + 1) + (sizeof(T) == 4 ? 4 * (TX + 2) * (TY + 2) : 0));
 }
 
 }  // namespace moses
