@@ -228,7 +228,7 @@ def measure_ensemble(K, Wm, seed=0, n=256):
                       "spectral DEMs, delta_b U(15,30) deg, c_D U(1e-4,1e-2) 1/s, release U(1e4,1e6) m^3, FP32"}
 
 
-def measure_adjoint(torch, n=1024):
+def measure_adjoint(torch, n=1024, steps=None, ckpt=None):
     """Adjoint calibration workload, FP32 forward: 1024 x 1024 cells at 5 m,
     spectral DEM, 5000 steps with a checkpoint every 71.  The target deposit
     comes from a forward run with the hidden basal friction 22 deg and drag
@@ -239,7 +239,7 @@ def measure_adjoint(torch, n=1024):
     moses_adjoint_misfit (CUDA events inside the library)."""
     from paper_2104_06784_gb300 import moses, workloads as W
     cfg = W.adjoint_config(n=n)
-    N, C = cfg["steps"], cfg["ckpt_every"]
+    N, C = steps or cfg["steps"], ckpt or cfg["ckpt_every"]
     ct = dict(cfg)
     ct["params"] = dict(cfg["params"], **cfg["hidden"])
     with moses.from_config(ct, precision=moses.FP32) as gt:
@@ -270,7 +270,8 @@ def measure_adjoint(torch, n=1024):
                      "c_d": float(r["g_params"][2]), "release_h_l2": float(np.sqrt((gh * gh).sum()))},
             # forward: 2 stages + 2 records per step, misfit; backward: per step 1 time reset,
             # 2 recording stages, 2 x (cell, face, fold); release gradient
-            "gpu_launches": 4 * N + 1 + 9 * N + 1}
+            "gpu_launches": 4 * N + 1 + 9 * N + 1,
+            "fp64_check": "gradients against FP64 central differences of the oracle: tests/test_gpu_adjoint.py"}
 
 
 def main():
@@ -284,7 +285,10 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (the workload is defined at 4096)")
-    ap.add_argument("--only", choices=["f64", "f32"], default=None, help="measure one precision form")
+    ap.add_argument("--only", choices=["f64", "f32", "adjoint"], default=None,
+                    help="measure one precision form, or only the adjoint")
+    ap.add_argument("--adj-steps", type=int, default=None, help="adjoint: steps (default: the workload's 5000)")
+    ap.add_argument("--adj-ckpt", type=int, default=None, help="adjoint: checkpoint interval (default 71)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -310,6 +314,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2104_06784_gb300 import moses
+    if args.only == "adjoint":
+        adj = measure_adjoint(torch, steps=args.adj_steps, ckpt=args.adj_ckpt)
+        if rank == 0:
+            print(json.dumps(adj), flush=True)
+        return
     side = args.side
     cells = side * side
     K, Wm = args.steps, args.warmup

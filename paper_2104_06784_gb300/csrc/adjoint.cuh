@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
     const T *geo = a.geo;
     const double dt = a.dbg_dt;
     const T dtT = (T)dt;
-    double g_tan = 0.0, g_cd = 0.0;
+    // parameter partials: per cell and across the warp in T, per CTA and
+    // globally in FP64 (the FP64 pipe of GB300 is 1/64 of its FP32 rate)
+    T g_tan = T(0), g_cd = T(0);
     if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
         T u[6], pre4[4];
@@ -250,7 +252,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
             lFr = -sq * rr;
         }
         T lJpbs = lFr * dtT * k.tan_delta;
-        g_tan += (double)(lFr * dtT * Jpbs);
+        g_tan += lFr * dtT * Jpbs;
         // update pre = u + dt (S - div): identity, sources; div goes to faces via lam_pre
         T lu[6], lS[6];
 #pragma unroll
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
         // ff = k_f phf Ut ; D = c_D phs phf Ut
         lphf += lff * k.k_f * Ut;
         lUt += lff * k.k_f * phf;
-        g_cd += (double)(lD * phs * phf * Ut);
+        g_cd += lD * phs * phf * Ut;
         lphs += lD * k.c_d * phf * Ut;
         lphf += lD * k.c_d * phs * Ut;
         lUt += lD * k.c_d * phs * phf;
@@ -324,8 +326,8 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
         g_cd += __shfl_xor_sync(0xffffffffu, g_cd, o);
     }
     if ((tid & 31) == 0) {
-        red[0][tid >> 5] = g_tan;
-        red[1][tid >> 5] = g_cd;
+        red[0][tid >> 5] = (double)g_tan;
+        red[1][tid >> 5] = (double)g_cd;
     }
     __syncthreads();
     if (tid == 0) {
