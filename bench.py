@@ -335,8 +335,12 @@ def main():
     forms = [("f64", moses.FP64), ("f32", moses.FP32)]
     if args.only:
         forms = [f for f in forms if f[0] == args.only]
+    tiles = {}
     for name, prec in forms:
         sim = moses.from_config(cfg, precision=prec)
+        tile, tile_ms = sim.autotune()  # the project's tile autotuner
+        tiles[name] = {"tile": moses.Sim.TILES[tile],
+                       "ms_per_launch": {moses.Sim.TILES[t]: tile_ms[t] for t in range(3)}}
         if dist is not None:
             dist.barrier()
         with (sampler if name == "f64" else _Null()):
@@ -422,6 +426,7 @@ def main():
         "ensemble": ens,
         "adjoint": adj,
         "stage_ms": {"f64": f64["stage_ms"], "f32": f32["stage_ms"]},
+        "tiles": tiles,
         "stage_source": h,
     }
     if rank == 0:

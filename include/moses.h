@@ -125,6 +125,26 @@ int moses_step(moses_sim *s, int nsteps, double *t_out);
  * per-kernel throughput measurements; otherwise identical to moses_step. */
 int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms);
 
+/* Tile shape of the stage kernel (not in the paper, which gives none):
+ * MOSES_TILE_32x8 (the default), MOSES_TILE_32x4 or MOSES_TILE_32x16 cells
+ * per CTA.  Every tile computes the same values (the state after a step is
+ * bit-identical); only the speed differs.  Errors: EINVAL for another value. */
+#define MOSES_TILE_32x8 0
+#define MOSES_TILE_32x4 1
+#define MOSES_TILE_32x16 2
+#define MOSES_NTILES 3
+int moses_set_tile(moses_sim *s, int tile);
+
+/* Autotuner: times `reps` (>= 1; 0 = 5) launches of one stage of the current
+ * state with each tile shape (CUDA events on the simulation's stream, after
+ * one warm-up launch each; the state is not changed), selects the fastest and
+ * returns it in *tile_out (may be NULL).  ms_out (may be NULL) receives the
+ * mean time per launch of each tile [ms], indexed by MOSES_TILE_*.  The choice
+ * is cached per process by (device, SM count, precision, nx, ny): a later call
+ * with ms_out == NULL on a simulation with the same key takes the cached tile
+ * without timing.  Errors: EINVAL, ESTATE (no state), ECUDA. */
+int moses_autotune(moses_sim *s, int reps, int *tile_out, double *ms_out);
+
 /* Advance with a prescribed time step dt > 0 (same stages, no CFL search).
  * Errors: EINVAL, ESTATE, ENONFINITE, ECUDA. */
 int moses_step_dt(moses_sim *s, int nsteps, double dt, double *t_out);

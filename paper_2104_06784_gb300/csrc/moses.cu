@@ -7,7 +7,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -704,6 +707,89 @@ int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms)
 {
     if (!s || !stage_ms) return MOSES_EINVAL;
     return run_steps(s, nsteps, 0.0, 0.0, t_out, stage_ms);
+}
+
+int moses_set_tile(moses_sim *s, int tile)
+{
+    if (!s) return MOSES_EINVAL;
+    if (tile < 0 || tile >= MOSES_NTILES) return fail(s, MOSES_EINVAL, "tile must be one of MOSES_TILE_*");
+    s->tile = tile;
+    return MOSES_OK;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::array<int, 5>, int> g_tune_cache;  // (device, SMs, precision, nx, ny) -> tile
+
+// one stage of the current state into the scratch buffer (no ghosts, no budgets)
+template <typename T>
+int probe_stage(moses_sim *s, int tile, double dt)
+{
+    StageArgs<T> a = base_args<T>(s);
+    a.Uin = (const T *)s->U;
+    a.Uout = (T *)s->Us;
+    a.Rin = rem<T>(s, s->U);
+    a.Rout = rem<T>(s, s->Us);
+    a.stage = 1;
+    a.debug_stage = 1;
+    a.dbg_dt = dt;
+    return launch_stage<T>(a, tile, s->stream);
+}
+}  // namespace
+
+int moses_autotune(moses_sim *s, int reps, int *tile_out, double *ms_out)
+{
+    if (!s) return MOSES_EINVAL;
+    if (reps < 0) return fail(s, MOSES_EINVAL, "reps must be >= 0");
+    if (reps == 0) reps = 5;
+    if (!s->have_state) return fail(s, MOSES_ESTATE, "no state");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const std::array<int, 5> key{dev, sms, s->prec, s->nx, s->ny};
+    if (!ms_out) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            s->tile = it->second;
+            if (tile_out) *tile_out = s->tile;
+            return MOSES_OK;
+        }
+    }
+    Ctl h;
+    int rc = read_ctl(s, &h);
+    if (rc) return rc;
+    const double dt = h.dt > 0.0 ? h.dt : s->ph.dt_max;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double ms[MOSES_NTILES];
+    int best = 0;
+    for (int t = 0; t < MOSES_NTILES && rc == 0; t++) {
+        for (int r = 0; r <= reps && rc == 0; r++) {
+            if (r == 1) cudaEventRecord(e0, s->stream);
+            rc = s->prec == MOSES_FP64 ? probe_stage<double>(s, t, dt) : probe_stage<float>(s, t, dt);
+        }
+        cudaEventRecord(e1, s->stream);
+        float f = 0.0f;
+        if (rc == 0 && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+            ms[t] = f / reps;
+        else
+            rc = -1;
+        if (rc == 0 && ms[t] < ms[best]) best = t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return fail(s, MOSES_ECUDA, "autotune launch failed");
+    s->tile = best;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if (tile_out) *tile_out = best;
+    if (ms_out)
+        for (int t = 0; t < MOSES_NTILES; t++) ms_out[t] = ms[t];
+    return MOSES_OK;
 }
 
 int moses_step_dt(moses_sim *s, int nsteps, double dt, double *t_out)

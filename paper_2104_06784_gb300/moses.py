@@ -65,6 +65,8 @@ SIGNATURES = [
     ("moses_step", C.c_int, [_vp, C.c_int, _dp]),
     ("moses_step_timed", C.c_int, [_vp, C.c_int, _dp, _dp]),
     ("moses_step_dt", C.c_int, [_vp, C.c_int, C.c_double, _dp]),
+    ("moses_set_tile", C.c_int, [_vp, C.c_int]),
+    ("moses_autotune", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), _dp]),
     ("moses_run_until", C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
     ("moses_next_dt", C.c_int, [_vp, _dp, _dp]),
     ("moses_get_state", C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _dp]),
@@ -198,6 +200,21 @@ class Sim:
         ms = (C.c_double * 2)()
         self._ck(self._L.moses_step_timed(self._h, int(n), C.byref(t), ms))
         return t.value, [ms[0], ms[1]]
+
+    # tile shape of the stage kernel -------------------------------------------
+    TILES = {0: "32x8", 1: "32x4", 2: "32x16"}
+
+    def set_tile(self, tile: int):
+        self._ck(self._L.moses_set_tile(self._h, int(tile)))
+
+    def autotune(self, reps: int = 5, timings: bool = True):
+        """Time one stage with each tile shape, keep the fastest; returns
+        (tile, [ms per launch for each tile]) (timings: None when the cached
+        choice was taken with timings=False)."""
+        t = C.c_int()
+        ms = np.zeros(3) if timings else None
+        self._ck(self._L.moses_autotune(self._h, int(reps), C.byref(t), _p(ms)))
+        return t.value, (None if ms is None else [float(x) for x in ms])
 
     def step_dt(self, dt: float, n: int = 1) -> float:
         t = C.c_double()

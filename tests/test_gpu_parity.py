@@ -296,3 +296,30 @@ def test_full_size_sampled_fp64():
         Uo = o.get_U()[:, m:m + w, m:m + w]
         Ug = U1[:, j0:j0 + w, i0:i0 + w]
         assert rel_maxnorm(Ug, Uo) < TOL64 or np.abs(Uo).max() == 0.0
+
+
+# ----------------------------------------------------------------------------
+# tile shapes and the autotuner
+
+
+@pytest.mark.parametrize("precision", [moses.FP64, moses.FP32])
+def test_tiles_give_identical_states_and_autotune_picks_one(precision):
+    cfg = W.large_release_config(n=150, ny=97, dx=10.0, seed=2, volume=5e5, radius_cells=10)
+    ref = moses.from_config(cfg, precision=precision)
+    ref.step(25)
+    U0 = ref.get_conserved()
+    for tile in (1, 2):
+        s = moses.from_config(cfg, precision=precision)
+        s.set_tile(tile)
+        s.step(25)
+        assert np.array_equal(s.get_conserved(), U0), tile
+    s = moses.from_config(cfg, precision=precision)
+    tile, ms = s.autotune(reps=3)
+    assert tile in (0, 1, 2) and all(m > 0 for m in ms) and ms[tile] == min(ms)
+    s.step(25)
+    assert np.array_equal(s.get_conserved(), U0)
+    # a second simulation of the same size takes the cached choice
+    s2 = moses.from_config(cfg, precision=precision)
+    assert s2.autotune(timings=False) == (tile, None)
+    with pytest.raises(moses.MosesError):
+        s2.set_tile(3)
