@@ -73,7 +73,10 @@ typedef struct {
     int k_mode;          /* 0: earth-pressure coefficient 1 as in App. A (only
                             value accepted)                                       */
     double c_d;          /* interphase drag c_D [s^-1] (Eqs. Src_v_Topo, SrcF_v)  */
-    double nu_f;         /* fluid viscosity eps/N_R [m^2 s^-1] (Eq. SrcF_vis_Topo)*/
+    double nu_f;         /* fluid viscosity eps/N_R [m^2 s^-1] (Eq. SrcF_vis_Topo);
+                            > 0 runs the 32 x 8 viscous form of the stage; not
+                            accepted by moses_batch_create, moses_adjoint_misfit,
+                            moses_step_static                                    */
     double k_f;          /* fluid basal friction vartheta_b/(eps N_R) [s^-1]      */
     double cfl;          /* Courant number (the paper uses 0.1, Sect. 2.2)        */
     double dt_max;       /* time step cap, and the step of a dry domain [s]       */

@@ -62,7 +62,10 @@ inline int grid_for(long long n, int block = 256)
     return (int)b;
 }
 
-inline int geo_planes(const moses_sim *s) { return s->prec == MOSES_FP32 ? GEO_PLANES_F32 : GEO_PLANES; }
+// the slope planes: always in FP32 (its stage rebuilds the geometry from
+// them), in FP64 only for the viscous term (face metric in the tile)
+inline bool has_slopes(const moses_sim *s) { return s->prec == MOSES_FP32 || s->p.nu_f > 0.0; }
+inline int geo_planes(const moses_sim *s) { return has_slopes(s) ? (int)GEO_PLANES_F32 : (int)GEO_PLANES; }
 
 // remainder planes (FP32 form) that follow the six state planes of a buffer
 template <typename T>

@@ -71,7 +71,7 @@ struct Slopes {
 
 template <typename T>
 __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, long long plane, double dx,
-                                double dy, Phys ph, T *geo)
+                                double dy, Phys ph, T *geo, int with_slopes)
 {
     const int W = nx + 4, H = ny + 4;  // padded cell range [-2, n+2)
     const long long n = (long long)W * H;
@@ -145,7 +145,7 @@ __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, l
             put(GY_FN2, g, 2.0 * ph.kap_f * An);
             put(GY_HG, g, ph.half_g * c2);
         }
-        if constexpr (sizeof(T) == 4) {
+        if (with_slopes) {
             const Slopes s = slopes(i, j);
             put(GS_SX, g, s.bX);
             put(GS_SY, g, s.bY);
@@ -379,7 +379,7 @@ static int check_params(const moses_params *p, std::string &why)
     if (!(fin(p->delta_b_deg) && p->delta_b_deg >= 0 && p->delta_b_deg < 90)) return why = "delta_b in [0, 90)", 1;
     if (p->k_mode != 0) return why = "only k_mode = 0 (earth-pressure coefficient 1, App. A) is implemented", 1;
     if (!(fin(p->c_d) && p->c_d >= 0)) return why = "c_d must be >= 0", 1;
-    if (!(fin(p->nu_f) && p->nu_f == 0)) return why = "nu_f > 0 is not implemented on the GPU path", 1;
+    if (!(fin(p->nu_f) && p->nu_f >= 0)) return why = "nu_f must be >= 0", 1;
     if (!(fin(p->k_f) && p->k_f >= 0)) return why = "k_f must be >= 0", 1;
     if (!(fin(p->cfl) && p->cfl > 0)) return why = "cfl must be > 0", 1;
     if (!(fin(p->dt_max) && p->dt_max > 0)) return why = "dt_max must be > 0", 1;
@@ -512,10 +512,10 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
         const long long ng = (long long)(nx + 4) * (ny + 4);
         if (s->prec == MOSES_FP64)
             geometry_kernel<double><<<grid_for(ng), 256, 0, s->stream>>>(d_ext, nx, ny, s->pitch, s->plane, dx, dy,
-                                                                         s->ph, (double *)s->geo);
+                                                                         s->ph, (double *)s->geo, has_slopes(s));
         else
             geometry_kernel<float><<<grid_for(ng), 256, 0, s->stream>>>(d_ext, nx, ny, s->pitch, s->plane, dx, dy,
-                                                                        s->ph, (float *)s->geo);
+                                                                        s->ph, (float *)s->geo, 1);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1058,6 +1058,7 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     std::string why;
     if (check_params(p, why)) return fail(s, MOSES_EINVAL, why);
     if (p->precision != MOSES_FP64) return fail(s, MOSES_EINVAL, "moses_step_static runs the FP64 form only");
+    if (p->nu_f != 0.0) return fail(s, MOSES_EINVAL, "moses_step_static: nu_f must be 0");
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(s, MOSES_EINVAL, "device ordinal out of range");
@@ -1086,7 +1087,7 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     extend_dem_kernel<<<grid_for((long long)(nx + 6) * (ny + 6)), 256, 0, st>>>(dem_device, nx, ny, bext);
     const Phys phs = make_phys(p, dx, dy);
     geometry_kernel<double><<<grid_for((long long)(nx + 4) * (ny + 4)), 256, 0, st>>>(bext, nx, ny, pitch, plane, dx,
-                                                                                     dy, phs, geo);
+                                                                                     dy, phs, geo, 0);
     unpack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U_in_device, U, nullptr, nx, ny, pitch, plane);
     CK(cudaGetLastError());
     StageArgs<double> a{};
@@ -1259,6 +1260,7 @@ int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out)
         if (sims[k]->prec != sims[0]->prec) return batch_fail(nullptr, MOSES_EINVAL, "members must share the precision");
         if (sims[k]->stream != sims[0]->stream) return batch_fail(nullptr, MOSES_EINVAL, "members must share the stream");
         if (!sims[k]->have_state) return batch_fail(nullptr, MOSES_ESTATE, "member without a state");
+        if (sims[k]->p.nu_f != 0.0) return batch_fail(nullptr, MOSES_EINVAL, "members must have nu_f = 0");
         for (int q = 0; q < k; q++)
             if (sims[q] == sims[k]) return batch_fail(nullptr, MOSES_EINVAL, "a simulation appears twice");
     }

@@ -58,9 +58,9 @@ enum GeoPlane : int {
     GY_HG,      //   (g/2) c^2
     GEO_PLANES
 };
-// FP32 form only: four more planes from which the stage kernel rebuilds the
-// cell and face geometry in the tile (the same formulas as the geometry pass,
-// in FP32): the cell's central slopes bX, bY and the face-normal differences
+// FP32 form (and FP64 with the viscous term): four more planes from which the
+// stage kernel rebuilds the cell and face geometry in the tile (the same
+// formulas as the geometry pass): the cell's central slopes bX, bY and the face-normal differences
 // (b_{i+1,j} - b_{i,j}) / dx, (b_{i,j+1} - b_{i,j}) / dy.  Curvatures follow
 // as differences of these: bXX from DBX, bYY from DBY, bXY from SY along X.
 enum SlopePlane : int { GS_SX = GEO_PLANES, GS_SY, GS_DBX, GS_DBY, GEO_PLANES_F32 };
@@ -114,6 +114,8 @@ struct KT {
     T eps_chi, eps_alpha, eps, alpha, c_d, k_f, hinv_dx, hinv_dy, tan_delta;
     // geometry rebuilt from slopes (FP32 form)
     T kap_s, kap_f, kap_f2, half_g, g_1ma, g, h_dry, inv_dx, inv_dy, inv_2dx;
+    // viscous term (Eq. SrcF_vis_Topo): nu_f, 1/(2 dy)
+    T nu_f, inv_2dy;
     double tan_delta_d;
 };
 
@@ -140,6 +142,8 @@ inline KT<T> make_kt(const Phys &p)
     k.inv_dx = (T)p.inv_dx;
     k.inv_dy = (T)p.inv_dy;
     k.inv_2dx = (T)(0.5 * p.inv_dx);
+    k.nu_f = (T)p.nu_f;
+    k.inv_2dy = (T)(0.5 * p.inv_dy);
     k.tan_delta_d = p.tan_delta;
     return k;
 }

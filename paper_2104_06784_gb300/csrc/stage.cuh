@@ -340,6 +340,42 @@ __device__ void write_ghosts(T *U, const T *geo, const StageArgs<T> &a, int i, i
             }
         }
     }
+    // corners: the S/N rule applied to the W/E mirror or copy ghosts (inflow
+    // segments do not reach them); read only by the viscous stencil
+    if ((i < 2 || i >= nx - 2) && (j < 2 || j >= ny - 2)) {
+#pragma unroll
+        for (int sx = 0; sx < 2; sx++) {
+            const bool cx = ph.bc[sx] == 0;
+            for (int kx = 0; kx < GH; kx++) {
+                const int gi = sx == 0 ? -1 - kx : nx + kx;
+                int srcx;
+                if (sx == 0) srcx = cx ? (kx < nx ? kx : nx - 1) : 0;
+                else srcx = cx ? (nx - 1 - kx >= 0 ? nx - 1 - kx : 0) : nx - 1;
+                if (srcx != i) continue;
+#pragma unroll
+                for (int sy = 2; sy < 4; sy++) {
+                    const bool cy = ph.bc[sy] == 0;
+                    for (int ky = 0; ky < GH; ky++) {
+                        const int gj = sy == 2 ? -1 - ky : ny + ky;
+                        int srcy;
+                        if (sy == 2) srcy = cy ? (ky < ny ? ky : ny - 1) : 0;
+                        else srcy = cy ? (ny - 1 - ky >= 0 ? ny - 1 - ky : 0) : ny - 1;
+                        if (srcy != j) continue;
+                        T u[6] = {v[0], v[1], v[2], v[3], v[4], v[5]};
+                        if (cx) {
+                            u[1] = -u[1];
+                            u[4] = -u[4];
+                        }
+                        if (cy) {
+                            u[2] = -u[2];
+                            u[5] = -u[5];
+                        }
+                        store6(U, plane, cell_index(gi, gj, pitch), u);
+                    }
+                }
+            }
+        }
+    }
 }
 
 // Largest cell-centre wave speed of a state (R7), both phases, both axes,
@@ -486,7 +522,7 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
 // ---- the stage kernel -------------------------------------------------------------
 // One stage on the tile (bx, by) of the simulation described by `a`; nb is the
 // number of CTAs working on that simulation in this launch (for the ticket).
-template <typename T, int TX, int TY, bool REC = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
     constexpr int NT = TX * TY;
@@ -500,10 +536,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     T *sHx = sSy + 6 * NSY;                    // [7][TY][TX+1]   2 x flux, 2 x P
     T *sHy = sHx + 7 * NXF;                    // [7][TY+1][TX]
     // FP32 form: bed slopes of the tile + 1-cell halo, [4][TY+2][TX+2]
-    // (SX, SY, DBX, DBY); the geometry is rebuilt from them
+    // (SX, SY, DBX, DBY); the geometry is rebuilt from them.  With the viscous
+    // term (both forms) also the fluid velocities of the same cells, [2][..].
     constexpr bool GL = sizeof(T) == 4;
+    constexpr bool SL = GL || VIS;
     constexpr int BW = TX + 2, NB = (TX + 2) * (TY + 2);
     T *sB = sHy + 7 * NYF;
+    T *sVf = sB + 4 * NB;
     auto SB = [&](int c, int cx, int cy) -> T { return sB[c * NB + cy * BW + cx]; };
     __shared__ T red[NT / 32];
     __shared__ double acc[4];
@@ -549,7 +588,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         const bool ok = gi < nx + 2 && gj < ny + 2;
         cp_async_elem(sU + e, a.Uin + (ok ? c * plane + cell_index(gi, gj, pitch) : 0), ok);
     }
-    if constexpr (GL) {
+    if constexpr (SL) {
         for (int e = tid; e < 4 * NB; e += NT) {  // cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
             const int c = e / NB, r = e - c * NB;
             const int ly = r / BW, lx = r - ly * BW;
@@ -562,6 +601,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     __syncthreads();
     const double t_now = s_t, dt = s_dt;
     const T dtT = s_dtT;
+    if constexpr (VIS) {
+        // fluid velocity of every cell of the slope tile (0 where the fluid is
+        // dry), with the same dry threshold as the cell update
+        for (int q = tid; q < NB; q += NT) {
+            const int ly = q / BW, lx = q - ly * BW;
+            const int gi = x0 - 1 + lx, gj = y0 - 1 + ly;
+            const int o = (ly + 1) * SW + lx + 1;
+            T jhdn;
+            if constexpr (GL) {
+                const float sx = SB(0, lx, ly), sy = SB(1, lx, ly);
+                const float s2 = fmaf(sx, sx, fmaf(sy, sy, 1.0f));
+                jhdn = s2 * frsqrt(s2) * k.h_dry;
+            } else {
+                jhdn = (gi <= nx + 1 && gj <= ny + 1) ? geo[GC_JHD * plane + cell_index(gi, gj, pitch)] : T(1);
+            }
+            const T u3 = sU[3 * SP + o];
+            const T rf = gtp(u3, jhdn) ? frcp(u3) : T(0);
+            sVf[q] = sU[4 * SP + o] * rf;
+            sVf[NB + q] = sU[5 * SP + o] * rf;
+        }
+    }
 
     // ---- minmod slopes, once per cell and direction -----------------------
     for (int e = tid; e < 6 * NSX; e += NT) {  // cells x0-1 .. x0+TX, rows y0 .. y0+TY-1
@@ -734,6 +794,57 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         S[2] = fma(Jpbs, nY, fma(bs, gY, aD * dvY));
         S[4] = fma(Jpbf, nX, fma(bf, gX, -fma(D, dvX, ff * vXf)));
         S[5] = fma(Jpbf, nY, fma(bf, gY, -fma(D, dvY, ff * vYf)));
+        if constexpr (VIS) {
+            // viscous term s_vis^f = nu_f phi^f (s_vis,X, s_vis,Y) (Eq. SrcF_vis_Topo):
+            // brackets J h (A grad v) on the four faces (face-normal differences,
+            // transverse derivatives as the mean of the two cells' central
+            // differences; face metric from the face slopes), differenced
+            if (gtp(Ut, jhd) && gtp(u[3], jhd)) {
+                const int cx = lx + 1, cy = ly + 1;
+                const auto V = [&](int m, int ddx, int ddy) -> T { return sVf[m * NB + (cy + ddy) * BW + cx + ddx]; };
+                const auto JH = [&](int ddx, int ddy) -> T {
+                    const int o = (ly + 2 + ddy) * SW + lx + 2 + ddx;
+                    return sU[o] + sU[3 * SP + o];
+                };
+                T brX[2][2], brY[2][2];
+#pragma unroll
+                for (int sd = 0; sd < 2; sd++) {
+                    const int l = sd - 1;  // lower cell of the face, offset along the normal
+                    {   // x-face between cells i+l and i+l+1
+                        const T bn = SB(2, cx + l, cy), bt = T(0.5) * (SB(1, cx + l, cy) + SB(1, cx + l + 1, cy));
+                        const T r2 = frcp(fma(bn, bn, fma(bt, bt, T(1))));
+                        const T A11 = fma(bt, bt, T(1)) * r2, A12 = -bn * bt * r2, A22 = fma(bn, bn, T(1)) * r2;
+                        const T Jh = T(0.5) * (JH(l, 0) + JH(l + 1, 0));
+                        T dX[2], dY[2];
+#pragma unroll
+                        for (int m = 0; m < 2; m++) {
+                            dX[m] = (V(m, l + 1, 0) - V(m, l, 0)) * k.inv_dx;
+                            dY[m] = T(0.5) * ((V(m, l, 1) - V(m, l, -1)) + (V(m, l + 1, 1) - V(m, l + 1, -1))) * k.inv_2dy;
+                        }
+                        brX[sd][0] = Jh * fma(A11, dX[0], A12 * dY[0]);
+                        brX[sd][1] = Jh * fma(A12, dX[0], fma(A22, dY[0], fma(A11, dX[1], A12 * dY[1])));
+                    }
+                    {   // y-face between cells j+l and j+l+1
+                        const T bn = SB(3, cx, cy + l), bt = T(0.5) * (SB(0, cx, cy + l) + SB(0, cx, cy + l + 1));
+                        const T r2 = frcp(fma(bn, bn, fma(bt, bt, T(1))));
+                        const T A11 = fma(bn, bn, T(1)) * r2, A12 = -bn * bt * r2, A22 = fma(bt, bt, T(1)) * r2;
+                        const T Jh = T(0.5) * (JH(0, l) + JH(0, l + 1));
+                        T dX[2], dY[2];
+#pragma unroll
+                        for (int m = 0; m < 2; m++) {
+                            dY[m] = (V(m, 0, l + 1) - V(m, 0, l)) * k.inv_dy;
+                            dX[m] = T(0.5) * ((V(m, 1, l) - V(m, -1, l)) + (V(m, 1, l + 1) - V(m, -1, l + 1))) * k.inv_2dx;
+                        }
+                        brY[sd][0] = Jh * fma(A12, dX[0], fma(A22, dY[0], fma(A11, dX[1], A12 * dY[1])));
+                        brY[sd][1] = Jh * fma(A12, dX[1], A22 * dY[1]);
+                    }
+                }
+                const T svX = fma(T(2) * (brX[1][0] - brX[0][0]), k.inv_dx, (brY[1][0] - brY[0][0]) * k.inv_dy);
+                const T svY = fma(T(2) * (brY[1][1] - brY[0][1]), k.inv_dy, (brX[1][1] - brX[0][1]) * k.inv_dx);
+                S[4] = fma(k.nu_f * phf, svX, S[4]);
+                S[5] = fma(k.nu_f * phf, svY, S[5]);
+            }
+        }
         T out[6];
         T lo[2] = {T(0), T(0)};  // FP32: rounding remainders of the masses
 #pragma unroll
@@ -869,10 +980,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
 }
 
-template <typename T, int TX, int TY, bool REC = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
 {
-    stage_tile<T, TX, TY, REC>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+    stage_tile<T, TX, TY, REC, VIS>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // Ensemble form: one launch runs the same stage of many simulations.  Each CTA
@@ -900,12 +1011,14 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
     stage_tile<T, TX, TY>(sa, w.bx, w.by, w.nb);
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool VIS = false>
 constexpr size_t stage_smem_bytes()
 {
-    // state halo tile, slopes, face fluxes; FP32: bed-slope tile
+    // state halo tile, slopes, face fluxes; FP32 or viscous: bed-slope tile;
+    // viscous: fluid velocities of the slope tile
     return sizeof(T) * (6 * (TX + 4) * (TY + 4) + 6 * (TX + 2) * TY + 6 * TX * (TY + 2) + 7 * (TX + 1) * TY +
-                        7 * TX * (TY + 1) + (sizeof(T) == 4 ? 4 * (TX + 2) * (TY + 2) : 0));
+                        7 * TX * (TY + 1) + ((sizeof(T) == 4 || VIS) ? 4 * (TX + 2) * (TY + 2) : 0) +
+                        (VIS ? 2 * (TX + 2) * (TY + 2) : 0));
 }
 
 }  // namespace moses

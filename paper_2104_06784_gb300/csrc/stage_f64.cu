@@ -6,21 +6,21 @@
 namespace moses {
 namespace {
 
-template <typename T, int TX, int TY, bool REC = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false>
 int launch_tile(const StageArgs<T> &a, cudaStream_t st)
 {
-    constexpr size_t smem = stage_smem_bytes<T, TX, TY>();
+    constexpr size_t smem = stage_smem_bytes<T, TX, TY, VIS>();
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC, VIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return -1;
         attr_set[dev] = true;
     }
     const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-    stage_kernel<T, TX, TY, REC><<<grid, TX * TY, smem, st>>>(a);
+    stage_kernel<T, TX, TY, REC, VIS><<<grid, TX * TY, smem, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -31,6 +31,7 @@ template <>
 int launch_stage<double>(const StageArgs<double> &a, int tile, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
+    if (a.ph.nu_f > 0.0) return launch_tile<double, 32, 8, false, true>(a, st);  // viscous form: one tile shape
     switch (tile) {
     case 1: return launch_tile<double, 32, 4>(a, st);
     case 2: return launch_tile<double, 32, 16>(a, st);

@@ -235,6 +235,51 @@ def test_inflow_fp32_mass_budget():
 
 
 # ----------------------------------------------------------------------------
+# viscous term of the fluid (Eq. SrcF_vis_Topo): a 3 x 3 stencil of fluid
+# velocities, so ghost corners take part
+
+
+@pytest.mark.parametrize("nx,ny", [(77, 53), (33, 9), (1, 17), (5, 2)])
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (0, 1, 1, 0)])
+def test_stage_parity_viscous_fp64(nx, ny, bc):
+    rng = np.random.default_rng(nx * 7 + ny)
+    dem = W.spectral_dem(nx, ny, 5.0, 2.2, 40.0, seed=nx + 3 * ny) + rng.random((ny, nx))
+    cfg = _random_case(nx, ny, dem, bc, seed=nx * ny + 11, nu_f=2.0)
+    g, o = both(cfg)
+    for t, dt in ((0.0, 0.01), (3.0, 0.05)):
+        err = rel_maxnorm(g.stage(t, dt), o.stage(t, dt))
+        assert err < TOL64, f"viscous stage parity {err} ({nx}x{ny}, bc={bc})"
+    # the term acts: without it the oracle's stage differs
+    o0 = oracle_from_config(dict(cfg, params=dict(cfg["params"], nu_f=0.0)))
+    if nx > 2 and ny > 2:
+        assert rel_maxnorm(o0.stage(0.0, 0.01), o.stage(0.0, 0.01)) > 1e-7
+
+
+def test_viscous_trajectories():
+    """Arc-plane release with nu_f = 1 m^2/s, 300 steps at CFL 0.1: the FP64
+    form at 1e-10, the FP32 form at 2e-4 (depth, velocities on cells > 1 cm)
+    and 1e-7 mass drift."""
+    cfg = W.release_config(nx=64, ny=64, cfl=0.1, nu_f=1.0)
+    g, o = both(cfg)
+    g.step(300)
+    o.step(300)
+    err = rel_maxnorm(g.get_conserved(), o.get_U())
+    assert err < TOL64, err
+    for m, errs in _fp32_vs_oracle(cfg, (300,)).items():
+        for k, v in errs.items():
+            assert v <= (1e-7 if k == "drift" else 2e-4), (k, v)
+
+
+def test_viscous_not_in_batch_or_adjoint():
+    cfg = W.release_config(nx=20, ny=20, nu_f=1.0)
+    a = moses.from_config(cfg)
+    with pytest.raises(moses.MosesError):
+        moses.Batch([a])
+    with pytest.raises(moses.MosesError):
+        a.adjoint_misfit(5, np.zeros((20, 20)))
+
+
+# ----------------------------------------------------------------------------
 # edge cases
 
 
