@@ -206,22 +206,44 @@ def measure(sim, cells, K, W, torch):
     return ms, stage_ms
 
 
-def measure_ensemble(K, Wm, seed=0, n=256):
+def reduce_over_ranks(x, op="max", dist=None, device="cpu"):
+    """max (or sum) of a scalar over the ranks; x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard(items, rank, world):
+    """The members of an ensemble that one rank advances: every world-th one
+    from `rank` (independent problems, no data-path exchange)."""
+    return list(items)[rank::world]
+
+
+def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="cpu"):
     """Batched ensemble, FP32: 256 members on square grids of lognormal side
     (64..1024 cells, 5 m), each its own spectral DEM, basal friction, drag and
     release volume; one batched launch per stage replayed from a CUDA graph.
-    Device time from CUDA events on the batch's stream."""
+    Device time from CUDA events on the batch's stream.  With several ranks
+    the members are sharded across them; the time is the max over ranks."""
     from paper_2104_06784_gb300 import moses, workloads as W
-    cfgs = W.ensemble_config(n, seed=seed)
-    cells = int(sum(c["dem"].size for c in cfgs))
+    cfgs = shard(W.ensemble_config(n, seed=seed), rank, world)
+    cells_rank = int(sum(c["dem"].size for c in cfgs))
     sims = [moses.from_config(c, precision=moses.FP32) for c in cfgs]
     with moses.Batch(sims) as b:
         b.step(Wm)
+        if dist is not None:
+            dist.barrier()
         ms = b.step_timed(K)
         tiles = b.tiles
     for s_ in sims:
         s_.close()
+    ms = reduce_over_ranks(ms, "max", dist, device)
+    cells = int(reduce_over_ranks(cells_rank, "sum", dist, device))
     return {"value": cells * K / (ms / 1e3), "unit": "cell-steps/s", "members": n, "cells": cells,
+            "members_per_rank": len(cfgs), "scaling": "strong" if world > 1 else None,
             "ms_per_step": ms / K, "steps": K, "warmup": Wm, "dtype": "f32", "gpu_launches": 2 * K,
             "tiles_per_launch": tiles,
             "config": "256 scenarios, sides clip(round16(lognormal(ln 256, ln4/2)), 64, 1024), dx 5 m, "
@@ -324,11 +346,7 @@ def main():
     K, Wm = args.steps, args.warmup
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", dist, "cuda")
 
     results = {}
     sampler = ClockSampler(local)
@@ -404,9 +422,7 @@ def main():
                "calls": "moses_set_conserved + moses_step(1) + moses_get_conserved, pinned host buffers"}
     f64["sim"].close()
 
-    ens = None if args.no_ensemble else measure_ensemble(K, Wm)
-    if ens is not None and world > 1:
-        ens["value"] = world * ens["value"]
+    ens = None if args.no_ensemble else measure_ensemble(K, Wm, rank=rank, world=world, dist=dist, device="cuda")
 
     adj = None if args.no_adjoint else measure_adjoint(torch)
 
