@@ -117,10 +117,8 @@ __device__ __forceinline__ int minmod_sel(double a, double b)
 }
 __device__ __forceinline__ int minmod_sel(float a, float b)
 {
-    const int ia = ibits(a), ib = ibits(b);
-    const int ma = ia & 0x7fffffff, mb = ib & 0x7fffffff;
-    if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0;
-    return ma < mb ? 1 : 2;
+    if (!(a * b > 0.0f)) return 0;  // as the FP32 minmod
+    return fabsf(a) < fabsf(b) ? 1 : 2;
 }
 
 // Arguments of the adjoint kernels

@@ -74,12 +74,12 @@ __device__ __forceinline__ double minmod(double a, double b)
     if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0.0;
     return ma < mb ? a : b;
 }
+// FP32: the sign test as a product (a b > 0: same sign, both nonzero; a
+// product that underflows counts as 0), the rest on magnitudes
 __device__ __forceinline__ float minmod(float a, float b)
 {
-    const int ia = ibits(a), ib = ibits(b);
-    const int ma = ia & 0x7fffffff, mb = ib & 0x7fffffff;
-    if ((ia ^ ib) < 0 || ma == 0 || mb == 0) return 0.0f;
-    return ma < mb ? a : b;
+    const float m = fabsf(a) < fabsf(b) ? a : b;
+    return a * b > 0.0f ? m : 0.0f;
 }
 
 // ---- reciprocal and square root ---------------------------------------------
@@ -580,21 +580,47 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     if (tid < 4) acc[tid] = 0.0;
 
     // ---- stage the tile + 2-cell halo of the six state planes -----------
-    // (asynchronous copies: every element of the thread in flight at once)
-    for (int e = tid; e < 6 * SP; e += NT) {
-        const int c = e / SP, r = e - c * SP;
-        const int ly = r / SW, lx = r - ly * SW;
-        const int gi = x0 - 2 + lx, gj = y0 - 2 + ly;
-        const bool ok = gi < nx + 2 && gj < ny + 2;
-        cp_async_elem(sU + e, a.Uin + (ok ? c * plane + cell_index(gi, gj, pitch) : 0), ok);
+    // (asynchronous copies: every element of the thread in flight at once).
+    // Each thread copies its own cell, then one cell of the halo if any, so
+    // that only the halo needs index arithmetic.
+    {
+        const auto copy_state = [&](int tx, int ty) {  // tile coordinates, -2 .. TX+1 / TY+1
+            const int gi = x0 + tx, gj = y0 + ty;
+            const bool ok = gi < nx + 2 && gj < ny + 2;
+            const T *src = a.Uin + (ok ? cell_index(gi, gj, pitch) : 0);
+            T *dst = sU + (ty + 2) * SW + tx + 2;
+#pragma unroll
+            for (int c = 0; c < 6; c++) cp_async_elem(dst + c * SP, src + (ok ? c * plane : 0), ok);
+        };
+        copy_state(tid % TX, tid / TX);
+        constexpr int RW = 2 * SW;  // cells in two full halo rows
+        for (int h = tid; h < SP - NT; h += NT) {
+            if (h < RW) copy_state(h % SW - 2, h / SW - 2);                  // rows -2, -1
+            else if (h < 2 * RW) copy_state((h - RW) % SW - 2, TY + (h - RW) / SW);  // rows TY, TY+1
+            else {                                                            // columns -2, -1, TX, TX+1
+                const int r = h - 2 * RW, k = r & 3;
+                copy_state(k < 2 ? k - 2 : TX + k - 2, r >> 2);
+            }
+        }
     }
     if constexpr (SL) {
-        for (int e = tid; e < 4 * NB; e += NT) {  // cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
-            const int c = e / NB, r = e - c * NB;
-            const int ly = r / BW, lx = r - ly * BW;
-            const int gi = x0 - 1 + lx, gj = y0 - 1 + ly;
+        // slope tile: cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
+        const auto copy_slopes = [&](int tx, int ty) {  // tile coordinates, -1 .. TX / TY
+            const int gi = x0 + tx, gj = y0 + ty;
             const bool ok = gi <= nx && gj <= ny;
-            cp_async_elem(sB + e, geo + (ok ? (GS_SX + c) * plane + cell_index(gi, gj, pitch) : 0), ok);
+            const T *src = geo + (ok ? GS_SX * plane + cell_index(gi, gj, pitch) : 0);
+            T *dst = sB + (ty + 1) * BW + tx + 1;
+#pragma unroll
+            for (int c = 0; c < 4; c++) cp_async_elem(dst + c * NB, src + (ok ? c * plane : 0), ok);
+        };
+        copy_slopes(tid % TX, tid / TX);
+        for (int h = tid; h < NB - NT; h += NT) {
+            if (h < BW) copy_slopes(h - 1, -1);                  // row -1
+            else if (h < 2 * BW) copy_slopes(h - BW - 1, TY);    // row TY
+            else {                                               // columns -1 and TX
+                const int r = h - 2 * BW;
+                copy_slopes((r & 1) ? TX : -1, r >> 1);
+            }
         }
     }
     cp_async_wait_all();
@@ -624,17 +650,34 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
 
     // ---- minmod slopes, once per cell and direction -----------------------
-    for (int e = tid; e < 6 * NSX; e += NT) {  // cells x0-1 .. x0+TX, rows y0 .. y0+TY-1
-        const int c = e / NSX, r = e - c * NSX;
-        const int ly = r / (TX + 2), lx = r - ly * (TX + 2);
-        const T *p = sU + c * SP + (ly + 2) * SW + lx + 1;
-        sSx[e] = minmod(p[0] - p[-1], p[1] - p[0]);
-    }
-    for (int e = tid; e < 6 * NSY; e += NT) {  // rows y0-1 .. y0+TY, cells x0 .. x0+TX-1
-        const int c = e / NSY, r = e - c * NSY;
-        const int ly = r / TX, lx = r - ly * TX;
-        const T *p = sU + c * SP + (ly + 1) * SW + lx + 2;
-        sSy[e] = minmod(p[0] - p[-SW], p[SW] - p[0]);
+    // sSx[c][ly][lx'] holds the x-slope of cell (x0-1+lx', y0+ly), sSy[c][ly'][lx]
+    // the y-slope of cell (x0+lx, y0-1+ly').  Each thread takes both slopes of
+    // its own cell, then a share of the halo ones (x: columns -1 and TX; y:
+    // rows -1 and TY), so that only the halo needs index arithmetic.
+    {
+        const int lx = tid % TX, ly = tid / TX;
+        const T *p = sU + (ly + 2) * SW + lx + 2;
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            const T *q = p + c * SP;
+            sSx[c * NSX + ly * (TX + 2) + lx + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
+            sSy[c * NSY + (ly + 1) * TX + lx] = minmod(q[0] - q[-SW], q[SW] - q[0]);
+        }
+        constexpr int NHX = 2 * TY, NHY = 2 * TX, NH1 = NHX + NHY;
+        for (int e = tid; e < 6 * NH1; e += NT) {
+            const int c = e / NH1;
+            int r = e - c * NH1;
+            if (r < NHY) {  // y-slopes of rows -1 (r < TX) and TY
+                const int side = r / TX, col = r - side * TX, row = side ? TY : -1;
+                const T *q = sU + c * SP + (row + 2) * SW + col + 2;
+                sSy[c * NSY + (row + 1) * TX + col] = minmod(q[0] - q[-SW], q[SW] - q[0]);
+            } else {  // x-slopes of columns -1 and TX
+                r -= NHY;
+                const int row = r >> 1, col = (r & 1) ? TX : -1;
+                const T *q = sU + c * SP + (row + 2) * SW + col + 2;
+                sSx[c * NSX + row * (TX + 2) + col + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
+            }
+        }
     }
     __syncthreads();
 
