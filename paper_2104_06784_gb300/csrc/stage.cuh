@@ -681,11 +681,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
     __syncthreads();
 
-    // ---- x-faces (i+1/2, j), i = x0-1 .. x0+TX-1 ---------------------------
-    for (int f = tid; f < NXF; f += NT) {
-        const int ly = f / (TX + 1), lx = f - ly * (TX + 1);
+    // ---- faces: x-faces (i+1/2, j), i = x0-1 .. x0+TX-1, at sHx[c][ly][lx],
+    // lx = i - x0 + 1; y-faces (i, j+1/2), j = y0-1 .. y0+TY-1, at
+    // sHy[c][ly][lx], ly = j - y0 + 1.  Each thread takes the right and the
+    // upper face of its own cell; warp 0 the left faces of column 0, warp 1
+    // the lower faces of row 0 (every warp then runs at most three faces).
+    const auto x_face = [&](const int lx, const int ly) {
         const int i = x0 + lx - 1, j = y0 + ly;
-        if (j >= ny || i >= nx) continue;
+        if (j >= ny || i >= nx) return;
+        const int f = ly * (TX + 1) + lx;
         FaceGeo<T> G;
         if constexpr (GL) {  // lower cell at (lx, ly + 1) of the slope tile
             G = face_geo32(SB(2, lx, ly + 1), 0.5f * (SB(1, lx, ly + 1) + SB(1, lx + 1, ly + 1)), k);
@@ -718,12 +722,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             atomicAdd(&acc[0], w * (double)H[0]);
             atomicAdd(&acc[1], w * (double)H[3]);
         }
-    }
-    // ---- y-faces (i, j+1/2), j = y0-1 .. y0+TY-1 ---------------------------
-    for (int f = tid; f < NYF; f += NT) {
-        const int ly = f / TX, lx = f - ly * TX;
+    };
+    const auto y_face = [&](const int lx, const int ly) {
         const int i = x0 + lx, j = y0 + ly - 1;
-        if (i >= nx || j >= ny) continue;
+        if (i >= nx || j >= ny) return;
+        const int f = ly * TX + lx;
         FaceGeo<T> G;
         if constexpr (GL) {  // lower cell at (lx + 1, ly) of the slope tile
             G = face_geo32(SB(3, lx + 1, ly), 0.5f * (SB(0, lx + 1, ly) + SB(0, lx + 1, ly + 1)), k);
@@ -754,7 +757,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             atomicAdd(&acc[0], w * (double)H[0]);
             atomicAdd(&acc[1], w * (double)H[3]);
         }
-    }
+    };
+    static_assert(NT >= 32 + TX && TY <= 32, "face assignment needs warps 0 and 1");
+    x_face(tid % TX + 1, tid / TX);
+    y_face(tid % TX, tid / TX + 1);
+    if (tid < TY) x_face(0, tid);
+    else if (tid >= 32 && tid < 32 + TX) y_face(tid - 32, 0);
     __syncthreads();
 
     // ---- cell update ------------------------------------------------------
