@@ -364,6 +364,29 @@ struct FaceAdjSmem {
     static constexpr size_t bytes = base + (STAGE ? sizeof(T) * (8 * LP + 7 * NF) : 0);
 };
 
+// Cell h (0 <= h < (TX + 2 HW)(TY + 2 HW) - TX TY) of the halo of width HW
+// around a TX x TY tile, in tile coordinates: the HW rows below, the HW rows
+// above, then HW columns on each side of the tile's rows.
+template <int TX, int TY, int HW>
+__device__ __forceinline__ void halo_cell(int h, int &tx, int &ty)
+{
+    constexpr int W = TX + 2 * HW, RW = HW * W;
+    if (h < RW) {
+        ty = h / W - HW;
+        tx = h - (ty + HW) * W - HW;
+    } else if (h < 2 * RW) {
+        h -= RW;
+        ty = h / W;
+        tx = h - ty * W - HW;
+        ty += TY;
+    } else {
+        h -= 2 * RW;
+        ty = h / (2 * HW);
+        const int k = h - ty * (2 * HW);
+        tx = k < HW ? k - HW : TX + k - HW;
+    }
+}
+
 template <typename T, int TX, int TY, int D>
 __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, unsigned char *sSel, T *sLum,
                                              T *sLup, T *sLs, const T *sLam, T *sG, T lres[6])
@@ -394,30 +417,48 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
     auto lidx = [&](int m, int p) {  // lam box index of line m, normal position p
         return D == 0 ? (m + 2) * LW + (p + 2) : (p + 2) * LW + (m + 2);
     };
+    // Positions (m, p): each thread takes the one of its own cell, p in [0, L),
+    // then a share of those outside the tile along the normal, p in
+    // [-nlo, 0) and [L, L + nhi), over all lines (index arithmetic only there).
+    const int m_own = D == 0 ? tid / TX : tid % TX, p_own = D == 0 ? tid % TX : tid / TX;
+    const auto extra = [&](const int nlo, const int nhi, const auto &fn) {
+        for (int e = tid; e < (nlo + nhi) * M; e += NT) {
+            const int kk = e / M, m = e - kk * M;
+            fn(m, kk < nlo ? kk - nlo : L + kk - nlo);
+        }
+    };
     if constexpr (SM::STAGE) {
         // face geometry of this direction, faces with lower cell p = -2 .. L
-        for (int e = tid; e < 7 * NF; e += NT) {
-            const int c = e / NF, r = e - c * NF;
-            const int m = r / NFl, p = r - m * NFl - 2;
+        const auto stage_g = [&](const int m, const int p) {
+            const int e = m * NFl + p + 2;
             const int lo = o0 + p, line = (D == 0 ? y0 : x0) + m;
             const bool ok = lo >= -1 && lo <= n - 1 && line < nt;
-            cp_async_elem(sG + e, ok ? geo + ((D == 0 ? GX_JHD : GY_JHD) + c) * plane + gidx(m, p) : geo, ok);
-        }
+            const T *src = ok ? geo + (D == 0 ? GX_JHD : GY_JHD) * plane + gidx(m, p) : geo;
+#pragma unroll
+            for (int c = 0; c < 7; c++) cp_async_elem(sG + c * NF + e, src + (ok ? c * plane : 0), ok);
+        };
+        stage_g(m_own, p_own);
+        extra(2, 1, stage_g);
     }
     // slopes and their selections, cells p = -2 .. L+1
-    for (int e = tid; e < 6 * NS; e += NT) {
-        const int c = e / NS, r = e - c * NS;
-        const int m = r / NSl, p = r - m * NSl - 2;
-        const T *u = sU + c * SP3 + sidx(m, p);
-        const T d1 = u[0] - u[-STEP], d2 = u[STEP] - u[0];
-        sS[e] = minmod(d1, d2);
-        sSel[e] = (unsigned char)minmod_sel(d1, d2);
-    }
+    const auto slope = [&](const int m, const int p) {
+        const int e = m * NSl + p + 2;
+        const T *u = sU + sidx(m, p);
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            const T *uc = u + c * SP3;
+            const T d1 = uc[0] - uc[-STEP], d2 = uc[STEP] - uc[0];
+            sS[c * NS + e] = minmod(d1, d2);
+            sSel[c * NS + e] = (unsigned char)minmod_sel(d1, d2);
+        }
+    };
+    slope(m_own, p_own);
+    extra(2, 2, slope);
     if constexpr (SM::STAGE) cp_async_wait_all();  // the face geometry
     __syncthreads();
     // face adjoints, faces with lower cell p = -2 .. L
-    for (int e = tid; e < NF; e += NT) {
-        const int m = e / NFl, p = e - m * NFl - 2;
+    const auto face = [&](const int m, const int p) {
+        const int e = m * NFl + p + 2;
         const int lo = o0 + p;                       // lower cell index along the normal
         const int line = (D == 0 ? y0 : x0) + m;     // index across
         const bool exists = lo >= -1 && lo <= n - 1 && line < nt;
@@ -470,15 +511,19 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
             sLum[c * NF + e] = lum[c];
             sLup[c * NF + e] = lup[c];
         }
-    }
+    };
+    face(m_own, p_own);
+    extra(2, 1, face);
     __syncthreads();
     // slope adjoints, cells p = -1 .. L: lam_sigma = (lam_um(face p) - lam_up(face p-1)) / 2
-    for (int e = tid; e < 6 * NL; e += NT) {
-        const int c = e / NL, r = e - c * NL;
-        const int m = r / NLl, p = r - m * NLl - 1;
+    const auto slope_adj = [&](const int m, const int p) {
+        const int e = m * NLl + p + 1;
         const int f = m * NFl + (p + 2);  // face with lower cell p
-        sLs[e] = T(0.5) * (sLum[c * NF + f] - sLup[c * NF + f - 1]);
-    }
+#pragma unroll
+        for (int c = 0; c < 6; c++) sLs[c * NL + e] = T(0.5) * (sLum[c * NF + f] - sLup[c * NF + f - 1]);
+    };
+    slope_adj(m_own, p_own);
+    extra(1, 1, slope_adj);
     __syncthreads();
     // gather for cell p at line m
     // p in [-2, L+1]: faces p (lower cell p) and p-1 exist in the tile's range for
@@ -500,12 +545,8 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
         return v;
     };
     // interior cell of this thread
-    {
-        const int lx = tid % TX, ly = tid / TX;
-        const int m = D == 0 ? ly : lx, p = D == 0 ? lx : ly;
 #pragma unroll
-        for (int c = 0; c < 6; c++) lres[c] += gather(m, p, c);
-    }
+    for (int c = 0; c < 6; c++) lres[c] += gather(m_own, p_own, c);
     // ghost cells beyond the domain boundary along this direction
     for (int e = tid; e < 4 * M; e += NT) {
         const int m = e / 4, w = e - m * 4;
@@ -542,25 +583,40 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
+    // each thread copies its own cell, then a share of the halo cells
     if constexpr (SM::STAGE) {
         // lam_pre (6) and lam_dp (2) of the tile and a 2-cell halo; 0 outside the domain
-        for (int e = tid; e < 8 * SM::LP; e += NT) {
-            const int c = e / SM::LP, r = e - c * SM::LP;
-            const int ly = r / SM::LW, lx = r - ly * SM::LW;
-            const int gi = x0 - 2 + lx, gj = y0 - 2 + ly;
+        const auto copy_lam = [&](const int tx, const int ty) {
+            const int gi = x0 + tx, gj = y0 + ty;
             const bool ok = gi >= 0 && gj >= 0 && gi < nx && gj < ny;
             const long long g = ok ? cell_index(gi, gj, pitch) : 0;
-            cp_async_elem(sLam + e, c < 6 ? q.lam_pre + c * plane + g : q.lam_dp + (c - 6) * plane + g, ok);
+            T *dst = sLam + (ty + 2) * SM::LW + tx + 2;
+#pragma unroll
+            for (int c = 0; c < 8; c++)
+                cp_async_elem(dst + c * SM::LP, c < 6 ? q.lam_pre + c * plane + g : q.lam_dp + (c - 6) * plane + g, ok);
+        };
+        copy_lam(tid % TX, tid / TX);
+        for (int h = tid; h < SM::LP - NT; h += NT) {
+            int tx, ty;
+            halo_cell<TX, TY, 2>(h, tx, ty);
+            copy_lam(tx, ty);
         }
     }
     // stage input with a 3-cell halo (cells beyond the 2 ghost layers read 0;
     // no forward face uses them)
-    for (int e = tid; e < 6 * SP3; e += NT) {
-        const int c = e / SP3, r = e - c * SP3;
-        const int ly = r / SW3, lx = r - ly * SW3;
-        const int gi = x0 - 3 + lx, gj = y0 - 3 + ly;
+    const auto copy_u = [&](const int tx, const int ty) {
+        const int gi = x0 + tx, gj = y0 + ty;
         const bool ok = gi >= -2 && gj >= -2 && gi < nx + 2 && gj < ny + 2;
-        cp_async_elem(sU + e, a.Uin + (ok ? c * plane + cell_index(gi, gj, pitch) : 0), ok);
+        const T *src = a.Uin + (ok ? cell_index(gi, gj, pitch) : 0);
+        T *dst = sU + (ty + 3) * SW3 + tx + 3;
+#pragma unroll
+        for (int c = 0; c < 6; c++) cp_async_elem(dst + c * SP3, src + (ok ? c * plane : 0), ok);
+    };
+    copy_u(tid % TX, tid / TX);
+    for (int h = tid; h < SP3 - NT; h += NT) {
+        int tx, ty;
+        halo_cell<TX, TY, 3>(h, tx, ty);
+        copy_u(tx, ty);
     }
     cp_async_wait_all();
     __syncthreads();
