@@ -180,22 +180,34 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
         for (int c = 0; c < 4; c++) pre4[c] = a.rec[c * plane + g];
         const T dPx = a.rec[4 * plane + g], dPy = a.rec[5 * plane + g];
         // ---- forward quantities of the cell (as in stage_tile) ----
-        const T jhd = geo[GC_JHD * plane + g];
+        // the cell geometry: FP32 rebuilt from the slope planes exactly as the
+        // FP32 stage does, FP64 read from the geometry planes
+        T jhd, kXX, kXY2, kYY, gc1, gcf, nX, nY, bX, bY, A11, A12, A22;
+        if constexpr (sizeof(T) == 4) {
+            const T *sl = geo + GS_SX * plane + g;
+            const CellGeo32 G = cell_geo32(sl[0], sl[plane], (sl[2 * plane] - sl[2 * plane - 1]) * k.inv_dx,
+                                           (sl[plane + 1] - sl[plane - 1]) * k.inv_2dx,
+                                           (sl[3 * plane] - sl[3 * plane - pitch]) * k.inv_dy, k);
+            jhd = G.jhd, kXX = G.kXX, kXY2 = G.kXY2, kYY = G.kYY, gc1 = G.gc1, gcf = G.gcf;
+            nX = G.nX, nY = G.nY, bX = G.bX, bY = G.bY, A11 = G.A11, A12 = G.A12, A22 = G.A22;
+        } else {
+            jhd = geo[GC_JHD * plane + g];
+            kXX = geo[GC_KXX * plane + g], kXY2 = geo[GC_KXY2 * plane + g], kYY = geo[GC_KYY * plane + g];
+            gc1 = geo[GC_GC1 * plane + g], gcf = geo[GC_GCF * plane + g];
+            nX = geo[GC_MNX * plane + g], nY = geo[GC_MNY * plane + g];
+            bX = geo[GC_BX * plane + g], bY = geo[GC_BY * plane + g];
+            A11 = geo[GC_A11 * plane + g], A12 = geo[GC_A12 * plane + g], A22 = geo[GC_A22 * plane + g];
+        }
         const T Ut = u[0] + u[3];
         const bool wmix = gtp(Ut, jhd), ws = gtp(u[0], jhd), wf = gtp(u[3], jhd);
         const T rUt = wmix ? frcp(Ut) : T(0);
         const T phs = u[0] * rUt, phf = u[3] * rUt;
         const T rs = ws ? frcp(u[0]) : T(0), rf = wf ? frcp(u[3]) : T(0);
         const T vXs = u[1] * rs, vYs = u[2] * rs, vXf = u[4] * rf, vYf = u[5] * rf;
-        const T kXX = geo[GC_KXX * plane + g], kXY2 = geo[GC_KXY2 * plane + g], kYY = geo[GC_KYY * plane + g];
         const T nks = fma(kXX, vXs * vXs, fma(kXY2, vXs * vYs, kYY * (vYs * vYs)));
         const T nkf = fma(kXX, vXf * vXf, fma(kXY2, vXf * vYf, kYY * (vYf * vYf)));
-        const T gc1 = geo[GC_GC1 * plane + g], gcf = geo[GC_GCF * plane + g];
         const T ps_raw = u[0] * fma(k.eps_chi, nks, gc1), pf_raw = u[3] * fma(k.eps_chi, nkf, gcf);
         const T Jpbs = pos(ps_raw);
-        const T nX = geo[GC_MNX * plane + g], nY = geo[GC_MNY * plane + g];
-        const T bX = geo[GC_BX * plane + g], bY = geo[GC_BY * plane + g];
-        const T A11 = geo[GC_A11 * plane + g], A12 = geo[GC_A12 * plane + g], A22 = geo[GC_A22 * plane + g];
         const T gX = fma(A11, dPx, A12 * dPy), gY = fma(A12, dPx, A22 * dPy);
         const bool pgf = a.ph.pg_mode == 1;
         const T bs = -k.eps_alpha * phs;
@@ -347,10 +359,11 @@ namespace moses {
 // D = 0: x-faces over rows of the tile; D = 1: y-faces over columns.  Along the
 // face normal the tile covers cells [o0 - 2, o0 + L + 1] with slopes, faces with
 // lower cell in [o0 - 2, o0 + L], slope adjoints for cells [o0 - 1, o0 + L].
-// In the FP32 form the face geometry (per direction) and the cell adjoints
-// lam_pre, lam_dp of the tile and a 2-cell halo are staged in shared memory
-// up front, so that the face loop reads no global memory; FP64 reads them in
-// the loop (its shared memory is full at two CTAs per SM).
+// In the FP32 form the bed slopes (4 planes, from which the face geometry is
+// rebuilt as the FP32 stage does) and the cell adjoints lam_pre, lam_dp of
+// the tile and a 2-cell halo are staged in shared memory up front, so that
+// the face loop reads no global memory; FP64 reads its face geometry and the
+// cell adjoints in the loop (its shared memory is full at two CTAs per SM).
 template <typename T, int TX, int TY>
 struct FaceAdjSmem {
     static constexpr bool STAGE = sizeof(T) == 4;
@@ -361,7 +374,7 @@ struct FaceAdjSmem {
     static constexpr int LW = TX + 4, LP = LW * (TY + 4);  // lam box: tile + 2-cell halo
     static constexpr size_t sel_bytes = (6 * NS + 15) / 16 * 16;
     static constexpr size_t base = sizeof(T) * (6 * SP3 + 6 * NS + 12 * NF + 6 * NL) + sel_bytes;
-    static constexpr size_t bytes = base + (STAGE ? sizeof(T) * (8 * LP + 7 * NF) : 0);
+    static constexpr size_t bytes = base + (STAGE ? sizeof(T) * (8 * LP + 4 * LP) : 0);
 };
 
 // Cell h (0 <= h < (TX + 2 HW)(TY + 2 HW) - TX TY) of the halo of width HW
@@ -389,7 +402,7 @@ __device__ __forceinline__ void halo_cell(int h, int &tx, int &ty)
 
 template <typename T, int TX, int TY, int D>
 __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, unsigned char *sSel, T *sLum,
-                                             T *sLup, T *sLs, const T *sLam, T *sG, T lres[6])
+                                             T *sLup, T *sLs, const T *sLam, const T *sBs, T lres[6])
 {
     using SM = FaceAdjSmem<T, TX, TY>;
     constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3, LW = SM::LW, LP = SM::LP;
@@ -427,19 +440,6 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
             fn(m, kk < nlo ? kk - nlo : L + kk - nlo);
         }
     };
-    if constexpr (SM::STAGE) {
-        // face geometry of this direction, faces with lower cell p = -2 .. L
-        const auto stage_g = [&](const int m, const int p) {
-            const int e = m * NFl + p + 2;
-            const int lo = o0 + p, line = (D == 0 ? y0 : x0) + m;
-            const bool ok = lo >= -1 && lo <= n - 1 && line < nt;
-            const T *src = ok ? geo + (D == 0 ? GX_JHD : GY_JHD) * plane + gidx(m, p) : geo;
-#pragma unroll
-            for (int c = 0; c < 7; c++) cp_async_elem(sG + c * NF + e, src + (ok ? c * plane : 0), ok);
-        };
-        stage_g(m_own, p_own);
-        extra(2, 1, stage_g);
-    }
     // slopes and their selections, cells p = -2 .. L+1
     const auto slope = [&](const int m, const int p) {
         const int e = m * NSl + p + 2;
@@ -454,7 +454,6 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
     };
     slope(m_own, p_own);
     extra(2, 2, slope);
-    if constexpr (SM::STAGE) cp_async_wait_all();  // the face geometry
     __syncthreads();
     // face adjoints, faces with lower cell p = -2 .. L
     const auto face = [&](const int m, const int p) {
@@ -467,10 +466,13 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
             FaceGeo<T> G;
             T lH[6], d0, d1;
             if constexpr (SM::STAGE) {
-                G = FaceGeo<T>{sG[e], sG[NF + e], sG[2 * NF + e], sG[3 * NF + e], sG[4 * NF + e], sG[5 * NF + e],
-                               sG[6 * NF + e]};
-                // cells outside the domain hold 0 in the lam box
+                // cells outside the domain hold 0 in the lam box; the slope box
+                // has the same layout (planes SX, SY, DBX, DBY)
                 const int bl = lidx(m, p), bh = lidx(m, p + 1);
+                if constexpr (D == 0)
+                    G = face_geo32(sBs[2 * LP + bl], T(0.5) * (sBs[LP + bl] + sBs[LP + bh]), q.f.k);
+                else
+                    G = face_geo32(sBs[3 * LP + bl], T(0.5) * (sBs[bl] + sBs[bh]), q.f.k);
 #pragma unroll
                 for (int c = 0; c < 6; c++) lH[c] = dtT * hinv * (sLam[c * LP + bh] - sLam[c * LP + bl]);
                 d0 = sLam[(6 + D) * LP + bl];
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     T *sLs = sLup + 6 * SM::NF;
     unsigned char *sSel = reinterpret_cast<unsigned char *>(sLs + 6 * SM::NL);
     T *sLam = reinterpret_cast<T *>(smem_raw + SM::base);  // FP32 form: [8][TY+4][TX+4]
-    T *sG = sLam + 8 * SM::LP;                              // FP32 form: [7][NF]
+    T *sBs = sLam + 8 * SM::LP;                             // FP32 form: [4][TY+4][TX+4] bed slopes
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -601,6 +603,21 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
             halo_cell<TX, TY, 2>(h, tx, ty);
             copy_lam(tx, ty);
         }
+        // bed slopes of the same box (computed for cells -2 .. n+1)
+        const auto copy_slopes = [&](const int tx, const int ty) {
+            const int gi = x0 + tx, gj = y0 + ty;
+            const bool ok = gi >= -2 && gj >= -2 && gi <= nx + 1 && gj <= ny + 1;
+            const T *src = a.geo + (ok ? GS_SX * plane + cell_index(gi, gj, pitch) : 0);
+            T *dst = sBs + (ty + 2) * SM::LW + tx + 2;
+#pragma unroll
+            for (int c = 0; c < 4; c++) cp_async_elem(dst + c * SM::LP, src + (ok ? c * plane : 0), ok);
+        };
+        copy_slopes(tid % TX, tid / TX);
+        for (int h = tid; h < SM::LP - NT; h += NT) {
+            int tx, ty;
+            halo_cell<TX, TY, 2>(h, tx, ty);
+            copy_slopes(tx, ty);
+        }
     }
     // stage input with a 3-cell halo (cells beyond the 2 ghost layers read 0;
     // no forward face uses them)
@@ -621,12 +638,22 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     cp_async_wait_all();
     __syncthreads();
     T lres[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sG, lres);
-    adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sG, lres);
+    adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
+    adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
     const int i = x0 + tid % TX, j = y0 + tid / TX;
     if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
-        const T jhd = q.heun == 1 ? a.geo[GC_JHD * plane + g] : T(0);
+        T jhd = T(0);
+        if (q.heun == 1) {
+            if constexpr (FaceAdjSmem<T, TX, TY>::STAGE) {  // as the FP32 stage: J h_dry from the slopes
+                const int o = (tid / TX + 2) * FaceAdjSmem<T, TX, TY>::LW + tid % TX + 2;
+                const T sX = sBs[o], sY = sBs[FaceAdjSmem<T, TX, TY>::LP + o];
+                const T s2 = fma(sX, sX, fma(sY, sY, T(1)));
+                jhd = s2 * frsqrt(s2) * a.k.h_dry;
+            } else {
+                jhd = a.geo[GC_JHD * plane + g];
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 6; c++) {
             T v = q.lam_acc[c * plane + g] + lres[c];
