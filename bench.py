@@ -49,9 +49,21 @@ DX = 10.0
 FLOPS_PER_CELL_STAGE = 488
 WORDS_PER_CELL_STEP = 13
 
-# DRAM traffic of one stage launch per cell from an ncu capture, valid only for
-# the stage kernel source it was taken on (sha256 of csrc/stage.cuh, first 12).
-TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one stage
+# launch per cell, from an ncu capture of the 2048 x 2048 case with the tile
+# pinned; valid only for the stage kernel source it was taken on (sha256 of
+# csrc/stage.cuh, first 12).  Traffic per cell does not depend on the grid
+# size, so a launch at side n moves n^2 times this.
+TRAFFIC = {
+    # ncu, 2048^2 spectral-DEM release, one launch each (profiles/stage_kernel_traffic_2048_release.md)
+    ("f64", "32x16", "4b0a78a3454a"): 312.01,
+    ("f32", "32x8", "4b0a78a3454a"): 72.41,
+}
+
+
+def _traffic(form, tile, h, side):
+    b = TRAFFIC.get((form, tile, h))
+    return None if b is None else b * side * side
 
 
 def peaks():
@@ -309,6 +321,8 @@ def main():
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (the workload is defined at 4096)")
     ap.add_argument("--only", choices=["f64", "f32", "adjoint"], default=None,
                     help="measure one precision form, or only the adjoint")
+    ap.add_argument("--tile", choices=["auto", "32x8", "32x4", "32x16"], default="auto",
+                    help="stage tile shape: autotuned (default) or pinned")
     ap.add_argument("--adj-steps", type=int, default=None, help="adjoint: steps (default: the workload's 5000)")
     ap.add_argument("--adj-ckpt", type=int, default=None, help="adjoint: checkpoint interval (default 71)")
     args = ap.parse_args()
@@ -356,9 +370,14 @@ def main():
     tiles = {}
     for name, prec in forms:
         sim = moses.from_config(cfg, precision=prec)
-        tile, tile_ms = sim.autotune()  # the project's tile autotuner
-        tiles[name] = {"tile": moses.Sim.TILES[tile],
-                       "ms_per_launch": {moses.Sim.TILES[t]: tile_ms[t] for t in range(3)}}
+        if args.tile == "auto":
+            tile, tile_ms = sim.autotune()  # the project's tile autotuner
+            tiles[name] = {"tile": moses.Sim.TILES[tile],
+                           "ms_per_launch": {moses.Sim.TILES[t]: tile_ms[t] for t in range(3)}}
+        else:
+            tile = {v: k for k, v in moses.Sim.TILES.items()}[args.tile]
+            sim.set_tile(tile)
+            tiles[name] = {"tile": args.tile, "pinned": True}
         if dist is not None:
             dist.barrier()
         with (sampler if name == "f64" else _Null()):
@@ -382,9 +401,10 @@ def main():
     flops_launch = FLOPS_PER_CELL_STAGE * cells
     ach = flops_launch / (f64["launch_ms"] / 1e3) / 1e12
     h = stage_hash()
+    t64, t32 = tiles["f64"]["tile"], tiles["f32"]["tile"]
     roof64 = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-              "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get(("f64", h)),
-              "kernel": "moses::stage_kernel<double,32,8>",
+              "frac": ach / FP64_PEAK_TFLOPS, "traffic": _traffic("f64", t64, h, side),
+              "kernel": f"moses::stage_kernel<double,{t64.replace('x', ',')}>",
               "peak_source": "GB300 FP64 vector rate from unit counts and clock (152 SMs x 2 DFMA/clk x 2.07 GHz)",
               "hbm": {"achieved_gbs": WORDS_PER_CELL_STEP * 8 * cells / (2 * f64["launch_ms"] / 1e3) / 1e9,
                       "peak_gbs": pk["hbm_gbs"], "peak_source": pk_src}}
@@ -392,8 +412,9 @@ def main():
     bytes_step32 = WORDS_PER_CELL_STEP * 4 * cells
     gbs32 = bytes_step32 / (2 * f32["launch_ms"] / 1e3) / 1e9
     roof32 = {"bound": "hbm", "achieved": gbs32, "peak": pk["hbm_gbs"], "unit": "GB/s",
-              "frac": gbs32 / pk["hbm_gbs"], "traffic": TRAFFIC.get(("f32", h)),
-              "kernel": "moses::stage_kernel<float,32,8>", "peak_source": pk_src}
+              "frac": gbs32 / pk["hbm_gbs"], "traffic": _traffic("f32", t32, h, side),
+              "kernel": f"moses::stage_kernel<float,{t32.replace('x', ',')}>", "peak_source": pk_src,
+              "limiter": "instruction issue (ncu: 72 % issue slots, DRAM 20 %), not bandwidth"}
 
     # end to end through the C-ABI with pinned host buffers: per step, upload
     # the state, one step, download the state
