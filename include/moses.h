@@ -119,7 +119,9 @@ int moses_set_inflow(moses_sim *s, int side, int i0, int i1, int npts, const dou
 
 /* Advance nsteps CFL-limited steps (Sect. 2.2; Stage 2 of Sect. 3.1.2).
  * t_out (may be NULL) receives the time after the last step.  Synchronises
- * the stream once at the end.  Errors: ESTATE, ENONFINITE, ECUDA. */
+ * the stream once at the end.  Errors: ESTATE, ENONFINITE (a kernel saw a
+ * non-finite value; the state is left as computed and every later step
+ * reports it again until a new state is set), ECUDA. */
 int moses_step(moses_sim *s, int nsteps, double *t_out);
 
 /* moses_step with CUDA events recorded on the stream around every stage
@@ -285,6 +287,14 @@ int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out
 int moses_step_static(const double *dem_device, int nx, int ny, double dx, double dy,
                       const moses_params *p, const double *U_in_device, double *U_out_device,
                       double t, double *dt_out, void *stream);
+
+/* Debugging aid (not in the paper): fills every element of the simulation's
+ * device buffers that no kernel may read -- the pitch padding to the right of
+ * the second ghost column, in every plane of the state, the Heun intermediate
+ * and the geometry -- with a quiet NaN.  A later run that gives the same
+ * result as an unpoisoned one shows that no stencil reads outside its cells
+ * (the canary test of the test suite).  Errors: EINVAL, ECUDA. */
+int moses_debug_poison(moses_sim *s);
 
 /* Library build identification (architecture, precision forms). */
 const char *moses_version(void);

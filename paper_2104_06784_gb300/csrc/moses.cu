@@ -357,6 +357,8 @@ static int refresh_t(moses_sim *s)
     fill_ghosts_kernel<T><<<grid_for(n), 256, 0, s->stream>>>(a, (T *)s->U, h.t);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(&s->ctl->amax, 0, sizeof(unsigned long long), s->stream));
+    // a new state clears a non-finite status left by an earlier step
+    CK(cudaMemsetAsync(&s->ctl->status, 0, sizeof(s->ctl->status), s->stream));
     max_speed_kernel<T><<<grid_for(n), 256, 0, s->stream>>>((const T *)s->U, (const T *)s->geo, s->nx, s->ny,
                                                              s->pitch, s->plane, s->ph, &s->ctl->amax);
     CK(cudaGetLastError());
@@ -439,6 +441,43 @@ static void free_sim(moses_sim *s)
 // C-ABI (C linkage comes from the declarations in moses.h)
 
 const char *moses_version(void) { return "moses-gb300 1.0 (sm_103a; FP64 and FP32 state forms)"; }
+
+namespace {
+// quiet NaN into columns [nx + 4, pitch) of `planes` planes of (ny + 4) rows
+template <typename T>
+__global__ void poison_kernel(T *buf, int planes, int nx, int ny, int pitch, long long plane)
+{
+    const int w = pitch - (nx + 2 * GH);
+    const long long n = (long long)planes * (ny + 2 * GH) * w;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / w;  // plane * rows + row
+        const int col = nx + 2 * GH + (int)(e - r * w);
+        const int pl = (int)(r / (ny + 2 * GH)), row = (int)(r - (long long)pl * (ny + 2 * GH));
+        buf[pl * plane + (long long)row * pitch + col] = (T)NAN;
+    }
+}
+}  // namespace
+
+int moses_debug_poison(moses_sim *s)
+{
+    if (!s) return MOSES_EINVAL;
+    if (s->pitch == s->nx + 2 * GH) return MOSES_OK;  // no padding to poison
+    const int sp = s->prec == MOSES_FP32 ? 8 : 6;
+    const long long cells = (long long)(s->ny + 2 * GH) * (s->pitch - s->nx - 2 * GH);
+    for (int q = 0; q < 3; q++) {
+        void *buf = q == 0 ? s->U : q == 1 ? s->Us : s->geo;
+        const int planes = q < 2 ? sp : geo_planes(s);
+        if (s->prec == MOSES_FP64)
+            poison_kernel<double><<<grid_for(planes * cells), 256, 0, s->stream>>>((double *)buf, planes, s->nx, s->ny,
+                                                                                 s->pitch, s->plane);
+        else
+            poison_kernel<float><<<grid_for(planes * cells), 256, 0, s->stream>>>((float *)buf, planes, s->nx, s->ny,
+                                                                                s->pitch, s->plane);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
 
 const char *moses_last_error(const moses_sim *s) { return s ? s->err.c_str() : g_create_err.c_str(); }
 

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("moses_last_error", C.c_char_p, [_vp]),
     ("moses_destroy", None, [_vp]),
     ("moses_version", C.c_char_p, []),
+    ("moses_debug_poison", C.c_int, [_vp]),
 ]
 
 
@@ -200,6 +201,10 @@ class Sim:
         ms = (C.c_double * 2)()
         self._ck(self._L.moses_step_timed(self._h, int(n), C.byref(t), ms))
         return t.value, [ms[0], ms[1]]
+
+    def debug_poison(self):
+        """Fill the never-read pitch padding of the device buffers with NaN."""
+        self._ck(self._L.moses_debug_poison(self._h))
 
     # tile shape of the stage kernel -------------------------------------------
     TILES = {0: "32x8", 1: "32x4", 2: "32x16"}
