@@ -1046,8 +1046,9 @@ struct BatchTile {
     unsigned int nb;  // CTAs of this simulation in the launch
 };
 
+// FP32: three 256-thread CTAs per SM (85 registers); FP64: two
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, 512 / (TX * TY))
+__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY))
     stage_kernel_batch(const StageArgs<T> *__restrict__ args, const BatchTile *__restrict__ tiles)
 {
     __shared__ StageArgs<T> sa;
