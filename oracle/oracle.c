@@ -68,6 +68,8 @@ typedef struct {
     double cfl, dt_max, h_dry;
     int bc[4]; /* W, E, S, N : 0 closed, 1 transmissive */
     int fluid_pg_mode;
+    int scheme; /* 0: central flux (Sect. 2.2); 1: central-upwind flux with
+                   one-sided local speeds (the cited second-order scheme)   */
 } orc_params;
 
 /* geometry of one location (cell centre or face) */
@@ -303,7 +305,7 @@ static double kappa_of(const orc_geom *G, double vX, double vY)
    wave speeds (R7) and P = J_b h pbar^f                                     */
 
 static void face_flux(const orc_params *p, const orc_geom *G, int d, const double u[6], double F[6],
-                      double *as, double *af, double *P)
+                      double *as, double *af, double *P, double spd[4])
 {
     double J = G->J, c = G->c, al = alpha_rho(p);
     double hs = u[0] / J, hf = u[3] / J, h = hs + hf;
@@ -324,9 +326,31 @@ static void face_flux(const orc_params *p, const orc_geom *G, int d, const doubl
     F[4] = J * hf * vXf * vnf + p->eps * J * h * Ad1 * pf;
     F[5] = J * hf * vYf * vnf + p->eps * J * h * Ad2 * pf;
     double Add = G->Ai[d][d];
-    *as = fabs(vns) + sqrt(p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0);
-    *af = fabs(vnf) + sqrt(p->eps * p->g * c * Add * h);
+    double cs = sqrt(p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0);
+    double cf = sqrt(p->eps * p->g * c * Add * h);
+    *as = fabs(vns) + cs;
+    *af = fabs(vnf) + cf;
     *P = J * h * pf;
+    if (spd) { /* normal velocities and wave-speed terms, for one-sided speeds */
+        spd[0] = vns;
+        spd[1] = cs;
+        spd[2] = vnf;
+        spd[3] = cf;
+    }
+}
+
+/* numerical flux of one component through a face from the two reconstructed
+   sides: the central flux (scheme 0) with the larger local speed a, or the
+   central-upwind flux (scheme 1) with one-sided speeds ap >= 0 >= am:
+   (ap Fm - am Fp) / (ap - am) + ap am / (ap - am) (up - um), which is the
+   mean of Fm and Fp when ap = am = 0 (both sides at rest and dry)           */
+static double numerical_flux(int scheme, double Fm, double Fp, double um, double up, double a, double ap,
+                             double am)
+{
+    if (scheme == 0) return 0.5 * (Fm + Fp) - 0.5 * a * (up - um);
+    double w = ap - am;
+    if (!(w > 0.0)) return 0.5 * (Fm + Fp);
+    return (ap * Fm - am * Fp) / w + ap * am / w * (up - um);
 }
 
 /* largest cell-centre wave speed over both phases and both directions (R7) */
@@ -336,8 +360,8 @@ static double cell_speed(const orc_sim *s, int i, int j, double *const U[6])
     long k = IS(s, i, j);
     for (int c = 0; c < 6; c++) u[c] = U[c][k];
     const orc_geom *G = &s->gc[k];
-    face_flux(&s->p, G, 0, u, F, &a[0], &a[1], &P);
-    face_flux(&s->p, G, 1, u, F, &a[2], &a[3], &P);
+    face_flux(&s->p, G, 0, u, F, &a[0], &a[1], &P, NULL);
+    face_flux(&s->p, G, 1, u, F, &a[2], &a[3], &P, NULL);
     double m = 0.0;
     for (int c = 0; c < 4; c++) m = fmax(m, a[c]);
     return m;
@@ -556,13 +580,16 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
                 up[c] = uR - 0.5 * sR;   /* u^+ : from the right cell */
             }
             const orc_geom *G = &s->gfx[IS(s, i, j)];
-            face_flux(p, G, 0, um, Fm, &asm_, &afm, &Pm);
-            face_flux(p, G, 0, up, Fp, &asp, &afp, &Pp);
+            double sm[4], sp[4];
+            face_flux(p, G, 0, um, Fm, &asm_, &afm, &Pm, sm);
+            face_flux(p, G, 0, up, Fp, &asp, &afp, &Pp, sp);
             double as = fmax(asm_, asp), af = fmax(afm, afp);
             long k = IS(s, i, j);
             for (int c = 0; c < 6; c++) {
-                double a = c < 3 ? as : af;
-                s->Hx[c][k] = 0.5 * (Fm[c] + Fp[c]) - 0.5 * a * (up[c] - um[c]);
+                int q = c < 3 ? 0 : 2; /* phase: normal velocity and wave term at spd[q], spd[q+1] */
+                double ap = fmax(fmax(sm[q] + sm[q + 1], sp[q] + sp[q + 1]), 0.0);
+                double am = fmin(fmin(sm[q] - sm[q + 1], sp[q] - sp[q + 1]), 0.0);
+                s->Hx[c][k] = numerical_flux(p->scheme, Fm[c], Fp[c], um[c], up[c], c < 3 ? as : af, ap, am);
             }
             s->Px[k] = 0.5 * (Pm + Pp);
         }
@@ -580,13 +607,16 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
                 up[c] = uR - 0.5 * sR;
             }
             const orc_geom *G = &s->gfy[IS(s, i, j)];
-            face_flux(p, G, 1, um, Fm, &asm_, &afm, &Pm);
-            face_flux(p, G, 1, up, Fp, &asp, &afp, &Pp);
+            double sm[4], sp[4];
+            face_flux(p, G, 1, um, Fm, &asm_, &afm, &Pm, sm);
+            face_flux(p, G, 1, up, Fp, &asp, &afp, &Pp, sp);
             double as = fmax(asm_, asp), af = fmax(afm, afp);
             long k = IS(s, i, j);
             for (int c = 0; c < 6; c++) {
-                double a = c < 3 ? as : af;
-                s->Hy[c][k] = 0.5 * (Fm[c] + Fp[c]) - 0.5 * a * (up[c] - um[c]);
+                int q = c < 3 ? 0 : 2;
+                double ap = fmax(fmax(sm[q] + sm[q + 1], sp[q] + sp[q + 1]), 0.0);
+                double am = fmin(fmin(sm[q] - sm[q + 1], sp[q] - sp[q + 1]), 0.0);
+                s->Hy[c][k] = numerical_flux(p->scheme, Fm[c], Fp[c], um[c], up[c], c < 3 ? as : af, ap, am);
             }
             s->Py[k] = 0.5 * (Pm + Pp);
         }
@@ -778,6 +808,7 @@ int orc_create(const double *dem, int nx, int ny, double dx, double dy, const or
     *out = NULL;
     if (!dem || !p || nx < 1 || ny < 1 || !(dx > 0.0) || !(dy > 0.0)) return ORC_EINVAL;
     if (p->k_mode != 0) return ORC_EINVAL;
+    if (p->scheme != 0 && p->scheme != 1) return ORC_EINVAL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return ORC_ENOMEM;
     s->nx = nx;

@@ -51,6 +51,7 @@ def default_params(**over) -> dict:
         h_dry=1e-3,
         bc=(BC_CLOSED,) * 4,
         fluid_pg_mode=0,
+        scheme=0,
     )
     p.update(over)
     return p

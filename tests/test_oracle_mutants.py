@@ -32,7 +32,16 @@ MUTANTS = [
     ("(1 - alpha) dropped from the solid pressure",
      "double Ns = p->g * c * (1.0 - al) * hs / 2.0;", "double Ns = p->g * c * hs / 2.0;"),
     ("KT numerical diffusion with the wrong sign",
-     "- 0.5 * a * (up[c] - um[c]);", "+ 0.5 * a * (up[c] - um[c]);"),
+     "return 0.5 * (Fm + Fp) - 0.5 * a * (up - um);", "return 0.5 * (Fm + Fp) + 0.5 * a * (up - um);"),
+    ("central-upwind diffusion term with the wrong sign",
+     "return (ap * Fm - am * Fp) / w + ap * am / w * (up - um);",
+     "return (ap * Fm - am * Fp) / w - ap * am / w * (up - um);"),
+    ("central-upwind with the one-sided speeds swapped between the two sides",
+     "return (ap * Fm - am * Fp) / w + ap * am / w * (up - um);",
+     "return (ap * Fp - am * Fm) / w + ap * am / w * (up - um);"),
+    ("central-upwind left speed without the wave term",
+     "double am = fmin(fmin(sm[q] - sm[q + 1], sp[q] - sp[q + 1]), 0.0);",
+     "double am = fmin(fmin(sm[q], sp[q]), 0.0);"),
     ("maxmod instead of minmod",
      "return (a > 0.0) ? fmin(a, b) : fmax(a, b);", "return (a > 0.0) ? fmax(a, b) : fmin(a, b);"),
     ("slopes not halved at the faces",
