@@ -86,7 +86,16 @@ typedef struct {
                             reaction of the solid buoyancy); 1: phi^f as printed
                             in Eq. SrcF_f_Topo                                    */
     int precision;       /* MOSES_FP64 or MOSES_FP32                              */
+    int scheme;          /* MOSES_SCHEME_CENTRAL: the central flux of Sect. 2.2
+                            (the paper's); MOSES_SCHEME_CENTRAL_UPWIND: the
+                            central-upwind flux with one-sided local speeds of
+                            the second-order scheme Sect. 2.2 cites (32 x 8
+                            tiles; not accepted by moses_batch_create,
+                            moses_adjoint_misfit, moses_step_static)          */
 } moses_params;
+
+#define MOSES_SCHEME_CENTRAL 0
+#define MOSES_SCHEME_CENTRAL_UPWIND 1
 
 typedef struct moses_sim moses_sim; /* opaque; owns all its device memory */
 

@@ -390,6 +390,8 @@ static int check_params(const moses_params *p, std::string &why)
         if (p->bc[k] != MOSES_BC_CLOSED && p->bc[k] != MOSES_BC_TRANSMISSIVE) return why = "bc must be 0 or 1", 1;
     if (p->fluid_pg_mode != 0 && p->fluid_pg_mode != 1) return why = "fluid_pg_mode must be 0 or 1", 1;
     if (p->precision != MOSES_FP64 && p->precision != MOSES_FP32) return why = "precision must be 0 or 1", 1;
+    if (p->scheme != MOSES_SCHEME_CENTRAL && p->scheme != MOSES_SCHEME_CENTRAL_UPWIND)
+        return why = "scheme must be 0 or 1", 1;
     return 0;
 }
 
@@ -420,6 +422,7 @@ static Phys make_phys(const moses_params *p, double dx, double dy)
     f.inv_dy = 1.0 / dy;
     f.cell_area = dx * dy;
     f.pg_mode = p->fluid_pg_mode;
+    f.scheme = p->scheme;
     for (int k = 0; k < 4; k++) f.bc[k] = p->bc[k];
     return f;
 }
@@ -1098,6 +1101,7 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     if (check_params(p, why)) return fail(s, MOSES_EINVAL, why);
     if (p->precision != MOSES_FP64) return fail(s, MOSES_EINVAL, "moses_step_static runs the FP64 form only");
     if (p->nu_f != 0.0) return fail(s, MOSES_EINVAL, "moses_step_static: nu_f must be 0");
+    if (p->scheme != MOSES_SCHEME_CENTRAL) return fail(s, MOSES_EINVAL, "moses_step_static: scheme must be 0");
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(s, MOSES_EINVAL, "device ordinal out of range");
@@ -1300,6 +1304,8 @@ int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out)
         if (sims[k]->stream != sims[0]->stream) return batch_fail(nullptr, MOSES_EINVAL, "members must share the stream");
         if (!sims[k]->have_state) return batch_fail(nullptr, MOSES_ESTATE, "member without a state");
         if (sims[k]->p.nu_f != 0.0) return batch_fail(nullptr, MOSES_EINVAL, "members must have nu_f = 0");
+        if (sims[k]->p.scheme != MOSES_SCHEME_CENTRAL)
+            return batch_fail(nullptr, MOSES_EINVAL, "members must use the central scheme");
         for (int q = 0; q < k; q++)
             if (sims[q] == sims[k]) return batch_fail(nullptr, MOSES_EINVAL, "a simulation appears twice");
     }

@@ -104,6 +104,7 @@ struct Phys {
     double dx, dy, inv_dx, inv_dy;
     double cell_area;  // dx dy
     int pg_mode;       // 0: phi^s (reaction reading), 1: phi^f (as printed)
+    int scheme;        // 0: central flux, 1: central-upwind flux
     int bc[4];
 };
 

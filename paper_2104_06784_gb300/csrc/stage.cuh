@@ -181,7 +181,8 @@ struct FaceGeo {
 // J h^p v_xi^p is the momentum component U_{2+d}, and the pressure terms
 // eps J h A_dk Nbar^s, eps J h A_dk pbar^f become (kap A_dk c^2) (J h) U.
 template <typename T, int D>
-__device__ __forceinline__ void side_flux(const T u[6], const FaceGeo<T> &G, T F[6], T &as, T &af, T &P)
+__device__ __forceinline__ void side_flux(const T u[6], const FaceGeo<T> &G, T F[6], T &as, T &af, T &P,
+                                          T *w = nullptr)
 {
     const T Ut = u[0] + u[3];
     const bool ws = gtp(u[0], G.jhd), wf = gtp(u[3], G.jhd);
@@ -201,9 +202,16 @@ __device__ __forceinline__ void side_flux(const T u[6], const FaceGeo<T> &G, T F
     F[3] = wf ? unf : T(0);
     F[4] = fma(fX, Pf, u[4] * vnf);
     F[5] = fma(fY, Pf, u[5] * vnf);
-    as = tabs(vns) + fsqrt(G.sn * (Ut + u[0]));
-    af = tabs(vnf) + fsqrt(G.fn2 * Ut);
+    const T cs = fsqrt(G.sn * (Ut + u[0])), cf = fsqrt(G.fn2 * Ut);
+    as = tabs(vns) + cs;
+    af = tabs(vnf) + cf;
     P = G.hg * Pf;
+    if (w) {  // normal velocities and wave-speed terms, for one-sided speeds
+        w[0] = vns;
+        w[1] = cs;
+        w[2] = vnf;
+        w[3] = cf;
+    }
 }
 
 // Twice the central flux through one face, from the face values um (left /
@@ -218,6 +226,30 @@ __device__ __forceinline__ void face_flux2(const T um[6], const T up[6], const F
     const T as = maxnn(asm_, asp), af = maxnn(afm, afp);
 #pragma unroll
     for (int c = 0; c < 6; c++) H[c] = fma(-(c < 3 ? as : af), up[c] - um[c], Fm[c] + Fp[c]);
+    H[6] = Pm + Pp;
+}
+
+// Twice the central-upwind flux (the second-order scheme Sect. 2.2 cites): per
+// phase one-sided speeds ap = max(vn + c, 0) and am = min(vn - c, 0) over the
+// two sides, H = (ap F(um) - am F(up)) / (ap - am) + ap am / (ap - am) (up - um);
+// the mean of the two fluxes where ap = am = 0.  H2[6] = P(um) + P(up).
+template <typename T, int D>
+__device__ __forceinline__ void face_flux2_cu(const T um[6], const T up[6], const FaceGeo<T> &G, T H[7])
+{
+    T Fm[6], Fp[6], wm[4], wp[4], a, Pm, Pp;
+    side_flux<T, D>(um, G, Fm, a, a, Pm, wm);
+    side_flux<T, D>(up, G, Fp, a, a, Pp, wp);
+#pragma unroll
+    for (int ph = 0; ph < 2; ph++) {
+        const T ap = fmax(fmax(wm[2 * ph] + wm[2 * ph + 1], wp[2 * ph] + wp[2 * ph + 1]), T(0));
+        const T am = fmin(fmin(wm[2 * ph] - wm[2 * ph + 1], wp[2 * ph] - wp[2 * ph + 1]), T(0));
+        const T w = ap - am;
+        const bool moving = w > T(0);
+        const T r2 = moving ? T(2) * frcp(w) : T(0);  // doubled flux
+#pragma unroll
+        for (int c = 3 * ph; c < 3 * ph + 3; c++)
+            H[c] = moving ? fma(ap * am * r2, up[c] - um[c], (ap * Fm[c] - am * Fp[c]) * r2) : Fm[c] + Fp[c];
+    }
     H[6] = Pm + Pp;
 }
 
@@ -522,7 +554,7 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
 // ---- the stage kernel -------------------------------------------------------------
 // One stage on the tile (bx, by) of the simulation described by `a`; nb is the
 // number of CTAs working on that simulation in this launch (for the ticket).
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
     constexpr int NT = TX * TY;
@@ -708,7 +740,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
         }
         T H[7];
-        face_flux2<T, 0>(um, up, G, H);
+        if constexpr (CU) face_flux2_cu<T, 0>(um, up, G, H);
+        else face_flux2<T, 0>(um, up, G, H);
         if constexpr (sizeof(T) == 4) {
             // FP32: the mass change this face gives each neighbour, rounded once
             H[0] *= dtT * k.hinv_dx;
@@ -745,7 +778,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
         }
         T H[7];
-        face_flux2<T, 1>(um, up, G, H);
+        if constexpr (CU) face_flux2_cu<T, 1>(um, up, G, H);
+        else face_flux2<T, 1>(um, up, G, H);
         if constexpr (sizeof(T) == 4) {
             H[0] *= dtT * k.hinv_dy;
             H[3] *= dtT * k.hinv_dy;
@@ -1031,10 +1065,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
 }
 
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
 {
-    stage_tile<T, TX, TY, REC, VIS>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+    stage_tile<T, TX, TY, REC, VIS, CU>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // Ensemble form: one launch runs the same stage of many simulations.  Each CTA

@@ -81,3 +81,8 @@ def test_null_pointers(L):
     assert L.moses_create(None, 4, 4, 1.0, 1.0, None, None, None) == moses.MOSES_EINVAL
     assert L.moses_step(None, 1, None) == moses.MOSES_EINVAL
     L.moses_destroy(None)
+
+
+def test_create_rejects_bad_scheme(L):
+    rc, h = _create(np.zeros((4, 4)), 4, 4, scheme=2)
+    assert rc == moses.MOSES_EINVAL and b"scheme" in L.moses_last_error(None)
