@@ -218,6 +218,22 @@ def measure(sim, cells, K, W, torch):
     return ms, stage_ms
 
 
+def measure_variants(cfg, K, Wm, torch):
+    """Step time of the model options the configurations leave off, on the
+    same 4096^2 workload (32 x 8 tiles, CUDA events on the stream): the
+    central-upwind flux (scheme 1) and the viscous term (nu_f = 1 m^2/s)."""
+    from paper_2104_06784_gb300 import moses
+    out = {}
+    for name, over in (("central_upwind", dict(scheme=1)), ("viscous", dict(nu_f=1.0))):
+        out[name] = {}
+        for form, prec in (("f64", moses.FP64), ("f32", moses.FP32)):
+            c = dict(cfg, params=dict(cfg["params"], **over))
+            with moses.from_config(c, precision=prec) as sim:
+                ms, _ = measure(sim, sim.nx * sim.ny, K, Wm, torch)
+            out[name][form] = {"ms_per_step": ms / K, "value": sim.nx * sim.ny * K / (ms / 1e3)}
+    return out
+
+
 def reduce_over_ranks(x, op="max", dist=None, device="cpu"):
     """max (or sum) of a scalar over the ranks; x itself without a process group."""
     if dist is None:
@@ -318,6 +334,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (the workload is defined at 4096)")
     ap.add_argument("--only", choices=["f64", "f32", "adjoint"], default=None,
                     help="measure one precision form, or only the adjoint")
@@ -446,6 +463,7 @@ def main():
     ens = None if args.no_ensemble else measure_ensemble(K, Wm, rank=rank, world=world, dist=dist, device="cuda")
 
     adj = None if args.no_adjoint else measure_adjoint(torch)
+    variants = None if args.no_variants else measure_variants(cfg, K, Wm, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -462,6 +480,7 @@ def main():
                 "roofline": roof32, "gpu_launches": 2 * K},
         "ensemble": ens,
         "adjoint": adj,
+        "variants": variants,
         "stage_ms": {"f64": f64["stage_ms"], "f32": f32["stage_ms"]},
         "tiles": tiles,
         "stage_source": h,
