@@ -932,6 +932,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         }
         T out[6];
         T lo[2] = {T(0), T(0)};  // FP32: rounding remainders of the masses
+        const T dthx = dtT * k.hinv_dx, dthy = dtT * k.hinv_dy;
 #pragma unroll
         for (int c = 0; c < 6; c++) {
             if constexpr (sizeof(T) == 4) {
@@ -951,10 +952,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                     continue;
                 }
             }
+            // u + dt S - dt (dH_x / 2dx + dH_y / 2dy), the sources first (the
+            // mass components have none)
             const T dx2 = sHx[c * NXF + fx + 1] - sHx[c * NXF + fx];
             const T dy2 = sHy[c * NYF + fy + TX] - sHy[c * NYF + fy];
-            const T div = fma(dx2, k.hinv_dx, dy2 * k.hinv_dy);
-            out[c] = fma(dtT, S[c] - div, u[c]);
+            const T base = (c == 0 || c == 3) ? u[c] : fma(dtT, S[c], u[c]);
+            out[c] = fma(-dthy, dy2, fma(-dthx, dx2, base));
         }
         if constexpr (REC) {
 #pragma unroll
