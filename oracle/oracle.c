@@ -70,6 +70,9 @@ typedef struct {
     int fluid_pg_mode;
     int scheme; /* 0: central flux (Sect. 2.2); 1: central-upwind flux with
                    one-sided local speeds (the cited second-order scheme)   */
+    int recon;  /* 0: minmod TVD slopes (Sect. 2.2); 1: third-order WENO     */
+    int rk;     /* 2: two-step modified Euler (Sect. 2.2); 3: three-stage
+                   strong-stability-preserving Runge-Kutta                  */
 } orc_params;
 
 /* geometry of one location (cell centre or face) */
@@ -264,6 +267,28 @@ static inline double minmod(double a, double b)
 {
     if (a * b <= 0.0) return 0.0;
     return (a > 0.0) ? fmin(a, b) : fmax(a, b);
+}
+
+/* third-order WENO (Sect. 2.2 names WENO reconstruction as an option) of the
+   value at the right face of cell b from the cells a, b, c: the two
+   second-order candidates on {a, b} and {b, c}, linear weights 1/3 and 2/3,
+   smoothness indicators the squared differences, nonlinear weights
+   d_k / (eps + beta_k)^2 with eps = 1e-6 m^2 + 1e-100, m the largest of
+   |a|, |b|, |c| (so the weights do not change when U is rescaled)         */
+static double weno3_right_face(double a, double b, double c)
+{
+    double q0 = -0.5 * a + 1.5 * b, q1 = 0.5 * b + 0.5 * c;
+    double b0 = (b - a) * (b - a), b1 = (c - b) * (c - b);
+    double m = fmax(fabs(a), fmax(fabs(b), fabs(c)));
+    double eps = 1e-6 * m * m + 1e-100;
+    double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+    double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+    return (a0 * q0 + a1 * q1) / (a0 + a1);
+}
+/* the mirror image: the value at the left face of cell b */
+static double weno3_left_face(double a, double b, double c)
+{
+    return weno3_right_face(c, b, a);
 }
 
 /* phase velocity (v_X, v_Y) from its depth J h and momenta (R5) */
@@ -574,10 +599,19 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
             for (int c = 0; c < 6; c++) {
                 double *V = Uin[c];
                 double uL = V[IS(s, i, j)], uR = V[IS(s, i + 1, j)];
-                double sL = minmod(uL - V[IS(s, i - 1, j)], uR - uL);
-                double sR = minmod(uR - uL, V[IS(s, i + 2, j)] - uR);
-                um[c] = uL + 0.5 * sL;   /* u^- : from the left cell  */
-                up[c] = uR - 0.5 * sR;   /* u^+ : from the right cell */
+                if (p->recon == 0) {
+                    double sL = minmod(uL - V[IS(s, i - 1, j)], uR - uL);
+                    double sR = minmod(uR - uL, V[IS(s, i + 2, j)] - uR);
+                    um[c] = uL + 0.5 * sL;   /* u^- : from the left cell  */
+                    up[c] = uR - 0.5 * sR;   /* u^+ : from the right cell */
+                } else {
+                    um[c] = weno3_right_face(V[IS(s, i - 1, j)], uL, uR);
+                    up[c] = weno3_left_face(uL, uR, V[IS(s, i + 2, j)]);
+                    if (c == 0 || c == 3) { /* masses stay >= 0 at the faces */
+                        um[c] = fmax(um[c], 0.0);
+                        up[c] = fmax(up[c], 0.0);
+                    }
+                }
             }
             const orc_geom *G = &s->gfx[IS(s, i, j)];
             double sm[4], sp[4];
@@ -601,10 +635,19 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
             for (int c = 0; c < 6; c++) {
                 double *V = Uin[c];
                 double uL = V[IS(s, i, j)], uR = V[IS(s, i, j + 1)];
-                double sL = minmod(uL - V[IS(s, i, j - 1)], uR - uL);
-                double sR = minmod(uR - uL, V[IS(s, i, j + 2)] - uR);
-                um[c] = uL + 0.5 * sL;
-                up[c] = uR - 0.5 * sR;
+                if (p->recon == 0) {
+                    double sL = minmod(uL - V[IS(s, i, j - 1)], uR - uL);
+                    double sR = minmod(uR - uL, V[IS(s, i, j + 2)] - uR);
+                    um[c] = uL + 0.5 * sL;
+                    up[c] = uR - 0.5 * sR;
+                } else {
+                    um[c] = weno3_right_face(V[IS(s, i, j - 1)], uL, uR);
+                    up[c] = weno3_left_face(uL, uR, V[IS(s, i, j + 2)]);
+                    if (c == 0 || c == 3) {
+                        um[c] = fmax(um[c], 0.0);
+                        up[c] = fmax(up[c], 0.0);
+                    }
+                }
             }
             const orc_geom *G = &s->gfy[IS(s, i, j)];
             double sm[4], sp[4];
@@ -765,6 +808,69 @@ static void heun_step(orc_sim *s, double dt)
     s->nsteps++;
 }
 
+/* dry rule on the combined state (R5) */
+static void dry_momentum(orc_sim *s, double *U[6])
+{
+    for (int j = 0; j < s->ny; j++)
+        for (int i = 0; i < s->nx; i++) {
+            long k = IS(s, i, j);
+            double J = s->gc[k].J;
+            for (int ph = 0; ph < 2; ph++) {
+                int c = 3 * ph;
+                if (U[c][k] <= J * s->p.h_dry) {
+                    U[c + 1][k] = 0.0;
+                    U[c + 2][k] = 0.0;
+                }
+            }
+        }
+}
+
+/* three-stage SSP Runge-Kutta step: W1 = S(U) at t; W2 = 3/4 U + 1/4 S(W1)
+   at t + dt; U' = 1/3 U + 2/3 S(W2) at t + dt/2 (S = one stage: U + dt L(U)
+   with friction, clamp and the dry rule); the dry rule after each
+   combination.  Boundary fluxes and clamp volumes enter the budgets with the
+   weights 1/6, 1/6, 2/3 with which each stage reaches U'. */
+static void rk3_step(orc_sim *s, double dt)
+{
+    double t0 = s->t, b[3][2], c[3][2];
+    long n = 0;
+    stage(s, s->U, s->W1, t0, dt);
+    for (int ph = 0; ph < 2; ph++) b[0][ph] = s->st_bnd[ph], c[0][ph] = s->st_clamp[ph];
+    n += s->st_clamp_cells;
+    stage(s, s->W1, s->W2, t0 + dt, dt);
+    for (int ph = 0; ph < 2; ph++) b[1][ph] = s->st_bnd[ph], c[1][ph] = s->st_clamp[ph];
+    n += s->st_clamp_cells;
+    for (int j = 0; j < s->ny; j++)
+        for (int i = 0; i < s->nx; i++) {
+            long k = IS(s, i, j);
+            for (int q = 0; q < 6; q++) s->W1[q][k] = 0.75 * s->U[q][k] + 0.25 * s->W2[q][k];
+        }
+    dry_momentum(s, s->W1);
+    stage(s, s->W1, s->W2, t0 + 0.5 * dt, dt);
+    for (int ph = 0; ph < 2; ph++) b[2][ph] = s->st_bnd[ph], c[2][ph] = s->st_clamp[ph];
+    n += s->st_clamp_cells;
+    for (int j = 0; j < s->ny; j++)
+        for (int i = 0; i < s->nx; i++) {
+            long k = IS(s, i, j);
+            for (int q = 0; q < 6; q++) s->U[q][k] = s->U[q][k] / 3.0 + 2.0 * s->W2[q][k] / 3.0;
+        }
+    dry_momentum(s, s->U);
+    for (int ph = 0; ph < 2; ph++) {
+        s->bnd_in[ph] += dt * (b[0][ph] / 6.0 + b[1][ph] / 6.0 + 2.0 * b[2][ph] / 3.0);
+        s->clamp_vol[ph] += c[0][ph] / 6.0 + c[1][ph] / 6.0 + 2.0 * c[2][ph] / 3.0;
+    }
+    s->clamp_cells += n;
+    s->t = t0 + dt;
+    s->last_dt = dt;
+    s->nsteps++;
+}
+
+static void time_step(orc_sim *s, double dt)
+{
+    if (s->p.rk == 3) rk3_step(s, dt);
+    else heun_step(s, dt);
+}
+
 static double cfl_dt(const orc_sim *s, double amax)
 {
     double dmin = s->dx < s->dy ? s->dx : s->dy;
@@ -809,6 +915,7 @@ int orc_create(const double *dem, int nx, int ny, double dx, double dy, const or
     if (!dem || !p || nx < 1 || ny < 1 || !(dx > 0.0) || !(dy > 0.0)) return ORC_EINVAL;
     if (p->k_mode != 0) return ORC_EINVAL;
     if (p->scheme != 0 && p->scheme != 1) return ORC_EINVAL;
+    if ((p->recon != 0 && p->recon != 1) || (p->rk != 2 && p->rk != 3)) return ORC_EINVAL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     if (!s) return ORC_ENOMEM;
     s->nx = nx;
@@ -922,7 +1029,7 @@ int orc_step(orc_sim *s, int n, double *dts)
 {
     for (int k = 0; k < n; k++) {
         double dt = cfl_dt(s, max_speed(s, s->U));
-        heun_step(s, dt);
+        time_step(s, dt);
         if (dts) dts[k] = dt;
     }
     return ORC_OK;
@@ -931,7 +1038,7 @@ int orc_step(orc_sim *s, int n, double *dts)
 /* one Heun step with a prescribed time step */
 int orc_step_dt(orc_sim *s, double dt)
 {
-    heun_step(s, dt);
+    time_step(s, dt);
     return ORC_OK;
 }
 

@@ -52,6 +52,8 @@ def default_params(**over) -> dict:
         bc=(BC_CLOSED,) * 4,
         fluid_pg_mode=0,
         scheme=0,
+        recon=0,
+        rk=2,
     )
     p.update(over)
     return p

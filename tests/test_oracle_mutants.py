@@ -33,6 +33,17 @@ MUTANTS = [
      "double Ns = p->g * c * (1.0 - al) * hs / 2.0;", "double Ns = p->g * c * hs / 2.0;"),
     ("KT numerical diffusion with the wrong sign",
      "return 0.5 * (Fm + Fp) - 0.5 * a * (up - um);", "return 0.5 * (Fm + Fp) + 0.5 * a * (up - um);"),
+    ("WENO: the downwind candidate replaced by the cell value",
+     "double q0 = -0.5 * a + 1.5 * b, q1 = 0.5 * b + 0.5 * c;", "double q0 = -0.5 * a + 1.5 * b, q1 = b;"),
+    ("WENO: equal linear weights instead of 1/3, 2/3",
+     "double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));", "double a0 = (2.0 / 3.0) / ((eps + b0) * (eps + b0));"),
+    ("WENO: smoothness indicator of the wrong stencil",
+     "double b0 = (b - a) * (b - a), b1 = (c - b) * (c - b);", "double b0 = (c - b) * (c - b), b1 = (b - a) * (b - a);"),
+    ("RK3: second combination with Heun weights",
+     "s->W1[q][k] = 0.75 * s->U[q][k] + 0.25 * s->W2[q][k];", "s->W1[q][k] = 0.5 * s->U[q][k] + 0.5 * s->W2[q][k];"),
+    ("RK3: boundary fluxes with equal stage weights",
+     "s->bnd_in[ph] += dt * (b[0][ph] / 6.0 + b[1][ph] / 6.0 + 2.0 * b[2][ph] / 3.0);",
+     "s->bnd_in[ph] += dt * (b[0][ph] + b[1][ph] + b[2][ph]) / 3.0;"),
     ("central-upwind diffusion term with the wrong sign",
      "return (ap * Fm - am * Fp) / w + ap * am / w * (up - um);",
      "return (ap * Fm - am * Fp) / w - ap * am / w * (up - um);"),
