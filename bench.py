@@ -221,10 +221,13 @@ def measure(sim, cells, K, W, torch):
 def measure_variants(cfg, K, Wm, torch):
     """Step time of the model options the configurations leave off, on the
     same 4096^2 workload (32 x 8 tiles, CUDA events on the stream): the
-    central-upwind flux (scheme 1) and the viscous term (nu_f = 1 m^2/s)."""
+    central-upwind flux (scheme 1), the viscous term (nu_f = 1 m^2/s), the
+    third-order WENO face values (recon 1), the three-stage SSP Runge-Kutta
+    (rk 3) and WENO with the three-stage Runge-Kutta together."""
     from paper_2104_06784_gb300 import moses
     out = {}
-    for name, over in (("central_upwind", dict(scheme=1)), ("viscous", dict(nu_f=1.0))):
+    for name, over in (("central_upwind", dict(scheme=1)), ("viscous", dict(nu_f=1.0)), ("weno3", dict(recon=1)),
+                       ("rk3", dict(rk=3)), ("weno3_rk3", dict(recon=1, rk=3))):
         out[name] = {}
         for form, prec in (("f64", moses.FP64), ("f32", moses.FP32)):
             c = dict(cfg, params=dict(cfg["params"], **over))

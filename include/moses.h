@@ -92,10 +92,21 @@ typedef struct {
                             the second-order scheme Sect. 2.2 cites (32 x 8
                             tiles; not accepted by moses_batch_create,
                             moses_adjoint_misfit, moses_step_static)          */
+    int recon;           /* MOSES_RECON_MINMOD: minmod TVD slopes (Sect. 2.2, the
+                            paper's); MOSES_RECON_WENO3: third-order WENO face
+                            values, the option Sect. 2.2 names (32 x 8 tiles)   */
+    int rk;              /* 0 or 2: the two-step modified Euler (Sect. 2.2, the
+                            paper's); 3: three-stage SSP Runge-Kutta, the
+                            multi-step option Sect. 2.2 names.  recon and rk
+                            other than the paper's are not accepted by
+                            moses_batch_create, moses_adjoint_misfit,
+                            moses_stage_adjoint, moses_step_static             */
 } moses_params;
 
 #define MOSES_SCHEME_CENTRAL 0
 #define MOSES_SCHEME_CENTRAL_UPWIND 1
+#define MOSES_RECON_MINMOD 0
+#define MOSES_RECON_WENO3 1
 
 typedef struct moses_sim moses_sim; /* opaque; owns all its device memory */
 

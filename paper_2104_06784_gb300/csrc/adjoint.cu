@@ -298,7 +298,8 @@ int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double 
     if (ckpt_every < 1) ckpt_every = (int)std::ceil(std::sqrt((double)nsteps));
     if (ckpt_every > nsteps) ckpt_every = nsteps;
     if (s->p.nu_f != 0.0) return fail(s, MOSES_EINVAL, "the adjoint does not cover the viscous term");
-    if (s->p.scheme != MOSES_SCHEME_CENTRAL) return fail(s, MOSES_EINVAL, "the adjoint covers the central scheme only");
+    if (s->p.scheme != MOSES_SCHEME_CENTRAL || s->ph.recon != 0 || s->ph.rk != 2)
+        return fail(s, MOSES_EINVAL, "the adjoint covers the paper's scheme only (central, minmod, two-step)");
     if (!s->have_state) return fail(s, MOSES_ESTATE, "no state");
     return s->prec == MOSES_FP64
                ? adjoint_impl<double>(s, nsteps, ckpt_every, hs_target, loss, g_params, g_state0, g_release_h,
@@ -382,8 +383,8 @@ int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out
 {
     if (!s || !lam_out || !lam_in) return MOSES_EINVAL;
     if (!(std::isfinite(dt) && dt >= 0)) return fail(s, MOSES_EINVAL, "bad dt");
-    if (s->p.nu_f != 0.0 || s->p.scheme != MOSES_SCHEME_CENTRAL)
-        return fail(s, MOSES_EINVAL, "the adjoint covers the central scheme without the viscous term");
+    if (s->p.nu_f != 0.0 || s->p.scheme != MOSES_SCHEME_CENTRAL || s->ph.recon != 0 || s->ph.rk != 2)
+        return fail(s, MOSES_EINVAL, "the adjoint covers the paper's scheme without the viscous term");
     // ghosts of the current state at time t, as moses_stage sees them
     double *tmp = nullptr;
     CK(cudaMallocHost(&tmp, sizeof(double) * 6 * (size_t)s->nx * s->ny));

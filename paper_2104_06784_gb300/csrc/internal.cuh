@@ -22,6 +22,7 @@ struct moses_sim {
     void *U = nullptr;     // state, 6 planes
     void *Us = nullptr;    // Heun intermediate, 6 planes
     void *geo = nullptr;   // geo_planes(s) planes
+    void *Us2 = nullptr;   // second intermediate of the three-stage Runge-Kutta (rk = 3 only)
     Ctl *ctl = nullptr;    // device control block
     InflowSeg *inflow_d = nullptr;
     InflowSeg inflow_h[MAX_INFLOW];

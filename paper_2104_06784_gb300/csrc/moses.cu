@@ -392,6 +392,8 @@ static int check_params(const moses_params *p, std::string &why)
     if (p->precision != MOSES_FP64 && p->precision != MOSES_FP32) return why = "precision must be 0 or 1", 1;
     if (p->scheme != MOSES_SCHEME_CENTRAL && p->scheme != MOSES_SCHEME_CENTRAL_UPWIND)
         return why = "scheme must be 0 or 1", 1;
+    if (p->recon != MOSES_RECON_MINMOD && p->recon != MOSES_RECON_WENO3) return why = "recon must be 0 or 1", 1;
+    if (p->rk != 0 && p->rk != 2 && p->rk != 3) return why = "rk must be 0, 2 or 3", 1;
     return 0;
 }
 
@@ -423,6 +425,8 @@ static Phys make_phys(const moses_params *p, double dx, double dy)
     f.cell_area = dx * dy;
     f.pg_mode = p->fluid_pg_mode;
     f.scheme = p->scheme;
+    f.recon = p->recon;
+    f.rk = p->rk == 3 ? 3 : 2;
     for (int k = 0; k < 4; k++) f.bc[k] = p->bc[k];
     return f;
 }
@@ -432,6 +436,7 @@ static void free_sim(moses_sim *s)
     if (!s) return;
     cudaFree(s->U);
     cudaFree(s->Us);
+    cudaFree(s->Us2);
     cudaFree(s->geo);
     cudaFree(s->ctl);
     cudaFree(s->inflow_d);
@@ -522,6 +527,7 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
     cudaError_t e;
     if ((e = cudaMalloc(&s->U, st)) != cudaSuccess || (e = cudaMalloc(&s->Us, st)) != cudaSuccess ||
         (e = cudaMalloc(&s->geo, (size_t)geo_planes(s) * s->plane * s->esz)) != cudaSuccess ||
+        (s->ph.rk == 3 && (e = cudaMalloc(&s->Us2, st)) != cudaSuccess) ||
         (e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = cudaMalloc(&s->inflow_d, sizeof(InflowSeg) * MAX_INFLOW)) != cudaSuccess ||
         (e = cudaMalloc(&s->red, 8 * sizeof(double))) != cudaSuccess) {
@@ -530,6 +536,7 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
     }
     if ((e = cudaMemsetAsync(s->U, 0, st, s->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(s->Us, 0, st, s->stream)) != cudaSuccess ||
+        (s->Us2 && (e = cudaMemsetAsync(s->Us2, 0, st, s->stream)) != cudaSuccess) ||
         (e = cudaMemsetAsync(s->geo, 0, (size_t)geo_planes(s) * s->plane * s->esz, s->stream)) != cudaSuccess) {
         s->err = std::string("memset: ") + cudaGetErrorString(e);
         return bail(MOSES_ECUDA);
@@ -671,48 +678,57 @@ int moses_set_inflow(moses_sim *s, int side, int i0, int i1, int npts, const dou
 template <typename T>
 static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
 {
-    StageArgs<T> a1 = base_args<T>(s), a2 = base_args<T>(s);
-    a1.Uin = (const T *)s->U;
-    a1.Uout = (T *)s->Us;
-    a1.Rin = rem<T>(s, s->U);
-    a1.Rout = rem<T>(s, s->Us);
-    a1.stage = 1;
-    a2.Uin = (const T *)s->Us;
-    a2.Un = (const T *)s->U;
-    a2.Uout = (T *)s->U;
-    a2.Rin = rem<T>(s, s->Us);
-    a2.Rn = rem<T>(s, s->U);
-    a2.Rout = rem<T>(s, s->U);
-    a2.stage = 2;
-    a2.want_amax = 1;
+    // the stages of one step: the two-step modified Euler (U -> Us -> U), or
+    // the three-stage SSP Runge-Kutta (U -> Us -> Us2 -> U)
+    StageArgs<T> a[3] = {base_args<T>(s), base_args<T>(s), base_args<T>(s)};
+    const bool rk3 = s->ph.rk == 3;
+    const int ns = rk3 ? 3 : 2;
+    void *out[3] = {s->Us, rk3 ? s->Us2 : s->U, s->U};
+    void *in[3] = {s->U, s->Us, s->Us2};
+    for (int q = 0; q < ns; q++) {
+        a[q].Uin = (const T *)in[q];
+        a[q].Uout = (T *)out[q];
+        a[q].Rin = rem<T>(s, in[q]);
+        a[q].Rout = rem<T>(s, out[q]);
+        a[q].stage = q == 0 ? 1 : 2;
+        if (q > 0) {
+            a[q].Un = (const T *)s->U;
+            a[q].Rn = rem<T>(s, s->U);
+        }
+        a[q].want_amax = q == ns - 1;
+        if (rk3) {
+            a[q].rk3 = q + 1;
+            a[q].rk3_bw = q == 2 ? 2.0 / 3.0 : 1.0 / 6.0;
+        }
+    }
     if (stage_ms) {
-        // events around every launch; summed after the last step
-        cudaEvent_t ev[3];
-        for (int q = 0; q < 3; q++) CK(cudaEventCreate(&ev[q]));
+        // events around every launch; the first stage in stage_ms[0], the others in stage_ms[1]
+        cudaEvent_t ev[4];
+        for (int q = 0; q < 4; q++) CK(cudaEventCreate(&ev[q]));
         double acc[2] = {0.0, 0.0};
         int rc = 0;
         for (int k = 0; k < nsteps && rc == 0; k++) {
             CK(cudaEventRecord(ev[0], s->stream));
-            rc = launch_stage<T>(a1, s->tile, s->stream);
-            CK(cudaEventRecord(ev[1], s->stream));
-            if (rc == 0) rc = launch_stage<T>(a2, s->tile, s->stream);
-            CK(cudaEventRecord(ev[2], s->stream));
-            CK(cudaEventSynchronize(ev[2]));
+            for (int q = 0; q < ns && rc == 0; q++) {
+                rc = launch_stage<T>(a[q], s->tile, s->stream);
+                CK(cudaEventRecord(ev[q + 1], s->stream));
+            }
+            CK(cudaEventSynchronize(ev[ns]));
             float m1 = 0.f, m2 = 0.f;
             CK(cudaEventElapsedTime(&m1, ev[0], ev[1]));
-            CK(cudaEventElapsedTime(&m2, ev[1], ev[2]));
+            CK(cudaEventElapsedTime(&m2, ev[1], ev[ns]));
             acc[0] += m1;
             acc[1] += m2;
         }
-        for (int q = 0; q < 3; q++) cudaEventDestroy(ev[q]);
+        for (int q = 0; q < 4; q++) cudaEventDestroy(ev[q]);
         if (rc) return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
         stage_ms[0] = acc[0];
         stage_ms[1] = acc[1];
         return MOSES_OK;
     }
     for (int k = 0; k < nsteps; k++) {
-        int rc = launch_stage<T>(a1, s->tile, s->stream);
-        if (rc == 0) rc = launch_stage<T>(a2, s->tile, s->stream);
+        int rc = 0;
+        for (int q = 0; q < ns && rc == 0; q++) rc = launch_stage<T>(a[q], s->tile, s->stream);
         if (rc) return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
     }
     return MOSES_OK;
@@ -1101,7 +1117,8 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     if (check_params(p, why)) return fail(s, MOSES_EINVAL, why);
     if (p->precision != MOSES_FP64) return fail(s, MOSES_EINVAL, "moses_step_static runs the FP64 form only");
     if (p->nu_f != 0.0) return fail(s, MOSES_EINVAL, "moses_step_static: nu_f must be 0");
-    if (p->scheme != MOSES_SCHEME_CENTRAL) return fail(s, MOSES_EINVAL, "moses_step_static: scheme must be 0");
+    if (p->scheme != MOSES_SCHEME_CENTRAL || p->recon != MOSES_RECON_MINMOD || p->rk == 3)
+        return fail(s, MOSES_EINVAL, "moses_step_static: the paper's scheme only (scheme 0, recon 0, rk 2)");
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(s, MOSES_EINVAL, "device ordinal out of range");
@@ -1304,8 +1321,8 @@ int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out)
         if (sims[k]->stream != sims[0]->stream) return batch_fail(nullptr, MOSES_EINVAL, "members must share the stream");
         if (!sims[k]->have_state) return batch_fail(nullptr, MOSES_ESTATE, "member without a state");
         if (sims[k]->p.nu_f != 0.0) return batch_fail(nullptr, MOSES_EINVAL, "members must have nu_f = 0");
-        if (sims[k]->p.scheme != MOSES_SCHEME_CENTRAL)
-            return batch_fail(nullptr, MOSES_EINVAL, "members must use the central scheme");
+        if (sims[k]->p.scheme != MOSES_SCHEME_CENTRAL || sims[k]->ph.recon != 0 || sims[k]->ph.rk != 2)
+            return batch_fail(nullptr, MOSES_EINVAL, "members must use the paper's scheme (central, minmod, two-step)");
         for (int q = 0; q < k; q++)
             if (sims[q] == sims[k]) return batch_fail(nullptr, MOSES_EINVAL, "a simulation appears twice");
     }

@@ -105,6 +105,8 @@ struct Phys {
     double cell_area;  // dx dy
     int pg_mode;       // 0: phi^s (reaction reading), 1: phi^f (as printed)
     int scheme;        // 0: central flux, 1: central-upwind flux
+    int recon;         // 0: minmod slopes, 1: third-order WENO
+    int rk;            // 2: two-step modified Euler, 3: three-stage SSP Runge-Kutta
     int bc[4];
 };
 
@@ -172,6 +174,11 @@ struct alignas(8) StageArgs {
     int want_amax;     // stage 2: reduce a_max of U^{n+1}
     int debug_stage;   // 1: single stage to Uout with a given dt (no Heun)
     double dbg_t, dbg_dt;
+    // three-stage SSP Runge-Kutta: 0 for the two-step Euler, else the stage
+    // (1, 2, 3; `stage` is 1 for the first, 2 for the others, which combine
+    // with Un); rk3_bw is the stage's weight in the budgets (1/6, 1/6, 2/3)
+    int rk3;
+    double rk3_bw;
     // recording form only (the adjoint's recompute): per interior cell the
     // trial masses and solid momenta before friction and the clamp, and the
     // gradient of P (6 planes: U1*, U2*, U3*, U4*, dP/dxi, dP/deta)

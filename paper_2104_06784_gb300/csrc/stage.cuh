@@ -154,6 +154,37 @@ __device__ __forceinline__ void cp_async_elem(T *dst, const T *src, bool valid)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Third-order WENO value at the right face of cell b from the cells a, b, c
+// (Sect. 2.2 names WENO reconstruction as an option): candidates on {a, b}
+// and {b, c}, linear weights 1/3 and 2/3, smoothness indicators the squared
+// differences, nonlinear weights d_k / (eps + beta_k)^2 with the
+// scale-invariant eps = 1e-6 m^2 + tiny (m = max |a|, |b|, |c|), written as
+// one reciprocal: w0 = d0 (eps + beta1)^2 / (d0 (eps + beta1)^2 + d1 (eps + beta0)^2).
+// The left-face value of b is the same function of (c, b, a).
+// FP32 takes the differences in units of m (a second reciprocal), so that the
+// squared indicators cannot underflow; the weights are unchanged by the
+// rescaling up to rounding.  Below m = 1e-30 (where a subnormal m would defeat
+// the reciprocal) the differences count as 0, which gives the linear weights.
+template <typename T>
+__device__ __forceinline__ T weno3_face(T a, T b, T c)
+{
+    const T q0 = fma(T(1.5), b, T(-0.5) * a), q1 = T(0.5) * (b + c);
+    T d0 = b - a, d1 = c - b;
+    const T m = fmax(fabs(a), fmax(fabs(b), fabs(c)));
+    T eps;
+    if constexpr (sizeof(T) == 8) {
+        eps = fma(1e-6 * m, m, 1e-100);
+    } else {
+        const float rm = m > 1e-30f ? frcp(m) : 0.0f;
+        d0 *= rm;
+        d1 *= rm;
+        eps = 1e-6f;
+    }
+    const T e0 = fma(d0, d0, eps), e1 = fma(d1, d1, eps);
+    const T n0 = T(1.0 / 3.0) * (e1 * e1), n1 = T(2.0 / 3.0) * (e0 * e0);
+    return fma(n0 * frcp(n0 + n1), q0 - q1, q1);
+}
+
 // error-free sum (Knuth's TwoSum): s + e == a + b exactly
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -554,7 +585,7 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
 // ---- the stage kernel -------------------------------------------------------------
 // One stage on the tile (bx, by) of the simulation described by `a`; nb is the
 // number of CTAs working on that simulation in this launch (for the ticket).
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
     constexpr int NT = TX * TY;
@@ -659,6 +690,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     __syncthreads();
     const double t_now = s_t, dt = s_dt;
     const T dtT = s_dtT;
+    // budget weight of this stage relative to the two-step Euler's 1/2
+    const double bwf = a.rk3 ? 2.0 * a.rk3_bw : 1.0;
     if constexpr (VIS) {
         // fluid velocity of every cell of the slope tile (0 where the fluid is
         // dry), with the same dry threshold as the cell update
@@ -686,7 +719,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     // the y-slope of cell (x0+lx, y0-1+ly').  Each thread takes both slopes of
     // its own cell, then a share of the halo ones (x: columns -1 and TX; y:
     // rows -1 and TY), so that only the halo needs index arithmetic.
-    {
+    // (The WENO form reconstructs each face value in the face loop instead.)
+    if constexpr (!WENO) {
         const int lx = tid % TX, ly = tid / TX;
         const T *p = sU + (ly + 2) * SW + lx + 2;
 #pragma unroll
@@ -736,8 +770,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         T um[6], up[6];
 #pragma unroll
         for (int c = 0; c < 6; c++) {
-            um[c] = fma(T(0.5), sSx[c * NSX + os], sU[c * SP + ou]);
-            up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
+            if constexpr (WENO) {
+                const T *p = sU + c * SP + ou;
+                um[c] = weno3_face(p[-1], p[0], p[1]);
+                up[c] = weno3_face(p[2], p[1], p[0]);
+                if (c == 0 || c == 3) {  // masses stay >= 0 at the faces
+                    um[c] = fmax(um[c], T(0));
+                    up[c] = fmax(up[c], T(0));
+                }
+            } else {
+                um[c] = fma(T(0.5), sSx[c * NSX + os], sU[c * SP + ou]);
+                up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
+            }
         }
         T H[7];
         if constexpr (CU) face_flux2_cu<T, 0>(um, up, G, H);
@@ -751,7 +795,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
         if (!a.debug_stage && (i == -1 || i == nx - 1)) {
             // Heun weight 1/2 x boundary volume flux of this stage
-            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dy) * (i == -1 ? 1.0 : -1.0);
+            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dy) * (i == -1 ? 1.0 : -1.0) * bwf;
             atomicAdd(&acc[0], w * (double)H[0]);
             atomicAdd(&acc[1], w * (double)H[3]);
         }
@@ -774,8 +818,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         T um[6], up[6];
 #pragma unroll
         for (int c = 0; c < 6; c++) {
-            um[c] = fma(T(0.5), sSy[c * NSY + os], sU[c * SP + ou]);
-            up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
+            if constexpr (WENO) {
+                const T *p = sU + c * SP + ou;
+                um[c] = weno3_face(p[-SW], p[0], p[SW]);
+                up[c] = weno3_face(p[2 * SW], p[SW], p[0]);
+                if (c == 0 || c == 3) {
+                    um[c] = fmax(um[c], T(0));
+                    up[c] = fmax(up[c], T(0));
+                }
+            } else {
+                um[c] = fma(T(0.5), sSy[c * NSY + os], sU[c * SP + ou]);
+                up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
+            }
         }
         T H[7];
         if constexpr (CU) face_flux2_cu<T, 1>(um, up, G, H);
@@ -787,7 +841,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
 #pragma unroll
         for (int c = 0; c < 7; c++) sHy[c * NYF + f] = H[c];
         if (!a.debug_stage && (j == -1 || j == ny - 1)) {
-            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dx) * (j == -1 ? 1.0 : -1.0);
+            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dx) * (j == -1 ? 1.0 : -1.0) * bwf;
             atomicAdd(&acc[0], w * (double)H[0]);
             atomicAdd(&acc[1], w * (double)H[3]);
         }
@@ -976,7 +1030,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             const int c = 3 * ph;
             if (negative(out[c])) {
                 if (!a.debug_stage) {
-                    atomicAdd(&acc[2 + ph], -0.5 * ((double)out[c] + (double)lo[ph]) * a.ph.cell_area);
+                    atomicAdd(&acc[2 + ph], -0.5 * ((double)out[c] + (double)lo[ph]) * a.ph.cell_area * bwf);
                     atomicAdd(&acc_n, 1u);
                 }
                 out[c] = T(0);
@@ -987,7 +1041,38 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                 out[c + 2] = T(0);
             }
         }
-        if (a.stage == 2 && !a.debug_stage) {
+        if (a.stage == 2 && !a.debug_stage && a.rk3) {
+            // three-stage Runge-Kutta: out + w (U^n - out), w = 3/4 (stage 2)
+            // or 1/3 (stage 3); the weights sum to 1 exactly in any precision
+            const T wn = a.rk3 == 2 ? T(0.75) : T(1.0 / 3.0);
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                if constexpr (sizeof(T) == 4) {
+                    if (c == 0 || c == 3) {
+                        // on (value, remainder) pairs: d = (U^n + R^n) - (out + lo)
+                        float dh, dl, sv, e;
+                        two_sum(a.Un[c * plane + g], -out[c], dh, dl);
+                        dl += a.Rn[(c / 3) * plane + g] - lo[c / 3];
+                        const float pr = wn * dh;
+                        const float pe = fmaf(wn, dh, -pr) + wn * dl;  // exact product error + low part
+                        two_sum(out[c], pr, sv, e);
+                        e += lo[c / 3] + pe;
+                        out[c] = sv + e;
+                        lo[c / 3] = e - (out[c] - sv);
+                        continue;
+                    }
+                }
+                out[c] = fma(wn, a.Un[c * plane + g] - out[c], out[c]);
+            }
+#pragma unroll
+            for (int ph = 0; ph < 2; ph++)
+                if (!gtp(out[3 * ph], jhd)) {
+                    out[3 * ph + 1] = T(0);
+                    out[3 * ph + 2] = T(0);
+                }
+            if (a.rk3 == 3 && a.want_amax)
+                speed = cell_speed(out, CG(GC_JHD), CG(GC_SXS), CG(GC_SXF), CG(GC_SYS), CG(GC_SYF));
+        } else if (a.stage == 2 && !a.debug_stage) {
             // Heun average with U^n (same cell), dry momentum again
 #pragma unroll
             for (int c = 0; c < 6; c++) {
@@ -1021,14 +1106,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             a.Rout[g] = lo[0];
             a.Rout[plane + g] = lo[1];
         }
-        if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, out, t_now + dt);
+        // ghosts at the time of this stage's output (the second RK3 stage: t + dt/2)
+        if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, out, t_now + (a.rk3 == 2 ? 0.5 * dt : dt));
     }
 
     if (a.debug_stage) return;
 
     // ---- CTA reductions ---------------------------------------------------
     if (bad) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
-    if (a.stage == 2 && a.want_amax) {
+    const bool finalize = a.stage == 2 && a.rk3 != 2;  // the step's last stage
+    if (finalize && a.want_amax) {
         if (nonfinite(speed)) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) speed = maxnn(speed, __shfl_xor_sync(0xffffffffu, speed, o));
@@ -1044,7 +1131,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             atomicAdd(&ctl->clamp_cells, (unsigned long long)acc_n);
         }
         if (a.stage == 1 && bx == 0 && by == 0) ctl->dt = dt;
-        if (a.stage == 2) {
+        if (finalize) {
             if (a.want_amax) {
                 T m = T(0);
                 for (int w = 0; w < NT / 32; w++) m = maxnn(m, red[w]);
@@ -1054,7 +1141,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             last_block = (atomicAdd(&ctl->ticket, 1u) == nb - 1);
         }
     }
-    if (a.stage != 2) return;
+    if (!finalize) return;
     __syncthreads();
     if (last_block && tid == 0) {
         __threadfence();
@@ -1068,10 +1155,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
 }
 
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
 {
-    stage_tile<T, TX, TY, REC, VIS, CU>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+    stage_tile<T, TX, TY, REC, VIS, CU, WENO>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // Ensemble form: one launch runs the same stage of many simulations.  Each CTA

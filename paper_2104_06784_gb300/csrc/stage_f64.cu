@@ -6,7 +6,7 @@
 namespace moses {
 namespace {
 
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
 int launch_tile(const StageArgs<T> &a, cudaStream_t st)
 {
     constexpr size_t smem = stage_smem_bytes<T, TX, TY, VIS>();
@@ -14,13 +14,13 @@ int launch_tile(const StageArgs<T> &a, cudaStream_t st)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC, VIS, CU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC, VIS, CU, WENO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return -1;
         attr_set[dev] = true;
     }
     const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-    stage_kernel<T, TX, TY, REC, VIS, CU><<<grid, TX * TY, smem, st>>>(a);
+    stage_kernel<T, TX, TY, REC, VIS, CU, WENO><<<grid, TX * TY, smem, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -31,11 +31,18 @@ template <>
 int launch_stage<double>(const StageArgs<double> &a, int tile, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    // the viscous and the central-upwind forms: one tile shape
-    if (a.ph.scheme == 1)
-        return a.ph.nu_f > 0.0 ? launch_tile<double, 32, 8, false, true, true>(a, st)
-                               : launch_tile<double, 32, 8, false, false, true>(a, st);
-    if (a.ph.nu_f > 0.0) return launch_tile<double, 32, 8, false, true>(a, st);
+    // the model options (viscous term, central-upwind flux, WENO): one tile shape
+    const bool vis = a.ph.nu_f > 0.0, cu = a.ph.scheme == 1, weno = a.ph.recon == 1;
+    if (weno) {
+        if (cu)
+            return vis ? launch_tile<double, 32, 8, false, true, true, true>(a, st)
+                       : launch_tile<double, 32, 8, false, false, true, true>(a, st);
+        return vis ? launch_tile<double, 32, 8, false, true, false, true>(a, st)
+                   : launch_tile<double, 32, 8, false, false, false, true>(a, st);
+    }
+    if (cu)
+        return vis ? launch_tile<double, 32, 8, false, true, true>(a, st) : launch_tile<double, 32, 8, false, false, true>(a, st);
+    if (vis) return launch_tile<double, 32, 8, false, true>(a, st);
     switch (tile) {
     case 1: return launch_tile<double, 32, 4>(a, st);
     case 2: return launch_tile<double, 32, 16>(a, st);

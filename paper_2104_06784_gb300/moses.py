@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("delta_b_deg", C.c_double), ("phi_int_deg", C.c_double), ("k_mode", C.c_int),
                 ("c_d", C.c_double), ("nu_f", C.c_double), ("k_f", C.c_double),
                 ("cfl", C.c_double), ("dt_max", C.c_double), ("h_dry", C.c_double),
-                ("bc", C.c_int * 4), ("fluid_pg_mode", C.c_int), ("precision", C.c_int), ("scheme", C.c_int)]
+                ("bc", C.c_int * 4), ("fluid_pg_mode", C.c_int), ("precision", C.c_int), ("scheme", C.c_int),
+                ("recon", C.c_int), ("rk", C.c_int)]
 
     @classmethod
     def from_dict(cls, p: dict, precision: int = FP64) -> "Params":
@@ -47,8 +48,8 @@ class Params(C.Structure):
                 setattr(s, name, int(p[name]))
             elif name == "precision":
                 s.precision = int(p.get("precision", precision))
-            elif name == "scheme":
-                s.scheme = int(p.get("scheme", 0))
+            elif name in ("scheme", "recon", "rk"):
+                setattr(s, name, int(p.get(name, 2 if name == "rk" else 0)))
             else:
                 setattr(s, name, float(p[name]))
         return s

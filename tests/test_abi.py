@@ -83,6 +83,7 @@ def test_null_pointers(L):
     L.moses_destroy(None)
 
 
-def test_create_rejects_bad_scheme(L):
-    rc, h = _create(np.zeros((4, 4)), 4, 4, scheme=2)
-    assert rc == moses.MOSES_EINVAL and b"scheme" in L.moses_last_error(None)
+@pytest.mark.parametrize("field,value", [("scheme", 2), ("recon", 2), ("recon", -1), ("rk", 1), ("rk", 4)])
+def test_create_rejects_bad_scheme_options(L, field, value):
+    rc, h = _create(np.zeros((4, 4)), 4, 4, **{field: value})
+    assert rc == moses.MOSES_EINVAL and field.encode() in L.moses_last_error(None)

@@ -337,6 +337,128 @@ def test_central_upwind_not_in_batch_or_adjoint():
 
 
 # ----------------------------------------------------------------------------
+# third-order WENO face values (recon 1) and the three-stage SSP Runge-Kutta
+# (rk 3): the higher-order options of Sect. 2.2
+
+
+@pytest.mark.parametrize("nx,ny", [(77, 53), (33, 9), (1, 17), (23, 1), (2, 2)])
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1), (0, 1, 1, 0)])
+def test_stage_parity_weno_fp64(nx, ny, bc):
+    rng = np.random.default_rng(nx * 53 + ny)
+    dem = W.spectral_dem(nx, ny, 5.0, 2.2, 40.0, seed=nx + 7 * ny) + rng.random((ny, nx))
+    cfg = _random_case(nx, ny, dem, bc, seed=nx * ny + 23, recon=1)
+    g, o = both(cfg)
+    for t, dt in ((0.0, 0.01), (3.0, 0.05)):
+        err = rel_maxnorm(g.stage(t, dt), o.stage(t, dt))
+        assert err < TOL64, f"WENO stage parity {err} ({nx}x{ny}, bc={bc})"
+    o0 = oracle_from_config(dict(cfg, params=dict(cfg["params"], recon=0)))
+    if nx > 2 or ny > 2:
+        assert rel_maxnorm(o0.stage(0.0, 0.01), o.stage(0.0, 0.01)) > 1e-7
+
+
+@pytest.mark.parametrize("scheme,nu_f", [(1, 0.0), (0, 1.5), (1, 1.5)])
+def test_stage_parity_weno_with_other_options(scheme, nu_f):
+    nx, ny = 70, 41
+    cfg = W.inflow_config(nx=nx, ny=ny, dx=5.0, inlet_cells=9)
+    cfg.update(W.random_state(nx, ny, seed=9))
+    cfg["params"] = dict(cfg["params"], recon=1, scheme=scheme, nu_f=nu_f, k_f=0.3, c_d=0.05)
+    g, o = both(cfg)
+    for t in (0.0, 61.0):
+        err = rel_maxnorm(g.stage(t, 0.02), o.stage(t, 0.02))
+        assert err < TOL64, f"WENO stage parity {err} at t={t} (scheme {scheme}, nu_f {nu_f})"
+
+
+def _rounding_sensitivity(cfg, steps, h_min=0.01):
+    """How far the FP64 oracle itself moves when its momenta are rounded to
+    FP32 after every step (the masses of the FP32 form are compensated, so
+    they are left alone): relative L1 of depth and velocities after `steps`,
+    as in `_fp32_vs_oracle`.  This measures the conditioning of the case, on
+    the oracle alone."""
+    a, b = oracle_from_config(cfg), oracle_from_config(cfg)
+    J = a.geometry()["J"]
+    hd = cfg["params"]["h_dry"]
+    for _ in range(steps):
+        a.step(1)
+        b.step(1)
+        U = b.get_U()
+        for c in (1, 2, 4, 5):
+            U[c] = U[c].astype(np.float32).astype(np.float64)
+        b.set_U(U)
+    ha, va, pa = _fields(a.get_U(), J, hd)
+    hb, vb, pb = _fields(b.get_U(), J, hd)
+    out = {"h": rel_l1(hb, ha)}
+    for name, x, y, dx_, dy_ in zip(("vx_s", "vy_s", "vx_f", "vy_f"), vb, va, pb, pa):
+        deep = (dx_ > h_min) & (dy_ > h_min)
+        out[name] = rel_l1(x[deep], y[deep])
+    return out
+
+
+@pytest.mark.parametrize("recon,rk,scheme", [(0, 3, 0), (1, 2, 0), (1, 3, 0), (1, 3, 1)])
+def test_higher_order_trajectories(recon, rk, scheme):
+    """Arc-plane release, 300 steps at CFL 0.1 with WENO faces and / or the
+    three-stage Runge-Kutta: FP64 at 1e-10; FP32 at 2e-4 (depth, velocities
+    on cells > 1 cm) with mass drift <= 1e-7.  With the central-upwind flux a
+    fluid film at the dry threshold amplifies rounding: the oracle alone,
+    with its momenta rounded to FP32 after each step, moves the fluid
+    velocities by ~4e-5 at step 300 (vs ~1e-7 with the central flux).  The
+    FP32 form rounds every operation of each stage, not only the stored
+    state, so a field's bar is max(2e-4, 10 x that sensitivity)."""
+    cfg = W.release_config(nx=64, ny=64, cfl=0.1, recon=recon, rk=rk, scheme=scheme)
+    g, o = both(cfg)
+    g.step(300)
+    o.step(300)
+    assert rel_maxnorm(g.get_conserved(), o.get_U()) < TOL64
+    assert abs(g.budget()["t"] - o.budget()["t"]) <= 1e-12 * o.budget()["t"]
+    sens = _rounding_sensitivity(cfg, 300)
+    for m, errs in _fp32_vs_oracle(cfg, (300,)).items():
+        for k, v in errs.items():
+            lim = 1e-7 if k == "drift" else max(2e-4, 10 * sens[k])
+            assert v <= lim, (k, v, lim, recon, rk, scheme)
+
+
+def test_rk3_inflow_budget_fp64_and_fp32():
+    """Channel-and-fan inflow with WENO and the three-stage Runge-Kutta: the
+    state at 1e-10 of the oracle's after 600 steps and the boundary inflow
+    volume (weights 1/6, 1/6, 2/3 over the stages) closing the mass budget in
+    both forms."""
+    cfg = W.inflow_config(nx=96, ny=48, dx=5.0, inlet_cells=8, recon=1, rk=3)
+    g, o = both(cfg)
+    g.step(600)
+    o.step(600)
+    assert rel_maxnorm(g.get_conserved(), o.get_U()) < TOL64
+    bg, bo = g.budget(), o.budget()
+    for ph in ("s", "f"):
+        assert abs(bg[f"bnd_in_{ph}"] - bo[f"bnd_in_{ph}"]) <= 1e-10 * abs(bo[f"bnd_in_{ph}"])
+    f = moses.from_config(cfg, precision=moses.FP32)
+    f.step(600)
+    b = f.budget()
+    for ph in ("s", "f"):
+        closure = b[f"vol_{ph}"] - b[f"bnd_in_{ph}"] - b[f"clamp_{ph}"]
+        assert abs(closure) <= 1e-7 * b[f"vol_{ph}"], f"FP32 RK3 inflow budget {closure / b[f'vol_{ph}']}"
+
+
+def test_weno_dry_cells_stay_finite_fp32():
+    """All-dry neighbourhoods give zero WENO indicators; the FP32 weights must
+    stay finite there (no 0/0)."""
+    cfg = W.release_config(nx=40, ny=40, cfl=0.2, recon=1)
+    with moses.from_config(cfg, precision=moses.FP32) as g:
+        g.step(50)
+        assert np.isfinite(g.get_conserved()).all()  # a non-finite step raises
+
+
+@pytest.mark.parametrize("over", [dict(recon=1), dict(rk=3)])
+def test_higher_order_not_in_batch_or_adjoint(over):
+    cfg = W.release_config(nx=20, ny=20, **over)
+    a = moses.from_config(cfg)
+    with pytest.raises(moses.MosesError):
+        moses.Batch([a])
+    with pytest.raises(moses.MosesError):
+        a.adjoint_misfit(5, np.zeros((20, 20)))
+    with pytest.raises(moses.MosesError):
+        a.stage_adjoint(0.0, 0.01, np.zeros((6, 20, 20)))
+
+
+# ----------------------------------------------------------------------------
 # edge cases
 
 
