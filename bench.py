@@ -56,8 +56,9 @@ WORDS_PER_CELL_STEP = 13
 # size, so a launch at side n moves n^2 times this.
 TRAFFIC = {
     # ncu, 2048^2 spectral-DEM release, one launch each (profiles/stage_kernel_traffic_2048_release.md)
-    ("f64", "32x16", "4b0a78a3454a"): 312.01,
-    ("f32", "32x8", "4b0a78a3454a"): 72.41,
+    ("f64", "32x8", "1e6157da0d6b"): 311.66,
+    ("f64", "32x16", "1e6157da0d6b"): 311.98,
+    ("f32", "32x8", "1e6157da0d6b"): 72.32,
 }
 
 

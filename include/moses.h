@@ -211,7 +211,7 @@ int moses_max_speed(moses_sim *s, double *amax);
 /* FP64 budgets, reduced on the GPU: out[0..1] solid / fluid volume
  * sum(U1), sum(U4) dx dy [m^3]; out[2..5] momenta sum(U2, U3, U5, U6) dx dy;
  * out[6..7] time-integrated boundary volume inflow per phase (the computed
- * face fluxes, Heun weights); out[8..9] volume added by the positivity clamp
+ * face fluxes with the stage weights of the step); out[8..9] volume added by the positivity clamp
  * per phase; out[10] clamp events; out[11] t; out[12] steps taken. */
 int moses_get_budget(moses_sim *s, double out[MOSES_BUDGET_LEN]);
 

@@ -619,7 +619,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     const KT<T> &k = a.k;
     const T *geo = a.geo;
     Ctl *ctl = a.ctl;
-    __shared__ double s_t, s_dt;
+    __shared__ double s_dt, s_tg, s_bwf;
     __shared__ T s_dtT;
 
     // the step's time and time step, once per CTA
@@ -635,9 +635,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             t_now = ctl->t;
             dt = ctl->dt;
         }
-        s_t = t_now;
         s_dt = dt;
         s_dtT = (T)dt;
+        // ghosts at the time of this stage's output (the second RK3 stage: t + dt/2)
+        s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
+        // budget weight of this stage relative to the two-step Euler's 1/2
+        s_bwf = a.rk3 ? 2.0 * a.rk3_bw : 1.0;
         acc_n = 0;
     }
     if (tid < 4) acc[tid] = 0.0;
@@ -688,10 +691,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
     cp_async_wait_all();
     __syncthreads();
-    const double t_now = s_t, dt = s_dt;
+    const double dt = s_dt;
     const T dtT = s_dtT;
-    // budget weight of this stage relative to the two-step Euler's 1/2
-    const double bwf = a.rk3 ? 2.0 * a.rk3_bw : 1.0;
+    const double bwf = s_bwf;
     if constexpr (VIS) {
         // fluid velocity of every cell of the slope tile (0 where the fluid is
         // dry), with the same dry threshold as the cell update
@@ -1106,8 +1108,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             a.Rout[g] = lo[0];
             a.Rout[plane + g] = lo[1];
         }
-        // ghosts at the time of this stage's output (the second RK3 stage: t + dt/2)
-        if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, out, t_now + (a.rk3 == 2 ? 0.5 * dt : dt));
+        if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, out, s_tg);
     }
 
     if (a.debug_stage) return;

@@ -2,7 +2,8 @@
 as the oracle: closed-box conservation, bodies at rest (lake, mixture, heap),
 the Ritter dam break, the Savage-Hutter similarity solution, drag and wave
 speeds, 90-degree rotation invariance, the closed box, the viscous and fluid
-friction checks and the central-upwind pins.  Each pin builds its inputs and
+friction checks, the central-upwind pins and the WENO / three-stage
+Runge-Kutta pins.  Each pin builds its inputs and
 runs a simulation through `_sim`; here `_sim` returns a GPU simulation with
 the oracle's interface, so the kernels are checked against closed forms and
 invariants directly, not only against the oracle.  (Pins that read the
@@ -27,6 +28,9 @@ class GpuSim:
 
     def set_release(self, h, phi_s, vx_s=None, vy_s=None, vx_f=None, vy_f=None):
         self.s.set_release(h, phi_s, vx_s, vy_s, vx_f, vy_f)
+
+    def set_inflow(self, side, i0, i1, t, Q, phi):
+        self.s.set_inflow(side, i0, i1, t, Q, phi)
 
     def set_U(self, U):
         self.s.set_conserved(U)
@@ -63,7 +67,9 @@ class GpuSim:
 GPU_PINS = [P.pin_conservation_closed, P.pin_lake_flat, P.pin_lake_plane, P.pin_mixture_plane_rest,
             P.pin_mixture_no_separation, P.pin_heap_rest, P.pin_ritter, P.pin_savage_hutter, P.pin_drag,
             P.pin_wave_speed, P.pin_rotation, P.pin_friction, P.pin_closed_box, P.pin_viscous,
-            P.pin_fluid_friction, P.pin_cu_upwind_dependence, P.pin_cu_conservation_and_ritter, P.pin_cu_rotation]
+            P.pin_fluid_friction, P.pin_cu_upwind_dependence, P.pin_cu_conservation_and_ritter, P.pin_cu_rotation,
+            P.pin_weno_linear_exact, P.pin_weno_rk3_dam_break, P.pin_weno_smooth_order, P.pin_rk3_drag_factor,
+            P.pin_weno_rk3_budgets_and_rotation]
 
 
 @pytest.mark.parametrize("pin", GPU_PINS, ids=lambda f: f.__name__)
