@@ -171,7 +171,28 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
     // parameter partials: per cell and across the warp in T, per CTA and
     // globally in FP64 (the FP64 pipe of GB300 is 1/64 of its FP32 rate)
     T g_tan = T(0), g_cd = T(0);
+    bool dry_cell = false;
     if (i < nx && j < ny) {
+        // no mass before the stage nor in its trial output: velocities,
+        // pressures, sources and friction are 0 and the dry rule zeroes the
+        // momenta, so the reverse passes the mass adjoints through and gives 0
+        // for the rest (what the full computation below gives for such a cell)
+        const long long g = cell_index(i, j, pitch);
+        if (a.Uin[g] == T(0) && a.Uin[3 * plane + g] == T(0) && a.rec[g] == T(0) && a.rec[3 * plane + g] == T(0)) {
+            dry_cell = true;
+            const T l0 = q.heun == 2 ? T(0.5) * q.lam_next[g] : q.lam_out[g];
+            const T l3 = q.heun == 2 ? T(0.5) * q.lam_next[3 * plane + g] : q.lam_out[3 * plane + g];
+            const T lp[6] = {l0, T(0), T(0), l3, T(0), T(0)};
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                q.lam_pre[c * plane + g] = lp[c];
+                q.lam_acc[c * plane + g] = lp[c];
+            }
+            q.lam_dp[g] = T(0);
+            q.lam_dp[plane + g] = T(0);
+        }
+    }
+    if (i < nx && j < ny && !dry_cell) {
         const long long g = cell_index(i, j, pitch);
         T u[6], pre4[4];
 #pragma unroll
@@ -565,6 +586,29 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
     __syncthreads();
 }
 
+// The ghost-cell adjoints a tile owns along direction D (as adj_face_dir
+// writes them), set to 0: a tile without face terms
+template <typename T, int TX, int TY, int D>
+__device__ __forceinline__ void adj_ghost_zero(const AdjArgs<T> &q)
+{
+    constexpr int NT = TX * TY;
+    constexpr int L = D == 0 ? TX : TY, M = D == 0 ? TY : TX;
+    const StageArgs<T> &a = q.f;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int o0 = D == 0 ? x0 : y0;
+    const int n = D == 0 ? a.nx : a.ny, nt = D == 0 ? a.ny : a.nx;
+    for (int e = threadIdx.x; e < 4 * M; e += NT) {
+        const int m = e / 4, w = e - m * 4;
+        const int line = (D == 0 ? y0 : x0) + m;
+        if (line >= nt) continue;
+        const int gpos = w < 2 ? -1 - w : n + (w - 2);
+        if (w < 2 ? o0 != 0 : !(o0 <= n - 1 && n - 1 < o0 + L)) continue;
+        const long long g = D == 0 ? cell_index(gpos, line, a.pitch) : cell_index(line, gpos, a.pitch);
+#pragma unroll
+        for (int c = 0; c < 6; c++) q.lam_in[c * a.plane + g] = T(0);
+    }
+}
+
 // FP32: three 256-thread CTAs per SM (80 registers); FP64: shared memory allows two
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY)) adj_face_kernel(const AdjArgs<T> q)
@@ -585,61 +629,95 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
-    // each thread copies its own cell, then a share of the halo cells
-    if constexpr (SM::STAGE) {
-        // lam_pre (6) and lam_dp (2) of the tile and a 2-cell halo; 0 outside the domain
-        const auto copy_lam = [&](const int tx, const int ty) {
-            const int gi = x0 + tx, gj = y0 + ty;
-            const bool ok = gi >= 0 && gj >= 0 && gi < nx && gj < ny;
-            const long long g = ok ? cell_index(gi, gj, pitch) : 0;
-            T *dst = sLam + (ty + 2) * SM::LW + tx + 2;
-#pragma unroll
-            for (int c = 0; c < 8; c++)
-                cp_async_elem(dst + c * SM::LP, c < 6 ? q.lam_pre + c * plane + g : q.lam_dp + (c - 6) * plane + g, ok);
-        };
-        copy_lam(tid % TX, tid / TX);
-        for (int h = tid; h < SM::LP - NT; h += NT) {
-            int tx, ty;
-            halo_cell<TX, TY, 2>(h, tx, ty);
-            copy_lam(tx, ty);
-        }
-        // bed slopes of the same box (computed for cells -2 .. n+1)
-        const auto copy_slopes = [&](const int tx, const int ty) {
-            const int gi = x0 + tx, gj = y0 + ty;
-            const bool ok = gi >= -2 && gj >= -2 && gi <= nx + 1 && gj <= ny + 1;
-            const T *src = a.geo + (ok ? GS_SX * plane + cell_index(gi, gj, pitch) : 0);
-            T *dst = sBs + (ty + 2) * SM::LW + tx + 2;
-#pragma unroll
-            for (int c = 0; c < 4; c++) cp_async_elem(dst + c * SM::LP, src + (ok ? c * plane : 0), ok);
-        };
-        copy_slopes(tid % TX, tid / TX);
-        for (int h = tid; h < SM::LP - NT; h += NT) {
-            int tx, ty;
-            halo_cell<TX, TY, 2>(h, tx, ty);
-            copy_slopes(tx, ty);
-        }
-    }
-    // stage input with a 3-cell halo (cells beyond the 2 ghost layers read 0;
-    // no forward face uses them)
-    const auto copy_u = [&](const int tx, const int ty) {
+    // The stage input's masses with a 3-cell halo come first (cells beyond
+    // the 2 ghost layers read 0; no forward face uses them).  Where none of
+    // them holds mass, every face state of the tile is dry: the side fluxes'
+    // derivatives vanish (velocities, pressures and speeds are 0 and the
+    // speed's square root is differentiated as 0 at 0), so the tile has no
+    // face terms and skips them; its cells keep their own contributions.
+    const auto copy_u = [&](const int tx, const int ty, const bool masses) {
         const int gi = x0 + tx, gj = y0 + ty;
         const bool ok = gi >= -2 && gj >= -2 && gi < nx + 2 && gj < ny + 2;
         const T *src = a.Uin + (ok ? cell_index(gi, gj, pitch) : 0);
         T *dst = sU + (ty + 3) * SW3 + tx + 3;
 #pragma unroll
-        for (int c = 0; c < 6; c++) cp_async_elem(dst + c * SP3, src + (ok ? c * plane : 0), ok);
+        for (int q4 = 0; q4 < 4; q4++) {
+            const int c = masses ? (q4 == 0 ? 0 : 3) : (q4 < 2 ? q4 + 1 : q4 + 2);
+            if (!masses || q4 < 2) cp_async_elem(dst + c * SP3, src + (ok ? c * plane : 0), ok);
+        }
     };
-    copy_u(tid % TX, tid / TX);
+    copy_u(tid % TX, tid / TX, true);
     for (int h = tid; h < SP3 - NT; h += NT) {
         int tx, ty;
         halo_cell<TX, TY, 3>(h, tx, ty);
-        copy_u(tx, ty);
+        copy_u(tx, ty, true);
     }
     cp_async_wait_all();
-    __syncthreads();
+    bool has_mass;
+    {
+        const auto massy = [&](const int tx, const int ty) {
+            const int o = (ty + 3) * SW3 + tx + 3;
+            return sU[o] != T(0) || sU[3 * SP3 + o] != T(0);
+        };
+        has_mass = massy(tid % TX, tid / TX);
+        for (int h = tid; h < SP3 - NT; h += NT) {
+            int tx, ty;
+            halo_cell<TX, TY, 3>(h, tx, ty);
+            has_mass |= massy(tx, ty);
+        }
+    }
+    const bool wet = __syncthreads_or(has_mass) != 0;
     T lres[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
-    adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
+    if (wet) {  // CTA-uniform
+        // the momenta; FP32 also the cell adjoints and bed slopes of the box
+        if constexpr (SM::STAGE) {
+            // lam_pre (6) and lam_dp (2) of the tile and a 2-cell halo; 0 outside the domain
+            const auto copy_lam = [&](const int tx, const int ty) {
+                const int gi = x0 + tx, gj = y0 + ty;
+                const bool ok = gi >= 0 && gj >= 0 && gi < nx && gj < ny;
+                const long long g = ok ? cell_index(gi, gj, pitch) : 0;
+                T *dst = sLam + (ty + 2) * SM::LW + tx + 2;
+#pragma unroll
+                for (int c = 0; c < 8; c++)
+                    cp_async_elem(dst + c * SM::LP, c < 6 ? q.lam_pre + c * plane + g : q.lam_dp + (c - 6) * plane + g, ok);
+            };
+            copy_lam(tid % TX, tid / TX);
+            for (int h = tid; h < SM::LP - NT; h += NT) {
+                int tx, ty;
+                halo_cell<TX, TY, 2>(h, tx, ty);
+                copy_lam(tx, ty);
+            }
+            // bed slopes of the same box (computed for cells -2 .. n+1)
+            const auto copy_slopes = [&](const int tx, const int ty) {
+                const int gi = x0 + tx, gj = y0 + ty;
+                const bool ok = gi >= -2 && gj >= -2 && gi <= nx + 1 && gj <= ny + 1;
+                const T *src = a.geo + (ok ? GS_SX * plane + cell_index(gi, gj, pitch) : 0);
+                T *dst = sBs + (ty + 2) * SM::LW + tx + 2;
+#pragma unroll
+                for (int c = 0; c < 4; c++) cp_async_elem(dst + c * SM::LP, src + (ok ? c * plane : 0), ok);
+            };
+            copy_slopes(tid % TX, tid / TX);
+            for (int h = tid; h < SM::LP - NT; h += NT) {
+                int tx, ty;
+                halo_cell<TX, TY, 2>(h, tx, ty);
+                copy_slopes(tx, ty);
+            }
+        }
+        copy_u(tid % TX, tid / TX, false);
+        for (int h = tid; h < SP3 - NT; h += NT) {
+            int tx, ty;
+            halo_cell<TX, TY, 3>(h, tx, ty);
+            copy_u(tx, ty, false);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
+        adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
+    } else {
+        // the ghost cells this tile owns get no face terms either
+        adj_ghost_zero<T, TX, TY, 0>(q);
+        adj_ghost_zero<T, TX, TY, 1>(q);
+    }
     const int i = x0 + tid % TX, j = y0 + tid / TX;
     if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
@@ -647,7 +725,8 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
         if (q.heun == 1) {
             if constexpr (FaceAdjSmem<T, TX, TY>::STAGE) {  // as the FP32 stage: J h_dry from the slopes
                 const int o = (tid / TX + 2) * FaceAdjSmem<T, TX, TY>::LW + tid % TX + 2;
-                const T sX = sBs[o], sY = sBs[FaceAdjSmem<T, TX, TY>::LP + o];
+                const T sX = wet ? sBs[o] : a.geo[GS_SX * plane + g];
+                const T sY = wet ? sBs[FaceAdjSmem<T, TX, TY>::LP + o] : a.geo[GS_SY * plane + g];
                 const T s2 = fma(sX, sX, fma(sY, sY, T(1)));
                 jhd = s2 * frsqrt(s2) * a.k.h_dry;
             } else {

@@ -647,220 +647,280 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
 
     // ---- stage the tile + 2-cell halo of the six state planes -----------
     // (asynchronous copies: every element of the thread in flight at once).
-    // Each thread copies its own cell, then one cell of the halo if any, so
-    // that only the halo needs index arithmetic.
+    // Each thread takes its own cell, then one cell of the halo if any, so
+    // that only the halo needs index arithmetic.  The two mass planes come
+    // first: they decide whether the tile has any work (below).
+    constexpr int HMAX = (SP - NT + NT - 1) / NT;  // halo cells per thread, at most
+    constexpr int NE = HMAX + 1;
+    int eo[NE];        // shared-memory offset of each staged cell (-1: none)
+    long long eg[NE];  // its global index
+    bool eok[NE];      // inside the ghost-extended grid (else zero-filled)
     {
-        const auto copy_state = [&](int tx, int ty) {  // tile coordinates, -2 .. TX+1 / TY+1
+        const auto entry = [&](int e, int tx, int ty) {  // tile coordinates, -2 .. TX+1 / TY+1
             const int gi = x0 + tx, gj = y0 + ty;
-            const bool ok = gi < nx + 2 && gj < ny + 2;
-            const T *src = a.Uin + (ok ? cell_index(gi, gj, pitch) : 0);
-            T *dst = sU + (ty + 2) * SW + tx + 2;
-#pragma unroll
-            for (int c = 0; c < 6; c++) cp_async_elem(dst + c * SP, src + (ok ? c * plane : 0), ok);
+            eok[e] = gi < nx + 2 && gj < ny + 2;
+            eg[e] = eok[e] ? cell_index(gi, gj, pitch) : 0;
+            eo[e] = (ty + 2) * SW + tx + 2;
         };
-        copy_state(tid % TX, tid / TX);
+        entry(0, tid % TX, tid / TX);
         constexpr int RW = 2 * SW;  // cells in two full halo rows
-        for (int h = tid; h < SP - NT; h += NT) {
-            if (h < RW) copy_state(h % SW - 2, h / SW - 2);                  // rows -2, -1
-            else if (h < 2 * RW) copy_state((h - RW) % SW - 2, TY + (h - RW) / SW);  // rows TY, TY+1
-            else {                                                            // columns -2, -1, TX, TX+1
-                const int r = h - 2 * RW, k = r & 3;
-                copy_state(k < 2 ? k - 2 : TX + k - 2, r >> 2);
+#pragma unroll
+        for (int r = 0; r < HMAX; r++) {
+            const int h = tid + r * NT;
+            eo[r + 1] = -1;
+            if (h >= SP - NT) continue;
+            if (h < RW) entry(r + 1, h % SW - 2, h / SW - 2);                     // rows -2, -1
+            else if (h < 2 * RW) entry(r + 1, (h - RW) % SW - 2, TY + (h - RW) / SW);  // rows TY, TY+1
+            else {                                                              // columns -2, -1, TX, TX+1
+                const int q = h - 2 * RW, kk = q & 3;
+                entry(r + 1, kk < 2 ? kk - 2 : TX + kk - 2, q >> 2);
             }
         }
     }
-    if constexpr (SL) {
-        // slope tile: cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
-        const auto copy_slopes = [&](int tx, int ty) {  // tile coordinates, -1 .. TX / TY
-            const int gi = x0 + tx, gj = y0 + ty;
-            const bool ok = gi <= nx && gj <= ny;
-            const T *src = geo + (ok ? GS_SX * plane + cell_index(gi, gj, pitch) : 0);
-            T *dst = sB + (ty + 1) * BW + tx + 1;
+    const auto copy_planes = [&](const int c0, const int c1, const int c2, const int c3, const int n) {
 #pragma unroll
-            for (int c = 0; c < 4; c++) cp_async_elem(dst + c * NB, src + (ok ? c * plane : 0), ok);
-        };
-        copy_slopes(tid % TX, tid / TX);
-        for (int h = tid; h < NB - NT; h += NT) {
-            if (h < BW) copy_slopes(h - 1, -1);                  // row -1
-            else if (h < 2 * BW) copy_slopes(h - BW - 1, TY);    // row TY
-            else {                                               // columns -1 and TX
-                const int r = h - 2 * BW;
-                copy_slopes((r & 1) ? TX : -1, r >> 1);
+        for (int e = 0; e < NE; e++) {
+            if (eo[e] < 0) continue;
+            const int cs[4] = {c0, c1, c2, c3};
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (q < n) cp_async_elem(sU + cs[q] * SP + eo[e], a.Uin + (eok[e] ? cs[q] * plane + eg[e] : 0), eok[e]);
+        }
+    };
+    copy_planes(0, 3, 0, 0, 2);
+    // Wet/dry masking: where no cell of the staged tile and halo holds mass
+    // (U1 = U4 = 0; in the FP32 form also the tile's mass remainders, and in
+    // a combining stage the tile's masses at U^n), every face flux, source
+    // and speed of the tile is exactly 0 and the stage leaves the tile at 0
+    // (zero masses, zero momenta by the dry rule; the recording form also
+    // zero records).  Such a CTA neither loads the momenta and the geometry
+    // nor does the arithmetic; the barrier tells every thread.  NaN counts as
+    // mass.  Each thread tests its own cell's remainders and U^n (loaded while
+    // the copies are in flight), then the cells it copied itself.
+    bool has_mass = false;
+    {
+        const int ci = x0 + tid % TX, cj = y0 + tid / TX;
+        if (ci < nx && cj < ny) {
+            const long long g = cell_index(ci, cj, pitch);
+            if constexpr (sizeof(T) == 4) has_mass |= a.Rin[g] != 0.0f || a.Rin[plane + g] != 0.0f;
+            if (a.stage == 2 && !a.debug_stage) {
+                has_mass |= a.Un[g] != T(0) || a.Un[3 * plane + g] != T(0);
+                if constexpr (sizeof(T) == 4) has_mass |= a.Rn[g] != 0.0f || a.Rn[plane + g] != 0.0f;
             }
         }
     }
     cp_async_wait_all();
-    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < NE; e++)
+        if (eo[e] >= 0) has_mass |= sU[eo[e]] != T(0) || sU[3 * SP + eo[e]] != T(0);
+    const bool wet = __syncthreads_or(has_mass) != 0;
+    if (wet) {  // CTA-uniform: the momenta, and the slope tile
+        copy_planes(1, 2, 4, 5, 4);
+        if constexpr (SL) {
+            // slope tile: cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
+            const auto copy_slopes = [&](int tx, int ty) {  // tile coordinates, -1 .. TX / TY
+                const int gi = x0 + tx, gj = y0 + ty;
+                const bool ok = gi <= nx && gj <= ny;
+                const T *src = geo + (ok ? GS_SX * plane + cell_index(gi, gj, pitch) : 0);
+                T *dst = sB + (ty + 1) * BW + tx + 1;
+#pragma unroll
+                for (int c = 0; c < 4; c++) cp_async_elem(dst + c * NB, src + (ok ? c * plane : 0), ok);
+            };
+            copy_slopes(tid % TX, tid / TX);
+            for (int h = tid; h < NB - NT; h += NT) {
+                if (h < BW) copy_slopes(h - 1, -1);                  // row -1
+                else if (h < 2 * BW) copy_slopes(h - BW - 1, TY);    // row TY
+                else {                                               // columns -1 and TX
+                    const int r = h - 2 * BW;
+                    copy_slopes((r & 1) ? TX : -1, r >> 1);
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
     const double dt = s_dt;
     const T dtT = s_dtT;
     const double bwf = s_bwf;
-    if constexpr (VIS) {
-        // fluid velocity of every cell of the slope tile (0 where the fluid is
-        // dry), with the same dry threshold as the cell update
-        for (int q = tid; q < NB; q += NT) {
-            const int ly = q / BW, lx = q - ly * BW;
-            const int gi = x0 - 1 + lx, gj = y0 - 1 + ly;
-            const int o = (ly + 1) * SW + lx + 1;
-            T jhdn;
-            if constexpr (GL) {
-                const float sx = SB(0, lx, ly), sy = SB(1, lx, ly);
-                const float s2 = fmaf(sx, sx, fmaf(sy, sy, 1.0f));
-                jhdn = s2 * frsqrt(s2) * k.h_dry;
-            } else {
-                jhdn = (gi <= nx + 1 && gj <= ny + 1) ? geo[GC_JHD * plane + cell_index(gi, gj, pitch)] : T(1);
-            }
-            const T u3 = sU[3 * SP + o];
-            const T rf = gtp(u3, jhdn) ? frcp(u3) : T(0);
-            sVf[q] = sU[4 * SP + o] * rf;
-            sVf[NB + q] = sU[5 * SP + o] * rf;
-        }
-    }
-
-    // ---- minmod slopes, once per cell and direction -----------------------
-    // sSx[c][ly][lx'] holds the x-slope of cell (x0-1+lx', y0+ly), sSy[c][ly'][lx]
-    // the y-slope of cell (x0+lx, y0-1+ly').  Each thread takes both slopes of
-    // its own cell, then a share of the halo ones (x: columns -1 and TX; y:
-    // rows -1 and TY), so that only the halo needs index arithmetic.
-    // (The WENO form reconstructs each face value in the face loop instead.)
-    if constexpr (!WENO) {
-        const int lx = tid % TX, ly = tid / TX;
-        const T *p = sU + (ly + 2) * SW + lx + 2;
-#pragma unroll
-        for (int c = 0; c < 6; c++) {
-            const T *q = p + c * SP;
-            sSx[c * NSX + ly * (TX + 2) + lx + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
-            sSy[c * NSY + (ly + 1) * TX + lx] = minmod(q[0] - q[-SW], q[SW] - q[0]);
-        }
-        constexpr int NHX = 2 * TY, NHY = 2 * TX, NH1 = NHX + NHY;
-        for (int e = tid; e < 6 * NH1; e += NT) {
-            const int c = e / NH1;
-            int r = e - c * NH1;
-            if (r < NHY) {  // y-slopes of rows -1 (r < TX) and TY
-                const int side = r / TX, col = r - side * TX, row = side ? TY : -1;
-                const T *q = sU + c * SP + (row + 2) * SW + col + 2;
-                sSy[c * NSY + (row + 1) * TX + col] = minmod(q[0] - q[-SW], q[SW] - q[0]);
-            } else {  // x-slopes of columns -1 and TX
-                r -= NHY;
-                const int row = r >> 1, col = (r & 1) ? TX : -1;
-                const T *q = sU + c * SP + (row + 2) * SW + col + 2;
-                sSx[c * NSX + row * (TX + 2) + col + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
-            }
-        }
-    }
-    __syncthreads();
-
-    // ---- faces: x-faces (i+1/2, j), i = x0-1 .. x0+TX-1, at sHx[c][ly][lx],
-    // lx = i - x0 + 1; y-faces (i, j+1/2), j = y0-1 .. y0+TY-1, at
-    // sHy[c][ly][lx], ly = j - y0 + 1.  Each thread takes the right and the
-    // upper face of its own cell; warp 0 the left faces of column 0, warp 1
-    // the lower faces of row 0 (every warp then runs at most three faces).
-    const auto x_face = [&](const int lx, const int ly) {
-        const int i = x0 + lx - 1, j = y0 + ly;
-        if (j >= ny || i >= nx) return;
-        const int f = ly * (TX + 1) + lx;
-        FaceGeo<T> G;
-        if constexpr (GL) {  // lower cell at (lx, ly + 1) of the slope tile
-            G = face_geo32(SB(2, lx, ly + 1), 0.5f * (SB(1, lx, ly + 1) + SB(1, lx + 1, ly + 1)), k);
-        } else {
-            const long long g = cell_index(i, j, pitch);
-            G = FaceGeo<T>{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
-                           geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
-                           geo[GX_HG * plane + g]};
-        }
-        const int ou = (ly + 2) * SW + lx + 1;  // left cell in sU
-        const int os = ly * (TX + 2) + lx;      // left cell in sSx
-        T um[6], up[6];
-#pragma unroll
-        for (int c = 0; c < 6; c++) {
-            if constexpr (WENO) {
-                const T *p = sU + c * SP + ou;
-                um[c] = weno3_face(p[-1], p[0], p[1]);
-                up[c] = weno3_face(p[2], p[1], p[0]);
-                if (c == 0 || c == 3) {  // masses stay >= 0 at the faces
-                    um[c] = fmax(um[c], T(0));
-                    up[c] = fmax(up[c], T(0));
+    if (wet) {  // CTA-uniform
+        if constexpr (VIS) {
+            // fluid velocity of every cell of the slope tile (0 where the fluid is
+            // dry), with the same dry threshold as the cell update
+            for (int q = tid; q < NB; q += NT) {
+                const int ly = q / BW, lx = q - ly * BW;
+                const int gi = x0 - 1 + lx, gj = y0 - 1 + ly;
+                const int o = (ly + 1) * SW + lx + 1;
+                T jhdn;
+                if constexpr (GL) {
+                    const float sx = SB(0, lx, ly), sy = SB(1, lx, ly);
+                    const float s2 = fmaf(sx, sx, fmaf(sy, sy, 1.0f));
+                    jhdn = s2 * frsqrt(s2) * k.h_dry;
+                } else {
+                    jhdn = (gi <= nx + 1 && gj <= ny + 1) ? geo[GC_JHD * plane + cell_index(gi, gj, pitch)] : T(1);
                 }
-            } else {
-                um[c] = fma(T(0.5), sSx[c * NSX + os], sU[c * SP + ou]);
-                up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
+                const T u3 = sU[3 * SP + o];
+                const T rf = gtp(u3, jhdn) ? frcp(u3) : T(0);
+                sVf[q] = sU[4 * SP + o] * rf;
+                sVf[NB + q] = sU[5 * SP + o] * rf;
             }
         }
-        T H[7];
-        if constexpr (CU) face_flux2_cu<T, 0>(um, up, G, H);
-        else face_flux2<T, 0>(um, up, G, H);
-        if constexpr (sizeof(T) == 4) {
-            // FP32: the mass change this face gives each neighbour, rounded once
-            H[0] *= dtT * k.hinv_dx;
-            H[3] *= dtT * k.hinv_dx;
-        }
-#pragma unroll
-        for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
-        if (!a.debug_stage && (i == -1 || i == nx - 1)) {
-            // Heun weight 1/2 x boundary volume flux of this stage
-            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dy) * (i == -1 ? 1.0 : -1.0) * bwf;
-            atomicAdd(&acc[0], w * (double)H[0]);
-            atomicAdd(&acc[1], w * (double)H[3]);
-        }
-    };
-    const auto y_face = [&](const int lx, const int ly) {
-        const int i = x0 + lx, j = y0 + ly - 1;
-        if (i >= nx || j >= ny) return;
-        const int f = ly * TX + lx;
-        FaceGeo<T> G;
-        if constexpr (GL) {  // lower cell at (lx + 1, ly) of the slope tile
-            G = face_geo32(SB(3, lx + 1, ly), 0.5f * (SB(0, lx + 1, ly) + SB(0, lx + 1, ly + 1)), k);
-        } else {
-            const long long g = cell_index(i, j, pitch);
-            G = FaceGeo<T>{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
-                           geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
-                           geo[GY_HG * plane + g]};
-        }
-        const int ou = (ly + 1) * SW + lx + 2;  // lower cell in sU
-        const int os = ly * TX + lx;            // lower cell in sSy
-        T um[6], up[6];
-#pragma unroll
-        for (int c = 0; c < 6; c++) {
-            if constexpr (WENO) {
-                const T *p = sU + c * SP + ou;
-                um[c] = weno3_face(p[-SW], p[0], p[SW]);
-                up[c] = weno3_face(p[2 * SW], p[SW], p[0]);
-                if (c == 0 || c == 3) {
-                    um[c] = fmax(um[c], T(0));
-                    up[c] = fmax(up[c], T(0));
+
+        // ---- minmod slopes, once per cell and direction -----------------------
+        // sSx[c][ly][lx'] holds the x-slope of cell (x0-1+lx', y0+ly), sSy[c][ly'][lx]
+        // the y-slope of cell (x0+lx, y0-1+ly').  Each thread takes both slopes of
+        // its own cell, then a share of the halo ones (x: columns -1 and TX; y:
+        // rows -1 and TY), so that only the halo needs index arithmetic.
+        // (The WENO form reconstructs each face value in the face loop instead.)
+        if constexpr (!WENO) {
+            const int lx = tid % TX, ly = tid / TX;
+            const T *p = sU + (ly + 2) * SW + lx + 2;
+    #pragma unroll
+            for (int c = 0; c < 6; c++) {
+                const T *q = p + c * SP;
+                sSx[c * NSX + ly * (TX + 2) + lx + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
+                sSy[c * NSY + (ly + 1) * TX + lx] = minmod(q[0] - q[-SW], q[SW] - q[0]);
+            }
+            constexpr int NHX = 2 * TY, NHY = 2 * TX, NH1 = NHX + NHY;
+            for (int e = tid; e < 6 * NH1; e += NT) {
+                const int c = e / NH1;
+                int r = e - c * NH1;
+                if (r < NHY) {  // y-slopes of rows -1 (r < TX) and TY
+                    const int side = r / TX, col = r - side * TX, row = side ? TY : -1;
+                    const T *q = sU + c * SP + (row + 2) * SW + col + 2;
+                    sSy[c * NSY + (row + 1) * TX + col] = minmod(q[0] - q[-SW], q[SW] - q[0]);
+                } else {  // x-slopes of columns -1 and TX
+                    r -= NHY;
+                    const int row = r >> 1, col = (r & 1) ? TX : -1;
+                    const T *q = sU + c * SP + (row + 2) * SW + col + 2;
+                    sSx[c * NSX + row * (TX + 2) + col + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
                 }
-            } else {
-                um[c] = fma(T(0.5), sSy[c * NSY + os], sU[c * SP + ou]);
-                up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
             }
         }
-        T H[7];
-        if constexpr (CU) face_flux2_cu<T, 1>(um, up, G, H);
-        else face_flux2<T, 1>(um, up, G, H);
-        if constexpr (sizeof(T) == 4) {
-            H[0] *= dtT * k.hinv_dy;
-            H[3] *= dtT * k.hinv_dy;
-        }
-#pragma unroll
-        for (int c = 0; c < 7; c++) sHy[c * NYF + f] = H[c];
-        if (!a.debug_stage && (j == -1 || j == ny - 1)) {
-            const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dx) * (j == -1 ? 1.0 : -1.0) * bwf;
-            atomicAdd(&acc[0], w * (double)H[0]);
-            atomicAdd(&acc[1], w * (double)H[3]);
-        }
-    };
-    static_assert(NT >= 32 + TX && TY <= 32, "face assignment needs warps 0 and 1");
-    x_face(tid % TX + 1, tid / TX);
-    y_face(tid % TX, tid / TX + 1);
-    if (tid < TY) x_face(0, tid);
-    else if (tid >= 32 && tid < 32 + TX) y_face(tid - 32, 0);
-    __syncthreads();
+        __syncthreads();
+
+        // ---- faces: x-faces (i+1/2, j), i = x0-1 .. x0+TX-1, at sHx[c][ly][lx],
+        // lx = i - x0 + 1; y-faces (i, j+1/2), j = y0-1 .. y0+TY-1, at
+        // sHy[c][ly][lx], ly = j - y0 + 1.  Each thread takes the right and the
+        // upper face of its own cell; warp 0 the left faces of column 0, warp 1
+        // the lower faces of row 0 (every warp then runs at most three faces).
+        const auto x_face = [&](const int lx, const int ly) {
+            const int i = x0 + lx - 1, j = y0 + ly;
+            if (j >= ny || i >= nx) return;
+            const int f = ly * (TX + 1) + lx;
+            FaceGeo<T> G;
+            if constexpr (GL) {  // lower cell at (lx, ly + 1) of the slope tile
+                G = face_geo32(SB(2, lx, ly + 1), 0.5f * (SB(1, lx, ly + 1) + SB(1, lx + 1, ly + 1)), k);
+            } else {
+                const long long g = cell_index(i, j, pitch);
+                G = FaceGeo<T>{geo[GX_JHD * plane + g], geo[GX_SN * plane + g], geo[GX_ST * plane + g],
+                               geo[GX_FN * plane + g],  geo[GX_FT * plane + g], geo[GX_FN2 * plane + g],
+                               geo[GX_HG * plane + g]};
+            }
+            const int ou = (ly + 2) * SW + lx + 1;  // left cell in sU
+            const int os = ly * (TX + 2) + lx;      // left cell in sSx
+            T um[6], up[6];
+    #pragma unroll
+            for (int c = 0; c < 6; c++) {
+                if constexpr (WENO) {
+                    const T *p = sU + c * SP + ou;
+                    um[c] = weno3_face(p[-1], p[0], p[1]);
+                    up[c] = weno3_face(p[2], p[1], p[0]);
+                    if (c == 0 || c == 3) {  // masses stay >= 0 at the faces
+                        um[c] = fmax(um[c], T(0));
+                        up[c] = fmax(up[c], T(0));
+                    }
+                } else {
+                    um[c] = fma(T(0.5), sSx[c * NSX + os], sU[c * SP + ou]);
+                    up[c] = fma(T(-0.5), sSx[c * NSX + os + 1], sU[c * SP + ou + 1]);
+                }
+            }
+            T H[7];
+            if constexpr (CU) face_flux2_cu<T, 0>(um, up, G, H);
+            else face_flux2<T, 0>(um, up, G, H);
+            if constexpr (sizeof(T) == 4) {
+                // FP32: the mass change this face gives each neighbour, rounded once
+                H[0] *= dtT * k.hinv_dx;
+                H[3] *= dtT * k.hinv_dx;
+            }
+    #pragma unroll
+            for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
+            if (!a.debug_stage && (i == -1 || i == nx - 1)) {
+                // Heun weight 1/2 x boundary volume flux of this stage
+                const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dy) * (i == -1 ? 1.0 : -1.0) * bwf;
+                atomicAdd(&acc[0], w * (double)H[0]);
+                atomicAdd(&acc[1], w * (double)H[3]);
+            }
+        };
+        const auto y_face = [&](const int lx, const int ly) {
+            const int i = x0 + lx, j = y0 + ly - 1;
+            if (i >= nx || j >= ny) return;
+            const int f = ly * TX + lx;
+            FaceGeo<T> G;
+            if constexpr (GL) {  // lower cell at (lx + 1, ly) of the slope tile
+                G = face_geo32(SB(3, lx + 1, ly), 0.5f * (SB(0, lx + 1, ly) + SB(0, lx + 1, ly + 1)), k);
+            } else {
+                const long long g = cell_index(i, j, pitch);
+                G = FaceGeo<T>{geo[GY_JHD * plane + g], geo[GY_SN * plane + g], geo[GY_ST * plane + g],
+                               geo[GY_FN * plane + g],  geo[GY_FT * plane + g], geo[GY_FN2 * plane + g],
+                               geo[GY_HG * plane + g]};
+            }
+            const int ou = (ly + 1) * SW + lx + 2;  // lower cell in sU
+            const int os = ly * TX + lx;            // lower cell in sSy
+            T um[6], up[6];
+    #pragma unroll
+            for (int c = 0; c < 6; c++) {
+                if constexpr (WENO) {
+                    const T *p = sU + c * SP + ou;
+                    um[c] = weno3_face(p[-SW], p[0], p[SW]);
+                    up[c] = weno3_face(p[2 * SW], p[SW], p[0]);
+                    if (c == 0 || c == 3) {
+                        um[c] = fmax(um[c], T(0));
+                        up[c] = fmax(up[c], T(0));
+                    }
+                } else {
+                    um[c] = fma(T(0.5), sSy[c * NSY + os], sU[c * SP + ou]);
+                    up[c] = fma(T(-0.5), sSy[c * NSY + os + TX], sU[c * SP + ou + SW]);
+                }
+            }
+            T H[7];
+            if constexpr (CU) face_flux2_cu<T, 1>(um, up, G, H);
+            else face_flux2<T, 1>(um, up, G, H);
+            if constexpr (sizeof(T) == 4) {
+                H[0] *= dtT * k.hinv_dy;
+                H[3] *= dtT * k.hinv_dy;
+            }
+    #pragma unroll
+            for (int c = 0; c < 7; c++) sHy[c * NYF + f] = H[c];
+            if (!a.debug_stage && (j == -1 || j == ny - 1)) {
+                const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dx) * (j == -1 ? 1.0 : -1.0) * bwf;
+                atomicAdd(&acc[0], w * (double)H[0]);
+                atomicAdd(&acc[1], w * (double)H[3]);
+            }
+        };
+        static_assert(NT >= 32 + TX && TY <= 32, "face assignment needs warps 0 and 1");
+        x_face(tid % TX + 1, tid / TX);
+        y_face(tid % TX, tid / TX + 1);
+        if (tid < TY) x_face(0, tid);
+        else if (tid >= 32 && tid < 32 + TX) y_face(tid - 32, 0);
+        __syncthreads();
+    }
 
     // ---- cell update ------------------------------------------------------
     const int lx = tid % TX, ly = tid / TX;
     const int i = x0 + lx, j = y0 + ly;
     T speed = T(0);
     bool bad = false;
-    if (i < nx && j < ny) {
+    if (!wet && i < nx && j < ny) {
+        const long long g = cell_index(i, j, pitch);
+        const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        store6(a.Uout, plane, g, z);
+        if constexpr (REC) store6(a.rec, plane, g, z);
+        if constexpr (sizeof(T) == 4) {
+            a.Rout[g] = 0.0f;
+            a.Rout[plane + g] = 0.0f;
+        }
+        if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, z, s_tg);
+    } else if (i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
         const int os = (ly + 2) * SW + lx + 2;
         // the cell's geometry: FP32 rebuilt from the slope tile, FP64 read

@@ -57,6 +57,60 @@ def test_stage_adjoint_dot_product(nx, ny, bc, inflow):
     assert abs(fd - ad) <= 1e-7 * abs(fd), (fd, ad)
 
 
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
+def test_stage_adjoint_dot_product_sparse(bc):
+    """Wet blobs on tile edges in a dry domain: the dry tiles skip their face
+    terms (wet/dry masking) and their neighbours read the mass-only adjoints
+    of the dry cells.  Dot-product test with lam everywhere and v on the wet
+    cells (the stage is differentiable there), central differences."""
+    nx, ny = 97, 41
+    dem = W.spectral_dem(nx, ny, 5.0, 2.2, 30.0, seed=4, band_m=40.0)
+    g = moses.Sim(dem, 5.0, 5.0, W.default_params(bc=bc, c_d=0.05))
+    rng = np.random.default_rng(17)
+    h = np.zeros((ny, nx))
+    for j0, i0 in ((6, 29), (15, 62), (30, 0), (0, 90), (23, 45)):
+        h[j0:j0 + 3, i0:i0 + 4] = 0.8 + rng.random((min(3, ny - j0), min(4, nx - i0)))
+    st = _wet_state(nx, ny, 5)
+    g.set_release(h, st["phi_s"], st["vx_s"], st["vy_s"], st["vx_f"], st["vy_f"])
+    U = g.get_conserved()
+    lam = rng.standard_normal(U.shape)
+    v = rng.standard_normal(U.shape) * np.abs(U).reshape(6, -1).max(axis=1)[:, None, None] * (h > 0)[None]
+    t, dt, eps = 0.0, 0.005, 1e-6
+    li, _ = g.stage_adjoint(t, dt, lam)
+    g.set_conserved(U + eps * v)
+    Sp = g.stage(t, dt)
+    g.set_conserved(U - eps * v)
+    Sm = g.stage(t, dt)
+    fd = (lam * (Sp - Sm)).sum() / (2 * eps)
+    ad = (li * v).sum()
+    assert abs(fd - ad) <= 1e-7 * abs(fd), (fd, ad)
+    # on cells at least 3 away from any mass the stage is the identity on the
+    # masses and zeroes the momenta: so is its adjoint there
+    far = np.ones((ny, nx), bool)
+    wet = h > 0
+    for dj in range(-3, 4):
+        for di in range(-3, 4):
+            far &= ~np.roll(np.roll(wet, dj, 0), di, 1) | _rolled_out(ny, nx, dj, di)
+    assert far.sum() > 0.5 * nx * ny
+    assert np.array_equal(li[0][far], lam[0][far]) and np.array_equal(li[3][far], lam[3][far])
+    for c in (1, 2, 4, 5):
+        assert not li[c][far].any()
+
+
+def _rolled_out(ny, nx, dj, di):
+    """Cells whose np.roll source wrapped around the grid edge (not neighbours)."""
+    m = np.zeros((ny, nx), bool)
+    if dj > 0:
+        m[:dj, :] = True
+    elif dj < 0:
+        m[dj:, :] = True
+    if di > 0:
+        m[:, :di] = True
+    elif di < 0:
+        m[:, di:] = True
+    return m
+
+
 def test_stage_adjoint_parameter_partials():
     """lam . dS/d tan(delta_b) and lam . dS/d c_D against central differences."""
     nx, ny = 40, 30
