@@ -9,9 +9,15 @@ Hsiaolin event of Sect. 4.1; the real DEM is not available).
 
 A step is one full time step: CFL time step from the exact max-reduction, two
 stages of the central scheme with all sources, Heun average, boundary fill.
-The headline is the FP64 form; the FP32 form (FP64 budgets and friction test)
-is measured in the same run.  The state (0.8 GB in FP64) is larger than L2, so
-no flush is needed between steps.
+Each stage is two launches: the wet/dry classification, which writes the
+stage result of every tile without mass in reach (the zero state), and the
+stage kernel on the listed tiles.  The release covers a small part of the
+terrain, so most tiles are dry: the step streams the state through HBM and
+the line reports the HBM roofline, the wet-tile fraction, and (`dense`) the
+same kernels on an all-wet state, where the stage is bound by its FP64
+arithmetic.  The headline is the FP64 form; the FP32 form (FP64 budgets and
+friction test) is measured in the same run.  The state (0.8 GB in FP64) is
+larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -49,22 +55,22 @@ DX = 10.0
 FLOPS_PER_CELL_STAGE = 488
 WORDS_PER_CELL_STEP = 13
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one stage
-# launch per cell, from an ncu capture of the 2048 x 2048 case with the tile
-# pinned; valid only for the stage kernel source it was taken on (sha256 of
-# csrc/stage.cuh, first 12).  Traffic per cell does not depend on the grid
-# size, so a launch at side n moves n^2 times this.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one stage of
+# a step -- the wet/dry classification launch plus the listed-tile stage
+# launch -- per cell of the 4096^2 workload, the mean of the two stages of a
+# step, from an ncu capture of bench.py itself at full size (one-pass
+# metrics); valid only for the stage kernel source it was taken on (sha256 of
+# csrc/stage.cuh, first 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
-    # ncu, 2048^2 spectral-DEM release, one launch each (profiles/stage_kernel_traffic_2048_release.md)
-    ("f64", "32x8", "1e6157da0d6b"): 311.66,
-    ("f64", "32x16", "1e6157da0d6b"): 311.98,
-    ("f32", "32x8", "1e6157da0d6b"): 72.32,
+    # profiles/stage_kernel_launch_list_4096_release.md
+    ("f64", "46f9221f5660"): 68.83,
+    ("f32", "46f9221f5660"): 53.31,
 }
 
 
-def _traffic(form, tile, h, side):
-    b = TRAFFIC.get((form, tile, h))
-    return None if b is None else b * side * side
+def _traffic(form, h, side):
+    b = TRAFFIC.get((form, h))
+    return None if b is None or side != N_SIDE else b * side * side
 
 
 def peaks():
@@ -471,15 +477,17 @@ def main():
     # (`dense`) gives the arithmetic-bound rate of the same kernel.
     gbs64 = WORDS_PER_CELL_STEP * 8 * cells / (2 * f64["launch_ms"] / 1e3) / 1e9
     roof64 = {"bound": "hbm", "achieved": gbs64, "peak": pk["hbm_gbs"], "unit": "GB/s",
-              "frac": gbs64 / pk["hbm_gbs"], "traffic": _traffic("f64", t64, h, side),
-              "kernel": f"moses::stage_kernel<double,{t64.replace('x', ',')}>", "peak_source": pk_src,
-              "wet_tiles": f64["wet_tiles"]}
+              "frac": gbs64 / pk["hbm_gbs"], "traffic": _traffic("f64", h, side),
+              "kernel": f"one stage: moses::classify_kernel<double,{t64.split('x')[1]}> + "
+                        f"moses::stage_kernel_list<double,{t64.replace('x', ',')}>",
+              "peak_source": pk_src, "wet_tiles": f64["wet_tiles"]}
     f32 = results["f32"]
     bytes_step32 = WORDS_PER_CELL_STEP * 4 * cells
     gbs32 = bytes_step32 / (2 * f32["launch_ms"] / 1e3) / 1e9
     roof32 = {"bound": "hbm", "achieved": gbs32, "peak": pk["hbm_gbs"], "unit": "GB/s",
-              "frac": gbs32 / pk["hbm_gbs"], "traffic": _traffic("f32", t32, h, side),
-              "kernel": f"moses::stage_kernel<float,{t32.replace('x', ',')}>", "peak_source": pk_src}
+              "frac": gbs32 / pk["hbm_gbs"], "traffic": _traffic("f32", h, side),
+              "kernel": f"one stage: moses::classify_kernel<float,{t32.split('x')[1]}> + "
+                        f"moses::stage_kernel_list<float,{t32.replace('x', ',')}>", "peak_source": pk_src}
 
     # end to end through the C-ABI with pinned host buffers: per step, upload
     # the state, one step, download the state
@@ -524,9 +532,9 @@ def main():
         "ms_per_step": f64["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded spectral DEM and release; see workloads.py)",
         "config": config_dict(cfg, args), "roofline": roof64, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": 2 * K, "clocks": sampler.summary(),
+        "gpu_launches": 4 * K, "clocks": sampler.summary(),
         "f32": {"value": world * cells * K / (f32["ms"] / 1e3), "ms_per_step": f32["ms"] / K, "dtype": "f32",
-                "roofline": roof32, "gpu_launches": 2 * K},
+                "roofline": roof32, "gpu_launches": 4 * K},
         "ensemble": ens,
         "adjoint": adj,
         "variants": variants,

@@ -138,7 +138,9 @@ int moses_set_inflow(moses_sim *s, int side, int i0, int i1, int npts, const dou
                      const double *Q, const double *phi_s);
 
 /* Advance nsteps CFL-limited steps (Sect. 2.2; Stage 2 of Sect. 3.1.2).
- * t_out (may be NULL) receives the time after the last step.  Synchronises
+ * Tiles with no mass within the stencil's reach are not computed: their
+ * stage result, the zero state, is written directly (wet/dry masking; the
+ * result is the same).  t_out (may be NULL) receives the time after the last step.  Synchronises
  * the stream once at the end.  Errors: ESTATE, ENONFINITE (a kernel saw a
  * non-finite value; the state is left as computed and every later step
  * reports it again until a new state is set), ECUDA. */
@@ -160,9 +162,10 @@ int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms);
 #define MOSES_NTILES 3
 int moses_set_tile(moses_sim *s, int tile);
 
-/* Autotuner: times `reps` (>= 1; 0 = 5) launches of one stage of the current
- * state with each tile shape (CUDA events on the simulation's stream, after
- * one warm-up launch each; the state is not changed), selects the fastest and
+/* Autotuner: times `reps` (>= 1; 0 = 5) first stages of a step from the
+ * current state, launched as moses_step launches them, with each tile shape
+ * (CUDA events on the simulation's stream, after one warm-up launch each; the
+ * state, time and budgets are not changed), selects the fastest and
  * returns it in *tile_out (may be NULL).  ms_out (may be NULL) receives the
  * mean time per launch of each tile [ms], indexed by MOSES_TILE_*.  The choice
  * is cached per process by (device, SM count, precision, nx, ny): a later call

@@ -23,6 +23,8 @@ struct moses_sim {
     void *Us = nullptr;    // Heun intermediate, 6 planes
     void *geo = nullptr;   // geo_planes(s) planes
     void *Us2 = nullptr;   // second intermediate of the three-stage Runge-Kutta (rk = 3 only)
+    int *wl = nullptr;              // wet-tile list of the stepping launches (one entry per 32 x 4 tile)
+    unsigned int *wl_n = nullptr;   // its two counters
     Ctl *ctl = nullptr;    // device control block
     InflowSeg *inflow_d = nullptr;
     InflowSeg inflow_h[MAX_INFLOW];

@@ -437,6 +437,8 @@ static void free_sim(moses_sim *s)
     cudaFree(s->U);
     cudaFree(s->Us);
     cudaFree(s->Us2);
+    cudaFree(s->wl);
+    cudaFree(s->wl_n);
     cudaFree(s->geo);
     cudaFree(s->ctl);
     cudaFree(s->inflow_d);
@@ -528,6 +530,8 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
     if ((e = cudaMalloc(&s->U, st)) != cudaSuccess || (e = cudaMalloc(&s->Us, st)) != cudaSuccess ||
         (e = cudaMalloc(&s->geo, (size_t)geo_planes(s) * s->plane * s->esz)) != cudaSuccess ||
         (s->ph.rk == 3 && (e = cudaMalloc(&s->Us2, st)) != cudaSuccess) ||
+        (e = cudaMalloc(&s->wl, sizeof(int) * (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
+        (e = cudaMalloc(&s->wl_n, 2 * sizeof(unsigned int))) != cudaSuccess ||
         (e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = cudaMalloc(&s->inflow_d, sizeof(InflowSeg) * MAX_INFLOW)) != cudaSuccess ||
         (e = cudaMalloc(&s->red, 8 * sizeof(double))) != cudaSuccess) {
@@ -537,6 +541,7 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
     if ((e = cudaMemsetAsync(s->U, 0, st, s->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(s->Us, 0, st, s->stream)) != cudaSuccess ||
         (s->Us2 && (e = cudaMemsetAsync(s->Us2, 0, st, s->stream)) != cudaSuccess) ||
+        (e = cudaMemsetAsync(s->wl_n, 0, 2 * sizeof(unsigned int), s->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(s->geo, 0, (size_t)geo_planes(s) * s->plane * s->esz, s->stream)) != cudaSuccess) {
         s->err = std::string("memset: ") + cudaGetErrorString(e);
         return bail(MOSES_ECUDA);
@@ -696,6 +701,8 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
             a[q].Rn = rem<T>(s, s->U);
         }
         a[q].want_amax = q == ns - 1;
+        a[q].wl = s->wl;
+        a[q].wl_n = s->wl_n;
         if (rk3) {
             a[q].rk3 = q + 1;
             a[q].rk3_bw = q == 2 ? 2.0 / 3.0 : 1.0 / 6.0;
@@ -779,9 +786,11 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::array<int, 5>, int> g_tune_cache;  // (device, SMs, precision, nx, ny) -> tile
 
-// one stage of the current state into the scratch buffer (no ghosts, no budgets)
+// the first stage of a step as moses_step launches it (wet-tile list and
+// all), from the current state into the scratch buffer; it also touches the
+// control block (time step, budgets), which the caller restores
 template <typename T>
-int probe_stage(moses_sim *s, int tile, double dt)
+int probe_stage(moses_sim *s, int tile)
 {
     StageArgs<T> a = base_args<T>(s);
     a.Uin = (const T *)s->U;
@@ -789,8 +798,8 @@ int probe_stage(moses_sim *s, int tile, double dt)
     a.Rin = rem<T>(s, s->U);
     a.Rout = rem<T>(s, s->Us);
     a.stage = 1;
-    a.debug_stage = 1;
-    a.dbg_dt = dt;
+    a.wl = s->wl;
+    a.wl_n = s->wl_n;
     return launch_stage<T>(a, tile, s->stream);
 }
 }  // namespace
@@ -817,7 +826,6 @@ int moses_autotune(moses_sim *s, int reps, int *tile_out, double *ms_out)
     Ctl h;
     int rc = read_ctl(s, &h);
     if (rc) return rc;
-    const double dt = h.dt > 0.0 ? h.dt : s->ph.dt_max;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -826,7 +834,7 @@ int moses_autotune(moses_sim *s, int reps, int *tile_out, double *ms_out)
     for (int t = 0; t < MOSES_NTILES && rc == 0; t++) {
         for (int r = 0; r <= reps && rc == 0; r++) {
             if (r == 1) cudaEventRecord(e0, s->stream);
-            rc = s->prec == MOSES_FP64 ? probe_stage<double>(s, t, dt) : probe_stage<float>(s, t, dt);
+            rc = s->prec == MOSES_FP64 ? probe_stage<double>(s, t) : probe_stage<float>(s, t);
         }
         cudaEventRecord(e1, s->stream);
         float f = 0.0f;
@@ -839,6 +847,9 @@ int moses_autotune(moses_sim *s, int reps, int *tile_out, double *ms_out)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return fail(s, MOSES_ECUDA, "autotune launch failed");
+    // the probes advanced nothing: put the control block back as it was
+    CK(cudaMemcpyAsync(s->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
     s->tile = best;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -183,6 +183,12 @@ struct alignas(8) StageArgs {
     // trial masses and solid momenta before friction and the clamp, and the
     // gradient of P (6 planes: U1*, U2*, U3*, U4*, dP/dxi, dP/deta)
     T *rec;
+    // wet-tile list of the stepping launches (plain form): classify_kernel
+    // writes the dry tiles' zero state and lists the tiles that hold mass,
+    // which the stage kernel then runs; wl_n[0] entries, wl_n[1] CTAs done.
+    // Null: every tile tests itself.
+    int *wl;
+    unsigned int *wl_n;
 };
 
 __host__ __device__ inline long long cell_index(int i, int j, int pitch)

@@ -582,9 +582,24 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
     coulomb(q1, q2, bX, bY, Fr);
 }
 
+// End of a step, by the last CTA of its last stage: publish a_max (the exact
+// maximum of the step's cell speeds, reduced on their IEEE bits) and advance t.
+template <typename T>
+__device__ __forceinline__ void end_step(const StageArgs<T> &a)
+{
+    Ctl *ctl = a.ctl;
+    const unsigned long long m = atomicExch(&ctl->amax_acc, 0ull);
+    if (a.want_amax) ctl->amax = m;
+    if (ctl->dt > 0.0) {
+        ctl->t = ctl->t + ctl->dt;
+        ctl->steps += 1;
+    }
+}
+
 // ---- the stage kernel -------------------------------------------------------------
 // One stage on the tile (bx, by) of the simulation described by `a`; nb is the
-// number of CTAs working on that simulation in this launch (for the ticket).
+// number of CTAs working on that simulation in this launch (for the ticket;
+// 0: the caller takes it).
 template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
@@ -687,35 +702,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                 if (q < n) cp_async_elem(sU + cs[q] * SP + eo[e], a.Uin + (eok[e] ? cs[q] * plane + eg[e] : 0), eok[e]);
         }
     };
-    copy_planes(0, 3, 0, 0, 2);
-    // Wet/dry masking: where no cell of the staged tile and halo holds mass
-    // (U1 = U4 = 0; in the FP32 form also the tile's mass remainders, and in
-    // a combining stage the tile's masses at U^n), every face flux, source
-    // and speed of the tile is exactly 0 and the stage leaves the tile at 0
-    // (zero masses, zero momenta by the dry rule; the recording form also
-    // zero records).  Such a CTA neither loads the momenta and the geometry
-    // nor does the arithmetic; the barrier tells every thread.  NaN counts as
-    // mass.  Each thread tests its own cell's remainders and U^n (loaded while
-    // the copies are in flight), then the cells it copied itself.
-    bool has_mass = false;
-    {
-        const int ci = x0 + tid % TX, cj = y0 + tid / TX;
-        if (ci < nx && cj < ny) {
-            const long long g = cell_index(ci, cj, pitch);
-            if constexpr (sizeof(T) == 4) has_mass |= a.Rin[g] != 0.0f || a.Rin[plane + g] != 0.0f;
-            if (a.stage == 2 && !a.debug_stage) {
-                has_mass |= a.Un[g] != T(0) || a.Un[3 * plane + g] != T(0);
-                if constexpr (sizeof(T) == 4) has_mass |= a.Rn[g] != 0.0f || a.Rn[plane + g] != 0.0f;
-            }
-        }
-    }
-    cp_async_wait_all();
-#pragma unroll
-    for (int e = 0; e < NE; e++)
-        if (eo[e] >= 0) has_mass |= sU[eo[e]] != T(0) || sU[3 * SP + eo[e]] != T(0);
-    const bool wet = __syncthreads_or(has_mass) != 0;
-    if (wet) {  // CTA-uniform: the momenta, and the slope tile
-        copy_planes(1, 2, 4, 5, 4);
+    // FP32 (and viscous) form: bed slopes of the tile + 1-cell halo
+    const auto copy_slope_tile = [&]() {
         if constexpr (SL) {
             // slope tile: cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
             const auto copy_slopes = [&](int tx, int ty) {  // tile coordinates, -1 .. TX / TY
@@ -736,6 +724,45 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                 }
             }
         }
+    };
+    // A tile from the wet-tile list holds mass: it copies everything at once.
+    const bool listed = a.wl != nullptr;
+    copy_planes(0, 3, 0, 0, 2);
+    if (listed) {
+        copy_planes(1, 2, 4, 5, 4);
+        copy_slope_tile();
+    }
+    // Wet/dry masking: where no cell of the staged tile and halo holds mass
+    // (U1 = U4 = 0; in the FP32 form also the tile's mass remainders, and in
+    // a combining stage the tile's masses at U^n), every face flux, source
+    // and speed of the tile is exactly 0 and the stage leaves the tile at 0
+    // (zero masses, zero momenta by the dry rule; the recording form also
+    // zero records).  Such a CTA neither loads the momenta and the geometry
+    // nor does the arithmetic; the barrier tells every thread.  NaN counts as
+    // mass.  Each thread tests its own cell's remainders and U^n (loaded while
+    // the copies are in flight), then the cells it copied itself.
+    bool has_mass = listed;
+    if (!listed) {
+        const int ci = x0 + tid % TX, cj = y0 + tid / TX;
+        if (ci < nx && cj < ny) {
+            const long long g = cell_index(ci, cj, pitch);
+            if constexpr (sizeof(T) == 4) has_mass |= (a.Rin[g] != 0.0f) | (a.Rin[plane + g] != 0.0f);
+            if (a.stage == 2 && !a.debug_stage) {
+                has_mass |= (a.Un[g] != T(0)) | (a.Un[3 * plane + g] != T(0));
+                if constexpr (sizeof(T) == 4) has_mass |= (a.Rn[g] != 0.0f) | (a.Rn[plane + g] != 0.0f);
+            }
+        }
+    }
+    cp_async_wait_all();
+    if (!listed) {
+#pragma unroll
+        for (int e = 0; e < NE; e++)
+            if (eo[e] >= 0) has_mass |= (sU[eo[e]] != T(0)) | (sU[3 * SP + eo[e]] != T(0));
+    }
+    const bool wet = __syncthreads_or(has_mass) != 0;
+    if (wet && !listed) {  // CTA-uniform: the momenta, and the slope tile
+        copy_planes(1, 2, 4, 5, 4);
+        copy_slope_tile();
         cp_async_wait_all();
         __syncthreads();
     }
@@ -1198,21 +1225,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                 for (int w = 0; w < NT / 32; w++) m = maxnn(m, red[w]);
                 atomicMax(&ctl->amax_acc, (unsigned long long)__double_as_longlong((double)m));
             }
-            __threadfence();
-            last_block = (atomicAdd(&ctl->ticket, 1u) == nb - 1);
+            if (nb) {
+                __threadfence();
+                last_block = (atomicAdd(&ctl->ticket, 1u) == nb - 1);
+            }
         }
     }
-    if (!finalize) return;
+    if (!finalize || nb == 0) return;  // nb == 0: the caller ends the step
     __syncthreads();
     if (last_block && tid == 0) {
         __threadfence();
-        const unsigned long long m = atomicExch(&ctl->amax_acc, 0ull);
-        if (a.want_amax) ctl->amax = m;
         ctl->ticket = 0;
-        if (ctl->dt > 0.0) {
-            ctl->t = ctl->t + ctl->dt;
-            ctl->steps += 1;
-        }
+        end_step(a);
     }
 }
 
@@ -1220,6 +1244,122 @@ template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool C
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
 {
     stage_tile<T, TX, TY, REC, VIS, CU, WENO>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+}
+
+// Wet/dry masking over a whole launch, for the stepping of the plain form.
+// A tile (32 x TY cells) holds work if a cell of it or of its 2-cell halo has
+// mass (U1 or U4 non-zero; NaN counts), or if a cell of it has a non-zero
+// FP32 mass remainder or, in a combining stage, mass at U^n.  A dry tile's
+// stage result is known -- zero state, zero remainders, the ghost cells it
+// owns filled from it -- and is written here; a tile with work is appended to
+// the list that stage_kernel_list runs.  One CTA (8 warps) covers a strip of
+// 32 x 32 cells: each warp tests whole rows of the strip and its halo (36
+// columns, coalesced) with a warp vote, so each mass is read about once; the
+// tiles of the strip then OR their rows.  The step's time step is taken here
+// as the stage kernel takes it (stage 1 records it).
+template <typename T, int TY>
+__global__ void __launch_bounds__(256) classify_kernel(const StageArgs<T> a)
+{
+    constexpr int S = 32, H = S + 4, NTL = S / TY;
+    static_assert(S % TY == 0, "strip of whole tiles");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int bx = blockIdx.x, x0 = bx * 32, y0 = blockIdx.y * S;
+    const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    const long long plane = a.plane;
+    Ctl *ctl = a.ctl;
+    __shared__ double s_tg;
+    __shared__ unsigned int s_row[H];  // row y0 - 2 + r of the strip and halo has work
+    __shared__ bool s_wet[NTL];
+    if (threadIdx.x == 0) {
+        const double t_now = ctl->t;
+        const double dt = a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
+        s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
+        if (a.stage == 1 && bx == 0 && blockIdx.y == 0) ctl->dt = dt;
+    }
+    // every load of the warp's rows first (all in flight together), then the votes
+    constexpr int RPW = (H + 7) / 8;  // rows per warp
+    bool m[RPW];
+#pragma unroll
+    for (int k = 0; k < RPW; k++) {
+        const int r = warp + 8 * k, gj = y0 + r - 2;  // gj >= -2
+        m[k] = false;
+        if (r >= H || gj >= ny + 2) continue;
+        const int gi = x0 + lane;
+        if (gi < nx + 2) {
+            const long long g = cell_index(gi, gj, pitch);
+            m[k] |= (a.Uin[g] != T(0)) | (a.Uin[3 * plane + g] != T(0));
+            if (r >= 2 && r < S + 2 && gj < ny && gi < nx) {  // a cell of the strip: its own extras
+                if constexpr (sizeof(T) == 4) m[k] |= (a.Rin[g] != 0.0f) | (a.Rin[plane + g] != 0.0f);
+                if (a.stage == 2) {
+                    m[k] |= (a.Un[g] != T(0)) | (a.Un[3 * plane + g] != T(0));
+                    if constexpr (sizeof(T) == 4) m[k] |= (a.Rn[g] != 0.0f) | (a.Rn[plane + g] != 0.0f);
+                }
+            }
+        }
+        if (lane < 4) {  // the halo columns x0-2, x0-1, x0+32, x0+33
+            const int ge = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;
+            if (ge < nx + 2) {
+                const long long g = cell_index(ge, gj, pitch);
+                m[k] |= (a.Uin[g] != T(0)) | (a.Uin[3 * plane + g] != T(0));
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RPW; k++) {
+        const unsigned int any = __any_sync(0xffffffffu, m[k]);
+        if (lane == 0 && warp + 8 * k < H) s_row[warp + 8 * k] = any;
+    }
+    __syncthreads();
+    if (threadIdx.x < NTL) {
+        const int t = threadIdx.x, ty0 = y0 + t * TY;
+        bool w = false;
+        if (ty0 < ny) {
+            for (int r = t * TY; r < t * TY + TY + 4; r++) w |= s_row[r] != 0u;
+            if (w) a.wl[atomicAdd(&a.wl_n[0], 1u)] = (ty0 / TY) * gridDim.x + bx;
+        }
+        s_wet[t] = w;
+    }
+    __syncthreads();
+    const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    for (int r = warp; r < S; r += 8) {
+        const int j = y0 + r, i = x0 + lane;
+        if (j >= ny || s_wet[r / TY] || i >= nx) continue;
+        const long long g = cell_index(i, j, pitch);
+        store6(a.Uout, plane, g, z);
+        if constexpr (sizeof(T) == 4) {
+            a.Rout[g] = 0.0f;
+            a.Rout[plane + g] = 0.0f;
+        }
+        write_ghosts(a.Uout, a.geo, a, i, j, z, s_tg);
+    }
+}
+
+// The stage on the listed tiles: a grid of resident CTAs takes the list's
+// entries in turn; the last CTA to finish empties the list and, after the
+// step's last stage, ends the step.
+// FP32: three 256-thread CTAs per SM (at most 85 registers); FP64: two
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY))
+    stage_kernel_list(const StageArgs<T> a, const int gx)
+{
+    __shared__ bool last;
+    const unsigned int n = a.wl_n[0];
+    for (unsigned int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int t = a.wl[w];
+        stage_tile<T, TX, TY>(a, t % gx, t / gx, 0u);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&a.wl_n[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        a.wl_n[0] = 0;
+        a.wl_n[1] = 0;
+        if (a.stage == 2 && a.rk3 != 2) end_step(a);
+    }
 }
 
 // Ensemble form: one launch runs the same stage of many simulations.  Each CTA

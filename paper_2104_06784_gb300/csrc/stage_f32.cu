@@ -24,15 +24,52 @@ int launch_tile(const StageArgs<T> &a, cudaStream_t st)
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
+// The stepping launches of the plain form: classify_kernel over every tile,
+// then stage_kernel_list on a grid of resident CTAs over the listed tiles.
+template <typename T, int TX, int TY>
+int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
+{
+    constexpr size_t smem = stage_smem_bytes<T, TX, TY>();
+    static int resident[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return -1;
+    if (!resident[dev]) {
+        int per_sm = 0, n_sm = 0;
+        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY>, TX * TY, smem) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
+            return -1;
+        resident[dev] = per_sm * n_sm;
+    }
+    static_assert(TX == 32, "classify_kernel works on 32-wide strips");
+    const int gx = (a.nx + TX - 1) / TX;
+    classify_kernel<T, TY><<<dim3(gx, (a.ny + 31) / 32), 256, 0, st>>>(a);
+    stage_kernel_list<T, TX, TY><<<resident[dev], TX * TY, smem, st>>>(a, gx);
+    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace
 
 // tile 0: 32 x 8 cells (256 threads); tile 1: 32 x 4; tile 2: 32 x 16
 template <>
-int launch_stage<float>(const StageArgs<float> &a, int tile, void *stream)
+int launch_stage<float>(const StageArgs<float> &a_in, int tile, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     // the model options (viscous term, central-upwind flux, WENO): one tile shape
-    const bool vis = a.ph.nu_f > 0.0, cu = a.ph.scheme == 1, weno = a.ph.recon == 1;
+    const bool vis = a_in.ph.nu_f > 0.0, cu = a_in.ph.scheme == 1, weno = a_in.ph.recon == 1;
+    if (a_in.wl && !vis && !cu && !weno && !a_in.debug_stage) {
+        switch (tile) {
+        case 1: return launch_tile_list<float, 32, 4>(a_in, st);
+        case 2: return launch_tile_list<float, 32, 16>(a_in, st);
+        default: return launch_tile_list<float, 32, 8>(a_in, st);
+        }
+    }
+    StageArgs<float> a = a_in;  // every tile tests itself
+    a.wl = nullptr;
+    a.wl_n = nullptr;
     if (weno) {
         if (cu)
             return vis ? launch_tile<float, 32, 8, false, true, true, true>(a, st)
