@@ -389,6 +389,8 @@ def main():
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (the workload is defined at 4096)")
     ap.add_argument("--only", choices=["f64", "f32", "adjoint"], default=None,
                     help="measure one precision form, or only the adjoint")
+    ap.add_argument("--wet-layer", type=float, default=0.0,
+                    help="add a mixture layer of this depth [m] on every cell (all tiles wet; for profiling)")
     ap.add_argument("--tile", choices=["auto", "32x8", "32x4", "32x16"], default="auto",
                     help="stage tile shape: autotuned (default) or pinned")
     ap.add_argument("--adj-steps", type=int, default=None, help="adjoint: steps (default: the workload's 5000)")
@@ -396,6 +398,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.wet_layer > 0 and args.only not in ("f64", "f32"):
+        ap.error("--wet-layer is for --only f64 / f32 profiling runs")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -403,6 +407,8 @@ def main():
 
     from paper_2104_06784_gb300 import workloads as W
     cfg = W.large_release_config(n=args.side, dx=DX, seed=0)
+    if args.wet_layer > 0:
+        cfg = dict(cfg, h=cfg["h"] + args.wet_layer)
 
     if args.impl == "reference":
         line = run_reference(args, cfg, rank)
