@@ -656,9 +656,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
         // budget weight of this stage relative to the two-step Euler's 1/2
         s_bwf = a.rk3 ? 2.0 * a.rk3_bw : 1.0;
+        // (thread 0 alone resets the accumulators it alone reads at the end,
+        // so a CTA can run the next tile without a barrier in between)
         acc_n = 0;
+        acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
     }
-    if (tid < 4) acc[tid] = 0.0;
 
     // ---- stage the tile + 2-cell halo of the six state planes -----------
     // (asynchronous copies: every element of the thread in flight at once).
@@ -1344,10 +1346,13 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
 {
     __shared__ bool last;
     const unsigned int n = a.wl_n[0];
+    // no barrier between tiles: after the last barrier of a tile only thread 0
+    // works (its atomics), and the next tile's shared data are written before
+    // that tile's first barrier only by thread 0 or by copies into buffers the
+    // previous tile no longer reads
     for (unsigned int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = a.wl[w];
         stage_tile<T, TX, TY>(a, t % gx, t / gx, 0u);
-        __syncthreads();
     }
     if (threadIdx.x == 0) {
         __threadfence();
