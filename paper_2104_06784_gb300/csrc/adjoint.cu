@@ -127,12 +127,12 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     const size_t lb = 6 * (size_t)plane * sizeof(T);
     const int nck = (nsteps + C - 1) / C;
     const size_t rb = 6 * (size_t)plane * sizeof(T);  // one stage's record
-    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, lacc, gpar, loss_d, tgt, phi_d, hbuf;
+    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, gpar, loss_d, tgt, phi_d, hbuf;
     CK(cudaMalloc(&dts_d.p, 2 * sizeof(double) * nsteps));
     CK(cudaMalloc(&ck.p, sb * nck));
     CK(cudaMalloc(&seg.p, sb * (2 * C + 1)));
     CK(cudaMalloc(&recb.p, rb * 2 * C));
-    for (DevBuf *b : {&lam, &lamA, &lpre, &lacc}) {
+    for (DevBuf *b : {&lam, &lamA, &lpre}) {
         CK(cudaMalloc(&b->p, lb));
         CK(cudaMemsetAsync(b->p, 0, lb, st));
     }
@@ -196,7 +196,6 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     AdjArgs<T> q{};
     q.lam_pre = (T *)lpre.p;
     q.lam_dp = (T *)ldp.p;
-    q.lam_acc = (T *)lacc.p;
     q.g_param = (double *)gpar.p;
     q.lam_next = (const T *)lam.p;
     for (int kseg = nck - 1; kseg >= 0; kseg--) {
@@ -327,12 +326,11 @@ int stage_adjoint_impl(moses_sim *s, double t, double dt, const double *lam_out,
     cudaStream_t st = s->stream;
     const long long n = (long long)s->nx * s->ny;
     const size_t lb = 6 * (size_t)s->plane * sizeof(T);
-    DevBuf lo, li, lpre, ldp, lacc, gp, hb, recb;
+    DevBuf lo, li, lpre, ldp, gp, hb, recb;
     CK(cudaMalloc(&recb.p, lb));
     CK(cudaMalloc(&lo.p, lb));
     CK(cudaMalloc(&li.p, lb));
     CK(cudaMalloc(&lpre.p, lb));
-    CK(cudaMalloc(&lacc.p, lb));
     CK(cudaMalloc(&ldp.p, 2 * (size_t)s->plane * sizeof(T)));
     CK(cudaMalloc(&gp.p, 2 * sizeof(double)));
     CK(cudaMalloc(&hb.p, sizeof(double) * 6 * n));
@@ -361,7 +359,6 @@ int stage_adjoint_impl(moses_sim *s, double t, double dt, const double *lam_out,
     q.lam_in = (T *)li.p;
     q.lam_pre = (T *)lpre.p;
     q.lam_dp = (T *)ldp.p;
-    q.lam_acc = (T *)lacc.p;
     q.g_param = (double *)gp.p;
     if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
     pack_lam_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const T *)li.p, (double *)hb.p, s->nx, s->ny, s->pitch,

@@ -16,17 +16,18 @@
 //      kept (StageArgs::rec), reverse the masks, the friction, the sources and
 //      the update.  Writes the adjoint of the pre-friction output lam_pre (6),
 //      of the pressure gradient (dP/dxi, dP/deta), the cell's own
-//      contributions lam_acc (identity + sources + friction), and the
-//      parameter partials (tan delta_b, c_D) reduced per CTA.
+//      contributions (identity + sources + friction, and the direct Heun
+//      term) into lam_in, and the parameter partials (tan delta_b, c_D)
+//      reduced per CTA.
 //   B  per face: recompute the face states (halo 3), form the flux adjoints
 //      from lam_pre and the pressure adjoints of the two neighbours, reverse
 //      the central flux and the minmod reconstruction, and gather per cell:
-//      lam_in = lam_acc + face terms, also for ghost cells at the boundary.
+//      lam_in += face terms; ghost cells at the boundary get theirs.
 //   C  fold the ghost cells' adjoints into their mirror / copy sources
 //      (inflow ghosts are constants).
 // Heun: U^{n+1} = dry(1/2 (U^n + S(S(U^n)))).  With lam^{n+1} given, the
 // second stage's A takes lam_out = 1/2 lam^{n+1} with the momenta zeroed where
-// U^{n+1} is dry, and the first stage's B adds that same term to its cell
+// U^{n+1} is dry, and the first stage's A adds that same term to its cell
 // result, writing lam^n over lam^{n+1} in place (each cell reads its own
 // value before it writes it; no other thread reads it).
 #pragma once
@@ -128,8 +129,8 @@ struct AdjArgs {
     const T *lam_out; // adjoint of the stage output (6 planes, interior); unused when heun == 2
     T *lam_pre;       // A -> B: adjoint of the pre-friction output (6 planes)
     T *lam_dp;        // A -> B: adjoint of dP/dxi, dP/deta (2 planes)
-    T *lam_acc;       // A -> B: the cell's own contributions (6 planes)
-    T *lam_in;        // B: adjoint of the stage input (6 planes, ghosts included)
+    T *lam_in;        // adjoint of the stage input (6 planes, ghosts included): A writes the
+                      // cells' own contributions, B adds the face terms and sets the ghosts
     double *g_param;  // [0] d/d tan(delta_b), [1] d/d c_D (FP64 accumulators)
     // Heun: 2 = second stage (A reads lam_next), 1 = first stage (B adds the
     // direct term; lam_in == lam_next), 0 = a lone stage
@@ -152,6 +153,19 @@ __device__ __forceinline__ T heun_half(const AdjArgs<T> &q, long long g, int c, 
 }  // namespace moses
 
 namespace moses {
+
+// J h_dry of cell g as the stage kernel computes it (FP32: from the slopes)
+template <typename T>
+__device__ __forceinline__ T cell_jhd(const StageArgs<T> &a, long long g)
+{
+    if constexpr (sizeof(T) == 4) {
+        const T sX = a.geo[GS_SX * a.plane + g], sY = a.geo[GS_SY * a.plane + g];
+        const T s2 = fma(sX, sX, fma(sY, sY, T(1)));
+        return s2 * frsqrt(s2) * a.k.h_dry;
+    } else {
+        return a.geo[GC_JHD * a.plane + g];
+    }
+}
 
 // ---- kernel A: cell adjoint (pointwise) --------------------------------------
 template <typename T>
@@ -184,10 +198,11 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
             const T l0 = q.heun == 2 ? T(0.5) * q.lam_next[g] : q.lam_out[g];
             const T l3 = q.heun == 2 ? T(0.5) * q.lam_next[3 * plane + g] : q.lam_out[3 * plane + g];
             const T lp[6] = {l0, T(0), T(0), l3, T(0), T(0)};
+            const T jhd1 = q.heun == 1 ? cell_jhd(a, g) : T(0);
 #pragma unroll
             for (int c = 0; c < 6; c++) {
                 q.lam_pre[c * plane + g] = lp[c];
-                q.lam_acc[c * plane + g] = lp[c];
+                q.lam_in[c * plane + g] = q.heun == 1 ? lp[c] + heun_half(q, g, c, jhd1) : lp[c];
             }
             q.lam_dp[g] = T(0);
             q.lam_dp[plane + g] = T(0);
@@ -347,7 +362,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
 #pragma unroll
         for (int c = 0; c < 6; c++) {
             q.lam_pre[c * plane + g] = lpre[c];
-            q.lam_acc[c * plane + g] = lu[c];
+            q.lam_in[c * plane + g] = q.heun == 1 ? lu[c] + heun_half(q, g, c, jhd) : lu[c];
         }
         q.lam_dp[g] = ldPx;
         q.lam_dp[plane + g] = ldPy;
@@ -719,27 +734,12 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
         adj_ghost_zero<T, TX, TY, 0>(q);
         adj_ghost_zero<T, TX, TY, 1>(q);
     }
+    // the face terms of the tile's cells (a dry tile has none)
     const int i = x0 + tid % TX, j = y0 + tid / TX;
-    if (i < nx && j < ny) {
+    if (wet && i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
-        T jhd = T(0);
-        if (q.heun == 1) {
-            if constexpr (FaceAdjSmem<T, TX, TY>::STAGE) {  // as the FP32 stage: J h_dry from the slopes
-                const int o = (tid / TX + 2) * FaceAdjSmem<T, TX, TY>::LW + tid % TX + 2;
-                const T sX = wet ? sBs[o] : a.geo[GS_SX * plane + g];
-                const T sY = wet ? sBs[FaceAdjSmem<T, TX, TY>::LP + o] : a.geo[GS_SY * plane + g];
-                const T s2 = fma(sX, sX, fma(sY, sY, T(1)));
-                jhd = s2 * frsqrt(s2) * a.k.h_dry;
-            } else {
-                jhd = a.geo[GC_JHD * plane + g];
-            }
-        }
 #pragma unroll
-        for (int c = 0; c < 6; c++) {
-            T v = q.lam_acc[c * plane + g] + lres[c];
-            if (q.heun == 1) v += heun_half(q, g, c, jhd);
-            q.lam_in[c * plane + g] = v;
-        }
+        for (int c = 0; c < 6; c++) q.lam_in[c * plane + g] += lres[c];
     }
 }
 
