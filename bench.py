@@ -304,7 +304,8 @@ def shard(items, rank, world):
 def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="cpu"):
     """Batched ensemble, FP32: 256 members on square grids of lognormal side
     (64..1024 cells, 5 m), each its own spectral DEM, basal friction, drag and
-    release volume; one batched launch per stage replayed from a CUDA graph.
+    release volume; per stage one batched classification launch and one
+    batched launch over the wet tiles of all members, replayed from a CUDA graph.
     Device time from CUDA events on the batch's stream.  With several ranks
     the members are sharded across them; the time is the max over ranks."""
     from paper_2104_06784_gb300 import moses, workloads as W
@@ -323,7 +324,7 @@ def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="c
     cells = int(reduce_over_ranks(cells_rank, "sum", dist, device))
     return {"value": cells * K / (ms / 1e3), "unit": "cell-steps/s", "members": n, "cells": cells,
             "members_per_rank": len(cfgs), "scaling": "strong" if world > 1 else None,
-            "ms_per_step": ms / K, "steps": K, "warmup": Wm, "dtype": "f32", "gpu_launches": 2 * K,
+            "ms_per_step": ms / K, "steps": K, "warmup": Wm, "dtype": "f32", "gpu_launches": 4 * K,
             "tiles_per_launch": tiles,
             "config": "256 scenarios, sides clip(round16(lognormal(ln 256, ln4/2)), 64, 1024), dx 5 m, "
                       "spectral DEMs, delta_b U(15,30) deg, c_D U(1e-4,1e-2) 1/s, release U(1e4,1e6) m^3, FP32"}

@@ -228,8 +228,9 @@ void moses_destroy(moses_sim *s);
 /* ---- Ensembles --------------------------------------------------------------
  * Many independent simulations advanced together, for the "abundant plausible
  * scenarios" and parameter back-calculation use of Sect. 5: each member keeps
- * its own DEM, grid size, parameters, time and CFL time step.  One batched
- * launch per Heun stage covers the 32 x 8 tiles of every member, and the time
+ * its own DEM, grid size, parameters, time and CFL time step.  Per Heun stage
+ * one batched launch classifies the 32 x 8 tiles of every member (the dry
+ * ones get their zero state) and one runs the stage on the wet ones; the time
  * loop is recorded once as a CUDA graph (16 steps) that moses_batch_step
  * replays.  Members are ordinary moses_sim objects created on the same stream
  * with the same precision form; their states and budgets are read with the

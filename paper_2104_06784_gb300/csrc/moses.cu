@@ -1211,8 +1211,11 @@ struct moses_batch {
     cudaEvent_t ev = nullptr;
     std::vector<moses_sim *> sims;
     void *args1 = nullptr, *args2 = nullptr;  // StageArgs<T>[n] for stage 1 / 2
-    BatchTile *tiles = nullptr;
-    int ntiles = 0;
+    BatchStrip *strips = nullptr;  // (member, 32 x 32 strip) of every member
+    int nstrips = 0;
+    int ntiles = 0;                // 32 x 8 tiles of all members
+    BatchTile *list = nullptr;     // wet-tile list (capacity ntiles)
+    unsigned int *list_n = nullptr;
     Ctl **ctls = nullptr;
     int *status = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1243,8 +1246,10 @@ int batch_fail(moses_batch *b, int code, const std::string &msg)
 template <typename T>
 int batch_launch_step(moses_batch *b)
 {
-    if (launch_stage_batch<T>((const StageArgs<T> *)b->args1, b->tiles, b->ntiles, b->stream)) return -1;
-    if (launch_stage_batch<T>((const StageArgs<T> *)b->args2, b->tiles, b->ntiles, b->stream)) return -1;
+    for (void *args : {b->args1, b->args2})
+        if (launch_stage_batch<T>((const StageArgs<T> *)args, b->n, b->strips, b->nstrips, b->list, b->list_n,
+                                  b->stream))
+            return -1;
     return 0;
 }
 
@@ -1252,7 +1257,8 @@ template <typename T>
 int batch_build(moses_batch *b)
 {
     std::vector<StageArgs<T>> a1(b->n), a2(b->n);
-    std::vector<BatchTile> tiles;
+    std::vector<BatchStrip> strips;
+    long long ntiles = 0;
     std::vector<Ctl *> ctls(b->n);
     for (int k = 0; k < b->n; k++) {
         moses_sim *s = b->sims[k];
@@ -1271,24 +1277,33 @@ int batch_build(moses_batch *b)
         a2[k].Rout = rem<T>(s, s->U);
         a2[k].stage = 2;
         a2[k].want_amax = 1;
+        // the launches run listed tiles (the pointer marks it; the batch has its own list)
+        a1[k].wl = a2[k].wl = s->wl;
         const int tx = (s->nx + kBatchTX - 1) / kBatchTX, ty = (s->ny + kBatchTY - 1) / kBatchTY;
-        for (int by = 0; by < ty; by++)
-            for (int bx = 0; bx < tx; bx++) tiles.push_back(BatchTile{k, bx, by, (unsigned)(tx * ty)});
+        ntiles += (long long)tx * ty;
+        for (int sy = 0; sy < (s->ny + 31) / 32; sy++)
+            for (int sx = 0; sx < tx; sx++) strips.push_back(BatchStrip{k, sx, sy});
         ctls[k] = s->ctl;
     }
-    b->ntiles = (int)tiles.size();
+    if (ntiles > (1ll << 30)) return batch_fail(b, MOSES_EINVAL, "too many tiles in the batch");
+    b->ntiles = (int)ntiles;
+    b->nstrips = (int)strips.size();
     moses_sim *s = nullptr;  // CK reports into g_create_err
     CK(cudaMalloc(&b->args1, sizeof(StageArgs<T>) * b->n));
     CK(cudaMalloc(&b->args2, sizeof(StageArgs<T>) * b->n));
-    CK(cudaMalloc(&b->tiles, sizeof(BatchTile) * tiles.size()));
+    CK(cudaMalloc(&b->strips, sizeof(BatchStrip) * strips.size()));
+    CK(cudaMalloc(&b->list, sizeof(BatchTile) * (size_t)b->ntiles));
+    CK(cudaMalloc(&b->list_n, 2 * sizeof(unsigned int)));
+    CK(cudaMemsetAsync(b->list_n, 0, 2 * sizeof(unsigned int), b->stream));
     CK(cudaMalloc(&b->ctls, sizeof(Ctl *) * b->n));
     CK(cudaMalloc(&b->status, sizeof(int)));
     CK(cudaMemcpyAsync(b->args1, a1.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync(b->args2, a2.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync(b->tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->strips, strips.data(), sizeof(BatchStrip) * strips.size(), cudaMemcpyHostToDevice,
+                       b->stream));
     CK(cudaMemcpyAsync(b->ctls, ctls.data(), sizeof(Ctl *) * b->n, cudaMemcpyHostToDevice, b->stream));
     // set the launch attributes outside any capture, then record the graph
-    if (launch_stage_batch<T>((const StageArgs<T> *)b->args1, b->tiles, 0, b->stream))
+    if (launch_stage_batch<T>((const StageArgs<T> *)b->args1, b->n, b->strips, 0, b->list, b->list_n, b->stream))
         return batch_fail(b, MOSES_ECUDA, "batched stage kernel attributes");
     CK(cudaStreamSynchronize(b->stream));
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -1312,7 +1327,9 @@ void free_batch(moses_batch *b)
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->args1);
     cudaFree(b->args2);
-    cudaFree(b->tiles);
+    cudaFree(b->strips);
+    cudaFree(b->list);
+    cudaFree(b->list_n);
     cudaFree(b->ctls);
     cudaFree(b->status);
     if (b->ev) cudaEventDestroy(b->ev);

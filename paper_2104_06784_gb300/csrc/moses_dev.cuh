@@ -201,12 +201,17 @@ __host__ __device__ inline long long cell_index(int i, int j, int pitch)
 // launchers of the templated stage kernels (one translation unit per type)
 namespace moses {
 struct BatchTile;
+struct BatchStrip;
 template <typename T>
 int launch_stage(const StageArgs<T> &a, int tile, void *stream);
 // the same stage (tile 32 x 8) that also writes a.rec
 template <typename T>
 int launch_stage_rec(const StageArgs<T> &a, void *stream);
-// batched stage over a work list of `ntiles` tiles (tile shape 32 x 8)
+// one stage of an ensemble of nsim simulations (descriptors args_device):
+// classification over the `nstrips` strips (32 x 32 cells), then the stage on
+// the wet 32 x 8 tiles listed in `list` (capacity: every tile; list_n: two
+// counters, zero between launches).  nstrips == 0 only sets the attributes.
 template <typename T>
-int launch_stage_batch(const StageArgs<T> *args_device, const BatchTile *tiles_device, int ntiles, void *stream);
+int launch_stage_batch(const StageArgs<T> *args_device, int nsim, const BatchStrip *strips_device, int nstrips,
+                       BatchTile *list, unsigned int *list_n, void *stream);
 }  // namespace moses

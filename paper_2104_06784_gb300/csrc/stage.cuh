@@ -1259,13 +1259,16 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
 // columns, coalesced) with a warp vote, so each mass is read about once; the
 // tiles of the strip then OR their rows.  The step's time step is taken here
 // as the stage kernel takes it (stage 1 records it).
-template <typename T, int TY>
-__global__ void __launch_bounds__(256) classify_kernel(const StageArgs<T> a)
+// The strip (bx, sy) of the simulation `a` (gx tiles across); `append(tx, ty)`
+// lists a wet tile.
+template <typename T, int TY, typename Append>
+__device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int bx, const int sy, const int gx,
+                                               const Append &append)
 {
     constexpr int S = 32, H = S + 4, NTL = S / TY;
     static_assert(S % TY == 0, "strip of whole tiles");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int bx = blockIdx.x, x0 = bx * 32, y0 = blockIdx.y * S;
+    const int x0 = bx * 32, y0 = sy * S;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
     Ctl *ctl = a.ctl;
@@ -1276,7 +1279,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const StageArgs<T> a)
         const double t_now = ctl->t;
         const double dt = a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
         s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
-        if (a.stage == 1 && bx == 0 && blockIdx.y == 0) ctl->dt = dt;
+        if (a.stage == 1 && bx == 0 && sy == 0) ctl->dt = dt;
     }
     // every load of the warp's rows first (all in flight together), then the votes
     constexpr int RPW = (H + 7) / 8;  // rows per warp
@@ -1317,7 +1320,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const StageArgs<T> a)
         bool w = false;
         if (ty0 < ny) {
             for (int r = t * TY; r < t * TY + TY + 4; r++) w |= s_row[r] != 0u;
-            if (w) a.wl[atomicAdd(&a.wl_n[0], 1u)] = (ty0 / TY) * gridDim.x + bx;
+            if (w) append(bx, ty0 / TY);
         }
         s_wet[t] = w;
     }
@@ -1334,6 +1337,13 @@ __global__ void __launch_bounds__(256) classify_kernel(const StageArgs<T> a)
         }
         write_ghosts(a.Uout, a.geo, a, i, j, z, s_tg);
     }
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(256) classify_kernel(const StageArgs<T> a)
+{
+    classify_strip<T, TY>(a, blockIdx.x, blockIdx.y, gridDim.x,
+                          [&](int tx, int ty) { a.wl[atomicAdd(&a.wl_n[0], 1u)] = ty * gridDim.x + tx; });
 }
 
 // The stage on the listed tiles: a grid of resident CTAs takes the list's
@@ -1367,30 +1377,71 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     }
 }
 
-// Ensemble form: one launch runs the same stage of many simulations.  Each CTA
-// takes one entry of the work list (simulation, tile x, tile y), copies that
-// simulation's arguments into shared memory and runs the tile.  Every
+// Ensemble form: the launches of one stage cover many simulations.  Each
 // simulation keeps its own control block, so its own time and time step.
+// classify_kernel_batch takes one entry of the strip list (simulation, strip)
+// per CTA and appends the wet 32 x 8 tiles, as (simulation, tile), to one list
+// for all simulations; stage_kernel_batch_list runs that list on resident
+// CTAs, each copying its tile's simulation arguments into shared memory; its
+// last CTA empties the list and ends the step of every simulation.
 struct BatchTile {
     int sim, bx, by;
-    unsigned int nb;  // CTAs of this simulation in the launch
+};
+struct BatchStrip {
+    int sim, sx, sy;
 };
 
-// FP32: three 256-thread CTAs per SM (85 registers); FP64: two
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY))
-    stage_kernel_batch(const StageArgs<T> *__restrict__ args, const BatchTile *__restrict__ tiles)
+template <typename T>
+__device__ __forceinline__ void copy_args(StageArgs<T> &dst, const StageArgs<T> *src)
+{
+    // cooperative copy of a descriptor (plain 4-byte words)
+    const int *s = reinterpret_cast<const int *>(src);
+    int *d = reinterpret_cast<int *>(&dst);
+    for (int q = threadIdx.x; q < (int)(sizeof(StageArgs<T>) / 4); q += blockDim.x) d[q] = s[q];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) classify_kernel_batch(const StageArgs<T> *__restrict__ args,
+                                                             const BatchStrip *__restrict__ strips,
+                                                             BatchTile *list, unsigned int *list_n)
 {
     __shared__ StageArgs<T> sa;
-    const BatchTile w = tiles[blockIdx.x];
-    {
-        // cooperative copy of the descriptor (plain 4-byte words)
-        const int *src = reinterpret_cast<const int *>(args + w.sim);
-        int *dst = reinterpret_cast<int *>(&sa);
-        for (int q = threadIdx.x; q < (int)(sizeof(StageArgs<T>) / 4); q += blockDim.x) dst[q] = src[q];
+    const BatchStrip w = strips[blockIdx.x];
+    copy_args(sa, args + w.sim);
+    __syncthreads();
+    classify_strip<T, 8>(sa, w.sx, w.sy, (sa.nx + 31) / 32,
+                         [&](int tx, int ty) { list[atomicAdd(&list_n[0], 1u)] = BatchTile{w.sim, tx, ty}; });
+}
+
+// FP32: three 256-thread CTAs per SM (at most 85 registers); FP64: two
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY))
+    stage_kernel_batch_list(const StageArgs<T> *__restrict__ args, const BatchTile *__restrict__ list,
+                            unsigned int *list_n, const int nsim)
+{
+    __shared__ StageArgs<T> sa;
+    __shared__ bool last;
+    const unsigned int n = list_n[0];
+    for (unsigned int w = blockIdx.x; w < n; w += gridDim.x) {
+        const BatchTile t = list[w];
+        __syncthreads();  // the previous tile is done with sa
+        copy_args(sa, args + t.sim);
+        __syncthreads();
+        stage_tile<T, TX, TY>(sa, t.bx, t.by, 0u);
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&list_n[1], 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    stage_tile<T, TX, TY>(sa, w.bx, w.by, w.nb);
+    if (!last) return;
+    __threadfence();
+    for (int k = threadIdx.x; k < nsim; k += blockDim.x)
+        if (args[k].stage == 2 && args[k].rk3 != 2) end_step(args[k]);
+    if (threadIdx.x == 0) {
+        list_n[0] = 0;
+        list_n[1] = 0;
+    }
 }
 
 template <typename T, int TX, int TY, bool VIS = false>

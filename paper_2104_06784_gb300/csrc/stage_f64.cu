@@ -95,20 +95,28 @@ int launch_stage_rec<double>(const StageArgs<double> &a, void *stream)
 }
 
 template <>
-int launch_stage_batch<double>(const StageArgs<double> *args_device, const BatchTile *tiles_device, int ntiles, void *stream)
+int launch_stage_batch<double>(const StageArgs<double> *args_device, int nsim, const BatchStrip *strips_device, int nstrips,
+                          BatchTile *list, unsigned int *list_n, void *stream)
 {
     constexpr size_t smem = stage_smem_bytes<double, 32, 8>();
-    static bool attr_set[64] = {};
+    static int resident[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(stage_kernel_batch<double, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
+    if (dev < 0 || dev >= 64) return -1;
+    if (!resident[dev]) {
+        int per_sm = 0, n_sm = 0;
+        if (cudaFuncSetAttribute(stage_kernel_batch_list<double, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_batch_list<double, 32, 8>, 256, smem) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
             return -1;
-        attr_set[dev] = true;
+        resident[dev] = per_sm * n_sm;
     }
-    if (ntiles <= 0) return 0;
-    stage_kernel_batch<double, 32, 8><<<ntiles, 256, smem, (cudaStream_t)stream>>>(args_device, tiles_device);
+    if (nstrips <= 0) return 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    classify_kernel_batch<double><<<nstrips, 256, 0, st>>>(args_device, strips_device, list, list_n);
+    stage_kernel_batch_list<double, 32, 8><<<resident[dev], 256, smem, st>>>(args_device, list, list_n, nsim);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
