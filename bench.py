@@ -63,8 +63,8 @@ WORDS_PER_CELL_STEP = 13
 # csrc/stage.cuh, first 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
     # profiles/stage_kernel_launch_list_4096_release.md
-    ("f64", "46f9221f5660"): 68.83,
-    ("f32", "46f9221f5660"): 53.31,
+    ("f64", "d0f9dfb0e460"): 68.82,
+    ("f32", "d0f9dfb0e460"): 53.33,
 }
 
 

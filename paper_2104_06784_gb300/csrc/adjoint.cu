@@ -172,6 +172,9 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     a2.Rout = rem<T>(s, s->U);
     a2.stage = 2;
     a2.want_amax = 1;
+    // the forward run steps as moses_step does (wet-tile list)
+    a1.wl = a2.wl = s->wl;
+    a1.wl_n = a2.wl_n = s->wl_n;
     const double zero = 0.0;
     CK(cudaMemcpyAsync(&s->ctl->dt_fixed, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(&s->ctl->t_end, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
@@ -206,6 +209,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
             const int m = k - start;
             set_dt_kernel<<<1, 1, 0, st>>>(s->ctl, dts[nsteps + k], dts[k]);
             StageArgs<T> r1 = a1, r2 = a2;
+            r1.wl = r2.wl = nullptr;  // the recording stage tests each tile itself
+            r1.wl_n = r2.wl_n = nullptr;
             r1.Uin = segU(m);
             r1.Uout = segS(m);
             r1.Rin = rem<T>(s, segU(m));
