@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
         // for the rest (what the full computation below gives for such a cell)
         const long long g = cell_index(i, j, pitch);
         const T m0 = a.Uin[g], m3 = a.Uin[3 * plane + g], p0 = a.rec[g], p3 = a.rec[3 * plane + g];
-        if ((m0 == T(0)) & (m3 == T(0)) & (p0 == T(0)) & (p3 == T(0))) {
+        if (!(nonzero(m0) | nonzero(m3) | nonzero(p0) | nonzero(p3))) {
             dry_cell = true;
             const T l0 = q.heun == 2 ? T(0.5) * q.lam_next[g] : q.lam_out[g];
             const T l3 = q.heun == 2 ? T(0.5) * q.lam_next[3 * plane + g] : q.lam_out[3 * plane + g];
@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     {
         const auto massy = [&](const int tx, const int ty) {
             const int o = (ty + 3) * SW3 + tx + 3;
-            return (sU[o] != T(0)) | (sU[3 * SP3 + o] != T(0));
+            return nonzero(sU[o]) | nonzero(sU[3 * SP3 + o]);
         };
         has_mass = massy(tid % TX, tid / TX);
         for (int h = tid; h < SP3 - NT; h += NT) {

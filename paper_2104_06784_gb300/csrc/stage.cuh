@@ -196,6 +196,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 __device__ __forceinline__ double tabs(double x) { return fabs(x); }
 __device__ __forceinline__ float tabs(float x) { return fabsf(x); }
 
+// x != 0 (NaN included) on the integer unit: GB300's FP64 pipe is the scarce
+// one, and the wet/dry tests read every cell
+__device__ __forceinline__ bool nonzero(double x)
+{
+    return (static_cast<unsigned long long>(__double_as_longlong(x)) << 1) != 0ull;
+}
+__device__ __forceinline__ bool nonzero(float x) { return (static_cast<unsigned int>(__float_as_int(x)) << 1) != 0u; }
+
 // ---- face flux -----------------------------------------------------------------
 template <typename T>
 struct FaceGeo {
@@ -748,10 +756,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         const int ci = x0 + tid % TX, cj = y0 + tid / TX;
         if (ci < nx && cj < ny) {
             const long long g = cell_index(ci, cj, pitch);
-            if constexpr (sizeof(T) == 4) has_mass |= (a.Rin[g] != 0.0f) | (a.Rin[plane + g] != 0.0f);
+            if constexpr (sizeof(T) == 4) has_mass |= nonzero(a.Rin[g]) | nonzero(a.Rin[plane + g]);
             if (a.stage == 2 && !a.debug_stage) {
-                has_mass |= (a.Un[g] != T(0)) | (a.Un[3 * plane + g] != T(0));
-                if constexpr (sizeof(T) == 4) has_mass |= (a.Rn[g] != 0.0f) | (a.Rn[plane + g] != 0.0f);
+                has_mass |= nonzero(a.Un[g]) | nonzero(a.Un[3 * plane + g]);
+                if constexpr (sizeof(T) == 4) has_mass |= nonzero(a.Rn[g]) | nonzero(a.Rn[plane + g]);
             }
         }
     }
@@ -759,7 +767,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     if (!listed) {
 #pragma unroll
         for (int e = 0; e < NE; e++)
-            if (eo[e] >= 0) has_mass |= (sU[eo[e]] != T(0)) | (sU[3 * SP + eo[e]] != T(0));
+            if (eo[e] >= 0) has_mass |= nonzero(sU[eo[e]]) | nonzero(sU[3 * SP + eo[e]]);
     }
     const bool wet = __syncthreads_or(has_mass) != 0;
     if (wet && !listed) {  // CTA-uniform: the momenta, and the slope tile
@@ -1292,12 +1300,12 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
         const int gi = x0 + lane;
         if (gi < nx + 2) {
             const long long g = cell_index(gi, gj, pitch);
-            m[k] |= (a.Uin[g] != T(0)) | (a.Uin[3 * plane + g] != T(0));
+            m[k] |= nonzero(a.Uin[g]) | nonzero(a.Uin[3 * plane + g]);
             if (r >= 2 && r < S + 2 && gj < ny && gi < nx) {  // a cell of the strip: its own extras
-                if constexpr (sizeof(T) == 4) m[k] |= (a.Rin[g] != 0.0f) | (a.Rin[plane + g] != 0.0f);
+                if constexpr (sizeof(T) == 4) m[k] |= nonzero(a.Rin[g]) | nonzero(a.Rin[plane + g]);
                 if (a.stage == 2) {
-                    m[k] |= (a.Un[g] != T(0)) | (a.Un[3 * plane + g] != T(0));
-                    if constexpr (sizeof(T) == 4) m[k] |= (a.Rn[g] != 0.0f) | (a.Rn[plane + g] != 0.0f);
+                    m[k] |= nonzero(a.Un[g]) | nonzero(a.Un[3 * plane + g]);
+                    if constexpr (sizeof(T) == 4) m[k] |= nonzero(a.Rn[g]) | nonzero(a.Rn[plane + g]);
                 }
             }
         }
@@ -1305,7 +1313,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
             const int ge = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;
             if (ge < nx + 2) {
                 const long long g = cell_index(ge, gj, pitch);
-                m[k] |= (a.Uin[g] != T(0)) | (a.Uin[3 * plane + g] != T(0));
+                m[k] |= nonzero(a.Uin[g]) | nonzero(a.Uin[3 * plane + g]);
             }
         }
     }
