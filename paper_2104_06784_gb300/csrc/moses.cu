@@ -762,6 +762,7 @@ static int run_steps(moses_sim *s, int nsteps, double dt_fixed, double t_end, do
     rc = read_ctl(s, &h);
     if (rc) return rc;
     if (t_out) *t_out = h.t;
+    if (h.status & STATUS_TIMEOUT) return fail(s, MOSES_ETIMEOUT, "a bounded device-side wait gave up");
     if (h.status & STATUS_NONFINITE) return fail(s, MOSES_ENONFINITE, "state or time step became non-finite");
     return MOSES_OK;
 }
@@ -1428,6 +1429,7 @@ static int batch_step(moses_batch *b, int nsteps, double *ms)
     int st = 0;
     CK(cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    if (st & STATUS_TIMEOUT) return batch_fail(b, MOSES_ETIMEOUT, "a bounded device-side wait gave up");
     if (st & STATUS_NONFINITE) return batch_fail(b, MOSES_ENONFINITE, "a member became non-finite");
     return MOSES_OK;
 }

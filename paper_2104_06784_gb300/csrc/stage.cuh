@@ -1256,6 +1256,38 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
     stage_tile<T, TX, TY, REC, VIS, CU, WENO>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
+// ---- bulk copies (the TMA engine) completed on an mbarrier -------------------------
+__device__ __forceinline__ unsigned int smem_u32(const void *p) { return (unsigned int)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned int bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared, `bytes` a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned int bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// wait for phase `parity` of the mbarrier, at most `limit` tries; false if it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned int parity, int limit)
+{
+    unsigned int done = 0;
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+    return done != 0;
+}
+
 // Wet/dry masking over a whole launch, for the stepping of the plain form.
 // A tile (32 x TY cells) holds work if a cell of it or of its 2-cell halo has
 // mass (U1 or U4 non-zero; NaN counts), or if a cell of it has a non-zero
@@ -1263,64 +1295,94 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
 // stage result is known -- zero state, zero remainders, the ghost cells it
 // owns filled from it -- and is written here; a tile with work is appended to
 // the list that stage_kernel_list runs.  One CTA (8 warps) covers a strip of
-// 32 x 32 cells: each warp tests whole rows of the strip and its halo (36
-// columns, coalesced) with a warp vote, so each mass is read about once; the
-// tiles of the strip then OR their rows.  The step's time step is taken here
-// as the stage kernel takes it (stage 1 records it).
+// 32 x 32 cells: one thread has the TMA engine copy the rows of the strip and
+// its halo (36 cells from x0 - 2, a 16-byte aligned start) of the planes the
+// test reads into shared memory, all in flight together, completed on one
+// mbarrier (a bounded wait); each warp then tests whole rows with a warp vote
+// and the tiles of the strip OR their rows.  The step's time step is taken
+// here as the stage kernel takes it (stage 1 records it).
 // The strip (bx, sy) of the simulation `a` (gx tiles across); `append(tx, ty)`
 // lists a wet tile.
 template <typename T, int TY, typename Append>
 __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int bx, const int sy, const int gx,
                                                const Append &append)
 {
-    constexpr int S = 32, H = S + 4, NTL = S / TY;
+    constexpr int S = 32, H = S + 4, W = 36, NTL = S / TY;
     static_assert(S % TY == 0, "strip of whole tiles");
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int CR = 16 / sizeof(T);  // cells per 16 bytes
+    __shared__ __align__(128) T s_m[2][H][W];              // U1, U4 of the strip and its halo
+    __shared__ __align__(128) T s_x[F32 ? 6 : 2][S][W];    // own extras: FP32 R (2); combining: U^n's U1, U4, FP32 R^n
+    __shared__ unsigned long long s_bar;
+    __shared__ double s_tg;
+    __shared__ unsigned int s_row[H];  // row y0 - 2 + r of the strip and halo has work
+    __shared__ bool s_wet[NTL];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = bx * 32, y0 = sy * S;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
     Ctl *ctl = a.ctl;
-    __shared__ double s_tg;
-    __shared__ unsigned int s_row[H];  // row y0 - 2 + r of the strip and halo has work
-    __shared__ bool s_wet[NTL];
-    if (threadIdx.x == 0) {
+    const bool combine = a.stage == 2;
+    const int nxp = (F32 ? 2 : 0) + (combine ? (F32 ? 4 : 2) : 0);  // extra planes copied
+    // cells x0-2 .. x0+33 clipped to the ghost-extended grid (gi < nx + 2),
+    // rounded up to 16 bytes (the few cells past nx + 1 lie in the row's
+    // padding or the next row, inside the plane, and are never tested)
+    const int l0 = min(W, nx + 4 - x0);
+    const unsigned int rb = (unsigned int)((l0 + CR - 1) / CR * CR * sizeof(T));
+    const int nrow = min(H, ny + 4 - y0);  // rows with gj = y0 - 2 + r < ny + 2
+    const int nown = min(S, ny - y0);      // rows of the strip inside the grid
+    const int nc = 2 * nrow + nxp * nown;  // row copies
+    if (tid == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
+    if (tid == 0) {
         const double t_now = ctl->t;
         const double dt = a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
         s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
         if (a.stage == 1 && bx == 0 && sy == 0) ctl->dt = dt;
+        mbar_expect_tx(&s_bar, rb * (unsigned int)nc);
     }
-    // every load of the warp's rows first (all in flight together), then the votes
-    constexpr int RPW = (H + 7) / 8;  // rows per warp
-    bool m[RPW];
-#pragma unroll
-    for (int k = 0; k < RPW; k++) {
-        const int r = warp + 8 * k, gj = y0 + r - 2;  // gj >= -2
-        m[k] = false;
-        if (r >= H || gj >= ny + 2) continue;
-        const int gi = x0 + lane;
-        if (gi < nx + 2) {
-            const long long g = cell_index(gi, gj, pitch);
-            m[k] |= nonzero(a.Uin[g]) | nonzero(a.Uin[3 * plane + g]);
-            if (r >= 2 && r < S + 2 && gj < ny && gi < nx) {  // a cell of the strip: its own extras
-                if constexpr (sizeof(T) == 4) m[k] |= nonzero(a.Rin[g]) | nonzero(a.Rin[plane + g]);
-                if (a.stage == 2) {
-                    m[k] |= nonzero(a.Un[g]) | nonzero(a.Un[3 * plane + g]);
-                    if constexpr (sizeof(T) == 4) m[k] |= nonzero(a.Rn[g]) | nonzero(a.Rn[plane + g]);
-                }
+    // the copies, spread over the threads (the barrier's phase cannot end
+    // before thread 0's arrival, whichever comes first)
+    for (int k = tid; k < nc; k += blockDim.x) {
+        if (k < 2 * nrow) {  // masses of the strip and its halo
+            const int p = k & 1, r = k >> 1;
+            bulk_g2s(&s_m[p][r][0], a.Uin + 3 * p * plane + cell_index(x0 - 2, y0 - 2 + r, pitch), rb, &s_bar);
+        } else {  // own extras
+            const int kk = k - 2 * nrow, e = kk % nxp, r = kk / nxp;
+            const long long g = cell_index(x0 - 2, y0 + r, pitch);
+            const T *src;
+            if constexpr (F32) {
+                src = e == 0 ? a.Rin + g : e == 1 ? a.Rin + plane + g : e == 2 ? a.Un + g
+                    : e == 3 ? a.Un + 3 * plane + g : e == 4 ? a.Rn + g : a.Rn + plane + g;
+            } else {
+                src = e == 0 ? a.Un + g : a.Un + 3 * plane + g;
             }
-        }
-        if (lane < 4) {  // the halo columns x0-2, x0-1, x0+32, x0+33
-            const int ge = lane < 2 ? x0 - 2 + lane : x0 + 30 + lane;
-            if (ge < nx + 2) {
-                const long long g = cell_index(ge, gj, pitch);
-                m[k] |= nonzero(a.Uin[g]) | nonzero(a.Uin[3 * plane + g]);
-            }
+            bulk_g2s(&s_x[e][r][0], src, rb, &s_bar);
         }
     }
-#pragma unroll
-    for (int k = 0; k < RPW; k++) {
-        const unsigned int any = __any_sync(0xffffffffu, m[k]);
-        if (lane == 0 && warp + 8 * k < H) s_row[warp + 8 * k] = any;
+    // every thread waits for the copies (bounded); if any gave up, the CTA
+    // reports it, lets the copies in flight land, and stops
+    const bool got = mbar_wait(&s_bar, 0, 1 << 20);
+    if (!__syncthreads_and(got)) {
+        if (tid == 0) atomicOr(&ctl->status, (int)STATUS_TIMEOUT);
+        mbar_wait(&s_bar, 0, 1 << 20);
+        return;
+    }
+    for (int r = warp; r < H; r += 8) {
+        const int gj = y0 + r - 2;  // >= -2
+        bool m = false;
+        if (gj < ny + 2) {
+            const int gi = x0 + lane;  // shared column lane + 2
+            if (gi < nx + 2) m |= nonzero(s_m[0][r][lane + 2]) | nonzero(s_m[1][r][lane + 2]);
+            if (lane < 4) {  // the halo columns x0-2, x0-1, x0+32, x0+33
+                const int col = lane < 2 ? lane : lane + 32;
+                if (x0 - 2 + col < nx + 2) m |= nonzero(s_m[0][r][col]) | nonzero(s_m[1][r][col]);
+            }
+            if (r >= 2 && r < S + 2 && gj < ny && gi < nx)  // a cell of the strip: its own extras
+                for (int e = 0; e < nxp; e++) m |= nonzero(s_x[e][r - 2][lane + 2]);
+        }
+        const unsigned int any = __any_sync(0xffffffffu, m);
+        if (lane == 0) s_row[r] = any;
     }
     __syncthreads();
     if (threadIdx.x < NTL) {
