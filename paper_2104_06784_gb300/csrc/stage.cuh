@@ -1410,7 +1410,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
 }
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(256) classify_kernel(const StageArgs<T> a)
+__global__ void __launch_bounds__(256, 5) classify_kernel(const StageArgs<T> a)
 {
     classify_strip<T, TY>(a, blockIdx.x, blockIdx.y, gridDim.x,
                           [&](int tx, int ty) { a.wl[atomicAdd(&a.wl_n[0], 1u)] = ty * gridDim.x + tx; });
