@@ -63,8 +63,8 @@ WORDS_PER_CELL_STEP = 13
 # csrc/stage.cuh, first 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
     # profiles/stage_kernel_launch_list_4096_release.md
-    ("f64", "5e2d5e254f25"): 69.55,
-    ("f32", "5e2d5e254f25"): 53.61,
+    ("f64", "9df69d17bde5"): 69.59,
+    ("f32", "9df69d17bde5"): 53.62,
 }
 
 

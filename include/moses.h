@@ -312,6 +312,14 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
                       const moses_params *p, const double *U_in_device, double *U_out_device,
                       double t, double *dt_out, void *stream);
 
+/* Testing the failure path of the one device-side wait: with on != 0 the
+ * wet/dry classification of the following steps waits for 16 bytes that no
+ * copy delivers, so its bounded wait (about 0.5 s per CTA, twice) runs out;
+ * the step then returns MOSES_ETIMEOUT, and a later step does so again until
+ * a new state is set.  No fault is raised: the wait simply ends.  on = 0
+ * restores normal stepping.  Errors: EINVAL. */
+int moses_debug_timeout(moses_sim *s, int on);
+
 /* Debugging aid (not in the paper): fills every element of the simulation's
  * device buffers that no kernel may read -- the pitch padding to the right of
  * the second ghost column, in every plane of the state, the Heun intermediate

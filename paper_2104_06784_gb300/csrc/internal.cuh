@@ -25,6 +25,7 @@ struct moses_sim {
     void *Us2 = nullptr;   // second intermediate of the three-stage Runge-Kutta (rk = 3 only)
     int *wl = nullptr;              // wet-tile list of the stepping launches (one entry per 32 x 4 tile)
     unsigned int *wl_n = nullptr;   // its two counters
+    int dbg_stall = 0;              // moses_debug_timeout: the classification's copy wait runs out
     Ctl *ctl = nullptr;    // device control block
     InflowSeg *inflow_d = nullptr;
     InflowSeg inflow_h[MAX_INFLOW];
@@ -91,6 +92,7 @@ inline StageArgs<T> base_args(moses_sim *s)
     a.plane = s->plane;
     a.ph = s->ph;
     a.k = make_kt<T>(s->ph);
+    a.dbg_stall_tx = s->dbg_stall ? 16u : 0u;
     return a;
 }
 

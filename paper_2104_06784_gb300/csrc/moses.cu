@@ -468,6 +468,13 @@ __global__ void poison_kernel(T *buf, int planes, int nx, int ny, int pitch, lon
 }
 }  // namespace
 
+int moses_debug_timeout(moses_sim *s, int on)
+{
+    if (!s) return MOSES_EINVAL;
+    s->dbg_stall = on ? 1 : 0;
+    return MOSES_OK;
+}
+
 int moses_debug_poison(moses_sim *s)
 {
     if (!s) return MOSES_EINVAL;

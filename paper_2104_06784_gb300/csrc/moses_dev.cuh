@@ -189,6 +189,9 @@ struct alignas(8) StageArgs {
     // Null: every tile tests itself.
     int *wl;
     unsigned int *wl_n;
+    // testing only: extra bytes the classification's copy barrier expects and
+    // no copy delivers, so that its bounded wait runs out (0 normally)
+    unsigned int dbg_stall_tx;
 };
 
 __host__ __device__ inline long long cell_index(int i, int j, int pitch)

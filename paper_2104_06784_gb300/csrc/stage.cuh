@@ -1276,15 +1276,25 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned in
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-// wait for phase `parity` of the mbarrier, at most `limit` tries; false if it gave up
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned int parity, int limit)
+__device__ __forceinline__ unsigned long long global_ns()
 {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for phase `parity` of the mbarrier for at most ~`ns` nanoseconds (and
+// at most 2^26 tries); false if it gave up
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned int parity, unsigned long long ns)
+{
+    const unsigned long long t0 = global_ns();
     unsigned int done = 0;
-    for (int it = 0; it < limit && !done; ++it)
+    for (int it = 0; it < (1 << 26) && !done; ++it) {
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done)
                      : "r"(smem_u32(bar)), "r"(parity)
                      : "memory");
+        if (!done && (it & 255) == 255 && global_ns() - t0 > ns) break;
+    }
     return done != 0;
 }
 
@@ -1339,7 +1349,8 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
         const double dt = a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
         s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
         if (a.stage == 1 && bx == 0 && sy == 0) ctl->dt = dt;
-        mbar_expect_tx(&s_bar, rb * (unsigned int)nc);
+        // (a.dbg_stall_tx: bytes no copy delivers, so that the wait below runs out; testing only)
+        mbar_expect_tx(&s_bar, rb * (unsigned int)nc + a.dbg_stall_tx);
     }
     // the copies, spread over the threads (the barrier's phase cannot end
     // before thread 0's arrival, whichever comes first)
@@ -1362,10 +1373,10 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
     }
     // every thread waits for the copies (bounded); if any gave up, the CTA
     // reports it, lets the copies in flight land, and stops
-    const bool got = mbar_wait(&s_bar, 0, 1 << 20);
+    const bool got = mbar_wait(&s_bar, 0, 500000000ull);  // 0.5 s
     if (!__syncthreads_and(got)) {
         if (tid == 0) atomicOr(&ctl->status, (int)STATUS_TIMEOUT);
-        mbar_wait(&s_bar, 0, 1 << 20);
+        mbar_wait(&s_bar, 0, 500000000ull);
         return;
     }
     for (int r = warp; r < H; r += 8) {

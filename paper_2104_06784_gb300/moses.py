@@ -93,6 +93,7 @@ SIGNATURES = [
     ("moses_last_error", C.c_char_p, [_vp]),
     ("moses_destroy", None, [_vp]),
     ("moses_version", C.c_char_p, []),
+    ("moses_debug_timeout", C.c_int, [_vp, C.c_int]),
     ("moses_debug_poison", C.c_int, [_vp]),
 ]
 
@@ -204,6 +205,11 @@ class Sim:
         ms = (C.c_double * 2)()
         self._ck(self._L.moses_step_timed(self._h, int(n), C.byref(t), ms))
         return t.value, [ms[0], ms[1]]
+
+    def debug_timeout(self, on: bool = True):
+        """Make the classification's bounded copy wait run out (testing the
+        MOSES_ETIMEOUT path without a fault); False restores normal steps."""
+        self._ck(self._L.moses_debug_timeout(self._h, int(bool(on))))
 
     def debug_poison(self):
         """Fill the never-read pitch padding of the device buffers with NaN."""

@@ -85,3 +85,27 @@ def test_overflow_is_reported_as_nonfinite(precision):
     s.set_conserved(U0)
     s.step(2)
     assert np.isfinite(s.get_conserved()).all()
+
+
+# ----------------------------------------------------------------------------
+# the one device-side wait (the classification's wait for its bulk copies on
+# an mbarrier) is bounded: made to run out -- the barrier expects bytes no
+# copy delivers -- it ends, the step reports MOSES_ETIMEOUT and the context
+# stays usable
+
+
+@pytest.mark.parametrize("precision", [moses.FP64, moses.FP32])
+def test_copy_wait_timeout_is_reported(precision):
+    cfg = W.release_config(nx=40, ny=30, cfl=0.2)
+    s = moses.from_config(cfg, precision=precision)
+    U0 = s.get_conserved()
+    s.debug_timeout(True)
+    with pytest.raises(moses.MosesError) as e:
+        s.step(1)
+    assert e.value.code == moses.MOSES_ETIMEOUT
+    s.debug_timeout(False)
+    s.set_conserved(U0)  # a new state clears the status word
+    s.step(5)
+    ref = moses.from_config(cfg, precision=precision)
+    ref.step(5)
+    assert np.array_equal(s.get_conserved(), ref.get_conserved())
