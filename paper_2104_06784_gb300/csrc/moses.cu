@@ -1219,7 +1219,7 @@ struct moses_batch {
     cudaEvent_t ev = nullptr;
     std::vector<moses_sim *> sims;
     void *args1 = nullptr, *args2 = nullptr;  // StageArgs<T>[n] for stage 1 / 2
-    BatchStrip *strips = nullptr;  // (member, 32 x 32 strip) of every member
+    BatchStrip *strips = nullptr;  // (member, 32 x kStripRows strip) of every member
     int nstrips = 0;
     int ntiles = 0;                // 32 x 8 tiles of all members
     BatchTile *list = nullptr;     // wet-tile list (capacity ntiles)
@@ -1289,7 +1289,7 @@ int batch_build(moses_batch *b)
         a1[k].wl = a2[k].wl = s->wl;
         const int tx = (s->nx + kBatchTX - 1) / kBatchTX, ty = (s->ny + kBatchTY - 1) / kBatchTY;
         ntiles += (long long)tx * ty;
-        for (int sy = 0; sy < (s->ny + 31) / 32; sy++)
+        for (int sy = 0; sy < (s->ny + kStripRows - 1) / kStripRows; sy++)
             for (int sx = 0; sx < tx; sx++) strips.push_back(BatchStrip{k, sx, sy});
         ctls[k] = s->ctl;
     }

@@ -205,13 +205,16 @@ __host__ __device__ inline long long cell_index(int i, int j, int pitch)
 namespace moses {
 struct BatchTile;
 struct BatchStrip;
+// the wet/dry classification works on strips of 32 columns by kStripRows rows,
+// one CTA of kStripWarps warps each
+constexpr int kStripRows = 16, kStripWarps = 4;
 template <typename T>
 int launch_stage(const StageArgs<T> &a, int tile, void *stream);
 // the same stage (tile 32 x 8) that also writes a.rec
 template <typename T>
 int launch_stage_rec(const StageArgs<T> &a, void *stream);
 // one stage of an ensemble of nsim simulations (descriptors args_device):
-// classification over the `nstrips` strips (32 x 32 cells), then the stage on
+// classification over the `nstrips` strips (32 x kStripRows cells), then the stage on
 // the wet 32 x 8 tiles listed in `list` (capacity: every tile; list_n: two
 // counters, zero between launches).  nstrips == 0 only sets the attributes.
 template <typename T>

@@ -1304,8 +1304,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned int 
 // FP32 mass remainder or, in a combining stage, mass at U^n.  A dry tile's
 // stage result is known -- zero state, zero remainders, the ghost cells it
 // owns filled from it -- and is written here; a tile with work is appended to
-// the list that stage_kernel_list runs.  One CTA (8 warps) covers a strip of
-// 32 x 32 cells: one thread has the TMA engine copy the rows of the strip and
+// the list that stage_kernel_list runs.  One CTA (kStripWarps warps) covers a
+// strip of 32 x kStripRows cells: the TMA engine copies the rows of the strip and
 // its halo (36 cells from x0 - 2, a 16-byte aligned start) of the planes the
 // test reads into shared memory, all in flight together, completed on one
 // mbarrier (a bounded wait); each warp then tests whole rows with a warp vote
@@ -1317,7 +1317,7 @@ template <typename T, int TY, typename Append>
 __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int bx, const int sy, const int gx,
                                                const Append &append)
 {
-    constexpr int S = 32, H = S + 4, W = 36, NTL = S / TY;
+    constexpr int S = kStripRows, H = S + 4, W = 36, NTL = S / TY, NW = kStripWarps;
     static_assert(S % TY == 0, "strip of whole tiles");
     constexpr bool F32 = sizeof(T) == 4;
     constexpr int CR = 16 / sizeof(T);  // cells per 16 bytes
@@ -1379,7 +1379,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
         mbar_wait(&s_bar, 0, 500000000ull);
         return;
     }
-    for (int r = warp; r < H; r += 8) {
+    for (int r = warp; r < H; r += NW) {
         const int gj = y0 + r - 2;  // >= -2
         bool m = false;
         if (gj < ny + 2) {
@@ -1407,7 +1407,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
     }
     __syncthreads();
     const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-    for (int r = warp; r < S; r += 8) {
+    for (int r = warp; r < S; r += NW) {
         const int j = y0 + r, i = x0 + lane;
         if (j >= ny || s_wet[r / TY] || i >= nx) continue;
         const long long g = cell_index(i, j, pitch);
@@ -1421,7 +1421,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
 }
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(256, 5) classify_kernel(const StageArgs<T> a)
+__global__ void __launch_bounds__(32 * kStripWarps, 10) classify_kernel(const StageArgs<T> a)
 {
     classify_strip<T, TY>(a, blockIdx.x, blockIdx.y, gridDim.x,
                           [&](int tx, int ty) { a.wl[atomicAdd(&a.wl_n[0], 1u)] = ty * gridDim.x + tx; });
@@ -1482,7 +1482,7 @@ __device__ __forceinline__ void copy_args(StageArgs<T> &dst, const StageArgs<T> 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) classify_kernel_batch(const StageArgs<T> *__restrict__ args,
+__global__ void __launch_bounds__(32 * kStripWarps) classify_kernel_batch(const StageArgs<T> *__restrict__ args,
                                                              const BatchStrip *__restrict__ strips,
                                                              BatchTile *list, unsigned int *list_n)
 {

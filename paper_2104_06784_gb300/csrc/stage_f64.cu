@@ -46,7 +46,7 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     }
     static_assert(TX == 32, "classify_kernel works on 32-wide strips");
     const int gx = (a.nx + TX - 1) / TX;
-    classify_kernel<T, TY><<<dim3(gx, (a.ny + 31) / 32), 256, 0, st>>>(a);
+    classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
     stage_kernel_list<T, TX, TY><<<resident[dev], TX * TY, smem, st>>>(a, gx);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
@@ -115,7 +115,7 @@ int launch_stage_batch<double>(const StageArgs<double> *args_device, int nsim, c
     }
     if (nstrips <= 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
-    classify_kernel_batch<double><<<nstrips, 256, 0, st>>>(args_device, strips_device, list, list_n);
+    classify_kernel_batch<double><<<nstrips, 32 * kStripWarps, 0, st>>>(args_device, strips_device, list, list_n);
     stage_kernel_batch_list<double, 32, 8><<<resident[dev], 256, smem, st>>>(args_device, list, list_n, nsim);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
