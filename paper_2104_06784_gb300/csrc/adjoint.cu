@@ -175,6 +175,9 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     // the forward run steps as moses_step does (wet-tile list)
     a1.wl = a2.wl = s->wl;
     a1.wl_n = a2.wl_n = s->wl_n;
+    a1.tw_next = s->tw[0];
+    a2.tw_prev = s->tw[0];
+    a2.tw_next = s->tw[1];
     const double zero = 0.0;
     CK(cudaMemcpyAsync(&s->ctl->dt_fixed, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(&s->ctl->t_end, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
@@ -211,6 +214,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
             StageArgs<T> r1 = a1, r2 = a2;
             r1.wl = r2.wl = nullptr;  // the recording stage tests each tile itself
             r1.wl_n = r2.wl_n = nullptr;
+            r1.tw_next = r2.tw_next = nullptr;
+            r2.tw_prev = nullptr;
             r1.Uin = segU(m);
             r1.Uout = segS(m);
             r1.Rin = rem<T>(s, segU(m));

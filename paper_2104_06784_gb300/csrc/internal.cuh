@@ -25,6 +25,7 @@ struct moses_sim {
     void *Us2 = nullptr;   // second intermediate of the three-stage Runge-Kutta (rk = 3 only)
     int *wl = nullptr;              // wet-tile list of the stepping launches (one entry per 32 x 4 tile)
     unsigned int *wl_n = nullptr;   // its two counters
+    unsigned char *tw[2] = {nullptr, nullptr};  // per-tile wet flags of the stages (ping-pong)
     int dbg_stall = 0;              // moses_debug_timeout: the classification's copy wait runs out
     Ctl *ctl = nullptr;    // device control block
     InflowSeg *inflow_d = nullptr;

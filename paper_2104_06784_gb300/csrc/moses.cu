@@ -439,6 +439,8 @@ static void free_sim(moses_sim *s)
     cudaFree(s->Us2);
     cudaFree(s->wl);
     cudaFree(s->wl_n);
+    cudaFree(s->tw[0]);
+    cudaFree(s->tw[1]);
     cudaFree(s->geo);
     cudaFree(s->ctl);
     cudaFree(s->inflow_d);
@@ -539,6 +541,8 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
         (s->ph.rk == 3 && (e = cudaMalloc(&s->Us2, st)) != cudaSuccess) ||
         (e = cudaMalloc(&s->wl, sizeof(int) * (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
         (e = cudaMalloc(&s->wl_n, 2 * sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMalloc(&s->tw[0], (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
+        (e = cudaMalloc(&s->tw[1], (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
         (e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = cudaMalloc(&s->inflow_d, sizeof(InflowSeg) * MAX_INFLOW)) != cudaSuccess ||
         (e = cudaMalloc(&s->red, 8 * sizeof(double))) != cudaSuccess) {
@@ -710,6 +714,9 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
         a[q].want_amax = q == ns - 1;
         a[q].wl = s->wl;
         a[q].wl_n = s->wl_n;
+        // the first stage classifies from the data, the later ones from the flags of the stage before
+        a[q].tw_next = s->tw[q % 2];
+        a[q].tw_prev = q > 0 ? s->tw[(q - 1) % 2] : nullptr;
         if (rk3) {
             a[q].rk3 = q + 1;
             a[q].rk3_bw = q == 2 ? 2.0 / 3.0 : 1.0 / 6.0;
@@ -808,6 +815,7 @@ int probe_stage(moses_sim *s, int tile)
     a.stage = 1;
     a.wl = s->wl;
     a.wl_n = s->wl_n;
+    a.tw_next = s->tw[0];
     return launch_stage<T>(a, tile, s->stream);
 }
 }  // namespace
@@ -1287,6 +1295,9 @@ int batch_build(moses_batch *b)
         a2[k].want_amax = 1;
         // the launches run listed tiles (the pointer marks it; the batch has its own list)
         a1[k].wl = a2[k].wl = s->wl;
+        a1[k].tw_next = s->tw[0];
+        a2[k].tw_prev = s->tw[0];
+        a2[k].tw_next = s->tw[1];
         const int tx = (s->nx + kBatchTX - 1) / kBatchTX, ty = (s->ny + kBatchTY - 1) / kBatchTY;
         ntiles += (long long)tx * ty;
         for (int sy = 0; sy < (s->ny + kStripRows - 1) / kStripRows; sy++)

@@ -189,6 +189,14 @@ struct alignas(8) StageArgs {
     // Null: every tile tests itself.
     int *wl;
     unsigned int *wl_n;
+    // per tile of the launch's shape (row-major, ceil(nx/32) across): 1 where
+    // the stage's classification found work.  The first stage of a step tests
+    // the data and writes tw_next; a later stage (tw_prev non-null) takes a
+    // tile as wet where it or a neighbouring tile was wet in the stage before
+    // (its input has mass only there, and the 2-cell halo lies in the
+    // neighbours), reading no state, and writes tw_next.
+    const unsigned char *tw_prev;
+    unsigned char *tw_next;
     // testing only: extra bytes the classification's copy barrier expects and
     // no copy delivers, so that its bounded wait runs out (0 normally)
     unsigned int dbg_stall_tx;

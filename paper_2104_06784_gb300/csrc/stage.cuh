@@ -1342,70 +1342,103 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
     const int nrow = min(H, ny + 4 - y0);  // rows with gj = y0 - 2 + r < ny + 2
     const int nown = min(S, ny - y0);      // rows of the strip inside the grid
     const int nc = 2 * nrow + nxp * nown;  // row copies
-    if (tid == 0) mbar_init(&s_bar, 1);
-    __syncthreads();
-    if (tid == 0) {
-        const double t_now = ctl->t;
-        const double dt = a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
-        s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
-        if (a.stage == 1 && bx == 0 && sy == 0) ctl->dt = dt;
-        // (a.dbg_stall_tx: bytes no copy delivers, so that the wait below runs out; testing only)
-        mbar_expect_tx(&s_bar, rb * (unsigned int)nc + a.dbg_stall_tx);
-    }
-    // the copies, spread over the threads (the barrier's phase cannot end
-    // before thread 0's arrival, whichever comes first)
-    for (int k = tid; k < nc; k += blockDim.x) {
-        if (k < 2 * nrow) {  // masses of the strip and its halo
-            const int p = k & 1, r = k >> 1;
-            bulk_g2s(&s_m[p][r][0], a.Uin + 3 * p * plane + cell_index(x0 - 2, y0 - 2 + r, pitch), rb, &s_bar);
-        } else {  // own extras
-            const int kk = k - 2 * nrow, e = kk % nxp, r = kk / nxp;
-            const long long g = cell_index(x0 - 2, y0 + r, pitch);
-            const T *src;
-            if constexpr (F32) {
-                src = e == 0 ? a.Rin + g : e == 1 ? a.Rin + plane + g : e == 2 ? a.Un + g
-                    : e == 3 ? a.Un + 3 * plane + g : e == 4 ? a.Rn + g : a.Rn + plane + g;
-            } else {
-                src = e == 0 ? a.Un + g : a.Un + 3 * plane + g;
+    const bool from_flags = a.tw_prev != nullptr && a.stage == 2;
+    if (from_flags) {
+        // a combining stage: its input has mass only in the tiles the stage
+        // before found wet (it wrote zeros elsewhere), and U^n only in the
+        // first stage's wet tiles, which those include; a tile with a wet
+        // neighbour (the 2-cell halo reaches into the neighbours) or on a side
+        // with an inflow segment (whose ghost state changes within the step)
+        // computes
+        if (tid == 0) {
+            s_tg = ctl->t + (a.rk3 == 2 ? 0.5 * ctl->dt : ctl->dt);
+        }
+        if (tid < NTL) {
+            const int t = tid, ty0 = y0 + t * TY, ty = ty0 / TY, gy = (ny + TY - 1) / TY;
+            bool w = false;
+            if (ty0 < ny) {
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        const int xx = bx + dx, yy = ty + dy;
+                        if (xx >= 0 && xx < gx && yy >= 0 && yy < gy) w |= a.tw_prev[yy * gx + xx] != 0;
+                    }
+                for (int f = 0; f < a.n_inflow; f++) {
+                    const int sd = a.inflow[f].side;
+                    w |= (sd == 0 && bx == 0) || (sd == 1 && bx == gx - 1) || (sd == 2 && ty == 0) || (sd == 3 && ty == gy - 1);
+                }
+                if (w) append(bx, ty);
+                a.tw_next[ty * gx + bx] = w;
             }
-            bulk_g2s(&s_x[e][r][0], src, rb, &s_bar);
+            s_wet[t] = w;
         }
-    }
-    // every thread waits for the copies (bounded); if any gave up, the CTA
-    // reports it, lets the copies in flight land, and stops
-    const bool got = mbar_wait(&s_bar, 0, 500000000ull);  // 0.5 s
-    if (!__syncthreads_and(got)) {
-        if (tid == 0) atomicOr(&ctl->status, (int)STATUS_TIMEOUT);
-        mbar_wait(&s_bar, 0, 500000000ull);
-        return;
-    }
-    for (int r = warp; r < H; r += NW) {
-        const int gj = y0 + r - 2;  // >= -2
-        bool m = false;
-        if (gj < ny + 2) {
-            const int gi = x0 + lane;  // shared column lane + 2
-            if (gi < nx + 2) m |= nonzero(s_m[0][r][lane + 2]) | nonzero(s_m[1][r][lane + 2]);
-            if (lane < 4) {  // the halo columns x0-2, x0-1, x0+32, x0+33
-                const int col = lane < 2 ? lane : lane + 32;
-                if (x0 - 2 + col < nx + 2) m |= nonzero(s_m[0][r][col]) | nonzero(s_m[1][r][col]);
+        __syncthreads();
+    } else {
+        if (tid == 0) mbar_init(&s_bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            const double t_now = ctl->t;
+            const double dt = a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
+            s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
+            if (a.stage == 1 && bx == 0 && sy == 0) ctl->dt = dt;
+            // (a.dbg_stall_tx: bytes no copy delivers, so that the wait below runs out; testing only)
+            mbar_expect_tx(&s_bar, rb * (unsigned int)nc + a.dbg_stall_tx);
+        }
+        // the copies, spread over the threads (the barrier's phase cannot end
+        // before thread 0's arrival, whichever comes first)
+        for (int k = tid; k < nc; k += blockDim.x) {
+            if (k < 2 * nrow) {  // masses of the strip and its halo
+                const int p = k & 1, r = k >> 1;
+                bulk_g2s(&s_m[p][r][0], a.Uin + 3 * p * plane + cell_index(x0 - 2, y0 - 2 + r, pitch), rb, &s_bar);
+            } else {  // own extras
+                const int kk = k - 2 * nrow, e = kk % nxp, r = kk / nxp;
+                const long long g = cell_index(x0 - 2, y0 + r, pitch);
+                const T *src;
+                if constexpr (F32) {
+                    src = e == 0 ? a.Rin + g : e == 1 ? a.Rin + plane + g : e == 2 ? a.Un + g
+                        : e == 3 ? a.Un + 3 * plane + g : e == 4 ? a.Rn + g : a.Rn + plane + g;
+                } else {
+                    src = e == 0 ? a.Un + g : a.Un + 3 * plane + g;
+                }
+                bulk_g2s(&s_x[e][r][0], src, rb, &s_bar);
             }
-            if (r >= 2 && r < S + 2 && gj < ny && gi < nx)  // a cell of the strip: its own extras
-                for (int e = 0; e < nxp; e++) m |= nonzero(s_x[e][r - 2][lane + 2]);
         }
-        const unsigned int any = __any_sync(0xffffffffu, m);
-        if (lane == 0) s_row[r] = any;
-    }
-    __syncthreads();
-    if (threadIdx.x < NTL) {
-        const int t = threadIdx.x, ty0 = y0 + t * TY;
-        bool w = false;
-        if (ty0 < ny) {
-            for (int r = t * TY; r < t * TY + TY + 4; r++) w |= s_row[r] != 0u;
-            if (w) append(bx, ty0 / TY);
+        // every thread waits for the copies (bounded); if any gave up, the CTA
+        // reports it, lets the copies in flight land, and stops
+        const bool got = mbar_wait(&s_bar, 0, 500000000ull);  // 0.5 s
+        if (!__syncthreads_and(got)) {
+            if (tid == 0) atomicOr(&ctl->status, (int)STATUS_TIMEOUT);
+            mbar_wait(&s_bar, 0, 500000000ull);
+            return;
         }
-        s_wet[t] = w;
+        for (int r = warp; r < H; r += NW) {
+            const int gj = y0 + r - 2;  // >= -2
+            bool m = false;
+            if (gj < ny + 2) {
+                const int gi = x0 + lane;  // shared column lane + 2
+                if (gi < nx + 2) m |= nonzero(s_m[0][r][lane + 2]) | nonzero(s_m[1][r][lane + 2]);
+                if (lane < 4) {  // the halo columns x0-2, x0-1, x0+32, x0+33
+                    const int col = lane < 2 ? lane : lane + 32;
+                    if (x0 - 2 + col < nx + 2) m |= nonzero(s_m[0][r][col]) | nonzero(s_m[1][r][col]);
+                }
+                if (r >= 2 && r < S + 2 && gj < ny && gi < nx)  // a cell of the strip: its own extras
+                    for (int e = 0; e < nxp; e++) m |= nonzero(s_x[e][r - 2][lane + 2]);
+            }
+            const unsigned int any = __any_sync(0xffffffffu, m);
+            if (lane == 0) s_row[r] = any;
+        }
+        __syncthreads();
+        if (threadIdx.x < NTL) {
+            const int t = threadIdx.x, ty0 = y0 + t * TY;
+            bool w = false;
+            if (ty0 < ny) {
+                for (int r = t * TY; r < t * TY + TY + 4; r++) w |= s_row[r] != 0u;
+                if (w) append(bx, ty0 / TY);
+                if (a.tw_next) a.tw_next[(ty0 / TY) * gx + bx] = w;
+            }
+            s_wet[t] = w;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     for (int r = warp; r < S; r += NW) {
         const int j = y0 + r, i = x0 + lane;
