@@ -63,8 +63,8 @@ WORDS_PER_CELL_STEP = 13
 # csrc/stage.cuh, first 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
     # profiles/stage_kernel_launch_list_4096_release.md
-    ("f64", "31b369355fcf"): 69.93,
-    ("f32", "31b369355fcf"): 53.36,
+    ("f64", "308338c9ae9c"): 54.32,
+    ("f32", "308338c9ae9c"): 39.16,
 }
 
 
