@@ -212,10 +212,7 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
             const int m = k - start;
             set_dt_kernel<<<1, 1, 0, st>>>(s->ctl, dts[nsteps + k], dts[k]);
             StageArgs<T> r1 = a1, r2 = a2;
-            r1.wl = r2.wl = nullptr;  // the recording stage tests each tile itself
-            r1.wl_n = r2.wl_n = nullptr;
-            r1.tw_next = r2.tw_next = nullptr;
-            r2.tw_prev = nullptr;
+            // (the recording stages run on the wet-tile list too, tile 32 x 8)
             r1.Uin = segU(m);
             r1.Uout = segS(m);
             r1.Rin = rem<T>(s, segU(m));

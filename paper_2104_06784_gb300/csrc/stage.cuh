@@ -1445,6 +1445,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
         if (j >= ny || s_wet[r / TY] || i >= nx) continue;
         const long long g = cell_index(i, j, pitch);
         store6(a.Uout, plane, g, z);
+        if (a.rec) store6(a.rec, plane, g, z);  // the recording form: zero records too
         if constexpr (sizeof(T) == 4) {
             a.Rout[g] = 0.0f;
             a.Rout[plane + g] = 0.0f;
@@ -1464,7 +1465,7 @@ __global__ void __launch_bounds__(32 * kStripWarps, 10) classify_kernel(const St
 // entries in turn; the last CTA to finish empties the list and, after the
 // step's last stage, ends the step.
 // FP32: three 256-thread CTAs per SM (at most 85 registers); FP64: two
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool REC = false>
 __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY))
     stage_kernel_list(const StageArgs<T> a, const int gx)
 {
@@ -1476,7 +1477,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     // previous tile no longer reads
     for (unsigned int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = a.wl[w];
-        stage_tile<T, TX, TY>(a, t % gx, t / gx, 0u);
+        stage_tile<T, TX, TY, REC>(a, t % gx, t / gx, 0u);
     }
     if (threadIdx.x == 0) {
         __threadfence();

@@ -26,7 +26,7 @@ int launch_tile(const StageArgs<T> &a, cudaStream_t st)
 
 // The stepping launches of the plain form: classify_kernel over every tile,
 // then stage_kernel_list on a grid of resident CTAs over the listed tiles.
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool REC = false>
 int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
 {
     constexpr size_t smem = stage_smem_bytes<T, TX, TY>();
@@ -36,9 +36,9 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     if (dev < 0 || dev >= 64) return -1;
     if (!resident[dev]) {
         int per_sm = 0, n_sm = 0;
-        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY>, TX * TY, smem) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY, REC>, TX * TY, smem) !=
                 cudaSuccess ||
             cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
             return -1;
@@ -47,7 +47,7 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     static_assert(TX == 32, "classify_kernel works on 32-wide strips");
     const int gx = (a.nx + TX - 1) / TX;
     classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
-    stage_kernel_list<T, TX, TY><<<resident[dev], TX * TY, smem, st>>>(a, gx);
+    stage_kernel_list<T, TX, TY, REC><<<resident[dev], TX * TY, smem, st>>>(a, gx);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -91,6 +91,7 @@ template <>
 int launch_stage_rec<double>(const StageArgs<double> &a, void *stream)
 {
     if (!a.rec) return -1;
+    if (a.wl) return launch_tile_list<double, 32, 8, true>(a, (cudaStream_t)stream);
     return launch_tile<double, 32, 8, true>(a, (cudaStream_t)stream);
 }
 
