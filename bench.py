@@ -63,8 +63,8 @@ WORDS_PER_CELL_STEP = 13
 # csrc/stage.cuh, first 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
     # profiles/stage_kernel_launch_list_4096_release.md
-    ("f64", "308338c9ae9c"): 54.32,
-    ("f32", "308338c9ae9c"): 39.16,
+    ("f64", "90cfbf738fab"): 54.38,
+    ("f32", "90cfbf738fab"): 39.13,
 }
 
 
@@ -94,59 +94,92 @@ def stage_hash():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
+
+    The sampler runs every 20 ms from before the measurement (it waits for
+    its first sample, so it is live) to after it; the timed window is marked
+    with begin() / end().  The samples that arrive within the window (plus
+    one interval) are summarised; a window shorter than the interval that
+    caught none is reported with the two samples bracketing it."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.p = None
-        self.lines = []
+        self.lines = []  # (arrival time, line)
+        self.windows = []
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
         except Exception:
             self.p = None
         return self
 
     def _read(self):
         for line in self.p.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def begin(self):
+        self.windows.append([time.time(), None])
+
+    def end(self):
+        if self.windows:
+            self.windows[-1][1] = time.time()
 
     def __exit__(self, *a):
         if self.p:
+            time.sleep(2.5 * self.INTERVAL_MS / 1e3)  # the samples of the window's end
             self.p.terminate()
             try:
                 self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
 
+    @staticmethod
+    def _parse(ln):
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            return None
+        try:
+            return float(f[1]), float(f[2]), f[5:9]
+        except ValueError:
+            return None
+
     def summary(self):
-        mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                mhz.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
+        lag = 1.5 * self.INTERVAL_MS / 1e3
+        parsed = [(t, self._parse(ln)) for t, ln in self.lines]
+        parsed = [(t, v) for t, v in parsed if v is not None]
+        inside = [v for t, v in parsed if any(w0 <= t <= (w1 or w0) + lag for w0, w1 in self.windows)]
+        how = "in the timed window"
+        if not inside and self.windows and parsed:
+            w0, w1 = self.windows[0][0], self.windows[-1][1] or self.windows[-1][0]
+            before = [v for t, v in parsed if t < w0][-1:]
+            after = [v for t, v in parsed if t > w1][:1]
+            inside = before + after
+            how = "bracketing the timed window (shorter than the sampling interval)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = set()
+        for _, _, act in inside:
+            for n, v in zip(names, act):
                 if v.lower() == "active":
                     reasons.add(n)
-        if not mhz:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(mhz)}
+        return {"sm_mhz": statistics.median(v[0] for v in inside), "sm_max_mhz": inside[-1][1],
+                "reasons": sorted(reasons), "samples": len(inside), "window": how,
+                "interval_ms": self.INTERVAL_MS}
 
 
 def cpu_baseline(cfg, steps=None, window=1024):
@@ -208,17 +241,21 @@ def config_dict(cfg, args):
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
 
 
-def measure(sim, cells, K, W, torch):
+def measure(sim, cells, K, W, torch, sampler=None):
     """Device time of K steps (after W warm-up steps) with CUDA events on the
     simulation's stream; per-stage launch times from moses_step_timed."""
     sim.step(W)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if sampler is not None:
+        sampler.begin()
     e0.record(stream)
     sim.step(K)
     e1.record(stream)
     torch.cuda.synchronize()
+    if sampler is not None:
+        sampler.end()
     ms = e0.elapsed_time(e1)
     # per-launch timing of the stage kernel over K more steps
     _, stage_ms = sim.step_timed(K)
@@ -456,7 +493,7 @@ def main():
         if dist is not None:
             dist.barrier()
         with (sampler if name == "f64" else _Null()):
-            ms, stage_ms = measure(sim, cells, K, Wm, torch)
+            ms, stage_ms = measure(sim, cells, K, Wm, torch, sampler if name == "f64" else None)
         ms = max_over_ranks(ms)
         launch_ms = (stage_ms[0] + stage_ms[1]) / (2 * K)
         results[name] = dict(ms=ms, launch_ms=launch_ms, stage_ms=[stage_ms[0] / K, stage_ms[1] / K], sim=sim)
