@@ -8,26 +8,34 @@
 // SrcF_v_Topo).  Coulomb friction is applied semi-implicitly with a stopping
 // condition, then the positivity clamp and the dry-momentum rule.
 //
-// Work decomposition: one CTA per TX x TY tile.  The CTA stages the six
-// state planes of the tile plus a 2-cell halo in shared memory (coalesced
-// loads), computes each cell's minmod slopes once, every x- and y-face flux
-// once, then updates its cells.  In stage 2 it also forms the Heun average in
-// place, writes the ghost cells of the new state (boundary conditions fused
-// into the producer) and reduces the CFL wave speed: warp shuffle max, CTA
-// max, one atomicMax on the IEEE bits of a non-negative double (exact,
-// independent of order).  The last CTA to finish (ticket counter, no waiting)
-// turns the maximum into the next time step.
+// Work decomposition: the stage of one TX x TY tile (stage_tile).  The CTA
+// stages the six state planes of the tile plus a 2-cell halo in shared
+// memory (cp.async), computes each cell's minmod slopes once, every x- and
+// y-face flux once, then updates its cells.  In a combining stage it also
+// forms the Heun average (or the Runge-Kutta combination) in place, writes
+// the ghost cells of the new state (boundary conditions fused into the
+// producer) and reduces the CFL wave speed: warp shuffle max, CTA max, one
+// atomicMax on the IEEE bits of a non-negative double (exact, independent of
+// order).  The last CTA to finish (ticket counter, no waiting) turns the
+// maximum into the next time step.
+//
+// Wet/dry masking: a tile with no mass within the stencil's reach has the
+// zero state as its stage result.  The stepping launches classify every tile
+// first (classify_kernel: TMA bulk copies of the mass rows of 32 x 16-cell
+// strips, warp votes; a combining stage uses the first stage's per-tile
+// flags), write the dry tiles' zero state there, and run stage_tile only on
+// the list of wet tiles (stage_kernel_list, resident CTAs); the other
+// launches test each tile inside stage_tile.
 //
 // GB300 executes two FP64 FMAs per clock per SM, so the FP64 form is bound by
 // the FP64 pipe.  Everything that can leave it does: the minmod limiter, the
-// dry tests, the stopping decision and every max are integer operations on
-// the IEEE bit patterns (exact for the non-negative operands they see);
+// dry and zero tests, the stopping decision and every max are integer
+// operations on the IEEE bit patterns (exact for the operands they see);
 // reciprocals and square roots start from the hardware approximations
-// (rcp/rsqrt.approx.ftz.f64) and take two Newton-Raphson steps (quadratic for
-// 1/x, y <- y (2 - x y); the sqrt residual step s <- s + (x - s^2) r/2),
-// which lands within an ulp or two of the correctly rounded result; fluxes
-// are kept doubled so the factor 1/2 folds into 1/dx; products of parameters
-// and geometry are precomputed per cell and face.
+// (rcp/rsqrt.approx.ftz.f64) and take one third-order refinement step each
+// (frcp, fsqrt, frsqrt below), which lands within an ulp of the correctly
+// rounded result; fluxes are kept doubled so the factor 1/2 folds into 1/dx;
+// products of parameters and geometry are precomputed per cell and face.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -882,7 +890,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     #pragma unroll
             for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
             if (!a.debug_stage && (i == -1 || i == nx - 1)) {
-                // Heun weight 1/2 x boundary volume flux of this stage
+                // the stage's budget weight (Heun 1/2; RK3 1/6, 1/6, 2/3) x boundary volume flux
                 const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dy) * (i == -1 ? 1.0 : -1.0) * bwf;
                 atomicAdd(&acc[0], w * (double)H[0]);
                 atomicAdd(&acc[1], w * (double)H[3]);
