@@ -63,8 +63,8 @@ WORDS_PER_CELL_STEP = 13
 # csrc/stage.cuh, first 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
     # profiles/stage_kernel_launch_list_4096_release.md
-    ("f64", "90cfbf738fab"): 54.38,
-    ("f32", "90cfbf738fab"): 39.13,
+    ("f64", "f1a1dc700d9f"): 54.43,
+    ("f32", "f1a1dc700d9f"): 38.90,
 }
 
 
