@@ -54,17 +54,28 @@ DX = 10.0
 # U^{n+1} (6), read the bed elevation (1).
 FLOPS_PER_CELL_STAGE = 488
 WORDS_PER_CELL_STEP = 13
+# With wet/dry masking a step need not touch a dry cell's state: it must read
+# the two mass planes of every cell once (the wet test; FP32: 2 x 4 B masses
+# and 2 x 4 B remainders, FP64: 2 x 8 B), and move the whole cell-step traffic
+# above only for the cells of the tiles that compute.
+MASS_TEST_BYTES = 16
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one stage of
-# a step -- the wet/dry classification launch plus the listed-tile stage
-# launch -- per cell of the 4096^2 workload, the mean of the two stages of a
-# step, from an ncu capture of bench.py itself at full size (one-pass
-# metrics); valid only for the stage kernel source it was taken on (sha256 of
-# csrc/stage.cuh, first 12) and for this workload (the wet fraction sets it).
+
+def step_bytes(cells, wet_frac, esz):
+    """Algorithmic HBM bytes of one masked step: the wet test over every cell
+    plus the cell-step traffic of the cells in tiles with work."""
+    return MASS_TEST_BYTES * cells + WORDS_PER_CELL_STEP * esz * wet_frac * cells
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step --
+# the wet/dry classification launch plus the listed-tile stage launch, both
+# stages -- per cell of the 4096^2 workload, from an ncu capture of bench.py
+# itself at full size (one-pass metrics) over the timed steps; valid only for
+# the stage kernel source it was taken on (sha256 of csrc/stage.cuh, first
+# 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
-    # profiles/stage_kernel_launch_list_4096_release.md
-    ("f64", "f1a1dc700d9f"): 54.43,
-    ("f32", "f1a1dc700d9f"): 38.90,
+    # before the known-zero tile flags (profiles/stage_kernel_launch_list_4096_release.md)
+    ("f64", "f1a1dc700d9f"): 108.86,
+    ("f32", "f1a1dc700d9f"): 77.80,
 }
 
 
@@ -497,7 +508,7 @@ def main():
         ms = max_over_ranks(ms)
         launch_ms = (stage_ms[0] + stage_ms[1]) / (2 * K)
         results[name] = dict(ms=ms, launch_ms=launch_ms, stage_ms=[stage_ms[0] / K, stage_ms[1] / K], sim=sim)
-        if name == "f64" and not args.only:
+        if not args.only:
             t = tiles[name]["tile"].split("x")
             results[name]["wet_tiles"] = wet_tile_fraction(sim.get_conserved(), int(t[0]), int(t[1]))
         if name == "f32":
@@ -515,23 +526,28 @@ def main():
     value = world * cells * K / (f64["ms"] / 1e3)
     h = stage_hash()
     t64, t32 = tiles["f64"]["tile"], tiles["f32"]["tile"]
-    # The release covers a small part of the terrain: most tiles are dry and
-    # skip their arithmetic (wet/dry masking), so on this workload the stage
-    # streams the state and is bound by HBM; the all-wet measurement
-    # (`dense`) gives the arithmetic-bound rate of the same kernel.
-    gbs64 = WORDS_PER_CELL_STEP * 8 * cells / (2 * f64["launch_ms"] / 1e3) / 1e9
+    # The release covers a small part of the terrain: most tiles are dry, skip
+    # their arithmetic and, once their output holds the zero state, their
+    # writes too (wet/dry masking with known-zero tile flags).  A step then
+    # reads the mass planes once (HBM) and runs the stage arithmetic on the
+    # few wet tiles (FP64 pipe); the roofline counts the bytes such a step
+    # must move (step_bytes).  The all-wet measurement (`dense`) gives the
+    # arithmetic-bound rate of the same kernel.
+    b64 = step_bytes(cells, f64["wet_tiles"], 8)
+    gbs64 = b64 / (2 * f64["launch_ms"] / 1e3) / 1e9
     roof64 = {"bound": "hbm", "achieved": gbs64, "peak": pk["hbm_gbs"], "unit": "GB/s",
               "frac": gbs64 / pk["hbm_gbs"], "traffic": _traffic("f64", h, side),
-              "kernel": f"one stage: moses::classify_kernel<double,{t64.split('x')[1]}> + "
-                        f"moses::stage_kernel_list<double,{t64.replace('x', ',')}>",
-              "peak_source": pk_src, "wet_tiles": f64["wet_tiles"]}
+              "kernel": f"one step: moses::classify_kernel<double,{t64.split('x')[1]}> + "
+                        f"moses::stage_kernel_list<double,{t64.replace('x', ',')}>, two stages",
+              "peak_source": pk_src, "wet_tiles": f64["wet_tiles"], "bytes_per_step": b64}
     f32 = results["f32"]
-    bytes_step32 = WORDS_PER_CELL_STEP * 4 * cells
-    gbs32 = bytes_step32 / (2 * f32["launch_ms"] / 1e3) / 1e9
+    b32 = step_bytes(cells, f32["wet_tiles"], 4)
+    gbs32 = b32 / (2 * f32["launch_ms"] / 1e3) / 1e9
     roof32 = {"bound": "hbm", "achieved": gbs32, "peak": pk["hbm_gbs"], "unit": "GB/s",
               "frac": gbs32 / pk["hbm_gbs"], "traffic": _traffic("f32", h, side),
-              "kernel": f"one stage: moses::classify_kernel<float,{t32.split('x')[1]}> + "
-                        f"moses::stage_kernel_list<float,{t32.replace('x', ',')}>", "peak_source": pk_src}
+              "kernel": f"one step: moses::classify_kernel<float,{t32.split('x')[1]}> + "
+                        f"moses::stage_kernel_list<float,{t32.replace('x', ',')}>, two stages",
+              "peak_source": pk_src, "wet_tiles": f32["wet_tiles"], "bytes_per_step": b32}
 
     # end to end through the C-ABI with pinned host buffers: per step, upload
     # the state, one step, download the state

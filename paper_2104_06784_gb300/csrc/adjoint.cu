@@ -298,6 +298,7 @@ int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double 
                          double g_params[3], double *g_state0, double *g_release_h, const double *release_phi,
                          double timing_ms[2])
 {
+    const ZkReset zr{s};
     if (!s) return MOSES_EINVAL;
     if (!hs_target) return fail(s, MOSES_EINVAL, "hs_target must be non-NULL");
     if (nsteps < 1) return fail(s, MOSES_EINVAL, "nsteps must be >= 1");
@@ -385,6 +386,7 @@ int stage_adjoint_impl(moses_sim *s, double t, double dt, const double *lam_out,
 
 int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out, double *lam_in, double *g_param)
 {
+    const ZkReset zr{s};
     if (!s || !lam_out || !lam_in) return MOSES_EINVAL;
     if (!(std::isfinite(dt) && dt >= 0)) return fail(s, MOSES_EINVAL, "bad dt");
     if (s->p.nu_f != 0.0 || s->p.scheme != MOSES_SCHEME_CENTRAL || s->ph.recon != 0 || s->ph.rk != 2)

@@ -26,6 +26,13 @@ struct moses_sim {
     int *wl = nullptr;              // wet-tile list of the stepping launches (one entry per 32 x 4 tile)
     unsigned int *wl_n = nullptr;   // its two counters
     unsigned char *tw[2] = {nullptr, nullptr};  // per-tile wet flags of the stages (ping-pong)
+    // known-zero tile flags of U, Us and Us2 (three arrays of one byte per
+    // 32 x 4 tile), kept by the stepping launches.  They describe the buffers
+    // only while the stepping launches are their sole writer: every other call
+    // that may write a buffer, or that changes the tile shape, clears
+    // zk_valid, and the next step starts from all-zero flags.
+    unsigned char *zk = nullptr;
+    bool zk_valid = false;
     int dbg_stall = 0;              // moses_debug_timeout: the classification's copy wait runs out
     Ctl *ctl = nullptr;    // device control block
     InflowSeg *inflow_d = nullptr;
@@ -42,6 +49,19 @@ extern std::string g_create_err;
 
 // ---------------------------------------------------------------------------
 // error helpers
+
+// the known-zero tile flags no longer describe the buffers (see moses_sim::zk)
+inline void zk_reset(moses_sim *s)
+{
+    if (s) s->zk_valid = false;
+}
+
+// declared first in a call that may write the state buffers by another route
+// than the stepping launches: clears zk_valid when the call returns
+struct ZkReset {
+    moses_sim *s;
+    ~ZkReset() { zk_reset(s); }
+};
 
 inline int fail(moses_sim *s, int code, const std::string &msg)
 {

@@ -441,6 +441,7 @@ static void free_sim(moses_sim *s)
     cudaFree(s->wl_n);
     cudaFree(s->tw[0]);
     cudaFree(s->tw[1]);
+    cudaFree(s->zk);
     cudaFree(s->geo);
     cudaFree(s->ctl);
     cudaFree(s->inflow_d);
@@ -472,6 +473,7 @@ __global__ void poison_kernel(T *buf, int planes, int nx, int ny, int pitch, lon
 
 int moses_debug_timeout(moses_sim *s, int on)
 {
+    const ZkReset zr{s};
     if (!s) return MOSES_EINVAL;
     s->dbg_stall = on ? 1 : 0;
     return MOSES_OK;
@@ -479,6 +481,7 @@ int moses_debug_timeout(moses_sim *s, int on)
 
 int moses_debug_poison(moses_sim *s)
 {
+    const ZkReset zr{s};
     if (!s) return MOSES_EINVAL;
     if (s->pitch == s->nx + 2 * GH) return MOSES_OK;  // no padding to poison
     const int sp = s->prec == MOSES_FP32 ? 8 : 6;
@@ -543,6 +546,7 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
         (e = cudaMalloc(&s->wl_n, 2 * sizeof(unsigned int))) != cudaSuccess ||
         (e = cudaMalloc(&s->tw[0], (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
         (e = cudaMalloc(&s->tw[1], (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
+        (e = cudaMalloc(&s->zk, 3 * (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
         (e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = cudaMalloc(&s->inflow_d, sizeof(InflowSeg) * MAX_INFLOW)) != cudaSuccess ||
         (e = cudaMalloc(&s->red, 8 * sizeof(double))) != cudaSuccess) {
@@ -616,6 +620,7 @@ static int upload_dense(moses_sim *s, const double *host6)
 int moses_set_release(moses_sim *s, const double *h, const double *phi_s, const double *vx_s, const double *vy_s,
                       const double *vx_f, const double *vy_f)
 {
+    const ZkReset zr{s};
     if (!s) return MOSES_EINVAL;
     if (!h) return fail(s, MOSES_EINVAL, "h must be non-NULL");
     const long long n = (long long)s->nx * s->ny;
@@ -658,6 +663,7 @@ int moses_set_release(moses_sim *s, const double *h, const double *phi_s, const 
 int moses_set_inflow(moses_sim *s, int side, int i0, int i1, int npts, const double *t, const double *Q,
                      const double *phi_s)
 {
+    const ZkReset zr{s};
     if (!s) return MOSES_EINVAL;
     if (s->n_inflow >= MAX_INFLOW) return fail(s, MOSES_EINVAL, "at most 8 inflow segments");
     if (side < 0 || side > 3) return fail(s, MOSES_EINVAL, "side must be 0..3");
@@ -701,6 +707,13 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
     const int ns = rk3 ? 3 : 2;
     void *out[3] = {s->Us, rk3 ? s->Us2 : s->U, s->U};
     void *in[3] = {s->U, s->Us, s->Us2};
+    // the known-zero tile flags of the output buffers: the plain form's
+    // classification keeps them (the model options test each tile in the
+    // stage kernel, which writes every tile)
+    const size_t nt = (size_t)((s->nx + 31) / 32) * ((s->ny + 3) / 4);
+    const bool zk_on = !(s->ph.nu_f > 0.0) && s->ph.scheme != 1 && s->ph.recon != 1;
+    if (zk_on && !s->zk_valid) CK(cudaMemsetAsync(s->zk, 0, 3 * nt, s->stream));
+    s->zk_valid = false;  // until the launches below are in
     for (int q = 0; q < ns; q++) {
         a[q].Uin = (const T *)in[q];
         a[q].Uout = (T *)out[q];
@@ -717,6 +730,7 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
         // the first stage classifies from the data, the later ones from the flags of the stage before
         a[q].tw_next = s->tw[q % 2];
         a[q].tw_prev = q > 0 ? s->tw[(q - 1) % 2] : nullptr;
+        if (zk_on) a[q].zk = s->zk + nt * (out[q] == s->U ? 0 : out[q] == s->Us ? 1 : 2);
         if (rk3) {
             a[q].rk3 = q + 1;
             a[q].rk3_bw = q == 2 ? 2.0 / 3.0 : 1.0 / 6.0;
@@ -745,6 +759,7 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
         if (rc) return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
         stage_ms[0] = acc[0];
         stage_ms[1] = acc[1];
+        s->zk_valid = zk_on;
         return MOSES_OK;
     }
     for (int k = 0; k < nsteps; k++) {
@@ -752,6 +767,7 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
         for (int q = 0; q < ns && rc == 0; q++) rc = launch_stage<T>(a[q], s->tile, s->stream);
         if (rc) return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
     }
+    s->zk_valid = zk_on;
     return MOSES_OK;
 }
 
@@ -776,6 +792,7 @@ static int run_steps(moses_sim *s, int nsteps, double dt_fixed, double t_end, do
     rc = read_ctl(s, &h);
     if (rc) return rc;
     if (t_out) *t_out = h.t;
+    if (h.status & (STATUS_TIMEOUT | STATUS_NONFINITE)) zk_reset(s);  // a classification may have stopped early
     if (h.status & STATUS_TIMEOUT) return fail(s, MOSES_ETIMEOUT, "a bounded device-side wait gave up");
     if (h.status & STATUS_NONFINITE) return fail(s, MOSES_ENONFINITE, "state or time step became non-finite");
     return MOSES_OK;
@@ -791,6 +808,7 @@ int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms)
 
 int moses_set_tile(moses_sim *s, int tile)
 {
+    const ZkReset zr{s};
     if (!s) return MOSES_EINVAL;
     if (tile < 0 || tile >= MOSES_NTILES) return fail(s, MOSES_EINVAL, "tile must be one of MOSES_TILE_*");
     s->tile = tile;
@@ -822,6 +840,7 @@ int probe_stage(moses_sim *s, int tile)
 
 int moses_autotune(moses_sim *s, int reps, int *tile_out, double *ms_out)
 {
+    const ZkReset zr{s};
     if (!s) return MOSES_EINVAL;
     if (reps < 0) return fail(s, MOSES_EINVAL, "reps must be >= 0");
     if (reps == 0) reps = 5;
@@ -979,12 +998,14 @@ static int set_from_device_buf(moses_sim *s, const double *src)
 
 int moses_set_conserved_device(moses_sim *s, const double *U_device)
 {
+    const ZkReset zr{s};
     if (!s || !U_device) return MOSES_EINVAL;
     return set_from_device_buf(s, U_device);
 }
 
 int moses_set_conserved(moses_sim *s, const double *U)
 {
+    const ZkReset zr{s};
     if (!s || !U) return MOSES_EINVAL;
     int rc = upload_dense(s, U);
     if (rc) return rc;
@@ -1018,6 +1039,7 @@ int moses_get_state(moses_sim *s, double *h, double *phi_s, double *vx_s, double
 
 int moses_stage(moses_sim *s, double t, double dt, double *U_out)
 {
+    const ZkReset zr{s};
     if (!s || !U_out) return MOSES_EINVAL;
     if (!(std::isfinite(dt) && dt >= 0 && std::isfinite(t))) return fail(s, MOSES_EINVAL, "bad t or dt");
     int rc = ensure_stage_buf(s);
@@ -1411,6 +1433,7 @@ static int batch_step(moses_batch *b, int nsteps, double *ms)
 {
     if (!b) return MOSES_EINVAL;
     if (nsteps < 0) return batch_fail(b, MOSES_EINVAL, "nsteps must be >= 0");
+    for (moses_sim *m : b->sims) zk_reset(m);  // the batched launches write the members' buffers
     moses_sim *s = nullptr;
     // order after the members' pending work
     CK(cudaEventRecord(b->ev, b->user_stream));

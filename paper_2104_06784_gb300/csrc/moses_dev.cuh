@@ -197,6 +197,14 @@ struct alignas(8) StageArgs {
     // neighbours), reading no state, and writes tw_next.
     const unsigned char *tw_prev;
     unsigned char *tw_next;
+    // known-zero flags of the output buffer, per tile of the launch's shape
+    // (null: every dry tile is written).  1 where the buffer's tile -- the
+    // state, the FP32 remainders and the ghost cells the tile's cells own --
+    // holds the zero state of an earlier write of the classification; such a
+    // tile, dry again, is not written again.  The classification keeps them:
+    // 1 for a dry tile, 0 for a tile with work and for a tile on a side with
+    // an inflow segment (its ghost state follows the hydrograph).
+    unsigned char *zk;
     // testing only: extra bytes the classification's copy barrier expects and
     // no copy delivers, so that its bounded wait runs out (0 normally)
     unsigned int dbg_stall_tx;

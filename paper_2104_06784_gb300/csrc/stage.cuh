@@ -23,9 +23,10 @@
 // zero state as its stage result.  The stepping launches classify every tile
 // first (classify_kernel: TMA bulk copies of the mass rows of 32 x 16-cell
 // strips, warp votes; a combining stage uses the first stage's per-tile
-// flags), write the dry tiles' zero state there, and run stage_tile only on
-// the list of wet tiles (stage_kernel_list, resident CTAs); the other
-// launches test each tile inside stage_tile.
+// flags), write the dry tiles' zero state there (skipping the tiles whose
+// output buffer holds it already, per-tile known-zero flags), and run
+// stage_tile only on the list of wet tiles (stage_kernel_list, resident
+// CTAs); the other launches test each tile inside stage_tile.
 //
 // GB300 executes two FP64 FMAs per clock per SM, so the FP64 form is bound by
 // the FP64 pipe.  Everything that can leave it does: the minmod limiter, the
@@ -1306,13 +1307,41 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned int 
     return done != 0;
 }
 
+// tile (tx, ty) of a gx x gy grid of tiles lies on a side with an inflow
+// segment (its ghost state changes within a step)
+template <typename T>
+__device__ __forceinline__ bool on_inflow_side(const StageArgs<T> &a, int tx, int ty, int gx, int gy)
+{
+    bool on = false;
+    for (int f = 0; f < a.n_inflow; f++) {
+        const int sd = a.inflow[f].side;
+        on |= (sd == 0 && tx == 0) || (sd == 1 && tx == gx - 1) || (sd == 2 && ty == 0) || (sd == 3 && ty == gy - 1);
+    }
+    return on;
+}
+
+// Whether the classification leaves tile `idx` unwritten: a tile with work
+// (the stage kernel writes it), or a dry tile whose output already holds the
+// zero state (known-zero flags; see StageArgs::zk; `known` is the tile's flag,
+// loaded early by the caller), which it keeps up to date.
+template <typename T>
+__device__ __forceinline__ bool keep_tile(const StageArgs<T> &a, bool wet, bool inflow_side, int idx,
+                                          unsigned char known)
+{
+    if (!a.zk) return wet;
+    const bool fixed = !wet && !inflow_side;  // the zero state written now stays valid
+    if (fixed != (known != 0)) a.zk[idx] = fixed;
+    return wet || (fixed && known != 0);
+}
+
 // Wet/dry masking over a whole launch, for the stepping of the plain form.
 // A tile (32 x TY cells) holds work if a cell of it or of its 2-cell halo has
 // mass (U1 or U4 non-zero; NaN counts), or if a cell of it has a non-zero
 // FP32 mass remainder or, in a combining stage, mass at U^n.  A dry tile's
 // stage result is known -- zero state, zero remainders, the ghost cells it
-// owns filled from it -- and is written here; a tile with work is appended to
-// the list that stage_kernel_list runs.  One CTA (kStripWarps warps) covers a
+// owns filled from it -- and is written here, unless the output buffer holds
+// it already from an earlier step (known-zero flags); a tile with work is
+// appended to the list that stage_kernel_list runs.  One CTA (kStripWarps warps) covers a
 // strip of 32 x kStripRows cells: the TMA engine copies the rows of the strip and
 // its halo (36 cells from x0 - 2, a 16-byte aligned start) of the planes the
 // test reads into shared memory, all in flight together, completed on one
@@ -1334,7 +1363,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
     __shared__ unsigned long long s_bar;
     __shared__ double s_tg;
     __shared__ unsigned int s_row[H];  // row y0 - 2 + r of the strip and halo has work
-    __shared__ bool s_wet[NTL];
+    __shared__ bool s_keep[NTL];  // the tile is not zero-written here (keep_tile)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = bx * 32, y0 = sy * S;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
@@ -1351,6 +1380,11 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
     const int nown = min(S, ny - y0);      // rows of the strip inside the grid
     const int nc = 2 * nrow + nxp * nown;  // row copies
     const bool from_flags = a.tw_prev != nullptr && a.stage == 2;
+    // the known-zero flags of the strip's tiles, loaded first: the CTA is
+    // latency-bound, and this load then overlaps the row copies (or the flag
+    // loads of a combining stage).  Only this CTA reads or writes them.
+    unsigned char known = 0;
+    if (a.zk && tid < NTL && y0 + tid * TY < ny) known = a.zk[((y0 + tid * TY) / TY) * gx + bx];
     if (from_flags) {
         // a combining stage: its input has mass only in the tiles the stage
         // before found wet (it wrote zeros elsewhere), and U^n only in the
@@ -1363,21 +1397,21 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
         }
         if (tid < NTL) {
             const int t = tid, ty0 = y0 + t * TY, ty = ty0 / TY, gy = (ny + TY - 1) / TY;
-            bool w = false;
+            bool keep = false;
             if (ty0 < ny) {
+                bool w = false;
                 for (int dy = -1; dy <= 1; dy++)
                     for (int dx = -1; dx <= 1; dx++) {
                         const int xx = bx + dx, yy = ty + dy;
                         if (xx >= 0 && xx < gx && yy >= 0 && yy < gy) w |= a.tw_prev[yy * gx + xx] != 0;
                     }
-                for (int f = 0; f < a.n_inflow; f++) {
-                    const int sd = a.inflow[f].side;
-                    w |= (sd == 0 && bx == 0) || (sd == 1 && bx == gx - 1) || (sd == 2 && ty == 0) || (sd == 3 && ty == gy - 1);
-                }
+                const bool inf = on_inflow_side(a, bx, ty, gx, gy);
+                w |= inf;
                 if (w) append(bx, ty);
                 a.tw_next[ty * gx + bx] = w;
+                keep = keep_tile(a, w, inf, ty * gx + bx, known);
             }
-            s_wet[t] = w;
+            s_keep[t] = keep;
         }
         __syncthreads();
     } else {
@@ -1436,21 +1470,24 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
         }
         __syncthreads();
         if (threadIdx.x < NTL) {
-            const int t = threadIdx.x, ty0 = y0 + t * TY;
-            bool w = false;
+            const int t = threadIdx.x, ty0 = y0 + t * TY, ty = ty0 / TY;
+            bool keep = false;
             if (ty0 < ny) {
+                bool w = false;
                 for (int r = t * TY; r < t * TY + TY + 4; r++) w |= s_row[r] != 0u;
-                if (w) append(bx, ty0 / TY);
-                if (a.tw_next) a.tw_next[(ty0 / TY) * gx + bx] = w;
+                if (w) append(bx, ty);
+                if (a.tw_next) a.tw_next[ty * gx + bx] = w;
+                const bool inf = a.zk != nullptr && on_inflow_side(a, bx, ty, gx, (ny + TY - 1) / TY);
+                keep = keep_tile(a, w, inf, ty * gx + bx, known);
             }
-            s_wet[t] = w;
+            s_keep[t] = keep;
         }
         __syncthreads();
     }
     const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     for (int r = warp; r < S; r += NW) {
         const int j = y0 + r, i = x0 + lane;
-        if (j >= ny || s_wet[r / TY] || i >= nx) continue;
+        if (j >= ny || s_keep[r / TY] || i >= nx) continue;
         const long long g = cell_index(i, j, pitch);
         store6(a.Uout, plane, g, z);
         if (a.rec) store6(a.rec, plane, g, z);  // the recording form: zero records too

@@ -1,5 +1,6 @@
 """Host-side logic of bench.py (no GPU): the wet-tile fraction that the line
-reports beside the roofline, and the clock sampler's window summary."""
+reports beside the roofline, the roofline's bytes of a masked step, and the
+clock sampler's window summary."""
 import time
 
 import numpy as np
@@ -54,3 +55,12 @@ def test_clock_summary_window_and_bracketing():
     assert got["samples"] == 2 and "bracketing" in got["window"]
     s.lines = []
     assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_step_bytes_of_a_masked_step():
+    """The roofline's bytes of one masked step: the wet test reads 16 B of
+    every cell; the cells of tiles with work add the 13-word cell-step
+    traffic (FP64 104 B, FP32 52 B)."""
+    assert bench.step_bytes(1000, 0.0, 8) == 16 * 1000
+    assert bench.step_bytes(1000, 1.0, 8) == (16 + 104) * 1000
+    assert bench.step_bytes(1000, 0.5, 4) == 16 * 1000 + 26 * 1000
