@@ -73,7 +73,10 @@ def step_bytes(cells, wet_frac, esz):
 # the stage kernel source it was taken on (sha256 of csrc/stage.cuh, first
 # 12) and for this workload (the wet fraction sets it).
 TRAFFIC = {
-    # before the known-zero tile flags (profiles/stage_kernel_launch_list_4096_release.md)
+    # profiles/stage_kernel_launch_list_4096_release.md (tile 32 x 8; the
+    # classification's read of the mass planes is 95 % of it at any tile shape)
+    ("f64", "beb8a8d2e738"): 16.87,
+    # before the known-zero tile flags
     ("f64", "f1a1dc700d9f"): 108.86,
     ("f32", "f1a1dc700d9f"): 77.80,
 }

@@ -1506,6 +1506,62 @@ __global__ void __launch_bounds__(32 * kStripWarps, 10) classify_kernel(const St
                           [&](int tx, int ty) { a.wl[atomicAdd(&a.wl_n[0], 1u)] = ty * gridDim.x + tx; });
 }
 
+// The classification of a combining stage (a.tw_prev set, a.stage 2), which
+// reads no state: one thread per tile of the gx x gy tiles takes the tile as
+// wet where it or a neighbouring tile was wet in the stage before, or where it
+// lies on a side with an inflow segment (as classify_strip does), lists it,
+// and keeps its flags; the CTA's warps then write the zero state of its dry
+// tiles that do not hold it yet, one row of 32 cells at a time.  Few CTAs
+// with short lives: a CTA per strip made this launch latency-bound.
+constexpr int kFlagThreads = 256;
+template <typename T, int TY>
+__global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const StageArgs<T> a, const int gx, const int gy)
+{
+    __shared__ int s_list[kFlagThreads];  // the CTA's tiles to zero-write
+    __shared__ unsigned int s_n;
+    __shared__ double s_tg;
+    const int tid = threadIdx.x;
+    const int idx = blockIdx.x * kFlagThreads + tid;  // tile (idx % gx, idx / gx)
+    const bool mine = idx < gx * gy;
+    const unsigned char known = (a.zk && mine) ? a.zk[idx] : 0;
+    if (tid == 0) {
+        s_n = 0u;
+        s_tg = a.ctl->t + (a.rk3 == 2 ? 0.5 * a.ctl->dt : a.ctl->dt);
+    }
+    __syncthreads();
+    if (mine) {
+        const int bx = idx % gx, ty = idx / gx;
+        bool w = false;
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                const int xx = bx + dx, yy = ty + dy;
+                if (xx >= 0 && xx < gx && yy >= 0 && yy < gy) w |= a.tw_prev[yy * gx + xx] != 0;
+            }
+        const bool inf = on_inflow_side(a, bx, ty, gx, gy);
+        w |= inf;
+        if (w) a.wl[atomicAdd(&a.wl_n[0], 1u)] = idx;
+        a.tw_next[idx] = w;
+        if (!keep_tile(a, w, inf, idx, known)) s_list[atomicAdd(&s_n, 1u)] = idx;
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nrows = (int)s_n * TY;
+    const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    for (int r = warp; r < nrows; r += kFlagThreads / 32) {
+        const int t = s_list[r / TY];
+        const int i = (t % gx) * 32 + lane, j = (t / gx) * TY + r % TY;
+        if (i >= a.nx || j >= a.ny) continue;
+        const long long g = cell_index(i, j, a.pitch);
+        store6(a.Uout, a.plane, g, z);
+        if (a.rec) store6(a.rec, a.plane, g, z);  // the recording form: zero records too
+        if constexpr (sizeof(T) == 4) {
+            a.Rout[g] = 0.0f;
+            a.Rout[a.plane + g] = 0.0f;
+        }
+        write_ghosts(a.Uout, a.geo, a, i, j, z, s_tg);
+    }
+}
+
 // The stage on the listed tiles: a grid of resident CTAs takes the list's
 // entries in turn; the last CTA to finish empties the list and, after the
 // step's last stage, ends the step.

@@ -24,8 +24,9 @@ int launch_tile(const StageArgs<T> &a, cudaStream_t st)
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-// The stepping launches of the plain form: classify_kernel over every tile,
-// then stage_kernel_list on a grid of resident CTAs over the listed tiles.
+// The stepping launches of the plain form: classify_kernel over every tile
+// (classify_flags_kernel in a combining stage), then stage_kernel_list on a
+// grid of resident CTAs over the listed tiles.
 template <typename T, int TX, int TY, bool REC = false>
 int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
 {
@@ -46,7 +47,12 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     }
     static_assert(TX == 32, "classify_kernel works on 32-wide strips");
     const int gx = (a.nx + TX - 1) / TX;
-    classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
+    if (a.tw_prev && a.stage == 2) {  // a combining stage: from the flags of the stage before
+        const int gy = (a.ny + TY - 1) / TY;
+        classify_flags_kernel<T, TY><<<(gx * gy + kFlagThreads - 1) / kFlagThreads, kFlagThreads, 0, st>>>(a, gx, gy);
+    } else {
+        classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
+    }
     stage_kernel_list<T, TX, TY, REC><<<resident[dev], TX * TY, smem, st>>>(a, gx);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
