@@ -139,8 +139,11 @@ int moses_set_inflow(moses_sim *s, int side, int i0, int i1, int npts, const dou
 
 /* Advance nsteps CFL-limited steps (Sect. 2.2; Stage 2 of Sect. 3.1.2).
  * Tiles with no mass within the stencil's reach are not computed: their
- * stage result, the zero state, is written directly (wet/dry masking; the
- * result is the same).  t_out (may be NULL) receives the time after the last step.  Synchronises
+ * stage result, the zero state, is written directly, and not written again
+ * while the buffer holds it from an earlier step of these calls (wet/dry
+ * masking with per-tile known-zero flags; the result is the same).  Any other
+ * call that may write the state, or moses_set_tile, makes the next step write
+ * every dry tile once.  t_out (may be NULL) receives the time after the last step.  Synchronises
  * the stream once at the end.  Errors: ESTATE, ENONFINITE (a kernel saw a
  * non-finite value; the state is left as computed and every later step
  * reports it again until a new state is set), ECUDA. */
