@@ -659,11 +659,15 @@ def test_conserved_roundtrip_is_exact():
 
 def test_full_size_sampled_fp64():
     """One CFL step of the 4096 x 4096 spectral-DEM release in the launch
-    configuration the benchmark times; 3 windows of 48 x 48 recomputed by the
-    oracle on crops with a 12-cell margin (a step reads 4 cells around a
-    cell; the geometry 3 more)."""
+    configuration the benchmark times: the autotuned tile, after steps that
+    leave the known-zero tile flags live, so the dry tiles are skipped; 3
+    windows of 48 x 48 recomputed by the oracle on crops with a 12-cell
+    margin (a step reads 4 cells around a cell; the geometry 3 more), and a
+    window the oracle finds dry must be exactly zero."""
     cfg = W.large_release_config(n=4096, dx=10.0, seed=0)
     g = moses.from_config(cfg)
+    g.autotune()
+    g.step(3)
     dt, _ = g.next_dt()
     U0 = g.get_conserved()
     g.step(1)
@@ -678,7 +682,10 @@ def test_full_size_sampled_fp64():
         o.step_dt(dt)
         Uo = o.get_U()[:, m:m + w, m:m + w]
         Ug = U1[:, j0:j0 + w, i0:i0 + w]
-        assert rel_maxnorm(Ug, Uo) < TOL64 or np.abs(Uo).max() == 0.0
+        if np.abs(Uo).max() > 0.0:
+            assert rel_maxnorm(Ug, Uo) < TOL64
+        else:
+            assert np.all(Ug == 0.0)
 
 
 # ----------------------------------------------------------------------------
