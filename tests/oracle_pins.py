@@ -793,9 +793,53 @@ def pin_weno_rk3_budgets_and_rotation(L=None):
     assert err < 1e-12, f"WENO/RK3 rotation invariance broken: {err}"
 
 
+
+def _dilate(m, r):
+    """Cells within Chebyshev distance r of a True cell (clipped at the edge)."""
+    d = m.copy()
+    for s in range(1, r + 1):
+        d[:, s:] |= m[:, :-s]
+        d[:, :-s] |= m[:, s:]
+    e = d.copy()
+    for s in range(1, r + 1):
+        e[s:, :] |= d[:-s, :]
+        e[:-s, :] |= d[s:, :]
+    return e
+
+
+def pin_masking_reach(L=None):
+    """Wet/dry masking's premise (Sect. 2.2 scheme, dry rule R5): where no cell
+    within the scheme's reach holds mass, the result is exactly the zero
+    state, whatever momenta the massless cells carry.  The face between two
+    dry cells has zero states on both sides (minmod(0, x) = 0), so one stage
+    reaches 1 cell and a two-step modified Euler step 2; the results inside the
+    reach are not all zero."""
+    nx, ny = 41, 33
+    rng = np.random.default_rng(23)
+    dem = W.spectral_dem(nx, ny, 5.0, 2.2, 40.0, seed=23) + rng.random((ny, nx))
+    U = np.zeros((6, ny, nx))
+    for j, i in ((3, 4), (16, 20), (30, 38), (0, 12), (20, 0)):
+        U[0, j, i], U[3, j, i] = 0.9, 0.5
+        U[1, j, i], U[2, j, i], U[4, j, i], U[5, j, i] = 0.9 * 1.5, -0.9 * 0.7, 0.5 * 0.4, 0.5 * 1.1
+    mass = (U[0] != 0) | (U[3] != 0)
+    for c in (1, 2, 4, 5):  # momenta on some massless cells: the dry rule zeroes them
+        U[c] = np.where(~mass & (rng.random((ny, nx)) < 0.3), rng.normal(0.0, 1.0, (ny, nx)), U[c])
+    for bc in ((0, 0, 0, 0), (1, 1, 1, 1)):
+        s = _sim(dem, 5.0, 5.0, W.default_params(bc=bc), L)
+        s.set_U(U)
+        for r, out in ((1, s.stage(0.0, 0.02)), (2, None)):
+            if out is None:
+                s.set_U(U)
+                s.step_dt(0.02)
+                out = s.get_U()
+            far = ~_dilate(mass, r)
+            assert np.all(out[:, far] == 0.0), f"non-zero result beyond {r} cells of any mass (bc {bc})"
+            assert np.any(out[:, ~far] != 0.0)
+
+
 ALL_PINS = [pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
             pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag, pin_wave_speed,
             pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,
             pin_cu_upwind_dependence, pin_cu_conservation_and_ritter, pin_cu_rotation,
             pin_weno_linear_exact, pin_weno_rk3_dam_break, pin_weno_smooth_order, pin_rk3_drag_factor,
-            pin_weno_rk3_budgets_and_rotation]
+            pin_weno_rk3_budgets_and_rotation, pin_masking_reach]

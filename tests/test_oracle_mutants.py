@@ -115,6 +115,8 @@ MUTANTS = [
      "double dPxi = (s->Px[k] - s->Px[IS(s, i, j)]) / s->dx;"),
     ("mass flux uses v_eta on xi faces",
      "double vns = d == 0 ? xs : es;", "double vns = es;"),
+    ("dry momentum rule dropped from the stage output (R5)",
+     "                if (out[c] <= J * p->h_dry) {", "                if (0 && out[c] <= J * p->h_dry) {"),
 ]
 
 
