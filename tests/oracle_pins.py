@@ -420,6 +420,128 @@ def pin_inflow(L=None):
         assert abs(vol - b[f"bnd_in_{ph}"] - b[f"clamp_{ph}"]) < 1e-12 * vol, "volume budget does not close"
 
 
+
+def pin_inflow_every_side(L=None):
+    """Mode-II inflow (Sect. 3.1.2; R11) on each of the four sides, with cells
+    of different width and height and a solid fraction other than 1/2: the
+    ghost state splits the mixture as the hydrograph's phi^s, carries the unit
+    discharge Q/W (W the segment's length along its side), moves into the
+    domain at the model's celerity sqrt(g c A_nn h) (critical depth) and has
+    no tangential momentum."""
+    nx, ny, dx, dy = 30, 24, 5.0, 4.0
+    dem = W.spectral_dem(nx, ny, dx, 2.2, 30.0, seed=5)
+    t, Q, phi = [0.0, 100.0], [2.0, 6.0], [0.7, 0.7]
+    i0, i1 = 5, 12
+    for side in range(4):
+        s = _sim(dem, dx, dy, W.default_params(), L)
+        s.set_inflow(side, i0, i1, t, Q, phi)
+        q = None
+        for tt in (10.0, 60.0):
+            q = np.interp(tt, t, Q) / ((i1 - i0) * (dy if side < 2 else dx))
+            for k in (0, 1):  # the two ghost layers
+                a = i0 + 3
+                gi, gj = {0: (-1 - k, a), 1: (nx + k, a), 2: (a, -1 - k), 3: (a, ny + k)}[side]
+                u = s.inflow_state(0, gi, gj, tt)
+                gm = s.cell_geom(gi, gj)
+                Jh = u[0] + u[3]
+                assert abs(u[0] / Jh - 0.7) < 1e-14, f"inflow solid fraction (side {side})"
+                n_c, t_c = (1, 2) if side < 2 else (2, 1)
+                vn = (u[n_c] + u[n_c + 3]) / Jh * (1.0 if side in (0, 2) else -1.0)
+                assert vn > 0.0, f"inflow ghost moves out of the domain (side {side})"
+                assert abs(Jh * vn - q) < 1e-12 * q, f"inflow ghost does not carry Q/W (side {side})"
+                assert u[t_c] == 0.0 and u[t_c + 3] == 0.0, f"tangential inflow momentum (side {side})"
+                cel = math.sqrt(G * gm["c"] * (gm["A11"] if side < 2 else gm["A22"]) * Jh / gm["J"])
+                assert abs(vn - cel) < 1e-12 * cel, f"inflow ghost not at critical depth (side {side})"
+
+
+def pin_stage_times(L=None):
+    """The stages sample the boundary data at their own times, as the schemes
+    define them (Sect. 2.2): the two-step modified Euler at t and t + dt, the
+    three-stage SSP Runge-Kutta at t, t + dt and t + dt/2.  A hydrograph that
+    is non-zero only in a short window delivers mass within one step exactly
+    when a stage time falls inside the window."""
+    nx, ny = 20, 12
+    dem = W.flat_dem(nx, ny)
+    t0, dt = 10.0, 1.0
+
+    def volume_after(rk, centre):
+        p = W.default_params(rk=rk, bc=(0, 1, 0, 0))
+        s = _sim(dem, 5.0, 5.0, p, L)
+        w = 0.1 * dt
+        s.set_inflow(0, 4, 8, [0.0, centre - 2 * w, centre - w, centre + w, centre + 2 * w, 100.0],
+                     [0.0, 0.0, 3.0, 3.0, 0.0, 0.0], [0.6] * 6)
+        s.t = t0
+        s.step_dt(dt)
+        b = s.budget()
+        return b["vol_s"] + b["vol_f"]
+
+    for rk, inside, outside in ((2, (0.0, 1.0), (0.5, 0.25)), (3, (0.0, 1.0, 0.5), (0.25, 0.75))):
+        for f in inside:
+            assert volume_after(rk, t0 + f * dt) > 0.0, f"rk {rk}: no stage at t + {f} dt"
+        for f in outside:
+            assert volume_after(rk, t0 + f * dt) == 0.0, f"rk {rk}: a stage at t + {f} dt"
+
+
+def pin_time_step_cap(L=None):
+    """The time step is CFL min(dx, dy) / a_max, capped at dt_max; a domain
+    without motion or mass takes dt_max (Sect. 2.2).  A pure-fluid lake at
+    rest on a flat bed has a_max = sqrt(g h)."""
+    nx, ny, dx, dy, h = 12, 9, 5.0, 4.0, 0.5
+    for dt_max in (0.05, 1.0):
+        p = _pure_fluid(dt_max=dt_max, cfl=0.1)
+        s = _sim(W.flat_dem(nx, ny), dx, dy, p, L)
+        assert s.cfl_dt() == dt_max, "a dry domain does not take dt_max"
+        s.set_release(np.full((ny, nx), h), np.zeros((ny, nx)))
+        want = min(dt_max, 0.1 * min(dx, dy) / math.sqrt(G * h))
+        assert abs(s.cfl_dt() - want) < 1e-14 * want, f"time step {s.cfl_dt()} != {want}"
+
+
+def pin_positivity_clamp(L=None):
+    """A step far beyond the CFL limit drives a cell's depth below zero: the
+    depths stay >= 0 (R5), the added volume is counted, and the closed box's
+    volume budget closes with it: volume(t) - volume(0) = clamp volume > 0."""
+    nx, ny = 16, 12
+    p = _pure_fluid(bc=(0, 0, 0, 0))
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, p, L)
+    h = np.zeros((ny, nx))
+    h[6, 7] = 0.8
+    vx = np.zeros((ny, nx))
+    vx[6, 7] = 2.0
+    s.set_release(h, np.zeros((ny, nx)), vx_f=vx)
+    v0 = s.budget()["vol_f"]
+    a = 2.0 + math.sqrt(G * 0.8)
+    s.step_dt(2.0 * 5.0 / a)  # the cell's outflow is twice its volume
+    U = s.get_U()
+    assert U[0].min() >= 0.0 and U[3].min() >= 0.0, "negative depth left by the step"
+    b = s.budget()
+    assert b["clamp_f"] > 0.0 and b["clamp_cells"] >= 1, "no clamp counted"
+    assert abs(b["vol_f"] - v0 - b["clamp_f"]) < 1e-12 * v0, "volume budget does not close with the clamp"
+
+
+def pin_rotation_transmissive(L=None, steps=30):
+    """pin_rotation with every side transmissive and water reaching every
+    side from the first step: rotating the problem by 90 degrees commutes with
+    the step, so the zero-gradient ghosts (R4) are the same on all four
+    sides."""
+    n = 32
+    rng = np.random.default_rng(8)
+    dem = W.spectral_dem(n, n, 5.0, 2.2, 20.0, seed=8) + rng.random((n, n))
+    p = W.default_params(bc=(1, 1, 1, 1), cfl=0.2)
+    h = 0.2 + 0.3 * rng.random((n, n))
+    phi = rng.uniform(0.4, 0.7, (n, n))
+    a = _sim(dem, 5.0, 5.0, p, L)
+    a.set_release(h, phi)
+    b = _sim(_rot(dem), 5.0, 5.0, p, L)
+    b.set_release(_rot(h), _rot(phi))
+    for _ in range(steps):
+        dt = a.cfl_dt()
+        a.step_dt(dt)
+        b.step_dt(dt)
+    Ua, Ub = a.get_U(), b.get_U()
+    exp = np.stack([_rot(Ua[0]), -_rot(Ua[2]), _rot(Ua[1]), _rot(Ua[3]), -_rot(Ua[5]), _rot(Ua[4])])
+    err = np.abs(Ub - exp).max() / np.abs(Ua).max()
+    assert err < 1e-12, f"rotation invariance with transmissive sides broken: {err}"
+
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
 
@@ -837,9 +959,13 @@ def pin_masking_reach(L=None):
             assert np.any(out[:, ~far] != 0.0)
 
 
-ALL_PINS = [pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
-            pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag, pin_wave_speed,
-            pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,
-            pin_cu_upwind_dependence, pin_cu_conservation_and_ritter, pin_cu_rotation,
-            pin_weno_linear_exact, pin_weno_rk3_dam_break, pin_weno_smooth_order, pin_rk3_drag_factor,
-            pin_weno_rk3_budgets_and_rotation, pin_masking_reach]
+ALL_PINS = [
+    # cheap pins first: the planted-mistake harness stops at the first pin that fails
+    pin_masking_reach, pin_inflow_every_side, pin_stage_times, pin_time_step_cap, pin_positivity_clamp,
+    pin_rotation_transmissive,
+    pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
+    pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
+    pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,
+    pin_cu_upwind_dependence, pin_cu_conservation_and_ritter, pin_cu_rotation,
+    pin_weno_linear_exact, pin_weno_rk3_dam_break, pin_weno_smooth_order, pin_rk3_drag_factor,
+    pin_weno_rk3_budgets_and_rotation]

@@ -117,6 +117,26 @@ MUTANTS = [
      "double vns = d == 0 ? xs : es;", "double vns = es;"),
     ("dry momentum rule dropped from the stage output (R5)",
      "                if (out[c] <= J * p->h_dry) {", "                if (0 && out[c] <= J * p->h_dry) {"),
+    ("inflow solid fraction given to the fluid",
+     "u[0] = G->J * hc * phs;\n    u[3] = G->J * hc * (1.0 - phs);",
+     "u[0] = G->J * hc * (1.0 - phs);\n    u[3] = G->J * hc * phs;"),
+    ("inflow on the east and north sides pointing out of the domain",
+     "double sgn = (f->side == 0 || f->side == 2) ? 1.0 : -1.0;", "double sgn = 1.0;"),
+    ("inflow width from the wrong cell side",
+     "double W = (f->i1 - f->i0) * ((f->side < 2) ? s->dy : s->dx);",
+     "double W = (f->i1 - f->i0) * ((f->side < 2) ? s->dx : s->dy);"),
+    ("transmissive west ghost copies the second cell",
+     "int sw = s->p.bc[0] == 0 ? k : 0;", "int sw = s->p.bc[0] == 0 ? k : 1;"),
+    ("time step not capped at dt_max",
+     "if (dt > s->p.dt_max) dt = s->p.dt_max;", ""),
+    ("clamp volume counted with the wrong sign",
+     "s->st_clamp[ph] += -out[c] * s->dx * s->dy;", "s->st_clamp[ph] += out[c] * s->dx * s->dy;"),
+    ("positivity clamp removed",
+     "if (out[c] < 0.0) {", "if (0 && out[c] < 0.0) {"),
+    ("Heun second stage's boundary data at the start time",
+     "stage(s, s->W1, s->W2, t0 + dt, dt);", "stage(s, s->W1, s->W2, t0, dt);"),
+    ("RK3 third stage's boundary data at t + dt instead of t + dt/2",
+     "stage(s, s->W1, s->W2, t0 + 0.5 * dt, dt);", "stage(s, s->W1, s->W2, t0 + dt, dt);"),
 ]
 
 
