@@ -427,7 +427,8 @@ def pin_inflow_every_side(L=None):
     ghost state splits the mixture as the hydrograph's phi^s, carries the unit
     discharge Q/W (W the segment's length along its side), moves into the
     domain at the model's celerity sqrt(g c A_nn h) (critical depth) and has
-    no tangential momentum."""
+    no tangential momentum; over the first steps the volume budget closes:
+    volume = time-integrated boundary flux + clamp volume."""
     nx, ny, dx, dy = 30, 24, 5.0, 4.0
     dem = W.spectral_dem(nx, ny, dx, 2.2, 30.0, seed=5)
     t, Q, phi = [0.0, 100.0], [2.0, 6.0], [0.7, 0.7]
@@ -452,6 +453,13 @@ def pin_inflow_every_side(L=None):
                 assert u[t_c] == 0.0 and u[t_c + 3] == 0.0, f"tangential inflow momentum (side {side})"
                 cel = math.sqrt(G * gm["c"] * (gm["A11"] if side < 2 else gm["A22"]) * Jh / gm["J"])
                 assert abs(vn - cel) < 1e-12 * cel, f"inflow ghost not at critical depth (side {side})"
+        s.step(30)  # the other sides closed: the volume is what came in
+        b = s.budget()
+        for ph in ("s", "f"):
+            vol = b[f"vol_{ph}"]
+            assert vol > 0.0
+            assert abs(vol - b[f"bnd_in_{ph}"] - b[f"clamp_{ph}"]) < 1e-12 * vol, \
+                f"volume budget does not close (inflow on side {side})"
 
 
 def pin_stage_times(L=None):
@@ -541,6 +549,32 @@ def pin_rotation_transmissive(L=None, steps=30):
     exp = np.stack([_rot(Ua[0]), -_rot(Ua[2]), _rot(Ua[1]), _rot(Ua[3]), -_rot(Ua[5]), _rot(Ua[4])])
     err = np.abs(Ub - exp).max() / np.abs(Ua).max()
     assert err < 1e-12, f"rotation invariance with transmissive sides broken: {err}"
+
+
+def pin_rotation_rectangular(L=None, steps=30):
+    """Rotation by 90 degrees with cells of different width and height: the
+    rotated problem has the cell sides exchanged (dx' = dy, dy' = dx), and the
+    step commutes with the rotation, so every difference along X and along Y
+    (slopes, curvature, fluxes, pressure gradient) uses its own spacing."""
+    n, dx, dy = 30, 5.0, 3.5
+    rng = np.random.default_rng(12)
+    dem = W.spectral_dem(n, n, dx, 2.2, 25.0, seed=12) + rng.random((n, n))
+    p = W.default_params(bc=(1, 1, 1, 1), cfl=0.2, c_d=0.05)
+    h = 0.2 + 0.3 * rng.random((n, n))
+    phi = rng.uniform(0.4, 0.7, (n, n))
+    a = _sim(dem, dx, dy, p, L)
+    a.set_release(h, phi)
+    b = _sim(_rot(dem), dy, dx, p, L)
+    b.set_release(_rot(h), _rot(phi))
+    for _ in range(steps):
+        dt = a.cfl_dt()
+        assert abs(dt - b.cfl_dt()) <= 1e-14 * dt, "rotated run takes a different dt"
+        a.step_dt(dt)
+        b.step_dt(dt)
+    Ua, Ub = a.get_U(), b.get_U()
+    exp = np.stack([_rot(Ua[0]), -_rot(Ua[2]), _rot(Ua[1]), _rot(Ua[3]), -_rot(Ua[5]), _rot(Ua[4])])
+    err = np.abs(Ub - exp).max() / np.abs(Ua).max()
+    assert err < 1e-12, f"rotation invariance with rectangular cells broken: {err}"
 
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
@@ -962,7 +996,7 @@ def pin_masking_reach(L=None):
 ALL_PINS = [
     # cheap pins first: the planted-mistake harness stops at the first pin that fails
     pin_masking_reach, pin_inflow_every_side, pin_stage_times, pin_time_step_cap, pin_positivity_clamp,
-    pin_rotation_transmissive,
+    pin_rotation_transmissive, pin_rotation_rectangular,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

@@ -137,6 +137,22 @@ MUTANTS = [
      "stage(s, s->W1, s->W2, t0 + dt, dt);", "stage(s, s->W1, s->W2, t0, dt);"),
     ("RK3 third stage's boundary data at t + dt instead of t + dt/2",
      "stage(s, s->W1, s->W2, t0 + 0.5 * dt, dt);", "stage(s, s->W1, s->W2, t0 + dt, dt);"),
+    ("south / north boundary budget over dy",
+     "bin[0] += (s->Hy[0][IS(s, i, -1)] - s->Hy[0][IS(s, i, ny - 1)]) * s->dx;",
+     "bin[0] += (s->Hy[0][IS(s, i, -1)] - s->Hy[0][IS(s, i, ny - 1)]) * s->dy;"),
+    ("boundary budget misses the east side",
+     "bin[0] += (s->Hx[0][IS(s, -1, j)] - s->Hx[0][IS(s, nx - 1, j)]) * s->dy;",
+     "bin[0] += s->Hx[0][IS(s, -1, j)] * s->dy;"),
+    ("eta divergence over dx",
+     "double divy = (s->Hy[c][k] - s->Hy[c][IS(s, i, j - 1)]) / s->dy;",
+     "double divy = (s->Hy[c][k] - s->Hy[c][IS(s, i, j - 1)]) / s->dx;"),
+    ("dP/deta over dx",
+     "double dPeta = (s->Py[k] - s->Py[IS(s, i, j - 1)]) / s->dy;",
+     "double dPeta = (s->Py[k] - s->Py[IS(s, i, j - 1)]) / s->dx;"),
+    ("cell slope b_Y over 2 dx",
+     "double bY = (B(i, j + 1) - B(i, j - 1)) / (2.0 * dy);", "double bY = (B(i, j + 1) - B(i, j - 1)) / (2.0 * dx);"),
+    ("y-face slope over dx",
+     "double bY = (B(i, j + 1) - B(i, j)) / dy;", "double bY = (B(i, j + 1) - B(i, j)) / dx;"),
 ]
 
 
