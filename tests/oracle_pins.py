@@ -149,16 +149,20 @@ def pin_lake_flat(L=None):
     assert np.abs(U - U0).max() < 1e-14
 
 
-def _plane_equilibrium(L, phi_s, delta_b, zeta=20.0, fluid_pg_mode=0):
-    """Depth with dh/dX = sin(zeta)/cos^2(zeta): the leading-order model's own
-    hydrostatic state of a fluid on a plane (dh/ds = tan(zeta) along slope).
-    Returns the largest interior momentum after two steps and its scale."""
+def _plane_equilibrium(L, phi_s, delta_b, zeta=20.0, fluid_pg_mode=0, eps=1.0):
+    """Depth with dh/dX = sin(zeta)/(eps cos^2(zeta)): the leading-order
+    model's own hydrostatic state of a fluid on a plane (dh/ds = tan(zeta)
+    along slope for eps = 1).  At rest the fluid's X-momentum balance is
+    eps d(J h A_11 g c h / 2)/dX = J g c h |n_X|: the pressure flux carries
+    eps, the basal normal source does not, and A_11 = cos^2(zeta), |n_X| =
+    sin(zeta).  Returns the largest interior momentum after two steps and its
+    scale."""
     nx, ny, dx, dt = 64, 5, 2.0, 0.05
     dem = W.incline_dem(nx, ny, dx, dx, zeta)
     tz = math.radians(zeta)
     x = (np.arange(nx) + 0.5) * dx
-    h = np.broadcast_to(2.0 + x * math.sin(tz) / math.cos(tz) ** 2, (ny, nx)).copy()
-    p = W.default_params(delta_b_deg=delta_b, bc=(W.BC_TRANSMISSIVE,) * 4, fluid_pg_mode=fluid_pg_mode)
+    h = np.broadcast_to(2.0 + x * math.sin(tz) / (eps * math.cos(tz) ** 2), (ny, nx)).copy()
+    p = W.default_params(delta_b_deg=delta_b, bc=(W.BC_TRANSMISSIVE,) * 4, fluid_pg_mode=fluid_pg_mode, eps=eps)
     s = _sim(dem, dx, dx, p, L)
     s.set_release(h, np.full((ny, nx), phi_s))
     s.step_dt(dt)
@@ -172,6 +176,18 @@ def _plane_equilibrium(L, phi_s, delta_b, zeta=20.0, fluid_pg_mode=0):
 def pin_lake_plane(L=None):
     m, scale = _plane_equilibrium(L, phi_s=0.0, delta_b=25.0)
     assert m < 1e-12 * scale, f"fluid equilibrium on a plane moved: {m}"
+
+
+def pin_plane_equilibrium_eps(L=None):
+    """The plane equilibria of pin_lake_plane and pin_mixture_plane_rest with
+    the aspect ratio eps of the dimensionless equations (App. A) other than
+    1: the equilibrium slope of the depth scales as 1/eps, and a mixture stays
+    at rest only if the fluid's pressure-gradient source carries the same eps
+    as the pressure flux (Eq. SrcF_f_Topo)."""
+    for eps in (0.5, 2.0):
+        for phi_s, delta_b in ((0.0, 25.0), (0.6, 35.0)):
+            m, scale = _plane_equilibrium(L, phi_s=phi_s, delta_b=delta_b, eps=eps)
+            assert m < 1e-12 * scale, f"plane equilibrium with eps = {eps}, phi_s = {phi_s} moved: {m}"
 
 
 def pin_mixture_plane_rest(L=None):
@@ -575,6 +591,105 @@ def pin_rotation_rectangular(L=None, steps=30):
     exp = np.stack([_rot(Ua[0]), -_rot(Ua[2]), _rot(Ua[1]), _rot(Ua[3]), -_rot(Ua[5]), _rot(Ua[4])])
     err = np.abs(Ub - exp).max() / np.abs(Ua).max()
     assert err < 1e-12, f"rotation invariance with rectangular cells broken: {err}"
+
+
+def pin_rotation_viscous(L=None, steps=20):
+    """pin_rotation_rectangular with the viscous fluid term (Eq.
+    SrcF_vis_Topo) on a rough bed, where A is not the identity: the face
+    brackets of the X and Y derivatives must map onto each other under the
+    rotation, with their own spacings and metric entries."""
+    n, dx, dy = 26, 5.0, 3.5
+    rng = np.random.default_rng(21)
+    dem = W.spectral_dem(n, n, dx, 2.2, 25.0, seed=21) + 2.0 * rng.random((n, n))
+    p = W.default_params(bc=(1, 1, 1, 1), cfl=0.2, nu_f=2.0)
+    h = 0.3 + 0.3 * rng.random((n, n))
+    phi = rng.uniform(0.2, 0.5, (n, n))
+    vx, vy = rng.normal(0, 0.5, (n, n)), rng.normal(0, 0.5, (n, n))
+    a = _sim(dem, dx, dy, p, L)
+    a.set_release(h, phi, vx, vy, vy, vx)
+    b = _sim(_rot(dem), dy, dx, p, L)
+    # velocities rotate as (vX, vY) -> (-vY, vX)
+    b.set_release(_rot(h), _rot(phi), -_rot(vy), _rot(vx), -_rot(vx), _rot(vy))
+    for _ in range(steps):
+        dt = a.cfl_dt()
+        a.step_dt(dt)
+        b.step_dt(dt)
+    Ua, Ub = a.get_U(), b.get_U()
+    exp = np.stack([_rot(Ua[0]), -_rot(Ua[2]), _rot(Ua[1]), _rot(Ua[3]), -_rot(Ua[5]), _rot(Ua[4])])
+    err = np.abs(Ub - exp).max() / np.abs(Ua).max()
+    assert err < 1e-12, f"rotation invariance with the viscous term broken: {err}"
+
+
+def pin_max_speed_everywhere(L=None):
+    """a_max is the largest local speed over every cell (R7), including the
+    last column and the last row; a solid layer without fluid moving at v on a
+    flat bed has the speed v + sqrt(g (1 - alpha) h) (the solid celerity
+    carries the buoyancy factor 1 - rho_f / rho_s)."""
+    nx, ny = 9, 7
+    for (j, i) in ((3, nx - 1), (ny - 1, 4), (ny - 1, nx - 1)):
+        h = np.full((ny, nx), 0.5)
+        h[j, i] = 2.0
+        s = _sim(W.flat_dem(nx, ny), 5.0, 4.0, _pure_fluid(), L)
+        s.set_release(h, np.zeros((ny, nx)))
+        assert abs(s.max_speed() - math.sqrt(G * 2.0)) < 1e-14, f"a_max misses cell ({i}, {j})"
+    p = W.default_params()  # rho_f / rho_s = 1100 / 2700
+    al = p["rho_f"] / p["rho_s"]
+    one = np.ones((ny, nx))
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, p, L)
+    s.set_release(1.5 * one, one, 12.0 * one, 0 * one)
+    want = 12.0 + math.sqrt(G * (1.0 - al) * 1.5)
+    assert abs(s.max_speed() - want) < 1e-13 * want, f"solid speed {s.max_speed()} != {want}"
+
+
+def pin_step_composition(L=None):
+    """The two-step modified Euler (Sect. 2.2) and the three-stage SSP
+    Runge-Kutta are convex combinations of single stages S (U + dt L(U) with
+    friction, clamp and the dry rule), with the dry rule (R5) applied to every
+    combined state:
+    - Heun: U' = D((U + S(S(U, t), t + dt)) / 2);
+    - RK3: W = D(3/4 U + 1/4 S(S(U, t), t + dt)), then U' = D(U/3 + 2/3 S(W, t + dt/2)).
+    Here D zeroes a phase's momentum where its mass is <= J h_dry.  The
+    oracle's whole step is checked against this composition of its
+    single-stage call.  The state is thin films near h_dry, where the dry rule
+    of the combinations decides."""
+    nx, ny, dt, t0 = 24, 18, 0.05, 3.0
+    rng = np.random.default_rng(31)
+    dem = W.spectral_dem(nx, ny, 2.0, 2.2, 3.0, seed=31) + 0.2 * rng.random((ny, nx))
+    for rk in (2, 3):
+        p = W.default_params(rk=rk, bc=(0, 1, 1, 0), h_dry=0.01)
+        s = _sim(dem, 2.0, 2.0, p, L)
+        J = s.geometry()["J"]
+        U = np.zeros((6, ny, nx))
+        for ph in (0, 1):
+            m = J * p["h_dry"] * rng.uniform(0.0, 3.0, (ny, nx)) * (rng.random((ny, nx)) < 0.7)
+            U[3 * ph] = m
+            wet = m > J * p["h_dry"]
+            U[3 * ph + 1] = np.where(wet, m * rng.normal(0, 1.0, (ny, nx)), 0.0)
+            U[3 * ph + 2] = np.where(wet, m * rng.normal(0, 1.0, (ny, nx)), 0.0)
+
+        def D(V):
+            V = V.copy()
+            for ph in (0, 1):
+                dry = V[3 * ph] <= J * p["h_dry"]
+                V[3 * ph + 1][dry] = 0.0
+                V[3 * ph + 2][dry] = 0.0
+            return V
+
+        def S(V, tt):
+            s.set_U(V)
+            return s.stage(tt, dt)
+
+        if rk == 2:
+            want = D(0.5 * (U + S(S(U, t0), t0 + dt)))
+        else:
+            Wc = D(0.75 * U + 0.25 * S(S(U, t0), t0 + dt))
+            want = D(U / 3.0 + 2.0 * S(Wc, t0 + 0.5 * dt) / 3.0)
+        s.set_U(U)
+        s.t = t0
+        s.step_dt(dt)
+        got = s.get_U()
+        err = np.abs(got - want).max() / np.abs(want).max()
+        assert err < 1e-13, f"rk {rk}: the step is not the composition of its stages ({err})"
 
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
@@ -996,7 +1111,8 @@ def pin_masking_reach(L=None):
 ALL_PINS = [
     # cheap pins first: the planted-mistake harness stops at the first pin that fails
     pin_masking_reach, pin_inflow_every_side, pin_stage_times, pin_time_step_cap, pin_positivity_clamp,
-    pin_rotation_transmissive, pin_rotation_rectangular,
+    pin_rotation_transmissive, pin_rotation_rectangular, pin_rotation_viscous, pin_max_speed_everywhere,
+    pin_plane_equilibrium_eps, pin_step_composition,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

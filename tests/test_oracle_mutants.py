@@ -153,6 +153,24 @@ MUTANTS = [
      "double bY = (B(i, j + 1) - B(i, j - 1)) / (2.0 * dy);", "double bY = (B(i, j + 1) - B(i, j - 1)) / (2.0 * dx);"),
     ("y-face slope over dx",
      "double bY = (B(i, j + 1) - B(i, j)) / dy;", "double bY = (B(i, j + 1) - B(i, j)) / dx;"),
+    ("viscous X bracket without its A_21 term",
+     "brX[sd][0] = Jh * (A11 * dvx[0] + A21 * dvy[0]);", "brX[sd][0] = Jh * (A11 * dvx[0]);"),
+    ("viscous cross derivative on y-faces over dy",
+     "                           / (2.0 * s->dx);\n                }\n                double A11 = G->Ai[0][0], A12 = G->Ai[0][1], A21 = G->Ai[1][0], A22 = G->Ai[1][1];\n                brY",
+     "                           / (2.0 * s->dy);\n                }\n                double A11 = G->Ai[0][0], A12 = G->Ai[0][1], A21 = G->Ai[1][0], A22 = G->Ai[1][1];\n                brY"),
+    ("viscous x-face depth from the left cell only",
+     "double Jh = 0.5 * (Uin[0][IS(s, il, j)] + Uin[3][IS(s, il, j)] +\n                                   Uin[0][IS(s, ir, j)] + Uin[3][IS(s, ir, j)]);",
+     "double Jh = (Uin[0][IS(s, il, j)] + Uin[3][IS(s, il, j)]);"),
+    ("fluid pressure-gradient source without eps",
+     "double sf_f = p->eps * fpg * grad;", "double sf_f = fpg * grad;"),
+    ("RK3 dry rule after the first combination dropped",
+     "    dry_momentum(s, s->W1);\n", "\n"),
+    ("a_max skips the last column",
+     "for (int i = 0; i < s->nx; i++) m = fmax(m, cell_speed(s, i, j, U));",
+     "for (int i = 0; i < s->nx - 1; i++) m = fmax(m, cell_speed(s, i, j, U));"),
+    ("solid celerity without (1 - alpha)",
+     "double cs = sqrt(p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0);",
+     "double cs = sqrt(p->eps * p->g * c * Add * (h + hs) / 2.0);"),
 ]
 
 
