@@ -440,14 +440,15 @@ def pin_inflow(L=None):
 def pin_inflow_every_side(L=None):
     """Mode-II inflow (Sect. 3.1.2; R11) on each of the four sides, with cells
     of different width and height and a solid fraction other than 1/2: the
-    ghost state splits the mixture as the hydrograph's phi^s, carries the unit
+    ghost state splits the mixture as the hydrograph's phi^s at that time
+    (linear between its points), carries the unit
     discharge Q/W (W the segment's length along its side), moves into the
     domain at the model's celerity sqrt(g c A_nn h) (critical depth) and has
     no tangential momentum; over the first steps the volume budget closes:
     volume = time-integrated boundary flux + clamp volume."""
     nx, ny, dx, dy = 30, 24, 5.0, 4.0
     dem = W.spectral_dem(nx, ny, dx, 2.2, 30.0, seed=5)
-    t, Q, phi = [0.0, 100.0], [2.0, 6.0], [0.7, 0.7]
+    t, Q, phi = [0.0, 100.0], [2.0, 6.0], [0.7, 0.5]
     i0, i1 = 5, 12
     for side in range(4):
         s = _sim(dem, dx, dy, W.default_params(), L)
@@ -461,7 +462,7 @@ def pin_inflow_every_side(L=None):
                 u = s.inflow_state(0, gi, gj, tt)
                 gm = s.cell_geom(gi, gj)
                 Jh = u[0] + u[3]
-                assert abs(u[0] / Jh - 0.7) < 1e-14, f"inflow solid fraction (side {side})"
+                assert abs(u[0] / Jh - np.interp(tt, t, phi)) < 1e-14, f"inflow solid fraction (side {side})"
                 n_c, t_c = (1, 2) if side < 2 else (2, 1)
                 vn = (u[n_c] + u[n_c + 3]) / Jh * (1.0 if side in (0, 2) else -1.0)
                 assert vn > 0.0, f"inflow ghost moves out of the domain (side {side})"
@@ -691,14 +692,47 @@ def pin_step_composition(L=None):
         err = np.abs(got - want).max() / np.abs(want).max()
         assert err < 1e-13, f"rk {rk}: the step is not the composition of its stages ({err})"
 
+
+def pin_phase_symmetry(L=None, steps=20):
+    """With rho_f = 0 (alpha = 0) and delta_b = 0 the solid's equations are
+    the fluid's (App. A): the same pressure, celerity and basal pressure with
+    its centripetal term, no buoyancy, friction or drag, and no fluid basal
+    friction (k_f = 0).  So a pure solid and a pure fluid with the same depth
+    and velocity evolve identically, component for component, on a rough bed
+    fast enough that the layer lifts off in places (p_b clamped at 0)."""
+    n = 28
+    rng = np.random.default_rng(17)
+    c = (np.arange(n) + 0.5) * 1.0
+    X, Y = np.meshgrid(c, c)
+    # bumps of curvature ~0.6 / m: at 8 m/s, v^2 kappa > g c on the crests
+    dem = 0.5 * np.sin(2 * np.pi * X / 8.0) * np.sin(2 * np.pi * Y / 8.0) + 0.05 * rng.random((n, n))
+    p = W.default_params(rho_f=0.0, delta_b_deg=0.0, k_f=0.0, bc=(0, 1, 1, 0), cfl=0.2)
+    h = 0.3 + 0.4 * rng.random((n, n))
+    vx, vy = 8.0 + rng.normal(0, 1.0, (n, n)), rng.normal(0, 2.0, (n, n))
+    zero = np.zeros((n, n))
+    a = _sim(dem, 1.0, 1.0, p, L)
+    a.set_release(h, np.ones((n, n)), vx, vy, zero, zero)
+    b = _sim(dem, 1.0, 1.0, p, L)
+    b.set_release(h, zero, zero, zero, vx, vy)
+    for _ in range(steps):
+        dt = a.cfl_dt()
+        assert abs(dt - b.cfl_dt()) <= 1e-14 * dt, "the two phases take different time steps"
+        a.step_dt(dt)
+        b.step_dt(dt)
+    Ua, Ub = a.get_U(), b.get_U()
+    err = np.abs(Ua[0:3] - Ub[3:6]).max() / np.abs(Ua).max()
+    assert err < 1e-12, f"solid and fluid phases differ: {err}"
+    assert np.abs(Ua[3:6]).max() == 0.0 and np.abs(Ub[0:3]).max() == 0.0
+
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
 
 
 def pin_friction(L=None):
     """(a) A uniform pure-solid layer sliding on a 30 deg plane (delta_b = 20
-    deg): one stage changes J h^s v_X^s = h v_s by dt h g (sin z -+ cos z tan d)
-    (friction opposes the motion, downslope or upslope).  (b) At the bottom of
+    deg): one stage changes J h^s v_X^s = h v_s by dt h g (1 - alpha) (sin z
+    -+ cos z tan d) (friction opposes the motion, downslope or upslope; alpha
+    = rho_f / rho_s, 0 without fluid density).  (b) At the bottom of
     a concave parabolic bed of radius R the basal pressure is h (g + V^2/R)
     (centripetal term, Eq. Src_nd_Topo with kappa < 0), so one stage removes
     dt h (g + V^2/R) tan d of momentum.  (c) Over a convex crest with V^2/R > g
@@ -708,14 +742,19 @@ def pin_friction(L=None):
     nx, ny, dx = 8, 6, 2.0
     one = np.ones((ny, nx))
     p = _pure_solid(delta_b_deg=delta, bc=(W.BC_TRANSMISSIVE,) * 4)
-    for vs in (4.0, -4.0):
-        s = _sim(W.incline_dem(nx, ny, dx, dx, zeta), dx, dx, p, L)
-        s.set_release(h * one, one, vs * math.cos(tz) * one, 0 * one)
-        U0 = s.get_U()
-        out = s.stage(0.0, dt)
-        dq = G * h * (math.sin(tz) - math.copysign(1.0, vs) * math.cos(tz) * math.tan(td))
-        assert np.allclose(out[1], U0[1] + dt * dq, rtol=1e-12, atol=0), "slide on a plane: wrong acceleration"
-        assert np.abs(out[2]).max() == 0.0
+    # the solid's basal pressure carries the buoyancy factor 1 - alpha (rho_f / rho_s),
+    # which scales both the drive and the friction of a solid layer (pure solid, alpha = 0,
+    # and the default densities)
+    pb = W.default_params(delta_b_deg=delta, bc=(W.BC_TRANSMISSIVE,) * 4)
+    for pp, buoy in ((p, 1.0), (pb, 1.0 - pb["rho_f"] / pb["rho_s"])):
+        for vs in (4.0, -4.0):
+            s = _sim(W.incline_dem(nx, ny, dx, dx, zeta), dx, dx, pp, L)
+            s.set_release(h * one, one, vs * math.cos(tz) * one, 0 * one)
+            U0 = s.get_U()
+            out = s.stage(0.0, dt)
+            dq = buoy * G * h * (math.sin(tz) - math.copysign(1.0, vs) * math.cos(tz) * math.tan(td))
+            assert np.allclose(out[1], U0[1] + dt * dq, rtol=1e-12, atol=0), "slide on a plane: wrong acceleration"
+            assert np.abs(out[2]).max() == 0.0
     R, V = 10.0, 12.0
     nx = 21
     x = (np.arange(nx) + 0.5) * dx
@@ -1112,7 +1151,7 @@ ALL_PINS = [
     # cheap pins first: the planted-mistake harness stops at the first pin that fails
     pin_masking_reach, pin_inflow_every_side, pin_stage_times, pin_time_step_cap, pin_positivity_clamp,
     pin_rotation_transmissive, pin_rotation_rectangular, pin_rotation_viscous, pin_max_speed_everywhere,
-    pin_plane_equilibrium_eps, pin_step_composition,
+    pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

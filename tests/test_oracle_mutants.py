@@ -171,6 +171,14 @@ MUTANTS = [
     ("solid celerity without (1 - alpha)",
      "double cs = sqrt(p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0);",
      "double cs = sqrt(p->eps * p->g * c * Add * (h + hs) / 2.0);"),
+    ("solid basal pressure without (1 - alpha)",
+     "double pbs = hs * (p->g * c0 * (1.0 - al) - p->eps_chi * ks);", "double pbs = hs * (p->g * c0 - p->eps_chi * ks);"),
+    ("kappa of the fluid from the solid velocity",
+     "double kf = kappa_of(G, vf[0], vf[1]);", "double kf = kappa_of(G, vs[0], vs[1]);"),
+    ("fluid basal pressure not clamped at 0",
+     "if (pbf < 0.0) pbf = 0.0;", ""),
+    ("inflow solid fraction held at the hydrograph's first point",
+     "double phs = interp_series(f->t, f->phi, f->npts, tt);", "double phs = f->phi[0];"),
 ]
 
 
