@@ -724,6 +724,80 @@ def pin_phase_symmetry(L=None, steps=20):
     assert err < 1e-12, f"solid and fluid phases differ: {err}"
     assert np.abs(Ua[3:6]).max() == 0.0 and np.abs(Ub[0:3]).max() == 0.0
 
+
+def pin_inflow_mirror(L=None, steps=60):
+    """Mirror symmetry with inflow (Sect. 3.1.2, Mode II): an inflow on the
+    west side of a terrain and the same inflow on the east side of the
+    terrain mirrored in X give mirrored states, with the X momenta negated.
+    The same holds for south and north in Y.  Both ghost layers of every side
+    then carry the inflow state alike."""
+    nx, ny = 36, 28
+    rng = np.random.default_rng(19)
+    dem = W.spectral_dem(nx, ny, 4.0, 2.2, 12.0, seed=19) + rng.random((ny, nx))
+    p = W.default_params(bc=(0, 0, 0, 0), cfl=0.2)
+    t, Q, phi = [0.0, 30.0, 200.0], [4.0, 9.0, 0.0], [0.6, 0.5, 0.5]
+    for axis, (sa, sb), (i0, i1) in ((1, (0, 1), (9, 17)), (0, (2, 3), (12, 22))):
+        da = dem
+        db = dem[:, ::-1].copy() if axis == 1 else dem[::-1, :].copy()
+        a = _sim(da, 4.0, 4.0, p, L)
+        a.set_inflow(sa, i0, i1, t, Q, phi)
+        b = _sim(db, 4.0, 4.0, p, L)
+        b.set_inflow(sb, i0, i1, t, Q, phi)
+        for _ in range(steps):
+            dt = a.cfl_dt()
+            assert abs(dt - b.cfl_dt()) <= 1e-14 * dt, "mirrored run takes a different dt"
+            a.step_dt(dt)
+            b.step_dt(dt)
+        Ua, Ub = a.get_U(), b.get_U()
+        flip = (lambda f: f[:, ::-1]) if axis == 1 else (lambda f: f[::-1, :])
+        neg = (1, 4) if axis == 1 else (2, 5)
+        exp = np.stack([-flip(Ua[c]) if c in neg else flip(Ua[c]) for c in range(6)])
+        assert np.abs(Ua[0]).max() > 0.0
+        err = np.abs(Ub - exp).max() / np.abs(Ua).max()
+        assert err < 1e-12, f"inflow mirror symmetry broken (sides {sa}, {sb}): {err}"
+
+
+def pin_uniform_flow_viscous(L=None):
+    """A uniform mixture flow (both phases at one velocity, no basal
+    friction) on a flat bed with transmissive sides has no gradient anywhere,
+    corners included.  One stage with the viscous term on leaves every cell
+    unchanged: the fluxes are uniform, the basal normal has no horizontal
+    part, the drag vanishes and the viscous brackets vanish."""
+    nx, ny = 14, 11
+    one = np.ones((ny, nx))
+    p = W.default_params(bc=(1, 1, 1, 1), nu_f=1.5, delta_b_deg=0.0)  # no basal friction
+    s = _sim(W.flat_dem(nx, ny), 2.0, 3.0, p, L)
+    s.set_release(0.8 * one, 0.4 * one, 1.2 * one, -0.7 * one, 1.2 * one, -0.7 * one)
+    U0 = s.get_U()
+    out = s.stage(0.0, 0.05)
+    err = np.abs(out - U0).max() / np.abs(U0).max()
+    assert err < 1e-14, f"a uniform flow changed: {err}"
+
+
+def pin_thin_film_has_no_velocity(L=None):
+    """The dry rule (R5) is a threshold on the normal thickness h = U / J,
+    not on U: a phase thinner than h_dry carries no velocity, on a 45 degree
+    plane (J = sqrt 2) as on a flat bed.  A film thinner than h_dry
+    everywhere, with momenta set on it, moves its mass in one stage exactly
+    as the same film without momenta: every face state is thinner than
+    h_dry, so no face has a velocity."""
+    nx, ny = 16, 12
+    rng = np.random.default_rng(27)
+    p = W.default_params(bc=(1, 1, 1, 1), h_dry=0.01)
+    dem = W.incline_dem(nx, ny, 1.0, 1.0, 45.0)
+    # thinner than h_dry, but J h above h_dry: a threshold on U would give it a velocity
+    h = p["h_dry"] * rng.uniform(0.75, 0.98, (ny, nx))
+    for phi_s in (0.0, 1.0):  # a pure fluid and a pure solid film
+        outs = []
+        for v in (0.0, 1.0):
+            s = _sim(dem, 1.0, 1.0, p, L)
+            s.set_release(h, np.full((ny, nx), phi_s), v * rng.normal(0, 2.0, (ny, nx)),
+                          v * rng.normal(0, 2.0, (ny, nx)), v * rng.normal(0, 2.0, (ny, nx)),
+                          v * rng.normal(0, 2.0, (ny, nx)))
+            outs.append(s.stage(0.0, 0.01))
+        for c in (0, 3):
+            assert np.array_equal(outs[0][c], outs[1][c]), "momenta of a film thinner than h_dry moved mass"
+
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
 
@@ -1151,7 +1225,8 @@ ALL_PINS = [
     # cheap pins first: the planted-mistake harness stops at the first pin that fails
     pin_masking_reach, pin_inflow_every_side, pin_stage_times, pin_time_step_cap, pin_positivity_clamp,
     pin_rotation_transmissive, pin_rotation_rectangular, pin_rotation_viscous, pin_max_speed_everywhere,
-    pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry,
+    pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
+    pin_uniform_flow_viscous, pin_thin_film_has_no_velocity,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

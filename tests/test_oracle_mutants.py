@@ -179,6 +179,13 @@ MUTANTS = [
      "if (pbf < 0.0) pbf = 0.0;", ""),
     ("inflow solid fraction held at the hydrograph's first point",
      "double phs = interp_series(f->t, f->phi, f->npts, tt);", "double phs = f->phi[0];"),
+    ("west inflow fills its first ghost layer twice and not the second",
+     "case 0: gi = -1 - k; gj = a; break;", "case 0: gi = -1; gj = a; break;"),
+    ("corner ghosts left unfilled",
+     "for (int i = -GS; i < nx + GS; i++) {\n        for (int k = 0; k < GS; k++) {\n            int gs = -1 - k, gn = ny + k;",
+     "for (int i = 0; i < nx; i++) {\n        for (int k = 0; k < GS; k++) {\n            int gs = -1 - k, gn = ny + k;"),
+    ("dry threshold of the phase velocity on U instead of the normal thickness",
+     "if (Jh > J * hdry) {", "if (Jh > hdry) {"),
 ]
 
 
