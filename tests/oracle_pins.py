@@ -798,6 +798,37 @@ def pin_thin_film_has_no_velocity(L=None):
         for c in (0, 3):
             assert np.array_equal(outs[0][c], outs[1][c]), "momenta of a film thinner than h_dry moved mass"
 
+
+def pin_clamp_count(L=None):
+    """The clamp-cell count of a Heun step is the number of phase masses set
+    to 0 by the positivity clamp in each of its two stages.  A stage never
+    drives a massless cell negative: the central flux moves mass into a dry
+    cell, not out of it.  So a mass that is positive before a stage and
+    exactly 0 after it was clamped.  The two stages are taken one by one
+    through the single-stage call and their clamps counted, and the step's
+    count must be their sum."""
+    nx, ny = 16, 12
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, _pure_fluid(bc=(0, 0, 0, 0)), L)
+    h = np.zeros((ny, nx))
+    h[6, 7], h[3, 3] = 0.8, 0.5
+    vx = np.zeros((ny, nx))
+    vx[6, 7], vx[3, 3] = 2.0, -1.0
+    s.set_release(h, np.zeros((ny, nx)), vx_f=vx)
+    U = s.get_U()
+    dt = 2.0 * 5.0 / (2.0 + math.sqrt(G * 0.8))
+
+    def clamped(before, after):
+        return sum(int(np.count_nonzero((before[c] > 0.0) & (after[c] == 0.0))) for c in (0, 3))
+
+    W1 = s.stage(0.0, dt)
+    s.set_U(W1)
+    W2 = s.stage(dt, dt)
+    want = clamped(U, W1) + clamped(W1, W2)
+    assert clamped(U, W1) >= 1
+    s.set_U(U)
+    s.step_dt(dt)
+    assert s.budget()["clamp_cells"] == want, f"clamp count {s.budget()['clamp_cells']} != {want}"
+
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
 
@@ -1226,7 +1257,7 @@ ALL_PINS = [
     pin_masking_reach, pin_inflow_every_side, pin_stage_times, pin_time_step_cap, pin_positivity_clamp,
     pin_rotation_transmissive, pin_rotation_rectangular, pin_rotation_viscous, pin_max_speed_everywhere,
     pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
-    pin_uniform_flow_viscous, pin_thin_film_has_no_velocity,
+    pin_uniform_flow_viscous, pin_thin_film_has_no_velocity, pin_clamp_count,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

@@ -186,6 +186,8 @@ MUTANTS = [
      "for (int i = 0; i < nx; i++) {\n        for (int k = 0; k < GS; k++) {\n            int gs = -1 - k, gn = ny + k;"),
     ("dry threshold of the phase velocity on U instead of the normal thickness",
      "if (Jh > J * hdry) {", "if (Jh > hdry) {"),
+    ("Heun step drops the first stage's clamp-cell count",
+     "s->clamp_cells += n1 + s->st_clamp_cells;", "s->clamp_cells += s->st_clamp_cells;"),
 ]
 
 
