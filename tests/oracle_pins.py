@@ -441,7 +441,7 @@ def pin_inflow_every_side(L=None):
     """Mode-II inflow (Sect. 3.1.2; R11) on each of the four sides, with cells
     of different width and height and a solid fraction other than 1/2: the
     ghost state splits the mixture as the hydrograph's phi^s at that time
-    (linear between its points), carries the unit
+    (linear between its points; no inflow outside its time span), carries the unit
     discharge Q/W (W the segment's length along its side), moves into the
     domain at the model's celerity sqrt(g c A_nn h) (critical depth) and has
     no tangential momentum; over the first steps the volume budget closes:
@@ -470,6 +470,8 @@ def pin_inflow_every_side(L=None):
                 assert u[t_c] == 0.0 and u[t_c + 3] == 0.0, f"tangential inflow momentum (side {side})"
                 cel = math.sqrt(G * gm["c"] * (gm["A11"] if side < 2 else gm["A22"]) * Jh / gm["J"])
                 assert abs(vn - cel) < 1e-12 * cel, f"inflow ghost not at critical depth (side {side})"
+        # outside the hydrograph's time span there is no inflow, even where its last discharge is not 0
+        assert np.all(s.inflow_state(0, *{0: (-1, 8), 1: (nx, 8), 2: (8, -1), 3: (8, ny)}[side], 150.0) == 0.0)
         s.step(30)  # the other sides closed: the volume is what came in
         b = s.budget()
         for ph in ("s", "f"):
@@ -526,21 +528,22 @@ def pin_positivity_clamp(L=None):
     depths stay >= 0 (R5), the added volume is counted, and the closed box's
     volume budget closes with it: volume(t) - volume(0) = clamp volume > 0."""
     nx, ny = 16, 12
-    p = _pure_fluid(bc=(0, 0, 0, 0))
-    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, p, L)
-    h = np.zeros((ny, nx))
-    h[6, 7] = 0.8
-    vx = np.zeros((ny, nx))
-    vx[6, 7] = 2.0
-    s.set_release(h, np.zeros((ny, nx)), vx_f=vx)
-    v0 = s.budget()["vol_f"]
-    a = 2.0 + math.sqrt(G * 0.8)
-    s.step_dt(2.0 * 5.0 / a)  # the cell's outflow is twice its volume
-    U = s.get_U()
-    assert U[0].min() >= 0.0 and U[3].min() >= 0.0, "negative depth left by the step"
-    b = s.budget()
-    assert b["clamp_f"] > 0.0 and b["clamp_cells"] >= 1, "no clamp counted"
-    assert abs(b["vol_f"] - v0 - b["clamp_f"]) < 1e-12 * v0, "volume budget does not close with the clamp"
+    for rk in (2, 3):  # the RK3 step weighs its stages' clamp volumes 1/6, 1/6, 2/3
+        p = _pure_fluid(bc=(0, 0, 0, 0), rk=rk)
+        s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, p, L)
+        h = np.zeros((ny, nx))
+        h[6, 7] = 0.8
+        vx = np.zeros((ny, nx))
+        vx[6, 7] = 2.0
+        s.set_release(h, np.zeros((ny, nx)), vx_f=vx)
+        v0 = s.budget()["vol_f"]
+        a = 2.0 + math.sqrt(G * 0.8)
+        s.step_dt(2.0 * 5.0 / a)  # the cell's outflow is twice its volume
+        U = s.get_U()
+        assert U[0].min() >= 0.0 and U[3].min() >= 0.0, "negative depth left by the step"
+        b = s.budget()
+        assert b["clamp_f"] > 0.0 and b["clamp_cells"] >= 1, "no clamp counted"
+        assert abs(b["vol_f"] - v0 - b["clamp_f"]) < 1e-12 * v0, f"rk {rk}: volume budget does not close with the clamp"
 
 
 def pin_rotation_transmissive(L=None, steps=30):
@@ -828,6 +831,63 @@ def pin_clamp_count(L=None):
     s.set_U(U)
     s.step_dt(dt)
     assert s.budget()["clamp_cells"] == want, f"clamp count {s.budget()['clamp_cells']} != {want}"
+
+
+def pin_viscous_only_where_the_fluid_is_wet(L=None):
+    """The viscous term (Eq. SrcF_vis_Topo) is a force on the fluid phase
+    where it moves; a cell whose fluid is thinner than h_dry has no fluid
+    velocity (R5) and gets no viscous force, even where a neighbour's sheared
+    fluid gives it velocity gradients and its fluid becomes wet within the
+    stage.  One stage with and without viscosity gives the same fluid
+    momenta on every cell whose fluid was thin."""
+    n = 24
+    p0 = W.default_params(bc=(1, 1, 1, 1), h_dry=0.01, delta_b_deg=0.0)
+    c = (np.arange(n) + 0.5) * 1.0
+    X, Y = np.meshgrid(c, c)
+    wet = X < n / 2
+    hs = np.full((n, n), 0.5)
+    hf = np.where(wet, 0.3, 0.5 * p0["h_dry"])
+    h = hs + hf
+    phi = hs / h
+    vyf = np.where(wet, 1.5 * np.sin(2 * np.pi * X / 8.0), 0.0)
+    zero = np.zeros((n, n))
+    outs = []
+    for nu in (0.0, 2.0):
+        s = _sim(W.flat_dem(n, n), 1.0, 1.0, dict(p0, nu_f=nu), L)
+        s.set_release(h, phi, zero, zero, zero, vyf)
+        outs.append(s.stage(0.0, 0.02))
+    thin = ~wet
+    assert np.any(outs[0][3][thin] > s.geometry()["J"][thin] * p0["h_dry"]), "no thin cell became wet"
+    for comp in (4, 5):
+        assert np.array_equal(outs[0][comp][thin], outs[1][comp][thin]), "viscous force on a cell without fluid velocity"
+    assert not np.array_equal(outs[0][5][wet], outs[1][5][wet])
+
+
+def pin_thin_cell_has_no_phase_fractions(L=None):
+    """A cell thinner than h_dry in total has no phase fractions (R5), so no
+    pressure-gradient source acts on it, whichever fraction the fluid's source
+    carries (phi^s by reading R1, or phi^f as printed in Eq. SrcF_f_Topo).
+    Next to a deep mixture, where grad P is large and the thin cells become
+    wet within the stage, one stage in the two forms gives the same fluid
+    momenta on every cell that was thin."""
+    n = 20
+    p0 = W.default_params(bc=(1, 1, 1, 1), h_dry=0.01, delta_b_deg=0.0)
+    c = (np.arange(n) + 0.5) * 1.0
+    X, _ = np.meshgrid(c, c)
+    deep = X < n / 2
+    h = np.where(deep, 1.0 + 0.05 * X, 0.6 * p0["h_dry"])
+    phi = np.full((n, n), 0.6)
+    outs = []
+    for mode in (0, 1):
+        s = _sim(W.flat_dem(n, n), 1.0, 1.0, dict(p0, fluid_pg_mode=mode), L)
+        s.set_release(h, phi)
+        outs.append(s.stage(0.0, 0.02))
+    thin = ~deep
+    J = s.geometry()["J"]
+    assert np.any(outs[0][3][thin] > J[thin] * p0["h_dry"]), "no thin cell became wet"
+    for comp in (4, 5):
+        assert np.array_equal(outs[0][comp][thin], outs[1][comp][thin]), "pressure-gradient source on a thin cell"
+    assert not np.array_equal(outs[0][4][deep], outs[1][4][deep])
 
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
@@ -1258,6 +1318,7 @@ ALL_PINS = [
     pin_rotation_transmissive, pin_rotation_rectangular, pin_rotation_viscous, pin_max_speed_everywhere,
     pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
     pin_uniform_flow_viscous, pin_thin_film_has_no_velocity, pin_clamp_count,
+    pin_viscous_only_where_the_fluid_is_wet, pin_thin_cell_has_no_phase_fractions,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

@@ -188,6 +188,15 @@ MUTANTS = [
      "if (Jh > J * hdry) {", "if (Jh > hdry) {"),
     ("Heun step drops the first stage's clamp-cell count",
      "s->clamp_cells += n1 + s->st_clamp_cells;", "s->clamp_cells += s->st_clamp_cells;"),
+    ("RK3 clamp volume with equal stage weights",
+     "s->clamp_vol[ph] += c[0][ph] / 6.0 + c[1][ph] / 6.0 + 2.0 * c[2][ph] / 3.0;",
+     "s->clamp_vol[ph] += (c[0][ph] + c[1][ph] + c[2][ph]) / 3.0;"),
+    ("hydrograph held at its last value after its end",
+     "if (n <= 0 || tt < t[0] || tt > t[n - 1]) return 0.0;", "if (n <= 0 || tt < t[0]) return 0.0;"),
+    ("viscous term on cells whose fluid is thinner than h_dry",
+     "if (!(h > p->h_dry) || !(Uin[3][k] > J * p->h_dry)) continue;", "if (!(h > p->h_dry)) continue;"),
+    ("phase fractions on cells thinner than h_dry",
+     "if (h > p->h_dry) {\n                phs = hs / h;", "if (h > 0.0) {\n                phs = hs / h;"),
 ]
 
 
