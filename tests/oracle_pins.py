@@ -4,8 +4,14 @@ Each ``pin_*`` function builds small seeded inputs, runs the oracle (the default
 build, or a build with a planted mistake passed as ``L``) and raises
 ``AssertionError`` when the oracle departs from a closed form, an invariant, a
 textbook special case or an exact identity.  None of them retypes an oracle
-formula: they compare it with analytic solutions (Ritter, Savage-Hutter),
-conservation and symmetry laws, and differential-geometric identities.
+formula.  They compare the oracle with:
+- analytic solutions (Ritter, Savage-Hutter);
+- conservation laws and symmetries (rotation, mirror, the solid and fluid
+  phases);
+- differential-geometric identities;
+- the schemes' own definitions of a step from its stages.
+Each is chosen so that a plausible mistake in the part it covers fails it:
+``tests/test_oracle_mutants.py`` plants such mistakes.
 
 Citations are to arXiv:2104.06784 (App. A equations by label, Sect. 2.1-2.2).
 """
