@@ -895,6 +895,24 @@ def pin_thin_cell_has_no_phase_fractions(L=None):
         assert np.array_equal(outs[0][comp][thin], outs[1][comp][thin]), "pressure-gradient source on a thin cell"
     assert not np.array_equal(outs[0][4][deep], outs[1][4][deep])
 
+
+def pin_budget_sums(L=None):
+    """The budgets' volumes and momenta are the sums of the six conserved
+    fields times the cell area (a10: sum U dx dy per component), each field
+    to its own entry, after a few steps of a flow on rectangular cells."""
+    nx, ny, dx, dy = 21, 17, 4.0, 3.0
+    rng = np.random.default_rng(41)
+    dem = W.spectral_dem(nx, ny, dx, 2.2, 10.0, seed=41)
+    s = _sim(dem, dx, dy, W.default_params(bc=(0, 1, 1, 0)), L)
+    s.set_release(0.3 + rng.random((ny, nx)), rng.uniform(0.3, 0.7, (ny, nx)), rng.normal(0, 1, (ny, nx)),
+                  rng.normal(0, 1, (ny, nx)), rng.normal(0, 1, (ny, nx)), rng.normal(0, 1, (ny, nx)))
+    s.step(5)
+    U, b = s.get_U(), s.budget()
+    for key, c in (("vol_s", 0), ("mom_xs", 1), ("mom_ys", 2), ("vol_f", 3), ("mom_xf", 4), ("mom_yf", 5)):
+        want = math.fsum(U[c].ravel()) * dx * dy
+        assert abs(b[key] - want) <= 1e-12 * max(abs(want), math.fsum(np.abs(U[c]).ravel()) * dx * dy), \
+            f"budget {key} is not the sum of field {c}"
+
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
 
@@ -1324,7 +1342,7 @@ ALL_PINS = [
     pin_rotation_transmissive, pin_rotation_rectangular, pin_rotation_viscous, pin_max_speed_everywhere,
     pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
     pin_uniform_flow_viscous, pin_thin_film_has_no_velocity, pin_clamp_count,
-    pin_viscous_only_where_the_fluid_is_wet, pin_thin_cell_has_no_phase_fractions,
+    pin_viscous_only_where_the_fluid_is_wet, pin_thin_cell_has_no_phase_fractions, pin_budget_sums,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

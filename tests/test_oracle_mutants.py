@@ -197,6 +197,8 @@ MUTANTS = [
      "if (!(h > p->h_dry) || !(Uin[3][k] > J * p->h_dry)) continue;", "if (!(h > p->h_dry)) continue;"),
     ("phase fractions on cells thinner than h_dry",
      "if (h > p->h_dry) {\n                phs = hs / h;", "if (h > 0.0) {\n                phs = hs / h;"),
+    ("budget's solid Y momentum from the fluid field",
+     "out[3] = sum[2] * a;", "out[3] = sum[5] * a;"),
 ]
 
 
