@@ -917,33 +917,44 @@ def pin_budget_sums(L=None):
 # Coulomb friction and the curvature term in the basal pressure
 
 
-def pin_friction(L=None):
-    """(a) A uniform pure-solid layer sliding on a 30 deg plane (delta_b = 20
-    deg): one stage changes J h^s v_X^s = h v_s by dt h g (1 - alpha) (sin z
-    -+ cos z tan d) (friction opposes the motion, downslope or upslope; alpha
-    = rho_f / rho_s, 0 without fluid density).  (b) At the bottom of
-    a concave parabolic bed of radius R the basal pressure is h (g + V^2/R)
-    (centripetal term, Eq. Src_nd_Topo with kappa < 0), so one stage removes
-    dt h (g + V^2/R) tan d of momentum.  (c) Over a convex crest with V^2/R > g
-    the layer lifts off: p_b is clamped at 0 and no friction acts."""
+def _slide_on_plane(p, buoy, L):
+    """One stage of a uniform solid layer sliding on a 30 deg plane (delta_b =
+    20 deg) up and down the slope: the X momentum changes by
+    dt h g buoy (sin z -+ cos z tan d)."""
     zeta, delta, h, dt = 30.0, 20.0, 2.0, 0.05
     tz, td = math.radians(zeta), math.radians(delta)
     nx, ny, dx = 8, 6, 2.0
     one = np.ones((ny, nx))
+    for vs in (4.0, -4.0):
+        s = _sim(W.incline_dem(nx, ny, dx, dx, zeta), dx, dx, p, L)
+        s.set_release(h * one, one, vs * math.cos(tz) * one, 0 * one)
+        U0 = s.get_U()
+        out = s.stage(0.0, dt)
+        dq = buoy * G * h * (math.sin(tz) - math.copysign(1.0, vs) * math.cos(tz) * math.tan(td))
+        assert np.allclose(out[1], U0[1] + dt * dq, rtol=1e-12, atol=0), "slide on a plane: wrong acceleration"
+        assert np.abs(out[2]).max() == 0.0
+
+
+def pin_friction_buoyant(L=None):
+    """The slide of pin_friction with the default densities: the solid's
+    basal pressure carries the buoyancy factor 1 - alpha (alpha = rho_f /
+    rho_s, Eq. Src_nd_Topo), which scales the drive and the friction alike."""
+    p = W.default_params(delta_b_deg=20.0, bc=(W.BC_TRANSMISSIVE,) * 4)
+    _slide_on_plane(p, 1.0 - p["rho_f"] / p["rho_s"], L)
+
+
+def pin_friction(L=None):
+    """(a) A uniform pure-solid layer sliding on a 30 deg plane (delta_b = 20
+    deg): one stage changes J h^s v_X^s = h v_s by dt h g (sin z -+ cos z tan d)
+    (friction opposes the motion, downslope or upslope).  (b) At the bottom of
+    a concave parabolic bed of radius R the basal pressure is h (g + V^2/R)
+    (centripetal term, Eq. Src_nd_Topo with kappa < 0), so one stage removes
+    dt h (g + V^2/R) tan d of momentum.  (c) Over a convex crest with V^2/R > g
+    the layer lifts off: p_b is clamped at 0 and no friction acts."""
+    delta, h, dt, dx = 20.0, 2.0, 0.05, 2.0
+    td = math.radians(delta)
     p = _pure_solid(delta_b_deg=delta, bc=(W.BC_TRANSMISSIVE,) * 4)
-    # the solid's basal pressure carries the buoyancy factor 1 - alpha (rho_f / rho_s),
-    # which scales both the drive and the friction of a solid layer (pure solid, alpha = 0,
-    # and the default densities)
-    pb = W.default_params(delta_b_deg=delta, bc=(W.BC_TRANSMISSIVE,) * 4)
-    for pp, buoy in ((p, 1.0), (pb, 1.0 - pb["rho_f"] / pb["rho_s"])):
-        for vs in (4.0, -4.0):
-            s = _sim(W.incline_dem(nx, ny, dx, dx, zeta), dx, dx, pp, L)
-            s.set_release(h * one, one, vs * math.cos(tz) * one, 0 * one)
-            U0 = s.get_U()
-            out = s.stage(0.0, dt)
-            dq = buoy * G * h * (math.sin(tz) - math.copysign(1.0, vs) * math.cos(tz) * math.tan(td))
-            assert np.allclose(out[1], U0[1] + dt * dq, rtol=1e-12, atol=0), "slide on a plane: wrong acceleration"
-            assert np.abs(out[2]).max() == 0.0
+    _slide_on_plane(p, 1.0, L)
     R, V = 10.0, 12.0
     nx = 21
     x = (np.arange(nx) + 0.5) * dx
@@ -1343,6 +1354,7 @@ ALL_PINS = [
     pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
     pin_uniform_flow_viscous, pin_thin_film_has_no_velocity, pin_clamp_count,
     pin_viscous_only_where_the_fluid_is_wet, pin_thin_cell_has_no_phase_fractions, pin_budget_sums,
+    pin_friction_buoyant,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,
