@@ -913,6 +913,25 @@ def pin_budget_sums(L=None):
         assert abs(b[key] - want) <= 1e-12 * max(abs(want), math.fsum(np.abs(U[c]).ravel()) * dx * dy), \
             f"budget {key} is not the sum of field {c}"
 
+
+def pin_step_clock(L=None):
+    """A CFL step takes dt = CFL min(dx, dy) / a_max of the state it starts
+    from (Sect. 2.2): for a pure-fluid lake at rest on a flat bed that is CFL
+    min(dx, dy) / sqrt(g h).  The clock advances by the steps' dts and the
+    step count by one per step, for both time integrators."""
+    nx, ny, dx, dy, h = 10, 8, 5.0, 4.0, 0.5
+    for rk in (2, 3):
+        s = _sim(W.flat_dem(nx, ny), dx, dy, _pure_fluid(cfl=0.1, rk=rk), L)
+        s.set_release(np.full((ny, nx), h), np.zeros((ny, nx)))
+        dts = s.step(1)
+        want = 0.1 * min(dx, dy) / math.sqrt(G * h)
+        assert abs(dts[0] - want) < 1e-14 * want and abs(s.last_dt - want) < 1e-14 * want, \
+            f"rk {rk}: the step's dt {dts[0]} != {want}"
+        dts = np.concatenate([dts, s.step(6)])
+        b = s.budget()
+        assert b["steps"] == 7, f"rk {rk}: step count {b['steps']}"
+        assert abs(b["t"] - math.fsum(dts)) < 1e-14 * b["t"], f"rk {rk}: clock {b['t']} != sum of dts"
+
 # ----------------------------------------------------------------------------
 # Coulomb friction and the curvature term in the basal pressure
 
@@ -1354,7 +1373,7 @@ ALL_PINS = [
     pin_plane_equilibrium_eps, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
     pin_uniform_flow_viscous, pin_thin_film_has_no_velocity, pin_clamp_count,
     pin_viscous_only_where_the_fluid_is_wet, pin_thin_cell_has_no_phase_fractions, pin_budget_sums,
-    pin_friction_buoyant,
+    pin_friction_buoyant, pin_step_clock,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

@@ -199,6 +199,10 @@ MUTANTS = [
      "if (h > p->h_dry) {\n                phs = hs / h;", "if (h > 0.0) {\n                phs = hs / h;"),
     ("budget's solid Y momentum from the fluid field",
      "out[3] = sum[2] * a;", "out[3] = sum[5] * a;"),
+    ("Heun step not counted",
+     "    s->last_dt = dt;\n    s->nsteps++;\n}\n\n/* dry rule", "    s->last_dt = dt;\n}\n\n/* dry rule"),
+    ("CFL step from twice the wave speed",
+     "double dt = cfl_dt(s, max_speed(s, s->U));", "double dt = cfl_dt(s, 2.0 * max_speed(s, s->U));"),
 ]
 
 
