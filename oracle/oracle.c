@@ -21,6 +21,11 @@
  *   Sect. 3.1.2        Mode-I release, Mode-II boundary inflow,
  *                      non-reflecting boundaries
  *
+ * Built plainly (no -fopenmp) for the tests; the OpenMP pragmas on the loops
+ * over rows then do nothing.  A second build with -fopenmp, used only to time
+ * the multi-core CPU baseline, runs the same rows on every host core (the
+ * clamp sums may then add in another order; nothing else changes).
+ *
  * Readings where the paper is silent, ambiguous or garbled (same numbering in
  * the library and the tests):
  *   R1  fluid pressure-gradient source uses phi^s (the reaction of the solid
@@ -44,6 +49,14 @@
  *       stages; dt = CFL min(dx,dy)/a_max, a_max over cell centres.
  *   R9  SI units: g multiplies c = n_Z in every pressure; eps = eps^chi = 1
  *       by default; c_D in 1/s, nu_f in m^2/s, k_f in 1/s.
+ *   R10 internal friction (k_mode = 1): the Savage-Hutter earth-pressure
+ *       coefficient multiplies the solid pressure in the flux of each
+ *       direction and the solid wave speed.  Per cell and direction:
+ *       K_pass where the cell and its two neighbours along that axis carry
+ *       solid (U1 > J h_dry) and the central difference of the solid
+ *       velocity along the axis is negative (compression), K_act otherwise;
+ *       each side of a face takes its own cell's coefficient.  The CFL wave
+ *       speed takes K_pass (the larger).  k_mode = 0: K = 1, the paper's.
  *   R11 inflow ghost state at critical depth for the unit discharge Q/W.
  *   R13 (div_xi + div_eta) summed before it is added to U.
  */
@@ -324,12 +337,45 @@ static double kappa_of(const orc_geom *G, double vX, double vY)
     return k;
 }
 
+/* Savage-Hutter earth-pressure coefficients (R10):
+   K_act/pass = 2 sec^2(phi_int) (1 -/+ sqrt(1 - cos^2(phi_int) sec^2(delta_b))) - 1,
+   defined for delta_b <= phi_int; both 1 when k_mode = 0 (App. A: the solid
+   pressure N^s is the basal one)                                           */
+static void earth_pressure(const orc_params *p, double *Ka, double *Kp)
+{
+    if (p->k_mode != 1) {
+        *Ka = *Kp = 1.0;
+        return;
+    }
+    double ph = p->phi_int_deg * M_PI / 180.0, de = p->delta_b_deg * M_PI / 180.0;
+    double cp2 = cos(ph) * cos(ph), cd2 = cos(de) * cos(de);
+    double r = sqrt(1.0 - cp2 / cd2);
+    *Ka = 2.0 / cp2 * (1.0 - r) - 1.0;
+    *Kp = 2.0 / cp2 * (1.0 + r) - 1.0;
+}
+
+/* K of cell k for direction d (0: xi, 1: eta), its neighbours along that
+   axis km (behind) and kp (ahead): K_pass where all three carry solid
+   (U1 > J h_dry) and the solid velocity along the axis (v_xi = v_X,
+   v_eta = v_Y, R2) is smaller ahead than behind, else K_act */
+static double cell_earth_pressure(const orc_sim *s, double *const U[6], long km, long k, long kp, int d,
+                                  double Ka, double Kp)
+{
+    if (s->p.k_mode != 1) return 1.0;
+    double hd = s->p.h_dry;
+    if (!(U[0][km] > s->gc[km].J * hd) || !(U[0][k] > s->gc[k].J * hd) || !(U[0][kp] > s->gc[kp].J * hd))
+        return Ka;
+    double vm = U[1 + d][km] / U[0][km], vp = U[1 + d][kp] / U[0][kp];
+    return (vp - vm < 0.0) ? Kp : Ka;
+}
+
 /* ------------------------------------------------------------------------ */
 /* physical flux through a face of direction d (0 = xi, 1 = eta) of one
    reconstructed state u (Eqs. FluxEqSxi..FluxEqFeta), the per-phase local
-   wave speeds (R7) and P = J_b h pbar^f                                     */
+   wave speeds (R7) and P = J_b h pbar^f; K multiplies the solid pressure
+   (R10; 1 in the paper's form)                                             */
 
-static void face_flux(const orc_params *p, const orc_geom *G, int d, const double u[6], double F[6],
+static void face_flux(const orc_params *p, const orc_geom *G, int d, double K, const double u[6], double F[6],
                       double *as, double *af, double *P, double spd[4])
 {
     double J = G->J, c = G->c, al = alpha_rho(p);
@@ -345,13 +391,13 @@ static void face_flux(const orc_params *p, const orc_geom *G, int d, const doubl
     double Ns = p->g * c * (1.0 - al) * hs / 2.0; /* depth-averaged solid pressure */
     double pf = p->g * c * h / 2.0;               /* mean fluid pressure            */
     F[0] = J * hs * vns;
-    F[1] = J * hs * vXs * vns + p->eps * J * h * Ad1 * Ns;
-    F[2] = J * hs * vYs * vns + p->eps * J * h * Ad2 * Ns;
+    F[1] = J * hs * vXs * vns + p->eps * J * h * Ad1 * (K * Ns);
+    F[2] = J * hs * vYs * vns + p->eps * J * h * Ad2 * (K * Ns);
     F[3] = J * hf * vnf;
     F[4] = J * hf * vXf * vnf + p->eps * J * h * Ad1 * pf;
     F[5] = J * hf * vYf * vnf + p->eps * J * h * Ad2 * pf;
     double Add = G->Ai[d][d];
-    double cs = sqrt(p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0);
+    double cs = sqrt(K * (p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0));
     double cf = sqrt(p->eps * p->g * c * Add * h);
     *as = fabs(vns) + cs;
     *af = fabs(vnf) + cf;
@@ -378,15 +424,17 @@ static double numerical_flux(int scheme, double Fm, double Fp, double um, double
     return (ap * Fm - am * Fp) / w + ap * am / w * (up - um);
 }
 
-/* largest cell-centre wave speed over both phases and both directions (R7) */
+/* largest cell-centre wave speed over both phases and both directions (R7;
+   the solid's with the larger earth-pressure coefficient K_pass, R10)     */
 static double cell_speed(const orc_sim *s, int i, int j, double *const U[6])
 {
-    double u[6], F[6], a[4], P;
+    double u[6], F[6], a[4], P, Ka, Kp;
     long k = IS(s, i, j);
     for (int c = 0; c < 6; c++) u[c] = U[c][k];
     const orc_geom *G = &s->gc[k];
-    face_flux(&s->p, G, 0, u, F, &a[0], &a[1], &P, NULL);
-    face_flux(&s->p, G, 1, u, F, &a[2], &a[3], &P, NULL);
+    earth_pressure(&s->p, &Ka, &Kp);
+    face_flux(&s->p, G, 0, Kp, u, F, &a[0], &a[1], &P, NULL);
+    face_flux(&s->p, G, 1, Kp, u, F, &a[2], &a[3], &P, NULL);
     double m = 0.0;
     for (int c = 0; c < 4; c++) m = fmax(m, a[c]);
     return m;
@@ -395,6 +443,7 @@ static double cell_speed(const orc_sim *s, int i, int j, double *const U[6])
 static double max_speed(const orc_sim *s, double *const U[6])
 {
     double m = 0.0;
+#pragma omp parallel for reduction(max : m)
     for (int j = 0; j < s->ny; j++)
         for (int i = 0; i < s->nx; i++) m = fmax(m, cell_speed(s, i, j, U));
     return m;
@@ -530,6 +579,7 @@ static void viscous_terms(orc_sim *s, double *Uin[6])
 {
     int nx = s->nx, ny = s->ny;
     const orc_params *p = &s->p;
+#pragma omp parallel for
     for (int j = 0; j < ny; j++) {
         for (int i = 0; i < nx; i++) {
             long k = IS(s, i, j);
@@ -590,9 +640,12 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
     const orc_params *p = &s->p;
     double al = alpha_rho(p);
     double tanb = tan(p->delta_b_deg * M_PI / 180.0);
+    double Ka, Kp;
+    earth_pressure(p, &Ka, &Kp);
     fill_ghosts(s, Uin, tt);
 
     /* x-faces i+1/2 for i = -1 .. nx-1: central flux with minmod slopes */
+#pragma omp parallel for
     for (int j = 0; j < ny; j++) {
         for (int i = -1; i < nx; i++) {
             double um[6], up[6], Fm[6], Fp[6], asm_, afm, asp, afp, Pm, Pp;
@@ -614,9 +667,11 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
                 }
             }
             const orc_geom *G = &s->gfx[IS(s, i, j)];
+            double KL = cell_earth_pressure(s, Uin, IS(s, i - 1, j), IS(s, i, j), IS(s, i + 1, j), 0, Ka, Kp);
+            double KR = cell_earth_pressure(s, Uin, IS(s, i, j), IS(s, i + 1, j), IS(s, i + 2, j), 0, Ka, Kp);
             double sm[4], sp[4];
-            face_flux(p, G, 0, um, Fm, &asm_, &afm, &Pm, sm);
-            face_flux(p, G, 0, up, Fp, &asp, &afp, &Pp, sp);
+            face_flux(p, G, 0, KL, um, Fm, &asm_, &afm, &Pm, sm);
+            face_flux(p, G, 0, KR, up, Fp, &asp, &afp, &Pp, sp);
             double as = fmax(asm_, asp), af = fmax(afm, afp);
             long k = IS(s, i, j);
             for (int c = 0; c < 6; c++) {
@@ -629,6 +684,7 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
         }
     }
     /* y-faces j+1/2 for j = -1 .. ny-1 */
+#pragma omp parallel for
     for (int j = -1; j < ny; j++) {
         for (int i = 0; i < nx; i++) {
             double um[6], up[6], Fm[6], Fp[6], asm_, afm, asp, afp, Pm, Pp;
@@ -650,9 +706,11 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
                 }
             }
             const orc_geom *G = &s->gfy[IS(s, i, j)];
+            double KL = cell_earth_pressure(s, Uin, IS(s, i, j - 1), IS(s, i, j), IS(s, i, j + 1), 1, Ka, Kp);
+            double KR = cell_earth_pressure(s, Uin, IS(s, i, j), IS(s, i, j + 1), IS(s, i, j + 2), 1, Ka, Kp);
             double sm[4], sp[4];
-            face_flux(p, G, 1, um, Fm, &asm_, &afm, &Pm, sm);
-            face_flux(p, G, 1, up, Fp, &asp, &afp, &Pp, sp);
+            face_flux(p, G, 1, KL, um, Fm, &asm_, &afm, &Pm, sm);
+            face_flux(p, G, 1, KR, up, Fp, &asp, &afp, &Pp, sp);
             double as = fmax(asm_, asp), af = fmax(afm, afp);
             long k = IS(s, i, j);
             for (int c = 0; c < 6; c++) {
@@ -679,10 +737,12 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
     }
     s->st_bnd[0] = bin[0];
     s->st_bnd[1] = bin[1];
-    s->st_clamp[0] = s->st_clamp[1] = 0.0;
-    s->st_clamp_cells = 0;
+    /* clamped volume per phase and clamped cells of this stage */
+    double cl_s = 0.0, cl_f = 0.0;
+    long cl_n = 0;
 
     /* cell update with the sources of App. A */
+#pragma omp parallel for reduction(+ : cl_s, cl_f, cl_n)
     for (int j = 0; j < ny; j++) {
         for (int i = 0; i < nx; i++) {
             long k = IS(s, i, j);
@@ -758,8 +818,9 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
             for (int ph = 0; ph < 2; ph++) {
                 int c = 3 * ph;
                 if (out[c] < 0.0) {
-                    s->st_clamp[ph] += -out[c] * s->dx * s->dy;
-                    s->st_clamp_cells++;
+                    if (ph == 0) cl_s += -out[c] * s->dx * s->dy;
+                    else cl_f += -out[c] * s->dx * s->dy;
+                    cl_n++;
                     out[c] = 0.0;
                 }
                 if (out[c] <= J * p->h_dry) {
@@ -770,6 +831,9 @@ static void stage(orc_sim *s, double *Uin[6], double *Uout[6], double tt, double
             for (int c = 0; c < 6; c++) Uout[c][k] = out[c];
         }
     }
+    s->st_clamp[0] = cl_s;
+    s->st_clamp[1] = cl_f;
+    s->st_clamp_cells = cl_n;
 }
 
 
@@ -789,6 +853,7 @@ static void heun_step(orc_sim *s, double dt)
         s->clamp_vol[ph] += 0.5 * (c1[ph] + s->st_clamp[ph]);
     }
     s->clamp_cells += n1 + s->st_clamp_cells;
+#pragma omp parallel for
     for (int j = 0; j < s->ny; j++) {
         for (int i = 0; i < s->nx; i++) {
             long k = IS(s, i, j);
@@ -811,6 +876,7 @@ static void heun_step(orc_sim *s, double dt)
 /* dry rule on the combined state (R5) */
 static void dry_momentum(orc_sim *s, double *U[6])
 {
+#pragma omp parallel for
     for (int j = 0; j < s->ny; j++)
         for (int i = 0; i < s->nx; i++) {
             long k = IS(s, i, j);
@@ -913,7 +979,9 @@ int orc_create(const double *dem, int nx, int ny, double dx, double dy, const or
 {
     *out = NULL;
     if (!dem || !p || nx < 1 || ny < 1 || !(dx > 0.0) || !(dy > 0.0)) return ORC_EINVAL;
-    if (p->k_mode != 0) return ORC_EINVAL;
+    if (p->k_mode != 0 && p->k_mode != 1) return ORC_EINVAL;
+    /* the Savage-Hutter coefficients need delta_b <= phi_int < 90 deg */
+    if (p->k_mode == 1 && !(p->delta_b_deg <= p->phi_int_deg && p->phi_int_deg < 90.0)) return ORC_EINVAL;
     if (p->scheme != 0 && p->scheme != 1) return ORC_EINVAL;
     if ((p->recon != 0 && p->recon != 1) || (p->rk != 2 && p->rk != 3)) return ORC_EINVAL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
@@ -1133,4 +1201,10 @@ int orc_cell_geom(const orc_sim *s, int gi, int gj, double *out4)
     out4[2] = G->Ai[0][0];
     out4[3] = G->Ai[1][1];
     return ORC_OK;
+}
+
+/* the earth-pressure coefficients K_act, K_pass of a parameter set (R10) */
+void orc_earth_pressure(const orc_params *p, double *out2)
+{
+    earth_pressure(p, &out2[0], &out2[1]);
 }

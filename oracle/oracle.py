@@ -16,17 +16,28 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c with plain -O2, no FMA contraction, no fast-math."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c with plain -O2, no FMA contraction, no fast-math.
+
+    openmp=True builds the copy that runs the loops over rows on every host
+    core (-fopenmp), for timing the multi-core CPU baseline only; the tests
+    use the plain build."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               *(["-fopenmp"] if openmp else []), "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
+def lib_openmp():
+    """The -fopenmp build of the oracle (multi-core CPU baseline timing)."""
+    return load(build(openmp=True))
 
 
 class _Params(C.Structure):
@@ -99,6 +110,7 @@ def _declare(L):
     L.orc_tangential.argtypes = [vp, C.c_int, C.c_int, C.c_double, C.c_double, dp]
     L.orc_inflow_state.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, dp]
     L.orc_cell_geom.argtypes = [vp, C.c_int, C.c_int, dp]
+    L.orc_earth_pressure.argtypes = [C.POINTER(_Params), dp]
 
 
 def _ptr(a: np.ndarray | None):
@@ -253,3 +265,12 @@ def from_config(cfg: dict, library=None) -> OracleSim:
         f = cfg["inflow"]
         s.set_inflow(f["side"], f["i0"], f["i1"], f["t"], f["Q"], f["phi"])
     return s
+
+
+def earth_pressure(params: dict, library=None):
+    """(K_act, K_pass) of a parameter set (reading R10; both 1 for k_mode 0)."""
+    L = library if library is not None else lib()
+    p = _params(params)
+    out = np.empty(2)
+    L.orc_earth_pressure(C.byref(p), _ptr(out))
+    return float(out[0]), float(out[1])

@@ -1366,6 +1366,213 @@ def pin_masking_reach(L=None):
             assert np.any(out[:, ~far] != 0.0)
 
 
+# ----------------------------------------------------------------------------
+# internal friction: the Savage-Hutter earth-pressure coefficient (reading R10)
+
+
+def _earth(params, L):
+    from oracle.oracle import earth_pressure
+    return earth_pressure(params, library=L)
+
+
+def pin_earth_pressure_limits(L=None):
+    """K_act/pass of the Savage-Hutter closure reduce to Rankine's coefficients
+    (1 -/+ sin phi) / (1 +/- sin phi) on a frictionless bed (delta_b = 0), meet
+    at (1 + sin^2 phi) / cos^2 phi when delta_b = phi_int, bracket 1
+    (K_act < 1 < K_pass) in between, and are both 1 in the paper's form."""
+    for phi in (20.0, 35.0, 41.0):
+        sp = math.sin(math.radians(phi))
+        ka, kp = _earth(W.default_params(k_mode=1, phi_int_deg=phi, delta_b_deg=0.0), L)
+        assert abs(ka - (1 - sp) / (1 + sp)) < 1e-14 and abs(kp - (1 + sp) / (1 - sp)) < 1e-13, (phi, ka, kp)
+        ka, kp = _earth(W.default_params(k_mode=1, phi_int_deg=phi, delta_b_deg=phi), L)
+        lim = (1 + sp * sp) / (1 - sp * sp)
+        assert abs(ka - lim) < 1e-12 and abs(kp - lim) < 1e-12, (phi, ka, kp, lim)
+        ka, kp = _earth(W.default_params(k_mode=1, phi_int_deg=phi, delta_b_deg=0.6 * phi), L)
+        assert ka < 1.0 < kp
+    assert _earth(W.default_params(k_mode=0), L) == (1.0, 1.0)
+
+
+def _solid_strip(nx, ny, dvx, dvy, seed=0, h0=2.0):
+    """A wet pure-solid layer with smooth depth, moving with (vX, vY) =
+    (3 + dvx i, -2 + dvy j) (dvx, dvy: velocity change per cell)."""
+    rng = np.random.default_rng(seed)
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny))
+    h = h0 + 0.3 * np.sin(0.4 * i + 0.3 * j) + 0.1 * rng.random((ny, nx))
+    return h, 3.0 + dvx * i, -2.0 + dvy * j
+
+
+def _stage_interior(dem, params, h, vx, vy, L, dt=0.05):
+    s = _sim(dem, 5.0, 5.0, params, L)
+    s.set_release(h, np.ones_like(h), vx, vy)
+    return s.stage(0.0, dt)[:, 2:-2, 2:-2]
+
+
+def pin_earth_pressure_regimes(L=None):
+    """One stage of a pure solid (rho_f = 0, no fluid) whose velocity grows
+    across every face (stretching) equals the paper's stage with eps scaled by
+    K_act -- eps enters a pure solid's step only through its pressure and
+    celerity -- and with a velocity that falls across every face
+    (compression) the one with eps scaled by K_pass; each axis chooses by its
+    own velocity component (an x-strip that compresses in X while its Y
+    velocity grows is passive, and the y-strip likewise); a face next to a
+    cell without solid is active."""
+    dem = W.incline_dem(24, 20, 5.0, 5.0, 15.0) + 0.5 * W.incline_dem(24, 20, 5.0, 5.0, 10.0, axis="y")
+    base = _pure_solid(k_mode=1, phi_int_deg=35.0, delta_b_deg=25.0, bc=(W.BC_TRANSMISSIVE,) * 4)
+    ka, kp = _earth(base, L)
+    k0 = dict(base, k_mode=0)
+    for dv, K in ((0.05, ka), (-0.05, kp)):
+        h, vx, vy = _solid_strip(24, 20, dv, dv)
+        got = _stage_interior(dem, base, h, vx, vy, L)
+        ref = _stage_interior(dem, dict(k0, eps=K), h, vx, vy, L)
+        assert np.allclose(got[:3], ref[:3], rtol=1e-12, atol=1e-12 * np.abs(ref[:3]).max()), (dv, K)
+        plain = _stage_interior(dem, k0, h, vx, vy, L)
+        assert np.abs(got[1:3] - plain[1:3]).max() > 1e-6 * np.abs(plain[1:3]).max(), "K has no effect"
+    # each axis by its own component: 1-cell-wide strips
+    for nx, ny, dvx, dvy in ((30, 1, -0.05, 0.05), (1, 30, 0.05, -0.05)):
+        demk = W.incline_dem(nx, ny, 5.0, 5.0, 12.0)
+        h, vx, vy = _solid_strip(nx, ny, dvx, dvy)
+        sl = (slice(None), slice(2, -2), slice(None)) if nx == 1 else (slice(None), slice(None), slice(2, -2))
+        s1 = _sim(demk, 5.0, 5.0, base, L)
+        s1.set_release(h, np.ones_like(h), vx, vy)
+        s2 = _sim(demk, 5.0, 5.0, dict(k0, eps=kp), L)
+        s2.set_release(h, np.ones_like(h), vx, vy)
+        got, ref = s1.stage(0.0, 0.05)[sl], s2.stage(0.0, 0.05)[sl]
+        assert np.allclose(got[:3], ref[:3], rtol=1e-12, atol=1e-12 * np.abs(ref[:3]).max()), (nx, ny)
+    # isolated solid cells moving fast: every face borders a cell without solid
+    # (empty, or a film thinner than h_dry whose momentum would, if counted,
+    # make the cell's velocity fall across it)
+    nx = ny = 12
+    h = np.zeros((ny, nx))
+    h[3, 3] = h[8, 7] = 1.5
+    vx = np.full((ny, nx), 4.0)
+    vy = np.full((ny, nx), -3.0)
+    h[8, 6] = h[8, 8] = h[7, 7] = h[9, 7] = 0.5 * base["h_dry"]
+    vx[8, 6], vx[8, 8], vy[7, 7], vy[9, 7] = 20.0, -20.0, 20.0, -20.0
+    flat = W.flat_dem(nx, ny)
+    got = _stage_interior(flat, base, h, vx, vy, L)
+    ref = _stage_interior(flat, dict(k0, eps=ka), h, vx, vy, L)
+    assert np.allclose(got[:3], ref[:3], rtol=1e-12, atol=1e-12 * np.abs(ref[:3]).max()), "dry neighbour"
+
+
+def pin_earth_pressure_fluid_unaffected(L=None):
+    """K belongs to the solid: in one stage of a two-phase mixture the fluid
+    components are the same in both forms, bit for bit."""
+    cfg = W.release_config(nx=20, ny=18, cfl=0.2)
+    st = W.random_state(20, 18, seed=4, dry_frac=0.0)
+    out = []
+    for km in (0, 1):
+        s = _sim(cfg["dem"], 5.0, 5.0, dict(cfg["params"], k_mode=km), L)
+        s.set_release(st["h"], st["phi_s"], st["vx_s"], st["vy_s"], st["vx_f"], st["vy_f"])
+        out.append(s.stage(0.0, 0.02))
+    assert np.array_equal(out[0][3:], out[1][3:]), "the earth pressure touched the fluid"
+    assert not np.array_equal(out[0][:3], out[1][:3])
+
+
+def pin_earth_pressure_wave_speed(L=None):
+    """The CFL wave speed of a pure solid at rest on a flat bed is
+    sqrt(K_pass g h) with the earth-pressure option (the larger coefficient
+    bounds the celerity in either regime)."""
+    nx, ny = 5, 4
+    one = np.ones((ny, nx))
+    p = _pure_solid(k_mode=1, phi_int_deg=35.0, delta_b_deg=25.0)
+    s = _sim(W.flat_dem(nx, ny), 5.0, 5.0, p, L)
+    s.set_release(3.0 * one, one)
+    _, kp = _earth(p, L)
+    assert abs(s.max_speed() - math.sqrt(kp * G * 3.0)) < 1e-13
+
+
+def _sh_k_reference(t_end, H0, L0, zeta, delta, K, u0=0.0, w0=0.0):
+    """Centre travel and half-length of the parabolic cap with earth-pressure
+    coefficient K: s_c'' = g (sin z - tan d cos z) with s_c'(0) = u0, and
+    L'' = 2 K g cos z H0 L0 / L^2 with L'(0) = w0 (RK4, fine steps)."""
+    a = G * (math.sin(zeta) - math.tan(delta) * math.cos(zeta))
+    k = 2 * K * G * math.cos(zeta) * H0 * L0
+
+    def f(y):
+        return np.array([y[1], k / y[0] ** 2])
+
+    y = np.array([L0, w0])
+    n = 20000
+    h = t_end / n
+    for _ in range(n):
+        k1 = f(y)
+        k2 = f(y + 0.5 * h * k1)
+        k3 = f(y + 0.5 * h * k2)
+        k4 = f(y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return u0 * t_end + 0.5 * a * t_end ** 2, y[0], y[1]
+
+
+def _cap_moments(s, x, zeta):
+    U1 = s.get_U()[0, 0]
+    sc = x / math.cos(zeta)
+    m = U1.sum()
+    c = (sc * U1).sum() / m
+    return c, math.sqrt(5 * ((sc - c) ** 2 * U1).sum() / m)
+
+
+def pin_savage_hutter_earth_pressure(L=None):
+    """The parabolic cap with internal friction (Savage-Hutter, K != 1), pure
+    solid on a 35 degree plane, delta_b = 25, phi_int = 35 degrees, launched
+    downslope with a linear velocity field along the slope, every point
+    moving downslope: spreading, every cell is active and the half-length
+    follows L'' = 2 K_act g cos z H0 L0 / L^2; converging, every cell is
+    passive (K_pass) until the cap turns.  The centre follows
+    s_c'' = g (sin z - tan d cos z) in both.  Each half-length is held
+    closer to its own coefficient's solution than a quarter of the distance
+    to the other regime's (K = 1 for the active case)."""
+    zeta, delta = math.radians(35.0), math.radians(25.0)
+    H0, L0, dx = 5.0, 100.0, 1.0
+    nx = 1400
+    x = (np.arange(nx) + 0.5) * dx
+    X0 = 200.0
+    p = _pure_solid(delta_b_deg=25.0, phi_int_deg=35.0, k_mode=1, cfl=0.1)
+    ka, kp = _earth(p, L)
+    h = H0 * np.clip(1 - ((x - X0) / (L0 * math.cos(zeta))) ** 2, 0, None)
+    dem = W.incline_dem(nx, 1, dx, dx, 35.0)
+    sc0 = X0 / math.cos(zeta)
+    for u0, w0, t_end, K, K_other in ((12.0, 5.0, 4.0, ka, 1.0), (15.0, -10.0, 1.5, kp, ka)):
+        # velocity along the slope u0 + (s - s_c) w0 / L0, as its horizontal projection
+        v = (u0 + (x / math.cos(zeta) - sc0) * w0 / L0) * math.cos(zeta)
+        s = _sim(dem, dx, dx, p, L)
+        s.set_release(h[None, :], np.ones((1, nx)), v[None, :], None)
+        while s.t < t_end:
+            s.step(5)
+        ds_ref, L_ref, w = _sh_k_reference(s.t, H0, L0, zeta, delta, K, u0, w0)
+        _, L_other, _ = _sh_k_reference(s.t, H0, L0, zeta, delta, K_other, u0, w0)
+        assert w * w0 > 0, "the reference cap turned within the window"
+        c, Lnum = _cap_moments(s, x, zeta)
+        ds = c - sc0
+        assert abs(ds - ds_ref) / ds_ref < 5e-3, f"SH-K centre travel {ds} vs {ds_ref} (w0 {w0})"
+        assert abs(Lnum - L_ref) < 0.25 * abs(L_ref - L_other), \
+            f"SH-K half-length {Lnum} vs {L_ref} (K {K}; {L_other} with K {K_other})"
+
+
+def pin_rotation_earth_pressure(L=None, steps=30):
+    """90 degree rotation invariance with the earth-pressure option (each axis
+    chooses its coefficient by its own velocity component)."""
+    n = 32
+    cfg = W.release_config(nx=n, ny=n, cfl=0.2)
+    p = dict(cfg["params"], k_mode=1)
+    rng = np.random.default_rng(8)
+    phi = rng.uniform(0.4, 0.7, (n, n))
+    h = cfg["h"] * (1 + 0.2 * rng.random((n, n)))
+    dem = cfg["dem"] + rng.random((n, n))
+    a = _sim(dem, 5.0, 5.0, p, L)
+    a.set_release(h, phi)
+    b = _sim(_rot(dem), 5.0, 5.0, p, L)
+    b.set_release(_rot(h), _rot(phi))
+    for _ in range(steps):
+        dt = a.cfl_dt()
+        assert abs(dt - b.cfl_dt()) <= 1e-14 * dt, "rotated run takes a different dt"
+        a.step_dt(dt)
+        b.step_dt(dt)
+    Ua, Ub = a.get_U(), b.get_U()
+    exp = np.stack([_rot(Ua[0]), -_rot(Ua[2]), _rot(Ua[1]), _rot(Ua[3]), -_rot(Ua[5]), _rot(Ua[4])])
+    err = np.abs(Ub - exp).max() / np.abs(Ua).max()
+    assert err < 1e-12, f"rotation invariance broken with k_mode 1: {err}"
+
+
 ALL_PINS = [
     # cheap pins first: the planted-mistake harness stops at the first pin that fails
     pin_masking_reach, pin_inflow_every_side, pin_stage_times, pin_time_step_cap, pin_positivity_clamp,
@@ -1379,4 +1586,6 @@ ALL_PINS = [
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,
     pin_cu_upwind_dependence, pin_cu_conservation_and_ritter, pin_cu_rotation,
     pin_weno_linear_exact, pin_weno_rk3_dam_break, pin_weno_smooth_order, pin_rk3_drag_factor,
-    pin_weno_rk3_budgets_and_rotation]
+    pin_weno_rk3_budgets_and_rotation,
+    pin_earth_pressure_limits, pin_earth_pressure_regimes, pin_earth_pressure_fluid_unaffected,
+    pin_earth_pressure_wave_speed, pin_savage_hutter_earth_pressure, pin_rotation_earth_pressure]

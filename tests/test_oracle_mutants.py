@@ -26,7 +26,7 @@ MUTANTS = [
     ("fluid pressure-gradient source as printed, phi^f (R1 undone)",
      "double fpg = (p->fluid_pg_mode == 1) ? phf : phs;", "double fpg = phf;"),
     ("A_11 dropped from the solid pressure flux",
-     "F[1] = J * hs * vXs * vns + p->eps * J * h * Ad1 * Ns;", "F[1] = J * hs * vXs * vns + p->eps * J * h * Ns;"),
+     "F[1] = J * hs * vXs * vns + p->eps * J * h * Ad1 * (K * Ns);", "F[1] = J * hs * vXs * vns + p->eps * J * h * (K * Ns);"),
     ("c dropped from the mean fluid pressure",
      "double pf = p->g * c * h / 2.0;", "double pf = p->g * h / 2.0;"),
     ("(1 - alpha) dropped from the solid pressure",
@@ -98,7 +98,7 @@ MUTANTS = [
      "double dt = (amax > 0.0) ? s->p.cfl * dmin / amax : s->p.dt_max;",
      "double dt = (amax > 0.0) ? s->p.cfl * dmin * amax : s->p.dt_max;"),
     ("solid celerity without the 1/2",
-     "(1.0 - al) * (h + hs) / 2.0);", "(1.0 - al) * (h + hs));"),
+     "(1.0 - al) * (h + hs) / 2.0));", "(1.0 - al) * (h + hs)));"),
     ("inflow depth with a square root instead of a cube root",
      "double hc = cbrt(q * q / (G->J * G->J * p->eps * p->g * G->c * Ann));",
      "double hc = sqrt(q * q / (G->J * G->J * p->eps * p->g * G->c * Ann));"),
@@ -130,7 +130,8 @@ MUTANTS = [
     ("time step not capped at dt_max",
      "if (dt > s->p.dt_max) dt = s->p.dt_max;", ""),
     ("clamp volume counted with the wrong sign",
-     "s->st_clamp[ph] += -out[c] * s->dx * s->dy;", "s->st_clamp[ph] += out[c] * s->dx * s->dy;"),
+     "if (ph == 0) cl_s += -out[c] * s->dx * s->dy;\n                    else cl_f += -out[c] * s->dx * s->dy;",
+     "if (ph == 0) cl_s += out[c] * s->dx * s->dy;\n                    else cl_f += out[c] * s->dx * s->dy;"),
     ("positivity clamp removed",
      "if (out[c] < 0.0) {", "if (0 && out[c] < 0.0) {"),
     ("Heun second stage's boundary data at the start time",
@@ -169,8 +170,8 @@ MUTANTS = [
      "for (int i = 0; i < s->nx; i++) m = fmax(m, cell_speed(s, i, j, U));",
      "for (int i = 0; i < s->nx - 1; i++) m = fmax(m, cell_speed(s, i, j, U));"),
     ("solid celerity without (1 - alpha)",
-     "double cs = sqrt(p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0);",
-     "double cs = sqrt(p->eps * p->g * c * Add * (h + hs) / 2.0);"),
+     "double cs = sqrt(K * (p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0));",
+     "double cs = sqrt(K * (p->eps * p->g * c * Add * (h + hs) / 2.0));"),
     ("solid basal pressure without (1 - alpha)",
      "double pbs = hs * (p->g * c0 * (1.0 - al) - p->eps_chi * ks);", "double pbs = hs * (p->g * c0 - p->eps_chi * ks);"),
     ("kappa of the fluid from the solid velocity",
@@ -203,6 +204,26 @@ MUTANTS = [
      "    s->last_dt = dt;\n    s->nsteps++;\n}\n\n/* dry rule", "    s->last_dt = dt;\n}\n\n/* dry rule"),
     ("CFL step from twice the wave speed",
      "double dt = cfl_dt(s, max_speed(s, s->U));", "double dt = cfl_dt(s, 2.0 * max_speed(s, s->U));"),
+    ("earth pressure: active and passive regimes swapped",
+     "return (vp - vm < 0.0) ? Kp : Ka;", "return (vp - vm < 0.0) ? Ka : Kp;"),
+    ("earth pressure: cos^2(delta_b) in place of sec^2(delta_b)",
+     "double r = sqrt(1.0 - cp2 / cd2);", "double r = sqrt(1.0 - cp2 * cd2);"),
+    ("earth pressure: solid celerity without K",
+     "double cs = sqrt(K * (p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0));",
+     "double cs = sqrt(p->eps * p->g * c * Add * (1.0 - al) * (h + hs) / 2.0);"),
+    ("earth pressure: K on the fluid pressure too",
+     "F[4] = J * hf * vXf * vnf + p->eps * J * h * Ad1 * pf;", "F[4] = J * hf * vXf * vnf + p->eps * J * h * Ad1 * (K * pf);"),
+    ("earth pressure: regime from the transverse velocity component",
+     "double vm = U[1 + d][km] / U[0][km], vp = U[1 + d][kp] / U[0][kp];",
+     "double vm = U[2 - d][km] / U[0][km], vp = U[2 - d][kp] / U[0][kp];"),
+    ("earth pressure: neighbours without solid not set aside",
+     "if (!(U[0][km] > s->gc[km].J * hd) || !(U[0][k] > s->gc[k].J * hd) || !(U[0][kp] > s->gc[kp].J * hd))",
+     "if (!(U[0][k] > s->gc[k].J * hd))"),
+    ("earth pressure: CFL celerity with K_act",
+     "face_flux(&s->p, G, 0, Kp, u, F, &a[0], &a[1], &P, NULL);", "face_flux(&s->p, G, 0, Ka, u, F, &a[0], &a[1], &P, NULL);"),
+    ("earth pressure: each side with the other cell's coefficient",
+     "face_flux(p, G, 0, KL, um, Fm, &asm_, &afm, &Pm, sm);\n            face_flux(p, G, 0, KR, up, Fp, &asp, &afp, &Pp, sp);",
+     "face_flux(p, G, 0, KR, um, Fm, &asm_, &afm, &Pm, sm);\n            face_flux(p, G, 0, KL, up, Fp, &asp, &afp, &Pp, sp);"),
 ]
 
 
