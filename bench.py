@@ -1,23 +1,35 @@
 #!/usr/bin/env python
 """Throughput of the two-phase shallow-flow step on one GB300 (cell-steps/s).
 
-Workload: the large-scale release event -- 4096 x 4096 cells at 10 m over a
-seeded 1/f^2.2 spectral DEM (1500 m relief) with one carved valley, a
-2.5e7 m^3 parabolic-cap release on a 30-40 degree slope, solid fraction
-U(0.55, 0.65), transmissive boundaries, CFL 0.1 (synthetic stand-in for the
-Hsiaolin event of Sect. 4.1; the real DEM is not available).
+Headline workload: the large-scale release event -- 4096 x 4096 cells at 10 m
+over a seeded 1/f^2.2 spectral DEM (1500 m relief) with one carved valley, a
+2.5e7 m^3 parabolic-cap release (bed-normal volume) on a 30-40 degree slope,
+solid fraction U(0.55, 0.65), transmissive boundaries, CFL 0.1, 10000 steps
+(synthetic stand-in for the Hsiaolin event of Sect. 4.1; the real DEM is not
+available).
 
 A step is one full time step: CFL time step from the exact max-reduction, two
 stages of the central scheme with all sources, Heun average, boundary fill.
 Each stage is two launches: the wet/dry classification, which writes the
 stage result of every tile without mass in reach (the zero state), and the
-stage kernel on the listed tiles.  The release covers a small part of the
-terrain, so most tiles are dry: the step streams the state through HBM and
-the line reports the HBM roofline, the wet-tile fraction, and (`dense`) the
-same kernels on an all-wet state, where the stage is bound by its FP64
-arithmetic.  The headline is the FP64 form; the FP32 form (FP64 budgets and
-friction test) is measured in the same run.  The state (0.8 GB in FP64) is
-larger than L2, so no flush is needed between steps.
+stage kernel on the listed tiles.  The event is first run through all its
+10000 steps (timed as a whole, with the wet-tile fraction at the start of
+each quarter); the headline then times K steps (after W warm-up steps) from
+the checkpoint at the start of each quarter, so that the K-step figure
+samples the whole event and not only its start.  Every cell of the grid
+counts in cell-steps/s, as in the paper's speed-up figures (Sect. 3.2); the
+kernel's own roofline comes from the same kernels on an all-wet state
+(`dense`: every tile computes), against the measured FP64 FMA rate and
+against HBM with 13 words per computed cell-step.  The headline is the FP64
+form; the FP32 form (FP64 budgets and friction test) is measured the same
+way in the same run.  The state (0.8 GB in FP64) is larger than L2, so no
+flush is needed between steps.
+
+The other configurations have lines of their own at their stated sizes and
+lengths: the arc-plane release (128^2, 2000 steps, FP64), the inflow
+hydrograph (2048 x 1024 to t = 600 s, FP32 with FP64 budgets), the 256-member
+ensemble (3000 steps, FP32) and the adjoint calibration (1024^2, 5000 steps,
+checkpoint every 71).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -54,37 +66,30 @@ DX = 10.0
 # U^{n+1} (6), read the bed elevation (1).
 FLOPS_PER_CELL_STAGE = 488
 WORDS_PER_CELL_STEP = 13
-# With wet/dry masking a step need not touch a dry cell's state: it must read
-# the two mass planes of every cell once (the wet test; FP32: 2 x 4 B masses
-# and 2 x 4 B remainders, FP64: 2 x 8 B), and move the whole cell-step traffic
-# above only for the cells of the tiles that compute.
-MASS_TEST_BYTES = 16
+EVENT_STEPS = 10000  # the large release event's length
+N_WINDOWS = 4        # timed windows, at the start of each quarter of the event
 
-
-def step_bytes(cells, wet_frac, esz):
-    """Algorithmic HBM bytes of one masked step: the wet test over every cell
-    plus the cell-step traffic of the cells in tiles with work."""
-    return MASS_TEST_BYTES * cells + WORDS_PER_CELL_STEP * esz * wet_frac * cells
-
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step --
-# the wet/dry classification launch plus the listed-tile stage launch, both
-# stages -- per cell of the 4096^2 workload, from an ncu capture of bench.py
-# itself at full size (one-pass metrics) over the timed steps; valid only for
-# the stage kernel source it was taken on (sha256 of csrc/stage.cuh, first
-# 12) and for this workload (the wet fraction sets it).
-TRAFFIC = {
-    # profiles/stage_kernel_launch_list_4096_release.md (tile 32 x 8; the
-    # classification's read of the mass planes is 95 % of it at any tile shape)
-    ("f64", "beb8a8d2e738"): 16.87,
-    # before the known-zero tile flags
-    ("f64", "f1a1dc700d9f"): 108.86,
-    ("f32", "f1a1dc700d9f"): 77.80,
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the stage
+# kernel on the all-wet state, per cell and stage launch, from an ncu capture of
+# stage_kernel_list on a 2048^2 all-wet case (the per-cell traffic of a
+# fully wet grid does not depend on its size once it exceeds L2); valid only
+# for the stage kernel source it was taken on (sha256 of csrc/stage.cuh,
+# first 12).
+TRAFFIC_PER_CELL_STAGE = {
+    # profiles/stage_kernel_list_wet_2048_full.md
+    ("f64", "beb8a8d2e738"): 273.0 + 46.0,
 }
 
 
-def _traffic(form, h, side):
-    b = TRAFFIC.get((form, h))
-    return None if b is None or side != N_SIDE else b * side * side
+def cell_step_gbs(cells, esz, step_s):
+    """HBM rate [GB/s] of a step over `cells` computed cells that takes step_s
+    seconds, at 13 words of esz bytes per cell-step (FP64 104 B, FP32 52 B)."""
+    return WORDS_PER_CELL_STEP * esz * cells / step_s / 1e9
+
+
+def _traffic(form, h, cells):
+    b = TRAFFIC_PER_CELL_STAGE.get((form, h))
+    return None if b is None else b * cells
 
 
 def peaks():
@@ -97,9 +102,13 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 vector peak of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
-# = 1.26 TFLOP/s, matching the 1.25 TFLOP/s nominal figure.
+# FP64 vector peak of GB300 from its unit counts and clock: 152 SMs x 2 FP64
+# FMA/clk x 2 flops x 2.07 GHz = 1.26 TFLOP/s (the 1.25 TFLOP/s nominal
+# figure).  The roofline takes the measured FMA rate (moses_debug_fp64_rate)
+# and keeps this one beside it.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 vector peak: 152 SMs x 128 FMA/clk x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def stage_hash():
@@ -196,63 +205,90 @@ class ClockSampler:
                 "interval_ms": self.INTERVAL_MS}
 
 
-def cpu_baseline(cfg, steps=None, window=1024):
-    """The FP64 oracle as it stands, single-threaded on the host, on a bounded
-    sample: `steps` steps on a window x window crop of the workload centred on
-    the release (throughput per cell-step does not depend on the size)."""
+def _oracle_window(cfg, window, library=None):
+    """The oracle on a window x window crop of the workload centred on the release."""
     from oracle.oracle import OracleSim
     ic, jc = cfg["release_cell"]
     n = cfg["dem"].shape[0]
     i0 = int(min(max(ic - window // 2, 0), n - window))
     j0 = int(min(max(jc - window // 2, 0), n - window))
     sl = (slice(j0, j0 + window), slice(i0, i0 + window))
-    o = OracleSim(cfg["dem"][sl], cfg["dx"], cfg["dy"], cfg["params"])
+    o = OracleSim(cfg["dem"][sl], cfg["dx"], cfg["dy"], cfg["params"], library=library)
     o.set_release(cfg["h"][sl], cfg["phi_s"][sl])
+    return o
+
+
+def _omp_threads():
+    return int(os.environ.get("OMP_NUM_THREADS", "0")) or os.cpu_count() or 1
+
+
+def cpu_baseline(cfg, window=1024):
+    """The FP64 oracle as it stands on the host, on a bounded sample: steps on
+    a window x window crop of the workload centred on the release (throughput
+    per cell-step does not depend on the size).  Two legs: the plain build on
+    one core (the paper's single-core baseline, Sect. 3.2) and the OpenMP
+    build over every host core; the line's value is the multi-core leg."""
+    from oracle import oracle as O
+    n = cfg["dem"].shape[0]
+    o = _oracle_window(cfg, window)
     o.step(1)
-    steps = steps or 20
     t0 = time.perf_counter()
-    o.step(steps)
-    el = time.perf_counter() - t0
-    return dict(value=window * window * steps / el, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{steps} FP64 steps of the oracle on the {window}x{window} window of the "
-                       f"{n}x{n} workload around the release, 1 thread",
-                seconds=el)
+    s1 = 20
+    o.step(s1)
+    el1 = time.perf_counter() - t0
+    cores = _omp_threads()
+    om = _oracle_window(cfg, window, library=O.lib_openmp())
+    om.step(1)
+    sm = 20 * max(1, min(cores, 16))
+    t0 = time.perf_counter()
+    om.step(sm)
+    elm = time.perf_counter() - t0
+    return dict(value=window * window * sm / elm, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{sm} FP64 steps of the oracle (OpenMP build, {cores} threads) on the {window}x{window} "
+                       f"window of the {n}x{n} workload around the release",
+                single_core={"value": window * window * s1 / el1, "cores": 1,
+                             "sample": f"{s1} steps of the plain build on the same window, 1 thread"},
+                seconds=el1 + elm)
 
 
 def run_reference(args, cfg, rank):
-    """The reference arm: the CPU oracle timed on the host, K steps after W
-    warm-up steps, each step one oracle step on a 1024 x 1024 window."""
+    """The reference arm: the CPU oracle (OpenMP build, every host core) timed
+    on the host, K steps after W warm-up steps, each step one oracle step on a
+    1024 x 1024 window of the workload around the release."""
     if rank != 0:
         return None
-    from oracle.oracle import OracleSim
+    from oracle import oracle as O
     window = 1024
-    ic, jc = cfg["release_cell"]
     n = cfg["dem"].shape[0]
-    i0 = int(min(max(ic - window // 2, 0), n - window))
-    j0 = int(min(max(jc - window // 2, 0), n - window))
-    sl = (slice(j0, j0 + window), slice(i0, i0 + window))
-    o = OracleSim(cfg["dem"][sl], cfg["dx"], cfg["dy"], cfg["params"])
-    o.set_release(cfg["h"][sl], cfg["phi_s"][sl])
+    o = _oracle_window(cfg, window, library=O.lib_openmp())
     o.step(args.warmup)
     t0 = time.perf_counter()
     o.step(args.steps)
     el = time.perf_counter() - t0
     v = window * window * args.steps / el
-    sample = f"each step: one FP64 oracle step on the {window}x{window} window of the {n}x{n} workload, 1 thread"
+    cores = _omp_threads()
+    sample = (f"each step: one FP64 oracle step (OpenMP build, {cores} threads) on the {window}x{window} window "
+              f"of the {n}x{n} workload")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(cfg, args),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def config_dict(cfg, args):
     n = cfg["dem"].shape[0]
     return {"workload": f"large-scale release event, {n}x{n} cells at {DX:g} m, spectral DEM "
-                        f"(beta 2.2, 1500 m relief, carved valley), 2.5e7 m^3 release, CFL 0.1",
+                        f"(beta 2.2, 1500 m relief, carved valley), 2.5e7 m^3 release (bed-normal), CFL 0.1, "
+                        f"{EVENT_STEPS} steps; K steps timed from each of {N_WINDOWS} checkpoints (the start of each "
+                        f"quarter of the event)",
             "cells": n * n, "dx_m": DX, "l2": "state larger than L2 (0.8 GB FP64, 0.4 GB FP32); no flush",
             "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
 def measure(sim, cells, K, W, torch, sampler=None):
@@ -261,7 +297,7 @@ def measure(sim, cells, K, W, torch, sampler=None):
     sim.step(W)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(torch)
     if sampler is not None:
         sampler.begin()
     e0.record(stream)
@@ -274,6 +310,55 @@ def measure(sim, cells, K, W, torch, sampler=None):
     # per-launch timing of the stage kernel over K more steps
     _, stage_ms = sim.step_timed(K)
     return ms, stage_ms
+
+
+def run_event(sim, torch, nsteps=EVENT_STEPS, nwin=N_WINDOWS, tile=(32, 8)):
+    """The whole event: nsteps steps in nwin segments, each timed with CUDA
+    events on the simulation's stream; before each segment the state is kept
+    (a device checkpoint for the windows) and its wet-tile fraction taken."""
+    seg = nsteps // nwin
+    stream = torch.cuda.current_stream()
+    ckpts, segs = [], []
+    for w in range(nwin):
+        ck = torch.empty((6, sim.ny, sim.nx), dtype=torch.float64, device="cuda")
+        sim.get_conserved_device(ck.data_ptr())
+        torch.cuda.synchronize()
+        wet = wet_tile_fraction(ck.cpu().numpy(), *tile)
+        t0 = sim.budget()["t"]
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        sim.step(seg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ckpts.append(ck)
+        segs.append({"from_step": w * seg, "t_s": t0, "wet_tiles": wet, "ms": e0.elapsed_time(e1)})
+    b = sim.budget()
+    U = sim.get_conserved()
+    total = sum(x["ms"] for x in segs)
+    return ckpts, {"steps": nwin * seg, "ms": total, "value": sim.nx * sim.ny * nwin * seg / (total / 1e3),
+                   "t_end_s": b["t"], "wet_tiles_end": wet_tile_fraction(U, *tile), "segments": segs}
+
+
+def measure_windows(sim, ckpts, K, W, torch, sampler=None):
+    """K steps timed (after W warm-up steps) from each checkpoint: CUDA events
+    on the simulation's stream around the K steps of each window."""
+    stream = torch.cuda.current_stream()
+    out = []
+    for ck in ckpts:
+        sim.set_conserved_device(ck.data_ptr())
+        sim.step(W)
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        if sampler is not None:
+            sampler.begin()
+        e0.record(stream)
+        sim.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.end()
+        out.append(e0.elapsed_time(e1))
+    return out
 
 
 def wet_tile_fraction(U, tx=32, ty=8):
@@ -296,23 +381,38 @@ def wet_tile_fraction(U, tx=32, ty=8):
     return float(t.mean())
 
 
-def measure_dense(cfg, K, Wm, torch):
+def measure_dense(cfg, K, Wm, torch, fp64_tflops, hbm_gbs, h):
     """The same 4096^2 terrain and release with a 5 cm mixture layer over every
-    cell, so that every tile computes (no dry tile to skip): the stage's
-    arithmetic-bound rate, for comparison with the masked workload."""
+    cell, so that every tile computes (no dry tile to skip): the stage's own
+    rate.  Per form its roofline: FP64 against the measured FP64 FMA rate
+    (the binding roof: 488 flops per cell and stage) and against HBM with the
+    13 words per computed cell-step (104 B); FP32 against HBM (52 B) and
+    against the FP32 FMA peak from unit counts and clock.  The launch time is
+    the summed device time of the stage launches (the classification and the
+    listed-tile stage kernel) from moses_step_timed, per launch pair."""
     from paper_2104_06784_gb300 import moses
     c = dict(cfg, h=cfg["h"] + 0.05)
     out = {"config": "the 4096^2 workload plus a 5 cm layer (phi_s as the release) on every cell: all tiles wet"}
-    for form, prec in (("f64", moses.FP64), ("f32", moses.FP32)):
+    for form, prec, esz in (("f64", moses.FP64, 8), ("f32", moses.FP32, 4)):
         with moses.from_config(c, precision=prec) as sim:
             ms, stage_ms = measure(sim, sim.nx * sim.ny, K, Wm, torch)
             cells = sim.nx * sim.ny
         launch_ms = (stage_ms[0] + stage_ms[1]) / (2 * K)
-        out[form] = {"ms_per_step": ms / K, "value": cells * K / (ms / 1e3), "launch_ms": launch_ms}
+        step_s = 2 * launch_ms / 1e3
+        gbs = cell_step_gbs(cells, esz, step_s)
+        tfl = FLOPS_PER_CELL_STAGE * cells / (launch_ms / 1e3) / 1e12
+        out[form] = {"ms_per_step": ms / K, "value": cells * K / (ms / 1e3), "launch_ms": launch_ms,
+                     "hbm": {"achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+                             "bytes_per_cell_step": WORDS_PER_CELL_STEP * esz}}
         if form == "f64":
-            ach = FLOPS_PER_CELL_STAGE * cells / (launch_ms / 1e3) / 1e12
-            out[form]["alu"] = {"achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                "frac": ach / FP64_PEAK_TFLOPS}
+            out[form]["alu"] = {"achieved": tfl, "peak": fp64_tflops, "unit": "TFLOP/s", "frac": tfl / fp64_tflops,
+                                "peak_source": "measured FP64 FMA rate (moses_debug_fp64_rate)",
+                                "peak_units_clock": FP64_PEAK_TFLOPS, "frac_units_clock": tfl / FP64_PEAK_TFLOPS}
+            tr = _traffic("f64", h, cells)
+            out[form]["traffic_per_launch"] = tr
+        else:
+            out[form]["alu"] = {"achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": tfl / FP32_PEAK_TFLOPS, "peak_source": "unit counts x 2.07 GHz"}
     return out
 
 
@@ -352,13 +452,14 @@ def shard(items, rank, world):
     return list(items)[rank::world]
 
 
-def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="cpu"):
+def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="cpu", steps=3000):
     """Batched ensemble, FP32: 256 members on square grids of lognormal side
     (64..1024 cells, 5 m), each its own spectral DEM, basal friction, drag and
     release volume; per stage one batched classification launch and one
     batched launch over the wet tiles of all members, replayed from a CUDA graph.
-    Device time from CUDA events on the batch's stream.  With several ranks
-    the members are sharded across them; the time is the max over ranks."""
+    The members' 3000 steps are timed whole (after Wm warm-up steps), device
+    time from CUDA events on the batch's stream.  With several ranks the
+    members are sharded across them; the time is the max over ranks."""
     from paper_2104_06784_gb300 import moses, workloads as W
     cfgs = shard(W.ensemble_config(n, seed=seed), rank, world)
     cells_rank = int(sum(c["dem"].size for c in cfgs))
@@ -367,18 +468,79 @@ def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="c
         b.step(Wm)
         if dist is not None:
             dist.barrier()
-        ms = b.step_timed(K)
+        ms = b.step_timed(steps)
         tiles = b.tiles
+    wet = float(np.mean([wet_tile_fraction(s_.get_conserved()) for s_ in sims]))
     for s_ in sims:
         s_.close()
     ms = reduce_over_ranks(ms, "max", dist, device)
     cells = int(reduce_over_ranks(cells_rank, "sum", dist, device))
-    return {"value": cells * K / (ms / 1e3), "unit": "cell-steps/s", "members": n, "cells": cells,
+    return {"value": cells * steps / (ms / 1e3), "unit": "cell-steps/s", "members": n, "cells": cells,
             "members_per_rank": len(cfgs), "scaling": "strong" if world > 1 else None,
-            "ms_per_step": ms / K, "steps": K, "warmup": Wm, "dtype": "f32", "gpu_launches": 4 * K,
-            "tiles_per_launch": tiles,
+            "ms_per_step": ms / steps, "steps": steps, "warmup": Wm, "dtype": "f32", "gpu_launches": 4 * steps,
+            "tiles_per_launch": tiles, "wet_tiles_end_mean": wet,
             "config": "256 scenarios, sides clip(round16(lognormal(ln 256, ln4/2)), 64, 1024), dx 5 m, "
-                      "spectral DEMs, delta_b U(15,30) deg, c_D U(1e-4,1e-2) 1/s, release U(1e4,1e6) m^3, FP32"}
+                      "spectral DEMs, delta_b U(15,30) deg, c_D U(1e-4,1e-2) 1/s, release U(1e4,1e6) m^3, FP32, "
+                      f"{steps} steps timed whole"}
+
+
+def measure_arc_plane(torch):
+    """The arc-plane release at its stated size and length: 128 x 128 cells at
+    5 m, closed boundaries, CFL 0.5, 2000 steps, FP64 (CUDA events)."""
+    from paper_2104_06784_gb300 import moses, workloads as W
+    cfg = W.release_config()
+    with moses.from_config(cfg, precision=moses.FP64) as sim:
+        sim.step(3)
+        sim.set_release(cfg["h"], cfg["phi_s"])
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        sim.step(cfg["steps"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        b = sim.budget()
+    v0 = W.release_volume(cfg["h"], cfg["dem"], cfg["dx"])
+    return {"config": "arc-plane release, 128x128 cells at 5 m, closed, CFL 0.5, 2000 steps, FP64",
+            "steps": cfg["steps"], "ms": ms, "value": 128 * 128 * cfg["steps"] / (ms / 1e3), "dtype": "f64",
+            "t_end_s": b["t"], "clamp_cells": b["clamp_cells"],
+            "volume_m3": b["vol_s"] + b["vol_f"], "release_volume_m3": v0}
+
+
+def measure_inflow(torch, precision=None):
+    """The inflow hydrograph at its stated size and length: 2048 x 1024 cells
+    at 5 m, channel-and-fan DEM, triangular hydrograph (800 m^3/s at 60 s, 0 by
+    300 s) at a 20-cell inlet, run to t = 600 s, FP32 state with FP64 budgets.
+    Device time from CUDA events around the whole run; the mass budget closes
+    on the boundary fluxes (volume - boundary inflow - clamp volume)."""
+    from paper_2104_06784_gb300 import moses, workloads as W
+    cfg = W.inflow_config()
+    prec = moses.FP32 if precision is None else precision
+    with moses.from_config(cfg, precision=prec) as sim:
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch)
+        e0.record(stream)
+        n = sim.run_until(cfg["t_end"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        b = sim.budget()
+        U = sim.get_conserved()
+    vol = b["vol_s"] + b["vol_f"]
+    bnd = b["bnd_in_s"] + b["bnd_in_f"]
+    clamp = b["clamp_s"] + b["clamp_f"]
+    tq, Q = np.asarray(cfg["inflow"]["t"]), np.asarray(cfg["inflow"]["Q"])
+    cells = U.shape[1] * U.shape[2]
+    return {"config": "inflow hydrograph, 2048x1024 cells at 5 m, channel-and-fan DEM, triangular Q (800 m^3/s "
+                      "peak at 60 s, 0 by 300 s), 20-cell inlet, to t = 600 s, FP32 state + FP64 budgets",
+            "steps": n, "t_end_s": b["t"], "ms": ms, "value": cells * n / (ms / 1e3),
+            "dtype": "f32" if prec == moses.FP32 else "f64",
+            "volume_m3": vol, "boundary_inflow_m3": bnd, "clamp_volume_m3": clamp,
+            "mass_drift_rel": abs(vol - bnd - clamp) / max(bnd, 1e-300),
+            "hydrograph_volume_m3": float(np.trapezoid(Q, tq)) if hasattr(np, "trapezoid") else float(np.trapz(Q, tq)),
+            "wet_tiles_end": wet_tile_fraction(U), "gpu_launches": 4 * n}
 
 
 def measure_adjoint(torch, n=1024, steps=None, ckpt=None):
@@ -438,9 +600,11 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the arc-plane and inflow lines")
     ap.add_argument("--side", type=int, default=N_SIDE, help="grid side (the workload is defined at 4096)")
+    ap.add_argument("--event-steps", type=int, default=EVENT_STEPS, help="length of the event (10000)")
     ap.add_argument("--only", choices=["f64", "f32", "adjoint"], default=None,
-                    help="measure one precision form, or only the adjoint")
+                    help="measure one precision form (K steps from the start), or only the adjoint")
     ap.add_argument("--wet-layer", type=float, default=0.0,
                     help="add a mixture layer of this depth [m] on every cell (all tiles wet; for profiling)")
     ap.add_argument("--tile", choices=["auto", "32x8", "32x4", "32x16"], default="auto",
@@ -488,12 +652,27 @@ def main():
     def max_over_ranks(x):
         return reduce_over_ranks(x, "max", dist, "cuda")
 
-    results = {}
-    sampler = ClockSampler(local)
     forms = [("f64", moses.FP64), ("f32", moses.FP32)]
     if args.only:
-        forms = [f for f in forms if f[0] == args.only]
-    tiles = {}
+        # profiling runs: K steps from the start of the event (or of the wet layer)
+        name, prec = [f for f in forms if f[0] == args.only][0]
+        sim = moses.from_config(cfg, precision=prec)
+        if args.tile != "auto":
+            sim.set_tile({v: k for k, v in moses.Sim.TILES.items()}[args.tile])
+        ms, stage_ms = measure(sim, cells, K, Wm, torch)
+        if rank == 0:
+            print(json.dumps({"form": name, "side": side, "ms_per_step": ms / K,
+                              "launch_ms": (stage_ms[0] + stage_ms[1]) / (2 * K),
+                              "value": world * cells * K / (ms / 1e3)}), flush=True)
+        sim.close()
+        return
+
+    pk, pk_src = peaks()
+    fp64_tflops = moses.fp64_rate()
+    h = stage_hash()
+    results, tiles = {}, {}
+    sampler = ClockSampler(local)
+    nwin = N_WINDOWS
     for name, prec in forms:
         sim = moses.from_config(cfg, precision=prec)
         if args.tile == "auto":
@@ -504,53 +683,37 @@ def main():
             tile = {v: k for k, v in moses.Sim.TILES.items()}[args.tile]
             sim.set_tile(tile)
             tiles[name] = {"tile": args.tile, "pinned": True}
+        ts = tuple(int(x) for x in tiles[name]["tile"].split("x"))
+        ckpts, event = run_event(sim, torch, nsteps=args.event_steps, nwin=nwin, tile=ts)
         if dist is not None:
             dist.barrier()
         with (sampler if name == "f64" else _Null()):
-            ms, stage_ms = measure(sim, cells, K, Wm, torch, sampler if name == "f64" else None)
-        ms = max_over_ranks(ms)
-        launch_ms = (stage_ms[0] + stage_ms[1]) / (2 * K)
-        results[name] = dict(ms=ms, launch_ms=launch_ms, stage_ms=[stage_ms[0] / K, stage_ms[1] / K], sim=sim)
-        if not args.only:
-            t = tiles[name]["tile"].split("x")
-            results[name]["wet_tiles"] = wet_tile_fraction(sim.get_conserved(), int(t[0]), int(t[1]))
+            win_ms = measure_windows(sim, ckpts, K, Wm, torch, sampler if name == "f64" else None)
+        del ckpts
+        ms = max_over_ranks(sum(win_ms))
+        results[name] = dict(ms=ms, win_ms=win_ms, event=event, sim=sim)
         if name == "f32":
             sim.close()
 
-    if args.only:
-        r = results[args.only]
-        if rank == 0:
-            print(json.dumps({"form": args.only, "side": side, "ms_per_step": r["ms"] / K,
-                              "launch_ms": r["launch_ms"], "value": world * cells * K / (r["ms"] / 1e3)}), flush=True)
-        r["sim"].close()
-        return
-    pk, pk_src = peaks()
-    f64 = results["f64"]
-    value = world * cells * K / (f64["ms"] / 1e3)
-    h = stage_hash()
-    t64, t32 = tiles["f64"]["tile"], tiles["f32"]["tile"]
-    # The release covers a small part of the terrain: most tiles are dry, skip
-    # their arithmetic and, once their output holds the zero state, their
-    # writes too (wet/dry masking with known-zero tile flags).  A step then
-    # reads the mass planes once (HBM) and runs the stage arithmetic on the
-    # few wet tiles (FP64 pipe); the roofline counts the bytes such a step
-    # must move (step_bytes).  The all-wet measurement (`dense`) gives the
-    # arithmetic-bound rate of the same kernel.
-    b64 = step_bytes(cells, f64["wet_tiles"], 8)
-    gbs64 = b64 / (2 * f64["launch_ms"] / 1e3) / 1e9
-    roof64 = {"bound": "hbm", "achieved": gbs64, "peak": pk["hbm_gbs"], "unit": "GB/s",
-              "frac": gbs64 / pk["hbm_gbs"], "traffic": _traffic("f64", h, side),
-              "kernel": f"one step: moses::classify_kernel<double,{t64.split('x')[1]}> + "
-                        f"moses::stage_kernel_list<double,{t64.replace('x', ',')}>, two stages",
-              "peak_source": pk_src, "wet_tiles": f64["wet_tiles"], "bytes_per_step": b64}
-    f32 = results["f32"]
-    b32 = step_bytes(cells, f32["wet_tiles"], 4)
-    gbs32 = b32 / (2 * f32["launch_ms"] / 1e3) / 1e9
-    roof32 = {"bound": "hbm", "achieved": gbs32, "peak": pk["hbm_gbs"], "unit": "GB/s",
-              "frac": gbs32 / pk["hbm_gbs"], "traffic": _traffic("f32", h, side),
-              "kernel": f"one step: moses::classify_kernel<float,{t32.split('x')[1]}> + "
-                        f"moses::stage_kernel_list<float,{t32.replace('x', ',')}>, two stages",
-              "peak_source": pk_src, "wet_tiles": f32["wet_tiles"], "bytes_per_step": b32}
+    f64, f32 = results["f64"], results["f32"]
+    value = world * cells * K * nwin / (f64["ms"] / 1e3)
+
+    # the kernels' own rate: every tile wet
+    dense = measure_dense(cfg, K, Wm, torch, fp64_tflops, pk["hbm_gbs"], h)
+    d64, d32 = dense["f64"], dense["f32"]
+    roof64 = {"bound": "alu", "achieved": d64["alu"]["achieved"], "peak": fp64_tflops, "unit": "TFLOP/s",
+              "frac": d64["alu"]["achieved"] / fp64_tflops, "traffic": d64["traffic_per_launch"],
+              "kernel": "moses::stage_kernel_list<double,32,8> with its classification launch, one stage, "
+                        "on the all-wet 4096^2 state (488 flops per cell and stage)",
+              "peak_source": "measured FP64 FMA rate (moses_debug_fp64_rate); "
+                             f"{FP64_PEAK_TFLOPS:.3f} TFLOP/s from unit counts and clock",
+              "hbm": {"achieved": d64["hbm"]["achieved"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                      "frac": d64["hbm"]["frac"], "bytes_per_cell_step": 104, "peak_source": pk_src}}
+    roof32 = {"bound": "hbm", "achieved": d32["hbm"]["achieved"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+              "frac": d32["hbm"]["frac"], "traffic": _traffic("f32", h, cells),
+              "kernel": "moses::stage_kernel_list<float,32,8> with its classification launch, one stage, "
+                        "on the all-wet 4096^2 state (52 B per cell-step)",
+              "peak_source": pk_src, "alu": d32["alu"]}
 
     # end to end through the C-ABI with pinned host buffers: per step, upload
     # the state, one step, download the state
@@ -576,33 +739,42 @@ def main():
         el = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": world * cells * Ke / el, "unit": UNIT, "h2d_bytes_per_step": int(Uh.nbytes),
                "d2h_bytes_per_step": int(Uh.nbytes),
-               "calls": "moses_set_conserved + moses_step(1) + moses_get_conserved, pinned host buffers"}
+               "calls": "moses_set_conserved + moses_step(1) + moses_get_conserved, pinned host buffers, "
+                        "on the state at the start of the last quarter of the event"}
     f64["sim"].close()
 
     ens = None if args.no_ensemble else measure_ensemble(K, Wm, rank=rank, world=world, dist=dist, device="cuda")
-
     adj = None if args.no_adjoint else measure_adjoint(torch)
     variants = None if args.no_variants else measure_variants(cfg, K, Wm, torch)
-    dense = None if args.no_variants else measure_dense(cfg, K, Wm, torch)
+    arc = None if args.no_configs else measure_arc_plane(torch)
+    infl = None if args.no_configs else measure_inflow(torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cfg)
         cpu.pop("seconds", None)
 
+    def windows(r):
+        return [{"from_step": sg["from_step"], "wet_tiles": sg["wet_tiles"], "ms_per_step": m / K}
+                for sg, m in zip(r["event"]["segments"], r["win_ms"])]
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
-        "ms_per_step": f64["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": f64["ms"] / (K * nwin), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded spectral DEM and release; see workloads.py)",
         "config": config_dict(cfg, args), "roofline": roof64, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": 4 * K, "clocks": sampler.summary(),
-        "f32": {"value": world * cells * K / (f32["ms"] / 1e3), "ms_per_step": f32["ms"] / K, "dtype": "f32",
-                "roofline": roof32, "gpu_launches": 4 * K},
+        "gpu_launches": 4 * K * nwin, "clocks": sampler.summary(),
+        "windows": windows(f64), "event": f64["event"],
+        "f32": {"value": world * cells * K * nwin / (f32["ms"] / 1e3), "ms_per_step": f32["ms"] / (K * nwin),
+                "dtype": "f32", "roofline": roof32, "gpu_launches": 4 * K * nwin, "windows": windows(f32),
+                "event": f32["event"]},
+        "dense": dense,
+        "fp64_fma_tflops": fp64_tflops,
+        "arc_plane": arc,
+        "inflow": infl,
         "ensemble": ens,
         "adjoint": adj,
         "variants": variants,
-        "dense": dense,
-        "stage_ms": {"f64": f64["stage_ms"], "f32": f32["stage_ms"]},
         "tiles": tiles,
         "stage_source": h,
     }

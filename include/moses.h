@@ -5,7 +5,7 @@
  *
  * What the library computes, per step (Sect. 2.2 and App. A):
  *   dt   = CFL min(dx, dy) / a_max,  a_max = largest per-phase wave speed over
- *          all cells (Sect. 3.1.2, Stage 2: "global maximum wave speed")
+ *          all cells (the CFL reduction of Sect. 3.1.2, Stage 2)
  *   U*   = U^n + dt L(U^n),   U** = U* + dt L(U*),   U^{n+1} = (U^n + U**)/2
  *          (two-step modified Euler, Sect. 2.2)
  *   L    = central (Kurganov-Tadmor) fluxes of Eqs. FluxEqSxi_Topo ..
@@ -286,9 +286,11 @@ int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out
 
 /* ---- Step without device allocation --------------------------------------
  * The paper has no counterpart to this call.  It is for callers that cannot
- * let a library allocate device memory: code that records its work into a
- * CUDA graph, host programs that reserve all device memory in their own pool,
- * processes under a hard device-memory limit.  It advances one FP64 Heun step
+ * let a library allocate device memory: host programs that reserve all device
+ * memory in their own pool (a foreign cudaMalloc fails or fragments it),
+ * processes under a hard device-memory limit, and loops that may not stall
+ * on the allocator (cudaMalloc and cudaFree synchronise the device).  It
+ * advances one FP64 Heun step
  * of a grid of at most MOSES_STATIC_MAX_NX x MOSES_STATIC_MAX_NY cells and
  * calls no cudaMalloc, cudaFree or allocating library routine: its scratch
  * (extended DEM, geometry, padded state, Heun intermediate, control block,
@@ -301,14 +303,22 @@ int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out
  *   t            time of U_in (start of the step); closed / transmissive
  *                boundaries only (no inflow segments); p->precision must be
  *                MOSES_FP64 and p->nu_f 0
- *   dt_out       host pointer receiving the time step taken (the call then
- *                synchronises the stream), or NULL (fully asynchronous)
+ *   dt_out       host pointer receiving the time step taken, or NULL.
+ *                Non-NULL: the call synchronises the stream, reads the time
+ *                step and the device status word, and returns ENONFINITE
+ *                when the input or the result holds a non-finite value.
+ *                NULL: nothing is read back, the call returns as soon as its
+ *                work is queued, and a non-finite result is not reported.
  *   stream       cudaStream_t or NULL
  * The first call on a device looks up that device's copy of the array
- * (cudaGetSymbolAddress); make it before any stream capture.  Every call
- * shares the array, so calls that overlap on the GPU (other streams, other
- * threads) race; serialise them.  Errors (read with moses_last_error(NULL)):
- * EINVAL for sizes beyond the limit or bad arguments, ECUDA. */
+ * (cudaGetSymbolAddress) and keeps the address for the rest of the process;
+ * make that first call before any stream capture, and do not use this call
+ * again on a device after cudaDeviceReset in the same process (the kept
+ * address would be stale).  Every call shares the array and overwrites it, so
+ * calls that overlap on the GPU (other streams, other threads) race;
+ * serialise them.  Errors (read with moses_last_error(NULL)): EINVAL for
+ * sizes beyond the limit or bad arguments, ENONFINITE (dt_out non-NULL
+ * only), ECUDA. */
 #define MOSES_STATIC_MAX_NX 128
 #define MOSES_STATIC_MAX_NY 128
 int moses_step_static(const double *dem_device, int nx, int ny, double dx, double dy,
@@ -330,6 +340,27 @@ int moses_debug_timeout(moses_sim *s, int on);
  * result as an unpoisoned one shows that no stencil reads outside its cells
  * (the canary test of the test suite).  Errors: EINVAL, ECUDA. */
 int moses_debug_poison(moses_sim *s);
+
+/* Testing the arithmetic the stage kernels build on (not in the paper): for
+ * each of the n host values x[k] (1 <= n <= 2^24), out (9 n doubles, host)
+ * receives, plane by plane: the kernels' FP64 reciprocal 1/x, CUDA's 1.0/x,
+ * the kernels' FP64 square root, CUDA's sqrt, the kernels' FP64 reciprocal
+ * square root, CUDA's rsqrt, and the kernels' FP32 reciprocal, square root
+ * and reciprocal square root of (float)x.  The FP64 functions start from the
+ * hardware approximations and take one third-order refinement step each
+ * (series of (1-e)^-1 and (1-d)^-1/2); the reciprocal is defined for x whose
+ * reciprocal is a normal number, the square root gives 0 for x <= 0 or
+ * subnormal.  Uses the current device; allocates and frees a scratch buffer.
+ * Errors (moses_last_error(NULL)): EINVAL, ECUDA. */
+int moses_debug_math(const double *x, int n, double *out);
+
+/* Measuring the FP64 roof the stage kernel's FP64 form runs against (not in
+ * the paper): times `reps` launches (1..1000, after one warm-up) of a kernel
+ * that runs eight independent FP64 FMA chains per thread in registers on
+ * 4 CTAs of 256 threads per SM, and returns the best rate in *tflops
+ * [TFLOP/s, 2 flops per FMA].  Uses the current device and the legacy default
+ * stream.  Errors (moses_last_error(NULL)): EINVAL, ECUDA. */
+int moses_debug_fp64_rate(int reps, double *tflops);
 
 /* Library build identification (architecture, precision forms). */
 const char *moses_version(void);

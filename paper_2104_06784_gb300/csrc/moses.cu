@@ -3,11 +3,12 @@
 // App. A: J_b, Omega_b^-1, basal normal and its derivatives), the initial
 // ghost fill, the exact CFL max-reduction and the FP64 budget reductions.
 // The per-step stage kernels live in stage.cuh (instantiated in
-// stage_f64.cu / stage_f32.cu).
+// stage_f64.cu / stage_f32.cu through stage_launch.cuh).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -498,6 +499,96 @@ int moses_debug_poison(moses_sim *s)
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+namespace {
+// the stage kernels' reciprocal and square roots beside CUDA's own results,
+// one input per thread (moses_debug_math)
+__global__ void math_kernel(const double *x, int n, double *out)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const double v = x[e];
+        const float f = (float)v;
+        out[0 * (long long)n + e] = moses::frcp(v);
+        out[1 * (long long)n + e] = 1.0 / v;
+        out[2 * (long long)n + e] = moses::fsqrt(v);
+        out[3 * (long long)n + e] = sqrt(v);
+        out[4 * (long long)n + e] = moses::frsqrt(v);
+        out[5 * (long long)n + e] = rsqrt(v);
+        out[6 * (long long)n + e] = (double)moses::frcp(f);
+        out[7 * (long long)n + e] = (double)moses::fsqrt(f);
+        out[8 * (long long)n + e] = (double)moses::frsqrt(f);
+    }
+}
+
+// FP64 FMA throughput: eight independent FMA chains per thread, in registers
+// only; b and c arrive at run time so nothing folds.  The sum of the chains
+// is written where no input makes it land (a value no chain reaches), which
+// keeps them live.
+__global__ void fp64_fma_probe_kernel(double *sink, int iters, double b, double c)
+{
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = 1e-3 * threadIdx.x + k;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = fma(a[k], b, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) t += a[k];
+    if (t == -1.0) sink[0] = t;
+}
+}  // namespace
+
+int moses_debug_fp64_rate(int reps, double *tflops)
+{
+    moses_sim *s = nullptr;  // errors go to moses_last_error(NULL)
+    if (!tflops || reps < 1 || reps > 1000) return fail(s, MOSES_EINVAL, "need tflops and 1 <= reps <= 1000");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    double *sink = nullptr;
+    CK(cudaMalloc(&sink, sizeof(double)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int blocks = sms * 4, threads = 256, iters = 4096;
+    double best = 0.0;
+    for (int r = 0; r <= reps && e == cudaSuccess; r++) {  // r = 0: warm-up
+        cudaEventRecord(e0);
+        fp64_fma_probe_kernel<<<blocks, threads>>>(sink, iters, 1.0000000001, 1e-12);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        const double fl = 2.0 * 8.0 * iters * (double)blocks * threads;
+        if (e == cudaSuccess && r > 0 && ms > 0.0f) best = std::max(best, fl / (ms * 1e-3) / 1e12);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return fail(s, MOSES_ECUDA, std::string("moses_debug_fp64_rate: ") + cudaGetErrorString(e));
+    *tflops = best;
+    return MOSES_OK;
+}
+
+int moses_debug_math(const double *x, int n, double *out)
+{
+    moses_sim *s = nullptr;  // errors go to moses_last_error(NULL)
+    if (!x || !out || n < 1 || n > (1 << 24)) return fail(s, MOSES_EINVAL, "need x, out and 1 <= n <= 2^24");
+    double *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(double) * 10 * (size_t)n));
+    cudaError_t e = cudaMemcpy(d, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        math_kernel<<<grid_for(n), 256>>>(d, n, d + n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + n, sizeof(double) * 9 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(s, MOSES_ECUDA, std::string("moses_debug_math: ") + cudaGetErrorString(e));
     return MOSES_OK;
 }
 
@@ -1124,13 +1215,14 @@ int moses_get_budget(moses_sim *s, double out[MOSES_BUDGET_LEN])
 
 // ---------------------------------------------------------------------------
 // No-allocation step (moses_step_static).  Some callers cannot let a library
-// call cudaMalloc: code that records its work into a CUDA graph, hosts that
-// pre-reserve all device memory in their own pool, or processes that run
-// under a hard device-memory limit.  For them, one FP64 Heun step of a small
-// grid runs with all of its scratch (extended DEM, geometry planes, padded
-// state, Heun intermediate, control block) in the statically sized device
-// array below, which every GPU that loads this library holds until exit.
-// Every call shares the array: calls that overlap on the GPU race.
+// call cudaMalloc: hosts that pre-reserve all device memory in their own pool
+// (a foreign allocation fails or fragments it), processes that run under a
+// hard device-memory limit, and loops that may not stall on the allocator
+// (cudaMalloc and cudaFree synchronise the device).  For them, one FP64 Heun
+// step of a small grid runs with all of its scratch (extended DEM, geometry
+// planes, padded state, Heun intermediate, control block) in the statically
+// sized device array below, which every GPU that loads this library holds
+// until exit.  Every call shares the array: calls that overlap on the GPU race.
 
 namespace {
 
@@ -1143,7 +1235,10 @@ static_assert(sizeof(Ctl) <= kStaticCtl * sizeof(double), "control block does no
 
 static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
 
-double *g_static_ptr[64] = {};
+// this process's device address of each device's copy of the array, looked up
+// once per device (atomics: two host threads making a first call on the same
+// device both look it up and store the same value)
+std::atomic<double *> g_static_ptr[64];
 
 __global__ void static_ctl_init_kernel(Ctl *ctl, double t)
 {
@@ -1171,15 +1266,16 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(s, MOSES_EINVAL, "device ordinal out of range");
-    if (!g_static_ptr[dev]) {
+    double *base = g_static_ptr[dev].load(std::memory_order_acquire);
+    if (!base) {
         // host code may not use the array's name as a device address: ask the
         // runtime for this device's copy (first call per device; do it before
         // any stream capture)
         void *ptr = nullptr;
         CK(cudaGetSymbolAddress(&ptr, g_static_scratch));
-        g_static_ptr[dev] = (double *)ptr;
+        base = (double *)ptr;
+        g_static_ptr[dev].store(base, std::memory_order_release);
     }
-    double *base = g_static_ptr[dev];
     cudaStream_t st = (cudaStream_t)stream;
     const int pitch = ((nx + 2 * GH) + 31) / 32 * 32;
     const long long plane = (long long)pitch * (ny + 2 * GH);
@@ -1227,8 +1323,15 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     pack_kernel<double><<<grid_for(6 * n), 256, 0, st>>>(U, nullptr, U_out_device, nx, ny, pitch, plane);
     CK(cudaGetLastError());
     if (dt_out) {
-        CK(cudaMemcpyAsync(dt_out, &ctl->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+        // the time step and the status word the stage kernels raise (a
+        // non-finite value in the input or the result) in one copy
+        Ctl h;
+        CK(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        *dt_out = h.dt;
+        if (h.status & STATUS_TIMEOUT) return fail(s, MOSES_ETIMEOUT, "moses_step_static: a bounded device-side wait gave up");
+        if (h.status & STATUS_NONFINITE)
+            return fail(s, MOSES_ENONFINITE, "moses_step_static: the state or the time step became non-finite");
     }
     return MOSES_OK;
 }

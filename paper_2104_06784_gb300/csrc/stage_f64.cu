@@ -1,130 +1,25 @@
-// stage_f64.cu -- instantiations and launcher of the double stage kernel.
-#include <cuda_runtime.h>
-
-#include "stage.cuh"
+// stage_f64.cu -- the stage kernels and their launchers for the double element type.
+#include "stage_launch.cuh"
 
 namespace moses {
-namespace {
 
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
-int launch_tile(const StageArgs<T> &a, cudaStream_t st)
-{
-    constexpr size_t smem = stage_smem_bytes<T, TX, TY, VIS>();
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC, VIS, CU, WENO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return -1;
-        attr_set[dev] = true;
-    }
-    const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-    stage_kernel<T, TX, TY, REC, VIS, CU, WENO><<<grid, TX * TY, smem, st>>>(a);
-    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
-}
-
-// The stepping launches of the plain form: classify_kernel over every tile
-// (classify_flags_kernel in a combining stage), then stage_kernel_list on a
-// grid of resident CTAs over the listed tiles.
-template <typename T, int TX, int TY, bool REC = false>
-int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
-{
-    constexpr size_t smem = stage_smem_bytes<T, TX, TY>();
-    static int resident[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return -1;
-    if (!resident[dev]) {
-        int per_sm = 0, n_sm = 0;
-        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY, REC>, TX * TY, smem) !=
-                cudaSuccess ||
-            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
-            return -1;
-        resident[dev] = per_sm * n_sm;
-    }
-    static_assert(TX == 32, "classify_kernel works on 32-wide strips");
-    const int gx = (a.nx + TX - 1) / TX;
-    if (a.tw_prev && a.stage == 2) {  // a combining stage: from the flags of the stage before
-        const int gy = (a.ny + TY - 1) / TY;
-        classify_flags_kernel<T, TY><<<(gx * gy + kFlagThreads - 1) / kFlagThreads, kFlagThreads, 0, st>>>(a, gx, gy);
-    } else {
-        classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
-    }
-    stage_kernel_list<T, TX, TY, REC><<<resident[dev], TX * TY, smem, st>>>(a, gx);
-    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
-}
-
-}  // namespace
-
-// tile 0: 32 x 8 cells (256 threads); tile 1: 32 x 4; tile 2: 32 x 16
 template <>
-int launch_stage<double>(const StageArgs<double> &a_in, int tile, void *stream)
+int launch_stage<double>(const StageArgs<double> &a, int tile, void *stream)
 {
-    cudaStream_t st = (cudaStream_t)stream;
-    // the model options (viscous term, central-upwind flux, WENO): one tile shape
-    const bool vis = a_in.ph.nu_f > 0.0, cu = a_in.ph.scheme == 1, weno = a_in.ph.recon == 1;
-    if (a_in.wl && !vis && !cu && !weno && !a_in.debug_stage) {
-        switch (tile) {
-        case 1: return launch_tile_list<double, 32, 4>(a_in, st);
-        case 2: return launch_tile_list<double, 32, 16>(a_in, st);
-        default: return launch_tile_list<double, 32, 8>(a_in, st);
-        }
-    }
-    StageArgs<double> a = a_in;  // every tile tests itself
-    a.wl = nullptr;
-    a.wl_n = nullptr;
-    if (weno) {
-        if (cu)
-            return vis ? launch_tile<double, 32, 8, false, true, true, true>(a, st)
-                       : launch_tile<double, 32, 8, false, false, true, true>(a, st);
-        return vis ? launch_tile<double, 32, 8, false, true, false, true>(a, st)
-                   : launch_tile<double, 32, 8, false, false, false, true>(a, st);
-    }
-    if (cu)
-        return vis ? launch_tile<double, 32, 8, false, true, true>(a, st) : launch_tile<double, 32, 8, false, false, true>(a, st);
-    if (vis) return launch_tile<double, 32, 8, false, true>(a, st);
-    switch (tile) {
-    case 1: return launch_tile<double, 32, 4>(a, st);
-    case 2: return launch_tile<double, 32, 16>(a, st);
-    default: return launch_tile<double, 32, 8>(a, st);
-    }
+    return launch_stage_impl<double>(a, tile, stream);
 }
 
 template <>
 int launch_stage_rec<double>(const StageArgs<double> &a, void *stream)
 {
-    if (!a.rec) return -1;
-    if (a.wl) return launch_tile_list<double, 32, 8, true>(a, (cudaStream_t)stream);
-    return launch_tile<double, 32, 8, true>(a, (cudaStream_t)stream);
+    return launch_stage_rec_impl<double>(a, stream);
 }
 
 template <>
 int launch_stage_batch<double>(const StageArgs<double> *args_device, int nsim, const BatchStrip *strips_device, int nstrips,
-                          BatchTile *list, unsigned int *list_n, void *stream)
+                            BatchTile *list, unsigned int *list_n, void *stream)
 {
-    constexpr size_t smem = stage_smem_bytes<double, 32, 8>();
-    static int resident[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return -1;
-    if (!resident[dev]) {
-        int per_sm = 0, n_sm = 0;
-        if (cudaFuncSetAttribute(stage_kernel_batch_list<double, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_batch_list<double, 32, 8>, 256, smem) !=
-                cudaSuccess ||
-            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
-            return -1;
-        resident[dev] = per_sm * n_sm;
-    }
-    if (nstrips <= 0) return 0;
-    cudaStream_t st = (cudaStream_t)stream;
-    classify_kernel_batch<double><<<nstrips, 32 * kStripWarps, 0, st>>>(args_device, strips_device, list, list_n);
-    stage_kernel_batch_list<double, 32, 8><<<resident[dev], 256, smem, st>>>(args_device, list, list_n, nsim);
-    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+    return launch_stage_batch_impl<double>(args_device, nsim, strips_device, nstrips, list, list_n, stream);
 }
 
 }  // namespace moses

@@ -95,6 +95,8 @@ SIGNATURES = [
     ("moses_version", C.c_char_p, []),
     ("moses_debug_timeout", C.c_int, [_vp, C.c_int]),
     ("moses_debug_poison", C.c_int, [_vp]),
+    ("moses_debug_math", C.c_int, [_dp, C.c_int, _dp]),
+    ("moses_debug_fp64_rate", C.c_int, [C.c_int, _dp]),
 ]
 
 
@@ -351,6 +353,27 @@ def from_config(cfg: dict, precision: int = FP64, stream=None) -> Sim:
         f = cfg["inflow"]
         s.set_inflow(f["side"], f["i0"], f["i1"], f["t"], f["Q"], f["phi"])
     return s
+
+
+def debug_math(x) -> dict:
+    """The stage kernels' reciprocal and square roots of the values x, beside
+    CUDA's own (moses_debug_math)."""
+    x = _f64(x).ravel()
+    out = np.empty((9, x.size))
+    rc = lib().moses_debug_math(_p(x), int(x.size), _p(out))
+    if rc != 0:
+        raise MosesError(rc, lib().moses_last_error(None).decode())
+    names = ("frcp", "cuda_rcp", "fsqrt", "cuda_sqrt", "frsqrt", "cuda_rsqrt", "frcp32", "fsqrt32", "frsqrt32")
+    return dict(zip(names, out))
+
+
+def fp64_rate(reps: int = 5) -> float:
+    """Measured FP64 FMA rate of the current device [TFLOP/s] (moses_debug_fp64_rate)."""
+    t = C.c_double()
+    rc = lib().moses_debug_fp64_rate(int(reps), C.byref(t))
+    if rc != 0:
+        raise MosesError(rc, lib().moses_last_error(None).decode())
+    return t.value
 
 
 def version() -> str:

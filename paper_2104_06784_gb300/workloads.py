@@ -190,6 +190,14 @@ def triangular_hydrograph(q_peak: float = 800.0, t_peak: float = 60.0, t_end: fl
     return t, Q, phi
 
 
+def release_volume(h: np.ndarray, dem: np.ndarray, dx: float) -> float:
+    """Volume of a layer of normal thickness h over the DEM: sum J h dx dy,
+    with J = sqrt(1 + b_X^2 + b_Y^2) from central differences of the DEM (the
+    area of the bed surface over a cell is J dx dy)."""
+    gy, gx = np.gradient(dem, dx)
+    return float((h * np.sqrt(1.0 + gx * gx + gy * gy)).sum() * dx * dx)
+
+
 def slope_deg(dem: np.ndarray, dx: float) -> np.ndarray:
     """Terrain slope angle from numpy's gradient (used only to place releases)."""
     gy, gx = np.gradient(dem, dx)
@@ -217,8 +225,9 @@ def large_release_config(n: int = 4096, dx: float = 10.0, seed: int = 0, ny: int
                          volume: float = 2.5e7, radius_cells: float = 43.0, **over) -> dict:
     """Spectral 1/f^2.2 DEM (1500 m relief) with one carved valley; a 2.5e7 m^3
     parabolic-cap release of radius 43 cells centred on the seeded cell whose
-    slope is nearest 35 deg within 30-40 deg; solid fraction U(0.55, 0.65) per
-    cell; transmissive boundaries; CFL 0.1; 10000 steps."""
+    slope is nearest 35 deg within 30-40 deg (the volume counted normal to the
+    bed, sum J h dx dy); solid fraction U(0.55, 0.65) per cell; transmissive
+    boundaries; CFL 0.1; 10000 steps."""
     ny = ny or n
     nx = n
     relief = 1500.0 * min(1.0, max(nx, ny) / 4096.0) if (nx < 4096) else 1500.0
@@ -237,8 +246,7 @@ def large_release_config(n: int = 4096, dx: float = 10.0, seed: int = 0, ny: int
     score = np.abs(sl[cand[:, 0], cand[:, 1]] - 35.0) + 1e-3 * rng.random(len(cand))
     jc, ic = cand[int(np.argmin(score))]
     shape = parabolic_cap(nx, ny, dx, dx, ic, jc, radius_cells, 1.0)
-    hmax = volume / (shape.sum() * dx * dx)
-    h = shape * hmax
+    h = shape * (volume / release_volume(shape, dem, dx))
     phi = rng.uniform(0.55, 0.65, size=(ny, nx))
     p = default_params(cfl=0.1, bc=(BC_TRANSMISSIVE,) * 4)
     p.update(over)
@@ -284,18 +292,27 @@ def ensemble_sides(n: int = 256, seed: int = 0, lo: int = 64, hi: int = 1024) ->
 
 def ensemble_config(n: int = 256, seed: int = 0, dx: float = 5.0, lo: int = 64, hi: int = 1024) -> list[dict]:
     """Independent scenarios on uneven square grids: each a seeded spectral
-    DEM (beta 2.2, relief proportional to the side), basal friction U(15, 30)
-    deg, drag U(1e-4, 1e-2) 1/s, release volume U(1e4, 1e6) m^3 as a
-    parabolic cap of radius N/16 cells at the grid centre, 3000 steps, FP32."""
+    DEM (beta 2.2, relief 0.15 N dx, rolled off below 320 m wavelength like
+    the large-release terrain: median slopes 14-29 deg, 90th percentiles
+    21-46 deg from the smallest to the largest grid), basal friction U(15, 30)
+    deg, drag U(1e-4, 1e-2) 1/s, release volume U(1e4, 1e6) m^3 (normal to
+    the bed, sum J h dx dy) as a parabolic cap at the grid centre whose radius
+    is N/16 cells or, for a large volume on a small grid, the radius of a cap
+    30 m high (at most N/3 cells), 3000 steps, FP32.  (Steeper terrain --
+    relief 0.3 N dx with an 80 m roll-off, median slopes up to 70 deg and bed
+    curvature up to 0.4 / m -- and radius N/16 throughout, which piles 1e6 m^3
+    into a tower a kilometre high on a 64 x 64 grid, put thin fluid films in
+    gullies with 60-70 deg walls, where the step runs away.)"""
     rng = np.random.default_rng(seed + 31337)
     out = []
     for k, N in enumerate(ensemble_sides(n, seed, lo, hi)):
-        dem = spectral_dem(N, N, dx, 2.2, 0.3 * N * dx, seed * 100003 + k, band_m=16 * dx)
+        dem = spectral_dem(N, N, dx, 2.2, 0.15 * N * dx, seed * 100003 + k, band_m=320.0)
         d_b = rng.uniform(15.0, 30.0)
         c_d = rng.uniform(1e-4, 1e-2)
         V = rng.uniform(1e4, 1e6)
-        shape = parabolic_cap(N, N, dx, dx, N // 2, N // 2, N / 16.0, 1.0)
-        h = shape * (V / (shape.sum() * dx * dx))
+        r30 = math.sqrt(2.0 * V / (math.pi * 30.0)) / dx
+        shape = parabolic_cap(N, N, dx, dx, N // 2, N // 2, min(max(N / 16.0, r30), N / 3.0), 1.0)
+        h = shape * (V / release_volume(shape, dem, dx))
         p = default_params(delta_b_deg=d_b, c_d=c_d, cfl=0.1, bc=(BC_TRANSMISSIVE,) * 4)
         out.append(dict(name=f"ensemble member {k} ({N}x{N})", dem=dem, dx=dx, dy=dx, params=p, h=h,
                         phi_s=np.full((N, N), 0.6), steps=3000))

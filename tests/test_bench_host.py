@@ -1,5 +1,5 @@
 """Host-side logic of bench.py (no GPU): the wet-tile fraction that the line
-reports beside the roofline, the roofline's bytes of a masked step, and the
+reports per window, the roofline's bytes per computed cell-step, and the
 clock sampler's window summary."""
 import time
 
@@ -57,10 +57,9 @@ def test_clock_summary_window_and_bracketing():
     assert s.summary()["reasons"] == ["unsampled"]
 
 
-def test_step_bytes_of_a_masked_step():
-    """The roofline's bytes of one masked step: the wet test reads 16 B of
-    every cell; the cells of tiles with work add the 13-word cell-step
-    traffic (FP64 104 B, FP32 52 B)."""
-    assert bench.step_bytes(1000, 0.0, 8) == 16 * 1000
-    assert bench.step_bytes(1000, 1.0, 8) == (16 + 104) * 1000
-    assert bench.step_bytes(1000, 0.5, 4) == 16 * 1000 + 26 * 1000
+def test_roofline_bytes_per_computed_cell_step():
+    """The roofline's HBM bytes: 13 words per computed cell-step (read U^n, write
+    U^{n+1}, read the bed), FP64 104 B and FP32 52 B."""
+    assert bench.cell_step_gbs(1e9, 8, 1.0) == 104.0
+    assert bench.cell_step_gbs(1e9, 4, 0.5) == 104.0
+    assert bench._traffic("f64", "no-such-source", 10) is None

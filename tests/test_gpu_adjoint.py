@@ -178,7 +178,7 @@ def _oracle_loss(cfg, params, dts, hs_t, J, h0=None):
 @pytest.mark.parametrize("case", ["spectral64", "arc", "inflow"])
 def test_misfit_gradient_matches_fp64_central_differences(case):
     if case == "spectral64":
-        cfg, N, C = W.large_release_config(n=64, dx=5.0, seed=7, volume=2e4, radius_cells=6), 80, 9
+        cfg, N, C = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6), 80, 9
     elif case == "arc":
         # a pile centred on a cell column stays mirror-symmetric, and across the
         # axis the two x-momentum differences are equal: minmod is at a tie,
@@ -205,19 +205,21 @@ def test_misfit_gradient_matches_fp64_central_differences(case):
     if case == "inflow":
         return
     # release thickness: directional derivative along a relative perturbation
-    # of the pile.  It moves the wet front, where cells cross the dry threshold
-    # whatever the step, so the differences carry a small noise of their own
-    # (a few 1e-6 relative); the bound is set above it.
+    # of the pile.  It moves the wet front, where a cell that crosses the dry
+    # threshold within the step puts a jump into L; three step sizes whose
+    # differences agree to 1e-6 show that none did, and the adjoint must then
+    # meet them at the tolerance of the other gradients.
     v = np.random.default_rng(5).standard_normal(cfg["h"].shape) * cfg["h"]
     fdh = [(_oracle_loss(cfg, p0, dts, hs_t, J, cfg["h"] + s * v) - _oracle_loss(cfg, p0, dts, hs_t, J, cfg["h"] - s * v))
-           / (2 * s) for s in (1e-6, 1e-7)]
+           / (2 * s) for s in (1e-6, 1e-7, 1e-8)]
     adh = float((r["g_release_h"] * v).sum())
-    assert abs(fdh[0] - fdh[1]) <= 5e-5 * abs(fdh[0]), ("finite differences cross a kink", adh, fdh)
-    assert abs(adh - fdh[1]) <= 5e-5 * abs(fdh[1]), (adh, fdh)
+    for a, b in ((0, 1), (1, 2)):
+        assert abs(fdh[a] - fdh[b]) <= 1e-6 * abs(fdh[a]), ("finite differences cross a kink", adh, fdh)
+    assert abs(adh - fdh[1]) <= 1e-5 * abs(fdh[1]), (adh, fdh)
 
 
 def test_misfit_gradient_does_not_depend_on_checkpoint_interval():
-    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2e4, radius_cells=6)
+    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6)
     hs_t, _, _ = _misfit_setup(cfg, 40)
     res = [moses.from_config(cfg).adjoint_misfit(40, hs_t, ckpt_every=C) for C in (1, 6, 40)]
     for r in res[1:]:
@@ -227,7 +229,7 @@ def test_misfit_gradient_does_not_depend_on_checkpoint_interval():
 
 
 def test_misfit_fp32_gradient_tracks_fp64():
-    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2e4, radius_cells=6)
+    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6)
     hs_t, _, _ = _misfit_setup(cfg, 80)
     r64 = moses.from_config(cfg).adjoint_misfit(80, hs_t, ckpt_every=9)
     r32 = moses.from_config(cfg, precision=moses.FP32).adjoint_misfit(80, hs_t, ckpt_every=9)
@@ -237,7 +239,7 @@ def test_misfit_fp32_gradient_tracks_fp64():
 
 def test_autograd_function():
     torch = pytest.importorskip("torch")
-    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2e4, radius_cells=6)
+    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6)
     hs_t, _, _ = _misfit_setup(cfg, 40)
     h0 = torch.tensor(cfg["h"], dtype=torch.float64, requires_grad=True)
     db = torch.tensor(25.0, dtype=torch.float64, requires_grad=True)

@@ -1,12 +1,15 @@
 """moses_step_static: the step for callers that cannot allocate device memory.
 
-Callers that record their work into a CUDA graph, that keep all device memory
-in their own pool, or that run under a hard device-memory limit cannot let a
-library call cudaMalloc.  moses_step_static gives them one FP64 step with its
-scratch in a statically sized device array.  This test drives it through the
-C-ABI with device buffers it owns and checks two calls in a row against the
-allocating path (moses_create + moses_step) at the FP64 parity tolerance of the
-other GPU tests.  It lives in a file of its own that pytest collects last.
+Callers that keep all device memory in their own pool, that run under a hard
+device-memory limit, or whose loop may not stall on the allocator (cudaMalloc
+synchronises the device) cannot let a library call cudaMalloc.
+moses_step_static gives them one FP64 step with its scratch in a statically
+sized device array.  These tests drive it through the C-ABI with device
+buffers they own and check two calls in a row against the allocating path
+(moses_create + moses_step) at the FP64 parity tolerance of the other GPU
+tests, with closed and with transmissive sides, in place (output buffer = input
+buffer), and that a non-finite input is reported.  They live in a file of their
+own that pytest collects last.
 """
 import ctypes as C
 
@@ -33,18 +36,21 @@ def _call(L, dem_d, nx, ny, dx, par, Uin, Uout, t, stream):
     return rc, dt.value
 
 
-def test_static_step_matches_the_allocating_step_on_two_calls():
+@pytest.mark.parametrize("bc,in_place", [((0, 0, 0, 0), False), ((1, 1, 1, 1), False), ((0, 1, 1, 0), True)])
+def test_static_step_matches_the_allocating_step_on_two_calls(bc, in_place):
     torch = pytest.importorskip("torch")
     L = moses.lib()
     nx, ny = 75, 61  # several 32 x 8 tiles with ragged tails, inside the 128 x 128 limit
     cfg = W.release_config(nx=nx, ny=ny, cfl=0.3)
+    cfg["params"] = dict(cfg["params"], bc=bc)
     ref = moses.from_config(cfg)
+    ref.step(40)  # the pile moving, so that the transmissive sides see flow
     dem_d = torch.tensor(cfg["dem"], dtype=torch.float64, device="cuda")
     Uin = torch.tensor(ref.get_conserved(), dtype=torch.float64, device="cuda")
-    Uout = torch.empty_like(Uin)
+    Uout = Uin if in_place else torch.empty_like(Uin)
     par = moses.Params.from_dict(cfg["params"])
     stream = torch.cuda.current_stream().cuda_stream
-    t = 0.0
+    t = ref.budget()["t"]
     for call in range(2):
         rc, dt = _call(L, dem_d, nx, ny, cfg["dx"], par, Uin, Uout, t, stream)
         assert rc == 0, L.moses_last_error(None).decode()
@@ -53,7 +59,30 @@ def test_static_step_matches_the_allocating_step_on_two_calls():
         assert err <= TOL64, f"call {call + 1}: static step departs from moses_step by {err}"
         assert abs((t + dt) - t_ref) <= 1e-12 * t_ref
         t += dt
-        Uin.copy_(Uout)
+        if not in_place:
+            Uin.copy_(Uout)
+
+
+def test_static_step_reports_a_non_finite_input():
+    torch = pytest.importorskip("torch")
+    L = moses.lib()
+    nx, ny = 40, 24
+    cfg = W.release_config(nx=nx, ny=ny, cfl=0.3)
+    ref = moses.from_config(cfg)
+    U = torch.tensor(ref.get_conserved(), dtype=torch.float64, device="cuda")
+    U[1, ny // 2, nx // 2] = float("nan")
+    dem_d = torch.tensor(cfg["dem"], dtype=torch.float64, device="cuda")
+    par = moses.Params.from_dict(cfg["params"])
+    rc, _ = _call(L, dem_d, nx, ny, cfg["dx"], par, U, torch.empty_like(U), 0.0, torch.cuda.current_stream().cuda_stream)
+    assert rc == moses.MOSES_ENONFINITE
+    assert b"non-finite" in L.moses_last_error(None)
+    # the next call on a finite state succeeds: the shared scratch starts clean
+    U2 = torch.tensor(ref.get_conserved(), dtype=torch.float64, device="cuda")
+    out = torch.empty_like(U2)
+    rc, _ = _call(L, dem_d, nx, ny, cfg["dx"], par, U2, out, 0.0, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, L.moses_last_error(None).decode()
+    ref.step(1)
+    assert _rel_maxnorm(out.cpu().numpy(), ref.get_conserved()) <= TOL64
 
 
 def test_static_step_rejects_grids_beyond_its_scratch():
