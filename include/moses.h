@@ -69,9 +69,21 @@ typedef struct {
     double eps_chi;      /* epsilon^chi in front of kappa in p_b (1 in SI)        */
     double rho_s, rho_f; /* densities; alpha_rho = rho_f / rho_s                 */
     double delta_b_deg;  /* basal friction angle delta_b (Sect. 3.1.2 (a))        */
-    double phi_int_deg;  /* internal friction angle; only k_mode = 1 would use it */
-    int k_mode;          /* 0: earth-pressure coefficient 1 as in App. A (only
-                            value accepted)                                       */
+    double phi_int_deg;  /* internal friction angle phi_int (k_mode 1 only)       */
+    int k_mode;          /* 0: earth-pressure coefficient 1, the solid pressure of
+                            App. A (below Eq. FluxEqFeta_Topo); 1: Savage-Hutter
+                            coefficients K_act/pass = 2 sec^2(phi_int) (1 -/+
+                            sqrt(1 - cos^2(phi_int) sec^2(delta_b))) - 1 on the
+                            solid pressure of each direction and the solid
+                            celerity: a cell is passive where it and its two
+                            neighbours along the axis carry solid and the solid
+                            velocity along the axis drops by more than
+                            1e-6 (|v+| + |v-|) + 1e-6 m/s, active otherwise;
+                            each side of a face takes its cell's K; the CFL
+                            celerity takes K_pass.  Needs delta_b <= phi_int
+                            < 90 deg, the central flux, minmod and nu_f = 0;
+                            not accepted by moses_batch_create or
+                            moses_step_static                                    */
     double c_d;          /* interphase drag c_D [s^-1] (Eqs. Src_v_Topo, SrcF_v)  */
     double nu_f;         /* fluid viscosity eps/N_R [m^2 s^-1] (Eq. SrcF_vis_Topo);
                             > 0 runs the 32 x 8 viscous form of the stage; not
@@ -263,15 +275,20 @@ void moses_batch_destroy(moses_batch *b);
  * segment is recomputed before it is swept backwards.
  *   hs_target    nx*ny target solid thickness [m] (host)
  *   loss         L [m^4]; may be NULL
- *   g_params     [0] dL/d delta_b per degree, [1] dL/d phi_int (0: the
- *                model has no internal friction, k_mode 0), [2] dL/d c_D
+ *   g_params     [0] dL/d delta_b per degree (through tan(delta_b) and, with
+ *                k_mode 1, through K_act and K_pass), [1] dL/d phi_int per
+ *                degree (k_mode 1; 0 for k_mode 0, whose model has no
+ *                internal friction), [2] dL/d c_D
  *   g_state0     6*nx*ny dL/dU at the start (host) or NULL
  *   g_release_h  nx*ny dL/dh of the release thickness (host) or NULL, with
  *                release_phi the release's solid fraction (NULL: U1/(U1+U4))
  *   timing_ms    [0] forward run, [1] recompute + backward sweep (CUDA
  *                events), or NULL
- * Afterwards the state and the time are those at the end of the forward run.
- * Not available with nu_f > 0.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+ * The regime of the earth-pressure coefficient (k_mode 1) is a kink like the
+ * others: the derivative holds it fixed.  Afterwards the state and the time
+ * are those at the end of the forward run.  Not available with nu_f > 0; with
+ * k_mode 1 it needs delta_b < phi_int.  Errors: EINVAL, ESTATE, ENOMEM,
+ * ECUDA. */
 int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double *hs_target, double *loss,
                          double g_params[3], double *g_state0, double *g_release_h, const double *release_phi,
                          double timing_ms[2]);
@@ -279,8 +296,10 @@ int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double 
 /* Adjoint of one stage at the current state (the reverse of moses_stage with
  * the time step dt held fixed): lam_in = (dS/dU)^T lam_out, both 6*nx*nx
  * doubles on the host in the plane order of moses_get_conserved;
- * g_param[0..1] (may be NULL) receive lam_out . dS/d tan(delta_b) and
- * lam_out . dS/d c_D.  For stage-level gradient checks. */
+ * g_param[0..2] (may be NULL) receive lam_out . dS/d tan(delta_b) (with
+ * k_mode 1 including its effect on K_act and K_pass), lam_out . dS/d c_D and
+ * lam_out . dS/d phi_int [per radian; 0 for k_mode 0].  For stage-level
+ * gradient checks. */
 int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out, double *lam_in,
                         double *g_param);
 

@@ -54,7 +54,8 @@
  *       direction and the solid wave speed.  Per cell and direction:
  *       K_pass where the cell and its two neighbours along that axis carry
  *       solid (U1 > J h_dry) and the central difference of the solid
- *       velocity along the axis is negative (compression), K_act otherwise;
+ *       velocity along the axis is negative beyond a dead band of 1e-6 of
+ *       the two speeds plus 1e-6 m/s (compression), K_act otherwise;
  *       each side of a face takes its own cell's coefficient.  The CFL wave
  *       speed takes K_pass (the larger).  k_mode = 0: K = 1, the paper's.
  *   R11 inflow ghost state at critical depth for the unit discharge Q/W.
@@ -357,7 +358,7 @@ static void earth_pressure(const orc_params *p, double *Ka, double *Kp)
 /* K of cell k for direction d (0: xi, 1: eta), its neighbours along that
    axis km (behind) and kp (ahead): K_pass where all three carry solid
    (U1 > J h_dry) and the solid velocity along the axis (v_xi = v_X,
-   v_eta = v_Y, R2) is smaller ahead than behind, else K_act */
+   v_eta = v_Y, R2) is definitely smaller ahead than behind, else K_act */
 static double cell_earth_pressure(const orc_sim *s, double *const U[6], long km, long k, long kp, int d,
                                   double Ka, double Kp)
 {
@@ -366,7 +367,10 @@ static double cell_earth_pressure(const orc_sim *s, double *const U[6], long km,
     if (!(U[0][km] > s->gc[km].J * hd) || !(U[0][k] > s->gc[k].J * hd) || !(U[0][kp] > s->gc[kp].J * hd))
         return Ka;
     double vm = U[1 + d][km] / U[0][km], vp = U[1 + d][kp] / U[0][kp];
-    return (vp - vm < 0.0) ? Kp : Ka;
+    /* compression needs a definite sign: a drop of more than 1e-6 of the two
+       speeds plus 1e-6 m/s (a cell between two neighbours at rest, or on a
+       mirror line, is not compressed by rounding noise) */
+    return (vp - vm < -(1e-6 * (fabs(vp) + fabs(vm)) + 1e-6)) ? Kp : Ka;
 }
 
 /* ------------------------------------------------------------------------ */

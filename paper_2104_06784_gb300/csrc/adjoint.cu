@@ -20,25 +20,32 @@ namespace {
 
 constexpr int ATX = 32, ATY = 8;
 
-template <typename T>
-int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
+template <typename T, bool KM>
+int launch_adj_face(const AdjArgs<T> &q, cudaStream_t st)
 {
     static bool attr[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    constexpr size_t smB = FaceAdjSmem<T, ATX, ATY>::bytes;
+    constexpr size_t smB = FaceAdjSmem<T, ATX, ATY, KM>::bytes;
     if (dev >= 0 && dev < 64 && !attr[dev]) {
         // the largest shared-memory carve-out, so that three FP32 CTAs fit on an SM
-        if (cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        if (cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smB) != cudaSuccess ||
+            cudaFuncSetAttribute(adj_face_kernel<T, ATX, ATY, KM>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return -1;
         attr[dev] = true;
     }
     const dim3 grid((q.f.nx + ATX - 1) / ATX, (q.f.ny + ATY - 1) / ATY);
+    adj_face_kernel<T, ATX, ATY, KM><<<grid, ATX * ATY, smB, st>>>(q);
+    return 0;
+}
+
+template <typename T>
+int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
+{
     adj_cell_kernel<T><<<dim3((q.f.nx + 31) / 32, (q.f.ny + 7) / 8), 256, 0, st>>>(q);
-    adj_face_kernel<T, ATX, ATY><<<grid, ATX * ATY, smB, st>>>(q);
+    if ((q.f.ph.k_mode == 1 ? launch_adj_face<T, true>(q, st) : launch_adj_face<T, false>(q, st)) != 0) return -1;
     const int nfold = 6 * (2 * q.f.nx + 2 * q.f.ny);
     adj_fold_kernel<T><<<(nfold + 255) / 256, 256, 0, st>>>(q);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
@@ -115,6 +122,25 @@ struct DevBuf {
     ~DevBuf() { cudaFree(p); }
 };
 
+// Partial derivatives of the Savage-Hutter coefficients (reading R10) with
+// respect to phi_int ([0]) and delta_b ([1]), in 1/rad; 0 for k_mode 0.  With
+// c = cos(phi_int), e = cos(delta_b), r = sqrt(1 - c^2 / e^2) and
+// K = 2 (1 -/+ r) / c^2 - 1:
+//   dK/dphi   = sin(phi) (4 (1 -/+ r) / c^3 -/+ 2 / (c e^2 r)),
+//   dK/ddelta = +/- 2 sin(delta) / (e^3 r)   (K_act: +, K_pass: -).
+void earth_pressure_partials(const moses_params &p, double dKa[2], double dKp[2])
+{
+    dKa[0] = dKa[1] = dKp[0] = dKp[1] = 0.0;
+    if (p.k_mode != 1) return;
+    const double ph = p.phi_int_deg * M_PI / 180.0, de = p.delta_b_deg * M_PI / 180.0;
+    const double c = cos(ph), e = cos(de);
+    const double r = sqrt(1.0 - c * c / (e * e));
+    dKa[0] = sin(ph) * (4.0 * (1.0 - r) / (c * c * c) - 2.0 / (c * e * e * r));
+    dKp[0] = sin(ph) * (4.0 * (1.0 + r) / (c * c * c) + 2.0 / (c * e * e * r));
+    dKa[1] = 2.0 * sin(de) / (e * e * e * r);
+    dKp[1] = -dKa[1];
+}
+
 template <typename T>
 int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, double *loss_out, double *g_params,
                  double *g_state0, double *g_release_h, const double *release_phi, double *timing)
@@ -138,8 +164,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     }
     CK(cudaMalloc(&ldp.p, 2 * (size_t)plane * sizeof(T)));
     CK(cudaMemsetAsync(ldp.p, 0, 2 * (size_t)plane * sizeof(T), st));
-    CK(cudaMalloc(&gpar.p, 2 * sizeof(double)));
-    CK(cudaMemsetAsync(gpar.p, 0, 2 * sizeof(double), st));
+    CK(cudaMalloc(&gpar.p, 4 * sizeof(double)));
+    CK(cudaMemsetAsync(gpar.p, 0, 4 * sizeof(double), st));
     CK(cudaMalloc(&loss_d.p, sizeof(double)));
     CK(cudaMemsetAsync(loss_d.p, 0, sizeof(double), st));
     CK(cudaMalloc(&tgt.p, sizeof(double) * n));
@@ -254,7 +280,7 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     CK(cudaGetLastError());
     CK(cudaEventRecord(ev[2], st));
     // ---- outputs; the state and the clock go back to the end of the forward run ----
-    double gp[2] = {0, 0}, loss = 0;
+    double gp[4] = {0, 0, 0, 0}, loss = 0;
     CK(cudaMemcpyAsync(gp, gpar.p, sizeof(gp), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&loss, loss_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (g_state0) {
@@ -285,8 +311,12 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     const double tand = s->ph.tan_delta;
     if (loss_out) *loss_out = loss;
     if (g_params) {
-        g_params[0] = gp[0] * (1.0 + tand * tand) * (M_PI / 180.0);  // per degree of delta_b
-        g_params[1] = 0.0;  // k_mode 0: the internal friction angle does not enter the model
+        // delta_b acts through tan(delta_b) and, with k_mode 1, through
+        // K_act and K_pass; phi_int only through them (k_mode 0: not at all)
+        double dKa[2], dKp[2];
+        earth_pressure_partials(s->p, dKa, dKp);
+        g_params[0] = (gp[0] * (1.0 + tand * tand) + gp[2] * dKa[1] + gp[3] * dKp[1]) * (M_PI / 180.0);
+        g_params[1] = (gp[2] * dKa[0] + gp[3] * dKp[0]) * (M_PI / 180.0);  // per degree of phi_int
         g_params[2] = gp[1];
     }
     return MOSES_OK;
@@ -307,6 +337,8 @@ int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double 
     if (s->p.nu_f != 0.0) return fail(s, MOSES_EINVAL, "the adjoint does not cover the viscous term");
     if (s->p.scheme != MOSES_SCHEME_CENTRAL || s->ph.recon != 0 || s->ph.rk != 2)
         return fail(s, MOSES_EINVAL, "the adjoint covers the paper's scheme only (central, minmod, two-step)");
+    if (s->ph.k_mode == 1 && !(s->p.delta_b_deg < s->p.phi_int_deg))
+        return fail(s, MOSES_EINVAL, "the adjoint of k_mode 1 needs delta_b < phi_int (K has no derivative at equality)");
     if (!s->have_state) return fail(s, MOSES_ESTATE, "no state");
     return s->prec == MOSES_FP64
                ? adjoint_impl<double>(s, nsteps, ckpt_every, hs_target, loss, g_params, g_state0, g_release_h,
@@ -340,11 +372,11 @@ int stage_adjoint_impl(moses_sim *s, double t, double dt, const double *lam_out,
     CK(cudaMalloc(&li.p, lb));
     CK(cudaMalloc(&lpre.p, lb));
     CK(cudaMalloc(&ldp.p, 2 * (size_t)s->plane * sizeof(T)));
-    CK(cudaMalloc(&gp.p, 2 * sizeof(double)));
+    CK(cudaMalloc(&gp.p, 4 * sizeof(double)));
     CK(cudaMalloc(&hb.p, sizeof(double) * 6 * n));
     CK(cudaMemsetAsync(lo.p, 0, lb, st));
     CK(cudaMemsetAsync(li.p, 0, lb, st));
-    CK(cudaMemsetAsync(gp.p, 0, 2 * sizeof(double), st));
+    CK(cudaMemsetAsync(gp.p, 0, 4 * sizeof(double), st));
     CK(cudaMemcpyAsync(hb.p, lam_out, sizeof(double) * 6 * n, cudaMemcpyHostToDevice, st));
     unpack_lam_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const double *)hb.p, (T *)lo.p, s->nx, s->ny, s->pitch,
                                                           s->plane);
@@ -373,12 +405,17 @@ int stage_adjoint_impl(moses_sim *s, double t, double dt, const double *lam_out,
                                                         s->plane);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(lam_in, hb.p, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
-    double g[2];
+    double g[4];
     CK(cudaMemcpyAsync(g, gp.p, sizeof(g), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (g_param) {
-        g_param[0] = g[0];
+        // tan(delta_b) also moves K_act and K_pass: d delta_b / d tan = cos^2
+        double dKa[2], dKp[2];
+        earth_pressure_partials(s->p, dKa, dKp);
+        const double c2 = 1.0 / (1.0 + s->ph.tan_delta * s->ph.tan_delta);
+        g_param[0] = g[0] + (g[2] * dKa[1] + g[3] * dKp[1]) * c2;
         g_param[1] = g[1];
+        g_param[2] = g[2] * dKa[0] + g[3] * dKp[0];  // per radian of phi_int
     }
     return MOSES_OK;
 }
@@ -391,6 +428,8 @@ int moses_stage_adjoint(moses_sim *s, double t, double dt, const double *lam_out
     if (!(std::isfinite(dt) && dt >= 0)) return fail(s, MOSES_EINVAL, "bad dt");
     if (s->p.nu_f != 0.0 || s->p.scheme != MOSES_SCHEME_CENTRAL || s->ph.recon != 0 || s->ph.rk != 2)
         return fail(s, MOSES_EINVAL, "the adjoint covers the paper's scheme without the viscous term");
+    if (s->ph.k_mode == 1 && !(s->p.delta_b_deg < s->p.phi_int_deg))
+        return fail(s, MOSES_EINVAL, "the adjoint of k_mode 1 needs delta_b < phi_int (K has no derivative at equality)");
     // ghosts of the current state at time t, as moses_stage sees them
     double *tmp = nullptr;
     CK(cudaMallocHost(&tmp, sizeof(double) * 6 * (size_t)s->nx * s->ny));

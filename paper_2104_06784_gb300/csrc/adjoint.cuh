@@ -84,14 +84,21 @@ __device__ __forceinline__ void side_flux_vjp(const T u[6], const FaceGeo<T> &G,
     lu[4 + D] += lunf;
 }
 
-// adjoint of face_flux2 (H2 = F(um) + F(up) - a (up - um), H2[6] = P(um) + P(up))
-template <typename T, int D>
-__device__ __forceinline__ void face_flux2_vjp(const T um[6], const T up[6], const FaceGeo<T> &G, const T lH[6],
-                                               T lP2, T lum[6], T lup[6])
+// adjoint of face_flux2 (H2 = F(um) + F(up) - a (up - um), H2[6] = P(um) + P(up));
+// Gm, Gp: the face geometry of each side (solid pressure coefficients scaled
+// by that side's earth-pressure coefficient with k_mode 1).  With KM it also
+// returns lH . dH2/dK for each side's coefficient (G: the unscaled geometry):
+// dF1/dK = sX Ps, dF2/dK = sY Ps, and the solid speed's
+// d sqrt(K sn (Ut + u0))/dK = sn (Ut + u0) / (2 sqrt(..)) where that side
+// gives the face its speed.
+template <typename T, int D, bool KM = false>
+__device__ __forceinline__ void face_flux2_vjp(const T um[6], const T up[6], const FaceGeo<T> &Gm, const FaceGeo<T> &Gp,
+                                               const T lH[6], T lP2, T lum[6], T lup[6], const FaceGeo<T> *G = nullptr,
+                                               T *lKm = nullptr, T *lKp = nullptr)
 {
     T Fm[6], Fp[6], asm_, afm, asp, afp, Pm, Pp;
-    side_flux<T, D>(um, G, Fm, asm_, afm, Pm);
-    side_flux<T, D>(up, G, Fp, asp, afp, Pp);
+    side_flux<T, D>(um, Gm, Fm, asm_, afm, Pm);
+    side_flux<T, D>(up, Gp, Fp, asp, afp, Pp);
     const bool ms = ibits(asm_) >= ibits(asp), mf = ibits(afm) >= ibits(afp);  // maxnn picks the first on ties
     const T as = ms ? asm_ : asp, af = mf ? afm : afp;
     T las = T(0), laf = T(0);
@@ -104,8 +111,20 @@ __device__ __forceinline__ void face_flux2_vjp(const T um[6], const T up[6], con
         lum[c] = a * lH[c];
         lup[c] = -a * lH[c];
     }
-    side_flux_vjp<T, D>(um, G, lH, ms ? las : T(0), mf ? laf : T(0), lP2, lum);
-    side_flux_vjp<T, D>(up, G, lH, ms ? T(0) : las, mf ? T(0) : laf, lP2, lup);
+    side_flux_vjp<T, D>(um, Gm, lH, ms ? las : T(0), mf ? laf : T(0), lP2, lum);
+    side_flux_vjp<T, D>(up, Gp, lH, ms ? T(0) : las, mf ? T(0) : laf, lP2, lup);
+    if constexpr (KM) {
+        const T sX = D == 0 ? G->sn : G->st, sY = D == 0 ? G->st : G->sn;
+        const auto dK = [&](const T u[6], const FaceGeo<T> &Gs, const bool sel) -> T {
+            const T Ut = u[0] + u[3], Ps = Ut * u[0], w = Ut + u[0];
+            T r = lH[1] * (sX * Ps) + lH[2] * (sY * Ps);
+            const T cs = fsqrt(Gs.sn * w);
+            if (sel && cs > T(0)) r += las * (G->sn * w / (T(2) * cs));
+            return r;
+        };
+        *lKm = dK(um, Gm, ms);
+        *lKp = dK(up, Gp, !ms);
+    }
 }
 
 // minmod selection: 0 -> returned 0, 1 -> returned a, 2 -> returned b
@@ -131,7 +150,8 @@ struct AdjArgs {
     T *lam_dp;        // A -> B: adjoint of dP/dxi, dP/deta (2 planes)
     T *lam_in;        // adjoint of the stage input (6 planes, ghosts included): A writes the
                       // cells' own contributions, B adds the face terms and sets the ghosts
-    double *g_param;  // [0] d/d tan(delta_b), [1] d/d c_D (FP64 accumulators)
+    double *g_param;  // [0] d/d tan(delta_b), [1] d/d c_D; with k_mode 1 also
+                      // [2] d/d K_act, [3] d/d K_pass (FP64 accumulators)
     // Heun: 2 = second stage (A reads lam_next), 1 = first stage (B adds the
     // direct term; lam_in == lam_next), 0 = a lone stage
     int heun;
@@ -401,7 +421,7 @@ namespace moses {
 // the tile and a 2-cell halo are staged in shared memory up front, so that
 // the face loop reads no global memory; FP64 reads its face geometry and the
 // cell adjoints in the loop (its shared memory is full at two CTAs per SM).
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool KM = false>
 struct FaceAdjSmem {
     static constexpr bool STAGE = sizeof(T) == 4;
     static constexpr int SW3 = TX + 6, SH3 = TY + 6, SP3 = SW3 * SH3;
@@ -411,7 +431,9 @@ struct FaceAdjSmem {
     static constexpr int LW = TX + 4, LP = LW * (TY + 4);  // lam box: tile + 2-cell halo
     static constexpr size_t sel_bytes = (6 * NS + 15) / 16 * 16;
     static constexpr size_t base = sizeof(T) * (6 * SP3 + 6 * NS + 12 * NF + 6 * NL) + sel_bytes;
-    static constexpr size_t bytes = base + (STAGE ? sizeof(T) * (8 * LP + 4 * LP) : 0);
+    static constexpr size_t staged = base + (STAGE ? sizeof(T) * (8 * LP + 4 * LP) : 0);
+    // earth-pressure form: solid velocities (v_X, v_Y) of the state box
+    static constexpr size_t bytes = staged + (KM ? sizeof(T) * 2 * SP3 : 0);
 };
 
 // Cell h (0 <= h < (TX + 2 HW)(TY + 2 HW) - TX TY) of the halo of width HW
@@ -437,11 +459,12 @@ __device__ __forceinline__ void halo_cell(int h, int &tx, int &ty)
     }
 }
 
-template <typename T, int TX, int TY, int D>
+template <typename T, int TX, int TY, int D, bool KM = false>
 __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, unsigned char *sSel, T *sLum,
-                                             T *sLup, T *sLs, const T *sLam, const T *sBs, T lres[6])
+                                             T *sLup, T *sLs, const T *sLam, const T *sBs, const T *sVs, T lres[6],
+                                             T &gKa, T &gKp)
 {
-    using SM = FaceAdjSmem<T, TX, TY>;
+    using SM = FaceAdjSmem<T, TX, TY, KM>;
     constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3, LW = SM::LW, LP = SM::LP;
     constexpr int L = D == 0 ? TX : TY;   // cells of the tile along the normal
     constexpr int M = D == 0 ? TY : TX;   // lines of the tile
@@ -543,7 +566,27 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
                 um[c] = fma(T(0.5), sS[c * NS + sl], sU[c * SP3 + sidx(m, p)]);
                 up[c] = fma(T(-0.5), sS[c * NS + sl + 1], sU[c * SP3 + sidx(m, p + 1)]);
             }
-            face_flux2_vjp<T, D>(um, up, G, lH, lP2, lum, lup);
+            if constexpr (KM) {
+                // each side with its cell's coefficient, as the forward stage;
+                // the coefficient partials of the faces this tile owns (lower
+                // cell in the tile, or the domain's first face)
+                const bool pm = cell_passive(sVs + D * SP3, sidx(m, p), STEP);
+                const bool pp = cell_passive(sVs + D * SP3, sidx(m, p + 1), STEP);
+                const T Km = pm ? a.k.Kp : a.k.Ka, Kq = pp ? a.k.Kp : a.k.Ka;
+                FaceGeo<T> Gm = G, Gp = G;
+                Gm.sn *= Km;
+                Gm.st *= Km;
+                Gp.sn *= Kq;
+                Gp.st *= Kq;
+                T lKm, lKp;
+                face_flux2_vjp<T, D, true>(um, up, Gm, Gp, lH, lP2, lum, lup, &G, &lKm, &lKp);
+                if ((p >= 0 && p < L) || lo == -1) {
+                    (pm ? gKp : gKa) += lKm;
+                    (pp ? gKp : gKa) += lKp;
+                }
+            } else {
+                face_flux2_vjp<T, D>(um, up, G, G, lH, lP2, lum, lup);
+            }
         }
 #pragma unroll
         for (int c = 0; c < 6; c++) {
@@ -626,10 +669,10 @@ __device__ __forceinline__ void adj_ghost_zero(const AdjArgs<T> &q)
 }
 
 // FP32: three 256-thread CTAs per SM (80 registers); FP64: shared memory allows two
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool KM = false>
 __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY)) adj_face_kernel(const AdjArgs<T> q)
 {
-    using SM = FaceAdjSmem<T, TX, TY>;
+    using SM = FaceAdjSmem<T, TX, TY, KM>;
     constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sU = reinterpret_cast<T *>(smem_raw);
@@ -640,6 +683,8 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     unsigned char *sSel = reinterpret_cast<unsigned char *>(sLs + 6 * SM::NL);
     T *sLam = reinterpret_cast<T *>(smem_raw + SM::base);  // FP32 form: [8][TY+4][TX+4]
     T *sBs = sLam + 8 * SM::LP;                             // FP32 form: [4][TY+4][TX+4] bed slopes
+    T *sVs = reinterpret_cast<T *>(smem_raw + SM::staged);  // KM: [2][TY+6][TX+6] solid velocities
+    __shared__ double kred[2][NT / 32];
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -684,6 +729,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     }
     const bool wet = __syncthreads_or(has_mass) != 0;
     T lres[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T gKa = T(0), gKp = T(0);
     if (wet) {  // CTA-uniform
         // the momenta; FP32 also the cell adjoints and bed slopes of the box
         if constexpr (SM::STAGE) {
@@ -727,8 +773,30 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
         }
         cp_async_wait_all();
         __syncthreads();
-        adj_face_dir<T, TX, TY, 0>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
-        adj_face_dir<T, TX, TY, 1>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, lres);
+        if constexpr (KM) {
+            // solid velocity of every cell of the state box, as the forward stage takes it
+            for (int e = tid; e < SP3; e += NT) {
+                const int gi = x0 + e % SW3 - 3, gj = y0 + e / SW3 - 3;
+                T vx = T(NAN), vy = T(NAN);
+                if (gi >= -2 && gj >= -2 && gi < nx + 2 && gj < ny + 2) {
+                    const T u1 = sU[e];
+                    if (gtp(u1, a.geo[GC_JHD * plane + cell_index(gi, gj, pitch)])) {
+                        if constexpr (sizeof(T) == 8) {
+                            vx = __ddiv_rn(sU[SP3 + e], u1);
+                            vy = __ddiv_rn(sU[2 * SP3 + e], u1);
+                        } else {
+                            vx = __fdiv_rn(sU[SP3 + e], u1);
+                            vy = __fdiv_rn(sU[2 * SP3 + e], u1);
+                        }
+                    }
+                }
+                sVs[e] = vx;
+                sVs[SP3 + e] = vy;
+            }
+            __syncthreads();
+        }
+        adj_face_dir<T, TX, TY, 0, KM>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, sVs, lres, gKa, gKp);
+        adj_face_dir<T, TX, TY, 1, KM>(q, sU, sS, sSel, sLum, sLup, sLs, sLam, sBs, sVs, lres, gKa, gKp);
     } else {
         // the ghost cells this tile owns get no face terms either
         adj_ghost_zero<T, TX, TY, 0>(q);
@@ -740,6 +808,27 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
         const long long g = cell_index(i, j, pitch);
 #pragma unroll
         for (int c = 0; c < 6; c++) q.lam_in[c * plane + g] += lres[c];
+    }
+    if constexpr (KM) {  // coefficient partials: per warp in T, per CTA and globally in FP64
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            gKa += __shfl_xor_sync(0xffffffffu, gKa, o);
+            gKp += __shfl_xor_sync(0xffffffffu, gKp, o);
+        }
+        if ((tid & 31) == 0) {
+            kred[0][tid >> 5] = (double)gKa;
+            kred[1][tid >> 5] = (double)gKp;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int w = 0; w < NT / 32; w++) {
+                s0 += kred[0][w];
+                s1 += kred[1][w];
+            }
+            if (s0 != 0.0) atomicAdd(&q.g_param[2], s0);
+            if (s1 != 0.0) atomicAdd(&q.g_param[3], s1);
+        }
     }
 }
 

@@ -111,9 +111,9 @@ __global__ void geometry_kernel(const double *bext, int nx, int ny, int pitch, l
             put(GC_KXX, g, c * bXX);
             put(GC_KXY2, g, 2.0 * c * bXY);
             put(GC_KYY, g, c * bYY);
-            put(GC_SXS, g, ph.kap_s * A11 * c2);
+            put(GC_SXS, g, ph.kap_s * ph.K_pass * A11 * c2);
             put(GC_SXF, g, 2.0 * ph.kap_f * A11 * c2);
-            put(GC_SYS, g, ph.kap_s * A22 * c2);
+            put(GC_SYS, g, ph.kap_s * ph.K_pass * A22 * c2);
             put(GC_SYF, g, 2.0 * ph.kap_f * A22 * c2);
         }
         // x-face (i+1/2, j): normal slope by the face difference, transverse
@@ -380,7 +380,13 @@ static int check_params(const moses_params *p, std::string &why)
     if (!(fin(p->rho_s) && p->rho_s > 0)) return why = "rho_s must be > 0", 1;
     if (!(fin(p->rho_f) && p->rho_f >= 0 && p->rho_f < p->rho_s)) return why = "need 0 <= rho_f < rho_s", 1;
     if (!(fin(p->delta_b_deg) && p->delta_b_deg >= 0 && p->delta_b_deg < 90)) return why = "delta_b in [0, 90)", 1;
-    if (p->k_mode != 0) return why = "only k_mode = 0 (earth-pressure coefficient 1, App. A) is implemented", 1;
+    if (p->k_mode != 0 && p->k_mode != 1) return why = "k_mode must be 0 or 1", 1;
+    if (p->k_mode == 1) {
+        if (!(fin(p->phi_int_deg) && p->phi_int_deg >= p->delta_b_deg && p->phi_int_deg < 90))
+            return why = "k_mode 1 needs delta_b <= phi_int < 90 deg", 1;
+        if (p->nu_f != 0.0 || p->scheme != MOSES_SCHEME_CENTRAL || p->recon != MOSES_RECON_MINMOD)
+            return why = "k_mode 1 runs with the central flux, minmod and nu_f = 0", 1;
+    }
     if (!(fin(p->c_d) && p->c_d >= 0)) return why = "c_d must be >= 0", 1;
     if (!(fin(p->nu_f) && p->nu_f >= 0)) return why = "nu_f must be >= 0", 1;
     if (!(fin(p->k_f) && p->k_f >= 0)) return why = "k_f must be >= 0", 1;
@@ -429,6 +435,18 @@ static Phys make_phys(const moses_params *p, double dx, double dy)
     f.recon = p->recon;
     f.rk = p->rk == 3 ? 3 : 2;
     for (int k = 0; k < 4; k++) f.bc[k] = p->bc[k];
+    // Savage-Hutter earth-pressure coefficients (reading R10), from the
+    // Mohr-Coulomb limit states of the solid against a bed of friction
+    // delta_b: K = 2 sec^2(phi) (1 -/+ sqrt(1 - cos^2(phi) / cos^2(delta))) - 1
+    f.k_mode = p->k_mode;
+    f.K_act = f.K_pass = 1.0;
+    if (p->k_mode == 1) {
+        const double cphi = cos(p->phi_int_deg * M_PI / 180.0), cdel = cos(p->delta_b_deg * M_PI / 180.0);
+        const double q = cphi * cphi / (cdel * cdel);
+        const double root = sqrt(q < 1.0 ? 1.0 - q : 0.0);
+        f.K_act = 2.0 / (cphi * cphi) * (1.0 - root) - 1.0;
+        f.K_pass = 2.0 / (cphi * cphi) * (1.0 + root) - 1.0;
+    }
     return f;
 }
 
@@ -1261,8 +1279,8 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     if (check_params(p, why)) return fail(s, MOSES_EINVAL, why);
     if (p->precision != MOSES_FP64) return fail(s, MOSES_EINVAL, "moses_step_static runs the FP64 form only");
     if (p->nu_f != 0.0) return fail(s, MOSES_EINVAL, "moses_step_static: nu_f must be 0");
-    if (p->scheme != MOSES_SCHEME_CENTRAL || p->recon != MOSES_RECON_MINMOD || p->rk == 3)
-        return fail(s, MOSES_EINVAL, "moses_step_static: the paper's scheme only (scheme 0, recon 0, rk 2)");
+    if (p->scheme != MOSES_SCHEME_CENTRAL || p->recon != MOSES_RECON_MINMOD || p->rk == 3 || p->k_mode != 0)
+        return fail(s, MOSES_EINVAL, "moses_step_static: the paper's scheme only (scheme 0, recon 0, rk 2, k_mode 0)");
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(s, MOSES_EINVAL, "device ordinal out of range");
@@ -1493,8 +1511,10 @@ int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out)
         if (sims[k]->stream != sims[0]->stream) return batch_fail(nullptr, MOSES_EINVAL, "members must share the stream");
         if (!sims[k]->have_state) return batch_fail(nullptr, MOSES_ESTATE, "member without a state");
         if (sims[k]->p.nu_f != 0.0) return batch_fail(nullptr, MOSES_EINVAL, "members must have nu_f = 0");
-        if (sims[k]->p.scheme != MOSES_SCHEME_CENTRAL || sims[k]->ph.recon != 0 || sims[k]->ph.rk != 2)
-            return batch_fail(nullptr, MOSES_EINVAL, "members must use the paper's scheme (central, minmod, two-step)");
+        if (sims[k]->p.scheme != MOSES_SCHEME_CENTRAL || sims[k]->ph.recon != 0 || sims[k]->ph.rk != 2 ||
+            sims[k]->ph.k_mode != 0)
+            return batch_fail(nullptr, MOSES_EINVAL,
+                              "members must use the paper's scheme (central, minmod, two-step, k_mode 0)");
         for (int q = 0; q < k; q++)
             if (sims[q] == sims[k]) return batch_fail(nullptr, MOSES_EINVAL, "a simulation appears twice");
     }

@@ -38,9 +38,9 @@ enum GeoPlane : int {
     GC_KXX,     // c bXX     kappa = -(KXX vX^2 + KXY2 vX vY + KYY vY^2)
     GC_KXY2,    // 2 c bXY
     GC_KYY,     // c bYY
-    GC_SXS,     // kap_s A11 c^2      cell-centre wave speeds (CFL)
+    GC_SXS,     // kap_s K_pass A11 c^2   cell-centre wave speeds (CFL; K_pass = 1 unless k_mode 1)
     GC_SXF,     // 2 kap_f A11 c^2
-    GC_SYS,     // kap_s A22 c^2
+    GC_SYS,     // kap_s K_pass A22 c^2
     GC_SYF,     // 2 kap_f A22 c^2
     GX_JHD,     // x-face (i+1/2, j): J h_dry
     GX_SN,      //   kap_s A11 c^2 : solid X-momentum pressure coefficient, solid speed
@@ -108,6 +108,11 @@ struct Phys {
     int recon;         // 0: minmod slopes, 1: third-order WENO
     int rk;            // 2: two-step modified Euler, 3: three-stage SSP Runge-Kutta
     int bc[4];
+    // internal friction (reading R10): k_mode 1 scales the solid pressure of
+    // each direction by the Savage-Hutter coefficient K_act or K_pass (both 1
+    // in the paper's form, k_mode 0); the CFL celerity takes K_pass
+    int k_mode;
+    double K_act, K_pass;
 };
 
 // Constants of the stage kernel in its arithmetic type, prepared on the host
@@ -119,6 +124,9 @@ struct KT {
     T kap_s, kap_f, kap_f2, half_g, g_1ma, g, h_dry, inv_dx, inv_dy, inv_2dx;
     // viscous term (Eq. SrcF_vis_Topo): nu_f, 1/(2 dy)
     T nu_f, inv_2dy;
+    // earth-pressure coefficients (k_mode 1) and the CFL celerity's solid
+    // pressure factor kap_s K_pass (FP32 form)
+    T Ka, Kp, kap_s_cfl;
     double tan_delta_d;
 };
 
@@ -147,6 +155,9 @@ inline KT<T> make_kt(const Phys &p)
     k.inv_2dx = (T)(0.5 * p.inv_dx);
     k.nu_f = (T)p.nu_f;
     k.inv_2dy = (T)(0.5 * p.inv_dy);
+    k.Ka = (T)p.K_act;
+    k.Kp = (T)p.K_pass;
+    k.kap_s_cfl = (T)(p.kap_s * p.K_pass);
     k.tan_delta_d = p.tan_delta;
     return k;
 }

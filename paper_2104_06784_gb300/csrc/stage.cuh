@@ -265,12 +265,16 @@ __device__ __forceinline__ void side_flux(const T u[6], const FaceGeo<T> &G, T F
 // Twice the central flux through one face, from the face values um (left /
 // lower cell) and up (right / upper cell): H2 = F(um) + F(up) - a (up - um),
 // a = max of the two sides' local speeds per phase; H2[6] = P(um) + P(up).
+// Gm, Gp: the face geometry as each side sees it (they differ only in the
+// solid pressure coefficients, scaled by each side's earth-pressure
+// coefficient with k_mode 1; the same otherwise).
 template <typename T, int D>
-__device__ __forceinline__ void face_flux2(const T um[6], const T up[6], const FaceGeo<T> &G, T H[7])
+__device__ __forceinline__ void face_flux2(const T um[6], const T up[6], const FaceGeo<T> &Gm, const FaceGeo<T> &Gp,
+                                           T H[7])
 {
     T Fm[6], Fp[6], asm_, afm, asp, afp, Pm, Pp;
-    side_flux<T, D>(um, G, Fm, asm_, afm, Pm);
-    side_flux<T, D>(up, G, Fp, asp, afp, Pp);
+    side_flux<T, D>(um, Gm, Fm, asm_, afm, Pm);
+    side_flux<T, D>(up, Gp, Fp, asp, afp, Pp);
     const T as = maxnn(asm_, asp), af = maxnn(afm, afp);
 #pragma unroll
     for (int c = 0; c < 6; c++) H[c] = fma(-(c < 3 ? as : af), up[c] - um[c], Fm[c] + Fp[c]);
@@ -299,6 +303,27 @@ __device__ __forceinline__ void face_flux2_cu(const T um[6], const T up[6], cons
             H[c] = moving ? fma(ap * am * r2, up[c] - um[c], (ap * Fm[c] - am * Fp[c]) * r2) : Fm[c] + Fp[c];
     }
     H[6] = Pm + Pp;
+}
+
+// Earth-pressure regime (k_mode 1, reading R10) of the cell at offset o of a
+// velocity box (v: the velocity component along the axis, NaN where the
+// cell carries no solid; st: the box's offset step along the axis): passive
+// where the cell carries solid and its velocity drops along the axis by more
+// than the dead band 1e-6 (|v+| + |v-|) + 1e-6 m/s (unfused IEEE operations,
+// as the oracle takes them); the stage kernel and its adjoint both use it
+template <typename T>
+__device__ __forceinline__ bool cell_passive(const T *v, const int o, const int st)
+{
+    const T vc = v[o], vp = v[o + st], vm = v[o - st];
+    T d, band;
+    if constexpr (sizeof(T) == 8) {
+        d = __dsub_rn(vp, vm);
+        band = __dadd_rn(__dmul_rn(1e-6, __dadd_rn(fabs(vp), fabs(vm))), 1e-6);
+    } else {
+        d = __fsub_rn(vp, vm);
+        band = __fadd_rn(__fmul_rn(1e-6f, __fadd_rn(fabsf(vp), fabsf(vm))), 1e-6f);
+    }
+    return vc == vc && d < -band;
 }
 
 // ---- Mode-II inflow and ghost cells ---------------------------------------------
@@ -506,9 +531,9 @@ __device__ __forceinline__ CellGeo32 cell_geo32(float sX, float sY, float bXX, f
     G.kXX = c * bXX;
     G.kXY2 = 2.0f * c * bXY;
     G.kYY = c * bYY;
-    G.sxs = k.kap_s * G.A11 * c2;
+    G.sxs = k.kap_s_cfl * G.A11 * c2;
     G.sxf = k.kap_f2 * G.A11 * c2;
-    G.sys = k.kap_s * G.A22 * c2;
+    G.sys = k.kap_s_cfl * G.A22 * c2;
     G.syf = k.kap_f2 * G.A22 * c2;
     return G;
 }
@@ -613,11 +638,26 @@ __device__ __forceinline__ void end_step(const StageArgs<T> &a)
     }
 }
 
+template <typename T, int TX, int TY, bool VIS = false, bool KM = false>
+constexpr size_t stage_smem_bytes()
+{
+    // state halo tile, slopes, face fluxes; FP32 or viscous: bed-slope tile;
+    // viscous: fluid velocities of the slope tile; earth pressure: solid
+    // velocities of the state halo tile
+    return sizeof(T) * (6 * (TX + 4) * (TY + 4) + 6 * (TX + 2) * TY + 6 * TX * (TY + 2) + 7 * (TX + 1) * TY +
+                        7 * TX * (TY + 1) + ((sizeof(T) == 4 || VIS) ? 4 * (TX + 2) * (TY + 2) : 0) +
+                        (VIS ? 2 * (TX + 2) * (TY + 2) : 0) + (KM ? 2 * (TX + 4) * (TY + 4) : 0));
+}
+
 // ---- the stage kernel -------------------------------------------------------------
 // One stage on the tile (bx, by) of the simulation described by `a`; nb is the
 // number of CTAs working on that simulation in this launch (for the ticket;
 // 0: the caller takes it).
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
+// KM: the earth-pressure form (k_mode 1, reading R10): each cell of the staged
+// tile and halo gets its solid velocity (NaN where the cell carries no
+// solid), from which each side of a face takes its cell's K_act or K_pass.
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false,
+          bool KM = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
     constexpr int NT = TX * TY;
@@ -636,8 +676,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     constexpr bool GL = sizeof(T) == 4;
     constexpr bool SL = GL || VIS;
     constexpr int BW = TX + 2, NB = (TX + 2) * (TY + 2);
-    T *sB = sHy + 7 * NYF;
-    T *sVf = sB + 4 * NB;
+    T *sB = sHy + 7 * NYF;                  // allocated in the FP32 and viscous forms only
+    T *sVf = sB + (SL ? 4 * NB : 0);        // viscous form only
+    // KM: solid velocities (v_X, v_Y) of every staged cell, [2][SH][SW]
+    T *sVs = sVf + (VIS ? 2 * NB : 0);
+    // the regions above end where the launchers' dynamic allocation ends
+    static_assert((6 * SP + 6 * NSX + 6 * NSY + 7 * NXF + 7 * NYF + (SL ? 4 * NB : 0) + (VIS ? 2 * NB : 0) +
+                   (KM ? 2 * SP : 0)) * sizeof(T) == stage_smem_bytes<T, TX, TY, VIS, KM>(),
+                  "shared-memory layout and allocation differ");
     auto SB = [&](int c, int cx, int cy) -> T { return sB[c * NB + cy * BW + cx]; };
     __shared__ T red[NT / 32];
     __shared__ double acc[4];
@@ -811,6 +857,30 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             }
         }
 
+        if constexpr (KM) {
+            // solid velocity of every staged cell where it carries solid
+            // (U1 > J h_dry), by IEEE division as the oracle takes it; NaN
+            // elsewhere, so that every comparison with it fails
+            for (int q = tid; q < SP; q += NT) {
+                const int gi = x0 + q % SW - 2, gj = y0 + q / SW - 2;
+                T vx = T(NAN), vy = T(NAN);
+                if (gi < nx + 2 && gj < ny + 2) {
+                    const T u1 = sU[q];
+                    if (gtp(u1, geo[GC_JHD * plane + cell_index(gi, gj, pitch)])) {
+                        if constexpr (sizeof(T) == 8) {
+                            vx = __ddiv_rn(sU[SP + q], u1);
+                            vy = __ddiv_rn(sU[2 * SP + q], u1);
+                        } else {
+                            vx = __fdiv_rn(sU[SP + q], u1);
+                            vy = __fdiv_rn(sU[2 * SP + q], u1);
+                        }
+                    }
+                }
+                sVs[q] = vx;
+                sVs[SP + q] = vy;
+            }
+        }
+
         // ---- minmod slopes, once per cell and direction -----------------------
         // sSx[c][ly][lx'] holds the x-slope of cell (x0-1+lx', y0+ly), sSy[c][ly'][lx]
         // the y-slope of cell (x0+lx, y0-1+ly').  Each thread takes both slopes of
@@ -849,6 +919,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         // sHy[c][ly][lx], ly = j - y0 + 1.  Each thread takes the right and the
         // upper face of its own cell; warp 0 the left faces of column 0, warp 1
         // the lower faces of row 0 (every warp then runs at most three faces).
+        // K of the staged cell at offset o for the axis with offset step `st`
+        // and velocity component c (KM): K_pass where cell_passive, else K_act
+        const auto cellK = [&](const int o, const int st, const int c) -> T {
+            return cell_passive(sVs + c * SP, o, st) ? k.Kp : k.Ka;
+        };
         const auto x_face = [&](const int lx, const int ly) {
             const int i = x0 + lx - 1, j = y0 + ly;
             if (j >= ny || i >= nx) return;
@@ -882,7 +957,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             }
             T H[7];
             if constexpr (CU) face_flux2_cu<T, 0>(um, up, G, H);
-            else face_flux2<T, 0>(um, up, G, H);
+            else if constexpr (KM) {
+                FaceGeo<T> Gm = G, Gp = G;
+                const T Km = cellK(ou, 1, 0), Kp = cellK(ou + 1, 1, 0);
+                Gm.sn *= Km;
+                Gm.st *= Km;
+                Gp.sn *= Kp;
+                Gp.st *= Kp;
+                face_flux2<T, 0>(um, up, Gm, Gp, H);
+            } else face_flux2<T, 0>(um, up, G, G, H);
             if constexpr (sizeof(T) == 4) {
                 // FP32: the mass change this face gives each neighbour, rounded once
                 H[0] *= dtT * k.hinv_dx;
@@ -930,7 +1013,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             }
             T H[7];
             if constexpr (CU) face_flux2_cu<T, 1>(um, up, G, H);
-            else face_flux2<T, 1>(um, up, G, H);
+            else if constexpr (KM) {
+                FaceGeo<T> Gm = G, Gp = G;
+                const T Km = cellK(ou, SW, 1), Kp = cellK(ou + SW, SW, 1);
+                Gm.sn *= Km;
+                Gm.st *= Km;
+                Gp.sn *= Kp;
+                Gp.st *= Kp;
+                face_flux2<T, 1>(um, up, Gm, Gp, H);
+            } else face_flux2<T, 1>(um, up, G, G, H);
             if constexpr (sizeof(T) == 4) {
                 H[0] *= dtT * k.hinv_dy;
                 H[3] *= dtT * k.hinv_dy;
@@ -1259,10 +1350,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     }
 }
 
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false,
+          bool KM = false>
 __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const StageArgs<T> a)
 {
-    stage_tile<T, TX, TY, REC, VIS, CU, WENO>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
+    stage_tile<T, TX, TY, REC, VIS, CU, WENO, KM>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
 // ---- bulk copies (the TMA engine) completed on an mbarrier -------------------------
@@ -1566,7 +1658,7 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
 // entries in turn; the last CTA to finish empties the list and, after the
 // step's last stage, ends the step.
 // FP32: three 256-thread CTAs per SM (at most 85 registers); FP64: two
-template <typename T, int TX, int TY, bool REC = false>
+template <typename T, int TX, int TY, bool REC = false, bool KM = false>
 __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY))
     stage_kernel_list(const StageArgs<T> a, const int gx)
 {
@@ -1578,7 +1670,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     // previous tile no longer reads
     for (unsigned int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = a.wl[w];
-        stage_tile<T, TX, TY, REC>(a, t % gx, t / gx, 0u);
+        stage_tile<T, TX, TY, REC, false, false, false, KM>(a, t % gx, t / gx, 0u);
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -1660,14 +1752,5 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     }
 }
 
-template <typename T, int TX, int TY, bool VIS = false>
-constexpr size_t stage_smem_bytes()
-{
-    // state halo tile, slopes, face fluxes; FP32 or viscous: bed-slope tile;
-    // viscous: fluid velocities of the slope tile
-    return sizeof(T) * (6 * (TX + 4) * (TY + 4) + 6 * (TX + 2) * TY + 6 * TX * (TY + 2) + 7 * (TX + 1) * TY +
-                        7 * TX * (TY + 1) + ((sizeof(T) == 4 || VIS) ? 4 * (TX + 2) * (TY + 2) : 0) +
-                        (VIS ? 2 * (TX + 2) * (TY + 2) : 0));
-}
 
 }  // namespace moses

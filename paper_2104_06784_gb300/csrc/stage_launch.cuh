@@ -10,40 +10,41 @@
 namespace moses {
 namespace {
 
-template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false>
+template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false,
+          bool KM = false>
 int launch_tile(const StageArgs<T> &a, cudaStream_t st)
 {
-    constexpr size_t smem = stage_smem_bytes<T, TX, TY, VIS>();
+    constexpr size_t smem = stage_smem_bytes<T, TX, TY, VIS, KM>();
     static bool attr_set[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC, VIS, CU, WENO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(stage_kernel<T, TX, TY, REC, VIS, CU, WENO, KM>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return -1;
         attr_set[dev] = true;
     }
     const dim3 grid((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY);
-    stage_kernel<T, TX, TY, REC, VIS, CU, WENO><<<grid, TX * TY, smem, st>>>(a);
+    stage_kernel<T, TX, TY, REC, VIS, CU, WENO, KM><<<grid, TX * TY, smem, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
 // The stepping launches of the plain form: classify_kernel over every tile
 // (classify_flags_kernel in a combining stage), then stage_kernel_list on a
 // grid of resident CTAs over the listed tiles.
-template <typename T, int TX, int TY, bool REC = false>
+template <typename T, int TX, int TY, bool REC = false, bool KM = false>
 int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
 {
-    constexpr size_t smem = stage_smem_bytes<T, TX, TY>();
+    constexpr size_t smem = stage_smem_bytes<T, TX, TY, false, KM>();
     static int resident[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return -1;
     if (!resident[dev]) {
         int per_sm = 0, n_sm = 0;
-        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY, REC>, TX * TY, smem) !=
+        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY, REC, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY, REC, KM>, TX * TY, smem) !=
                 cudaSuccess ||
             cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
             return -1;
@@ -57,7 +58,7 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     } else {
         classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
     }
-    stage_kernel_list<T, TX, TY, REC><<<resident[dev], TX * TY, smem, st>>>(a, gx);
+    stage_kernel_list<T, TX, TY, REC, KM><<<resident[dev], TX * TY, smem, st>>>(a, gx);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -66,6 +67,23 @@ template <typename T>
 int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
+    if (a_in.ph.k_mode == 1) {  // the earth-pressure form: the paper's scheme, every tile shape
+        if (a_in.wl && !a_in.debug_stage) {
+            switch (tile) {
+            case 1: return launch_tile_list<T, 32, 4, false, true>(a_in, st);
+            case 2: return launch_tile_list<T, 32, 16, false, true>(a_in, st);
+            default: return launch_tile_list<T, 32, 8, false, true>(a_in, st);
+            }
+        }
+        StageArgs<T> a = a_in;
+        a.wl = nullptr;
+        a.wl_n = nullptr;
+        switch (tile) {
+        case 1: return launch_tile<T, 32, 4, false, false, false, false, true>(a, st);
+        case 2: return launch_tile<T, 32, 16, false, false, false, false, true>(a, st);
+        default: return launch_tile<T, 32, 8, false, false, false, false, true>(a, st);
+        }
+    }
     // the model options (viscous term, central-upwind flux, WENO): one tile shape
     const bool vis = a_in.ph.nu_f > 0.0, cu = a_in.ph.scheme == 1, weno = a_in.ph.recon == 1;
     if (a_in.wl && !vis && !cu && !weno && !a_in.debug_stage) {
@@ -99,6 +117,10 @@ template <typename T>
 int launch_stage_rec_impl(const StageArgs<T> &a, void *stream)
 {
     if (!a.rec) return -1;
+    if (a.ph.k_mode == 1) {
+        if (a.wl) return launch_tile_list<T, 32, 8, true, true>(a, (cudaStream_t)stream);
+        return launch_tile<T, 32, 8, true, false, false, false, true>(a, (cudaStream_t)stream);
+    }
     if (a.wl) return launch_tile_list<T, 32, 8, true>(a, (cudaStream_t)stream);
     return launch_tile<T, 32, 8, true>(a, (cudaStream_t)stream);
 }

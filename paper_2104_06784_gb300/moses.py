@@ -273,10 +273,10 @@ class Sim:
 
     def stage_adjoint(self, t: float, dt: float, lam_out):
         """(dS/dU)^T lam_out for one stage at the current state; also the
-        parameter partials [d/d tan(delta_b), d/d c_D]."""
+        parameter partials [d/d tan(delta_b), d/d c_D, d/d phi_int (per radian)]."""
         lo = _f64(lam_out)
         li = np.empty((6, self.ny, self.nx))
-        gp = np.zeros(2)
+        gp = np.zeros(3)
         self._ck(self._L.moses_stage_adjoint(self._h, float(t), float(dt), _p(lo), _p(li), _p(gp)))
         return li, gp
 
@@ -385,7 +385,8 @@ def deposit_misfit(cfg: dict, h0, delta_b_deg, c_d, phi_int_deg, hs_target, nste
     """Deposit misfit L = sum (h^s(t_N) - h^s_target)^2 dx dy as a differentiable
     torch function of the release thickness h0, the basal friction angle
     delta_b (degrees), the drag coefficient c_D and the internal friction
-    angle phi_int (degrees; it does not enter the model, gradient 0).
+    angle phi_int (degrees; it enters the model through the Savage-Hutter
+    earth-pressure coefficients when cfg's k_mode is 1, else its gradient is 0).
 
     The forward pass and the gradients both come from moses_adjoint_misfit
     (one forward run, checkpointed recomputation, reverse sweep); backward

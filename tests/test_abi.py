@@ -60,7 +60,7 @@ def _create(dem, nx, ny, dx=5.0, dy=5.0, **over):
 @pytest.mark.parametrize("nx,ny,dx,over", [
     (0, 4, 5.0, {}), (4, 0, 5.0, {}), (4, 4, 0.0, {}), (4, 4, -1.0, {}), (4, 4, float("nan"), {}),
     (4, 4, 5.0, dict(cfl=0.0)), (4, 4, 5.0, dict(rho_f=3000.0)), (4, 4, 5.0, dict(h_dry=0.0)),
-    (4, 4, 5.0, dict(bc=(0, 2, 0, 0))), (4, 4, 5.0, dict(k_mode=1)), (4, 4, 5.0, dict(delta_b_deg=95.0)),
+    (4, 4, 5.0, dict(bc=(0, 2, 0, 0))), (4, 4, 5.0, dict(k_mode=2)), (4, 4, 5.0, dict(k_mode=1, phi_int_deg=20.0)), (4, 4, 5.0, dict(k_mode=1, scheme=1)), (4, 4, 5.0, dict(delta_b_deg=95.0)),
     (4, 4, 5.0, dict(c_d=-1.0)), (4, 4, 5.0, dict(g=0.0)), (4, 4, 5.0, dict(fluid_pg_mode=3)),
 ])
 def test_create_rejects_bad_arguments(L, nx, ny, dx, over):

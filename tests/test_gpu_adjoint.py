@@ -24,24 +24,25 @@ def _wet_state(nx, ny, seed):
                 vx_f=rng.standard_normal((ny, nx)), vy_f=rng.standard_normal((ny, nx)))
 
 
-def _stage_sim(nx, ny, bc, inflow, prec, seed):
+def _stage_sim(nx, ny, bc, inflow, prec, seed, k_mode=0):
     if inflow:
-        cfg = W.inflow_config(nx=nx, ny=ny, dx=5.0, inlet_cells=6)
+        cfg = W.inflow_config(nx=nx, ny=ny, dx=5.0, inlet_cells=6, k_mode=k_mode)
         g = moses.Sim(cfg["dem"], 5.0, 5.0, cfg["params"], precision=prec)
         f = cfg["inflow"]
         g.set_inflow(f["side"], f["i0"], f["i1"], f["t"], f["Q"], f["phi"])
     else:
         dem = W.spectral_dem(nx, ny, 5.0, 2.2, 30.0, seed=seed, band_m=40.0)
-        g = moses.Sim(dem, 5.0, 5.0, W.default_params(bc=bc, c_d=0.05), precision=prec)
+        g = moses.Sim(dem, 5.0, 5.0, W.default_params(bc=bc, c_d=0.05, k_mode=k_mode), precision=prec)
     st = _wet_state(nx, ny, seed)
     g.set_release(st["h"], st["phi_s"], st["vx_s"], st["vy_s"], st["vx_f"], st["vy_f"])
     return g
 
 
+@pytest.mark.parametrize("k_mode", [0, 1])
 @pytest.mark.parametrize("nx,ny,bc,inflow", [(45, 37, (0, 0, 0, 0), False), (70, 20, (1, 1, 1, 1), False),
                                              (33, 41, (0, 1, 1, 0), False), (60, 30, (1, 1, 1, 1), True)])
-def test_stage_adjoint_dot_product(nx, ny, bc, inflow):
-    g = _stage_sim(nx, ny, bc, inflow, moses.FP64, seed=1)
+def test_stage_adjoint_dot_product(nx, ny, bc, inflow, k_mode):
+    g = _stage_sim(nx, ny, bc, inflow, moses.FP64, seed=1, k_mode=k_mode)
     U = g.get_conserved()
     rng = np.random.default_rng(101)
     lam = rng.standard_normal(U.shape)
@@ -111,8 +112,10 @@ def _rolled_out(ny, nx, dj, di):
     return m
 
 
-def test_stage_adjoint_parameter_partials():
-    """lam . dS/d tan(delta_b) and lam . dS/d c_D against central differences."""
+@pytest.mark.parametrize("k_mode", [0, 1])
+def test_stage_adjoint_parameter_partials(k_mode):
+    """lam . dS/d tan(delta_b), lam . dS/d c_D and (k_mode 1) lam . dS/d phi_int
+    against central differences of the stage."""
     nx, ny = 40, 30
     dem = W.spectral_dem(nx, ny, 5.0, 2.2, 30.0, seed=3, band_m=40.0)
     st = _wet_state(nx, ny, 3)
@@ -120,8 +123,9 @@ def test_stage_adjoint_parameter_partials():
     lam = rng.standard_normal((6, ny, nx))
     t, dt = 0.0, 0.01
 
-    def stage(delta_deg, c_d):
-        g = moses.Sim(dem, 5.0, 5.0, W.default_params(delta_b_deg=delta_deg, c_d=c_d, bc=(1, 1, 1, 1)))
+    def stage(delta_deg, c_d, phi_deg=35.0):
+        g = moses.Sim(dem, 5.0, 5.0, W.default_params(delta_b_deg=delta_deg, c_d=c_d, bc=(1, 1, 1, 1), k_mode=k_mode,
+                                                      phi_int_deg=phi_deg))
         g.set_release(st["h"], st["phi_s"], st["vx_s"], st["vy_s"], st["vx_f"], st["vy_f"])
         return g, g.stage(t, dt)
 
@@ -133,6 +137,11 @@ def test_stage_adjoint_parameter_partials():
     fd_cd = (lam * (stage(25.0, 0.05 + 1e-7)[1] - stage(25.0, 0.05 - 1e-7)[1])).sum() / 2e-7
     assert abs(gp[0] - fd_tan) <= 1e-6 * abs(fd_tan), (gp[0], fd_tan)
     assert abs(gp[1] - fd_cd) <= 1e-6 * abs(fd_cd), (gp[1], fd_cd)
+    if k_mode == 0:
+        assert gp[2] == 0.0
+        return
+    fd_phi = (lam * (stage(25.0, 0.05, 35.0 + np.degrees(h))[1] - stage(25.0, 0.05, 35.0 - np.degrees(h))[1])).sum() / (2 * h)
+    assert gp[2] != 0.0 and abs(gp[2] - fd_phi) <= 1e-6 * abs(fd_phi), (gp[2], fd_phi)
 
 
 def test_stage_adjoint_fp32_tracks_fp64():
@@ -175,15 +184,18 @@ def _oracle_loss(cfg, params, dts, hs_t, J, h0=None):
     return float(((hs - hs_t) ** 2).sum() * cfg["dx"] * cfg["dy"])
 
 
-@pytest.mark.parametrize("case", ["spectral64", "arc", "inflow"])
-def test_misfit_gradient_matches_fp64_central_differences(case):
+@pytest.mark.parametrize("case,k_mode", [("spectral64", 0), ("arc", 0), ("inflow", 0), ("spectral64", 1),
+                                         ("arc", 1)])
+def test_misfit_gradient_matches_fp64_central_differences(case, k_mode):
+    """With k_mode 1 also the internal friction angle, which enters through
+    the Savage-Hutter coefficients (and delta_b through them besides tan)."""
     if case == "spectral64":
-        cfg, N, C = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6), 80, 9
+        cfg, N, C = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6, k_mode=k_mode), 80, 9
     elif case == "arc":
         # a pile centred on a cell column stays mirror-symmetric, and across the
         # axis the two x-momentum differences are equal: minmod is at a tie,
         # where the step is not differentiable.  The pile is moved off the axis.
-        cfg, N, C = W.release_config(nx=48, ny=64, cfl=0.2), 60, 7
+        cfg, N, C = W.release_config(nx=48, ny=64, cfl=0.2, k_mode=k_mode), 60, 7
         cfg["h"] = W.parabolic_cap(48, 64, 5.0, 5.0, 24.37, 63 - 30 * 64 // 128, 20 * 48 / 128, 5.0)
     else:  # material enters through a hydrograph: the recompute must see the same times
         cfg, N, C = W.inflow_config(nx=48, ny=32, dx=5.0, inlet_cells=6), 120, 11
@@ -196,12 +208,14 @@ def test_misfit_gradient_matches_fp64_central_differences(case):
     # below the tolerance while the chance of crossing a kink (a cell reaching
     # the dry threshold or the stopping condition) shrinks with the step; two
     # step sizes must agree, which shows that no kink was crossed
-    for name, idx, h in (("delta_b_deg", 0, 1e-5), ("c_d", 2, 1e-8)):
+    params = [("delta_b_deg", 0, 1e-5), ("c_d", 2, 1e-8)] + ([("phi_int_deg", 1, 1e-5)] if k_mode == 1 else [])
+    for name, idx, h in params:
         fd = [(_oracle_loss(cfg, dict(p0, **{name: p0[name] + s}), dts, hs_t, J)
                - _oracle_loss(cfg, dict(p0, **{name: p0[name] - s}), dts, hs_t, J)) / (2 * s) for s in (h, h / 2)]
         assert fd[1] != 0.0 and abs(fd[0] - fd[1]) <= 2e-6 * abs(fd[0]), (name, "finite differences cross a kink", fd)
         assert abs(r["g_params"][idx] - fd[1]) <= 1e-5 * abs(fd[1]), (name, r["g_params"][idx], fd)
-    assert r["g_params"][1] == 0.0
+    if k_mode == 0:
+        assert r["g_params"][1] == 0.0
     if case == "inflow":
         return
     # release thickness: directional derivative along a relative perturbation
@@ -210,8 +224,9 @@ def test_misfit_gradient_matches_fp64_central_differences(case):
     # differences agree to 1e-6 show that none did, and the adjoint must then
     # meet them at the tolerance of the other gradients.
     v = np.random.default_rng(5).standard_normal(cfg["h"].shape) * cfg["h"]
+    steps = (1e-7, 3e-8, 1e-8) if k_mode == 1 else (1e-6, 1e-7, 1e-8)
     fdh = [(_oracle_loss(cfg, p0, dts, hs_t, J, cfg["h"] + s * v) - _oracle_loss(cfg, p0, dts, hs_t, J, cfg["h"] - s * v))
-           / (2 * s) for s in (1e-6, 1e-7, 1e-8)]
+           / (2 * s) for s in steps]
     adh = float((r["g_release_h"] * v).sum())
     for a, b in ((0, 1), (1, 2)):
         assert abs(fdh[a] - fdh[b]) <= 1e-6 * abs(fdh[a]), ("finite differences cross a kink", adh, fdh)
@@ -228,12 +243,13 @@ def test_misfit_gradient_does_not_depend_on_checkpoint_interval():
         assert np.allclose(r["g_release_h"], res[0]["g_release_h"], rtol=1e-12, atol=1e-300)
 
 
-def test_misfit_fp32_gradient_tracks_fp64():
-    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6)
+@pytest.mark.parametrize("k_mode", [0, 1])
+def test_misfit_fp32_gradient_tracks_fp64(k_mode):
+    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6, k_mode=k_mode)
     hs_t, _, _ = _misfit_setup(cfg, 80)
     r64 = moses.from_config(cfg).adjoint_misfit(80, hs_t, ckpt_every=9)
     r32 = moses.from_config(cfg, precision=moses.FP32).adjoint_misfit(80, hs_t, ckpt_every=9)
-    for idx in (0, 2):
+    for idx in ((0, 1, 2) if k_mode else (0, 2)):
         assert abs(r32["g_params"][idx] - r64["g_params"][idx]) <= 1e-3 * abs(r64["g_params"][idx])
 
 
@@ -253,3 +269,21 @@ def test_autograd_function():
     assert abs(float(cd.grad) - 2 * r["g_params"][2]) <= 1e-12 * abs(r["g_params"][2])
     assert float(pi.grad) == 0.0
     assert np.allclose(h0.grad.numpy(), 2 * r["g_release_h"], rtol=1e-12, atol=0)
+
+
+def test_autograd_function_internal_friction():
+    """With the earth-pressure option the internal friction angle has a
+    gradient, and the autograd.Function passes it through."""
+    torch = pytest.importorskip("torch")
+    cfg = W.large_release_config(n=64, dx=5.0, seed=7, volume=2.5e4, radius_cells=6, k_mode=1)
+    hs_t, _, _ = _misfit_setup(cfg, 40)
+    h0 = torch.tensor(cfg["h"], dtype=torch.float64, requires_grad=True)
+    db = torch.tensor(25.0, dtype=torch.float64, requires_grad=True)
+    cd = torch.tensor(1e-3, dtype=torch.float64, requires_grad=True)
+    pi = torch.tensor(35.0, dtype=torch.float64, requires_grad=True)
+    loss = moses.deposit_misfit(cfg, h0, db, cd, pi, hs_t, 40, precision=moses.FP64)
+    loss.backward()
+    r = moses.from_config(cfg).adjoint_misfit(40, hs_t, release_phi=cfg["phi_s"])
+    assert r["g_params"][1] != 0.0
+    assert abs(float(pi.grad) - r["g_params"][1]) <= 1e-12 * abs(r["g_params"][1])
+    assert abs(float(db.grad) - r["g_params"][0]) <= 1e-12 * abs(r["g_params"][0])

@@ -2,8 +2,9 @@
 as the oracle: closed-box conservation, bodies at rest (lake, mixture, heap),
 the Ritter dam break, the Savage-Hutter similarity solution, drag and wave
 speeds, 90-degree rotation invariance, the closed box, the viscous and fluid
-friction checks, the central-upwind pins and the WENO / three-stage
-Runge-Kutta pins.  Each pin builds its inputs and
+friction checks, the central-upwind pins, the WENO / three-stage
+Runge-Kutta pins and the earth-pressure pins (regimes, similarity solutions
+spreading and contracting, celerity, rotation).  Each pin builds its inputs and
 runs a simulation through `_sim`; here `_sim` returns a GPU simulation with
 the oracle's interface, so the kernels are checked against closed forms and
 invariants directly, not only against the oracle.  (Pins that read the
@@ -69,7 +70,9 @@ GPU_PINS = [P.pin_conservation_closed, P.pin_lake_flat, P.pin_lake_plane, P.pin_
             P.pin_wave_speed, P.pin_rotation, P.pin_friction, P.pin_closed_box, P.pin_viscous,
             P.pin_fluid_friction, P.pin_cu_upwind_dependence, P.pin_cu_conservation_and_ritter, P.pin_cu_rotation,
             P.pin_weno_linear_exact, P.pin_weno_rk3_dam_break, P.pin_weno_smooth_order, P.pin_rk3_drag_factor,
-            P.pin_weno_rk3_budgets_and_rotation]
+            P.pin_weno_rk3_budgets_and_rotation,
+            P.pin_earth_pressure_regimes, P.pin_earth_pressure_fluid_unaffected, P.pin_earth_pressure_wave_speed,
+            P.pin_savage_hutter_earth_pressure, P.pin_rotation_earth_pressure]
 
 
 @pytest.mark.parametrize("pin", GPU_PINS, ids=lambda f: f.__name__)

@@ -205,7 +205,8 @@ MUTANTS = [
     ("CFL step from twice the wave speed",
      "double dt = cfl_dt(s, max_speed(s, s->U));", "double dt = cfl_dt(s, 2.0 * max_speed(s, s->U));"),
     ("earth pressure: active and passive regimes swapped",
-     "return (vp - vm < 0.0) ? Kp : Ka;", "return (vp - vm < 0.0) ? Ka : Kp;"),
+     "return (vp - vm < -(1e-6 * (fabs(vp) + fabs(vm)) + 1e-6)) ? Kp : Ka;",
+     "return (vp - vm < -(1e-6 * (fabs(vp) + fabs(vm)) + 1e-6)) ? Ka : Kp;"),
     ("earth pressure: cos^2(delta_b) in place of sec^2(delta_b)",
      "double r = sqrt(1.0 - cp2 / cd2);", "double r = sqrt(1.0 - cp2 * cd2);"),
     ("earth pressure: solid celerity without K",
