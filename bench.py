@@ -545,7 +545,8 @@ def measure_inflow(torch, precision=None):
 
 def measure_adjoint(torch, n=1024, steps=None, ckpt=None):
     """Adjoint calibration workload, FP32 forward: 1024 x 1024 cells at 5 m,
-    spectral DEM, 5000 steps with a checkpoint every 71.  The target deposit
+    spectral DEM, internal friction 35 deg (Savage-Hutter earth pressure),
+    5000 steps with a checkpoint every 71.  The target deposit
     comes from a forward run with the hidden basal friction 22 deg and drag
     3e-3 1/s; the gradient of the deposit misfit at 25 deg, 1e-3 1/s is taken
     with respect to delta_b, phi_int, c_D and the release thickness.  Times:
@@ -575,17 +576,18 @@ def measure_adjoint(torch, n=1024, steps=None, ckpt=None):
         r = g.adjoint_misfit(N, hs_t, ckpt_every=C, release_phi=cfg["phi_s"])
     tf, tb = (float(x) for x in r["timing_ms"])
     gh = r["g_release_h"]
-    return {"config": f"adjoint calibration, {n}x{n} cells at 5 m, spectral DEM, 1e6 m^3 release, FP32 forward, "
-                      f"{N} steps, checkpoint every {C}; target from delta_b 22 deg, c_D 3e-3",
+    return {"config": f"adjoint calibration, {n}x{n} cells at 5 m, spectral DEM, 1e6 m^3 release, phi_int 35 deg "
+                      f"(k_mode 1), FP32 forward, {N} steps, checkpoint every {C}; target from delta_b 22 deg, c_D 3e-3",
             "steps": N, "ckpt_every": C, "dtype": "f32", "forward_ms": fwd_ms,
             "adjoint_forward_ms": tf, "adjoint_backward_ms": tb,
             "backward_over_forward": tb / fwd_ms, "total_over_forward": (tf + tb) / fwd_ms,
             "loss": r["loss"],
             "grad": {"delta_b_per_deg": float(r["g_params"][0]), "phi_int_per_deg": float(r["g_params"][1]),
                      "c_d": float(r["g_params"][2]), "release_h_l2": float(np.sqrt((gh * gh).sum()))},
-            # forward: 2 stages + 2 records per step, misfit; backward: per step 1 time reset,
-            # 2 recording stages, 2 x (cell, face, fold); release gradient
-            "gpu_launches": 4 * N + 1 + 9 * N + 1,
+            # forward: 2 stages of 2 launches per step (the first stage logs the clock), misfit;
+            # backward: per step 2 recording stages of 2 launches and 2 x (cell, face; the face
+            # kernel folds the ghosts on this grid); release gradient
+            "gpu_launches": 4 * N + 1 + 8 * N + 1,
             "fp64_check": "gradients against FP64 central differences of the oracle: tests/test_gpu_adjoint.py"}
 
 

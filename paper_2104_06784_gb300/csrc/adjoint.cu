@@ -46,21 +46,13 @@ int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
 {
     adj_cell_kernel<T><<<dim3((q.f.nx + 31) / 32, (q.f.ny + 7) / 8), 256, 0, st>>>(q);
     if ((q.f.ph.k_mode == 1 ? launch_adj_face<T, true>(q, st) : launch_adj_face<T, false>(q, st)) != 0) return -1;
-    const int nfold = 6 * (2 * q.f.nx + 2 * q.f.ny);
-    adj_fold_kernel<T><<<(nfold + 255) / 256, 256, 0, st>>>(q);
+    if (!q.fold_inline) {
+        const int nfold = 6 * (2 * q.f.nx + 2 * q.f.ny);
+        adj_fold_kernel<T><<<(nfold + 255) / 256, 256, 0, st>>>(q);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-// before step n: its start time; after it: its time step
-__global__ void record_t_kernel(const Ctl *ctl, double *ts, int n) { ts[n] = ctl->t; }
-__global__ void record_dt_kernel(const Ctl *ctl, double *dts, int n) { dts[n] = ctl->dt; }
-// recompute a step exactly as the forward run took it: same time (the inflow
-// hydrograph depends on it) and same time step
-__global__ void set_dt_kernel(Ctl *ctl, double t, double dt)
-{
-    ctl->t = t;
-    ctl->dt_fixed = dt;
-}
 
 // L = sum (h^s - h^s_target)^2 dx dy with h^s = U1 / J; lam = dL/dU (U1 only)
 template <typename T>
@@ -153,11 +145,17 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     const size_t lb = 6 * (size_t)plane * sizeof(T);
     const int nck = (nsteps + C - 1) / C;
     const size_t rb = 6 * (size_t)plane * sizeof(T);  // one stage's record
-    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, gpar, loss_d, tgt, phi_d, hbuf;
+    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, gpar, loss_d, tgt, phi_d, hbuf, zkseg, twseg, lamz;
+    // tiles of the 32 x 8 launches (the forward run, the recording recompute
+    // and the adjoint kernels share this tiling)
+    const int tgx = (nx + 31) / 32, tgy = (ny + 7) / 8;
+    const size_t nt = (size_t)tgx * tgy;
     CK(cudaMalloc(&dts_d.p, 2 * sizeof(double) * nsteps));
     CK(cudaMalloc(&ck.p, sb * nck));
-    CK(cudaMalloc(&seg.p, sb * (2 * C + 1)));
-    CK(cudaMalloc(&recb.p, rb * 2 * C));
+    // two sets of segment buffers: the recompute of one segment runs on a
+    // second stream while the reverse sweep of the segment after it runs
+    CK(cudaMalloc(&seg.p, 2 * sb * (2 * C + 1)));
+    CK(cudaMalloc(&recb.p, 2 * rb * 2 * C));
     for (DevBuf *b : {&lam, &lamA, &lpre}) {
         CK(cudaMalloc(&b->p, lb));
         CK(cudaMemsetAsync(b->p, 0, lb, st));
@@ -168,16 +166,29 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     CK(cudaMemsetAsync(gpar.p, 0, 4 * sizeof(double), st));
     CK(cudaMalloc(&loss_d.p, sizeof(double)));
     CK(cudaMemsetAsync(loss_d.p, 0, sizeof(double), st));
+    // per set: known-zero tile flags of the recompute's output buffers
+    // (segU(1..C), segS(0..C-1); each with its record buffer, a fixed pairing
+    // across segments) and the stages' tile-wet maps of a segment; the
+    // per-tile flags of lam's momentum adjoints (all 0 after the misfit)
+    CK(cudaMalloc(&zkseg.p, 2 * nt * (2 * C + 1)));
+    CK(cudaMemsetAsync(zkseg.p, 0, 2 * nt * (2 * C + 1), st));
+    CK(cudaMalloc(&twseg.p, 2 * nt * 2 * C));
+    CK(cudaMemsetAsync(twseg.p, 0, 2 * nt * 2 * C, st));
+    CK(cudaMalloc(&lamz.p, nt));
+    CK(cudaMemsetAsync(lamz.p, 1, nt, st));
     CK(cudaMalloc(&tgt.p, sizeof(double) * n));
     CK(cudaMemcpyAsync(tgt.p, hs_target, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     if (release_phi) {
         CK(cudaMalloc(&phi_d.p, sizeof(double) * n));
         CK(cudaMemcpyAsync(phi_d.p, release_phi, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     }
-    char *ckp = (char *)ck.p, *segp = (char *)seg.p, *recp = (char *)recb.p;
-    auto segU = [&](int q) { return (T *)(segp + sb * q); };            // U^{start+q}, q = 0..C
-    auto segS = [&](int q) { return (T *)(segp + sb * (C + 1 + q)); };  // U* of step start+q
-    auto rec = [&](int q, int stage) { return (T *)(recp + rb * (2 * q + stage - 1)); };
+    char *ckp = (char *)ck.p;
+    // set b of the segment buffers
+    auto segU = [&](int b, int q) { return (T *)((char *)seg.p + sb * ((2 * C + 1) * b + q)); };  // U^{start+q}
+    auto segS = [&](int b, int q) { return (T *)((char *)seg.p + sb * ((2 * C + 1) * b + C + 1 + q)); };  // U*
+    auto rec = [&](int b, int q, int stage) { return (T *)((char *)recb.p + rb * (2 * C * b + 2 * q + stage - 1)); };
+    auto zks = [&](int b) { return (unsigned char *)zkseg.p + nt * (2 * C + 1) * b; };
+    auto tws = [&](int b) { return (unsigned char *)twseg.p + nt * 2 * C * b; };
 
     cudaEvent_t ev[4];
     for (int q = 0; q < 4; q++) CK(cudaEventCreate(&ev[q]));
@@ -198,20 +209,26 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     a2.Rout = rem<T>(s, s->U);
     a2.stage = 2;
     a2.want_amax = 1;
-    // the forward run steps as moses_step does (wet-tile list)
+    // the forward run steps as moses_step does (wet-tile list, known-zero tile
+    // flags of U and U* for the 32 x 8 tiling, cleared first)
     a1.wl = a2.wl = s->wl;
     a1.wl_n = a2.wl_n = s->wl_n;
     a1.tw_next = s->tw[0];
     a2.tw_prev = s->tw[0];
     a2.tw_next = s->tw[1];
+    CK(cudaMemsetAsync(s->zk, 0, 2 * nt, st));
+    a1.zk = s->zk + nt;
+    a2.zk = s->zk;
     const double zero = 0.0;
     CK(cudaMemcpyAsync(&s->ctl->dt_fixed, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(&s->ctl->t_end, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
+    // the first stage of each step logs its start time and time step
+    a1.t_log = (double *)dts_d.p + nsteps;
+    a1.dt_log = (double *)dts_d.p;
     for (int k = 0; k < nsteps; k++) {
         if (k % C == 0) CK(cudaMemcpyAsync(ckp + sb * (k / C), s->U, sb, cudaMemcpyDeviceToDevice, st));
-        record_t_kernel<<<1, 1, 0, st>>>(s->ctl, (double *)dts_d.p + nsteps, k);
+        a1.log_idx = k;
         if (launch_stage<T>(a1, 0, st) || launch_stage<T>(a2, 0, st)) return fail(s, MOSES_ECUDA, "forward launch");
-        record_dt_kernel<<<1, 1, 0, st>>>(s->ctl, (double *)dts_d.p, k);
     }
     CK(cudaGetLastError());
     Ctl ctl_end;
@@ -230,53 +247,113 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     q.lam_dp = (T *)ldp.p;
     q.g_param = (double *)gpar.p;
     q.lam_next = (const T *)lam.p;
-    for (int kseg = nck - 1; kseg >= 0; kseg--) {
-        const int start = kseg * C, end = std::min(start + C, nsteps);
-        // recompute the segment into its buffers, recording each stage
-        CK(cudaMemcpyAsync(segU(0), ckp + sb * kseg, sb, cudaMemcpyDeviceToDevice, st));
+    q.tgx = tgx;
+    q.tgy = tgy;
+    q.lamz = (unsigned char *)lamz.p;
+    // every ghost's source lies in the tile that owns the ghost (32 x 8 tiles)
+    q.fold_inline = (nx == 1 || nx % ATX != 1) && (ny == 1 || ny % ATY != 1);
+    // The recompute of segment k runs on stream rs into set k & 1, after the
+    // sweep that last read that set (segment k + 2); the sweep of segment k
+    // runs on st after its recompute.  Issuing the recompute of k - 1 before
+    // the sweep of k lets the two overlap: both are latency-bound on a few
+    // wet tiles.  Only the recompute touches the control block and the
+    // wet-tile list; the sweep reads its set and its own adjoint buffers.
+    cudaStream_t rs = nullptr;
+    cudaEvent_t rec_done[2] = {nullptr, nullptr}, sweep_done[2] = {nullptr, nullptr};
+    struct Streams {
+        cudaStream_t &rs;
+        cudaEvent_t *a, *b;
+        ~Streams()
+        {
+            if (rs) cudaStreamDestroy(rs);
+            for (int k = 0; k < 2; k++) {
+                if (a[k]) cudaEventDestroy(a[k]);
+                if (b[k]) cudaEventDestroy(b[k]);
+            }
+        }
+    } streams_guard{rs, rec_done, sweep_done};
+    CK(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; k++) {
+        CK(cudaEventCreateWithFlags(&rec_done[k], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&sweep_done[k], cudaEventDisableTiming));
+    }
+    bool swept[2] = {false, false};
+    auto recompute = [&](const int kseg) -> int {
+        const int b = kseg & 1, start = kseg * C, end = std::min(start + C, nsteps);
+        if (swept[b]) CK(cudaStreamWaitEvent(rs, sweep_done[b], 0));
+        CK(cudaMemcpyAsync(segU(b, 0), ckp + sb * kseg, sb, cudaMemcpyDeviceToDevice, rs));
         for (int k = start; k < end; k++) {
             const int m = k - start;
-            set_dt_kernel<<<1, 1, 0, st>>>(s->ctl, dts[nsteps + k], dts[k]);
             StageArgs<T> r1 = a1, r2 = a2;
+            // the step's start time and time step as the forward run took them
+            r1.t_log = r1.dt_log = nullptr;
+            r1.fix = 1;
+            r1.fix_t = dts[nsteps + k];
+            r1.fix_dt = dts[k];
             // (the recording stages run on the wet-tile list too, tile 32 x 8)
-            r1.Uin = segU(m);
-            r1.Uout = segS(m);
-            r1.Rin = rem<T>(s, segU(m));
-            r1.Rout = rem<T>(s, segS(m));
-            r1.rec = rec(m, 1);
-            r2.Uin = segS(m);
-            r2.Un = segU(m);
-            r2.Uout = segU(m + 1);
-            r2.Rin = rem<T>(s, segS(m));
-            r2.Rn = rem<T>(s, segU(m));
-            r2.Rout = rem<T>(s, segU(m + 1));
-            r2.rec = rec(m, 2);
+            r1.Uin = segU(b, m);
+            r1.Uout = segS(b, m);
+            r1.Rin = rem<T>(s, segU(b, m));
+            r1.Rout = rem<T>(s, segS(b, m));
+            r1.rec = rec(b, m, 1);
+            r2.Uin = segS(b, m);
+            r2.Un = segU(b, m);
+            r2.Uout = segU(b, m + 1);
+            r2.Rin = rem<T>(s, segS(b, m));
+            r2.Rn = rem<T>(s, segU(b, m));
+            r2.Rout = rem<T>(s, segU(b, m + 1));
+            r2.rec = rec(b, m, 2);
             r2.want_amax = 0;
-            if (launch_stage_rec<T>(r1, st) || launch_stage_rec<T>(r2, st))
+            r1.zk = zks(b) + nt * (C + 1 + m);
+            r2.zk = zks(b) + nt * (m + 1);
+            r1.tw_next = tws(b) + nt * (2 * m);
+            r2.tw_prev = tws(b) + nt * (2 * m);
+            r2.tw_next = tws(b) + nt * (2 * m + 1);
+            if (launch_stage_rec<T>(r1, rs) || launch_stage_rec<T>(r2, rs))
                 return fail(s, MOSES_ECUDA, "recompute launch");
         }
+        CK(cudaEventRecord(rec_done[b], rs));
+        return MOSES_OK;
+    };
+    auto sweep = [&](const int kseg) -> int {
+        const int b = kseg & 1, start = kseg * C, end = std::min(start + C, nsteps);
+        CK(cudaStreamWaitEvent(st, rec_done[b], 0));
         for (int k = end - 1; k >= start; k--) {
             const int m = k - start;
             q.f = base_args<T>(s);
             q.f.debug_stage = 1;
             q.f.dbg_dt = dts[k];
-            q.U_next = segU(m + 1);
+            q.U_next = segU(b, m + 1);
             // stage 2 at U*: lam_out = the Heun term of lam^{n+1} -> lamA
-            q.f.Uin = segS(m);
-            q.f.rec = rec(m, 2);
+            q.f.Uin = segS(b, m);
+            q.f.rec = rec(b, m, 2);
+            q.tw = tws(b) + nt * (2 * m + 1);
             q.heun = 2;
             q.lam_out = nullptr;
             q.lam_in = (T *)lamA.p;
             if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
             // stage 1 at U^n: lam_out = lamA; lam^n = its input adjoint + the Heun term, over lam^{n+1}
-            q.f.Uin = segU(m);
-            q.f.rec = rec(m, 1);
+            q.f.Uin = segU(b, m);
+            q.f.rec = rec(b, m, 1);
+            q.tw = tws(b) + nt * (2 * m);
             q.heun = 1;
             q.lam_out = (const T *)lamA.p;
             q.lam_in = (T *)lam.p;
             if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
         }
+        CK(cudaEventRecord(sweep_done[b], st));
+        swept[b] = true;
+        return MOSES_OK;
+    };
+    // the recompute stream starts after the forward run and the misfit
+    CK(cudaEventRecord(sweep_done[0], st));
+    CK(cudaStreamWaitEvent(rs, sweep_done[0], 0));
+    int rc = recompute(nck - 1);
+    for (int kseg = nck - 1; kseg >= 0 && rc == 0; kseg--) {
+        if (kseg > 0) rc = recompute(kseg - 1);
+        if (rc == 0) rc = sweep(kseg);
     }
+    if (rc) return rc;
     CK(cudaGetLastError());
     CK(cudaEventRecord(ev[2], st));
     // ---- outputs; the state and the clock go back to the end of the forward run ----

@@ -157,7 +157,36 @@ struct AdjArgs {
     int heun;
     const T *lam_next;  // lam^{n+1} (6 planes, interior)
     const T *U_next;    // U^{n+1} (its dry mask)
+    // Tiles far from any mass (the run of many steps): tw is the stage's
+    // tile-wet map of the recording recompute (32 x 8 tiles, tgx x tgy; null:
+    // every tile computes).  A tile with no wet tile within two tiles has no
+    // mass near its cells, the face tiles that read its cells' lam_pre and
+    // lam_dp are dry too, and the exact reverse there is the identity on the
+    // mass adjoints with zero momentum adjoints: the second Heun stage skips
+    // it (its lam_in is read only where the first stage computes), the first
+    // stage leaves lam in place and zeroes its momentum planes unless lamz
+    // (one byte per tile: the tile's momentum adjoints of lam are 0) says so.
+    const unsigned char *tw;
+    int tgx, tgy;
+    unsigned char *lamz;
+    // the face kernel folds the ghost adjoints its tile owns into their
+    // sources itself (every source lies in the owning tile: the last tile
+    // along each axis holds two cells or more), and no fold kernel runs
+    int fold_inline;
 };
+
+// the tile (bx, by) of the adjoint kernels lies two tiles or more from every
+// wet tile of the stage (see AdjArgs::tw)
+template <typename T>
+__device__ __forceinline__ bool adj_far_from_mass(const AdjArgs<T> &q, int bx, int by)
+{
+    for (int dy = -2; dy <= 2; dy++)
+        for (int dx = -2; dx <= 2; dx++) {
+            const int xx = bx + dx, yy = by + dy;
+            if (xx >= 0 && xx < q.tgx && yy >= 0 && yy < q.tgy && q.tw[yy * q.tgx + xx]) return false;
+        }
+    return true;
+}
 
 // 1/2 lam^{n+1}, momenta zeroed where U^{n+1} is dry (adjoint of the Heun
 // average followed by the dry rule), component c of cell g
@@ -202,6 +231,20 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
     const T *geo = a.geo;
     const double dt = a.dbg_dt;
     const T dtT = (T)dt;
+    if (q.tw && adj_far_from_mass(q, blockIdx.x, blockIdx.y)) {  // CTA-uniform (AdjArgs::tw)
+        if (q.heun != 1) return;
+        const int tile = blockIdx.y * q.tgx + blockIdx.x;
+        if (q.lamz[tile]) return;
+        if (i < nx && j < ny) {
+            const long long g = cell_index(i, j, pitch);
+#pragma unroll
+            for (int c = 0; c < 6; c++)
+                if (c != 0 && c != 3) q.lam_in[c * plane + g] = T(0);
+        }
+        if (tid == 0) q.lamz[tile] = 1;
+        return;
+    }
+    if (q.lamz && q.heun == 1 && tid == 0) q.lamz[blockIdx.y * q.tgx + blockIdx.x] = 0;
     // parameter partials: per cell and across the warp in T, per CTA and
     // globally in FP64 (the FP64 pipe of GB300 is 1/64 of its FP32 rate)
     T g_tan = T(0), g_cd = T(0);
@@ -669,6 +712,49 @@ __device__ __forceinline__ void adj_ghost_zero(const AdjArgs<T> &q)
 }
 
 // FP32: three 256-thread CTAs per SM (80 registers); FP64: shared memory allows two
+// The fold of kernel C for the ghost cells this face tile owns (as
+// adj_face_dir assigns them), by the tile itself once its cells hold their
+// face terms: every source of these ghosts lies in the tile (AdjArgs::fold_inline).
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void adj_fold_tile(const AdjArgs<T> &q)
+{
+    constexpr int NT = TX * TY;
+    const StageArgs<T> &a = q.f;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const long long plane = a.plane;
+#pragma unroll
+    for (int D = 0; D < 2; D++) {
+        const int L = D == 0 ? TX : TY, M = D == 0 ? TY : TX;
+        const int o0 = D == 0 ? x0 : y0;
+        const int n = D == 0 ? a.nx : a.ny, nt = D == 0 ? a.ny : a.nx;
+        for (int e = threadIdx.x; e < 24 * M; e += NT) {
+            const int c = e / (4 * M), r = e - c * 4 * M, m = r >> 2, w = r & 3;
+            const int line = (D == 0 ? y0 : x0) + m;
+            if (line >= nt || (w < 2 ? o0 != 0 : !(o0 <= n - 1 && n - 1 < o0 + L))) continue;
+            const int side = 2 * D + (w < 2 ? 0 : 1);
+            bool inflow = false;
+            for (int f = 0; f < a.n_inflow; f++)
+                inflow |= a.inflow[f].side == side && line >= a.inflow[f].i0 && line < a.inflow[f].i1;
+            if (inflow) continue;  // the ghost state is a given function of time
+            const bool closed = a.ph.bc[side] == 0;
+            const bool flip = closed && (D == 0 ? (c == 1 || c == 4) : (c == 2 || c == 5));
+            const int kk = w & 1;
+            int gpos, src;
+            if (w < 2) {
+                gpos = -1 - kk;
+                src = closed ? (kk < n ? kk : n - 1) : 0;
+            } else {
+                gpos = n + kk;
+                src = closed ? (n - 1 - kk >= 0 ? n - 1 - kk : 0) : n - 1;
+            }
+            const long long gg = D == 0 ? cell_index(gpos, line, a.pitch) : cell_index(line, gpos, a.pitch);
+            const long long gs = D == 0 ? cell_index(src, line, a.pitch) : cell_index(line, src, a.pitch);
+            const T v = q.lam_in[c * plane + gg];
+            if (v != T(0)) atomicAdd(&q.lam_in[c * plane + gs], flip ? -v : v);
+        }
+    }
+}
+
 template <typename T, int TX, int TY, bool KM = false>
 __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY)) adj_face_kernel(const AdjArgs<T> q)
 {
@@ -690,6 +776,11 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
+    if (q.tw && adj_far_from_mass(q, blockIdx.x, blockIdx.y)) {  // CTA-uniform: no face terms (AdjArgs::tw)
+        adj_ghost_zero<T, TX, TY, 0>(q);
+        adj_ghost_zero<T, TX, TY, 1>(q);
+        return;
+    }
     // The stage input's masses with a 3-cell halo come first (cells beyond
     // the 2 ghost layers read 0; no forward face uses them).  Where none of
     // them holds mass, every face state of the tile is dry: the side fluxes'
@@ -829,6 +920,10 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
             if (s0 != 0.0) atomicAdd(&q.g_param[2], s0);
             if (s1 != 0.0) atomicAdd(&q.g_param[3], s1);
         }
+    }
+    if (q.fold_inline && wet) {  // CTA-uniform; a dry tile's ghosts hold 0
+        __syncthreads();  // the tile's cells hold their face terms
+        adj_fold_tile<T, TX, TY>(q);
     }
 }
 

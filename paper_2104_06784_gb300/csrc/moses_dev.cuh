@@ -219,6 +219,15 @@ struct alignas(8) StageArgs {
     // testing only: extra bytes the classification's copy barrier expects and
     // no copy delivers, so that its bounded wait runs out (0 normally)
     unsigned int dbg_stall_tx;
+    // the adjoint's runs: fix != 0 makes the step's first stage start at fix_t
+    // with the time step fix_dt (a recomputed step, as the forward took it)
+    // instead of the control block's time and CFL step; with t_log non-null
+    // the first stage writes the step's start time and time step to
+    // t_log[log_idx], dt_log[log_idx] (the forward run's record)
+    int fix;
+    double fix_t, fix_dt;
+    double *t_log, *dt_log;
+    int log_idx;
 };
 
 __host__ __device__ inline long long cell_index(int i, int j, int pitch)

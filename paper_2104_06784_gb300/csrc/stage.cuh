@@ -624,6 +624,20 @@ __device__ __forceinline__ void coulomb(double &q1, double &q2, double bX, doubl
     coulomb(q1, q2, bX, bY, Fr);
 }
 
+// The first stage of a step publishes its time step to the later stages (and,
+// when the step's start time was given, that time too); the adjoint's forward
+// run also logs both (StageArgs::fix, t_log).  One thread of one CTA.
+template <typename T>
+__device__ __forceinline__ void first_stage_clock(const StageArgs<T> &a, double t_now, double dt)
+{
+    a.ctl->dt = dt;
+    if (a.fix) a.ctl->t = t_now;
+    if (a.t_log) {
+        a.t_log[a.log_idx] = t_now;
+        a.dt_log[a.log_idx] = dt;
+    }
+}
+
 // End of a step, by the last CTA of its last stage: publish a_max (the exact
 // maximum of the step's cell speeds, reduced on their IEEE bits) and advance t.
 template <typename T>
@@ -706,6 +720,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         if (a.debug_stage) {
             t_now = a.dbg_t;
             dt = a.dbg_dt;
+        } else if (a.stage == 1 && a.fix) {
+            t_now = a.fix_t;
+            dt = a.fix_dt;
         } else if (a.stage == 1) {
             t_now = ctl->t;
             dt = dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
@@ -1328,7 +1345,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             atomicAdd(&ctl->clamp_vol[1], acc[3]);
             atomicAdd(&ctl->clamp_cells, (unsigned long long)acc_n);
         }
-        if (a.stage == 1 && bx == 0 && by == 0) ctl->dt = dt;
+        if (a.stage == 1 && bx == 0 && by == 0) first_stage_clock(a, a.fix ? a.fix_t : ctl->t, dt);
         if (finalize) {
             if (a.want_amax) {
                 T m = T(0);
@@ -1510,10 +1527,12 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
         if (tid == 0) mbar_init(&s_bar, 1);
         __syncthreads();
         if (tid == 0) {
-            const double t_now = ctl->t;
-            const double dt = a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
+            const bool fixed = a.stage == 1 && a.fix;
+            const double t_now = fixed ? a.fix_t : ctl->t;
+            const double dt = fixed ? a.fix_dt
+                            : a.stage == 1 ? dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax)) : ctl->dt;
             s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
-            if (a.stage == 1 && bx == 0 && sy == 0) ctl->dt = dt;
+            if (a.stage == 1 && bx == 0 && sy == 0) first_stage_clock(a, t_now, dt);
             // (a.dbg_stall_tx: bytes no copy delivers, so that the wait below runs out; testing only)
             mbar_expect_tx(&s_bar, rb * (unsigned int)nc + a.dbg_stall_tx);
         }

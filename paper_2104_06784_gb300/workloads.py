@@ -258,9 +258,12 @@ def adjoint_config(n: int = 1024, dx: float = 5.0, seed: int = 0, **over) -> dic
     """Calibration workload: the large-release terrain at n x n cells of dx
     (spectral DEM, relief 1500 m x n / 4096, one carved valley) with a
     1e6 m^3 parabolic-cap release of radius 43 cells on a 30-40 deg slope;
-    FP32 state; 5000 steps with a checkpoint every 71; the target deposit comes
-    from the hidden basal friction 22 deg and drag 3e-3 1/s, the start is
-    25 deg and 1e-3 1/s."""
+    internal friction 35 deg through the Savage-Hutter earth-pressure option
+    (k_mode 1), so that both friction angles have gradients; FP32 state; 5000
+    steps with a checkpoint every 71; the target deposit comes from the hidden
+    basal friction 22 deg and drag 3e-3 1/s, the start is 25 deg and
+    1e-3 1/s."""
+    over = dict(dict(k_mode=1), **over)
     cfg = large_release_config(n=n, dx=dx, seed=seed, volume=1e6, radius_cells=43.0, **over)
     cfg.update(name=f"adjoint calibration {n}x{n} dx={dx} m", steps=5000, ckpt_every=71, precision="fp32",
                hidden=dict(delta_b_deg=22.0, c_d=3e-3))
