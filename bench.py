@@ -76,8 +76,9 @@ N_WINDOWS = 4        # timed windows, at the start of each quarter of the event
 # for the stage kernel source it was taken on (sha256 of csrc/stage.cuh,
 # first 12).
 TRAFFIC_PER_CELL_STAGE = {
-    # profiles/stage_kernel_list_wet_2048_full.md
-    ("f64", "beb8a8d2e738"): 273.0 + 46.0,
+    # profiles/stage_kernel_list_all_wet_2048.md
+    ("f64", "4b85dae668f9"): 315.45,
+    ("f32", "4b85dae668f9"): 72.92,
 }
 
 
@@ -339,9 +340,11 @@ def run_event(sim, torch, nsteps=EVENT_STEPS, nwin=N_WINDOWS, tile=(32, 8)):
                    "t_end_s": b["t"], "wet_tiles_end": wet_tile_fraction(U, *tile), "segments": segs}
 
 
-def measure_windows(sim, ckpts, K, W, torch, sampler=None):
+def measure_windows(sim, ckpts, K, W, torch, sampler=None, nvtx=None):
     """K steps timed (after W warm-up steps) from each checkpoint: CUDA events
-    on the simulation's stream around the K steps of each window."""
+    on the simulation's stream around the K steps of each window.  With
+    `nvtx` the timed steps sit in an NVTX range of that name (a profiler can
+    then take exactly those launches)."""
     stream = torch.cuda.current_stream()
     out = []
     for ck in ckpts:
@@ -351,9 +354,13 @@ def measure_windows(sim, ckpts, K, W, torch, sampler=None):
         e0, e1 = _events(torch)
         if sampler is not None:
             sampler.begin()
+        if nvtx:
+            torch.cuda.nvtx.range_push(nvtx)
         e0.record(stream)
         sim.step(K)
         e1.record(stream)
+        if nvtx:
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if sampler is not None:
             sampler.end()
@@ -413,6 +420,7 @@ def measure_dense(cfg, K, Wm, torch, fp64_tflops, hbm_gbs, h):
         else:
             out[form]["alu"] = {"achieved": tfl, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": tfl / FP32_PEAK_TFLOPS, "peak_source": "unit counts x 2.07 GHz"}
+            out[form]["traffic_per_launch"] = _traffic("f32", h, cells)
     return out
 
 
@@ -690,7 +698,8 @@ def main():
         if dist is not None:
             dist.barrier()
         with (sampler if name == "f64" else _Null()):
-            win_ms = measure_windows(sim, ckpts, K, Wm, torch, sampler if name == "f64" else None)
+            win_ms = measure_windows(sim, ckpts, K, Wm, torch, sampler if name == "f64" else None,
+                                     nvtx=f"headline_windows_{name}")
         del ckpts
         ms = max_over_ranks(sum(win_ms))
         results[name] = dict(ms=ms, win_ms=win_ms, event=event, sim=sim)
@@ -712,7 +721,7 @@ def main():
               "hbm": {"achieved": d64["hbm"]["achieved"], "peak": pk["hbm_gbs"], "unit": "GB/s",
                       "frac": d64["hbm"]["frac"], "bytes_per_cell_step": 104, "peak_source": pk_src}}
     roof32 = {"bound": "hbm", "achieved": d32["hbm"]["achieved"], "peak": pk["hbm_gbs"], "unit": "GB/s",
-              "frac": d32["hbm"]["frac"], "traffic": _traffic("f32", h, cells),
+              "frac": d32["hbm"]["frac"], "traffic": d32["traffic_per_launch"],
               "kernel": "moses::stage_kernel_list<float,32,8> with its classification launch, one stage, "
                         "on the all-wet 4096^2 state (52 B per cell-step)",
               "peak_source": pk_src, "alu": d32["alu"]}

@@ -226,6 +226,51 @@ int moses_stage(moses_sim *s, double t, double dt, double *U_out);
  * step), reduced exactly on the GPU. */
 int moses_max_speed(moses_sim *s, double *amax);
 
+/* ---- One strip of a row-decomposed domain ------------------------------
+ *
+ * The paper runs one simulation per GPU (Sect. 3.2).  A domain too large for
+ * one GPU is split into strips of whole rows, one simulation per strip, each
+ * created on its own rows plus `o` rows of overlap on every side that meets
+ * another strip (its window), with that strip's slice of the DEM and
+ * release.  o = 2 x (stages per step) + 1: a stage reads state and bed
+ * geometry two cells away, and the geometry of a window's last row comes
+ * from a bed extrapolated past the window.  Every step each strip steps its
+ * whole window,
+ * then receives the o overlap rows from the strips that own them
+ * (moses_get_rows_device there, moses_set_rows_device here), and the
+ * strips agree on the CFL maximum (the largest moses_max_speed of all
+ * strips, written back with moses_set_max_speed).  The owned rows then
+ * evolve bit for bit as in the undecomposed run: their stencils see only
+ * exact values, and the maximum is the same exact maximum.  The host side
+ * of this (row split, exchange over torch.distributed, maximum) is
+ * paper_2104_06784_gb300/decomp.py. */
+
+/* Rows [j0, j1) of this simulation are its own: only their cells enter the
+ * CFL maximum, the clamp counts and the volume sums of moses_get_budget,
+ * only their boundary faces the boundary inflow.  Default: every row.
+ * A strip with owned rows set joins no batch and has no adjoint (EINVAL). */
+int moses_set_owned_rows(moses_sim *s, int j0, int j1);
+
+/* Planes per row of the row buffers: 6 (FP64 state) or 8 (FP32 state and
+ * its two mass remainder planes).  0 for NULL. */
+int moses_row_planes(const moses_sim *s);
+
+/* Rows [j0, j0 + nrows) of the state to / from a device buffer owned by the
+ * caller, moses_row_planes(s) * nrows * nx doubles, [plane][row][i] (exact
+ * in both directions for values of the simulation's precision).  get is
+ * asynchronous on the simulation's stream.  set takes the values as given
+ * (no validation: a non-finite value raises MOSES_ENONFINITE at the next
+ * step), refills the ghost cells those rows own at the current time, and
+ * updates the stepping launches' per-tile records (known-zero flags, mass
+ * bits) of the tiles it touches; it is asynchronous too.  EINVAL: rows
+ * outside the grid; ESTATE: no state set yet. */
+int moses_get_rows_device(moses_sim *s, int j0, int nrows, double *rows_device);
+int moses_set_rows_device(moses_sim *s, int j0, int nrows, const double *rows_device);
+
+/* Replace the CFL maximum the next step takes its time step from (finite,
+ * >= 0; the maximum over all strips).  Synchronous. */
+int moses_set_max_speed(moses_sim *s, double amax);
+
 /* FP64 budgets, reduced on the GPU: out[0..1] solid / fluid volume
  * sum(U1), sum(U4) dx dy [m^3]; out[2..5] momenta sum(U2, U3, U5, U6) dx dy;
  * out[6..7] time-integrated boundary volume inflow per phase (the computed

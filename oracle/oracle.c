@@ -1094,6 +1094,15 @@ double orc_last_dt(const orc_sim *s) { return s->last_dt; }
 
 double orc_max_speed(orc_sim *s) { return max_speed(s, s->U); }
 
+/* the largest cell speed over rows [j0, j1) (a strip's own rows) */
+double orc_max_speed_rows(orc_sim *s, int j0, int j1)
+{
+    double m = 0.0;
+    for (int j = j0 < 0 ? 0 : j0; j < j1 && j < s->ny; j++)
+        for (int i = 0; i < s->nx; i++) m = fmax(m, cell_speed(s, i, j, s->U));
+    return m;
+}
+
 double orc_cfl_dt(orc_sim *s) { return cfl_dt(s, max_speed(s, s->U)); }
 
 /* n CFL-limited steps; dts (optional, n entries) receives the time steps */
@@ -1105,6 +1114,18 @@ int orc_step(orc_sim *s, int n, double *dts)
         if (dts) dts[k] = dt;
     }
     return ORC_OK;
+}
+
+/* one step whose CFL time step comes from the given largest wave speed
+   instead of this simulation's own: a strip of a row-decomposed domain
+   steps with the largest speed of all strips (the whole domain's a_max,
+   Sect. 2.2), so that every strip takes the undecomposed step.  Returns the
+   time step. */
+double orc_step_amax(orc_sim *s, double amax)
+{
+    double dt = cfl_dt(s, amax);
+    time_step(s, dt);
+    return dt;
 }
 
 /* one Heun step with a prescribed time step */

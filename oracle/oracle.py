@@ -98,10 +98,14 @@ def _declare(L):
     L.orc_last_dt.restype = C.c_double
     L.orc_max_speed.argtypes = [vp]
     L.orc_max_speed.restype = C.c_double
+    L.orc_max_speed_rows.argtypes = [vp, C.c_int, C.c_int]
+    L.orc_max_speed_rows.restype = C.c_double
     L.orc_cfl_dt.argtypes = [vp]
     L.orc_cfl_dt.restype = C.c_double
     L.orc_step.argtypes = [vp, C.c_int, dp]
     L.orc_step_dt.argtypes = [vp, C.c_double]
+    L.orc_step_amax.argtypes = [vp, C.c_double]
+    L.orc_step_amax.restype = C.c_double
     L.orc_stage.argtypes = [vp, C.c_double, C.c_double, dp]
     L.orc_budget.argtypes = [vp, dp]
     L.orc_geometry.argtypes = [vp, dp]
@@ -191,6 +195,10 @@ class OracleSim:
     def max_speed(self) -> float:
         return self._L.orc_max_speed(self._h)
 
+    def max_speed_rows(self, j0: int, j1: int) -> float:
+        """The largest cell speed over rows [j0, j1)."""
+        return self._L.orc_max_speed_rows(self._h, int(j0), int(j1))
+
     def cfl_dt(self) -> float:
         return self._L.orc_cfl_dt(self._h)
 
@@ -201,6 +209,11 @@ class OracleSim:
 
     def step_dt(self, dt: float):
         self._L.orc_step_dt(self._h, float(dt))
+
+    def step_amax(self, amax: float) -> float:
+        """One step with the CFL time step of the given largest wave speed
+        (a strip of a decomposed domain); returns the time step."""
+        return self._L.orc_step_amax(self._h, float(amax))
 
     def stage(self, t: float, dt: float) -> np.ndarray:
         out = np.empty((6, self.ny, self.nx))

@@ -145,7 +145,7 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     const size_t lb = 6 * (size_t)plane * sizeof(T);
     const int nck = (nsteps + C - 1) / C;
     const size_t rb = 6 * (size_t)plane * sizeof(T);  // one stage's record
-    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, gpar, loss_d, tgt, phi_d, hbuf, zkseg, twseg, lamz;
+    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, gpar, loss_d, tgt, phi_d, hbuf, zkseg, twseg, lamz, mbseg;
     // tiles of the 32 x 8 launches (the forward run, the recording recompute
     // and the adjoint kernels share this tiling)
     const int tgx = (nx + 31) / 32, tgy = (ny + 7) / 8;
@@ -173,6 +173,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     CK(cudaMalloc(&zkseg.p, 2 * nt * (2 * C + 1)));
     CK(cudaMemsetAsync(zkseg.p, 0, 2 * nt * (2 * C + 1), st));
     CK(cudaMalloc(&twseg.p, 2 * nt * 2 * C));
+    // mass bits of each buffer of the two segment sets (written before read)
+    CK(cudaMalloc(&mbseg.p, 2 * sizeof(unsigned short) * nt * (2 * C + 1)));
     CK(cudaMemsetAsync(twseg.p, 0, 2 * nt * 2 * C, st));
     CK(cudaMalloc(&lamz.p, nt));
     CK(cudaMemsetAsync(lamz.p, 1, nt, st));
@@ -189,6 +191,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     auto rec = [&](int b, int q, int stage) { return (T *)((char *)recb.p + rb * (2 * C * b + 2 * q + stage - 1)); };
     auto zks = [&](int b) { return (unsigned char *)zkseg.p + nt * (2 * C + 1) * b; };
     auto tws = [&](int b) { return (unsigned char *)twseg.p + nt * 2 * C * b; };
+    // mass bits of segU(b, m) at m, of segS(b, m) at C + 1 + m
+    auto mbs = [&](int b) { return (unsigned short *)mbseg.p + nt * (2 * C + 1) * b; };
 
     cudaEvent_t ev[4];
     for (int q = 0; q < 4; q++) CK(cudaEventCreate(&ev[q]));
@@ -219,6 +223,14 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     CK(cudaMemsetAsync(s->zk, 0, 2 * nt, st));
     a1.zk = s->zk + nt;
     a2.zk = s->zk;
+    // mass bits of U and U* (the first stage of the first step classifies
+    // from the data and writes U's)
+    a1.mb_in = s->mb;
+    a1.mb_out = s->mb + nt;
+    a2.mb_in = s->mb + nt;
+    a2.mb_n = s->mb;
+    a2.mb_out = s->mb;
+    a2.mb_ok = 1;
     const double zero = 0.0;
     CK(cudaMemcpyAsync(&s->ctl->dt_fixed, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(&s->ctl->t_end, &zero, sizeof(double), cudaMemcpyHostToDevice, st));
@@ -228,6 +240,7 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     for (int k = 0; k < nsteps; k++) {
         if (k % C == 0) CK(cudaMemcpyAsync(ckp + sb * (k / C), s->U, sb, cudaMemcpyDeviceToDevice, st));
         a1.log_idx = k;
+        a1.mb_ok = k > 0;
         if (launch_stage<T>(a1, 0, st) || launch_stage<T>(a2, 0, st)) return fail(s, MOSES_ECUDA, "forward launch");
     }
     CK(cudaGetLastError());
@@ -309,6 +322,14 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
             r1.tw_next = tws(b) + nt * (2 * m);
             r2.tw_prev = tws(b) + nt * (2 * m);
             r2.tw_next = tws(b) + nt * (2 * m + 1);
+            // mass bits: the segment's first stage classifies from the data
+            r1.mb_in = mbs(b) + nt * m;
+            r1.mb_out = mbs(b) + nt * (C + 1 + m);
+            r1.mb_ok = m > 0;
+            r2.mb_in = mbs(b) + nt * (C + 1 + m);
+            r2.mb_n = mbs(b) + nt * m;
+            r2.mb_out = mbs(b) + nt * (m + 1);
+            r2.mb_ok = 1;
             if (launch_stage_rec<T>(r1, rs) || launch_stage_rec<T>(r2, rs))
                 return fail(s, MOSES_ECUDA, "recompute launch");
         }
@@ -416,6 +437,7 @@ int moses_adjoint_misfit(moses_sim *s, int nsteps, int ckpt_every, const double 
         return fail(s, MOSES_EINVAL, "the adjoint covers the paper's scheme only (central, minmod, two-step)");
     if (s->ph.k_mode == 1 && !(s->p.delta_b_deg < s->p.phi_int_deg))
         return fail(s, MOSES_EINVAL, "the adjoint of k_mode 1 needs delta_b < phi_int (K has no derivative at equality)");
+    if (is_strip(s)) return fail(s, MOSES_EINVAL, "the adjoint covers a whole domain, not a strip of one");
     if (!s->have_state) return fail(s, MOSES_ESTATE, "no state");
     return s->prec == MOSES_FP64
                ? adjoint_impl<double>(s, nsteps, ckpt_every, hs_target, loss, g_params, g_state0, g_release_h,

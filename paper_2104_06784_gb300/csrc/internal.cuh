@@ -33,6 +33,9 @@ struct moses_sim {
     // zk_valid, and the next step starts from all-zero flags.
     unsigned char *zk = nullptr;
     bool zk_valid = false;
+    // mass bits of U, Us and Us2 (StageArgs::mb_in), valid with zk_valid: the
+    // first stage of a step then classifies from U's bits
+    unsigned short *mb = nullptr;
     int dbg_stall = 0;              // moses_debug_timeout: the classification's copy wait runs out
     Ctl *ctl = nullptr;    // device control block
     InflowSeg *inflow_d = nullptr;
@@ -42,6 +45,7 @@ struct moses_sim {
     double *red = nullptr;        // 8 doubles for reductions
     bool have_state = false;
     int tile = 0;
+    int own_j0 = 0, own_j1 = 0;  // owned rows (moses_set_owned_rows; all rows by default)
     std::string err;
 };
 
@@ -79,6 +83,9 @@ inline int fail(moses_sim *s, int code, const std::string &msg)
     } while (0)
 
 
+// the simulation is one strip of a decomposed domain (moses_set_owned_rows)
+inline bool is_strip(const moses_sim *s) { return s->own_j0 != 0 || s->own_j1 != s->ny; }
+
 inline int grid_for(long long n, int block = 256)
 {
     long long b = (n + block - 1) / block;
@@ -109,6 +116,8 @@ inline StageArgs<T> base_args(moses_sim *s)
     a.n_inflow = s->n_inflow;
     a.nx = s->nx;
     a.ny = s->ny;
+    a.own_j0 = s->own_j0;
+    a.own_j1 = s->own_j1;
     a.pitch = s->pitch;
     a.plane = s->plane;
     a.ph = s->ph;

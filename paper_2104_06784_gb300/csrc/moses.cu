@@ -176,14 +176,13 @@ __global__ void fill_ghosts_kernel(const StageArgs<T> a, T *U, double tg)
 }
 
 template <typename T>
-__global__ void max_speed_kernel(const T *U, const T *geo, int nx, int ny, int pitch, long long plane, Phys ph,
+__global__ void max_speed_kernel(const T *U, const T *geo, int nx, int j0, int j1, int pitch, long long plane,
                                  unsigned long long *out)
 {
-    (void)ph;
-    const long long n = (long long)nx * ny;
+    const long long n = (long long)nx * (j1 - j0);  // the rows [j0, j1)
     double m = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const int j = j0 + (int)(e / nx), i = (int)(e - (long long)(j - j0) * nx);
         const long long g = cell_index(i, j, pitch);
         T u[6];
 #pragma unroll
@@ -232,6 +231,80 @@ __global__ void pack_kernel(const T *U, const T *R, double *dst, int nx, int ny,
         if (R && (c == 0 || c == 3)) v += (double)R[(c / 3) * plane + g];
         dst[e] = v;
     }
+}
+
+// rows [j0, j0 + nrows) of the state (and, FP32, of the two mass remainder
+// planes) <-> a dense buffer [plane][row][i] of doubles (exact both ways for
+// values of the simulation's own type)
+template <typename T>
+__global__ void rows_pack_kernel(const T *U, const T *R, double *dst, int nx, int j0, int nrows, int pitch,
+                                 long long plane)
+{
+    const int np = R ? 8 : 6;
+    const long long n = (long long)nx * nrows;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < np * n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const long long r = e - c * n;
+        const int j = j0 + (int)(r / nx), i = (int)(r - (long long)(j - j0) * nx);
+        const long long g = cell_index(i, j, pitch);
+        dst[e] = c < 6 ? (double)U[c * plane + g] : (double)R[(c - 6) * plane + g];
+    }
+}
+
+template <typename T>
+__global__ void rows_unpack_kernel(const double *src, T *U, T *R, int nx, int j0, int nrows, int pitch, long long plane)
+{
+    const int np = R ? 8 : 6;
+    const long long n = (long long)nx * nrows;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < np * n; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const long long r = e - c * n;
+        const int j = j0 + (int)(r / nx), i = (int)(r - (long long)(j - j0) * nx);
+        const long long g = cell_index(i, j, pitch);
+        if (c < 6) U[c * plane + g] = (T)src[e];
+        else R[(c - 6) * plane + g] = (T)src[e];
+    }
+}
+
+// the ghost cells that the cells of rows [j0, j1) own (write_ghosts), at
+// the control block's time: after rows were replaced from outside
+template <typename T>
+__global__ void fill_ghosts_rows_kernel(const StageArgs<T> a, T *U, int j0, int j1)
+{
+    const int nx = a.nx, ny = a.ny;
+    const long long n = (long long)nx * (j1 - j0);
+    const double tg = a.ctl->t;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int j = j0 + (int)(e / nx), i = (int)(e - (long long)(j - j0) * nx);
+        if (!(i < 2 || i >= nx - 2 || j < 2 || j >= ny - 2)) continue;
+        const long long g = cell_index(i, j, a.pitch);
+        T v[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) v[c] = U[c * a.plane + g];
+        write_ghosts(U, a.geo, a, i, j, v, tg);
+    }
+}
+
+// mass bits (MB_*) of U for the 32 x TY tiles of tile rows [ty0, ty0 +
+// gridDim.y): a CTA per tile, a warp per row
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY) mass_bits_kernel(const T *U, const T *R, int nx, int ny, int pitch,
+                                                            long long plane, int ty0, unsigned short *mb)
+{
+    __shared__ unsigned int rows[TY];
+    const int lane = threadIdx.x & 31, r = threadIdx.x >> 5;
+    const int bx = blockIdx.x, ty = ty0 + blockIdx.y;
+    const int i = bx * 32 + lane, j = ty * TY + r;
+    bool m = false;
+    if (i < nx && j < ny) {
+        const long long g = cell_index(i, j, pitch);
+        m = nonzero(U[g]) | nonzero(U[3 * plane + g]);
+        if (R) m |= nonzero(R[g]) | nonzero(R[plane + g]);
+    }
+    const unsigned int b = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) rows[r] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) mb[ty * gridDim.x + bx] = mass_bits<TY>(rows);
 }
 
 // release (h, phi_s, velocities) -> conserved U = J h (phi, phi v)
@@ -292,12 +365,12 @@ __global__ void prims_kernel(const T *U, const T *R, const T *geo, int nx, int n
 }
 
 template <typename T>
-__global__ void budget_kernel(const T *U, const T *R, int nx, int ny, int pitch, long long plane, double *out)
+__global__ void budget_kernel(const T *U, const T *R, int nx, int j0, int j1, int pitch, long long plane, double *out)
 {
-    const long long n = (long long)nx * ny;
+    const long long n = (long long)nx * (j1 - j0);  // the rows [j0, j1)
     double s[6] = {0, 0, 0, 0, 0, 0};
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / nx), i = (int)(e - (long long)j * nx);
+        const int j = j0 + (int)(e / nx), i = (int)(e - (long long)(j - j0) * nx);
         const long long g = cell_index(i, j, pitch);
 #pragma unroll
         for (int c = 0; c < 6; c++) s[c] += (double)U[c * plane + g];
@@ -360,8 +433,8 @@ static int refresh_t(moses_sim *s)
     CK(cudaMemsetAsync(&s->ctl->amax, 0, sizeof(unsigned long long), s->stream));
     // a new state clears a non-finite status left by an earlier step
     CK(cudaMemsetAsync(&s->ctl->status, 0, sizeof(s->ctl->status), s->stream));
-    max_speed_kernel<T><<<grid_for(n), 256, 0, s->stream>>>((const T *)s->U, (const T *)s->geo, s->nx, s->ny,
-                                                             s->pitch, s->plane, s->ph, &s->ctl->amax);
+    max_speed_kernel<T><<<grid_for(n), 256, 0, s->stream>>>((const T *)s->U, (const T *)s->geo, s->nx, s->own_j0,
+                                                             s->own_j1, s->pitch, s->plane, &s->ctl->amax);
     CK(cudaGetLastError());
     return MOSES_OK;
 }
@@ -461,6 +534,7 @@ static void free_sim(moses_sim *s)
     cudaFree(s->tw[0]);
     cudaFree(s->tw[1]);
     cudaFree(s->zk);
+    cudaFree(s->mb);
     cudaFree(s->geo);
     cudaFree(s->ctl);
     cudaFree(s->inflow_d);
@@ -632,6 +706,8 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
     if (!s) return fail(nullptr, MOSES_ENOMEM, "host allocation failed");
     s->nx = nx;
     s->ny = ny;
+    s->own_j0 = 0;
+    s->own_j1 = ny;
     s->dx = dx;
     s->dy = dy;
     s->p = *p;
@@ -656,6 +732,8 @@ int moses_create(const double *dem, int nx, int ny, double dx, double dy, const 
         (e = cudaMalloc(&s->tw[0], (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
         (e = cudaMalloc(&s->tw[1], (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
         (e = cudaMalloc(&s->zk, 3 * (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) != cudaSuccess ||
+        (e = cudaMalloc(&s->mb, 3 * sizeof(unsigned short) * (size_t)((nx + 31) / 32) * ((ny + 3) / 4))) !=
+            cudaSuccess ||
         (e = cudaMalloc(&s->ctl, sizeof(Ctl))) != cudaSuccess ||
         (e = cudaMalloc(&s->inflow_d, sizeof(InflowSeg) * MAX_INFLOW)) != cudaSuccess ||
         (e = cudaMalloc(&s->red, 8 * sizeof(double))) != cudaSuccess) {
@@ -822,7 +900,11 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
     const size_t nt = (size_t)((s->nx + 31) / 32) * ((s->ny + 3) / 4);
     const bool zk_on = !(s->ph.nu_f > 0.0) && s->ph.scheme != 1 && s->ph.recon != 1;
     if (zk_on && !s->zk_valid) CK(cudaMemsetAsync(s->zk, 0, 3 * nt, s->stream));
+    // U's mass bits describe U where the flags do (the last stepping launches
+    // wrote both); the copy-wait test needs the data classification
+    const bool mb_first = s->zk_valid && zk_on && !s->dbg_stall;
     s->zk_valid = false;  // until the launches below are in
+    auto bufno = [&](const void *b) { return b == s->U ? 0 : b == s->Us ? 1 : 2; };
     for (int q = 0; q < ns; q++) {
         a[q].Uin = (const T *)in[q];
         a[q].Uout = (T *)out[q];
@@ -839,12 +921,21 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
         // the first stage classifies from the data, the later ones from the flags of the stage before
         a[q].tw_next = s->tw[q % 2];
         a[q].tw_prev = q > 0 ? s->tw[(q - 1) % 2] : nullptr;
-        if (zk_on) a[q].zk = s->zk + nt * (out[q] == s->U ? 0 : out[q] == s->Us ? 1 : 2);
+        if (zk_on) {
+            a[q].zk = s->zk + nt * bufno(out[q]);
+            a[q].mb_in = s->mb + nt * bufno(in[q]);
+            a[q].mb_out = s->mb + nt * bufno(out[q]);
+            if (q > 0) a[q].mb_n = s->mb;
+            a[q].mb_ok = q > 0 || mb_first;
+        }
         if (rk3) {
             a[q].rk3 = q + 1;
             a[q].rk3_bw = q == 2 ? 2.0 / 3.0 : 1.0 / 6.0;
         }
     }
+    // the later steps of this call: the first stage from the bits the step before wrote
+    StageArgs<T> a0_next = a[0];
+    if (zk_on && !s->dbg_stall) a0_next.mb_ok = 1;
     if (stage_ms) {
         // events around every launch; the first stage in stage_ms[0], the others in stage_ms[1]
         cudaEvent_t ev[4];
@@ -854,7 +945,7 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
         for (int k = 0; k < nsteps && rc == 0; k++) {
             CK(cudaEventRecord(ev[0], s->stream));
             for (int q = 0; q < ns && rc == 0; q++) {
-                rc = launch_stage<T>(a[q], s->tile, s->stream);
+                rc = launch_stage<T>(q == 0 && k > 0 ? a0_next : a[q], s->tile, s->stream);
                 CK(cudaEventRecord(ev[q + 1], s->stream));
             }
             CK(cudaEventSynchronize(ev[ns]));
@@ -873,7 +964,7 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
     }
     for (int k = 0; k < nsteps; k++) {
         int rc = 0;
-        for (int q = 0; q < ns && rc == 0; q++) rc = launch_stage<T>(a[q], s->tile, s->stream);
+        for (int q = 0; q < ns && rc == 0; q++) rc = launch_stage<T>(q == 0 && k > 0 ? a0_next : a[q], s->tile, s->stream);
         if (rc) return fail(s, MOSES_ECUDA, std::string("stage launch: ") + cudaGetErrorString(cudaGetLastError()));
     }
     s->zk_valid = zk_on;
@@ -1124,6 +1215,106 @@ int moses_set_conserved(moses_sim *s, const double *U)
     return MOSES_OK;
 }
 
+// ---------------------------------------------------------------------------
+// One strip of a row-decomposed domain: owned rows, row exchange, the CFL
+// maximum over all strips.
+
+int moses_set_owned_rows(moses_sim *s, int j0, int j1)
+{
+    if (!s) return MOSES_EINVAL;
+    if (j0 < 0 || j1 > s->ny || j1 <= j0) return fail(s, MOSES_EINVAL, "owned rows must satisfy 0 <= j0 < j1 <= ny");
+    s->own_j0 = j0;
+    s->own_j1 = j1;
+    // the CFL maximum of the current state over the own rows (the rows near
+    // a window's inner edges see an extrapolated bed)
+    if (!s->have_state) return MOSES_OK;
+    CK(cudaMemsetAsync(&s->ctl->amax, 0, sizeof(unsigned long long), s->stream));
+    const long long n = (long long)s->nx * (j1 - j0);
+    if (s->prec == MOSES_FP64)
+        max_speed_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, (const double *)s->geo,
+                                                                     s->nx, j0, j1, s->pitch, s->plane, &s->ctl->amax);
+    else
+        max_speed_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, (const float *)s->geo, s->nx,
+                                                                    j0, j1, s->pitch, s->plane, &s->ctl->amax);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
+int moses_row_planes(const moses_sim *s) { return s ? (s->prec == MOSES_FP32 ? 8 : 6) : 0; }
+
+int moses_get_rows_device(moses_sim *s, int j0, int nrows, double *rows_device)
+{
+    if (!s || !rows_device) return MOSES_EINVAL;
+    if (j0 < 0 || nrows < 1 || j0 + nrows > s->ny) return fail(s, MOSES_EINVAL, "rows outside the grid");
+    const long long n = (long long)moses_row_planes(s) * s->nx * nrows;
+    if (s->prec == MOSES_FP64)
+        rows_pack_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, nullptr, rows_device, s->nx,
+                                                                     j0, nrows, s->pitch, s->plane);
+    else
+        rows_pack_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, rem<float>(s, s->U),
+                                                                    rows_device, s->nx, j0, nrows, s->pitch, s->plane);
+    CK(cudaGetLastError());
+    return MOSES_OK;
+}
+
+namespace {
+template <typename T, int TY>
+int rows_mass_bits(moses_sim *s, int ty0, int ty1)
+{
+    const dim3 grid((s->nx + 31) / 32, ty1 - ty0);
+    mass_bits_kernel<T, TY><<<grid, 32 * TY, 0, s->stream>>>((const T *)s->U, rem<T>(s, s->U), s->nx, s->ny, s->pitch,
+                                                             s->plane, ty0, s->mb);
+    CK(cudaGetLastError());
+    return MOSES_OK;
+}
+
+// after rows [j0, j1) of U were replaced: their ghosts; the known-zero flags
+// and mass bits of the tiles they touch (the stepping launches' own records
+// of U stay valid for every other tile)
+template <typename T>
+int rows_replaced(moses_sim *s, int j0, int j1)
+{
+    StageArgs<T> a = base_args<T>(s);
+    fill_ghosts_rows_kernel<T><<<grid_for((long long)s->nx * (j1 - j0)), 256, 0, s->stream>>>(a, (T *)s->U, j0, j1);
+    CK(cudaGetLastError());
+    const int TY = s->tile == 1 ? 4 : s->tile == 2 ? 16 : 8;
+    const int gx = (s->nx + 31) / 32, ty0 = j0 / TY, ty1 = (j1 - 1) / TY + 1;
+    CK(cudaMemsetAsync(s->zk + (size_t)ty0 * gx, 0, (size_t)(ty1 - ty0) * gx, s->stream));  // U's flags
+    switch (TY) {
+    case 4: return rows_mass_bits<T, 4>(s, ty0, ty1);
+    case 16: return rows_mass_bits<T, 16>(s, ty0, ty1);
+    default: return rows_mass_bits<T, 8>(s, ty0, ty1);
+    }
+}
+}  // namespace
+
+int moses_set_rows_device(moses_sim *s, int j0, int nrows, const double *rows_device)
+{
+    if (!s || !rows_device) return MOSES_EINVAL;
+    if (!s->have_state) return fail(s, MOSES_ESTATE, "no state");
+    if (j0 < 0 || nrows < 1 || j0 + nrows > s->ny) return fail(s, MOSES_EINVAL, "rows outside the grid");
+    const long long n = (long long)moses_row_planes(s) * s->nx * nrows;
+    if (s->prec == MOSES_FP64)
+        rows_unpack_kernel<double><<<grid_for(n), 256, 0, s->stream>>>(rows_device, (double *)s->U, nullptr, s->nx, j0,
+                                                                       nrows, s->pitch, s->plane);
+    else
+        rows_unpack_kernel<float><<<grid_for(n), 256, 0, s->stream>>>(rows_device, (float *)s->U, rem<float>(s, s->U),
+                                                                      s->nx, j0, nrows, s->pitch, s->plane);
+    CK(cudaGetLastError());
+    return s->prec == MOSES_FP64 ? rows_replaced<double>(s, j0, j0 + nrows) : rows_replaced<float>(s, j0, j0 + nrows);
+}
+
+int moses_set_max_speed(moses_sim *s, double amax)
+{
+    if (!s) return MOSES_EINVAL;
+    if (!(std::isfinite(amax) && amax >= 0.0)) return fail(s, MOSES_EINVAL, "amax must be finite and >= 0");
+    const double v = amax + 0.0;  // -0 -> +0: the step reads the IEEE bits as a non-negative double
+    CK(cudaMemcpyAsync(&s->ctl->amax, &v, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return MOSES_OK;
+}
+
 int moses_get_state(moses_sim *s, double *h, double *phi_s, double *vx_s, double *vy_s, double *vx_f, double *vy_f)
 {
     if (!s) return MOSES_EINVAL;
@@ -1200,14 +1391,14 @@ int moses_stage(moses_sim *s, double t, double dt, double *U_out)
 int moses_get_budget(moses_sim *s, double out[MOSES_BUDGET_LEN])
 {
     if (!s || !out) return MOSES_EINVAL;
-    const long long n = (long long)s->nx * s->ny;
+    const long long n = (long long)s->nx * (s->own_j1 - s->own_j0);  // the owned rows
     CK(cudaMemsetAsync(s->red, 0, 6 * sizeof(double), s->stream));
     if (s->prec == MOSES_FP64)
-        budget_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, nullptr, s->nx, s->ny, s->pitch,
-                                                                  s->plane, s->red);
+        budget_kernel<double><<<grid_for(n), 256, 0, s->stream>>>((const double *)s->U, nullptr, s->nx, s->own_j0,
+                                                                  s->own_j1, s->pitch, s->plane, s->red);
     else
-        budget_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, rem<float>(s, s->U), s->nx, s->ny, s->pitch,
-                                                                 s->plane, s->red);
+        budget_kernel<float><<<grid_for(n), 256, 0, s->stream>>>((const float *)s->U, rem<float>(s, s->U), s->nx,
+                                                                 s->own_j0, s->own_j1, s->pitch, s->plane, s->red);
     CK(cudaGetLastError());
     double sums[6];
     CK(cudaMemcpyAsync(sums, s->red, sizeof(sums), cudaMemcpyDeviceToHost, s->stream));
@@ -1320,12 +1511,14 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
     a.n_inflow = 0;
     a.nx = nx;
     a.ny = ny;
+    a.own_j0 = 0;
+    a.own_j1 = ny;
     a.pitch = pitch;
     a.plane = plane;
     a.ph = phs;
     a.k = make_kt<double>(phs);
     fill_ghosts_kernel<double><<<grid_for(n), 256, 0, st>>>(a, U, t);
-    max_speed_kernel<double><<<grid_for(n), 256, 0, st>>>(U, geo, nx, ny, pitch, plane, a.ph, &ctl->amax);
+    max_speed_kernel<double><<<grid_for(n), 256, 0, st>>>(U, geo, nx, 0, ny, pitch, plane, &ctl->amax);
     CK(cudaGetLastError());
     StageArgs<double> a1 = a, a2 = a;
     a1.Uin = U;
@@ -1515,6 +1708,7 @@ int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out)
             sims[k]->ph.k_mode != 0)
             return batch_fail(nullptr, MOSES_EINVAL,
                               "members must use the paper's scheme (central, minmod, two-step, k_mode 0)");
+        if (is_strip(sims[k])) return batch_fail(nullptr, MOSES_EINVAL, "a strip of a decomposed domain (owned rows set)");
         for (int q = 0; q < k; q++)
             if (sims[q] == sims[k]) return batch_fail(nullptr, MOSES_EINVAL, "a simulation appears twice");
     }

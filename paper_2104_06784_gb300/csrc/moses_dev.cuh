@@ -178,6 +178,11 @@ struct alignas(8) StageArgs {
     const InflowSeg *inflow;
     int n_inflow;
     int nx, ny, pitch;
+    // rows [own_j0, own_j1) are this simulation's own (all rows, unless it is
+    // one strip of a decomposed domain): only their cells enter the CFL
+    // maximum and the clamp counts, only their boundary faces the boundary
+    // budget
+    int own_j0, own_j1;
     long long plane;   // elements per plane
     Phys ph;
     KT<T> k;
@@ -216,6 +221,16 @@ struct alignas(8) StageArgs {
     // 1 for a dry tile, 0 for a tile with work and for a tile on a side with
     // an inflow segment (its ghost state follows the hydrograph).
     unsigned char *zk;
+    // per-tile mass bits (MB_* below), so that a stage can be classified
+    // without reading the state.  mb_out: the bits of Uout, written for every
+    // tile (the classification zeroes a dry tile's, the stage kernel sets a
+    // wet tile's from the values it stores).  mb_in: the bits of Uin; with
+    // mb_ok the classification takes the wet tiles from them, otherwise the
+    // data classification of a first stage writes them.  mb_n: the bits of
+    // U^n in a combining stage.  All null outside the stepping launches.
+    unsigned short *mb_in, *mb_out;
+    const unsigned short *mb_n;
+    int mb_ok;
     // testing only: extra bytes the classification's copy barrier expects and
     // no copy delivers, so that its bounded wait runs out (0 normally)
     unsigned int dbg_stall_tx;
@@ -228,6 +243,17 @@ struct alignas(8) StageArgs {
     double fix_t, fix_dt;
     double *t_log, *dt_log;
     int log_idx;
+};
+
+// Mass bits of a 32 x TY tile: where its cells hold mass (U1 or U4 non-zero,
+// NaN included, or a non-zero FP32 mass remainder).  MB_ANY: some cell; the
+// others: a cell within two cells of a side (W: columns 0-1, E: columns
+// 30-31, S: rows 0-1, N: the last two rows) or of a corner (both).  A tile
+// needs its stage where its own bits have MB_ANY or a neighbour's bits have
+// the side or corner that faces it (the stencil's 2-cell reach).
+enum : unsigned short {
+    MB_ANY = 1u, MB_W = 2u, MB_E = 4u, MB_S = 8u, MB_N = 16u,
+    MB_SW = 32u, MB_SE = 64u, MB_NW = 128u, MB_NE = 256u
 };
 
 __host__ __device__ inline long long cell_index(int i, int j, int pitch)

@@ -663,6 +663,54 @@ constexpr size_t stage_smem_bytes()
                         (VIS ? 2 * (TX + 2) * (TY + 2) : 0) + (KM ? 2 * (TX + 4) * (TY + 4) : 0));
 }
 
+// Mass bits (MB_*) of a tile of TY rows from the ballots of its rows (bit l
+// of rows[r]: column l of row r holds mass; columns and rows outside the
+// grid hold none).
+template <int TY>
+__device__ __forceinline__ unsigned short mass_bits(const unsigned int *rows)
+{
+    static_assert(TY >= 2, "the side bits take two rows");
+    unsigned int all = 0u;
+    for (int r = 0; r < TY; r++) all |= rows[r];
+    const unsigned int s = rows[0] | rows[1], n = rows[TY - 2] | rows[TY - 1];
+    constexpr unsigned int W = 0x3u, E = 0xC0000000u;
+    unsigned int b = 0u;
+    if (all) b |= MB_ANY;
+    if (all & W) b |= MB_W;
+    if (all & E) b |= MB_E;
+    if (s) b |= MB_S;
+    if (n) b |= MB_N;
+    if (s & W) b |= MB_SW;
+    if (s & E) b |= MB_SE;
+    if (n & W) b |= MB_NW;
+    if (n & E) b |= MB_NE;
+    return (unsigned short)b;
+}
+
+// Tile (bx, ty) of a gx x gy grid has mass within two cells of it, from the
+// mass bits of its own and its eight neighbours' cells.  The 2-cell halo of a
+// tile also takes ghost cells; a closed or transmissive ghost repeats a cell
+// of the same row (column) within two cells of the side, so its mass shows
+// in those bits too; inflow ghosts are the caller's (on_inflow_side).
+__device__ __forceinline__ bool wet_from_bits(const unsigned short *mb, int bx, int ty, int gx, int gy)
+{
+    unsigned int w = mb[ty * gx + bx] & MB_ANY;
+    const bool wx = bx > 0, ex = bx + 1 < gx, sy = ty > 0, ny_ = ty + 1 < gy;
+    if (wx) w |= mb[ty * gx + bx - 1] & MB_E;
+    if (ex) w |= mb[ty * gx + bx + 1] & MB_W;
+    if (sy) {
+        w |= mb[(ty - 1) * gx + bx] & MB_N;
+        if (wx) w |= mb[(ty - 1) * gx + bx - 1] & MB_NE;
+        if (ex) w |= mb[(ty - 1) * gx + bx + 1] & MB_NW;
+    }
+    if (ny_) {
+        w |= mb[(ty + 1) * gx + bx] & MB_S;
+        if (wx) w |= mb[(ty + 1) * gx + bx - 1] & MB_SE;
+        if (ex) w |= mb[(ty + 1) * gx + bx + 1] & MB_SW;
+    }
+    return w != 0u;
+}
+
 // ---- the stage kernel -------------------------------------------------------------
 // One stage on the tile (bx, by) of the simulation described by `a`; nb is the
 // number of CTAs working on that simulation in this launch (for the ticket;
@@ -990,7 +1038,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             }
     #pragma unroll
             for (int c = 0; c < 7; c++) sHx[c * NXF + f] = H[c];
-            if (!a.debug_stage && (i == -1 || i == nx - 1)) {
+            if (!a.debug_stage && (i == -1 || i == nx - 1) && j >= a.own_j0 && j < a.own_j1) {
                 // the stage's budget weight (Heun 1/2; RK3 1/6, 1/6, 2/3) x boundary volume flux
                 const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dy) * (i == -1 ? 1.0 : -1.0) * bwf;
                 atomicAdd(&acc[0], w * (double)H[0]);
@@ -1045,7 +1093,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             }
     #pragma unroll
             for (int c = 0; c < 7; c++) sHy[c * NYF + f] = H[c];
-            if (!a.debug_stage && (j == -1 || j == ny - 1)) {
+            if (!a.debug_stage && ((j == -1 && a.own_j0 == 0) || (j == ny - 1 && a.own_j1 == ny))) {
                 const double w = (sizeof(T) == 4 ? 0.5 * a.ph.cell_area : 0.25 * dt * a.ph.dx) * (j == -1 ? 1.0 : -1.0) * bwf;
                 atomicAdd(&acc[0], w * (double)H[0]);
                 atomicAdd(&acc[1], w * (double)H[3]);
@@ -1064,6 +1112,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     const int i = x0 + lx, j = y0 + ly;
     T speed = T(0);
     bool bad = false;
+    bool mass = false;  // the cell's output holds mass (mass bits)
     if (!wet && i < nx && j < ny) {
         const long long g = cell_index(i, j, pitch);
         const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -1245,7 +1294,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         for (int ph = 0; ph < 2; ph++) {
             const int c = 3 * ph;
             if (negative(out[c])) {
-                if (!a.debug_stage) {
+                if (!a.debug_stage && j >= a.own_j0 && j < a.own_j1) {
                     atomicAdd(&acc[2 + ph], -0.5 * ((double)out[c] + (double)lo[ph]) * a.ph.cell_area * bwf);
                     atomicAdd(&acc_n, 1u);
                 }
@@ -1318,19 +1367,27 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
 #pragma unroll
         for (int c = 0; c < 6; c++) bad |= nonfinite(out[c]);
         store6(a.Uout, plane, g, out);
+        mass = nonzero(out[0]) | nonzero(out[3]);
         if constexpr (sizeof(T) == 4) {
             a.Rout[g] = lo[0];
             a.Rout[plane + g] = lo[1];
+            mass |= nonzero(lo[0]) | nonzero(lo[1]);
         }
         if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, out, s_tg);
     }
 
     if (a.debug_stage) return;
+    __shared__ unsigned int s_mrow[TY];  // ballots of the output's mass by row (TX == 32: a warp per row)
+    if (TX == 32 && a.mb_out) {
+        const unsigned int row = __ballot_sync(0xffffffffu, mass);
+        if ((tid & 31) == 0) s_mrow[tid >> 5] = row;
+    }
 
     // ---- CTA reductions ---------------------------------------------------
     if (bad) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
     const bool finalize = a.stage == 2 && a.rk3 != 2;  // the step's last stage
     if (finalize && a.want_amax) {
+        if (j < a.own_j0 || j >= a.own_j1) speed = T(0);  // a row another strip owns
         if (nonfinite(speed)) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) speed = maxnn(speed, __shfl_xor_sync(0xffffffffu, speed, o));
@@ -1346,6 +1403,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             atomicAdd(&ctl->clamp_cells, (unsigned long long)acc_n);
         }
         if (a.stage == 1 && bx == 0 && by == 0) first_stage_clock(a, a.fix ? a.fix_t : ctl->t, dt);
+        if (TX == 32 && a.mb_out) a.mb_out[by * ((nx + 31) / 32) + bx] = mass_bits<TY>(s_mrow);
         if (finalize) {
             if (a.want_amax) {
                 T m = T(0);
@@ -1472,6 +1530,7 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
     __shared__ unsigned long long s_bar;
     __shared__ double s_tg;
     __shared__ unsigned int s_row[H];  // row y0 - 2 + r of the strip and halo has work
+    __shared__ unsigned int s_own[S];  // the strip's own cells with mass in Uin, by row (ballots)
     __shared__ bool s_keep[NTL];  // the tile is not zero-written here (keep_tile)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = bx * 32, y0 = sy * S;
@@ -1578,6 +1637,15 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
             }
             const unsigned int any = __any_sync(0xffffffffu, m);
             if (lane == 0) s_row[r] = any;
+            if (r >= 2 && r < S + 2) {  // the input's own mass, for its mass bits
+                bool mo = false;
+                if (gj < ny && x0 + lane < nx) {
+                    mo = nonzero(s_m[0][r][lane + 2]) | nonzero(s_m[1][r][lane + 2]);
+                    if constexpr (F32) mo |= nonzero(s_x[0][r - 2][lane + 2]) | nonzero(s_x[1][r - 2][lane + 2]);
+                }
+                const unsigned int own = __ballot_sync(0xffffffffu, mo);
+                if (lane == 0) s_own[r - 2] = own;
+            }
         }
         __syncthreads();
         if (threadIdx.x < NTL) {
@@ -1588,6 +1656,8 @@ __device__ __forceinline__ void classify_strip(const StageArgs<T> &a, const int 
                 for (int r = t * TY; r < t * TY + TY + 4; r++) w |= s_row[r] != 0u;
                 if (w) append(bx, ty);
                 if (a.tw_next) a.tw_next[ty * gx + bx] = w;
+                if (a.mb_in && a.stage == 1) a.mb_in[ty * gx + bx] = mass_bits<TY>(&s_own[t * TY]);
+                if (a.mb_out && !w) a.mb_out[ty * gx + bx] = 0;
                 const bool inf = a.zk != nullptr && on_inflow_side(a, bx, ty, gx, (ny + TY - 1) / TY);
                 keep = keep_tile(a, w, inf, ty * gx + bx, known);
             }
@@ -1617,13 +1687,18 @@ __global__ void __launch_bounds__(32 * kStripWarps, 10) classify_kernel(const St
                           [&](int tx, int ty) { a.wl[atomicAdd(&a.wl_n[0], 1u)] = ty * gridDim.x + tx; });
 }
 
-// The classification of a combining stage (a.tw_prev set, a.stage 2), which
-// reads no state: one thread per tile of the gx x gy tiles takes the tile as
-// wet where it or a neighbouring tile was wet in the stage before, or where it
-// lies on a side with an inflow segment (as classify_strip does), lists it,
-// and keeps its flags; the CTA's warps then write the zero state of its dry
-// tiles that do not hold it yet, one row of 32 cells at a time.  Few CTAs
-// with short lives: a CTA per strip made this launch latency-bound.
+// The classification that reads no state: one thread per tile of the gx x gy
+// tiles takes the tile as wet
+// - from the mass bits of the input (a.mb_ok): where it has mass within two
+//   cells (wet_from_bits) or, in a combining stage, U^n has mass in it;
+// - else, in a combining stage (a.tw_prev): where it or a neighbouring tile
+//   was wet in the stage before (its input has mass only there);
+// and where it lies on a side with an inflow segment (as classify_strip
+// does), lists it, and keeps its flags; the CTA's warps then write the zero
+// state of its dry tiles that do not hold it yet, one row of 32 cells at a
+// time.  Few CTAs with short lives: a CTA per strip made this launch
+// latency-bound.  A first stage also takes the step's time step here, as
+// the data classification does.
 constexpr int kFlagThreads = 256;
 template <typename T, int TY>
 __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const StageArgs<T> a, const int gx, const int gy)
@@ -1637,21 +1712,36 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
     const unsigned char known = (a.zk && mine) ? a.zk[idx] : 0;
     if (tid == 0) {
         s_n = 0u;
-        s_tg = a.ctl->t + (a.rk3 == 2 ? 0.5 * a.ctl->dt : a.ctl->dt);
+        const Ctl *ctl = a.ctl;
+        if (a.stage == 1) {
+            const bool fixed = a.fix != 0;
+            const double t_now = fixed ? a.fix_t : ctl->t;
+            const double dt = fixed ? a.fix_dt : dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
+            s_tg = t_now + dt;
+            if (blockIdx.x == 0) first_stage_clock(a, t_now, dt);
+        } else {
+            s_tg = ctl->t + (a.rk3 == 2 ? 0.5 * ctl->dt : ctl->dt);
+        }
     }
     __syncthreads();
     if (mine) {
         const int bx = idx % gx, ty = idx / gx;
         bool w = false;
-        for (int dy = -1; dy <= 1; dy++)
-            for (int dx = -1; dx <= 1; dx++) {
-                const int xx = bx + dx, yy = ty + dy;
-                if (xx >= 0 && xx < gx && yy >= 0 && yy < gy) w |= a.tw_prev[yy * gx + xx] != 0;
-            }
+        if (a.mb_ok) {
+            w = wet_from_bits(a.mb_in, bx, ty, gx, gy);
+            if (a.mb_n) w |= (a.mb_n[idx] & MB_ANY) != 0;
+        } else {
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int xx = bx + dx, yy = ty + dy;
+                    if (xx >= 0 && xx < gx && yy >= 0 && yy < gy) w |= a.tw_prev[yy * gx + xx] != 0;
+                }
+        }
         const bool inf = on_inflow_side(a, bx, ty, gx, gy);
         w |= inf;
         if (w) a.wl[atomicAdd(&a.wl_n[0], 1u)] = idx;
-        a.tw_next[idx] = w;
+        if (a.tw_next) a.tw_next[idx] = w;
+        if (a.mb_out && !w) a.mb_out[idx] = 0;
         if (!keep_tile(a, w, inf, idx, known)) s_list[atomicAdd(&s_n, 1u)] = idx;
     }
     __syncthreads();

@@ -30,8 +30,9 @@ int launch_tile(const StageArgs<T> &a, cudaStream_t st)
 }
 
 // The stepping launches of the plain form: classify_kernel over every tile
-// (classify_flags_kernel in a combining stage), then stage_kernel_list on a
-// grid of resident CTAs over the listed tiles.
+// (classify_flags_kernel where the input's mass bits are known, and in a
+// combining stage), then stage_kernel_list on a grid of resident CTAs over
+// the listed tiles.
 template <typename T, int TX, int TY, bool REC = false, bool KM = false>
 int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
 {
@@ -52,7 +53,7 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     }
     static_assert(TX == 32, "classify_kernel works on 32-wide strips");
     const int gx = (a.nx + TX - 1) / TX;
-    if (a.tw_prev && a.stage == 2) {  // a combining stage: from the flags of the stage before
+    if (a.mb_ok || (a.tw_prev && a.stage == 2)) {  // from the input's mass bits, or the flags of the stage before
         const int gy = (a.ny + TY - 1) / TY;
         classify_flags_kernel<T, TY><<<(gx * gy + kFlagThreads - 1) / kFlagThreads, kFlagThreads, 0, st>>>(a, gx, gy);
     } else {
@@ -60,6 +61,16 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     }
     stage_kernel_list<T, TX, TY, REC, KM><<<resident[dev], TX * TY, smem, st>>>(a, gx);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+// the launches that test each tile inside the stage kernel keep no mass bits
+template <typename T>
+void no_mass_bits(StageArgs<T> &a)
+{
+    a.mb_in = nullptr;
+    a.mb_out = nullptr;
+    a.mb_n = nullptr;
+    a.mb_ok = 0;
 }
 
 // tile 0: 32 x 8 cells (256 threads); tile 1: 32 x 4; tile 2: 32 x 16
@@ -78,6 +89,7 @@ int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
         StageArgs<T> a = a_in;
         a.wl = nullptr;
         a.wl_n = nullptr;
+        no_mass_bits(a);
         switch (tile) {
         case 1: return launch_tile<T, 32, 4, false, false, false, false, true>(a, st);
         case 2: return launch_tile<T, 32, 16, false, false, false, false, true>(a, st);
@@ -96,6 +108,7 @@ int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
     StageArgs<T> a = a_in;  // every tile tests itself
     a.wl = nullptr;
     a.wl_n = nullptr;
+    no_mass_bits(a);
     if (weno) {
         if (cu)
             return vis ? launch_tile<T, 32, 8, false, true, true, true>(a, st)

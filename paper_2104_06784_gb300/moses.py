@@ -79,6 +79,11 @@ SIGNATURES = [
     ("moses_set_conserved_device", C.c_int, [_vp, _vp]),
     ("moses_stage", C.c_int, [_vp, C.c_double, C.c_double, _dp]),
     ("moses_max_speed", C.c_int, [_vp, _dp]),
+    ("moses_set_owned_rows", C.c_int, [_vp, C.c_int, C.c_int]),
+    ("moses_row_planes", C.c_int, [_vp]),
+    ("moses_get_rows_device", C.c_int, [_vp, C.c_int, C.c_int, _vp]),
+    ("moses_set_rows_device", C.c_int, [_vp, C.c_int, C.c_int, _vp]),
+    ("moses_set_max_speed", C.c_int, [_vp, C.c_double]),
     ("moses_get_budget", C.c_int, [_vp, _dp]),
     ("moses_step_static", C.c_int, [_vp, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(Params), _vp, _vp,
                                     C.c_double, _dp, _vp]),
@@ -265,6 +270,25 @@ class Sim:
 
     def get_conserved_device(self, ptr: int):
         self._ck(self._L.moses_get_conserved_device(self._h, C.c_void_p(ptr)))
+
+    # one strip of a row-decomposed domain (decomp.py) -------------------------
+    def set_owned_rows(self, j0: int, j1: int):
+        self._ck(self._L.moses_set_owned_rows(self._h, int(j0), int(j1)))
+
+    @property
+    def row_planes(self) -> int:
+        return int(self._L.moses_row_planes(self._h))
+
+    def get_rows_device(self, j0: int, nrows: int, ptr: int):
+        """Rows [j0, j0 + nrows) into the device buffer at ptr
+        (row_planes x nrows x nx doubles), asynchronous on the stream."""
+        self._ck(self._L.moses_get_rows_device(self._h, int(j0), int(nrows), C.c_void_p(ptr)))
+
+    def set_rows_device(self, j0: int, nrows: int, ptr: int):
+        self._ck(self._L.moses_set_rows_device(self._h, int(j0), int(nrows), C.c_void_p(ptr)))
+
+    def set_max_speed(self, amax: float):
+        self._ck(self._L.moses_set_max_speed(self._h, float(amax)))
 
     def get_state(self) -> dict:
         arrs = [np.empty((self.ny, self.nx)) for _ in range(6)]

@@ -8,6 +8,10 @@ C-ABI call that takes a simulation must do one of three things:
 - only read it;
 - clear the flags when it returns (a `ZkReset` declared first).
 
+Two more lists: calls that write only the control block (the owned rows and
+the CFL maximum of a strip), and the row exchange of a decomposed domain,
+which updates the flags (and the mass bits) of exactly the tiles it writes.
+
 This test holds every such call of the library's sources to one of those
 lists.  A new call must be placed in one before the suite passes again.
 Ensemble steps must clear the flags of every member.
@@ -19,7 +23,9 @@ SRC = pathlib.Path(__file__).resolve().parents[1] / "paper_2104_06784_gb300" / "
 
 STEPPING = {"moses_step", "moses_step_timed", "moses_step_dt", "moses_run_until"}
 READ_ONLY = {"moses_next_dt", "moses_max_speed", "moses_get_conserved_device", "moses_get_conserved",
-             "moses_get_state", "moses_get_budget", "moses_destroy"}
+             "moses_get_state", "moses_get_budget", "moses_destroy", "moses_get_rows_device"}
+CONTROL_ONLY = {"moses_set_owned_rows", "moses_set_max_speed"}
+KEEPS_FLAGS = {"moses_set_rows_device"}
 
 
 def _bodies():
@@ -45,6 +51,13 @@ def test_every_call_on_a_simulation_keeps_the_flags_valid():
             assert "ZkReset" not in body, name
         elif name in READ_ONLY:
             assert "ZkReset" not in body, name
+        elif name in CONTROL_ONLY:
+            assert "ZkReset" not in body, name
+            assert "unpack_kernel" not in body, name
+            assert all("cudaMemcpyAsync(&s->ctl->amax," in ln for ln in body.splitlines() if "Memcpy" in ln), name
+        elif name in KEEPS_FLAGS:
+            assert "ZkReset" not in body, name
+            assert "rows_replaced<" in body, name
         else:
             first = body.strip().splitlines()[0].strip()
             assert first == "const ZkReset zr{s};", f"{name}: declare `const ZkReset zr{{s}};` first, or list it"
@@ -67,3 +80,12 @@ def test_stepping_sets_the_flags_valid_only_after_its_launches():
     # every `zk_valid = zk_on` comes after the last stage launch of its branch
     for m in re.finditer(r"s->zk_valid = zk_on;", body):
         assert body.rfind("launch_stage<T>(", 0, m.start()) > first_false
+
+
+def test_row_exchange_updates_the_flags_of_the_tiles_it_writes():
+    text = (SRC / "moses.cu").read_text()
+    start = text.index("int rows_replaced(moses_sim *s, int j0, int j1)")
+    body = text[start:text.index("\n}\n", start)]
+    assert "fill_ghosts_rows_kernel" in body  # the ghosts those rows own
+    assert "cudaMemsetAsync(s->zk + (size_t)ty0 * gx, 0, (size_t)(ty1 - ty0) * gx" in body  # U's flags
+    assert "rows_mass_bits<T, 4>" in body and "rows_mass_bits<T, 8>" in body and "rows_mass_bits<T, 16>" in body
