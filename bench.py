@@ -463,11 +463,13 @@ def shard(items, rank, world):
 def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="cpu", steps=3000):
     """Batched ensemble, FP32: 256 members on square grids of lognormal side
     (64..1024 cells, 5 m), each its own spectral DEM, basal friction, drag and
-    release volume; per stage one batched classification launch and one
-    batched launch over the wet tiles of all members, replayed from a CUDA graph.
-    The members' 3000 steps are timed whole (after Wm warm-up steps), device
-    time from CUDA events on the batch's stream.  With several ranks the
-    members are sharded across them; the time is the max over ranks."""
+    release volume; all the steps of a call in one cooperative launch (per
+    stage the classification of every member's tiles and the stage on the wet
+    ones, the CTAs meeting on a bounded grid barrier in between), with the
+    tile shape the batch's tuner chose.  The members' 3000 steps are timed
+    whole (after Wm warm-up steps), device time from CUDA events on the
+    batch's stream.  With several ranks the members are sharded across them;
+    the time is the max over ranks."""
     from paper_2104_06784_gb300 import moses, workloads as W
     cfgs = shard(W.ensemble_config(n, seed=seed), rank, world)
     cells_rank = int(sum(c["dem"].size for c in cfgs))
@@ -478,6 +480,7 @@ def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="c
             dist.barrier()
         ms = b.step_timed(steps)
         tiles = b.tiles
+        rows, tune_ms = b.tile_rows()
     wet = float(np.mean([wet_tile_fraction(s_.get_conserved()) for s_ in sims]))
     for s_ in sims:
         s_.close()
@@ -485,8 +488,10 @@ def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="c
     cells = int(reduce_over_ranks(cells_rank, "sum", dist, device))
     return {"value": cells * steps / (ms / 1e3), "unit": "cell-steps/s", "members": n, "cells": cells,
             "members_per_rank": len(cfgs), "scaling": "strong" if world > 1 else None,
-            "ms_per_step": ms / steps, "steps": steps, "warmup": Wm, "dtype": "f32", "gpu_launches": 4 * steps,
-            "tiles_per_launch": tiles, "wet_tiles_end_mean": wet,
+            "ms_per_step": ms / steps, "steps": steps, "warmup": Wm, "dtype": "f32", "gpu_launches": 1,
+            "tiles": tiles, "tile": f"32x{rows}",
+            "tile_tuning_ms": {"32x4": tune_ms[0], "32x8": tune_ms[1], "32x16": tune_ms[2]},
+            "wet_tiles_end_mean": wet,
             "config": "256 scenarios, sides clip(round16(lognormal(ln 256, ln4/2)), 64, 1024), dx 5 m, "
                       "spectral DEMs, delta_b U(15,30) deg, c_D U(1e-4,1e-2) 1/s, release U(1e4,1e6) m^3, FP32, "
                       f"{steps} steps timed whole"}

@@ -288,24 +288,41 @@ void moses_destroy(moses_sim *s);
 /* ---- Ensembles --------------------------------------------------------------
  * Many independent simulations advanced together, for the "abundant plausible
  * scenarios" and parameter back-calculation use of Sect. 5: each member keeps
- * its own DEM, grid size, parameters, time and CFL time step.  Per Heun stage
- * one batched launch classifies the 32 x 8 tiles of every member (the dry
- * ones get their zero state) and one runs the stage on the wet ones; the time
- * loop is recorded once as a CUDA graph (16 steps) that moses_batch_step
- * replays.  Members are ordinary moses_sim objects created on the same stream
- * with the same precision form; their states and budgets are read with the
- * per-simulation calls.  The batch does not own them: destroy the batch before
- * its members.  Errors (moses_batch_last_error): EINVAL, ESTATE, ENONFINITE,
- * ECUDA. */
+ * its own DEM, grid size, parameters, time and CFL time step.  A call of
+ * moses_batch_step is one cooperative launch of every CTA that fits on the
+ * GPU at once, which runs all its steps for every member: per Heun stage the
+ * wet tiles of every member are classified (from the data on the call's first
+ * stage, then from the per-tile mass bits the stage keeps) and the stage runs
+ * on them, with the CTAs meeting on a grid barrier between the phases.  Every
+ * wait of that barrier is bounded (0.5 s): one that runs out ends the launch
+ * and the call returns MOSES_ETIMEOUT.  The tile shape (32 x 4, 32 x 8 or
+ * 32 x 16) is the fastest of one first stage per shape on the members' states,
+ * timed by moses_batch_create (the members' control blocks are restored; their
+ * U* scratch buffers are overwritten).  Members are ordinary moses_sim objects
+ * created on the same stream with the same precision form; their states and
+ * budgets are read with the per-simulation calls.  The batch does not own
+ * them: destroy the batch before its members.  Errors (moses_batch_last_error):
+ * EINVAL, ESTATE, ENONFINITE, ETIMEOUT, ECUDA. */
 typedef struct moses_batch moses_batch;
 int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out);
-/* every member advances nsteps CFL-limited steps; synchronises at the end */
+/* every member advances nsteps CFL-limited steps (one launch); synchronises at
+ * the end */
 int moses_batch_step(moses_batch *b, int nsteps);
-/* the same, with CUDA events on the batch's stream around the steps: *ms
- * receives their device time [ms] */
+/* the same, with CUDA events on the batch's stream around the launch: *ms
+ * receives its device time [ms] */
 int moses_batch_step_timed(moses_batch *b, int nsteps, double *ms);
-/* number of tiles (CTAs) in one batched stage launch */
+/* number of tiles of all members in the chosen tile shape */
 int moses_batch_tiles(const moses_batch *b);
+/* rows of the chosen tile shape (4, 8 or 16; 0 for NULL); ms_out (may be
+ * NULL) receives the timed first stage of the 32 x 4, 32 x 8 and 32 x 16
+ * shapes [ms] */
+int moses_batch_tile_rows(const moses_batch *b, double ms_out[3]);
+/* replace the chosen tile shape by 32 x rows (4, 8 or 16); EINVAL else */
+int moses_batch_set_tile_rows(moses_batch *b, int rows);
+/* testing only: on != 0 makes the launch's grid barrier wait for one CTA
+ * more than the grid holds, so that every wait runs out (no fault); the call
+ * then returns MOSES_ETIMEOUT.  0 restores normal steps. */
+int moses_batch_debug_timeout(moses_batch *b, int on);
 const char *moses_batch_last_error(const moses_batch *b);
 void moses_batch_destroy(moses_batch *b);
 

@@ -1549,35 +1549,43 @@ int moses_step_static(const double *dem_device, int nx, int ny, double dx, doubl
 
 // ---------------------------------------------------------------------------
 // Ensembles: many independent simulations (own DEM, parameters, grid size,
-// time step) advanced together.  One batched launch per Heun stage covers the
-// tiles of every member; the time loop is recorded once as a CUDA graph of
-// kGraphSteps steps and replayed, so a whole run is a handful of graph
-// launches.  Members stay ordinary moses_sim objects.
+// time step) advanced together.  One cooperative launch runs every stage of
+// every member for all the steps of a call (batch_persistent_kernel); the
+// tile height is the fastest of 32 x 4, 32 x 8 and 32 x 16 on the members'
+// own states, timed when the batch is made.  Members stay ordinary moses_sim
+// objects.
 
 struct moses_batch {
     int n = 0;
     int prec = MOSES_FP64;
-    cudaStream_t stream = nullptr;       // the batch's own stream (graphs cannot be
-                                         // recorded on the legacy default stream)
+    cudaStream_t stream = nullptr;       // the batch's own stream
     cudaStream_t user_stream = nullptr;  // the members' stream
     cudaEvent_t ev = nullptr;
     std::vector<moses_sim *> sims;
     void *args1 = nullptr, *args2 = nullptr;  // StageArgs<T>[n] for stage 1 / 2
     BatchStrip *strips = nullptr;  // (member, 32 x kStripRows strip) of every member
     int nstrips = 0;
-    int ntiles = 0;                // 32 x 8 tiles of all members
-    BatchTile *list = nullptr;     // wet-tile list (capacity ntiles)
+    int ty = 8;                    // tile height of the launch
+    int ntiles = 0;                // 32 x ty tiles of all members
+    int cap = 0;                   // 32 x 4 tiles of all members (the most of any shape)
+    int *tile_sim = nullptr;       // [cap] member of each tile
+    int *tile_base = nullptr;      // [n] first tile of each member
+    BatchTile *list = nullptr;     // wet-tile list (capacity cap)
     unsigned int *list_n = nullptr;
+    unsigned char *zk = nullptr;   // known-zero flags of U* then U, [2][cap]
+    unsigned short *mb = nullptr;  // mass bits of U then U*, [2][cap]
+    GridSync *sync = nullptr;
+    int *from_data = nullptr;
+    int grid = 0;                  // CTAs of the launch
+    int dbg_stall = 0;             // moses_batch_debug_timeout
+    double tune_ms[3] = {0, 0, 0}; // one first stage per tile shape (32 x 4, 32 x 8, 32 x 16)
     Ctl **ctls = nullptr;
+    Ctl *ctl_save = nullptr;       // the members' control blocks while the shapes are timed
     int *status = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     std::string err;
 };
 
 namespace {
-constexpr int kGraphSteps = 16;
-constexpr int kBatchTX = 32, kBatchTY = 8;
 
 __global__ void batch_status_kernel(Ctl *const *ctls, int n, int *out)
 {
@@ -1588,6 +1596,14 @@ __global__ void batch_status_kernel(Ctl *const *ctls, int n, int *out)
     }
 }
 
+__global__ void batch_ctl_copy_kernel(Ctl *const *ctls, Ctl *save, int n, int restore)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (restore) *ctls[k] = save[k];
+        else save[k] = *ctls[k];
+    }
+}
+
 int batch_fail(moses_batch *b, int code, const std::string &msg)
 {
     if (b) b->err = msg;
@@ -1595,25 +1611,22 @@ int batch_fail(moses_batch *b, int code, const std::string &msg)
     return code;
 }
 
+// the stage descriptors and the tile enumeration of the 32 x ty shape
 template <typename T>
-int batch_launch_step(moses_batch *b)
-{
-    for (void *args : {b->args1, b->args2})
-        if (launch_stage_batch<T>((const StageArgs<T> *)args, b->n, b->strips, b->nstrips, b->list, b->list_n,
-                                  b->stream))
-            return -1;
-    return 0;
-}
-
-template <typename T>
-int batch_build(moses_batch *b)
+int batch_layout(moses_batch *b, int ty)
 {
     std::vector<StageArgs<T>> a1(b->n), a2(b->n);
-    std::vector<BatchStrip> strips;
-    long long ntiles = 0;
-    std::vector<Ctl *> ctls(b->n);
+    std::vector<int> tile_sim, tile_base(b->n);
     for (int k = 0; k < b->n; k++) {
         moses_sim *s = b->sims[k];
+        const int gx = (s->nx + 31) / 32, gy = (s->ny + ty - 1) / ty;
+        tile_base[k] = (int)tile_sim.size();
+        tile_sim.insert(tile_sim.end(), (size_t)gx * gy, k);
+    }
+    const size_t nt = tile_sim.size();
+    for (int k = 0; k < b->n; k++) {
+        moses_sim *s = b->sims[k];
+        const size_t tb = (size_t)tile_base[k];
         a1[k] = base_args<T>(s);
         a1[k].Uin = (const T *)s->U;
         a1[k].Uout = (T *)s->Us;
@@ -1629,63 +1642,160 @@ int batch_build(moses_batch *b)
         a2[k].Rout = rem<T>(s, s->U);
         a2[k].stage = 2;
         a2[k].want_amax = 1;
-        // the launches run listed tiles (the pointer marks it; the batch has its own list)
+        // the stage kernel runs listed tiles (the pointer marks it; the batch has its own list)
         a1[k].wl = a2[k].wl = s->wl;
-        a1[k].tw_next = s->tw[0];
-        a2[k].tw_prev = s->tw[0];
-        a2[k].tw_next = s->tw[1];
-        const int tx = (s->nx + kBatchTX - 1) / kBatchTX, ty = (s->ny + kBatchTY - 1) / kBatchTY;
-        ntiles += (long long)tx * ty;
+        a1[k].zk = b->zk + tb;
+        a2[k].zk = b->zk + b->cap + tb;
+        a1[k].mb_in = b->mb + tb;
+        a1[k].mb_out = b->mb + b->cap + tb;
+        a2[k].mb_in = b->mb + b->cap + tb;
+        a2[k].mb_n = b->mb + tb;
+        a2[k].mb_out = b->mb + tb;
+    }
+    moses_sim *s = nullptr;  // CK reports into g_create_err
+    CK(cudaMemcpyAsync(b->args1, a1.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->args2, a2.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->tile_sim, tile_sim.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->tile_base, tile_base.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));  // the host vectors go out of scope
+    b->ty = ty;
+    b->ntiles = (int)nt;
+    return MOSES_OK;
+}
+
+// one launch of `nstages` stages; from_data: the first classifies from the data
+template <typename T>
+int batch_run(moses_batch *b, int nstages, bool from_data)
+{
+    moses_sim *s = nullptr;
+    BatchRun<T> r{};
+    r.args1 = (const StageArgs<T> *)b->args1;
+    r.args2 = (const StageArgs<T> *)b->args2;
+    r.nsim = b->n;
+    r.strips = b->strips;
+    r.nstrips = b->nstrips;
+    r.tile_sim = b->tile_sim;
+    r.tile_base = b->tile_base;
+    r.ntiles = b->ntiles;
+    r.list = b->list;
+    r.list_n = b->list_n;
+    r.sync = b->sync;
+    r.from_data = b->from_data;
+    r.nstages = 0;
+    if (launch_batch<T>(r, b->ty, &b->grid, b->stream)) return batch_fail(b, MOSES_ECUDA, "ensemble kernel attributes");
+    const GridSync g0{0u, 0u, (unsigned int)b->grid + (b->dbg_stall ? 1u : 0u), 0};
+    const int fd = from_data ? 1 : 0;
+    CK(cudaMemcpyAsync(b->sync, &g0, sizeof(GridSync), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->from_data, &fd, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemsetAsync(b->list_n, 0, 2 * sizeof(unsigned int), b->stream));
+    if (from_data) CK(cudaMemsetAsync(b->zk, 0, 2 * (size_t)b->cap, b->stream));
+    r.nstages = nstages;
+    if (nstages > 0 && launch_batch<T>(r, b->ty, nullptr, b->stream))
+        return batch_fail(b, MOSES_ECUDA, std::string("ensemble launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return MOSES_OK;
+}
+
+// the tile height: one first stage per shape on the members' states (after
+// one untimed first stage that classifies from the data), the fastest kept;
+// the members' control blocks are restored afterwards (the stage writes U*,
+// scratch between steps, and the time step and budgets in the control block)
+template <typename T>
+int batch_tune(moses_batch *b)
+{
+    moses_sim *s = nullptr;
+    batch_ctl_copy_kernel<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctls, b->ctl_save, b->n, 0);
+    CK(cudaGetLastError());
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int shapes[3] = {4, 8, 16};
+    int best = 8;
+    double best_ms = 0.0;
+    int rc = MOSES_OK;
+    for (int q = 0; q < 3 && rc == MOSES_OK; q++) {
+        rc = batch_layout<T>(b, shapes[q]);
+        if (rc == MOSES_OK) rc = batch_run<T>(b, 1, true);
+        float m = 0.f;
+        if (rc == MOSES_OK) {
+            cudaEventRecord(e0, b->stream);
+            rc = batch_run<T>(b, 1, false);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&m, e0, e1) != cudaSuccess)
+                rc = batch_fail(b, MOSES_ECUDA, "ensemble tile timing");
+        }
+        b->tune_ms[q] = m;
+        if (rc == MOSES_OK && (q == 0 || m < best_ms)) {
+            best = shapes[q];
+            best_ms = m;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    batch_ctl_copy_kernel<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctls, b->ctl_save, b->n, 1);
+    if (rc) return rc;
+    CK(cudaGetLastError());
+    GridSync g{};
+    CK(cudaMemcpyAsync(&g, b->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    if (g.fail) return batch_fail(b, MOSES_ETIMEOUT, "a bounded device-side wait gave up while timing the tiles");
+    return batch_layout<T>(b, best);
+}
+
+template <typename T>
+int batch_build(moses_batch *b)
+{
+    std::vector<BatchStrip> strips;
+    std::vector<Ctl *> ctls(b->n);
+    long long cap = 0;
+    for (int k = 0; k < b->n; k++) {
+        moses_sim *s = b->sims[k];
+        const int gx = (s->nx + 31) / 32;
+        cap += (long long)gx * ((s->ny + 3) / 4);
         for (int sy = 0; sy < (s->ny + kStripRows - 1) / kStripRows; sy++)
-            for (int sx = 0; sx < tx; sx++) strips.push_back(BatchStrip{k, sx, sy});
+            for (int sx = 0; sx < gx; sx++) strips.push_back(BatchStrip{k, sx, sy});
         ctls[k] = s->ctl;
     }
-    if (ntiles > (1ll << 30)) return batch_fail(b, MOSES_EINVAL, "too many tiles in the batch");
-    b->ntiles = (int)ntiles;
+    if (cap > (1ll << 30)) return batch_fail(b, MOSES_EINVAL, "too many tiles in the batch");
+    b->cap = (int)cap;
     b->nstrips = (int)strips.size();
     moses_sim *s = nullptr;  // CK reports into g_create_err
     CK(cudaMalloc(&b->args1, sizeof(StageArgs<T>) * b->n));
     CK(cudaMalloc(&b->args2, sizeof(StageArgs<T>) * b->n));
     CK(cudaMalloc(&b->strips, sizeof(BatchStrip) * strips.size()));
-    CK(cudaMalloc(&b->list, sizeof(BatchTile) * (size_t)b->ntiles));
+    CK(cudaMalloc(&b->list, sizeof(BatchTile) * (size_t)b->cap));
     CK(cudaMalloc(&b->list_n, 2 * sizeof(unsigned int)));
-    CK(cudaMemsetAsync(b->list_n, 0, 2 * sizeof(unsigned int), b->stream));
+    CK(cudaMalloc(&b->tile_sim, sizeof(int) * (size_t)b->cap));
+    CK(cudaMalloc(&b->tile_base, sizeof(int) * b->n));
+    CK(cudaMalloc(&b->zk, 2 * (size_t)b->cap));
+    CK(cudaMalloc(&b->mb, 2 * sizeof(unsigned short) * (size_t)b->cap));
+    CK(cudaMalloc(&b->sync, sizeof(GridSync)));
+    CK(cudaMalloc(&b->from_data, sizeof(int)));
     CK(cudaMalloc(&b->ctls, sizeof(Ctl *) * b->n));
+    CK(cudaMalloc(&b->ctl_save, sizeof(Ctl) * b->n));
     CK(cudaMalloc(&b->status, sizeof(int)));
-    CK(cudaMemcpyAsync(b->args1, a1.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync(b->args2, a2.data(), sizeof(StageArgs<T>) * b->n, cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync(b->strips, strips.data(), sizeof(BatchStrip) * strips.size(), cudaMemcpyHostToDevice,
                        b->stream));
     CK(cudaMemcpyAsync(b->ctls, ctls.data(), sizeof(Ctl *) * b->n, cudaMemcpyHostToDevice, b->stream));
-    // set the launch attributes outside any capture, then record the graph
-    if (launch_stage_batch<T>((const StageArgs<T> *)b->args1, b->n, b->strips, 0, b->list, b->list_n, b->stream))
-        return batch_fail(b, MOSES_ECUDA, "batched stage kernel attributes");
     CK(cudaStreamSynchronize(b->stream));
-    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = 0;
-    for (int q = 0; q < kGraphSteps && rc == 0; q++) rc = batch_launch_step<T>(b);
-    cudaGraph_t g = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
-    if (rc || ec != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return batch_fail(b, MOSES_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-    }
-    b->graph = g;
-    CK(cudaGraphInstantiate(&b->exec, g, 0));
-    return MOSES_OK;
+    return batch_tune<T>(b);
 }
 
 void free_batch(moses_batch *b)
 {
     if (!b) return;
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->args1);
     cudaFree(b->args2);
     cudaFree(b->strips);
     cudaFree(b->list);
     cudaFree(b->list_n);
+    cudaFree(b->tile_sim);
+    cudaFree(b->tile_base);
+    cudaFree(b->zk);
+    cudaFree(b->mb);
+    cudaFree(b->sync);
+    cudaFree(b->from_data);
     cudaFree(b->ctls);
+    cudaFree(b->ctl_save);
     cudaFree(b->status);
     if (b->ev) cudaEventDestroy(b->ev);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -1725,6 +1835,7 @@ int moses_batch_create(int n, moses_sim *const *sims, moses_batch **out)
         free_batch(b);
         return MOSES_ECUDA;
     }
+    for (moses_sim *m : b->sims) zk_reset(m);  // timing the tile shapes writes the members' U*
     const int rc = b->prec == MOSES_FP64 ? batch_build<double>(b) : batch_build<float>(b);
     if (rc) {
         if (b->err.empty()) b->err = g_create_err;
@@ -1764,14 +1875,9 @@ static int batch_step(moses_batch *b, int nsteps, double *ms)
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, b->stream));
     }
-    int left = nsteps;
-    while (left >= kGraphSteps) {
-        CK(cudaGraphLaunch(b->exec, b->stream));
-        left -= kGraphSteps;
-    }
-    for (; left > 0; left--) {
-        const int rc = b->prec == MOSES_FP64 ? batch_launch_step<double>(b) : batch_launch_step<float>(b);
-        if (rc) return batch_fail(b, MOSES_ECUDA, "batched stage launch failed");
+    if (nsteps > 0) {
+        const int rc = b->prec == MOSES_FP64 ? batch_run<double>(b, 2 * nsteps, true) : batch_run<float>(b, 2 * nsteps, true);
+        if (rc) return rc;
     }
     if (ms) {
         CK(cudaEventRecord(e1, b->stream));
@@ -1785,14 +1891,39 @@ static int batch_step(moses_batch *b, int nsteps, double *ms)
     CK(cudaMemsetAsync(b->status, 0, sizeof(int), b->stream));
     batch_status_kernel<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctls, b->n, b->status);
     int st = 0;
+    GridSync g{};
     CK(cudaMemcpyAsync(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(&g, b->sync, sizeof(GridSync), cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    if (nsteps > 0 && g.fail) return batch_fail(b, MOSES_ETIMEOUT, "a bounded wait of the ensemble launch gave up");
     if (st & STATUS_TIMEOUT) return batch_fail(b, MOSES_ETIMEOUT, "a bounded device-side wait gave up");
     if (st & STATUS_NONFINITE) return batch_fail(b, MOSES_ENONFINITE, "a member became non-finite");
     return MOSES_OK;
 }
 
 int moses_batch_tiles(const moses_batch *b) { return b ? b->ntiles : 0; }
+
+int moses_batch_tile_rows(const moses_batch *b, double ms_out[3])
+{
+    if (!b) return 0;
+    if (ms_out)
+        for (int q = 0; q < 3; q++) ms_out[q] = b->tune_ms[q];
+    return b->ty;
+}
+
+int moses_batch_set_tile_rows(moses_batch *b, int rows)
+{
+    if (!b) return MOSES_EINVAL;
+    if (rows != 4 && rows != 8 && rows != 16) return batch_fail(b, MOSES_EINVAL, "tile rows must be 4, 8 or 16");
+    return b->prec == MOSES_FP64 ? batch_layout<double>(b, rows) : batch_layout<float>(b, rows);
+}
+
+int moses_batch_debug_timeout(moses_batch *b, int on)
+{
+    if (!b) return MOSES_EINVAL;
+    b->dbg_stall = on ? 1 : 0;
+    return MOSES_OK;
+}
 
 const char *moses_batch_last_error(const moses_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
 

@@ -275,11 +275,11 @@ int launch_stage(const StageArgs<T> &a, int tile, void *stream);
 // the same stage (tile 32 x 8) that also writes a.rec
 template <typename T>
 int launch_stage_rec(const StageArgs<T> &a, void *stream);
-// one stage of an ensemble of nsim simulations (descriptors args_device):
-// classification over the `nstrips` strips (32 x kStripRows cells), then the stage on
-// the wet 32 x 8 tiles listed in `list` (capacity: every tile; list_n: two
-// counters, zero between launches).  nstrips == 0 only sets the attributes.
+// an ensemble run (BatchRun, stage.cuh) with 32 x ty tiles (ty 4, 8 or 16):
+// one cooperative launch of every CTA that fits at once; *grid (may be NULL)
+// gets that grid; with r.nstages == 0 nothing is launched
 template <typename T>
-int launch_stage_batch(const StageArgs<T> *args_device, int nsim, const BatchStrip *strips_device, int nstrips,
-                       BatchTile *list, unsigned int *list_n, void *stream);
+struct BatchRun;
+template <typename T>
+int launch_batch(const BatchRun<T> &r, int ty, int *grid, void *stream);
 }  // namespace moses

@@ -16,10 +16,9 @@ int launch_stage_rec<float>(const StageArgs<float> &a, void *stream)
 }
 
 template <>
-int launch_stage_batch<float>(const StageArgs<float> *args_device, int nsim, const BatchStrip *strips_device, int nstrips,
-                            BatchTile *list, unsigned int *list_n, void *stream)
+int launch_batch<float>(const BatchRun<float> &r, int ty, int *grid, void *stream)
 {
-    return launch_stage_batch_impl<float>(args_device, nsim, strips_device, nstrips, list, list_n, stream);
+    return launch_batch_impl<float>(r, ty, grid, stream);
 }
 
 }  // namespace moses

@@ -16,10 +16,9 @@ int launch_stage_rec<double>(const StageArgs<double> &a, void *stream)
 }
 
 template <>
-int launch_stage_batch<double>(const StageArgs<double> *args_device, int nsim, const BatchStrip *strips_device, int nstrips,
-                            BatchTile *list, unsigned int *list_n, void *stream)
+int launch_batch<double>(const BatchRun<double> &r, int ty, int *grid, void *stream)
 {
-    return launch_stage_batch_impl<double>(args_device, nsim, strips_device, nstrips, list, list_n, stream);
+    return launch_batch_impl<double>(r, ty, grid, stream);
 }
 
 }  // namespace moses

@@ -138,30 +138,47 @@ int launch_stage_rec_impl(const StageArgs<T> &a, void *stream)
     return launch_tile<T, 32, 8, true>(a, (cudaStream_t)stream);
 }
 
-template <typename T>
-int launch_stage_batch_impl(const StageArgs<T> *args_device, int nsim, const BatchStrip *strips_device, int nstrips,
-                            BatchTile *list, unsigned int *list_n, void *stream)
+// The ensemble launch with 32 x TY tiles: the grid is every CTA that fits at
+// once (a cooperative launch, so that all of them are resident and can meet);
+// with r.nstages == 0 it only reports that grid.
+template <typename T, int TY>
+int launch_batch_tile(const BatchRun<T> &r, int *grid_out, cudaStream_t st)
 {
-    constexpr size_t smem = stage_smem_bytes<T, 32, 8>();
+    constexpr size_t ss = stage_smem_bytes<T, 32, TY>();
+    constexpr size_t smem = ss > sizeof(ClassifySmem<T>) ? ss : sizeof(ClassifySmem<T>);
     static int resident[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return -1;
     if (!resident[dev]) {
         int per_sm = 0, n_sm = 0;
-        if (cudaFuncSetAttribute(stage_kernel_batch_list<T, 32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(batch_persistent_kernel<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_batch_list<T, 32, 8>, 256, smem) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel<T, TY>, 32 * TY, smem) !=
                 cudaSuccess ||
             cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
             return -1;
         resident[dev] = per_sm * n_sm;
     }
-    if (nstrips <= 0) return 0;
+    if (grid_out) *grid_out = resident[dev];
+    if (r.nstages <= 0) return 0;
+    BatchRun<T> rr = r;
+    void *params[] = {(void *)&rr};
+    return cudaLaunchCooperativeKernel((const void *)batch_persistent_kernel<T, TY>, dim3(resident[dev]), dim3(32 * TY),
+                                       params, smem, st) == cudaSuccess
+               ? 0
+               : -1;
+}
+
+template <typename T>
+int launch_batch_impl(const BatchRun<T> &r, int ty, int *grid_out, void *stream)
+{
     cudaStream_t st = (cudaStream_t)stream;
-    classify_kernel_batch<T><<<nstrips, 32 * kStripWarps, 0, st>>>(args_device, strips_device, list, list_n);
-    stage_kernel_batch_list<T, 32, 8><<<resident[dev], 256, smem, st>>>(args_device, list, list_n, nsim);
-    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+    switch (ty) {
+    case 4: return launch_batch_tile<T, 4>(r, grid_out, st);
+    case 16: return launch_batch_tile<T, 16>(r, grid_out, st);
+    default: return launch_batch_tile<T, 8>(r, grid_out, st);
+    }
 }
 
 }  // namespace

@@ -91,6 +91,9 @@ SIGNATURES = [
     ("moses_batch_step", C.c_int, [_vp, C.c_int]),
     ("moses_batch_step_timed", C.c_int, [_vp, C.c_int, _dp]),
     ("moses_batch_tiles", C.c_int, [_vp]),
+    ("moses_batch_tile_rows", C.c_int, [_vp, _dp]),
+    ("moses_batch_set_tile_rows", C.c_int, [_vp, C.c_int]),
+    ("moses_batch_debug_timeout", C.c_int, [_vp, C.c_int]),
     ("moses_batch_last_error", C.c_char_p, [_vp]),
     ("moses_batch_destroy", None, [_vp]),
     ("moses_adjoint_misfit", C.c_int, [_vp, C.c_int, C.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
@@ -354,6 +357,25 @@ class Batch:
     @property
     def tiles(self) -> int:
         return self._L.moses_batch_tiles(self._h)
+
+    def tile_rows(self):
+        """(rows of the chosen 32-wide tile shape, [ms of one first stage for
+        32 x 4, 32 x 8, 32 x 16]) as timed by moses_batch_create."""
+        ms = np.zeros(3)
+        ty = self._L.moses_batch_tile_rows(self._h, _p(ms))
+        return ty, [float(x) for x in ms]
+
+    def set_tile_rows(self, rows: int):
+        rc = self._L.moses_batch_set_tile_rows(self._h, int(rows))
+        if rc != 0:
+            raise MosesError(rc, self._L.moses_batch_last_error(self._h).decode())
+
+    def debug_timeout(self, on: bool = True):
+        """Make every wait of the launch's grid barrier run out (testing the
+        MOSES_ETIMEOUT path without a fault); False restores normal steps."""
+        rc = self._L.moses_batch_debug_timeout(self._h, int(bool(on)))
+        if rc != 0:
+            raise MosesError(rc, self._L.moses_batch_last_error(self._h).decode())
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,9 +1,13 @@
 """Ensembles (moses_batch_*): members of different sizes, DEMs and parameters
-advanced together by batched launches replayed from a CUDA graph.
+advanced together, all the steps of a call in one cooperative launch whose
+CTAs meet on a bounded grid barrier between the phases of a stage.
 
-Each member must equal its solo run bit for bit (the batched launch runs the
-same tile code), keep its own time and CFL time step, and match the FP64
-oracle at the parity tolerance.
+Each member must equal its solo run bit for bit (the launch runs the same tile
+code) for every tile shape the tuner can choose, keep its own time and CFL
+time step, and match the FP64 oracle at the parity tolerance.  A barrier
+whose waits run out (moses_batch_debug_timeout: it waits for one CTA more than
+the grid holds) ends the launch with MOSES_ETIMEOUT, no fault, and the batch
+steps normally afterwards.
 """
 import numpy as np
 import pytest
@@ -25,14 +29,22 @@ def _members():
     return cfgs
 
 
+@pytest.mark.parametrize("rows", [None, 4, 8, 16])
 @pytest.mark.parametrize("precision", [moses.FP64, moses.FP32])
-def test_batch_equals_solo_runs(precision):
+def test_batch_equals_solo_runs(precision, rows):
     cfgs = _members()
-    steps = 37  # two graph replays of 16 steps and 5 single steps
+    steps = 37  # two calls: 20 steps and 17 steps
     members = [moses.from_config(c, precision=precision) for c in cfgs]
     with moses.Batch(members) as b:
-        assert b.tiles == sum(((m.nx + 31) // 32) * ((m.ny + 7) // 8) for m in members)
-        b.step(steps)
+        ty, ms = b.tile_rows()
+        assert ty in (4, 8, 16) and all(m > 0 for m in ms)
+        if rows is not None:
+            b.set_tile_rows(rows)
+            ty = rows
+        assert b.tile_rows()[0] == ty
+        assert b.tiles == sum(((m.nx + 31) // 32) * ((m.ny + ty - 1) // ty) for m in members)
+        b.step(20)
+        b.step(steps - 20)
     times = []
     for c, m in zip(cfgs, members):
         solo = moses.from_config(c, precision=precision)
@@ -67,3 +79,31 @@ def test_batch_rejects_bad_members():
         moses.Batch([a, f])
     with pytest.raises(moses.MosesError):
         moses.Batch([a, a])
+
+
+@pytest.mark.parametrize("precision", [moses.FP64, moses.FP32])
+def test_barrier_timeout_is_reported_and_the_batch_recovers(precision):
+    cfgs = _members()[:3]
+    members = [moses.from_config(c, precision=precision) for c in cfgs]
+    U0 = [m.get_conserved() for m in members]
+    with moses.Batch(members) as b:
+        b.debug_timeout(True)
+        with pytest.raises(moses.MosesError) as e:
+            b.step(3)
+        assert e.value.code == moses.MOSES_ETIMEOUT
+        # the launch ended at its first meeting: no stage reached the states
+        for m, u in zip(members, U0):
+            assert np.array_equal(m.get_conserved(), u)
+        b.debug_timeout(False)
+        b.step(12)
+    for c, m in zip(cfgs, members):
+        solo = moses.from_config(c, precision=precision)
+        solo.step(12)
+        assert np.array_equal(m.get_conserved(), solo.get_conserved()), c["name"]
+
+
+def test_batch_rejects_bad_tile_rows():
+    members = [moses.from_config(c) for c in _members()[:2]]
+    with moses.Batch(members) as b:
+        with pytest.raises(moses.MosesError):
+            b.set_tile_rows(6)
