@@ -7,6 +7,8 @@
 // adjoints of adjoint.cuh.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -20,8 +22,21 @@ namespace {
 
 constexpr int ATX = 32, ATY = 8;
 
+// a box of 32 x 8 tiles, inclusive; empty where x1 < x0
+struct TileBox {
+    int x0, y0, x1, y1;
+    bool empty() const { return x1 < x0 || y1 < y0; }
+};
+inline TileBox box_union(const TileBox &a, const TileBox &b)
+{
+    if (a.empty()) return b;
+    if (b.empty()) return a;
+    return TileBox{std::min(a.x0, b.x0), std::min(a.y0, b.y0), std::max(a.x1, b.x1), std::max(a.y1, b.y1)};
+}
+inline dim3 box_grid(const TileBox &b) { return dim3(b.x1 - b.x0 + 1, b.y1 - b.y0 + 1); }
+
 template <typename T, bool KM>
-int launch_adj_face(const AdjArgs<T> &q, cudaStream_t st)
+int launch_adj_face(const AdjArgs<T> &q, cudaStream_t st, const TileBox &box)
 {
     static bool attr[64] = {};
     int dev = 0;
@@ -36,16 +51,27 @@ int launch_adj_face(const AdjArgs<T> &q, cudaStream_t st)
             return -1;
         attr[dev] = true;
     }
-    const dim3 grid((q.f.nx + ATX - 1) / ATX, (q.f.ny + ATY - 1) / ATY);
-    adj_face_kernel<T, ATX, ATY, KM><<<grid, ATX * ATY, smB, st>>>(q);
+    adj_face_kernel<T, ATX, ATY, KM><<<box_grid(box), ATX * ATY, smB, st>>>(q);
     return 0;
 }
 
+// the cell kernel on the tiles of `cell`, the face kernel on those of `face`
+// (every tile outside them is one that the kernels would leave at once)
 template <typename T>
-int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
+int launch_adj_stage(const AdjArgs<T> &q_in, cudaStream_t st, const TileBox &cell, const TileBox &face)
 {
-    adj_cell_kernel<T><<<dim3((q.f.nx + 31) / 32, (q.f.ny + 7) / 8), 256, 0, st>>>(q);
-    if ((q.f.ph.k_mode == 1 ? launch_adj_face<T, true>(q, st) : launch_adj_face<T, false>(q, st)) != 0) return -1;
+    AdjArgs<T> q = q_in;
+    if (!cell.empty()) {
+        q.bx0 = cell.x0;
+        q.by0 = cell.y0;
+        adj_cell_kernel<T><<<box_grid(cell), 256, 0, st>>>(q);
+    }
+    if (!face.empty()) {
+        q.bx0 = face.x0;
+        q.by0 = face.y0;
+        if ((q.f.ph.k_mode == 1 ? launch_adj_face<T, true>(q, st, face) : launch_adj_face<T, false>(q, st, face)) != 0)
+            return -1;
+    }
     if (!q.fold_inline) {
         const int nfold = 6 * (2 * q.f.nx + 2 * q.f.ny);
         adj_fold_kernel<T><<<(nfold + 255) / 256, 256, 0, st>>>(q);
@@ -53,6 +79,18 @@ int launch_adj_stage(const AdjArgs<T> &q, cudaStream_t st)
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
+
+// n empty boxes (x min, y min = INT_MAX; x max, y max = -1), widened by the
+// classification (StageArgs::wbox)
+__global__ void box_init_kernel(int *box, int n)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        box[4 * k] = INT_MAX;
+        box[4 * k + 1] = INT_MAX;
+        box[4 * k + 2] = -1;
+        box[4 * k + 3] = -1;
+    }
+}
 
 // L = sum (h^s - h^s_target)^2 dx dy with h^s = U1 / J; lam = dL/dU (U1 only)
 template <typename T>
@@ -145,7 +183,7 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     const size_t lb = 6 * (size_t)plane * sizeof(T);
     const int nck = (nsteps + C - 1) / C;
     const size_t rb = 6 * (size_t)plane * sizeof(T);  // one stage's record
-    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, gpar, loss_d, tgt, phi_d, hbuf, zkseg, twseg, lamz, mbseg;
+    DevBuf dts_d, ck, seg, recb, lam, lamA, lpre, ldp, gpar, loss_d, tgt, phi_d, hbuf, zkseg, twseg, lamz, mbseg, boxd;
     // tiles of the 32 x 8 launches (the forward run, the recording recompute
     // and the adjoint kernels share this tiling)
     const int tgx = (nx + 31) / 32, tgy = (ny + 7) / 8;
@@ -178,6 +216,14 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     CK(cudaMemsetAsync(twseg.p, 0, 2 * nt * 2 * C, st));
     CK(cudaMalloc(&lamz.p, nt));
     CK(cudaMemsetAsync(lamz.p, 1, nt, st));
+    // per set and stage of a segment: the box of the tiles the recompute's
+    // classification listed, read back by the host before the segment's sweep
+    CK(cudaMalloc(&boxd.p, sizeof(int) * 4 * 2 * 2 * C));
+    struct PinnedInts {
+        int *p = nullptr;
+        ~PinnedInts() { cudaFreeHost(p); }
+    } boxh;
+    CK(cudaMallocHost(&boxh.p, sizeof(int) * 4 * 2 * 2 * C));
     CK(cudaMalloc(&tgt.p, sizeof(double) * n));
     CK(cudaMemcpyAsync(tgt.p, hs_target, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     if (release_phi) {
@@ -193,6 +239,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
     auto tws = [&](int b) { return (unsigned char *)twseg.p + nt * 2 * C * b; };
     // mass bits of segU(b, m) at m, of segS(b, m) at C + 1 + m
     auto mbs = [&](int b) { return (unsigned short *)mbseg.p + nt * (2 * C + 1) * b; };
+    // the listed-tile box of stage (m, stage) of set b
+    auto boxes = [&](int b) { return (int *)boxd.p + 4 * 2 * C * b; };
 
     cudaEvent_t ev[4];
     for (int q = 0; q < 4; q++) CK(cudaEventCreate(&ev[q]));
@@ -295,6 +343,7 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
         const int b = kseg & 1, start = kseg * C, end = std::min(start + C, nsteps);
         if (swept[b]) CK(cudaStreamWaitEvent(rs, sweep_done[b], 0));
         CK(cudaMemcpyAsync(segU(b, 0), ckp + sb * kseg, sb, cudaMemcpyDeviceToDevice, rs));
+        box_init_kernel<<<1, 256, 0, rs>>>(boxes(b), 2 * C);
         for (int k = start; k < end; k++) {
             const int m = k - start;
             StageArgs<T> r1 = a1, r2 = a2;
@@ -330,15 +379,30 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
             r2.mb_n = mbs(b) + nt * m;
             r2.mb_out = mbs(b) + nt * (m + 1);
             r2.mb_ok = 1;
+            r1.wbox = boxes(b) + 4 * (2 * m);
+            r2.wbox = boxes(b) + 4 * (2 * m + 1);
             if (launch_stage_rec<T>(r1, rs) || launch_stage_rec<T>(r2, rs))
                 return fail(s, MOSES_ECUDA, "recompute launch");
         }
+        CK(cudaMemcpyAsync(boxh.p + 4 * 2 * C * b, boxes(b), sizeof(int) * 4 * 2 * C, cudaMemcpyDeviceToHost, rs));
         CK(cudaEventRecord(rec_done[b], rs));
         return MOSES_OK;
     };
+    // the near box of a stage: its listed tiles' box widened by the two tiles
+    // of the adjoint kernels' far test (AdjArgs::tw), within the grid
+    auto near_box = [&](int b, int idx) {
+        const int *w = boxh.p + 4 * (2 * C * b + idx);
+        if (w[2] < w[0]) return TileBox{0, 0, -1, -1};
+        return TileBox{std::max(w[0] - 2, 0), std::max(w[1] - 2, 0), std::min(w[2] + 2, tgx - 1),
+                       std::min(w[3] + 2, tgy - 1)};
+    };
+    // the near box of the last first-stage reverse: its tiles may hold momentum
+    // adjoints that the next one zeroes where it finds them far (AdjArgs::lamz)
+    TileBox prev1{0, 0, -1, -1};
     auto sweep = [&](const int kseg) -> int {
         const int b = kseg & 1, start = kseg * C, end = std::min(start + C, nsteps);
         CK(cudaStreamWaitEvent(st, rec_done[b], 0));
+        CK(cudaEventSynchronize(rec_done[b]));  // the segment's boxes (the sweep before keeps the GPU busy)
         for (int k = end - 1; k >= start; k--) {
             const int m = k - start;
             q.f = base_args<T>(s);
@@ -352,7 +416,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
             q.heun = 2;
             q.lam_out = nullptr;
             q.lam_in = (T *)lamA.p;
-            if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
+            const TileBox n2 = near_box(b, 2 * m + 1), n1 = near_box(b, 2 * m);
+            if (launch_adj_stage<T>(q, st, n2, n2)) return fail(s, MOSES_ECUDA, "adjoint launch");
             // stage 1 at U^n: lam_out = lamA; lam^n = its input adjoint + the Heun term, over lam^{n+1}
             q.f.Uin = segU(b, m);
             q.f.rec = rec(b, m, 1);
@@ -360,7 +425,8 @@ int adjoint_impl(moses_sim *s, int nsteps, int C, const double *hs_target, doubl
             q.heun = 1;
             q.lam_out = (const T *)lamA.p;
             q.lam_in = (T *)lam.p;
-            if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
+            if (launch_adj_stage<T>(q, st, box_union(n1, prev1), n1)) return fail(s, MOSES_ECUDA, "adjoint launch");
+            prev1 = n1;
         }
         CK(cudaEventRecord(sweep_done[b], st));
         swept[b] = true;
@@ -499,7 +565,8 @@ int stage_adjoint_impl(moses_sim *s, double t, double dt, const double *lam_out,
     q.lam_pre = (T *)lpre.p;
     q.lam_dp = (T *)ldp.p;
     q.g_param = (double *)gp.p;
-    if (launch_adj_stage<T>(q, st)) return fail(s, MOSES_ECUDA, "adjoint launch");
+    const TileBox all{0, 0, (s->nx + ATX - 1) / ATX - 1, (s->ny + ATY - 1) / ATY - 1};
+    if (launch_adj_stage<T>(q, st, all, all)) return fail(s, MOSES_ECUDA, "adjoint launch");
     pack_lam_kernel<T><<<grid_for(6 * n), 256, 0, st>>>((const T *)li.p, (double *)hb.p, s->nx, s->ny, s->pitch,
                                                         s->plane);
     CK(cudaGetLastError());

@@ -173,19 +173,27 @@ struct AdjArgs {
     // sources itself (every source lies in the owning tile: the last tile
     // along each axis holds two cells or more), and no fold kernel runs
     int fold_inline;
+    // the launch covers a box of tiles: CTA (blockIdx.x, blockIdx.y) takes
+    // the 32 x 8 tile (bx0 + blockIdx.x, by0 + blockIdx.y)
+    int bx0, by0;
 };
 
 // the tile (bx, by) of the adjoint kernels lies two tiles or more from every
 // wet tile of the stage (see AdjArgs::tw)
+// (the 25 flags are loaded together, one memory latency, and OR-ed: an early
+// exit would chain the loads, and most CTAs of a step are such far tiles)
 template <typename T>
 __device__ __forceinline__ bool adj_far_from_mass(const AdjArgs<T> &q, int bx, int by)
 {
+    unsigned int any = 0u;
+#pragma unroll
     for (int dy = -2; dy <= 2; dy++)
+#pragma unroll
         for (int dx = -2; dx <= 2; dx++) {
             const int xx = bx + dx, yy = by + dy;
-            if (xx >= 0 && xx < q.tgx && yy >= 0 && yy < q.tgy && q.tw[yy * q.tgx + xx]) return false;
+            if (xx >= 0 && xx < q.tgx && yy >= 0 && yy < q.tgy) any |= q.tw[yy * q.tgx + xx];
         }
-    return true;
+    return any == 0u;
 }
 
 // 1/2 lam^{n+1}, momenta zeroed where U^{n+1} is dry (adjoint of the Heun
@@ -224,16 +232,17 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
     __shared__ double red[2][NT / 32];
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * 32 + (tid & 31), j = blockIdx.y * 8 + (tid >> 5);
+    const int tbx = q.bx0 + (int)blockIdx.x, tby = q.by0 + (int)blockIdx.y;  // the tile (AdjArgs::bx0)
+    const int i = tbx * 32 + (tid & 31), j = tby * 8 + (tid >> 5);
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
     const KT<T> &k = a.k;
     const T *geo = a.geo;
     const double dt = a.dbg_dt;
     const T dtT = (T)dt;
-    if (q.tw && adj_far_from_mass(q, blockIdx.x, blockIdx.y)) {  // CTA-uniform (AdjArgs::tw)
+    if (q.tw && adj_far_from_mass(q, tbx, tby)) {  // CTA-uniform (AdjArgs::tw)
         if (q.heun != 1) return;
-        const int tile = blockIdx.y * q.tgx + blockIdx.x;
+        const int tile = tby * q.tgx + tbx;
         if (q.lamz[tile]) return;
         if (i < nx && j < ny) {
             const long long g = cell_index(i, j, pitch);
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
         if (tid == 0) q.lamz[tile] = 1;
         return;
     }
-    if (q.lamz && q.heun == 1 && tid == 0) q.lamz[blockIdx.y * q.tgx + blockIdx.x] = 0;
+    if (q.lamz && q.heun == 1 && tid == 0) q.lamz[tby * q.tgx + tbx] = 0;
     // parameter partials: per cell and across the warp in T, per CTA and
     // globally in FP64 (the FP64 pipe of GB300 is 1/64 of its FP32 rate)
     T g_tan = T(0), g_cd = T(0);
@@ -516,7 +525,7 @@ __device__ __forceinline__ void adj_face_dir(const AdjArgs<T> &q, T *sU, T *sS, 
     constexpr int STEP = D == 0 ? 1 : SW3;  // smem stride along the normal
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = (q.bx0 + (int)blockIdx.x) * TX, y0 = (q.by0 + (int)blockIdx.y) * TY;
     const int o0 = D == 0 ? x0 : y0;
     const int n = D == 0 ? a.nx : a.ny, nt = D == 0 ? a.ny : a.nx;  // along, across
     const int pitch = a.pitch;
@@ -696,7 +705,7 @@ __device__ __forceinline__ void adj_ghost_zero(const AdjArgs<T> &q)
     constexpr int NT = TX * TY;
     constexpr int L = D == 0 ? TX : TY, M = D == 0 ? TY : TX;
     const StageArgs<T> &a = q.f;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = (q.bx0 + (int)blockIdx.x) * TX, y0 = (q.by0 + (int)blockIdx.y) * TY;
     const int o0 = D == 0 ? x0 : y0;
     const int n = D == 0 ? a.nx : a.ny, nt = D == 0 ? a.ny : a.nx;
     for (int e = threadIdx.x; e < 4 * M; e += NT) {
@@ -720,7 +729,7 @@ __device__ __forceinline__ void adj_fold_tile(const AdjArgs<T> &q)
 {
     constexpr int NT = TX * TY;
     const StageArgs<T> &a = q.f;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = (q.bx0 + (int)blockIdx.x) * TX, y0 = (q.by0 + (int)blockIdx.y) * TY;
     const long long plane = a.plane;
 #pragma unroll
     for (int D = 0; D < 2; D++) {
@@ -773,10 +782,10 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     __shared__ double kred[2][NT / 32];
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = (q.bx0 + (int)blockIdx.x) * TX, y0 = (q.by0 + (int)blockIdx.y) * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
-    if (q.tw && adj_far_from_mass(q, blockIdx.x, blockIdx.y)) {  // CTA-uniform: no face terms (AdjArgs::tw)
+    if (q.tw && adj_far_from_mass(q, q.bx0 + (int)blockIdx.x, q.by0 + (int)blockIdx.y)) {  // CTA-uniform: no face terms (AdjArgs::tw)
         adj_ghost_zero<T, TX, TY, 0>(q);
         adj_ghost_zero<T, TX, TY, 1>(q);
         return;

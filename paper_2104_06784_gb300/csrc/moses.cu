@@ -918,9 +918,10 @@ static int launch_steps(moses_sim *s, int nsteps, double *stage_ms = nullptr)
         a[q].want_amax = q == ns - 1;
         a[q].wl = s->wl;
         a[q].wl_n = s->wl_n;
-        // the first stage classifies from the data, the later ones from the flags of the stage before
+        // the first stage classifies from the data or the mass bits, the later
+        // ones from the mass bits (the stage-before flags only where the bits are off)
         a[q].tw_next = s->tw[q % 2];
-        a[q].tw_prev = q > 0 ? s->tw[(q - 1) % 2] : nullptr;
+        a[q].tw_prev = q > 0 && !zk_on ? s->tw[(q - 1) % 2] : nullptr;
         if (zk_on) {
             a[q].zk = s->zk + nt * bufno(out[q]);
             a[q].mb_in = s->mb + nt * bufno(in[q]);

@@ -243,6 +243,10 @@ struct alignas(8) StageArgs {
     double fix_t, fix_dt;
     double *t_log, *dt_log;
     int log_idx;
+    // with wbox non-null the classification also widens wbox (x min, y min,
+    // x max, y max of the launch's tiles) to every tile it lists: the box of
+    // the stage's work, which the adjoint's kernels then cover
+    int *wbox;
 };
 
 // Mass bits of a 32 x TY tile: where its cells hold mass (U1 or U4 non-zero,

@@ -1521,6 +1521,15 @@ struct __align__(16) ClassifySmem {
     bool keep[kStripRows];                               // the tile is not zero-written here (keep_tile)
 };
 
+// the box b (x min, y min, x max, y max) widened to the tile (x, y)
+__device__ __forceinline__ void box_add(int *b, int x, int y)
+{
+    atomicMin(&b[0], x);
+    atomicMin(&b[1], y);
+    atomicMax(&b[2], x);
+    atomicMax(&b[3], y);
+}
+
 // Wet/dry masking over a whole launch, for the stepping of the plain form.
 // A tile (32 x TY cells) holds work if a cell of it or of its 2-cell halo has
 // mass (U1 or U4 non-zero; NaN counts), or if a cell of it has a non-zero
@@ -1596,6 +1605,7 @@ __device__ __forceinline__ bool classify_strip(const StageArgs<T> &a, const int 
                 const bool inf = on_inflow_side(a, bx, ty, gx, gy);
                 w |= inf;
                 if (w) append(bx, ty);
+                if (w && a.wbox) box_add(a.wbox, bx, ty);
                 a.tw_next[ty * gx + bx] = w;
                 keep = keep_tile(a, w, inf, ty * gx + bx, known);
             }
@@ -1676,6 +1686,7 @@ __device__ __forceinline__ bool classify_strip(const StageArgs<T> &a, const int 
                 bool w = false;
                 for (int r = t * TY; r < t * TY + TY + 4; r++) w |= s_row[r] != 0u;
                 if (w) append(bx, ty);
+                if (w && a.wbox) box_add(a.wbox, bx, ty);
                 if (a.tw_next) a.tw_next[ty * gx + bx] = w;
                 if (a.mb_in && a.stage == 1) a.mb_in[ty * gx + bx] = mass_bits<TY>(&s_own[t * TY]);
                 if (a.mb_out && !w) a.mb_out[ty * gx + bx] = 0;
@@ -1753,6 +1764,9 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
         if (a.mb_ok) {
             w = wet_from_bits(a.mb_in, bx, ty, gx, gy);
             if (a.mb_n) w |= (a.mb_n[idx] & MB_ANY) != 0;
+            // the adjoint's runs: a combining stage also lists the first
+            // stage's wet tiles (its reverse relies on that inclusion)
+            if (a.tw_prev) w |= a.tw_prev[idx] != 0;
         } else {
             for (int dy = -1; dy <= 1; dy++)
                 for (int dx = -1; dx <= 1; dx++) {
@@ -1763,6 +1777,7 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
         const bool inf = on_inflow_side(a, bx, ty, gx, gy);
         w |= inf;
         if (w) a.wl[atomicAdd(&a.wl_n[0], 1u)] = idx;
+        if (w && a.wbox) box_add(a.wbox, bx, ty);
         if (a.tw_next) a.tw_next[idx] = w;
         if (a.mb_out && !w) a.mb_out[idx] = 0;
         if (!keep_tile(a, w, inf, idx, known)) s_list[atomicAdd(&s_n, 1u)] = idx;
