@@ -178,9 +178,12 @@ int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms);
 int moses_set_tile(moses_sim *s, int tile);
 
 /* Autotuner: times `reps` (>= 1; 0 = 5) first stages of a step from the
- * current state, launched as moses_step launches them, with each tile shape
- * (CUDA events on the simulation's stream, after one warm-up launch each; the
- * state, time and budgets are not changed), selects the fastest and
+ * current state, launched as moses_step launches them in a run (classified
+ * from the per-tile mass bits, dry tiles that hold the zero state left
+ * unwritten), with each tile shape (CUDA events on the simulation's stream,
+ * after one untimed stage each that classifies from the data and sets those
+ * records up; the state, time and budgets are not changed), selects the
+ * fastest and
  * returns it in *tile_out (may be NULL).  ms_out (may be NULL) receives the
  * mean time per launch of each tile [ms], indexed by MOSES_TILE_*.  The choice
  * is cached per process by (device, SM count, precision, nx, ny): a later call

@@ -1020,12 +1020,16 @@ namespace {
 std::mutex g_tune_mu;
 std::map<std::array<int, 5>, int> g_tune_cache;  // (device, SMs, precision, nx, ny) -> tile
 
-// the first stage of a step as moses_step launches it (wet-tile list and
-// all), from the current state into the scratch buffer; it also touches the
-// control block (time step, budgets), which the caller restores
+// the first stage of a step as moses_step launches it in its steady state
+// (wet-tile list, known-zero flags of U*, mass bits of U), from the current
+// state into the scratch buffer; `steady` false: the first such stage after a
+// state change, which classifies from the data and writes U's mass bits.  It
+// also touches the control block (time step, budgets), which the caller
+// restores
 template <typename T>
-int probe_stage(moses_sim *s, int tile)
+int probe_stage(moses_sim *s, int tile, bool steady)
 {
+    const size_t nt = (size_t)((s->nx + 31) / 32) * ((s->ny + 3) / 4);
     StageArgs<T> a = base_args<T>(s);
     a.Uin = (const T *)s->U;
     a.Uout = (T *)s->Us;
@@ -1035,6 +1039,10 @@ int probe_stage(moses_sim *s, int tile)
     a.wl = s->wl;
     a.wl_n = s->wl_n;
     a.tw_next = s->tw[0];
+    a.zk = s->zk + nt;
+    a.mb_in = s->mb;
+    a.mb_out = s->mb + nt;
+    a.mb_ok = steady;
     return launch_stage<T>(a, tile, s->stream);
 }
 }  // namespace
@@ -1067,10 +1075,16 @@ int moses_autotune(moses_sim *s, int reps, int *tile_out, double *ms_out)
     CK(cudaEventCreate(&e1));
     double ms[MOSES_NTILES];
     int best = 0;
+    const size_t nt = (size_t)((s->nx + 31) / 32) * ((s->ny + 3) / 4);
+    const bool listed = !(s->ph.nu_f > 0.0) && s->ph.scheme != 1 && s->ph.recon != 1;
     for (int t = 0; t < MOSES_NTILES && rc == 0; t++) {
+        // an untimed first stage sets up the shape's flags and mass bits; the
+        // timed ones then run as the steps of a run do
+        if (cudaMemsetAsync(s->zk, 0, 3 * nt, s->stream) != cudaSuccess) rc = -1;
         for (int r = 0; r <= reps && rc == 0; r++) {
             if (r == 1) cudaEventRecord(e0, s->stream);
-            rc = s->prec == MOSES_FP64 ? probe_stage<double>(s, t) : probe_stage<float>(s, t);
+            const bool steady = r > 0 && listed;
+            rc = s->prec == MOSES_FP64 ? probe_stage<double>(s, t, steady) : probe_stage<float>(s, t, steady);
         }
         cudaEventRecord(e1, s->stream);
         float f = 0.0f;

@@ -262,23 +262,71 @@ __device__ __forceinline__ void side_flux(const T u[6], const FaceGeo<T> &G, T F
     }
 }
 
+// What the central flux needs of one reconstructed side (as side_flux): the
+// mass fluxes (0 where the phase is dry), the normal velocities, the pressure
+// products Ut U1 and Ut^2 and the per-phase local speeds (R7).
+template <typename T>
+struct SideTerms {
+    T m0, m3, vs, vf, Ps, Pf, as, af;
+};
+template <typename T, int D>
+__device__ __forceinline__ SideTerms<T> side_terms(const T u[6], const FaceGeo<T> &G)
+{
+    SideTerms<T> r;
+    const T Ut = u[0] + u[3];
+    const bool ws = gtp(u[0], G.jhd), wf = gtp(u[3], G.jhd);
+    const T rs = ws ? frcp(u[0]) : T(0);
+    const T rf = wf ? frcp(u[3]) : T(0);
+    const T uns = D == 0 ? u[1] : u[2];
+    const T unf = D == 0 ? u[4] : u[5];
+    r.vs = uns * rs;
+    r.vf = unf * rf;
+    r.m0 = ws ? uns : T(0);
+    r.m3 = wf ? unf : T(0);
+    r.Ps = Ut * u[0];
+    r.Pf = Ut * Ut;
+    r.as = tabs(r.vs) + fsqrt(G.sn * (Ut + u[0]));
+    r.af = tabs(r.vf) + fsqrt(G.fn2 * Ut);
+    return r;
+}
+
 // Twice the central flux through one face, from the face values um (left /
 // lower cell) and up (right / upper cell): H2 = F(um) + F(up) - a (up - um),
 // a = max of the two sides' local speeds per phase; H2[6] = P(um) + P(up).
+// With F = (U v_n + s P) for a momentum component (s its pressure
+// coefficient, P the side's pressure product) the momentum rows are taken as
+// um (v_n(um) + a) + up (v_n(up) - a) + (s P(um) + s P(up)), the same sum with
+// fewer FP64 operations (the factors v_n +- a and P(um) + P(up) shared by the
+// components of a phase).
 // Gm, Gp: the face geometry as each side sees it (they differ only in the
 // solid pressure coefficients, scaled by each side's earth-pressure
-// coefficient with k_mode 1; the same otherwise).
-template <typename T, int D>
+// coefficient with k_mode 1: SAME false; the same otherwise).
+template <typename T, int D, bool SAME = true>
 __device__ __forceinline__ void face_flux2(const T um[6], const T up[6], const FaceGeo<T> &Gm, const FaceGeo<T> &Gp,
                                            T H[7])
 {
-    T Fm[6], Fp[6], asm_, afm, asp, afp, Pm, Pp;
-    side_flux<T, D>(um, Gm, Fm, asm_, afm, Pm);
-    side_flux<T, D>(up, Gp, Fp, asp, afp, Pp);
-    const T as = maxnn(asm_, asp), af = maxnn(afm, afp);
-#pragma unroll
-    for (int c = 0; c < 6; c++) H[c] = fma(-(c < 3 ? as : af), up[c] - um[c], Fm[c] + Fp[c]);
-    H[6] = Pm + Pp;
+    const SideTerms<T> m = side_terms<T, D>(um, Gm), p = side_terms<T, D>(up, Gp);
+    const T as = maxnn(m.as, p.as), af = maxnn(m.af, p.af);
+    H[0] = fma(-as, up[0] - um[0], m.m0 + p.m0);
+    H[3] = fma(-af, up[3] - um[3], m.m3 + p.m3);
+    const T As = m.vs + as, Bs = p.vs - as, Af = m.vf + af, Bf = p.vf - af;
+    // X-momentum uses the normal coefficient on x-faces, the transverse one
+    // on y-faces; Y-momentum the other way round
+    const T sXm = D == 0 ? Gm.sn : Gm.st, sYm = D == 0 ? Gm.st : Gm.sn;
+    if constexpr (SAME) {
+        const T Ss = m.Ps + p.Ps;
+        H[1] = fma(um[1], As, fma(up[1], Bs, sXm * Ss));
+        H[2] = fma(um[2], As, fma(up[2], Bs, sYm * Ss));
+    } else {
+        const T sXp = D == 0 ? Gp.sn : Gp.st, sYp = D == 0 ? Gp.st : Gp.sn;
+        H[1] = fma(um[1], As, fma(up[1], Bs, fma(sXm, m.Ps, sXp * p.Ps)));
+        H[2] = fma(um[2], As, fma(up[2], Bs, fma(sYm, m.Ps, sYp * p.Ps)));
+    }
+    const T fX = D == 0 ? Gm.fn : Gm.ft, fY = D == 0 ? Gm.ft : Gm.fn;
+    const T Sf = m.Pf + p.Pf;
+    H[4] = fma(um[4], Af, fma(up[4], Bf, fX * Sf));
+    H[5] = fma(um[5], Af, fma(up[5], Bf, fY * Sf));
+    H[6] = Gm.hg * Sf;  // hg is the face's (the earth-pressure scaling leaves it)
 }
 
 // Twice the central-upwind flux (the second-order scheme Sect. 2.2 cites): per
@@ -1029,7 +1077,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                 Gm.st *= Km;
                 Gp.sn *= Kp;
                 Gp.st *= Kp;
-                face_flux2<T, 0>(um, up, Gm, Gp, H);
+                face_flux2<T, 0, false>(um, up, Gm, Gp, H);
             } else face_flux2<T, 0>(um, up, G, G, H);
             if constexpr (sizeof(T) == 4) {
                 // FP32: the mass change this face gives each neighbour, rounded once
@@ -1085,7 +1133,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                 Gm.st *= Km;
                 Gp.sn *= Kp;
                 Gp.st *= Kp;
-                face_flux2<T, 1>(um, up, Gm, Gp, H);
+                face_flux2<T, 1, false>(um, up, Gm, Gp, H);
             } else face_flux2<T, 1>(um, up, G, G, H);
             if constexpr (sizeof(T) == 4) {
                 H[0] *= dtT * k.hinv_dy;

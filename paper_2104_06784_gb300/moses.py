@@ -230,6 +230,11 @@ class Sim:
 
     def set_tile(self, tile: int):
         self._ck(self._L.moses_set_tile(self._h, int(tile)))
+        self._tile = int(tile)
+
+    def tile_name(self) -> str:
+        """The tile shape the stepping launches use (set_tile / autotune; 32x8 by default)."""
+        return self.TILES[getattr(self, "_tile", 0)]
 
     def autotune(self, reps: int = 5, timings: bool = True):
         """Time one stage with each tile shape, keep the fastest; returns
@@ -238,6 +243,7 @@ class Sim:
         t = C.c_int()
         ms = np.zeros(3) if timings else None
         self._ck(self._L.moses_autotune(self._h, int(reps), C.byref(t), _p(ms)))
+        self._tile = t.value
         return t.value, (None if ms is None else [float(x) for x in ms])
 
     def step_dt(self, dt: float, n: int = 1) -> float:
