@@ -71,6 +71,7 @@ GPU_PINS = [P.pin_conservation_closed, P.pin_lake_flat, P.pin_lake_plane, P.pin_
             P.pin_fluid_friction, P.pin_cu_upwind_dependence, P.pin_cu_conservation_and_ritter, P.pin_cu_rotation,
             P.pin_weno_linear_exact, P.pin_weno_rk3_dam_break, P.pin_weno_smooth_order, P.pin_rk3_drag_factor,
             P.pin_weno_rk3_budgets_and_rotation,
+            P.pin_lake_curved_bed_residual_converges,
             P.pin_earth_pressure_regimes, P.pin_earth_pressure_fluid_unaffected, P.pin_earth_pressure_wave_speed,
             P.pin_savage_hutter_earth_pressure, P.pin_rotation_earth_pressure]
 
