@@ -58,6 +58,35 @@ def test_stage_adjoint_dot_product(nx, ny, bc, inflow, k_mode):
     assert abs(fd - ad) <= 1e-7 * abs(fd), (fd, ad)
 
 
+@pytest.mark.parametrize("k_mode", [0, 1])
+@pytest.mark.parametrize("nx,ny,bc,inflow", [(45, 37, (0, 0, 0, 0), False), (70, 20, (1, 1, 1, 1), False),
+                                             (60, 30, (1, 1, 1, 1), True)])
+def test_stage_adjoint_dot_product_richardson(nx, ny, bc, inflow, k_mode):
+    """The dot-product test against a sharper difference quotient: central
+    differences at two step sizes extrapolated (Richardson, error O(e^4)), so
+    that the bar is set by the FP64 rounding of the forward stage (relative
+    noise about 1e-16 / e) rather than by the truncation error: 1e-9."""
+    g = _stage_sim(nx, ny, bc, inflow, moses.FP64, seed=3, k_mode=k_mode)
+    U = g.get_conserved()
+    rng = np.random.default_rng(202)
+    lam = rng.standard_normal(U.shape)
+    v = rng.standard_normal(U.shape) * np.abs(U).reshape(6, -1).max(axis=1)[:, None, None]
+    t, dt = 30.0, 0.01
+    li, _ = g.stage_adjoint(t, dt, lam)
+    ad = (li * v).sum()
+
+    def quotient(eps):
+        g.set_conserved(U + eps * v)
+        Sp = g.stage(t, dt)
+        g.set_conserved(U - eps * v)
+        Sm = g.stage(t, dt)
+        return (lam * (Sp - Sm)).sum() / (2 * eps)
+
+    d1, d2 = quotient(2e-6), quotient(1e-6)
+    rich = (4 * d2 - d1) / 3
+    assert abs(rich - ad) <= 1e-9 * abs(rich), (rich, ad, d1, d2)
+
+
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
 def test_stage_adjoint_dot_product_sparse(bc):
     """Wet blobs on tile edges in a dry domain: the dry tiles skip their face
