@@ -1792,19 +1792,7 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
     const int idx = blockIdx.x * kFlagThreads + tid;  // tile (idx % gx, idx / gx)
     const bool mine = idx < gx * gy;
     const unsigned char known = (a.zk && mine) ? a.zk[idx] : 0;
-    if (tid == 0) {
-        s_n = 0u;
-        const Ctl *ctl = a.ctl;
-        if (a.stage == 1) {
-            const bool fixed = a.fix != 0;
-            const double t_now = fixed ? a.fix_t : ctl->t;
-            const double dt = fixed ? a.fix_dt : dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
-            s_tg = t_now + dt;
-            if (blockIdx.x == 0) first_stage_clock(a, t_now, dt);
-        } else {
-            s_tg = ctl->t + (a.rk3 == 2 ? 0.5 * ctl->dt : ctl->dt);
-        }
-    }
+    if (tid == 0) s_n = 0u;
     __syncthreads();
     if (mine) {
         const int bx = idx % gx, ty = idx / gx;
@@ -1830,9 +1818,27 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
         if (a.mb_out && !w) a.mb_out[idx] = 0;
         if (!keep_tile(a, w, inf, idx, known)) s_list[atomicAdd(&s_n, 1u)] = idx;
     }
+    // the step's clock (the control block's reads stay off the tiles' path:
+    // only a CTA with tiles to zero-write, and the first CTA of a first
+    // stage, wait for them)
+    const bool clock = a.stage == 1 && blockIdx.x == 0;
+    __syncthreads();
+    const int nrows = (int)s_n * TY;
+    if (tid == 0 && (nrows > 0 || clock)) {
+        const Ctl *ctl = a.ctl;
+        if (a.stage == 1) {
+            const bool fixed = a.fix != 0;
+            const double t_now = fixed ? a.fix_t : ctl->t;
+            const double dt = fixed ? a.fix_dt : dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
+            s_tg = t_now + dt;
+            if (clock) first_stage_clock(a, t_now, dt);
+        } else {
+            s_tg = ctl->t + (a.rk3 == 2 ? 0.5 * ctl->dt : ctl->dt);
+        }
+    }
+    if (nrows == 0) return;  // CTA-uniform
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5;
-    const int nrows = (int)s_n * TY;
     const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     for (int r = warp; r < nrows; r += kFlagThreads / 32) {
         const int t = s_list[r / TY];
