@@ -77,8 +77,8 @@ N_WINDOWS = 4        # timed windows, at the start of each quarter of the event
 # first 12).
 TRAFFIC_PER_CELL_STAGE = {
     # profiles/stage_kernel_list_all_wet_2048.md
-    ("f64", "fd12e4235c74"): 329.56,
-    ("f32", "fd12e4235c74"): 75.93,
+    ("f64", "dc68d2e04ef7"): 330.14,
+    ("f32", "dc68d2e04ef7"): 74.41,
 }
 
 

@@ -182,10 +182,10 @@ int moses_set_tile(moses_sim *s, int tile);
  * from the per-tile mass bits, dry tiles that hold the zero state left
  * unwritten), with each tile shape (CUDA events on the simulation's stream,
  * after one untimed stage each that classifies from the data and sets those
- * records up; the state, time and budgets are not changed), selects the
- * fastest and
- * returns it in *tile_out (may be NULL).  ms_out (may be NULL) receives the
- * mean time per launch of each tile [ms], indexed by MOSES_TILE_*.  The choice
+ * records up; two rounds over the shapes; the state, time and budgets are
+ * not changed), selects the shape with the fastest launch and returns it in
+ * *tile_out (may be NULL).  ms_out (may be NULL) receives the fastest launch
+ * of each tile [ms], indexed by MOSES_TILE_*.  The choice
  * is cached per process by (device, SM count, precision, nx, ny): a later call
  * with ms_out == NULL on a simulation with the same key takes the cached tile
  * without timing.  Errors: EINVAL, ESTATE (no state), ECUDA. */

@@ -810,34 +810,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     __shared__ double s_dt, s_tg, s_bwf;
     __shared__ T s_dtT;
 
-    // the step's time and time step, once per CTA
-    if (tid == 0) {
-        double t_now, dt;
-        if (a.debug_stage) {
-            t_now = a.dbg_t;
-            dt = a.dbg_dt;
-        } else if (a.stage == 1 && a.fix) {
-            t_now = a.fix_t;
-            dt = a.fix_dt;
-        } else if (a.stage == 1) {
-            t_now = ctl->t;
-            dt = dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
-        } else {
-            t_now = ctl->t;
-            dt = ctl->dt;
-        }
-        s_dt = dt;
-        s_dtT = (T)dt;
-        // ghosts at the time of this stage's output (the second RK3 stage: t + dt/2)
-        s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
-        // budget weight of this stage relative to the two-step Euler's 1/2
-        s_bwf = a.rk3 ? 2.0 * a.rk3_bw : 1.0;
-        // (thread 0 alone resets the accumulators it alone reads at the end,
-        // so a CTA can run the next tile without a barrier in between)
-        acc_n = 0;
-        acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
-    }
-
     // ---- stage the tile + 2-cell halo of the six state planes -----------
     // (asynchronous copies: every element of the thread in flight at once).
     // Each thread takes its own cell, then one cell of the halo if any, so
@@ -910,6 +882,35 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         copy_planes(1, 2, 4, 5, 4);
         copy_slope_tile();
     }
+    // the step's time and time step, once per CTA (after the copies are
+    // issued: thread 0's control-block reads then overlap them)
+    if (tid == 0) {
+        double t_now, dt;
+        if (a.debug_stage) {
+            t_now = a.dbg_t;
+            dt = a.dbg_dt;
+        } else if (a.stage == 1 && a.fix) {
+            t_now = a.fix_t;
+            dt = a.fix_dt;
+        } else if (a.stage == 1) {
+            t_now = ctl->t;
+            dt = dt_from(ctl, a.ph, __longlong_as_double((long long)ctl->amax));
+        } else {
+            t_now = ctl->t;
+            dt = ctl->dt;
+        }
+        s_dt = dt;
+        s_dtT = (T)dt;
+        // ghosts at the time of this stage's output (the second RK3 stage: t + dt/2)
+        s_tg = t_now + (a.rk3 == 2 ? 0.5 * dt : dt);
+        // budget weight of this stage relative to the two-step Euler's 1/2
+        s_bwf = a.rk3 ? 2.0 * a.rk3_bw : 1.0;
+        // (thread 0 alone resets the accumulators it alone reads at the end,
+        // so a CTA can run the next tile without a barrier in between)
+        acc_n = 0;
+        acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+    }
+
     // Wet/dry masking: where no cell of the staged tile and halo holds mass
     // (U1 = U4 = 0; in the FP32 form also the tile's mass remainders, and in
     // a combining stage the tile's masses at U^n), every face flux, source
