@@ -21,6 +21,7 @@
 
 #include "../../include/moses.h"
 #include "moses_dev.cuh"
+#include "batch.cuh"
 #include "stage.cuh"
 
 using namespace moses;

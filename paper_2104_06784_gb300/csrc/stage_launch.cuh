@@ -1,10 +1,12 @@
-// stage_launch.cuh -- launchers of the templated stage kernels (stage.cuh),
+// stage_launch.cuh -- launchers of the templated stage kernels (stage.cuh,
+// and the ensemble kernel of batch.cuh),
 // shared by the two precision forms; stage_f64.cu and stage_f32.cu each
 // instantiate them for one element type (one translation unit per type, so
 // that the two compile in parallel).
 #pragma once
 #include <cuda_runtime.h>
 
+#include "batch.cuh"
 #include "stage.cuh"
 
 namespace moses {
