@@ -622,7 +622,7 @@ def main():
                     help="measure one precision form (K steps from the start), or only the adjoint")
     ap.add_argument("--wet-layer", type=float, default=0.0,
                     help="add a mixture layer of this depth [m] on every cell (all tiles wet; for profiling)")
-    ap.add_argument("--tile", choices=["auto", "32x8", "32x4", "32x16"], default="auto",
+    ap.add_argument("--tile", choices=["auto", "32x8", "32x4", "32x16", "32x4-2t"], default="auto",
                     help="stage tile shape: autotuned (default) or pinned")
     ap.add_argument("--from-step", type=int, default=0,
                     help="--only f64 / f32: advance this many steps of the event first (untimed)")
@@ -703,12 +703,12 @@ def main():
         if args.tile == "auto":
             tile, tile_ms = sim.autotune()  # the project's tile autotuner
             tiles[name] = {"tile": moses.Sim.TILES[tile],
-                           "ms_per_launch": {moses.Sim.TILES[t]: tile_ms[t] for t in range(3)}}
+                           "ms_per_launch": {moses.Sim.TILES[t]: tile_ms[t] for t in range(len(tile_ms))}}
         else:
             tile = {v: k for k, v in moses.Sim.TILES.items()}[args.tile]
             sim.set_tile(tile)
             tiles[name] = {"tile": args.tile, "pinned": True}
-        ts = tuple(int(x) for x in tiles[name]["tile"].split("x"))
+        ts = moses.Sim.TILE_SHAPES[tile]
         ckpts, event = run_event(sim, torch, nsteps=args.event_steps, nwin=nwin, tile=ts)
         if dist is not None:
             dist.barrier()

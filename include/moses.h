@@ -169,12 +169,17 @@ int moses_step_timed(moses_sim *s, int nsteps, double *t_out, double *stage_ms);
 
 /* Tile shape of the stage kernel (not in the paper, which gives none):
  * MOSES_TILE_32x8 (the default), MOSES_TILE_32x4 or MOSES_TILE_32x16 cells
- * per CTA.  Every tile computes the same values (the state after a step is
+ * per CTA, or MOSES_TILE_32x4_2T: 32 x 4 cells with two threads per cell on
+ * the listed wet tiles of the plain form (one thread takes the cell's x-face,
+ * the other its y-face; the cell update runs on the first of the two), for
+ * steps with few wet tiles per SM, whose time is the latency of one tile.
+ * Every tile computes the same values (the state after a step is
  * bit-identical); only the speed differs.  Errors: EINVAL for another value. */
 #define MOSES_TILE_32x8 0
 #define MOSES_TILE_32x4 1
 #define MOSES_TILE_32x16 2
-#define MOSES_NTILES 3
+#define MOSES_TILE_32x4_2T 3
+#define MOSES_NTILES 4
 int moses_set_tile(moses_sim *s, int tile);
 
 /* Autotuner: times `reps` (>= 1; 0 = 5) first stages of a step from the

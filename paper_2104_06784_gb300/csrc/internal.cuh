@@ -49,6 +49,9 @@ struct moses_sim {
     std::string err;
 };
 
+// rows of the tiles of a MOSES_TILE_* shape
+inline int tile_rows(int tile) { return tile == 1 || tile == 3 ? 4 : tile == 2 ? 16 : 8; }
+
 extern std::string g_create_err;
 
 // ---------------------------------------------------------------------------

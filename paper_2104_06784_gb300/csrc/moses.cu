@@ -1301,7 +1301,7 @@ int rows_replaced(moses_sim *s, int j0, int j1)
     StageArgs<T> a = base_args<T>(s);
     fill_ghosts_rows_kernel<T><<<grid_for((long long)s->nx * (j1 - j0)), 256, 0, s->stream>>>(a, (T *)s->U, j0, j1);
     CK(cudaGetLastError());
-    const int TY = s->tile == 1 ? 4 : s->tile == 2 ? 16 : 8;
+    const int TY = tile_rows(s->tile);
     const int gx = (s->nx + 31) / 32, ty0 = j0 / TY, ty1 = (j1 - 1) / TY + 1;
     CK(cudaMemsetAsync(s->zk + (size_t)ty0 * gx, 0, (size_t)(ty1 - ty0) * gx, s->stream));  // U's flags
     switch (TY) {

@@ -766,11 +766,17 @@ __device__ __forceinline__ bool wet_from_bits(const unsigned short *mb, int bx, 
 // KM: the earth-pressure form (k_mode 1, reading R10): each cell of the staged
 // tile and halo gets its solid velocity (NaN where the cell carries no
 // solid), from which each side of a face takes its cell's K_act or K_pass.
+// P2: two threads per cell (2 TX TY threads): in the face phase the first TX TY
+// take the x-faces, the others the y-faces, so that every SM sub-partition
+// runs two warps of faces; the staging and the cell update stay on the first
+// TX TY.  A step with about one wet tile per SM is bound by the latency of
+// that tile's FP64 chain, which the second warp hides.
 template <typename T, int TX, int TY, bool REC = false, bool VIS = false, bool CU = false, bool WENO = false,
-          bool KM = false>
+          bool KM = false, bool P2 = false>
 __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, const int by, const unsigned int nb)
 {
     constexpr int NT = TX * TY;
+    constexpr int NTH = P2 ? 2 * NT : NT;  // threads of the CTA
     constexpr int SW = TX + 4, SH = TY + 4, SP = SW * SH;
     constexpr int NSX = (TX + 2) * TY, NSY = TX * (TY + 2);  // cells with x- / y-slopes
     constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);  // x- / y-faces
@@ -801,6 +807,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     __shared__ bool last_block;
 
     const int tid = threadIdx.x;
+    const bool cell_thread = !P2 || tid < NT;  // a thread with a cell of its own
     const int x0 = bx * TX, y0 = by * TY;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;
@@ -820,7 +827,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     int eo[NE];        // shared-memory offset of each staged cell (-1: none)
     long long eg[NE];  // its global index
     bool eok[NE];      // inside the ghost-extended grid (else zero-filled)
-    {
+    if (!cell_thread) {
+#pragma unroll
+        for (int e = 0; e < NE; e++) eo[e] = -1;
+    } else {
         const auto entry = [&](int e, int tx, int ty) {  // tile coordinates, -2 .. TX+1 / TY+1
             const int gi = x0 + tx, gj = y0 + ty;
             eok[e] = gi < nx + 2 && gj < ny + 2;
@@ -854,6 +864,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     };
     // FP32 (and viscous) form: bed slopes of the tile + 1-cell halo
     const auto copy_slope_tile = [&]() {
+        if (!cell_thread) return;
         if constexpr (SL) {
             // slope tile: cells x0-1 .. x0+TX, rows y0-1 .. y0+TY
             const auto copy_slopes = [&](int tx, int ty) {  // tile coordinates, -1 .. TX / TY
@@ -921,7 +932,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     // mass.  Each thread tests its own cell's remainders and U^n (loaded while
     // the copies are in flight), then the cells it copied itself.
     bool has_mass = listed;
-    if (!listed) {
+    if (!listed && cell_thread) {
         const int ci = x0 + tid % TX, cj = y0 + tid / TX;
         if (ci < nx && cj < ny) {
             const long long g = cell_index(ci, cj, pitch);
@@ -952,7 +963,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         if constexpr (VIS) {
             // fluid velocity of every cell of the slope tile (0 where the fluid is
             // dry), with the same dry threshold as the cell update
-            for (int q = tid; q < NB; q += NT) {
+            for (int q = tid; q < NB; q += NTH) {
                 const int ly = q / BW, lx = q - ly * BW;
                 const int gi = x0 - 1 + lx, gj = y0 - 1 + ly;
                 const int o = (ly + 1) * SW + lx + 1;
@@ -975,7 +986,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             // solid velocity of every staged cell where it carries solid
             // (U1 > J h_dry), by IEEE division as the oracle takes it; NaN
             // elsewhere, so that every comparison with it fails
-            for (int q = tid; q < SP; q += NT) {
+            for (int q = tid; q < SP; q += NTH) {
                 const int gi = x0 + q % SW - 2, gj = y0 + q / SW - 2;
                 T vx = T(NAN), vy = T(NAN);
                 if (gi < nx + 2 && gj < ny + 2) {
@@ -1002,16 +1013,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         // rows -1 and TY), so that only the halo needs index arithmetic.
         // (The WENO form reconstructs each face value in the face loop instead.)
         if constexpr (!WENO) {
-            const int lx = tid % TX, ly = tid / TX;
-            const T *p = sU + (ly + 2) * SW + lx + 2;
+            if (cell_thread) {
+                const int lx = tid % TX, ly = tid / TX;
+                const T *p = sU + (ly + 2) * SW + lx + 2;
     #pragma unroll
-            for (int c = 0; c < 6; c++) {
-                const T *q = p + c * SP;
-                sSx[c * NSX + ly * (TX + 2) + lx + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
-                sSy[c * NSY + (ly + 1) * TX + lx] = minmod(q[0] - q[-SW], q[SW] - q[0]);
+                for (int c = 0; c < 6; c++) {
+                    const T *q = p + c * SP;
+                    sSx[c * NSX + ly * (TX + 2) + lx + 1] = minmod(q[0] - q[-1], q[1] - q[0]);
+                    sSy[c * NSY + (ly + 1) * TX + lx] = minmod(q[0] - q[-SW], q[SW] - q[0]);
+                }
             }
             constexpr int NHX = 2 * TY, NHY = 2 * TX, NH1 = NHX + NHY;
-            for (int e = tid; e < 6 * NH1; e += NT) {
+            for (int e = tid; e < 6 * NH1; e += NTH) {
                 const int c = e / NH1;
                 int r = e - c * NH1;
                 if (r < NHY) {  // y-slopes of rows -1 (r < TX) and TY
@@ -1148,21 +1161,34 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
                 atomicAdd(&acc[1], w * (double)H[3]);
             }
         };
-        static_assert(NT >= 32 + TX && TY <= 32, "face assignment needs warps 0 and 1");
-        x_face(tid % TX + 1, tid / TX);
-        y_face(tid % TX, tid / TX + 1);
-        if (tid < TY) x_face(0, tid);
-        else if (tid >= 32 && tid < 32 + TX) y_face(tid - 32, 0);
+        if constexpr (P2) {
+            // the x-faces on the first NT threads, the y-faces on the others;
+            // the lower faces of row 0 on warp 2 and the left faces of column 0
+            // on the last warp (warps w and w + 4 share a sub-partition: the
+            // extra rounds land on two different ones)
+            static_assert(TX == 32 && NT >= 96 && TY <= 32, "face assignment of the two-thread form");
+            if (tid < NT) x_face(tid % TX + 1, tid / TX);
+            else y_face((tid - NT) % TX, (tid - NT) / TX + 1);
+            if (tid >= 64 && tid < 64 + TX) y_face(tid - 64, 0);
+            else if (tid >= NTH - 32 && tid < NTH - 32 + TY) x_face(0, tid - (NTH - 32));
+        } else {
+            static_assert(NT >= 32 + TX && TY <= 32, "face assignment needs warps 0 and 1");
+            x_face(tid % TX + 1, tid / TX);
+            y_face(tid % TX, tid / TX + 1);
+            if (tid < TY) x_face(0, tid);
+            else if (tid >= 32 && tid < 32 + TX) y_face(tid - 32, 0);
+        }
         __syncthreads();
     }
 
     // ---- cell update ------------------------------------------------------
     const int lx = tid % TX, ly = tid / TX;
     const int i = x0 + lx, j = y0 + ly;
+    const bool in_grid = cell_thread && i < nx && j < ny;
     T speed = T(0);
     bool bad = false;
     bool mass = false;  // the cell's output holds mass (mass bits)
-    if (!wet && i < nx && j < ny) {
+    if (!wet && in_grid) {
         const long long g = cell_index(i, j, pitch);
         const T z[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         store6(a.Uout, plane, g, z);
@@ -1172,7 +1198,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
             a.Rout[plane + g] = 0.0f;
         }
         if (!a.debug_stage) write_ghosts(a.Uout, geo, a, i, j, z, s_tg);
-    } else if (i < nx && j < ny) {
+    } else if (in_grid) {
         const long long g = cell_index(i, j, pitch);
         const int os = (ly + 2) * SW + lx + 2;
         // the cell's geometry: FP32 rebuilt from the slope tile, FP64 read
@@ -1429,7 +1455,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
     __shared__ unsigned int s_mrow[TY];  // ballots of the output's mass by row (TX == 32: a warp per row)
     if (TX == 32 && a.mb_out) {
         const unsigned int row = __ballot_sync(0xffffffffu, mass);
-        if ((tid & 31) == 0) s_mrow[tid >> 5] = row;
+        if ((tid & 31) == 0 && cell_thread) s_mrow[tid >> 5] = row;
     }
 
     // ---- CTA reductions ---------------------------------------------------
@@ -1440,7 +1466,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs<T> &a, const int bx, 
         if (nonfinite(speed)) atomicOr(&ctl->status, (int)STATUS_NONFINITE);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) speed = maxnn(speed, __shfl_xor_sync(0xffffffffu, speed, o));
-        if ((tid & 31) == 0) red[tid >> 5] = speed;
+        if ((tid & 31) == 0 && cell_thread) red[tid >> 5] = speed;
     }
     __syncthreads();
     if (tid == 0) {
@@ -1860,8 +1886,9 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
 // entries in turn; the last CTA to finish empties the list and, after the
 // step's last stage, ends the step.
 // FP32: three 256-thread CTAs per SM (at most 85 registers); FP64: two
-template <typename T, int TX, int TY, bool REC = false, bool KM = false>
-__global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * TY))
+// P2: two threads per cell (stage_tile), 2 TX TY threads
+template <typename T, int TX, int TY, bool REC = false, bool KM = false, bool P2 = false>
+__global__ void __launch_bounds__(TX *TY * (P2 ? 2 : 1), (sizeof(T) == 4 ? 768 : 512) / (TX * TY * (P2 ? 2 : 1)))
     stage_kernel_list(const StageArgs<T> a, const int gx)
 {
     __shared__ bool last;
@@ -1872,7 +1899,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     // previous tile no longer reads
     for (unsigned int w = blockIdx.x; w < n; w += gridDim.x) {
         const int t = a.wl[w];
-        stage_tile<T, TX, TY, REC, false, false, false, KM>(a, t % gx, t / gx, 0u);
+        stage_tile<T, TX, TY, REC, false, false, false, KM, P2>(a, t % gx, t / gx, 0u);
     }
     if (threadIdx.x == 0) {
         __threadfence();

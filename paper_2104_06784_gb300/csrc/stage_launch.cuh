@@ -34,10 +34,11 @@ int launch_tile(const StageArgs<T> &a, cudaStream_t st)
 // The stepping launches of the plain form: classify_kernel over every tile
 // (classify_flags_kernel where the input's mass bits are known, and in a
 // combining stage), then stage_kernel_list on a grid of resident CTAs over
-// the listed tiles.
-template <typename T, int TX, int TY, bool REC = false, bool KM = false>
+// the listed tiles (P2: two threads per cell).
+template <typename T, int TX, int TY, bool REC = false, bool KM = false, bool P2 = false>
 int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
 {
+    constexpr int NTH = TX * TY * (P2 ? 2 : 1);
     constexpr size_t smem = stage_smem_bytes<T, TX, TY, false, KM>();
     static int resident[64] = {};
     int dev = 0;
@@ -45,9 +46,9 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     if (dev < 0 || dev >= 64) return -1;
     if (!resident[dev]) {
         int per_sm = 0, n_sm = 0;
-        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY, REC, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(stage_kernel_list<T, TX, TY, REC, KM, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY, REC, KM>, TX * TY, smem) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel_list<T, TX, TY, REC, KM, P2>, NTH, smem) !=
                 cudaSuccess ||
             cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1 || n_sm < 1)
             return -1;
@@ -61,7 +62,7 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     } else {
         classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
     }
-    stage_kernel_list<T, TX, TY, REC, KM><<<resident[dev], TX * TY, smem, st>>>(a, gx);
+    stage_kernel_list<T, TX, TY, REC, KM, P2><<<resident[dev], NTH, smem, st>>>(a, gx);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -75,7 +76,9 @@ void no_mass_bits(StageArgs<T> &a)
     a.mb_ok = 0;
 }
 
-// tile 0: 32 x 8 cells (256 threads); tile 1: 32 x 4; tile 2: 32 x 16
+// tile 0: 32 x 8 cells (256 threads); tile 1: 32 x 4; tile 2: 32 x 16; tile 3:
+// 32 x 4 with two threads per cell on the listed tiles (the launches that test
+// each tile themselves take it as 32 x 4)
 template <typename T>
 int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
 {
@@ -85,6 +88,7 @@ int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
             switch (tile) {
             case 1: return launch_tile_list<T, 32, 4, false, true>(a_in, st);
             case 2: return launch_tile_list<T, 32, 16, false, true>(a_in, st);
+            case 3: return launch_tile_list<T, 32, 4, false, true, true>(a_in, st);
             default: return launch_tile_list<T, 32, 8, false, true>(a_in, st);
             }
         }
@@ -93,7 +97,8 @@ int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
         a.wl_n = nullptr;
         no_mass_bits(a);
         switch (tile) {
-        case 1: return launch_tile<T, 32, 4, false, false, false, false, true>(a, st);
+        case 1:
+        case 3: return launch_tile<T, 32, 4, false, false, false, false, true>(a, st);
         case 2: return launch_tile<T, 32, 16, false, false, false, false, true>(a, st);
         default: return launch_tile<T, 32, 8, false, false, false, false, true>(a, st);
         }
@@ -104,6 +109,7 @@ int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
         switch (tile) {
         case 1: return launch_tile_list<T, 32, 4>(a_in, st);
         case 2: return launch_tile_list<T, 32, 16>(a_in, st);
+        case 3: return launch_tile_list<T, 32, 4, false, false, true>(a_in, st);
         default: return launch_tile_list<T, 32, 8>(a_in, st);
         }
     }
@@ -122,7 +128,8 @@ int launch_stage_impl(const StageArgs<T> &a_in, int tile, void *stream)
         return vis ? launch_tile<T, 32, 8, false, true, true>(a, st) : launch_tile<T, 32, 8, false, false, true>(a, st);
     if (vis) return launch_tile<T, 32, 8, false, true>(a, st);
     switch (tile) {
-    case 1: return launch_tile<T, 32, 4>(a, st);
+    case 1:
+    case 3: return launch_tile<T, 32, 4>(a, st);
     case 2: return launch_tile<T, 32, 16>(a, st);
     default: return launch_tile<T, 32, 8>(a, st);
     }

@@ -226,7 +226,8 @@ class Sim:
         self._ck(self._L.moses_debug_poison(self._h))
 
     # tile shape of the stage kernel -------------------------------------------
-    TILES = {0: "32x8", 1: "32x4", 2: "32x16"}
+    TILES = {0: "32x8", 1: "32x4", 2: "32x16", 3: "32x4-2t"}  # 32x4-2t: two threads per cell
+    TILE_SHAPES = {0: (32, 8), 1: (32, 4), 2: (32, 16), 3: (32, 4)}  # cells of each tile
 
     def set_tile(self, tile: int):
         self._ck(self._L.moses_set_tile(self._h, int(tile)))
@@ -241,7 +242,7 @@ class Sim:
         (tile, [ms per launch for each tile]) (timings: None when the cached
         choice was taken with timings=False)."""
         t = C.c_int()
-        ms = np.zeros(3) if timings else None
+        ms = np.zeros(len(self.TILES)) if timings else None
         self._ck(self._L.moses_autotune(self._h, int(reps), C.byref(t), _p(ms)))
         self._tile = t.value
         return t.value, (None if ms is None else [float(x) for x in ms])

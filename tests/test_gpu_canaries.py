@@ -27,7 +27,7 @@ def test_steps_ignore_padding(precision, case):
     a = moses.from_config(cfg, precision=precision)
     b = moses.from_config(cfg, precision=precision)
     b.debug_poison()
-    for tile in (0, 1, 2):
+    for tile in (0, 1, 2, 3):
         a.set_tile(tile)
         b.set_tile(tile)
         a.step(15)

@@ -60,7 +60,7 @@ def test_strips_equal_the_whole_domain_bit_for_bit(precision, world, bc):
         assert rel_maxnorm(_own(strips), o.get_U()) < TOL64
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 def test_every_tile_shape(tile):
     cfg = _spectral()
     strips = _strips(cfg, 3, moses.FP64, tile)

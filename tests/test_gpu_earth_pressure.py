@@ -46,7 +46,7 @@ def test_stage_parity_fp64(nx, ny, bc):
         assert rel_maxnorm(o0.stage(0.0, 0.01), o.stage(0.0, 0.01)) > 1e-6
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 def test_stage_parity_every_tile(tile):
     cfg = _random_case(70, 37, (0, 1, 1, 0), seed=5)
     g, o = both(cfg)
@@ -54,7 +54,7 @@ def test_stage_parity_every_tile(tile):
     assert rel_maxnorm(g.stage(1.0, 0.02), o.stage(1.0, 0.02)) < TOL64
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 def test_masked_steps_fp64(tile):
     """moses_step (wet/dry classification and the listed tiles) with the
     earth-pressure form: a pile in a mostly dry domain, 60 steps."""

@@ -566,7 +566,7 @@ def _sparse_cfg(nx, ny, bc):
                 phi_s=np.zeros((ny, nx)))
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
 def test_sparse_wet_cells_stage_and_steps(tile, bc):
     """FP64: one stage and five steps from isolated wet cells on tile edges and
@@ -598,7 +598,7 @@ def test_sparse_wet_cells_stage_and_steps(tile, bc):
 
 
 @pytest.mark.parametrize("nx,ny", [(1, 1), (1, 17), (23, 1), (33, 9), (5, 70), (77, 53), (130, 35)])
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 def test_masked_steps_on_ragged_grids(nx, ny, tile):
     """Steps through moses_step (the classification over 32 x 16-cell strips,
     its bulk row copies clipped at the grid's edge, and the listed-tile
@@ -637,7 +637,7 @@ def test_sparse_wet_cells_fp32_tiles_agree(bc):
     cfg = _sparse_cfg(nx, ny, bc)
     U = _sparse_state(nx, ny, seed=11 + bc[0])
     outs = []
-    for tile in (0, 1, 2):
+    for tile in (0, 1, 2, 3):
         with moses.from_config(cfg, precision=moses.FP32) as g:
             g.set_tile(tile)
             g.set_conserved(U)
@@ -652,7 +652,7 @@ def test_sparse_wet_cells_fp32_tiles_agree(bc):
 
 
 @pytest.mark.parametrize("prec", [moses.FP64, moses.FP32])
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
 def test_known_zero_tiles_match_written_tiles(prec, tile):
     """Known-zero tile flags: a run whose dry tiles are written only when
     their output buffer does not hold the zero state yet gives the state, bit
@@ -774,18 +774,18 @@ def test_tiles_give_identical_states_and_autotune_picks_one(precision):
     ref = moses.from_config(cfg, precision=precision)
     ref.step(25)
     U0 = ref.get_conserved()
-    for tile in (1, 2):
+    for tile in (1, 2, 3):
         s = moses.from_config(cfg, precision=precision)
         s.set_tile(tile)
         s.step(25)
         assert np.array_equal(s.get_conserved(), U0), tile
     s = moses.from_config(cfg, precision=precision)
     tile, ms = s.autotune(reps=3)
-    assert tile in (0, 1, 2) and all(m > 0 for m in ms) and ms[tile] == min(ms)
+    assert tile in (0, 1, 2, 3) and len(ms) == 4 and all(m > 0 for m in ms) and ms[tile] == min(ms)
     s.step(25)
     assert np.array_equal(s.get_conserved(), U0)
     # a second simulation of the same size takes the cached choice
     s2 = moses.from_config(cfg, precision=precision)
     assert s2.autotune(timings=False) == (tile, None)
     with pytest.raises(moses.MosesError):
-        s2.set_tile(3)
+        s2.set_tile(4)
