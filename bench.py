@@ -726,6 +726,12 @@ def main():
 
     # the kernels' own rate: every tile wet
     dense = measure_dense(cfg, K, Wm, torch, fp64_tflops, pk["hbm_gbs"], h)
+    # the flux phase in double-float arithmetic (pairs of FP32 numbers, not
+    # IEEE FP64) against FP64, on 4M synthetic faces: an evaluation, not a
+    # stepping form
+    dfe = moses.flux_eval(1 << 22, 10)
+    dfe["speedup"] = dfe["df_gfaces_per_s"] / dfe["f64_gfaces_per_s"] if dfe["f64_gfaces_per_s"] > 0 else None
+    dfe["note"] = "central face flux (face_flux2) only; double-float is not IEEE FP64"
     d64, d32 = dense["f64"], dense["f32"]
     roof64 = {"bound": "alu", "achieved": d64["alu"]["achieved"], "peak": fp64_tflops, "unit": "TFLOP/s",
               "frac": d64["alu"]["achieved"] / fp64_tflops, "traffic": d64["traffic_per_launch"],
@@ -796,6 +802,7 @@ def main():
                 "event": f32["event"]},
         "dense": dense,
         "fp64_fma_tflops": fp64_tflops,
+        "double_float_flux": dfe,
         "arc_plane": arc,
         "inflow": infl,
         "ensemble": ens,

@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libmoses.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-SOURCES = ["moses.cu", "stage_f64.cu", "stage_f32.cu", "adjoint.cu"]
+SOURCES = ["moses.cu", "stage_f64.cu", "stage_f32.cu", "adjoint.cu", "flux_eval.cu"]
 
 
 def nvcc() -> str:

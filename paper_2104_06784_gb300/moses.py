@@ -105,6 +105,7 @@ SIGNATURES = [
     ("moses_debug_poison", C.c_int, [_vp]),
     ("moses_debug_math", C.c_int, [_dp, C.c_int, _dp]),
     ("moses_debug_fp64_rate", C.c_int, [C.c_int, _dp]),
+    ("moses_debug_flux_eval", C.c_int, [C.c_longlong, C.c_int, _dp]),
 ]
 
 
@@ -427,6 +428,19 @@ def fp64_rate(reps: int = 5) -> float:
     if rc != 0:
         raise MosesError(rc, lib().moses_last_error(None).decode())
     return t.value
+
+
+def flux_eval(n: int = 1 << 22, reps: int = 10) -> dict:
+    """The central face flux in FP64 and in double-float arithmetic (pairs of
+    FP32 numbers; not IEEE FP64) on n synthetic faces (moses_debug_flux_eval):
+    face fluxes per second of each form and the double-float fluxes' relative
+    max-norm and largest relative difference against the FP64 ones."""
+    r = np.zeros(4)
+    rc = lib().moses_debug_flux_eval(int(n), int(reps), _p(r))
+    if rc != 0:
+        raise MosesError(rc, lib().moses_last_error(None).decode())
+    return {"f64_gfaces_per_s": float(r[0]), "df_gfaces_per_s": float(r[1]),
+            "relmax_vs_f64": float(r[2]), "max_rel_vs_f64": float(r[3])}
 
 
 def version() -> str:
