@@ -77,8 +77,8 @@ N_WINDOWS = 4        # timed windows, at the start of each quarter of the event
 # first 12).
 TRAFFIC_PER_CELL_STAGE = {
     # profiles/stage_kernel_list_all_wet_2048.md
-    ("f64", "794dee897659"): 330.33,
-    ("f32", "794dee897659"): 73.88,
+    ("f64", "135442891e6c"): 330.74,
+    ("f32", "135442891e6c"): 77.01,
 }
 
 

@@ -51,8 +51,9 @@ int launch_adj_face(const AdjArgs<T> &q, cudaStream_t st, const TileBox &box)
             return -1;
         attr[dev] = true;
     }
-    adj_face_kernel<T, ATX, ATY, KM><<<box_grid(box), ATX * ATY, smB, st>>>(q);
-    return 0;
+    return launch_after(adj_face_kernel<T, ATX, ATY, KM>, box_grid(box), dim3(ATX * ATY), smB, st, q) == cudaSuccess
+               ? 0
+               : -1;
 }
 
 // the cell kernel on the tiles of `cell`, the face kernel on those of `face`
@@ -64,7 +65,7 @@ int launch_adj_stage(const AdjArgs<T> &q_in, cudaStream_t st, const TileBox &cel
     if (!cell.empty()) {
         q.bx0 = cell.x0;
         q.by0 = cell.y0;
-        adj_cell_kernel<T><<<box_grid(cell), 256, 0, st>>>(q);
+        if (launch_after(adj_cell_kernel<T>, box_grid(cell), dim3(256), 0, st, q) != cudaSuccess) return -1;
     }
     if (!face.empty()) {
         q.bx0 = face.x0;
@@ -74,7 +75,7 @@ int launch_adj_stage(const AdjArgs<T> &q_in, cudaStream_t st, const TileBox &cel
     }
     if (!q.fold_inline) {
         const int nfold = 6 * (2 * q.f.nx + 2 * q.f.ny);
-        adj_fold_kernel<T><<<(nfold + 255) / 256, 256, 0, st>>>(q);
+        if (launch_after(adj_fold_kernel<T>, dim3((nfold + 255) / 256), dim3(256), 0, st, q) != cudaSuccess) return -1;
     }
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }

@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs<T> q)
 {
     constexpr int NT = 256;
     __shared__ double red[2][NT / 32];
+    wait_prior_grid();  // launched after the kernel before it (launch_after)
     const StageArgs<T> &a = q.f;
     const int tid = threadIdx.x;
     const int tbx = q.bx0 + (int)blockIdx.x, tby = q.by0 + (int)blockIdx.y;  // the tile (AdjArgs::bx0)
@@ -770,6 +771,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
     using SM = FaceAdjSmem<T, TX, TY, KM>;
     constexpr int NT = TX * TY, SW3 = SM::SW3, SP3 = SM::SP3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    wait_prior_grid();  // launched after the kernel before it (launch_after)
     T *sU = reinterpret_cast<T *>(smem_raw);
     T *sS = sU + 6 * SP3;
     T *sLum = sS + 6 * SM::NS;
@@ -941,6 +943,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(T) == 4 ? 768 : 512) / (TX * T
 template <typename T>
 __global__ void adj_fold_kernel(const AdjArgs<T> q)
 {
+    wait_prior_grid();  // launched after the kernel before it (launch_after)
     const StageArgs<T> &a = q.f;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
     const long long plane = a.plane;

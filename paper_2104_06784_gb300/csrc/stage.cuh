@@ -40,6 +40,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "moses_dev.cuh"
 
 namespace moses {
@@ -1507,6 +1509,36 @@ __global__ void __launch_bounds__(TX *TY, 512 / (TX * TY)) stage_kernel(const St
     stage_tile<T, TX, TY, REC, VIS, CU, WENO, KM>(a, blockIdx.x, blockIdx.y, gridDim.x * gridDim.y);
 }
 
+// The stepping launches follow one another as programmatic dependent launches
+// (stage_launch.cuh): a kernel may start while the one before it finishes, and
+// waits here, before its first read of anything that kernel wrote, until it
+// has completed and its writes are visible.  Without such a launch the wait
+// returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// A launch that may begin while the stream's previous kernel finishes
+// (programmatic dependent launch): its CTAs are scheduled as the previous
+// kernel's CTAs retire, and the kernel waits (wait_prior_grid) before its first
+// read of that kernel's results.  The stepping launches chain this way, so that
+// each one's launch latency overlaps the tail of the one before.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_after(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                         Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+
 // ---- bulk copies (the TMA engine) completed on an mbarrier -------------------------
 __device__ __forceinline__ unsigned int smem_u32(const void *p) { return (unsigned int)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned int count)
@@ -1792,6 +1824,7 @@ template <typename T, int TY>
 __global__ void __launch_bounds__(32 * kStripWarps, 10) classify_kernel(const StageArgs<T> a)
 {
     __shared__ ClassifySmem<T> sm;
+    wait_prior_grid();
     classify_strip<T, TY>(a, blockIdx.x, blockIdx.y, gridDim.x, sm,
                           [&](int tx, int ty) { a.wl[atomicAdd(&a.wl_n[0], 1u)] = ty * gridDim.x + tx; });
 }
@@ -1815,6 +1848,7 @@ __global__ void __launch_bounds__(kFlagThreads) classify_flags_kernel(const Stag
     __shared__ int s_list[kFlagThreads];  // the CTA's tiles to zero-write
     __shared__ unsigned int s_n;
     __shared__ double s_tg;
+    wait_prior_grid();
     const int tid = threadIdx.x;
     const int idx = blockIdx.x * kFlagThreads + tid;  // tile (idx % gx, idx / gx)
     const bool mine = idx < gx * gy;
@@ -1892,6 +1926,7 @@ __global__ void __launch_bounds__(TX *TY * (P2 ? 2 : 1), (sizeof(T) == 4 ? 768 :
     stage_kernel_list(const StageArgs<T> a, const int gx)
 {
     __shared__ bool last;
+    wait_prior_grid();
     const unsigned int n = a.wl_n[0];
     // no barrier between tiles: after the last barrier of a tile only thread 0
     // works (its atomics), and the next tile's shared data are written before

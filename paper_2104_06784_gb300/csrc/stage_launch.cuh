@@ -58,11 +58,17 @@ int launch_tile_list(const StageArgs<T> &a, cudaStream_t st)
     const int gx = (a.nx + TX - 1) / TX;
     if (a.mb_ok || (a.tw_prev && a.stage == 2)) {  // from the input's mass bits, or the flags of the stage before
         const int gy = (a.ny + TY - 1) / TY;
-        classify_flags_kernel<T, TY><<<(gx * gy + kFlagThreads - 1) / kFlagThreads, kFlagThreads, 0, st>>>(a, gx, gy);
+        if (launch_after(classify_flags_kernel<T, TY>, dim3((gx * gy + kFlagThreads - 1) / kFlagThreads),
+                         dim3(kFlagThreads), 0, st, a, gx, gy) != cudaSuccess)
+            return -1;
     } else {
-        classify_kernel<T, TY><<<dim3(gx, (a.ny + kStripRows - 1) / kStripRows), 32 * kStripWarps, 0, st>>>(a);
+        if (launch_after(classify_kernel<T, TY>, dim3(gx, (a.ny + kStripRows - 1) / kStripRows), dim3(32 * kStripWarps),
+                         0, st, a) != cudaSuccess)
+            return -1;
     }
-    stage_kernel_list<T, TX, TY, REC, KM, P2><<<resident[dev], NTH, smem, st>>>(a, gx);
+    if (launch_after(stage_kernel_list<T, TX, TY, REC, KM, P2>, dim3(resident[dev]), dim3(NTH), smem, st, a, gx) !=
+        cudaSuccess)
+        return -1;
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
