@@ -499,12 +499,16 @@ def measure_ensemble(K, Wm, seed=0, n=256, rank=0, world=1, dist=None, device="c
 
 def measure_arc_plane(torch):
     """The arc-plane release at its stated size and length: 128 x 128 cells at
-    5 m, closed boundaries, CFL 0.5, 2000 steps, FP64 (CUDA events)."""
+    5 m, closed boundaries, CFL 0.5, 2000 steps, FP64 (CUDA events); the tile
+    shape from the autotuner on the release state (its probes change no
+    state)."""
     from paper_2104_06784_gb300 import moses, workloads as W
     cfg = W.release_config()
     with moses.from_config(cfg, precision=moses.FP64) as sim:
         sim.step(3)
         sim.set_release(cfg["h"], cfg["phi_s"])
+        sim.autotune()
+        tile = sim.tile_name()
         stream = torch.cuda.current_stream()
         torch.cuda.synchronize()
         e0, e1 = _events(torch)
@@ -517,6 +521,7 @@ def measure_arc_plane(torch):
     v0 = W.release_volume(cfg["h"], cfg["dem"], cfg["dx"])
     return {"config": "arc-plane release, 128x128 cells at 5 m, closed, CFL 0.5, 2000 steps, FP64",
             "steps": cfg["steps"], "ms": ms, "value": 128 * 128 * cfg["steps"] / (ms / 1e3), "dtype": "f64",
+            "tile": tile,
             "t_end_s": b["t"], "clamp_cells": b["clamp_cells"],
             "volume_m3": b["vol_s"] + b["vol_f"], "release_volume_m3": v0}
 
@@ -526,11 +531,18 @@ def measure_inflow(torch, precision=None):
     at 5 m, channel-and-fan DEM, triangular hydrograph (800 m^3/s at 60 s, 0 by
     300 s) at a 20-cell inlet, run to t = 600 s, FP32 state with FP64 budgets.
     Device time from CUDA events around the whole run; the mass budget closes
-    on the boundary fluxes (volume - boundary inflow - clamp volume)."""
+    on the boundary fluxes (volume - boundary inflow - clamp volume).  The
+    run starts dry, so the tile shape comes from the autotuner on a second
+    simulation of the same workload advanced to t = 120 s (untimed)."""
     from paper_2104_06784_gb300 import moses, workloads as W
     cfg = W.inflow_config()
     prec = moses.FP32 if precision is None else precision
+    with moses.from_config(cfg, precision=prec) as probe:
+        probe.run_until(120.0)
+        tile_id, _ = probe.autotune()
     with moses.from_config(cfg, precision=prec) as sim:
+        sim.set_tile(tile_id)
+        tile = sim.tile_name()
         stream = torch.cuda.current_stream()
         torch.cuda.synchronize()
         e0, e1 = _events(torch)
@@ -549,7 +561,7 @@ def measure_inflow(torch, precision=None):
     return {"config": "inflow hydrograph, 2048x1024 cells at 5 m, channel-and-fan DEM, triangular Q (800 m^3/s "
                       "peak at 60 s, 0 by 300 s), 20-cell inlet, to t = 600 s, FP32 state + FP64 budgets",
             "steps": n, "t_end_s": b["t"], "ms": ms, "value": cells * n / (ms / 1e3),
-            "dtype": "f32" if prec == moses.FP32 else "f64",
+            "dtype": "f32" if prec == moses.FP32 else "f64", "tile": tile,
             "volume_m3": vol, "boundary_inflow_m3": bnd, "clamp_volume_m3": clamp,
             "mass_drift_rel": abs(vol - bnd - clamp) / max(bnd, 1e-300),
             "hydrograph_volume_m3": float(np.trapezoid(Q, tq)) if hasattr(np, "trapezoid") else float(np.trapz(Q, tq)),
