@@ -454,19 +454,21 @@ int moses_debug_fp64_rate(int reps, double *tflops);
 /* Evaluating a double-float flux phase (not in the paper; the arithmetic is
  * NOT IEEE FP64): the stage's central flux through one face (twice the flux
  * of Sect. 2.2 with the fluxes of App. A) on n synthetic x-faces
- * (1 <= n <= 2^24; masses, velocities and pressure coefficients of a release
+ * (1 <= n <= 2^22; masses, velocities and pressure coefficients of a release
  * event, one side and phase in eight dry), computed in FP64 and in
  * double-float arithmetic (each value a pair of FP32 numbers, about 48
- * significant bits, on the FP32 pipes).  Each form runs `reps` (4..64)
+ * significant bits, on the FP32 pipes).  The inputs are made once in both
+ * types before the timed launches, which only load them, run the flux and
+ * store the results in their own type.  Each form runs `reps` (4..64)
  * dependent repetitions per face; the rate counts the difference between
  * `reps` and 2 repetitions (CUDA events, the fastest of three launches each),
- * so that the face generation and the stores cancel.  res (4 doubles, host):
+ * so that the loads and the stores cancel.  res (4 doubles, host):
  * [0] FP64 face fluxes per second over the GPU [1e9 / s], [1] the same in
  * double-float, [2] the relative max-norm of the double-float fluxes against
  * the FP64 ones (over the seven flux components, max |difference| / max |FP64
  * value|), [3] the largest relative difference of one component where the
  * FP64 value exceeds 1e-6 of its component's largest.  Uses the current
- * device; allocates and frees 112 n bytes.
+ * device; allocates and frees 472 n bytes.
  * Errors (moses_last_error(NULL)): EINVAL, ENOMEM, ECUDA. */
 int moses_debug_flux_eval(long long n, int reps, double *res);
 

@@ -62,29 +62,59 @@ __device__ void eval_face(long long k, double um[6], double up[6], FaceGeo<doubl
         }
 }
 
+// A face's inputs: um[6], up[6] and the seven geometry terms, 19 values,
+// stored as 19 planes of n elements of the arithmetic type
+constexpr int kFaceIn = 19;
+
+__device__ __forceinline__ void put(double *p, long long i, double x) { p[i] = x; }
+__device__ __forceinline__ void put(df *p, long long i, double x) { p[i] = df(x); }
 __device__ __forceinline__ double as_double(double x) { return x; }
 __device__ __forceinline__ double as_double(df x) { return x.to_double(); }
+
+// the faces' inputs in both types (untimed: the conversions to double-float
+// run here, on the FP64 pipe, and not in the timed kernels)
+__global__ void flux_eval_setup_kernel(long long n, double *in64, df *indf)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
+        double v[kFaceIn];
+        FaceGeo<double> G;
+        eval_face(k, v, v + 6, G);
+        v[12] = G.jhd;
+        v[13] = G.sn;
+        v[14] = G.st;
+        v[15] = G.fn;
+        v[16] = G.ft;
+        v[17] = G.fn2;
+        v[18] = G.hg;
+#pragma unroll
+        for (int c = 0; c < kFaceIn; c++) {
+            put(in64, c * n + k, v[c]);
+            put(indf, c * n + k, v[c]);
+        }
+    }
+}
+
 // the next repetition's input depends on this one's output, times a zero the
 // compiler cannot see: no repetition is hoisted or dropped, no value changes
 __device__ __forceinline__ void feed(double &u, double h, double zd, float) { u = ::fma(zd, h, u); }
 __device__ __forceinline__ void feed(df &u, df h, double, float zf) { u.hi = fmaf(zf, h.hi, u.hi); }
 
-// out: 7 planes of n, the fluxes of the last repetition as doubles
+// in: kFaceIn planes of n; out: 7 planes of n, the fluxes of the last
+// repetition, both in the arithmetic type (no conversion in the timed kernel)
 template <typename T>
-__global__ void __launch_bounds__(256) flux_eval_kernel(long long n, int reps, double zd, float zf, double *out)
+__global__ void __launch_bounds__(256) flux_eval_kernel(long long n, int reps, double zd, float zf, const T *in, T *out)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
-        double umd[6], upd[6];
-        FaceGeo<double> Gd;
-        eval_face(k, umd, upd, Gd);
         T um[6], up[6];
 #pragma unroll
         for (int c = 0; c < 6; c++) {
-            um[c] = T(umd[c]);
-            up[c] = T(upd[c]);
+            um[c] = in[c * n + k];
+            up[c] = in[(6 + c) * n + k];
         }
-        const FaceGeo<T> G{T(Gd.jhd), T(Gd.sn), T(Gd.st), T(Gd.fn), T(Gd.ft), T(Gd.fn2), T(Gd.hg)};
+        const FaceGeo<T> G{in[12 * n + k], in[13 * n + k], in[14 * n + k], in[15 * n + k],
+                           in[16 * n + k], in[17 * n + k], in[18 * n + k]};
         T H[7];
         for (int r = 0; r < reps; r++) {
             face_flux2<T, 0>(um, up, G, G, H);
@@ -93,8 +123,15 @@ __global__ void __launch_bounds__(256) flux_eval_kernel(long long n, int reps, d
             feed(up[0], H[6], zd, zf);
         }
 #pragma unroll
-        for (int c = 0; c < 7; c++) out[c * n + k] = as_double(H[c]);
+        for (int c = 0; c < 7; c++) out[c * n + k] = H[c];
     }
+}
+
+// the double-float fluxes as doubles (untimed)
+__global__ void flux_eval_widen_kernel(long long m, const df *a, double *b)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m; k += stride) b[k] = as_double(a[k]);
 }
 
 __device__ __forceinline__ void max_bits(double *dst, double v)  // v >= 0
@@ -140,25 +177,37 @@ __global__ void flux_rel_kernel(long long n, const double *a, const double *b, d
 int moses_debug_flux_eval(long long n, int reps, double *res)
 {
     moses_sim *s = nullptr;  // errors go to moses_last_error(NULL)
-    if (!res || n < 1 || n > (1ll << 24) || reps < 4 || reps > 64)
-        return fail(s, MOSES_EINVAL, "need res, 1 <= n <= 2^24 and 4 <= reps <= 64");
+    if (!res || n < 1 || n > (1ll << 22) || reps < 4 || reps > 64)
+        return fail(s, MOSES_EINVAL, "need res, 1 <= n <= 2^22 and 4 <= reps <= 64");
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    double *d = nullptr;
-    CK(cudaMalloc(&d, sizeof(double) * (14 * (size_t)n + 16)));
-    double *out64 = d, *outdf = d + 7 * n, *acc = d + 14 * n;
+    // inputs (19 planes) and fluxes (7 planes) of both types, the double-float
+    // fluxes widened to doubles, the reduction words
+    unsigned char *d = nullptr;
+    const size_t plane8 = sizeof(double) * (size_t)n;
+    CK(cudaMalloc(&d, plane8 * (2 * kFaceIn + 2 * 7 + 7) + sizeof(double) * 16));
+    double *in64 = reinterpret_cast<double *>(d);
+    df *indf = reinterpret_cast<df *>(d + plane8 * kFaceIn);
+    double *out64 = reinterpret_cast<double *>(d + plane8 * 2 * kFaceIn);
+    df *outdf = reinterpret_cast<df *>(d + plane8 * (2 * kFaceIn + 7));
+    double *wide = reinterpret_cast<double *>(d + plane8 * (2 * kFaceIn + 14));
+    double *acc = reinterpret_cast<double *>(d + plane8 * (2 * kFaceIn + 21));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const int blocks = sms * 8, threads = 256;
+    if (e == cudaSuccess) {
+        flux_eval_setup_kernel<<<blocks, threads>>>(n, in64, indf);
+        e = cudaGetLastError();
+    }
     // the fastest of three launches of `r` repetitions
-    const auto timed = [&](bool dbl, int r, double *out) -> double {
+    const auto timed = [&](bool dbl, int r) -> double {
         float best = 1e30f;
         for (int t = 0; t < 3 && e == cudaSuccess; t++) {
             cudaEventRecord(e0);
-            if (dbl) flux_eval_kernel<double><<<blocks, threads>>>(n, r, 0.0, 0.0f, out);
-            else flux_eval_kernel<df><<<blocks, threads>>>(n, r, 0.0, 0.0f, out);
+            if (dbl) flux_eval_kernel<double><<<blocks, threads>>>(n, r, 0.0, 0.0f, in64, out64);
+            else flux_eval_kernel<df><<<blocks, threads>>>(n, r, 0.0, 0.0f, indf, outdf);
             cudaEventRecord(e1);
             e = cudaEventSynchronize(e1);
             float ms = 0.0f;
@@ -167,17 +216,19 @@ int moses_debug_flux_eval(long long n, int reps, double *res)
         }
         return (double)best;
     };
-    // the flux alone: the difference of `reps` and 2 repetitions (the face
-    // generation, the conversions and the stores cancel)
-    const double t64 = timed(true, reps, out64) - timed(true, 2, out64);
-    const double tdf = timed(false, reps, outdf) - timed(false, 2, outdf);
-    timed(true, reps, out64);  // the outputs of `reps` repetitions in both buffers
-    timed(false, reps, outdf);
+    // the flux alone: the difference of `reps` and 2 repetitions (the loads
+    // and the stores cancel); the `reps` launches run last, so that both
+    // output buffers hold their results
+    const double t64_2 = timed(true, 2);
+    const double t64 = timed(true, reps) - t64_2;
+    const double tdf_2 = timed(false, 2);
+    const double tdf = timed(false, reps) - tdf_2;
     double h[15] = {};
     if (e == cudaSuccess) e = cudaMemset(acc, 0, sizeof(double) * 16);
     if (e == cudaSuccess) {
-        flux_diff_kernel<<<blocks, threads>>>(n, out64, outdf, acc);
-        flux_rel_kernel<<<blocks, threads>>>(n, out64, outdf, acc);
+        flux_eval_widen_kernel<<<blocks, threads>>>(7 * n, outdf, wide);
+        flux_diff_kernel<<<blocks, threads>>>(n, out64, wide, acc);
+        flux_rel_kernel<<<blocks, threads>>>(n, out64, wide, acc);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(h, acc, sizeof(h), cudaMemcpyDeviceToHost);
