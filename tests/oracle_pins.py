@@ -695,6 +695,58 @@ def pin_max_speed_everywhere(L=None):
     assert abs(s.max_speed() - want) < 1e-13 * want, f"solid speed {s.max_speed()} != {want}"
 
 
+def pin_max_speed_rows(L=None):
+    """The largest wave speed over a range of rows [j0, j1) (the strip of a
+    row-decomposed domain takes the CFL maximum of its own rows, Sect. 2.2):
+    with one fast cell in row r of a still fluid layer on a flat bed (speed
+    sqrt(g h)), a range holds the fast speed exactly when it holds row r,
+    the first and the last row included, and every range's maximum is the
+    largest of its rows' own."""
+    nx, ny = 7, 9
+    slow, fast = math.sqrt(G * 0.5), math.sqrt(G * 2.0)
+    for r in (0, 4, ny - 1):
+        h = np.full((ny, nx), 0.5)
+        h[r, 3] = 2.0
+        s = _sim(W.flat_dem(nx, ny), 5.0, 4.0, _pure_fluid(), L)
+        s.set_release(h, np.zeros((ny, nx)))
+        for j0 in range(ny):
+            for j1 in range(j0 + 1, ny + 1):
+                want = fast if j0 <= r < j1 else slow
+                got = s.max_speed_rows(j0, j1)
+                assert abs(got - want) < 1e-14 * want, f"rows [{j0}, {j1}) with the fast row {r}: {got} != {want}"
+        assert abs(s.max_speed_rows(0, ny) - s.max_speed()) < 1e-15 * fast
+
+
+def pin_step_amax(L=None):
+    """A step whose CFL time step comes from a given largest speed (a strip of
+    a decomposed domain steps with the whole domain's a_max, Sect. 2.2): with
+    the simulation's own a_max it is the ordinary step, bit for bit; with
+    another speed a its time step is CFL min(dx, dy) / a, and the state is the
+    step with that prescribed time step."""
+    nx, ny = 24, 16
+    cfg = W.release_config(nx=nx, ny=ny, dx=5.0)
+    dx, dy = 5.0, 4.0
+    cfl = cfg["params"]["cfl"]
+    def fresh():
+        s = _sim(cfg["dem"], dx, dy, cfg["params"], L)
+        s.set_release(cfg["h"], cfg["phi_s"])
+        s.step(3)
+        return s
+    a, b = fresh(), fresh()
+    amax = a.max_speed()
+    dt_a = a.step_amax(amax)
+    b.step(1)
+    assert np.array_equal(a.get_U(), b.get_U()) and dt_a == b.last_dt, "step_amax with the own a_max is not the step"
+    for scale in (2.0, 3.5):
+        c, d = fresh(), fresh()
+        speed = scale * c.max_speed()
+        dt_c = c.step_amax(speed)
+        want = cfl * min(dx, dy) / speed
+        assert abs(dt_c - want) < 1e-15 * want, f"dt {dt_c} != CFL min(dx, dy) / a = {want}"
+        d.step_dt(dt_c)
+        assert np.array_equal(c.get_U(), d.get_U()), "step_amax is not the step with its own time step"
+
+
 def pin_step_composition(L=None):
     """The two-step modified Euler (Sect. 2.2) and the three-stage SSP
     Runge-Kutta are convex combinations of single stages S (U + dt L(U) with
@@ -1624,7 +1676,7 @@ ALL_PINS = [
     pin_plane_equilibrium_eps, pin_lake_curved_bed_residual_converges, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
     pin_uniform_flow_viscous, pin_thin_film_has_no_velocity, pin_clamp_count,
     pin_viscous_only_where_the_fluid_is_wet, pin_thin_cell_has_no_phase_fractions, pin_budget_sums,
-    pin_friction_buoyant, pin_step_clock,
+    pin_friction_buoyant, pin_step_clock, pin_max_speed_rows, pin_step_amax,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,

@@ -225,6 +225,16 @@ MUTANTS = [
     ("earth pressure: each side with the other cell's coefficient",
      "face_flux(p, G, 0, KL, um, Fm, &asm_, &afm, &Pm, sm);\n            face_flux(p, G, 0, KR, up, Fp, &asp, &afp, &Pp, sp);",
      "face_flux(p, G, 0, KR, um, Fm, &asm_, &afm, &Pm, sm);\n            face_flux(p, G, 0, KL, up, Fp, &asp, &afp, &Pp, sp);"),
+    ("row-range speed takes row j1 too",
+     "for (int j = j0 < 0 ? 0 : j0; j < j1 && j < s->ny; j++)",
+     "for (int j = j0 < 0 ? 0 : j0; j <= j1 && j < s->ny; j++)"),
+    ("row-range speed starts one row late",
+     "for (int j = j0 < 0 ? 0 : j0; j < j1 && j < s->ny; j++)",
+     "for (int j = j0 < 0 ? 1 : j0 + 1; j < j1 && j < s->ny; j++)"),
+    ("step with a given speed ignores it",
+     "double dt = cfl_dt(s, amax);", "double dt = cfl_dt(s, max_speed(s, s->U));"),
+    ("step with a given speed doubles it",
+     "double dt = cfl_dt(s, amax);", "double dt = cfl_dt(s, 2.0 * amax);"),
 ]
 
 
