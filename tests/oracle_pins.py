@@ -390,6 +390,30 @@ def pin_drag(L=None):
     assert np.allclose(mix, mix0, rtol=1e-13, atol=1e-12 * np.abs(mix0).max()), "drag not momentum-neutral"
 
 
+def pin_drag_neutral_on_a_slope(L=None):
+    """On a 25-degree plane (J = sec 25 deg, not 1), a uniform mixture with
+    different phase velocities, transmissive sides and no basal friction: the
+    interphase drag (Eqs. Src_v_Topo, SrcF_v_Topo) moves momentum between the
+    phases and adds none to the mixture, so rho^s q^s + rho^f q^f after ten
+    steps is the same with the drag as without it, while the phases' own
+    momenta differ."""
+    nx, ny = 6, 5
+    dem = W.incline_dem(nx, ny, 5.0, 4.0, 25.0, "x")
+    one = np.ones((ny, nx))
+    runs = []
+    for cd in (0.0, 0.8):
+        p = W.default_params(c_d=cd, delta_b_deg=0.0, bc=(W.BC_TRANSMISSIVE,) * 4)
+        s = _sim(dem, 5.0, 4.0, p, L)
+        s.set_release(2.0 * one, 0.6 * one, 1.0 * one, 0.5 * one, 3.0 * one, -1.0 * one)
+        for _ in range(10):
+            s.step_dt(0.05)
+        U = s.get_U()
+        runs.append((p["rho_s"] * U[1:3] + p["rho_f"] * U[4:6], U[1:3].copy()))
+    (m0, q0), (m1, q1) = runs
+    assert np.abs(q1 - q0).max() > 1e-3 * np.abs(q0).max(), "the drag changed nothing"
+    assert np.allclose(m1, m0, rtol=1e-12, atol=1e-12 * np.abs(m0).max()), "drag not momentum-neutral on a slope"
+
+
 # ----------------------------------------------------------------------------
 # wave speeds and the CFL time step (Sect. 2.2; reading R7)
 
@@ -594,6 +618,19 @@ def pin_positivity_clamp(L=None):
         b = s.budget()
         assert b["clamp_f"] > 0.0 and b["clamp_cells"] >= 1, "no clamp counted"
         assert abs(b["vol_f"] - v0 - b["clamp_f"]) < 1e-12 * v0, f"rk {rk}: volume budget does not close with the clamp"
+    # the solid phase too, on cells with dx != dy (a clamped volume is a depth times dx dy)
+    p = _pure_solid(bc=(0, 0, 0, 0), delta_b_deg=0.0)
+    s = _sim(W.flat_dem(nx, ny), 5.0, 4.0, p, L)
+    h = np.zeros((ny, nx))
+    h[6, 7] = 0.8
+    vx = np.zeros((ny, nx))
+    vx[6, 7] = 2.0
+    s.set_release(h, np.ones((ny, nx)), vx_s=vx)
+    v0 = s.budget()["vol_s"]
+    s.step_dt(2.0 * 5.0 / (2.0 + math.sqrt(G * 0.8)))
+    b = s.budget()
+    assert s.get_U()[0].min() >= 0.0 and b["clamp_s"] > 0.0, "no solid clamp"
+    assert abs(b["vol_s"] - v0 - b["clamp_s"]) < 1e-12 * v0, "solid volume budget does not close with the clamp"
 
 
 def pin_rotation_transmissive(L=None, steps=30):
@@ -1676,7 +1713,7 @@ ALL_PINS = [
     pin_plane_equilibrium_eps, pin_lake_curved_bed_residual_converges, pin_step_composition, pin_phase_symmetry, pin_inflow_mirror,
     pin_uniform_flow_viscous, pin_thin_film_has_no_velocity, pin_clamp_count,
     pin_viscous_only_where_the_fluid_is_wet, pin_thin_cell_has_no_phase_fractions, pin_budget_sums,
-    pin_friction_buoyant, pin_step_clock, pin_max_speed_rows, pin_step_amax,
+    pin_friction_buoyant, pin_step_clock, pin_max_speed_rows, pin_step_amax, pin_drag_neutral_on_a_slope,
     pin_geometry_plane, pin_curvature, pin_conservation_closed, pin_lake_flat, pin_lake_plane,
     pin_mixture_plane_rest, pin_mixture_no_separation, pin_heap_rest, pin_ritter, pin_savage_hutter, pin_drag,
     pin_wave_speed, pin_rotation, pin_inflow, pin_friction, pin_closed_box, pin_viscous, pin_fluid_friction,
