@@ -8,6 +8,7 @@ the oracle.  Nothing here touches a GPU.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import os
 import subprocess
 import tempfile
@@ -285,27 +286,37 @@ MUTANTS = [
 ]
 
 
-@pytest.fixture(scope="module")
-def tmpdir_mod():
-    with tempfile.TemporaryDirectory() as d:
-        yield d
-
-
-def _build_mutant(src_text: str, old: str, new: str, path: str):
+def _compile_mutant(src_text: str, old: str, new: str, path: str) -> str:
     assert src_text.count(old) >= 1, f"mutation anchor not found: {old}"
     text = src_text.replace(old, new, 1)
     c = path + ".c"
     with open(c, "w") as f:
         f.write(text)
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", path, c, "-lm"])
-    return O.load(path)
+    return path
+
+
+def _build_mutant(src_text: str, old: str, new: str, path: str):
+    return O.load(_compile_mutant(src_text, old, new, path))
+
+
+@pytest.fixture(scope="module")
+def mutant_libs():
+    """Every planted mistake compiled up front on all host cores (the
+    compilations are independent; the pins then run on one mutant at a
+    time)."""
+    src = open(SRC).read()
+    with tempfile.TemporaryDirectory() as d:
+        with cf.ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+            futs = {what: ex.submit(_compile_mutant, src, old, new, os.path.join(d, f"mut{k}.so"))
+                    for k, (what, old, new) in enumerate(MUTANTS)}
+            paths = {what: f.result() for what, f in futs.items()}
+        yield paths
 
 
 @pytest.mark.parametrize("what,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_mutant_is_caught(what, old, new, tmpdir_mod):
-    src = open(SRC).read()
-    path = os.path.join(tmpdir_mod, f"mut{abs(hash(what)) % 10**8}.so")
-    L = _build_mutant(src, old, new, path)
+def test_mutant_is_caught(what, old, new, mutant_libs):
+    L = O.load(mutant_libs[what])
     failed = []
     for pin in P.ALL_PINS:
         try:
